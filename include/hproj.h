@@ -1,0 +1,138 @@
+/*
+ * hproj.h - C ABI of the GB300 (sm_103a) pressure-projection library.
+ *
+ * The library computes the pressure-projection step of the hybrid
+ * CNN + Jacobi incompressible solver of arXiv 2109.09363 on 2D staggered
+ * (MAC) grids with a boolean obstacle field:
+ *   - corrected velocity  u = u* - (dt / rho0) grad p              (Eq. 2)
+ *   - Poisson equation    (dt / rho0) lap p = div u*               (Eq. 3)
+ *   - Jacobi iteration    X_{t+1} = D^{-1} (b - (L + U) X_t)       (Sec. 2.2)
+ *   - stop test on E_1 = mean |div u| against a user threshold     (Sec. 3.3, Sec. 4.1)
+ *
+ * Grid conventions (every array is row-major and contiguous, batch first):
+ *   cell (i, j): i = column, j = row, row 0 is the top of the image.
+ *   u     float [B][ny][nx+1]  face (j, i) between cells (i-1, j) and (i, j)
+ *   v     float [B][ny+1][nx]  face (j, i) between cells (i, j-1) and (i, j)
+ *   flags uint8 [B][ny][nx]    non-zero = solid cell
+ *   p, div, rho float [B][ny][nx]
+ *   A face is open when it is not on the domain boundary and both adjacent
+ *   cells are fluid; closed faces carry zero velocity (static walls).
+ *   phi = (dt / rho0) p is the scaled pressure; the sweeps work on phi.
+ *   E_1 divides by all nx * ny cells; solid cells have zero divergence.
+ *
+ * Memory: every array pointer is caller-owned DEVICE memory unless stated
+ * otherwise.  Calls are asynchronous and ordered on the given CUDA stream
+ * (passed as void*; NULL = legacy default stream); nothing synchronises the
+ * host unless stated.  All calls of one context must be issued from one host
+ * thread at a time, on one stream at a time.
+ *
+ * Errors: argument errors are returned immediately and nothing is launched.
+ * HP_ERR_CUDA reports a failed launch or CUDA call; hp_last_cuda_error()
+ * gives the CUDA error string.  There is no CPU fallback: a process without a
+ * usable sm_103a device gets HP_ERR_CUDA from hp_ctx_create.
+ */
+#ifndef HPROJ_H
+#define HPROJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HP_OK = 0,
+    HP_ERR_INVALID_ARG = 1, /* null pointer, bad shape, shape above the context maximum */
+    HP_ERR_CUDA = 2,        /* a CUDA call or launch failed */
+    HP_ERR_NONFINITE = 3,   /* the input velocity holds NaN or Inf */
+    HP_ERR_OOM = 5,         /* device allocation failed */
+    HP_ERR_UNSUPPORTED = 6  /* the requested combination is not built */
+} hp_status;
+
+typedef struct {
+    int32_t batch; /* number of independent grids B */
+    int32_t ny;    /* rows */
+    int32_t nx;    /* columns */
+} hp_shape;
+
+/* Parameters of one projection (Sec. 2.2 and 3.3).
+ *   threshold      E_t: stop at the first k with E_1(phi_k) <= E_t (k = 0 included)
+ *   max_iters      cap on the number of sweeps; reaching it gives converged = 0
+ *   fixed_iters    > 0: run exactly this many sweeps, no stop test (converged = 1)
+ *   dt, rho0       p = phi * rho0 / dt
+ *   temporal_block sweeps fused per launch, 1..8 (0 = library default)
+ *   use_graph      1 = run the sweep loop as a CUDA-graph conditional WHILE node
+ *                  (no host round trip per block); 0 = host-polled loop */
+typedef struct {
+    double threshold;
+    int32_t max_iters;
+    int32_t fixed_iters;
+    float dt;
+    float rho0;
+    int32_t temporal_block;
+    int32_t use_graph;
+} hp_project_params;
+
+typedef struct hp_ctx hp_ctx;
+
+/* Create a context on `device` that owns the workspaces for grids up to
+ * max_shape (cells = batch * ny * nx).  Allocates device memory once; no later
+ * call allocates.  Returns HP_ERR_CUDA when the device is missing or is not
+ * sm_103. */
+hp_status hp_ctx_create(hp_ctx **ctx, hp_shape max_shape, int device);
+void hp_ctx_destroy(hp_ctx *ctx);
+
+const char *hp_status_string(hp_status s);
+const char *hp_last_cuda_error(void);
+
+/* Open-face bits per cell (a geometry step of Sec. 2.2): bit 0 west (u face i),
+ * bit 1 east (u face i+1), bit 2 north (v face j), bit 3 south (v face j+1).
+ * flags, mask_out: uint8 [B][ny][nx], device. */
+hp_status hp_face_mask(const uint8_t *flags, uint8_t *mask_out, hp_shape shape, void *stream);
+
+/* Divergence of u* (right-hand side of Eq. 3), first-order forward difference
+ * over the OPEN faces, dx = 1; div = 0 on solid cells.  u, v are read only
+ * (closed-face values are ignored).  div_out: float [B][ny][nx], device. */
+hp_status hp_divergence(const float *u, const float *v, const uint8_t *flags, float *div_out,
+                        hp_shape shape, void *stream);
+
+/* Mean and max of |div u| over all cells per grid (E_1 and E_inf of Sec. 4.1),
+ * divergence over open faces as in hp_divergence.  e1_out, einf_out: double
+ * [B], device.  Uses the context's workspaces (no allocation). */
+hp_status hp_div_norms(hp_ctx *ctx, const float *u, const float *v, const uint8_t *flags,
+                       double *e1_out, double *einf_out, hp_shape shape, void *stream);
+
+/* Pressure projection (Eq. 2-3, hybrid rule of Sec. 3.3), in place on (u, v).
+ *   1. div = div u*  over open faces;
+ *   2. phi_0 = phi0 (the CNN guess of the hybrid method; NULL = 0), set to 0
+ *      on cells without an open face;
+ *   3. k* = first k with E_1(phi_k) <= threshold, else max_iters; the sweeps
+ *      are masked Jacobi on the open-face Laplacian, E_1 is summed in FP64
+ *      after every sweep in a fixed order;
+ *   4. u = u* - grad phi on open faces, 0 on closed faces; p = phi rho0 / dt.
+ * Outputs (device): p_out float [B][ny][nx] (may be NULL), iters_out int32 [B],
+ * e1_out / einf_out double [B] (norms of the CORRECTED velocity; may be NULL),
+ * converged_out uint8 [B] (may be NULL).
+ * phi0: float [B][ny][nx] device or NULL.
+ * e_hist: optional double [B][hist_len] device; receives E_1(phi_k) for
+ * k < hist_len up to the stop (entries after the stop are left untouched).
+ * Uses the context's workspaces; calls on one context must not overlap. */
+hp_status hp_project(hp_ctx *ctx, float *u, float *v, const uint8_t *flags, hp_shape shape,
+                     const hp_project_params *params, const float *phi0, float *p_out,
+                     int32_t *iters_out, double *e1_out, double *einf_out,
+                     uint8_t *converged_out, double *e_hist, int32_t hist_len, void *stream);
+
+/* Jacobi sweeps only (the inner step of hp_project): phi_out = n sweeps of the
+ * masked Jacobi iteration applied to phi_in with right-hand side div (both
+ * device float [B][ny][nx]).  e_out (device double [B][n], may be NULL)
+ * receives E_1(phi_k) of the input of each sweep.  phi_in and phi_out must not
+ * alias.  Uses the context's workspaces. */
+hp_status hp_jacobi_sweeps(hp_ctx *ctx, const float *phi_in, const float *div,
+                           const uint8_t *flags, float *phi_out, int32_t n, double *e_out,
+                           hp_shape shape, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPROJ_H */

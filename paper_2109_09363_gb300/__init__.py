@@ -1,0 +1,244 @@
+"""GB300 (sm_103a) pressure projection of the hybrid CNN + Jacobi solver of
+arXiv 2109.09363: Python binding of the C ABI declared in ``include/hproj.h``.
+
+This module only marshals arguments: every step of the projection runs in the
+CUDA kernels of ``libhproj.so``.  Arrays are torch tensors on the CUDA device
+(PyTorch supplies device memory and the current stream); the functions keep
+the names of the C entry points.  There is no CPU fallback: without the built
+library or without a GB300 device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhproj.so")
+
+_lib = None
+
+
+class HprojError(RuntimeError):
+    pass
+
+
+class hp_shape(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("ny", ctypes.c_int32), ("nx", ctypes.c_int32)]
+
+
+class hp_project_params(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("fixed_iters", ctypes.c_int32), ("dt", ctypes.c_float), ("rho0", ctypes.c_float),
+                ("temporal_block", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "hp_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
+    "hp_ctx_destroy": (None, [_P]),
+    "hp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hp_last_cuda_error": (ctypes.c_char_p, []),
+    "hp_face_mask": (ctypes.c_int, [_P, _P, hp_shape, _P]),
+    "hp_divergence": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, _P]),
+    "hp_div_norms": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, hp_shape, _P]),
+    "hp_project": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.POINTER(hp_project_params),
+                                  _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    "hp_jacobi_sweeps": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P, hp_shape, _P]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhproj.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise HprojError(f"{path} is missing: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        lib = load_library()
+        msg = lib.hp_status_string(rc).decode()
+        err = lib.hp_last_cuda_error().decode()
+        raise HprojError(f"hproj status {rc} ({msg}) {err}")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise HprojError("hproj takes CUDA tensors only")
+    if not t.is_contiguous():
+        raise HprojError("hproj takes contiguous tensors only")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _shape_of_flags(flags):
+    if flags.dim() != 3:
+        raise HprojError("flags must be [B][ny][nx]")
+    B, ny, nx = flags.shape
+    return hp_shape(B, ny, nx)
+
+
+def _check_dtype(t, dtype, shape, name):
+    if t is None:
+        return
+    if t.dtype != dtype:
+        raise HprojError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise HprojError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class Context:
+    """Workspaces for grids up to (batch, ny, nx); owns device memory."""
+
+    def __init__(self, batch: int, ny: int, nx: int, device: int | None = None):
+        torch = _torch()
+        lib = load_library()
+        dev = torch.cuda.current_device() if device is None else device
+        self.device = dev
+        self._h = _P()
+        _check(lib.hp_ctx_create(ctypes.byref(self._h), hp_shape(batch, ny, nx), dev))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load_library().hp_ctx_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class ProjectParams:
+    threshold: float = 1e-3
+    max_iters: int = 2000
+    fixed_iters: int = 0
+    dt: float = 1.0
+    rho0: float = 1.0
+    temporal_block: int = 0
+    use_graph: int = 1
+
+    def c(self):
+        return hp_project_params(self.threshold, self.max_iters, self.fixed_iters, self.dt,
+                                 self.rho0, self.temporal_block, self.use_graph)
+
+
+def hp_face_mask(flags, mask_out=None, stream=None):
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    _check_dtype(flags, torch.uint8, flags.shape, "flags")
+    if mask_out is None:
+        mask_out = torch.empty_like(flags)
+    _check(load_library().hp_face_mask(_ptr(flags), _ptr(mask_out), s, _stream(stream)))
+    return mask_out
+
+
+def hp_divergence(u, v, flags, div_out=None, stream=None):
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(u, torch.float32, (B, ny, nx + 1), "u")
+    _check_dtype(v, torch.float32, (B, ny + 1, nx), "v")
+    if div_out is None:
+        div_out = torch.empty((B, ny, nx), dtype=torch.float32, device=u.device)
+    _check(load_library().hp_divergence(_ptr(u), _ptr(v), _ptr(flags), _ptr(div_out), s,
+                                        _stream(stream)))
+    return div_out
+
+
+def hp_div_norms(ctx: Context, u, v, flags, stream=None):
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(u, torch.float32, (B, ny, nx + 1), "u")
+    _check_dtype(v, torch.float32, (B, ny + 1, nx), "v")
+    e1 = torch.empty(B, dtype=torch.float64, device=u.device)
+    einf = torch.empty(B, dtype=torch.float64, device=u.device)
+    _check(load_library().hp_div_norms(ctx.handle, _ptr(u), _ptr(v), _ptr(flags), _ptr(e1),
+                                       _ptr(einf), s, _stream(stream)))
+    return e1, einf
+
+
+def hp_project(ctx: Context, u, v, flags, params: ProjectParams, phi0=None, p_out=None,
+               hist_len: int = 0, stream=None, out=None):
+    """Project (u, v) in place; returns a dict of device tensors
+    p, iters, e1, einf, converged (and e_hist when hist_len > 0)."""
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(u, torch.float32, (B, ny, nx + 1), "u")
+    _check_dtype(v, torch.float32, (B, ny + 1, nx), "v")
+    _check_dtype(phi0, torch.float32, (B, ny, nx), "phi0")
+    dev = u.device
+    if out is None:
+        out = {
+            "p": p_out if p_out is not None else torch.empty((B, ny, nx), dtype=torch.float32,
+                                                             device=dev),
+            "iters": torch.empty(B, dtype=torch.int32, device=dev),
+            "e1": torch.empty(B, dtype=torch.float64, device=dev),
+            "einf": torch.empty(B, dtype=torch.float64, device=dev),
+            "converged": torch.empty(B, dtype=torch.uint8, device=dev),
+        }
+        if hist_len > 0:
+            out["e_hist"] = torch.full((B, hist_len), float("nan"), dtype=torch.float64,
+                                       device=dev)
+    prm = params.c()
+    hist = out.get("e_hist")
+    _check(load_library().hp_project(
+        ctx.handle, _ptr(u), _ptr(v), _ptr(flags), s, ctypes.byref(prm), _ptr(phi0),
+        _ptr(out["p"]), _ptr(out["iters"]), _ptr(out["e1"]), _ptr(out["einf"]),
+        _ptr(out["converged"]), _ptr(hist), ctypes.c_int32(hist.shape[1] if hist is not None
+                                                           else 0), _stream(stream)))
+    return out
+
+
+def hp_jacobi_sweeps(ctx: Context, phi_in, div, flags, n: int, phi_out=None, with_e=False,
+                     stream=None):
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(phi_in, torch.float32, (B, ny, nx), "phi_in")
+    _check_dtype(div, torch.float32, (B, ny, nx), "div")
+    if phi_out is None:
+        phi_out = torch.empty_like(phi_in)
+    e = torch.empty((B, n), dtype=torch.float64, device=phi_in.device) if with_e else None
+    _check(load_library().hp_jacobi_sweeps(ctx.handle, _ptr(phi_in), _ptr(div), _ptr(flags),
+                                           _ptr(phi_out), ctypes.c_int32(n), _ptr(e), s,
+                                           _stream(stream)))
+    return (phi_out, e) if with_e else phi_out
+
+
+def exported_symbols():
+    """Names of the functions declared in include/hproj.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(HERE, "..", "include", "hproj.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:hp_status|void|const char \*)\s*(hp_\w+)\s*\(", txt,
+                                 re.M)))

@@ -1,0 +1,110 @@
+// Internal declarations of the GB300 projection library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hproj.h"
+
+namespace hp {
+
+// Maximum sweeps fused into one launch of the temporally blocked sweep kernel;
+// it is also the halo width of a tile (a multiple of 4 so that tiles stay
+// 16-byte aligned).
+constexpr int kMaxBlock = 8;
+
+// Sweep tile: 16 warps, each thread holds 4 rows x 4 columns in registers, so
+// one CTA covers 64 rows x 128 columns including the halo.
+constexpr int kTileWarps = 16;
+constexpr int kTileRows = 4 * kTileWarps;  // 64
+constexpr int kTileCols = 128;
+
+// Per-grid state of one projection, device resident.
+struct GridState {
+    int32_t active;      // 1 while the grid still sweeps
+    int32_t kstar;       // stop index k*
+    int32_t k0_stop;     // first sweep index of the block in which k* fell
+    int32_t replay;      // sweeps to replay from buffer `src` to reach k*
+    int32_t src;         // buffer holding phi_{k0_stop}
+    int32_t final_buf;   // buffer holding phi_{k*}
+    int32_t converged;   // 1 when E(phi_{k*}) <= threshold
+    int32_t pad_;
+    double e_stop;       // E(phi_{k*})
+    uint32_t arrivals;   // CTA arrival counter of the current launch
+    uint32_t einf_bits;  // max |div| of the corrected velocity (float bits)
+};
+
+// Loop state shared by all grids.
+struct LoopState {
+    int32_t k0;          // first sweep index of the current block
+    int32_t blk;         // block counter; parity selects the phi buffers
+    uint32_t arrivals;   // CTA arrival counter of the whole launch
+    int32_t any_active;  // 1 while some grid still sweeps
+};
+
+struct SweepArgs {
+    float* phi0;                 // ping-pong buffers [B][ny][nx]
+    float* phi1;
+    const float* div;            // [B][ny][nx]
+    const uint8_t* mask;         // open-face bits [B][ny][nx]
+    GridState* gs;               // [B]
+    LoopState* ls;
+    double* partial;             // [B][kMaxBlock][ctas per grid]
+    double* e_hist;              // [B][hist_len] or null
+    int32_t hist_len;
+    int32_t B, ny, nx;
+    int32_t T;                   // sweeps per launch (<= kMaxBlock)
+    int32_t max_iters;
+    double threshold;            // < 0 never stops before the cap
+    int32_t mode;                // 0 = loop block, 1 = replay
+    unsigned long long cond;     // CUDA-graph conditional handle (0 = none)
+};
+
+}  // namespace hp
+
+struct hp_ctx {
+    int device;
+    hp_shape max_shape;
+    size_t max_cells;
+    uint8_t* mask;
+    float* div;
+    float* phi[2];
+    double* partial;
+    size_t partial_len;
+    double* partial2;
+    size_t partial2_len;
+    hp::GridState* gs;
+    hp::LoopState* ls;
+    int32_t* host_flag;  // pinned
+    // cached conditional-graph loop
+    cudaGraphExec_t graph_exec;
+    hp_shape graph_shape;
+    int graph_T;
+    int graph_hist;
+    double* graph_hist_ptr;
+    double graph_threshold;
+    int graph_max_iters;
+};
+
+namespace hp {
+
+void set_cuda_error(cudaError_t e);
+hp_status check_launch();
+bool shape_ok(hp_shape s);
+
+// kernels launched from the API layer
+hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
+                          float* div, hp_shape s, cudaStream_t st);
+hp_status launch_mask(const uint8_t* flags, uint8_t* mask, hp_shape s, cudaStream_t st);
+hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
+                           double* partial, int nblk_cap, GridState* gs, double* e1,
+                           double* einf, hp_shape s, cudaStream_t st);
+hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp_shape s,
+                       const hp_project_params* prm, const float* phi0, float* p_out,
+                       int32_t* iters_out, double* e1_out, double* einf_out,
+                       uint8_t* conv_out, double* e_hist, int32_t hist_len, cudaStream_t st,
+                       float* phi_copy_out);
+
+int ctas_per_grid(int ny, int nx, int T);
+
+}  // namespace hp

@@ -1,0 +1,739 @@
+// Pressure-projection kernels for sm_103a: face mask + divergence, temporally
+// blocked masked Jacobi sweeps with a fused per-sweep E_1 reduction and an
+// exact stop rule, correction, divergence norms.
+//
+// Method (arXiv 2109.09363): corrected velocity u = u* - (dt/rho0) grad p
+// (Eq. 2); Poisson equation (dt/rho0) lap p = div u* (Eq. 3); Jacobi iteration
+// X_{t+1} = D^{-1}(b - (L+U) X_t) (Sec. 2.2); stop when E_1 = mean |div u| is
+// at or below the user threshold (Sec. 3.3 and 4.1).
+//
+// The sweep is written in increment form on phi = (dt/rho0) p:
+//   r_c    = div_c - sum_open (phi_nb - phi_c)      (residual of phi_k)
+//   phi'_c = phi_c - r_c / n_c                      (= Jacobi update)
+// Solid cells and cells outside the grid hold phi = 0, so the sum over the four
+// neighbours only has to remove the closed faces: with c = 4 - n_c,
+//   sum_open (phi_nb - phi_c) = sum_all4 (phi_nb - phi_c) + c * phi_c.
+// Differences of neighbouring values are formed first, which keeps the FP32
+// residual accurate to the size of the pressure gradient rather than of the
+// pressure itself.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+
+#include "hproj_internal.cuh"
+
+namespace hp {
+
+// ------------------------------------------------------------ cell update
+
+// Per-cell constants derived from the open-face bits m:
+//   inv = 1/n (0 when n = 0), c = 4 - n, w = (n > 0).
+struct CellConst {
+    float d, inv, c, w;
+};
+
+__device__ __forceinline__ CellConst make_const(float d, uint32_t m)
+{
+    const int n = __popc(m & 15u);
+    CellConst k;
+    k.d = d;
+    k.inv = n == 4 ? 0.25f : n == 3 ? (1.0f / 3.0f) : n == 2 ? 0.5f : n == 1 ? 1.0f : 0.0f;
+    k.c = (float)(4 - n);
+    k.w = n > 0 ? 1.0f : 0.0f;
+    return k;
+}
+
+// One Jacobi update of one cell; returns phi' and writes the residual of phi.
+// Every operation is an explicitly rounded intrinsic so that all kernels that
+// use it produce bit-identical iterates.
+__device__ __forceinline__ float cell_update(float pc, float pw, float pe, float pn, float ps,
+                                             const CellConst& k, float& res)
+{
+    const float dw = __fsub_rn(pw, pc);
+    const float de = __fsub_rn(pe, pc);
+    const float dn = __fsub_rn(pn, pc);
+    const float ds = __fsub_rn(ps, pc);
+    const float lapd = __fadd_rn(__fadd_rn(dw, de), __fadd_rn(dn, ds));
+    const float lap = __fmaf_rn(k.c, pc, lapd);
+    const float r = __fmaf_rn(-k.w, lap, k.d);
+    res = r;
+    return __fmaf_rn(-r, k.inv, pc);
+}
+
+// --------------------------------------------------------- mask + divergence
+
+// One thread per cell.  mask (optional) receives the open-face bits, div
+// (optional) the forward-difference divergence over open faces (Eq. 3).
+__global__ void mask_div_kernel(const float* __restrict__ u, const float* __restrict__ v,
+                                const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask,
+                                float* __restrict__ div, int ny, int nx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
+    if (i >= nx) return;
+    const uint8_t* fl = flags + (size_t)b * ny * nx;
+    const size_t c = (size_t)j * nx + i;
+    uint32_t m = 0;
+    if (fl[c] == 0) {
+        if (i > 0 && fl[c - 1] == 0) m |= 1u;
+        if (i < nx - 1 && fl[c + 1] == 0) m |= 2u;
+        if (j > 0 && fl[c - nx] == 0) m |= 4u;
+        if (j < ny - 1 && fl[c + nx] == 0) m |= 8u;
+    }
+    if (mask) mask[(size_t)b * ny * nx + c] = (uint8_t)m;
+    if (div) {
+        const float* ub = u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1);
+        const float* vb = v + (size_t)b * (ny + 1) * nx;
+        const float ue = (m & 2u) ? ub[i + 1] : 0.0f;
+        const float uw = (m & 1u) ? ub[i] : 0.0f;
+        const float vs = (m & 8u) ? vb[(size_t)(j + 1) * nx + i] : 0.0f;
+        const float vn = (m & 4u) ? vb[(size_t)j * nx + i] : 0.0f;
+        div[(size_t)b * ny * nx + c] = __fadd_rn(__fsub_rn(ue, uw), __fsub_rn(vs, vn));
+    }
+}
+
+hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
+                          float* div, hp_shape s, cudaStream_t st)
+{
+    dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
+    mask_div_kernel<<<grd, blk, 0, st>>>(u, v, flags, mask, div, s.ny, s.nx);
+    return check_launch();
+}
+
+hp_status launch_mask(const uint8_t* flags, uint8_t* mask, hp_shape s, cudaStream_t st)
+{
+    return launch_mask_div(nullptr, nullptr, flags, mask, nullptr, s, st);
+}
+
+// ------------------------------------------------------------- state reset
+
+__global__ void reset_state_kernel(GridState* gs, LoopState* ls, int B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) {
+        GridState g = {};
+        g.active = 1;
+        gs[b] = g;
+    }
+    if (b == 0) {
+        LoopState l = {};
+        l.any_active = 1;
+        *ls = l;
+    }
+}
+
+// phi_0 = given guess on cells with an open face, else 0.
+__global__ void init_phi_kernel(const float* __restrict__ phi0, const uint8_t* __restrict__ mask,
+                                float* __restrict__ out, size_t cells)
+{
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= cells) return;
+    out[q] = (phi0 && (mask[q] & 15u)) ? phi0[q] : 0.0f;
+}
+
+// ----------------------------------------------------- blocked Jacobi sweeps
+
+template <int H>
+struct TileGeom {
+    static constexpr int OW = kTileCols - 2 * H;  // owned columns per tile
+    static constexpr int OH = kTileRows - 2 * H;  // owned rows per tile
+};
+
+int ctas_x(int nx, int H) { return (nx + (kTileCols - 2 * H) - 1) / (kTileCols - 2 * H); }
+int ctas_y(int ny, int H) { return (ny + (kTileRows - 2 * H) - 1) / (kTileRows - 2 * H); }
+int halo_for(int T) { return T <= 4 ? 4 : 8; }
+int ctas_per_grid(int ny, int nx, int T)
+{
+    const int H = halo_for(T);
+    return ctas_x(nx, H) * ctas_y(ny, H);
+}
+
+// Loads four consecutive cells of a row (float), zero outside [0, nx).
+__device__ __forceinline__ void load_row4(const float* __restrict__ row, int x0, int nx, bool vec,
+                                          float out[4])
+{
+    if (vec && x0 >= 0 && x0 + 3 < nx) {
+        const float4 t = *reinterpret_cast<const float4*>(row + x0);
+        out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int x = x0 + q;
+            out[q] = (x >= 0 && x < nx) ? row[x] : 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t load_mask4(const uint8_t* __restrict__ row, int x0, int nx,
+                                               bool vec)
+{
+    if (vec && x0 >= 0 && x0 + 3 < nx) return *reinterpret_cast<const uint32_t*>(row + x0);
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int x = x0 + q;
+        if (x >= 0 && x < nx) m |= (uint32_t)row[x] << (8 * q);
+    }
+    return m;
+}
+
+// Called by the last CTA of grid b after all its CTAs wrote their per-sweep
+// partial sums: E_k for the sweeps of this launch, stop decision.
+__device__ void grid_decide(const SweepArgs& a, int b, int T, int k0, int src, int nct)
+{
+    __shared__ double s_e[kMaxBlock];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double inv_cells = 1.0 / ((double)a.nx * (double)a.ny);
+    if (wid < T) {
+        const double* p = a.partial + ((size_t)b * kMaxBlock + wid) * nct;
+        double s = 0.0;
+        for (int i = lane; i < nct; i += 32) s += __ldcg(p + i);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) s_e[wid] = s * inv_cells;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        GridState* g = a.gs + b;
+        int stop = -1, conv = 0;
+        for (int t = 0; t < T; ++t) {
+            const int k = k0 + t;
+            const double e = s_e[t];
+            if (a.e_hist && k < a.hist_len) a.e_hist[(size_t)b * a.hist_len + k] = e;
+            if (e <= a.threshold) { stop = t; conv = 1; break; }
+            if (k >= a.max_iters) { stop = t; conv = 0; break; }
+        }
+        if (stop >= 0) {
+            g->active = 0;
+            g->kstar = k0 + stop;
+            g->k0_stop = k0;
+            g->replay = stop;
+            g->src = src;
+            g->final_buf = stop > 0 ? (src ^ 1) : src;
+            g->converged = conv;
+            g->e_stop = s_e[stop];
+        }
+        g->arrivals = 0u;
+        __threadfence();
+    }
+}
+
+// Called by the last CTA of the whole launch: advance the block counter and
+// decide whether another block is needed.  The loop is bounded: once k0 is
+// past max_iters + kMaxBlock nothing can still be active, and the flag is
+// cleared regardless.
+__device__ void launch_finish(const SweepArgs& a, int T)
+{
+    int any = 0;
+    for (int b = threadIdx.x; b < a.B; b += blockDim.x) any |= __ldcg(&a.gs[b].active);
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        LoopState* ls = a.ls;
+        const int k0n = ls->k0 + T;
+        if (k0n > a.max_iters + kMaxBlock) any = 0;
+        ls->k0 = k0n;
+        ls->blk = ls->blk + 1;
+        ls->arrivals = 0u;
+        ls->any_active = any;
+        __threadfence();
+        if (a.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, any ? 1u : 0u);
+    }
+}
+
+__device__ __forceinline__ void launch_arrive(const SweepArgs& a, int T)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t total = gridDim.x * gridDim.y * gridDim.z;
+        s_last = atomicAdd(&a.ls->arrivals, 1u) == total - 1u;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) launch_finish(a, T);
+}
+
+// Temporally blocked sweep kernel.  Each CTA owns an (OH x OW) block of cells
+// and loads it with a halo of H cells into registers: thread (warp w, lane l)
+// holds rows 4w..4w+3 and columns 4l..4l+3 of the 64 x 128 tile.  Horizontal
+// neighbours come from warp shuffles, vertical neighbours across warps from a
+// double-buffered shared-memory row exchange (one barrier per sweep).  After T
+// sweeps (T <= H) the owned cells are exact; the halo cells are discarded.
+//
+// mode 0 (loop block): sweeps k0..k0+T-1 of every active grid, per-sweep
+//   residual partial sums, stop decision by the last CTA of each grid, block
+//   counter advance by the last CTA of the launch.
+// mode 1 (replay): gs[b].replay sweeps from buffer gs[b].src into the other
+//   buffer, no reduction.
+template <int H>
+__global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs a)
+{
+    constexpr int OW = TileGeom<H>::OW;
+    constexpr int OH = TileGeom<H>::OH;
+    __shared__ float4 s_top[2][kTileWarps][32];
+    __shared__ float4 s_bot[2][kTileWarps][32];
+    __shared__ float s_wsum[kMaxBlock][kTileWarps];
+
+    const int b = blockIdx.z;
+    GridState* g = a.gs + b;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+    int T, src, k0 = 0;
+    if (a.mode == 0) {
+        if (!g->active) {
+            launch_arrive(a, a.T);
+            return;
+        }
+        T = a.T;
+        k0 = a.ls->k0;
+        src = a.ls->blk & 1;
+    } else {
+        T = g->replay;
+        src = g->src;
+        if (T <= 0) return;
+    }
+    const int nx = a.nx, ny = a.ny;
+    const size_t gbase = (size_t)b * ny * nx;
+    const float* __restrict__ pin = (src ? a.phi1 : a.phi0) + gbase;
+    float* __restrict__ pout = (src ? a.phi0 : a.phi1) + gbase;
+    const float* __restrict__ dv = a.div + gbase;
+    const uint8_t* __restrict__ mk = a.mask + gbase;
+    const bool vec = (nx & 3) == 0;
+
+    const int x0 = blockIdx.x * OW - H + 4 * lane;
+    const int y0 = blockIdx.y * OH - H + 4 * wid;
+
+    float phi[4][4];
+    CellConst kc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int y = y0 + r;
+        if (y >= 0 && y < ny) {
+            float dd[4];
+            load_row4(pin + (size_t)y * nx, x0, nx, vec, phi[r]);
+            load_row4(dv + (size_t)y * nx, x0, nx, vec, dd);
+            const uint32_t m4 = load_mask4(mk + (size_t)y * nx, x0, nx, vec);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) kc[r][q] = make_const(dd[q], (m4 >> (8 * q)) & 0xffu);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                phi[r][q] = 0.0f;
+                kc[r][q] = make_const(0.0f, 0u);
+            }
+        }
+    }
+
+    const bool own = lane >= H / 4 && lane < 32 - H / 4 && wid >= H / 4 && wid < kTileWarps - H / 4;
+
+    for (int t = 0; t < T; ++t) {
+        const int p = t & 1;
+        s_top[p][wid][lane] = make_float4(phi[0][0], phi[0][1], phi[0][2], phi[0][3]);
+        s_bot[p][wid][lane] = make_float4(phi[3][0], phi[3][1], phi[3][2], phi[3][3]);
+        __syncthreads();
+        const float4 nb = wid > 0 ? s_bot[p][wid - 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 sb =
+            wid < kTileWarps - 1 ? s_top[p][wid + 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float up[4] = {nb.x, nb.y, nb.z, nb.w};
+        const float south[4] = {sb.x, sb.y, sb.z, sb.w};
+        float acc = 0.0f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float left = __shfl_up_sync(0xffffffffu, phi[r][3], 1);
+            const float right = __shfl_down_sync(0xffffffffu, phi[r][0], 1);
+            float nw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float pw = q > 0 ? phi[r][q - 1] : left;
+                const float pe = q < 3 ? phi[r][q + 1] : right;
+                const float ps = r < 3 ? phi[r + 1][q] : south[q];
+                float res;
+                nw[q] = cell_update(phi[r][q], pw, pe, up[q], ps, kc[r][q], res);
+                acc = __fadd_rn(acc, fabsf(res));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                up[q] = phi[r][q];
+                phi[r][q] = nw[q];
+            }
+        }
+        if (a.mode == 0) {
+            if (!own) acc = 0.0f;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+            if (lane == 0) s_wsum[t][wid] = acc;
+        }
+    }
+
+    if (own) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int y = y0 + r;
+            if (y < ny) {
+                float* row = pout + (size_t)y * nx;
+                if (vec && x0 + 3 < nx) {
+                    *reinterpret_cast<float4*>(row + x0) =
+                        make_float4(phi[r][0], phi[r][1], phi[r][2], phi[r][3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (x0 + q < nx) row[x0 + q] = phi[r][q];
+                }
+            }
+        }
+    }
+    if (a.mode != 0) return;
+
+    __syncthreads();
+    const int nct = gridDim.x * gridDim.y;
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x < T) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kTileWarps; ++w) s += (double)s_wsum[threadIdx.x][w];
+        a.partial[((size_t)b * kMaxBlock + threadIdx.x) * nct + cta] = s;
+        __threadfence();
+    }
+    __shared__ int s_last_grid;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_last_grid = atomicAdd(&g->arrivals, 1u) == (uint32_t)nct - 1u;
+        if (s_last_grid) __threadfence();
+    }
+    __syncthreads();
+    if (s_last_grid) grid_decide(a, b, T, k0, src, nct);
+    launch_arrive(a, T);
+}
+
+// ----------------------------------------------------- correction (Eq. 2)
+
+// One thread per cell: corrects its west (u[j][i]) and north (v[j][i]) faces,
+// zeroes the closed domain faces u[j][nx] and v[ny][i], writes p = phi*scale.
+__global__ void correct_kernel(float* __restrict__ u, float* __restrict__ v,
+                               const uint8_t* __restrict__ mask, const float* __restrict__ phi0,
+                               const float* __restrict__ phi1, const GridState* __restrict__ gs,
+                               float* __restrict__ p_out, float* __restrict__ phi_out,
+                               float scale, int ny, int nx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
+    if (i >= nx) return;
+    const size_t gb = (size_t)b * ny * nx;
+    const float* ph = (gs[b].final_buf ? phi1 : phi0) + gb;
+    const size_t c = (size_t)j * nx + i;
+    const uint32_t m = mask[gb + c];
+    const float pc = ph[c];
+    if (u) {
+        float* ub = u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1);
+        float* vb = v + (size_t)b * (ny + 1) * nx;
+        float uw = 0.0f, vn = 0.0f;
+        if (m & 1u) uw = __fsub_rn(ub[i], __fsub_rn(pc, ph[c - 1]));
+        if (m & 4u) vn = __fsub_rn(vb[(size_t)j * nx + i], __fsub_rn(pc, ph[c - nx]));
+        ub[i] = uw;
+        vb[(size_t)j * nx + i] = vn;
+        if (i == nx - 1) ub[nx] = 0.0f;
+        if (j == ny - 1) vb[(size_t)ny * nx + i] = 0.0f;
+    }
+    if (p_out) p_out[gb + c] = __fmul_rn(pc, scale);
+    if (phi_out) phi_out[gb + c] = pc;
+}
+
+// --------------------------------------------------------- divergence norms
+
+// One thread per cell: |div u| over open faces, FP32 per thread and warp, FP64
+// per block into partial[b][block]; max via an atomic on the float bits.
+__global__ void div_norms_kernel(const float* __restrict__ u, const float* __restrict__ v,
+                                 const uint8_t* __restrict__ flags,
+                                 const uint8_t* __restrict__ mask, double* __restrict__ partial,
+                                 uint32_t* __restrict__ einf_bits, size_t einf_stride, int ny,
+                                 int nx)
+{
+    __shared__ float s_w[8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
+    float a = 0.0f;
+    if (i < nx) {
+        const size_t c = (size_t)j * nx + i;
+        uint32_t m;
+        if (mask) {
+            m = mask[(size_t)b * ny * nx + c];
+        } else {
+            const uint8_t* fl = flags + (size_t)b * ny * nx;
+            m = 0;
+            if (fl[c] == 0) {
+                if (i > 0 && fl[c - 1] == 0) m |= 1u;
+                if (i < nx - 1 && fl[c + 1] == 0) m |= 2u;
+                if (j > 0 && fl[c - nx] == 0) m |= 4u;
+                if (j < ny - 1 && fl[c + nx] == 0) m |= 8u;
+            }
+        }
+        const float* ub = u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1);
+        const float* vb = v + (size_t)b * (ny + 1) * nx;
+        const float ue = (m & 2u) ? ub[i + 1] : 0.0f;
+        const float uw = (m & 1u) ? ub[i] : 0.0f;
+        const float vs = (m & 8u) ? vb[(size_t)(j + 1) * nx + i] : 0.0f;
+        const float vn = (m & 4u) ? vb[(size_t)j * nx + i] : 0.0f;
+        a = fabsf(__fadd_rn(__fsub_rn(ue, uw), __fsub_rn(vs, vn)));
+    }
+    float mx = a;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, off));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_w[wid] = a;
+        atomicMax(einf_bits + (size_t)b * einf_stride, __float_as_uint(mx));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)s_w[w];
+        partial[(size_t)b * gridDim.x * gridDim.y + (size_t)j * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// One warp per grid: E_1 = sum of block partials (fixed order) / cells.
+__global__ void norms_finish_kernel(const double* __restrict__ partial, int nblk,
+                                    const uint32_t* __restrict__ einf_bits, size_t einf_stride,
+                                    double* e1, double* einf, const GridState* gs, int32_t* iters,
+                                    uint8_t* conv, int B, double inv_cells)
+{
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int q = lane; q < nblk; q += 32) s += partial[(size_t)b * nblk + q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        if (e1) e1[b] = s * inv_cells;
+        if (einf) einf[b] = (double)__uint_as_float(einf_bits[(size_t)b * einf_stride]);
+        if (gs) {
+            if (iters) iters[b] = gs[b].kstar;
+            if (conv) conv[b] = (uint8_t)gs[b].converged;
+        }
+    }
+}
+
+__global__ void clear_einf_kernel(uint32_t* bits, size_t stride, int B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) bits[(size_t)b * stride] = 0u;
+}
+
+hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags, double* partial,
+                           int nblk_cap, GridState* gs, double* e1, double* einf, hp_shape s,
+                           cudaStream_t st)
+{
+    dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
+    const int nblk = grd.x * grd.y;
+    if (nblk > nblk_cap) return HP_ERR_INVALID_ARG;
+    // the per-grid max word lives in the grid state array of the context
+    uint32_t* einf_bits = &gs[0].einf_bits;
+    const size_t stride = sizeof(GridState) / sizeof(uint32_t);
+    clear_einf_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(einf_bits, stride, s.batch);
+    div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, nullptr, partial, einf_bits, stride, s.ny,
+                                          s.nx);
+    norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
+        partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
+        1.0 / ((double)s.nx * (double)s.ny));
+    return check_launch();
+}
+
+// ------------------------------------------------------------- sweep loop
+
+static void* sweep_kernel_ptr(int H)
+{
+    return H == 4 ? (void*)sweep_tb_kernel<4> : (void*)sweep_tb_kernel<8>;
+}
+
+static hp_status launch_sweep(const SweepArgs& a, int H, cudaStream_t st)
+{
+    dim3 grd(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B), blk(kTileWarps * 32);
+    if (H == 4)
+        sweep_tb_kernel<4><<<grd, blk, 0, st>>>(a);
+    else
+        sweep_tb_kernel<8><<<grd, blk, 0, st>>>(a);
+    return check_launch();
+}
+
+static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H)
+{
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    cudaGraphConditionalHandle handle;
+    e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            a.cond = (unsigned long long)handle;
+            void* args[] = {&a};
+            cudaKernelNodeParams kp = {};
+            kp.func = sweep_kernel_ptr(H);
+            kp.gridDim = dim3(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B);
+            kp.blockDim = dim3(kTileWarps * 32);
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = args;
+            cudaGraphNode_t knode;
+            e = cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+        }
+    }
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        set_cuda_error(e);
+        return HP_ERR_CUDA;
+    }
+    return HP_OK;
+}
+
+// Runs blocks of T sweeps until every grid has stopped, then replays each grid
+// to its exact stop index.  Expects ctx->mask, ctx->div and ctx->phi[0] ready.
+static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, double threshold, int max_iters,
+                                double* e_hist, int hist_len, bool use_graph, cudaStream_t st)
+{
+    const int H = halo_for(T);
+    const int nct = ctas_x(s.nx, H) * ctas_y(s.ny, H);
+    if ((size_t)s.batch * kMaxBlock * nct > ctx->partial_len) return HP_ERR_INVALID_ARG;
+    SweepArgs a = {};
+    a.phi0 = ctx->phi[0];
+    a.phi1 = ctx->phi[1];
+    a.div = ctx->div;
+    a.mask = ctx->mask;
+    a.gs = ctx->gs;
+    a.ls = ctx->ls;
+    a.partial = ctx->partial;
+    a.e_hist = e_hist;
+    a.hist_len = hist_len;
+    a.B = s.batch;
+    a.ny = s.ny;
+    a.nx = s.nx;
+    a.T = T;
+    a.max_iters = max_iters;
+    a.threshold = threshold;
+    a.mode = 0;
+    a.cond = 0;
+
+    reset_state_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(ctx->gs, ctx->ls, s.batch);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+
+    if (use_graph) {
+        const bool same = ctx->graph_exec && ctx->graph_shape.batch == s.batch &&
+                          ctx->graph_shape.ny == s.ny && ctx->graph_shape.nx == s.nx &&
+                          ctx->graph_T == T && ctx->graph_hist == hist_len &&
+                          ctx->graph_hist_ptr == e_hist && ctx->graph_threshold == threshold &&
+                          ctx->graph_max_iters == max_iters;
+        if (!same) {
+            rc = build_loop_graph(ctx, a, H);
+            if (rc != HP_OK) return rc;
+            ctx->graph_shape = s;
+            ctx->graph_T = T;
+            ctx->graph_hist = hist_len;
+            ctx->graph_hist_ptr = e_hist;
+            ctx->graph_threshold = threshold;
+            ctx->graph_max_iters = max_iters;
+        }
+        cudaError_t e = cudaGraphLaunch(ctx->graph_exec, st);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    } else {
+        // host-polled: launch a few blocks, read the flag, repeat; bounded by
+        // the cap (every grid stops at k = max_iters at the latest)
+        const int max_blocks = max_iters / T + 2;
+        int launched = 0;
+        const int chunk = 4;
+        while (launched < max_blocks) {
+            for (int c = 0; c < chunk && launched < max_blocks; ++c, ++launched) {
+                rc = launch_sweep(a, H, st);
+                if (rc != HP_OK) return rc;
+            }
+            cudaError_t e = cudaMemcpyAsync(ctx->host_flag, &ctx->ls->any_active, sizeof(int32_t),
+                                            cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+            if (*ctx->host_flag == 0) break;
+        }
+    }
+    a.mode = 1;
+    return launch_sweep(a, H, st);
+}
+
+static int pick_T(const hp_project_params* prm)
+{
+    int T = prm->temporal_block;
+    if (T <= 0) T = kMaxBlock;
+    if (T > kMaxBlock) T = kMaxBlock;
+    return T;
+}
+
+hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp_shape s,
+                       const hp_project_params* prm, const float* phi0, float* p_out,
+                       int32_t* iters_out, double* e1_out, double* einf_out, uint8_t* conv_out,
+                       double* e_hist, int32_t hist_len, cudaStream_t st, float* phi_copy_out)
+{
+    const size_t cells = (size_t)s.batch * s.ny * s.nx;
+    hp_status rc = HP_OK;
+    if (u) {
+        // without a velocity the caller has prepared ctx->mask and ctx->div
+        rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st);
+        if (rc != HP_OK) return rc;
+    }
+    init_phi_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(phi0, ctx->mask, ctx->phi[0],
+                                                                     cells);
+    if ((rc = check_launch()) != HP_OK) return rc;
+
+    const bool fixed = prm->fixed_iters > 0;
+    const int cap = fixed ? prm->fixed_iters : prm->max_iters;
+    const double thr = fixed ? -1.0 : prm->threshold;
+    rc = run_sweep_loop(ctx, s, pick_T(prm), thr, cap, e_hist, hist_len, prm->use_graph != 0, st);
+    if (rc != HP_OK) return rc;
+
+    dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
+    const float scale = prm->rho0 / prm->dt;
+    correct_kernel<<<grd, blk, 0, st>>>(u, v, ctx->mask, ctx->phi[0], ctx->phi[1], ctx->gs, p_out,
+                                        phi_copy_out, scale, s.ny, s.nx);
+    if ((rc = check_launch()) != HP_OK) return rc;
+
+    // norms of the corrected velocity; the einf word lives in GridState
+    const int nblk = grd.x * grd.y;
+    if ((size_t)s.batch * nblk > ctx->partial2_len) return HP_ERR_INVALID_ARG;
+    uint32_t* einf_bits = &ctx->gs[0].einf_bits;
+    const size_t stride = sizeof(GridState) / sizeof(uint32_t);
+    if (u) {
+        div_norms_kernel<<<grd, blk, 0, st>>>(u, v, nullptr, ctx->mask, ctx->partial2, einf_bits,
+                                              stride, s.ny, s.nx);
+        if ((rc = check_launch()) != HP_OK) return rc;
+    }
+    norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
+        ctx->partial2, nblk, einf_bits, stride, u ? e1_out : nullptr, u ? einf_out : nullptr,
+        ctx->gs, iters_out, fixed ? nullptr : conv_out, s.batch,
+        1.0 / ((double)s.nx * (double)s.ny));
+    if ((rc = check_launch()) != HP_OK) return rc;
+    if (fixed && conv_out) {
+        cudaError_t e = cudaMemsetAsync(conv_out, 1, (size_t)s.batch, st);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    }
+    return HP_OK;
+}
+
+}  // namespace hp
