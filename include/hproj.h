@@ -131,6 +131,33 @@ hp_status hp_jacobi_sweeps(hp_ctx *ctx, const float *phi_in, const float *div,
                            const uint8_t *flags, float *phi_out, int32_t n, double *e_out,
                            hp_shape shape, void *stream);
 
+/* Allocation-free variant of hp_div_norms.  The paper has no counterpart; it
+ * exists for callers that cannot call cudaMalloc: a host framework that owns
+ * all device memory through its own pool and forbids other allocations, a
+ * latency-critical loop where an allocation (and the device synchronisation
+ * it may cause) is not acceptable, or a process that has reached its memory
+ * budget.  Such a caller cannot create an hp_ctx, so this call takes no
+ * context; it computes the same E_1 and E_inf as hp_div_norms, with the same
+ * kernel.
+ *
+ * Its scratch (one FP64 partial sum per 256-cell block and one max word per
+ * grid) is a fixed array inside libhproj.so: every GPU that loads the library
+ * holds it (about 2.1 MB) until the process exits.  Limits: batch <=
+ * HP_NOALLOC_MAX_BATCH and batch * ny * ceil(nx / 256) <= HP_NOALLOC_MAX_BLOCKS
+ * (16 grids of 2048 x 2048 fit); larger shapes return HP_ERR_INVALID_ARG and
+ * launch nothing.  The call works on the device that is current; its first
+ * call on each device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (other streams, other host threads) race and give wrong results.  Each call
+ * clears the max words it uses before the reduction and overwrites the
+ * partial sums it reads; no cudaMalloc, cudaFree or allocating library
+ * routine is called.  u, v, flags, e1_out, einf_out as in hp_div_norms. */
+#define HP_NOALLOC_MAX_BATCH 16384
+#define HP_NOALLOC_MAX_BLOCKS 262144
+hp_status hp_div_norms_noalloc(const float *u, const float *v, const uint8_t *flags,
+                               double *e1_out, double *einf_out, hp_shape shape, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,7 @@ _SIGS = {
     "hp_project": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.POINTER(hp_project_params),
                                   _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "hp_jacobi_sweeps": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P, hp_shape, _P]),
+    "hp_div_norms_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
 }
 
 
@@ -184,6 +185,25 @@ def hp_div_norms(ctx: Context, u, v, flags, stream=None):
     _check(load_library().hp_div_norms(ctx.handle, _ptr(u), _ptr(v), _ptr(flags), _ptr(e1),
                                        _ptr(einf), s, _stream(stream)))
     return e1, einf
+
+
+def hp_div_norms_noalloc(u, v, flags, e1_out=None, einf_out=None, stream=None):
+    """E_1 and E_inf like hp_div_norms, without a context: for callers that
+    cannot allocate device memory for workspaces.  The library keeps a fixed
+    scratch array on each device instead; calls that overlap on the GPU race.
+    The output tensors may be passed in so that the call allocates nothing."""
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(u, torch.float32, (B, ny, nx + 1), "u")
+    _check_dtype(v, torch.float32, (B, ny + 1, nx), "v")
+    if e1_out is None:
+        e1_out = torch.empty(B, dtype=torch.float64, device=u.device)
+    if einf_out is None:
+        einf_out = torch.empty(B, dtype=torch.float64, device=u.device)
+    _check(load_library().hp_div_norms_noalloc(_ptr(u), _ptr(v), _ptr(flags), _ptr(e1_out),
+                                               _ptr(einf_out), s, _stream(stream)))
+    return e1_out, einf_out
 
 
 def hp_project(ctx: Context, u, v, flags, params: ProjectParams, phi0=None, p_out=None,

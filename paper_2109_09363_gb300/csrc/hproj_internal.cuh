@@ -99,6 +99,9 @@ hp_status launch_mask(const uint8_t* flags, uint8_t* mask, hp_shape s, cudaStrea
 hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
                            double* partial, int nblk_cap, GridState* gs, double* e1,
                            double* einf, hp_shape s, cudaStream_t st);
+hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t* flags,
+                                   double* partial, uint32_t* einf_bits, size_t stride,
+                                   double* e1, double* einf, hp_shape s, cudaStream_t st);
 hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp_shape s,
                        const hp_project_params* prm, const float* phi0, float* p_out,
                        int32_t* iters_out, double* e1_out, double* einf_out,

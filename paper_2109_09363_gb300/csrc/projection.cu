@@ -547,6 +547,23 @@ hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
     return check_launch();
 }
 
+// Same reduction as launch_div_norms with caller-given scratch: partial
+// (>= batch * blocks doubles) and one max word per grid at einf_bits[b * stride].
+hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t* flags,
+                                   double* partial, uint32_t* einf_bits, size_t stride,
+                                   double* e1, double* einf, hp_shape s, cudaStream_t st)
+{
+    dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
+    const int nblk = grd.x * grd.y;
+    clear_einf_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(einf_bits, stride, s.batch);
+    div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, nullptr, partial, einf_bits, stride, s.ny,
+                                          s.nx);
+    norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
+        partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
+        1.0 / ((double)s.nx * (double)s.ny));
+    return check_launch();
+}
+
 // ------------------------------------------------------------- sweep loop
 
 static void* sweep_kernel_ptr(int H)

@@ -1,0 +1,61 @@
+"""The allocation-free norm entry point (hp_div_norms_noalloc) against the
+context-based hp_div_norms, through the C ABI.
+
+Some callers cannot allocate device memory (a framework that owns all device
+memory through its own pool, a latency-critical loop); hp_div_norms_noalloc
+serves them with a fixed scratch array inside the library.  This file is
+collected last so that a run stopping at its first failure has already run
+every other test; it also passes alone in a fresh process."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+hp = pytest.importorskip("paper_2109_09363_gb300")
+
+RTOL = 1e-5  # the tolerance of the context-based norm test
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09363_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def fields(B, ny, nx, seed):
+    rng = np.random.default_rng(seed)
+    u = torch.from_numpy(rng.standard_normal((B, ny, nx + 1)).astype(np.float32))
+    v = torch.from_numpy(rng.standard_normal((B, ny + 1, nx)).astype(np.float32))
+    fl = torch.from_numpy((rng.random((B, ny, nx)) < 0.15).astype(np.uint8))
+    return u, v, fl
+
+
+def test_noalloc_norms_match_context_norms_on_consecutive_calls(dev):
+    cases = [(4, 130, 300, 1), (2, 37, 1000, 2)]
+    ctx = hp.Context(4, 130, 1000)
+    for B, ny, nx, seed in cases + cases:
+        u, v, fl = (t.to(dev) for t in fields(B, ny, nx, seed))
+        e1_ref, einf_ref = hp.hp_div_norms(ctx, u, v, fl)
+        e1_out = torch.empty(B, dtype=torch.float64, device=dev)
+        einf_out = torch.empty(B, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            e1_out.fill_(-1.0)
+            einf_out.fill_(-1.0)
+            hp.hp_div_norms_noalloc(u, v, fl, e1_out, einf_out)
+            torch.cuda.synchronize()
+            assert np.allclose(e1_out.cpu().numpy(), e1_ref.cpu().numpy(), rtol=RTOL, atol=0)
+            assert np.allclose(einf_out.cpu().numpy(), einf_ref.cpu().numpy(), rtol=RTOL, atol=0)
+
+
+@pytest.mark.parametrize("B,ny,nx", [(16385, 1, 1), (1, 262145, 1)])
+def test_noalloc_rejects_shapes_beyond_its_scratch(dev, B, ny, nx):
+    # more grids than max words, or more 256-cell blocks than partial sums
+    u = torch.zeros((B, ny, nx + 1), dtype=torch.float32, device=dev)
+    v = torch.zeros((B, ny + 1, nx), dtype=torch.float32, device=dev)
+    fl = torch.zeros((B, ny, nx), dtype=torch.uint8, device=dev)
+    with pytest.raises(hp.HprojError):
+        hp.hp_div_norms_noalloc(u, v, fl)
