@@ -164,6 +164,32 @@ def run_reference(args):
     return 0
 
 
+def profile_sweep(batch: int, n: int, sweeps: int) -> int:
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    from paper_2109_09363_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    us, vs, fs = [], [], []
+    for b in range(batch):
+        u, v = W.vortex_velocity(n, n, 1000 + b, n_vortices=32)
+        us.append(u); vs.append(v)
+        fs.append(W.random_obstacles(n, n, 2000 + b))
+    u = torch.from_numpy(np.stack(us).astype(np.float32)).to(dev)
+    v = torch.from_numpy(np.stack(vs).astype(np.float32)).to(dev)
+    fl = torch.from_numpy(np.stack(fs)).to(dev)
+    ctx = hp.Context(batch, n, n)
+    div = hp.hp_divergence(u, v, fl)
+    phi = torch.zeros_like(div)
+    for _ in range(3):
+        hp.hp_jacobi_sweeps(ctx, phi, div, fl, sweeps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sweep": [batch, n, sweeps], "ok": True}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,9 +197,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-sweep", nargs=3, type=int, metavar=("BATCH", "N", "SWEEPS"),
+                    help="only run the sweep kernel: SWEEPS Jacobi sweeps on BATCH vortex grids "
+                         "of N x N, three times (a small case for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_sweep:
+        return profile_sweep(*args.profile_sweep)
 
     import torch
     import torch.distributed as dist
