@@ -164,7 +164,13 @@ def run_reference(args):
     return 0
 
 
-def profile_sweep(batch: int, n: int, sweeps: int) -> int:
+def streaming_chosen(kernel: int, cells: int) -> bool:
+    """The library's sweep-kernel choice (hp_project with sweep_kernel = 0)."""
+    return kernel == 1
+
+
+def profile_sweep(batch: int, n: int, sweeps: int, host_loop: bool = False,
+                  kernel: int = 0) -> int:
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -180,10 +186,19 @@ def profile_sweep(batch: int, n: int, sweeps: int) -> int:
     v = torch.from_numpy(np.stack(vs).astype(np.float32)).to(dev)
     fl = torch.from_numpy(np.stack(fs)).to(dev)
     ctx = hp.Context(batch, n, n)
-    div = hp.hp_divergence(u, v, fl)
-    phi = torch.zeros_like(div)
-    for _ in range(3):
-        hp.hp_jacobi_sweeps(ctx, phi, div, fl, sweeps)
+    if host_loop:
+        prm = hp.ProjectParams(fixed_iters=sweeps, temporal_block=T_BLOCK, use_graph=0,
+                               sweep_kernel=kernel)
+        uw, vw = torch.empty_like(u), torch.empty_like(v)
+        for _ in range(3):
+            uw.copy_(u)
+            vw.copy_(v)
+            hp.hp_project(ctx, uw, vw, fl, prm)
+    else:
+        div = hp.hp_divergence(u, v, fl)
+        phi = torch.zeros_like(div)
+        for _ in range(3):
+            hp.hp_jacobi_sweeps(ctx, phi, div, fl, sweeps)
     torch.cuda.synchronize()
     print(json.dumps({"profile_sweep": [batch, n, sweeps], "ok": True}))
     ctx.close()
@@ -191,6 +206,7 @@ def profile_sweep(batch: int, n: int, sweeps: int) -> int:
 
 
 def main():
+    global T_BLOCK
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -200,11 +216,21 @@ def main():
     ap.add_argument("--profile-sweep", nargs=3, type=int, metavar=("BATCH", "N", "SWEEPS"),
                     help="only run the sweep kernel: SWEEPS Jacobi sweeps on BATCH vortex grids "
                          "of N x N, three times (a small case for ncu)")
+    ap.add_argument("--temporal-block", type=int, default=T_BLOCK,
+                    help="sweeps per launch of the temporally blocked kernel (1..8)")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="0 = library choice, 1 = streaming, 2 = temporally blocked")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="launch the sweep blocks from a host-polled loop instead of the "
+                         "CUDA-graph conditional loop (same kernels; ncu cannot profile kernel "
+                         "nodes of graphs with conditional nodes)")
     args = ap.parse_args()
+    T_BLOCK = args.temporal_block
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_sweep:
-        return profile_sweep(*args.profile_sweep)
+        return profile_sweep(*args.profile_sweep, host_loop=args.host_loop,
+                             kernel=args.sweep_kernel)
 
     import torch
     import torch.distributed as dist
@@ -226,7 +252,11 @@ def main():
     u = torch.empty_like(u0)
     v = torch.empty_like(v0)
     ctx = hp.Context(B, N, N, device=local)
-    prm = hp.ProjectParams(threshold=THR, max_iters=CAP, temporal_block=T_BLOCK, use_graph=1)
+    prm = hp.ProjectParams(threshold=THR, max_iters=CAP, temporal_block=T_BLOCK,
+                           use_graph=0 if args.host_loop else 1,
+                           sweep_kernel=args.sweep_kernel)
+    stream = streaming_chosen(args.sweep_kernel, B * N * N)
+    per_launch = 1 if stream else T_BLOCK
     stream = torch.cuda.current_stream()
     out = None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -241,8 +271,12 @@ def main():
         step()
     torch.cuda.synchronize()
     iters = out["iters"].cpu().numpy()
-    blocks = int(iters.max()) // T_BLOCK + 1
-    launches_per_step = 7 + blocks
+    if stream:
+        # 8 sweep launches per graph-loop iteration, plus mask/div, init,
+        # reset, correction, norms, finish
+        launches_per_step = 6 + 8 * ((int(iters.max()) + 1 + 7) // 8)
+    else:
+        launches_per_step = 7 + int(iters.max()) // T_BLOCK + 1
 
     # timed region: per-step CUDA events, L2 flushed (untimed) between steps
     if ws > 1:
@@ -271,30 +305,37 @@ def main():
     # dominant kernel: the temporally blocked sweep, per-launch duration from
     # the difference of two fixed-length sweep runs (same shape, same T, all
     # 16 grids active), CUDA events on the launching stream
-    div = hp.hp_divergence(u0, v0, fl)
-    phi = torch.zeros_like(div)
     n1, n2 = 8 * 20, 8 * 220
+    fprm = [hp.ProjectParams(fixed_iters=n, temporal_block=T_BLOCK, use_graph=1,
+                             sweep_kernel=args.sweep_kernel) for n in (n1, n2)]
     for _ in range(2):
-        hp.hp_jacobi_sweeps(ctx, phi, div, fl, n1)
-        hp.hp_jacobi_sweeps(ctx, phi, div, fl, n2)
+        for fp in fprm:
+            u.copy_(u0)
+            v.copy_(v0)
+            hp.hp_project(ctx, u, v, fl, fp)
     tl = []
-    for n in (n1, n2):
+    for fp in fprm:
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u.copy_(u0)
+        v.copy_(v0)
         flush.fill_(1.0)
         a.record(stream)
-        hp.hp_jacobi_sweeps(ctx, phi, div, fl, n)
+        hp.hp_project(ctx, u, v, fl, fp)
         b_.record(stream)
         torch.cuda.synchronize()
         tl.append(a.elapsed_time(b_))
-    t_launch_ms = (tl[1] - tl[0]) / ((n2 - n1) / T_BLOCK)
+    t_launch_ms = (tl[1] - tl[0]) / ((n2 - n1) / per_launch)
     cells = B * N * N
-    alg_bytes = BYTES_PER_CELL_SWEEP * cells * T_BLOCK
+    alg_bytes = BYTES_PER_CELL_SWEEP * cells * per_launch
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (t_launch_ms * 1e-3) / 1e9
+    # DRAM bytes per launch from an ncu capture of the same kernel and
+    # workload (committed summary); null when the kernel changed since
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "sweep_tb_traffic.json")
+    tp = os.path.join(ROOT, "profiles", "dram_traffic_16x512.json")
+    kname = "sweep1_kernel" if stream else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>"
     if os.path.exists(tp):
-        traffic = json.load(open(tp)).get("bytes_per_launch")
+        traffic = json.load(open(tp)).get(kname)
 
     # end to end through the public API with host buffers: H2D of u*, v*, flags
     # from pinned memory, projection, D2H of u, v, p, iterations
@@ -303,11 +344,13 @@ def main():
     op = torch.empty((B, N, N), dtype=torch.float32).pin_memory()
     oi = torch.empty(B, dtype=torch.int32).pin_memory()
     flh = torch.empty_like(fl)
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(3, min(args.steps, 5))
     e2e_out = None
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    t0 = 0.0
+    for it in range(e2e_steps + 1):
+        if it == 1:  # the first iteration is an untimed warm-up
+            t0 = time.perf_counter()
         u.copy_(hu, non_blocking=True)
         v.copy_(hv, non_blocking=True)
         flh.copy_(hf, non_blocking=True)
@@ -328,18 +371,24 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "method": "plain Jacobi", "grids_per_gpu": B,
                        "grid": [N, N], "threshold": THR, "cap": CAP,
-                       "temporal_block": T_BLOCK, "loop": "CUDA-graph conditional while",
+                       "sweep_kernel": "streaming" if stream else "temporally blocked",
+                       "temporal_block": None if stream else T_BLOCK,
+                       "loop": "host-polled" if args.host_loop else "CUDA-graph conditional while",
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "iters_per_grid": iters.tolist()},
-            "roofline": {"bound": "hbm", "kernel": "sweep_tb_kernel<8>",
+            "roofline": {"bound": "hbm",
+                         "kernel": kname if stream else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "launch_ms": t_launch_ms,
-                         "note": "13 B per cell-sweep x 4.19 M cells x 8 sweeps per launch; "
-                                 "temporal blocking keeps 8 sweeps on chip, so frac is an "
-                                 "effective HBM fraction"},
+                         "note": ("13 B per cell-sweep x 4.19 M cells, one sweep per launch; "
+                                  "the 54.5 MB working set is L2-resident between launches"
+                                  if stream else
+                                  "13 B per cell-sweep x 4.19 M cells x 8 sweeps per launch; "
+                                  "temporal blocking keeps 8 sweeps on chip, so frac is an "
+                                  "effective HBM fraction")},
             "e2e": {"value": ws * B / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,

@@ -60,9 +60,14 @@ typedef struct {
  *   max_iters      cap on the number of sweeps; reaching it gives converged = 0
  *   fixed_iters    > 0: run exactly this many sweeps, no stop test (converged = 1)
  *   dt, rho0       p = phi * rho0 / dt
- *   temporal_block sweeps fused per launch, 1..8 (0 = library default)
+ *   temporal_block sweeps fused per launch of the blocked kernel, 1..8
+ *                  (0 = library default)
  *   use_graph      1 = run the sweep loop as a CUDA-graph conditional WHILE node
- *                  (no host round trip per block); 0 = host-polled loop */
+ *                  (no host round trip per block); 0 = host-polled loop
+ *   sweep_kernel   0 = library choice, 1 = streaming (one sweep per launch,
+ *                  exact stop per launch), 2 = temporally blocked (T sweeps
+ *                  per launch, replay to the exact stop).  Both give the same
+ *                  iterates bit for bit. */
 typedef struct {
     double threshold;
     int32_t max_iters;
@@ -71,6 +76,7 @@ typedef struct {
     float rho0;
     int32_t temporal_block;
     int32_t use_graph;
+    int32_t sweep_kernel;
 } hp_project_params;
 
 typedef struct hp_ctx hp_ctx;

@@ -14,7 +14,8 @@ import os
 from dataclasses import dataclass
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhproj.so")
+# HPROJ_LIBRARY selects another build of the same C ABI (e.g. a debug build)
+LIB_PATH = os.environ.get("HPROJ_LIBRARY") or os.path.join(HERE, "libhproj.so")
 
 _lib = None
 
@@ -30,7 +31,8 @@ class hp_shape(ctypes.Structure):
 class hp_project_params(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("fixed_iters", ctypes.c_int32), ("dt", ctypes.c_float), ("rho0", ctypes.c_float),
-                ("temporal_block", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("temporal_block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("sweep_kernel", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -145,10 +147,12 @@ class ProjectParams:
     rho0: float = 1.0
     temporal_block: int = 0
     use_graph: int = 1
+    sweep_kernel: int = 0
 
     def c(self):
         return hp_project_params(self.threshold, self.max_iters, self.fixed_iters, self.dt,
-                                 self.rho0, self.temporal_block, self.use_graph)
+                                 self.rho0, self.temporal_block, self.use_graph,
+                                 self.sweep_kernel)
 
 
 def hp_face_mask(flags, mask_out=None, stream=None):

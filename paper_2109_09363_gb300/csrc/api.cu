@@ -105,12 +105,18 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
     hp_ctx* c = (hp_ctx*)calloc(1, sizeof(hp_ctx));
     if (!c) return HP_ERR_OOM;
     c->device = device;
+    c->num_sms = prop.multiProcessorCount;
     c->max_shape = mx;
     c->max_cells = (size_t)mx.batch * mx.ny * mx.nx;
     const int nct = ctas_per_grid(mx.ny, mx.nx, kMaxBlock) > ctas_per_grid(mx.ny, mx.nx, 4)
                         ? ctas_per_grid(mx.ny, mx.nx, kMaxBlock)
                         : ctas_per_grid(mx.ny, mx.nx, 4);
     c->partial_len = (size_t)mx.batch * kMaxBlock * nct;
+    {
+        // the streaming sweep keeps one partial per 8 x 128 block
+        const size_t s1 = (size_t)mx.batch * ((mx.nx + 127) / 128) * ((mx.ny + 7) / 8);
+        if (s1 > c->partial_len) c->partial_len = s1;
+    }
     c->partial2_len = (size_t)mx.batch * ((mx.nx + 255) / 256) * mx.ny;
     hp_status rc;
     if ((rc = dalloc(&c->mask, c->max_cells)) != HP_OK ||
@@ -174,7 +180,7 @@ hp_status hp_project(hp_ctx* c, float* u, float* v, const uint8_t* flags, hp_sha
     if (!c || !u || !v || !flags || !prm || !iters_out || !fits(c, s)) return HP_ERR_INVALID_ARG;
     if (prm->max_iters < 0 || prm->fixed_iters < 0 || prm->temporal_block < 0 ||
         prm->temporal_block > kMaxBlock || !(prm->threshold >= 0.0) || !(prm->dt > 0.0f) ||
-        !(prm->rho0 > 0.0f))
+        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 2)
         return HP_ERR_INVALID_ARG;
     if ((e_hist == nullptr) != (hist_len <= 0)) return HP_ERR_INVALID_ARG;
     return project_impl(c, u, v, flags, s, prm, phi0, p_out, iters_out, e1_out, einf_out, conv_out,

@@ -38,8 +38,10 @@ struct GridState {
 struct LoopState {
     int32_t k0;          // first sweep index of the current block
     int32_t blk;         // block counter; parity selects the phi buffers
-    uint32_t arrivals;   // CTA arrival counter of the whole launch
+    uint32_t arrivals;   // CTA (blocked kernel) or grid (streaming kernel) arrivals
     int32_t any_active;  // 1 while some grid still sweeps
+    int32_t n_active;    // grids still sweeping when the current launch started
+    int32_t pad_;
 };
 
 struct SweepArgs {
@@ -64,6 +66,7 @@ struct SweepArgs {
 
 struct hp_ctx {
     int device;
+    int num_sms;
     hp_shape max_shape;
     size_t max_cells;
     uint8_t* mask;
@@ -84,6 +87,7 @@ struct hp_ctx {
     double* graph_hist_ptr;
     double graph_threshold;
     int graph_max_iters;
+    int graph_kernel;
 };
 
 namespace hp {

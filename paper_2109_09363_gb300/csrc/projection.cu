@@ -119,6 +119,7 @@ __global__ void reset_state_kernel(GridState* gs, LoopState* ls, int B)
     if (b == 0) {
         LoopState l = {};
         l.any_active = 1;
+        l.n_active = B;
         *ls = l;
     }
 }
@@ -408,6 +409,142 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
     launch_arrive(a, T);
 }
 
+// ------------------------------------------------ streaming single sweep
+
+// Rows and columns of one block of the streaming kernel: one warp per row,
+// four consecutive cells per lane.
+constexpr int kS1Rows = 8;
+constexpr int kS1Cols = 128;
+
+int s1_blocks_x(int nx) { return (nx + kS1Cols - 1) / kS1Cols; }
+int s1_blocks_y(int ny) { return (ny + kS1Rows - 1) / kS1Rows; }
+
+// One Jacobi sweep of every active grid (phi_k -> phi_{k+1}, k = ls->k0) with
+// the E_1 of phi_k.  The last block of a grid sums the block partials in a
+// fixed order and takes the stop decision for k (the result phi_k is the
+// input buffer, no replay); the last grid to finish advances k and sets the
+// CUDA-graph conditional.  Neighbour rows come through L1/L2 (the working set
+// of a batch of 512^2 grids is L2-resident).
+__global__ void __launch_bounds__(kS1Rows * 32) sweep1_kernel(SweepArgs a)
+{
+    __shared__ float s_w[kS1Rows];
+    __shared__ int s_last;
+    const int b = blockIdx.z;
+    GridState* g = a.gs + b;
+    if (!g->active) return;
+    const int k = a.ls->k0;
+    const int src = a.ls->blk & 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nx = a.nx, ny = a.ny;
+    const size_t gbase = (size_t)b * ny * nx;
+    const float* __restrict__ pin = (src ? a.phi1 : a.phi0) + gbase;
+    float* __restrict__ pout = (src ? a.phi0 : a.phi1) + gbase;
+    const bool vec = (nx & 3) == 0;
+    const int x0 = blockIdx.x * kS1Cols + 4 * lane;
+    const int y = blockIdx.y * kS1Rows + wid;
+    float acc = 0.0f;
+    if (y < ny) {
+        float c[4], up[4] = {0.f, 0.f, 0.f, 0.f}, dn[4] = {0.f, 0.f, 0.f, 0.f}, dd[4];
+        const float* row = pin + (size_t)y * nx;
+        load_row4(row, x0, nx, vec, c);
+        if (y > 0) load_row4(row - nx, x0, nx, vec, up);
+        if (y < ny - 1) load_row4(row + nx, x0, nx, vec, dn);
+        load_row4(a.div + gbase + (size_t)y * nx, x0, nx, vec, dd);
+        const uint32_t m4 = load_mask4(a.mask + gbase + (size_t)y * nx, x0, nx, vec);
+        float left = __shfl_up_sync(0xffffffffu, c[3], 1);
+        float right = __shfl_down_sync(0xffffffffu, c[0], 1);
+        if (lane == 0) left = (x0 > 0 && x0 - 1 < nx) ? row[x0 - 1] : 0.0f;
+        if (lane == 31) right = (x0 + 4 < nx) ? row[x0 + 4] : 0.0f;
+        float nv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float pw = q > 0 ? c[q - 1] : left;
+            const float pe = q < 3 ? c[q + 1] : right;
+            float res;
+            nv[q] = cell_update(c[q], pw, pe, up[q], dn[q], make_const(dd[q], (m4 >> (8 * q)) & 0xffu),
+                                res);
+            acc = __fadd_rn(acc, fabsf(res));
+        }
+        float* orow = pout + (size_t)y * nx;
+        if (vec && x0 + 3 < nx) {
+            *reinterpret_cast<float4*>(orow + x0) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (x0 + q < nx) orow[x0 + q] = nv[q];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+    if (lane == 0) s_w[wid] = acc;
+    __syncthreads();
+    const int nbx = gridDim.x, nblk = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kS1Rows; ++w) sum += (double)s_w[w];
+        a.partial[(size_t)b * nblk + (size_t)blockIdx.y * nbx + blockIdx.x] = sum;
+        __threadfence();
+        s_last = atomicAdd(&g->arrivals, 1u) == (uint32_t)nblk - 1u;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) return;
+
+    // last block of grid b: E_k and the stop decision
+    __shared__ int s_last_launch;
+    if (wid == 0) {
+        const double* p = a.partial + (size_t)b * nblk;
+        double sum = 0.0;
+        for (int i = lane; i < nblk; i += 32) sum += __ldcg(p + i);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+        if (lane == 0) {
+            const double e = sum / ((double)nx * (double)ny);
+            if (a.e_hist && k < a.hist_len) a.e_hist[(size_t)b * a.hist_len + k] = e;
+            int stop = 0, conv = 0;
+            if (e <= a.threshold) { stop = 1; conv = 1; }
+            else if (k >= a.max_iters) { stop = 1; conv = 0; }
+            if (stop) {
+                g->active = 0;
+                g->kstar = k;
+                g->k0_stop = k;
+                g->replay = 0;
+                g->src = src;
+                g->final_buf = src;
+                g->converged = conv;
+                g->e_stop = e;
+            }
+            g->arrivals = 0u;
+            __threadfence();
+            s_last_launch = atomicAdd(&a.ls->arrivals, 1u) == (uint32_t)a.ls->n_active - 1u;
+            if (s_last_launch) __threadfence();
+        }
+    }
+    __syncthreads();
+    if (!s_last_launch) return;
+    // last grid of the launch: advance k, count the grids still sweeping
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    int n = 0;
+    for (int bb = threadIdx.x; bb < a.B; bb += blockDim.x) n += __ldcg(&a.gs[bb].active) ? 1 : 0;
+    if (n) atomicAdd(&s_count, n);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = s_count;
+        LoopState* ls = a.ls;
+        if (k + 1 > a.max_iters + 1) tot = 0;
+        ls->k0 = k + 1;
+        ls->blk = ls->blk + 1;
+        ls->arrivals = 0u;
+        ls->n_active = tot;
+        ls->any_active = tot > 0;
+        __threadfence();
+        if (a.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, tot > 0 ? 1u : 0u);
+    }
+}
+
 // ----------------------------------------------------- correction (Eq. 2)
 
 // One thread per cell: corrects its west (u[j][i]) and north (v[j][i]) faces,
@@ -581,7 +718,11 @@ static hp_status launch_sweep(const SweepArgs& a, int H, cudaStream_t st)
     return check_launch();
 }
 
-static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H)
+// Sweep launches per iteration of the graph loop with the streaming kernel
+// (grids that stopped skip the remaining launches of the iteration).
+constexpr int kStreamUnroll = 8;
+
+static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H, bool stream)
 {
     if (ctx->graph_exec) {
         cudaGraphExecDestroy(ctx->graph_exec);
@@ -605,13 +746,24 @@ static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H)
             a.cond = (unsigned long long)handle;
             void* args[] = {&a};
             cudaKernelNodeParams kp = {};
-            kp.func = sweep_kernel_ptr(H);
-            kp.gridDim = dim3(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B);
-            kp.blockDim = dim3(kTileWarps * 32);
-            kp.sharedMemBytes = 0;
+            if (stream) {
+                kp.func = (void*)sweep1_kernel;
+                kp.gridDim = dim3(s1_blocks_x(a.nx), s1_blocks_y(a.ny), a.B);
+                kp.blockDim = dim3(kS1Rows * 32);
+                kp.sharedMemBytes = 0;
+            } else {
+                kp.func = sweep_kernel_ptr(H);
+                kp.gridDim = dim3(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B);
+                kp.blockDim = dim3(kTileWarps * 32);
+                kp.sharedMemBytes = 0;
+            }
             kp.kernelParams = args;
-            cudaGraphNode_t knode;
-            e = cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+            cudaGraphNode_t prev = nullptr, knode = nullptr;
+            const int nodes = stream ? kStreamUnroll : 1;
+            for (int i = 0; i < nodes && e == cudaSuccess; ++i) {
+                e = cudaGraphAddKernelNode(&knode, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+                prev = knode;
+            }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
         }
     }
@@ -626,12 +778,22 @@ static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H)
 
 // Runs blocks of T sweeps until every grid has stopped, then replays each grid
 // to its exact stop index.  Expects ctx->mask, ctx->div and ctx->phi[0] ready.
-static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, double threshold, int max_iters,
-                                double* e_hist, int hist_len, bool use_graph, cudaStream_t st)
+static hp_status launch_sweep1(const SweepArgs& a, cudaStream_t st)
+{
+    dim3 grd(s1_blocks_x(a.nx), s1_blocks_y(a.ny), a.B), blk(kS1Rows * 32);
+    sweep1_kernel<<<grd, blk, 0, st>>>(a);
+    return check_launch();
+}
+
+static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, double threshold,
+                                int max_iters, double* e_hist, int hist_len, bool use_graph,
+                                cudaStream_t st)
 {
     const int H = halo_for(T);
     const int nct = ctas_x(s.nx, H) * ctas_y(s.ny, H);
     if ((size_t)s.batch * kMaxBlock * nct > ctx->partial_len) return HP_ERR_INVALID_ARG;
+    if ((size_t)s.batch * s1_blocks_x(s.nx) * s1_blocks_y(s.ny) > ctx->partial_len)
+        return HP_ERR_INVALID_ARG;
     SweepArgs a = {};
     a.phi0 = ctx->phi[0];
     a.phi1 = ctx->phi[1];
@@ -660,10 +822,11 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, double threshold
                           ctx->graph_shape.ny == s.ny && ctx->graph_shape.nx == s.nx &&
                           ctx->graph_T == T && ctx->graph_hist == hist_len &&
                           ctx->graph_hist_ptr == e_hist && ctx->graph_threshold == threshold &&
-                          ctx->graph_max_iters == max_iters;
+                          ctx->graph_max_iters == max_iters && ctx->graph_kernel == (int)stream;
         if (!same) {
-            rc = build_loop_graph(ctx, a, H);
+            rc = build_loop_graph(ctx, a, H, stream);
             if (rc != HP_OK) return rc;
+            ctx->graph_kernel = (int)stream;
             ctx->graph_shape = s;
             ctx->graph_T = T;
             ctx->graph_hist = hist_len;
@@ -676,12 +839,12 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, double threshold
     } else {
         // host-polled: launch a few blocks, read the flag, repeat; bounded by
         // the cap (every grid stops at k = max_iters at the latest)
-        const int max_blocks = max_iters / T + 2;
+        const int max_blocks = stream ? max_iters + 1 : max_iters / T + 2;
         int launched = 0;
-        const int chunk = 4;
+        const int chunk = stream ? kStreamUnroll : 4;
         while (launched < max_blocks) {
             for (int c = 0; c < chunk && launched < max_blocks; ++c, ++launched) {
-                rc = launch_sweep(a, H, st);
+                rc = stream ? launch_sweep1(a, st) : launch_sweep(a, H, st);
                 if (rc != HP_OK) return rc;
             }
             cudaError_t e = cudaMemcpyAsync(ctx->host_flag, &ctx->ls->any_active, sizeof(int32_t),
@@ -691,6 +854,7 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, double threshold
             if (*ctx->host_flag == 0) break;
         }
     }
+    if (stream) return HP_OK;  // the streaming kernel stops exactly, nothing to replay
     a.mode = 1;
     return launch_sweep(a, H, st);
 }
@@ -722,7 +886,11 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     const bool fixed = prm->fixed_iters > 0;
     const int cap = fixed ? prm->fixed_iters : prm->max_iters;
     const double thr = fixed ? -1.0 : prm->threshold;
-    rc = run_sweep_loop(ctx, s, pick_T(prm), thr, cap, e_hist, hist_len, prm->use_graph != 0, st);
+    // library choice: the temporally blocked kernel (measured faster than the
+    // streaming one at 16 x 512^2 and above)
+    const bool stream = prm->sweep_kernel == 1;
+    rc = run_sweep_loop(ctx, s, pick_T(prm), stream, thr, cap, e_hist, hist_len,
+                        prm->use_graph != 0, st);
     if (rc != HP_OK) return rc;
 
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);

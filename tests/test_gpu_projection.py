@@ -175,24 +175,35 @@ def test_project_matches_oracle(dev, shape, thr, cap):
     check_projection(g, u, v, fl, thr, cap)
 
 
-def test_temporal_block_and_loop_mode_do_not_change_results(dev):
+def test_sweep_kernel_block_size_and_loop_mode_do_not_change_results(dev):
     u, v, fl = vortex(3, 96, 160, seed=5)
     base = None
-    for T in [1, 2, 3, 4, 5, 8]:
-        for graph in [0, 1]:
-            g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=700,
-                                                        temporal_block=T, use_graph=graph))
-            if base is None:
-                base = g
-                continue
-            for k in ["iters", "converged", "p", "u", "v", "e1", "einf"]:
-                assert np.array_equal(g[k], base[k]), (T, graph, k)
+    cases = [(1, 1, g) for g in (0, 1)] + [(2, T, g) for T in (1, 2, 3, 4, 5, 8) for g in (0, 1)]
+    for kern, T, graph in cases:
+        g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=700,
+                                                    temporal_block=T, use_graph=graph,
+                                                    sweep_kernel=kern))
+        if base is None:
+            base = g
+            continue
+        for k in ["iters", "converged", "p", "u", "v", "e1", "einf"]:
+            assert np.array_equal(g[k], base[k]), (kern, T, graph, k)
 
 
-def test_history_matches_oracle(dev):
+@pytest.mark.parametrize("kern", [1, 2])
+def test_both_sweep_kernels_match_oracle(dev, kern):
+    u, v, fl = vortex(3, 67, 130, seed=12)
+    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=2000,
+                                                sweep_kernel=kern))
+    check_projection(g, u, v, fl, 1e-3, 2000)
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+def test_history_matches_oracle(dev, kern):
     u, v, fl = vortex(2, 64, 96, seed=9)
     thr, cap = 1e-3, 400
-    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap), hist_len=cap + 1)
+    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap, sweep_kernel=kern),
+                hist_len=cap + 1)
     ref = oracle.project(u.astype(np.float64), v.astype(np.float64), fl, thr, cap,
                          hist_len=cap + 1)
     for b in range(2):
@@ -267,6 +278,8 @@ def test_full_size_vortex_benchmark_sampled(dev):
     u, v = f32(u64), f32(v64)
     g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap))
     assert np.all(g["iters"] > 0)
+    g2 = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap, sweep_kernel=2))
+    assert np.array_equal(g2["u"], g["u"]) and np.array_equal(g2["iters"], g["iters"])
     oracle.set_threads(0)
     sample = [0, 5, 10, 15]
     sub = {k: g[k][sample] for k in ["u", "v", "p", "iters", "converged", "e1"]}

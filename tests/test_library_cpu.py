@@ -36,7 +36,7 @@ def test_status_strings(lib):
 def test_argument_errors_are_returned_before_any_launch(lib):
     # null context / pointers are rejected on the host
     s = hp.hp_shape(1, 4, 4)
-    prm = hp.hp_project_params(1e-3, 10, 0, 1.0, 1.0, 0, 1)
+    prm = hp.hp_project_params(1e-3, 10, 0, 1.0, 1.0, 0, 1, 0)
     rc = lib.hp_project(None, None, None, None, s, ctypes.byref(prm), None, None, None, None,
                         None, None, None, 0, None)
     assert rc == 1
