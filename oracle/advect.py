@@ -1,0 +1,83 @@
+"""FP64 oracle of the plume driver step (advection and buoyancy), numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Sec. 2.2 of the paper advects the density and the velocity with a
+semi-Lagrangian scheme and adds the external forces with forward Euler,
+giving u*; the projection follows.  This oracle takes the first-order
+semi-Lagrangian form (one Euler backtrace, bilinear interpolation) and the
+Boussinesq buoyancy of the plume case:
+
+  1. inlet: rho = rho_in on the inlet cells (bottom row, columns [x0, x1));
+  2. every quantity q (rho at cell centres, u and v at their faces) is
+     sampled at the departure point x - dt * vel(x), with vel the velocity at
+     the start of the step (u^n, v^n) interpolated bilinearly per component;
+     sample positions are clamped to the span of the quantity's grid;
+  3. buoyancy on the interior v faces: v += dt * g * (rho_face - rho_amb) with
+     rho_face the mean of the two adjacent advected cell densities;
+  4. the velocity of every closed face is set to zero.
+
+Positions: cell (i, j) centred at (i + 1/2, j + 1/2); u face (j, i) at
+(i, j + 1/2); v face (j, i) at (i + 1/2, j); row 0 is the top of the image,
+so a negative v points up.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def bilinear(q, x, y, ox, oy):
+    """Bilinear sample of q[j][i] (sample (j, i) at (i + ox, j + oy)) at
+    points (x, y); positions outside the sample span are clamped to it."""
+    My, Mx = q.shape
+    tx = np.clip(x - ox, 0.0, Mx - 1.0)
+    ty = np.clip(y - oy, 0.0, My - 1.0)
+    i0 = np.minimum(np.floor(tx).astype(np.int64), max(Mx - 2, 0))
+    j0 = np.minimum(np.floor(ty).astype(np.int64), max(My - 2, 0))
+    fx = tx - i0
+    fy = ty - j0
+    i1 = np.minimum(i0 + 1, Mx - 1)
+    j1 = np.minimum(j0 + 1, My - 1)
+    top = q[j0, i0] * (1.0 - fx) + q[j0, i1] * fx
+    bot = q[j1, i0] * (1.0 - fx) + q[j1, i1] * fx
+    return top * (1.0 - fy) + bot * fy
+
+
+def velocity_at(u, v, x, y):
+    """(u, v) at points (x, y): each component interpolated on its own faces."""
+    return bilinear(u, x, y, 0.0, 0.5), bilinear(v, x, y, 0.5, 0.0)
+
+
+def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, inlet=None):
+    """One driver step on one grid; returns (u*, v*, rho) in FP64.
+
+    u [ny][nx+1], v [ny+1][nx], rho, flags [ny][nx]; inlet = (x0, x1) columns
+    of the bottom-row density source or None.
+    """
+    u = np.asarray(u, np.float64)
+    v = np.asarray(v, np.float64)
+    rho = np.array(rho, np.float64)
+    ny, nx = rho.shape
+    if inlet is not None:
+        rho[ny - 1, inlet[0]:inlet[1]] = rho_in
+    # departure points of the cell centres, u faces and v faces
+    jc, ic = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    xc, yc = ic + 0.5, jc + 0.5
+    ju, iu = np.meshgrid(np.arange(ny), np.arange(nx + 1), indexing="ij")
+    xu, yu = iu.astype(np.float64), ju + 0.5
+    jv, iv = np.meshgrid(np.arange(ny + 1), np.arange(nx), indexing="ij")
+    xv, yv = iv + 0.5, jv.astype(np.float64)
+
+    vx, vy = velocity_at(u, v, xc, yc)
+    rho_new = bilinear(rho, xc - dt * vx, yc - dt * vy, 0.5, 0.5)
+    vx, vy = velocity_at(u, v, xu, yu)
+    u_new = bilinear(u, xu - dt * vx, yu - dt * vy, 0.0, 0.5)
+    vx, vy = velocity_at(u, v, xv, yv)
+    v_new = bilinear(v, xv - dt * vx, yv - dt * vy, 0.5, 0.0)
+    # Boussinesq buoyancy on interior v faces (forward Euler)
+    rho_face = 0.5 * (rho_new[:-1, :] + rho_new[1:, :])
+    v_new[1:ny, :] += dt * gravity * (rho_face - rho_amb)
+    uz, vz = oracle.zero_closed_faces(u_new, v_new, flags)
+    return uz[0], vz[0], rho_new

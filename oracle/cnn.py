@@ -1,0 +1,181 @@
+"""FP64 oracle of the MultiScale CNN (Sec. 3.1, MultiScale architecture), numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Readings of the paper (listed in the design notes): every convolution is 3 x 3
+with replication padding; scale 1/4 is 2 -> 32 -> 64 -> 64 -> 32 -> 1 (5
+convolutions), scales 1/2 and 1 are 3 -> 32 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1
+(7 convolutions) with input [div/s, flags, upsampled coarser output]; ReLU
+after every convolution of a branch except its last two; down-sampling is 2 x
+2 (4 x 4) average pooling, which equals bilinear down-sampling by 1/2 at
+half-pixel centres; up-sampling is bilinear x 2 at half-pixel centres with the
+edge sample repeated.  372,643 parameters.
+
+Layout: activations [C][H][W] (one grid), weights [Cout][Cin][3][3].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BRANCH_WIDTHS = {
+    4: [2, 32, 64, 64, 32, 1],               # scale 1/4
+    2: [3, 32, 64, 64, 64, 64, 32, 1],       # scale 1/2
+    1: [3, 32, 64, 64, 64, 64, 32, 1],       # full scale
+}
+SCALES = (4, 2, 1)
+
+
+def param_shapes():
+    """[(scale, layer, (Cout, Cin, 3, 3), (Cout,))] in network order."""
+    out = []
+    for sc in SCALES:
+        w = BRANCH_WIDTHS[sc]
+        for l in range(len(w) - 1):
+            out.append((sc, l, (w[l + 1], w[l], 3, 3), (w[l + 1],)))
+    return out
+
+
+def param_count():
+    return sum(int(np.prod(ws)) + int(np.prod(bs)) for _, _, ws, bs in param_shapes())
+
+
+def relu_after(sc, l):
+    """ReLU after every convolution of a branch except its last two."""
+    return l < len(BRANCH_WIDTHS[sc]) - 3
+
+
+def init_params(seed=0):
+    """He-uniform weights, zero biases (a deterministic starting point)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    params = []
+    for sc, l, ws, bs in param_shapes():
+        fan_in = ws[1] * 9
+        lim = np.sqrt(6.0 / fan_in)
+        params.append((g.uniform(-lim, lim, ws), np.zeros(bs)))
+    return params
+
+
+# ------------------------------------------------------------- primitives
+
+def conv3x3(x, w, b):
+    """y[o, i, j] = b[o] + sum_{c, dy, dx} w[o, c, dy, dx] x_pad[c, i + dy, j + dx],
+    x_pad = x with one replicated ghost cell on each side."""
+    C, H, W = x.shape
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    y = np.zeros((w.shape[0], H, W))
+    for dy in range(3):
+        for dx in range(3):
+            y += np.einsum("oc,chw->ohw", w[:, :, dy, dx], xp[:, dy:dy + H, dx:dx + W])
+    return y + b[:, None, None]
+
+
+def conv3x3_backward(x, w, gy):
+    """Gradients of conv3x3 w.r.t. x, w and b given gy = dL/dy."""
+    C, H, W = x.shape
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1)), mode="edge")
+    gw = np.zeros_like(w)
+    gxp = np.zeros_like(xp)
+    for dy in range(3):
+        for dx in range(3):
+            gw[:, :, dy, dx] = np.einsum("ohw,chw->oc", gy, xp[:, dy:dy + H, dx:dx + W])
+            gxp[:, dy:dy + H, dx:dx + W] += np.einsum("oc,ohw->chw", w[:, :, dy, dx], gy)
+    # transpose of the replication padding: ghost gradients go to the edge
+    gxp[:, 1, :] += gxp[:, 0, :]
+    gxp[:, H, :] += gxp[:, H + 1, :]
+    gxp[:, :, 1] += gxp[:, :, 0]
+    gxp[:, :, W] += gxp[:, :, W + 1]
+    return gxp[:, 1:H + 1, 1:W + 1], gw, gy.sum(axis=(1, 2))
+
+
+def avgpool2(x):
+    C, H, W = x.shape
+    return x.reshape(C, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
+
+
+def avgpool2_backward(gy):
+    return np.repeat(np.repeat(gy, 2, axis=1), 2, axis=2) / 4.0
+
+
+def _up1d(x, axis):
+    """Bilinear x 2 along one axis, half-pixel centres, edge repeated:
+    out[2i] = 3/4 x[i] + 1/4 x[i-1], out[2i+1] = 3/4 x[i] + 1/4 x[i+1]."""
+    n = x.shape[axis]
+    idx = np.arange(n)
+    prev = np.take(x, np.maximum(idx - 1, 0), axis=axis)
+    nxt = np.take(x, np.minimum(idx + 1, n - 1), axis=axis)
+    even = 0.75 * x + 0.25 * prev
+    odd = 0.75 * x + 0.25 * nxt
+    out = np.stack([even, odd], axis=axis + 1)
+    shape = list(x.shape)
+    shape[axis] = 2 * n
+    return out.reshape(shape)
+
+
+def upsample2(x):
+    return _up1d(_up1d(x, 1), 2)
+
+
+def _up1d_backward(g, axis):
+    """Transpose of _up1d along `axis`."""
+    g = np.moveaxis(g, axis, 0)
+    ge, go = g[0::2], g[1::2]
+    n = ge.shape[0]
+    gx = 0.75 * (ge + go)
+    idx = np.arange(n)
+    np.add.at(gx, np.maximum(idx - 1, 0), 0.25 * ge)
+    np.add.at(gx, np.minimum(idx + 1, n - 1), 0.25 * go)
+    return np.moveaxis(gx, 0, axis)
+
+
+def upsample2_backward(g):
+    return _up1d_backward(_up1d_backward(g, 2), 1)
+
+
+# --------------------------------------------------------------- network
+
+def forward(params, div, flags, keep=False):
+    """phi_hat = MultiScale([div_s, flags]) for one grid (H, W divisible by 4).
+
+    div_s is the already scaled divergence (the caller divides by s and
+    multiplies the output by s).  With keep=True returns (out, tape) for
+    backward."""
+    x0 = np.stack([np.asarray(div, np.float64), (np.asarray(flags) != 0).astype(np.float64)])
+    xin = {1: x0, 2: avgpool2(x0)}
+    xin[4] = avgpool2(xin[2])
+    tape = []
+    p = iter(params)
+    prev = None
+    for sc in SCALES:
+        h = xin[sc] if prev is None else np.concatenate([xin[sc], upsample2(prev)], axis=0)
+        for l in range(len(BRANCH_WIDTHS[sc]) - 1):
+            w, b = next(p)
+            pre = conv3x3(h, w, b)
+            out = np.maximum(pre, 0.0) if relu_after(sc, l) else pre
+            tape.append((sc, l, h, pre))
+            h = out
+        prev = h
+    return (prev[0], tape) if keep else prev[0]
+
+
+def backward(params, tape, g_out):
+    """Gradients of the network output (given dL/dphi_hat) w.r.t. every
+    parameter, as a list aligned with params: [(gw, gb), ...]."""
+    grads = [None] * len(params)
+    g = g_out[None].astype(np.float64)
+    idx = len(params) - 1
+    g_prev_up = None
+    for sc in reversed(SCALES):
+        nl = len(BRANCH_WIDTHS[sc]) - 1
+        if g_prev_up is not None:
+            g = g_prev_up
+        for l in reversed(range(nl)):
+            _, _, h, pre = tape[idx]
+            if relu_after(sc, l):
+                g = g * (pre > 0)
+            gx, gw, gb = conv3x3_backward(h, params[idx][0], g)
+            grads[idx] = (gw, gb)
+            g = gx
+            idx -= 1
+        # g is the gradient of this branch's input [x_sc(, upsampled coarser)]
+        g_prev_up = upsample2_backward(g[2:3]) if sc != 4 else None
+    return grads

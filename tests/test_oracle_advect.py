@@ -1,0 +1,82 @@
+"""Pins of the FP64 advection/buoyancy oracle (driver step of Sec. 2.2):
+identity at rest, exact integer shifts, exactness on linear fields, a
+library interpolator, and the buoyancy increment."""
+import numpy as np
+
+from oracle import advect as A
+
+
+def test_bilinear_matches_scipy_regular_grid_interpolator():
+    from scipy.interpolate import RegularGridInterpolator
+    rng = np.random.default_rng(0)
+    q = rng.standard_normal((9, 13))
+    ox, oy = 0.5, 0.0
+    x = rng.uniform(ox, 12 + ox, 200)
+    y = rng.uniform(oy, 8 + oy, 200)
+    f = RegularGridInterpolator((np.arange(9) + oy, np.arange(13) + ox), q, method="linear")
+    assert np.allclose(A.bilinear(q, x, y, ox, oy), f(np.stack([y, x], axis=1)), atol=1e-13)
+
+
+def test_bilinear_is_exact_on_linear_fields_and_clamps():
+    jj, ii = np.meshgrid(np.arange(7), np.arange(11), indexing="ij")
+    q = 0.3 * (ii + 0.5) - 1.7 * (jj + 0.5) + 2.0
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0.5, 10.5, 100)
+    y = rng.uniform(0.5, 6.5, 100)
+    assert np.allclose(A.bilinear(q, x, y, 0.5, 0.5), 0.3 * x - 1.7 * y + 2.0, atol=1e-13)
+    # outside the span: clamped to the edge sample
+    assert A.bilinear(q, np.array([-5.0]), np.array([0.5]), 0.5, 0.5)[0] == q[0, 0]
+
+
+def test_rest_state_is_unchanged_and_inlet_is_set():
+    n = 16
+    rho = 1.0 + np.zeros((n, n))
+    u, v = np.zeros((n, n + 1)), np.zeros((n + 1, n))
+    fl = np.zeros((n, n), np.uint8)
+    u2, v2, r2 = A.advect_step(u, v, rho, fl, dt=0.1, gravity=0.0, inlet=(6, 10))
+    assert np.all(u2 == 0) and np.all(v2 == 0)
+    exp = rho.copy()
+    exp[n - 1, 6:10] = 1.1
+    assert np.array_equal(r2, exp)
+
+
+def test_uniform_velocity_integer_shift_is_exact_in_the_interior():
+    n, U, dt = 24, 5.0, 0.4  # dt * U = 2 cells
+    rng = np.random.default_rng(2)
+    rho = rng.standard_normal((n, n))
+    u = np.full((n, n + 1), U)
+    v = np.zeros((n + 1, n))
+    fl = np.zeros((n, n), np.uint8)
+    _, _, r2 = A.advect_step(u, v, rho, fl, dt=dt, gravity=0.0)
+    assert np.allclose(r2[:, 2:], rho[:, :-2], atol=1e-14, rtol=0)
+    # v moves the field down by 3 rows
+    u0 = np.zeros((n, n + 1))
+    vv = np.full((n + 1, n), 7.5)
+    _, _, r3 = A.advect_step(u0, vv, rho, fl, dt=dt, gravity=0.0)
+    assert np.allclose(r3[3:, :], rho[:-3, :], atol=1e-14, rtol=0)
+
+
+def test_buoyancy_increment():
+    n, dt, g = 12, 0.1, -0.002
+    rng = np.random.default_rng(3)
+    rho = 1.0 + 0.1 * rng.random((n, n))
+    u, v = np.zeros((n, n + 1)), np.zeros((n + 1, n))
+    fl = np.zeros((n, n), np.uint8)
+    _, v2, r2 = A.advect_step(u, v, rho, fl, dt=dt, gravity=g)
+    assert np.array_equal(r2, rho)
+    exp = dt * g * (0.5 * (rho[:-1, :] + rho[1:, :]) - 1.0)
+    assert np.allclose(v2[1:n, :], exp, rtol=1e-15, atol=0)
+    assert np.all(v2[0] == 0) and np.all(v2[n] == 0)
+
+
+def test_closed_faces_are_zeroed():
+    n = 10
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((n, n + 1))
+    v = rng.standard_normal((n + 1, n))
+    fl = np.zeros((n, n), np.uint8)
+    fl[4:6, 4:6] = 1
+    u2, v2, _ = A.advect_step(u, v, np.ones((n, n)), fl, dt=0.05)
+    assert np.all(u2[:, 0] == 0) and np.all(u2[:, n] == 0)
+    assert np.all(v2[0, :] == 0) and np.all(v2[n, :] == 0)
+    assert np.all(u2[4:6, 4:7] == 0) and np.all(v2[4:7, 4:6] == 0)

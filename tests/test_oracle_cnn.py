@@ -1,0 +1,106 @@
+"""Pins of the FP64 MultiScale CNN oracle (Sec. 3.1): library special cases
+(torch conv2d / pooling / interpolation in FP64 on CPU, used only here to pin
+the oracle), adjointness, finite differences and the parameter count."""
+import numpy as np
+import pytest
+
+from oracle import cnn as C
+
+torch = pytest.importorskip("torch")
+F = torch.nn.functional
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).double()
+
+
+def test_parameter_count():
+    assert C.param_count() == 372643
+
+
+def test_conv3x3_replicate_matches_library():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((5, 9, 11))
+    w = rng.standard_normal((7, 5, 3, 3))
+    b = rng.standard_normal(7)
+    ref = F.conv2d(F.pad(T(x)[None], (1, 1, 1, 1), mode="replicate"), T(w), T(b))[0].numpy()
+    assert np.allclose(C.conv3x3(x, w, b), ref, atol=1e-12)
+
+
+def test_conv3x3_backward_matches_autograd():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((4, 6, 7))
+    w = rng.standard_normal((3, 4, 3, 3))
+    b = rng.standard_normal(3)
+    gy = rng.standard_normal((3, 6, 7))
+    xt, wt, bt = (T(a).requires_grad_() for a in (x, w, b))
+    y = F.conv2d(F.pad(xt[None], (1, 1, 1, 1), mode="replicate"), wt, bt)[0]
+    y.backward(T(gy))
+    gx, gw, gb = C.conv3x3_backward(x, w, gy)
+    assert np.allclose(gx, xt.grad.numpy(), atol=1e-12)
+    assert np.allclose(gw, wt.grad.numpy(), atol=1e-12)
+    assert np.allclose(gb, bt.grad.numpy(), atol=1e-12)
+
+
+def test_avgpool_is_bilinear_half_and_matches_library():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((3, 8, 12))
+    p = C.avgpool2(x)
+    assert np.allclose(p, F.avg_pool2d(T(x)[None], 2)[0].numpy(), atol=1e-14)
+    bil = F.interpolate(T(x)[None], scale_factor=0.5, mode="bilinear", align_corners=False)
+    assert np.allclose(p, bil[0].numpy(), atol=1e-14)
+
+
+def test_upsample_matches_library_and_is_adjoint():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((2, 5, 7))
+    up = C.upsample2(x)
+    ref = F.interpolate(T(x)[None], scale_factor=2, mode="bilinear", align_corners=False)
+    assert np.allclose(up, ref[0].numpy(), atol=1e-14)
+    y = rng.standard_normal(up.shape)
+    assert np.isclose(np.sum(up * y), np.sum(x * C.upsample2_backward(y)), rtol=1e-13)
+    gp = rng.standard_normal((2, 4, 6))
+    xx = rng.standard_normal((2, 8, 12))
+    assert np.isclose(np.sum(C.avgpool2(xx) * gp), np.sum(xx * C.avgpool2_backward(gp)),
+                      rtol=1e-13)
+
+
+def test_network_gradients_by_central_differences():
+    rng = np.random.default_rng(4)
+    params = C.init_params(seed=1)
+    # small random biases so that ReLU masks are not degenerate
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in params]
+    n = 8
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    gout = rng.standard_normal((n, n))
+    out, tape = C.forward(params, div, fl, keep=True)
+    grads = C.backward(params, tape, gout)
+    eps = 1e-6
+    checked = 0
+    for li in [0, 3, 4, 5, 9, 11, 12, 18]:
+        w, b = params[li]
+        for _ in range(3):
+            idx = tuple(rng.integers(0, s) for s in w.shape)
+            wp = [(ww.copy(), bb) for ww, bb in params]
+            wm = [(ww.copy(), bb) for ww, bb in params]
+            wp[li][0][idx] += eps
+            wm[li][0][idx] -= eps
+            fd = (np.sum(C.forward(wp, div, fl) * gout) - np.sum(C.forward(wm, div, fl) * gout)) / (2 * eps)
+            assert np.isclose(grads[li][0][idx], fd, rtol=1e-5, atol=1e-8), (li, idx)
+            checked += 1
+        j = int(rng.integers(0, b.shape[0]))
+        bp = [(ww, bb.copy()) for ww, bb in params]
+        bm = [(ww, bb.copy()) for ww, bb in params]
+        bp[li][1][j] += eps
+        bm[li][1][j] -= eps
+        fd = (np.sum(C.forward(bp, div, fl) * gout) - np.sum(C.forward(bm, div, fl) * gout)) / (2 * eps)
+        assert np.isclose(grads[li][1][j], fd, rtol=1e-5, atol=1e-8)
+    assert checked == 24
+
+
+def test_forward_shapes_and_scale_structure():
+    params = C.init_params(seed=2)
+    assert len(params) == 5 + 7 + 7
+    out = C.forward(params, np.zeros((16, 16)), np.zeros((16, 16), np.uint8))
+    assert out.shape == (16, 16)
