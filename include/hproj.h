@@ -137,6 +137,38 @@ hp_status hp_jacobi_sweeps(hp_ctx *ctx, const float *phi_in, const float *div,
                            const uint8_t *flags, float *phi_out, int32_t n, double *e_out,
                            hp_shape shape, void *stream);
 
+/* Parameters of the plume driver step (Sec. 2.2: semi-Lagrangian advection
+ * of the density and of the velocity, then the external force by forward
+ * Euler, giving u* for the projection).
+ *   dt        time step
+ *   gravity   g of the Boussinesq force on v: v += dt * g * (rho_face - rho_amb);
+ *             row 0 is the top, so g < 0 makes light fluid rise
+ *   rho_amb   ambient density
+ *   rho_in    density imposed on the inlet cells before the step
+ *   inlet_x0, inlet_x1  inlet columns [x0, x1) of the bottom row (x1 <= x0: no inlet) */
+typedef struct {
+    float dt;
+    float gravity;
+    float rho_amb;
+    float rho_in;
+    int32_t inlet_x0;
+    int32_t inlet_x1;
+} hp_plume_params;
+
+/* One driver step on B grids, out of place (outputs must not alias inputs):
+ *   1. rho = rho_in on the inlet cells;
+ *   2. rho (cell centres), u and v (faces) sampled bilinearly at the departure
+ *      point x - dt * vel(x), vel = the input velocity interpolated per
+ *      component; positions clamped to each quantity's sample span;
+ *   3. v += dt * g * (mean of the two advected densities next to the face
+ *      - rho_amb) on interior v faces;
+ *   4. every closed face set to zero.
+ * u, u_out float [B][ny][nx+1]; v, v_out [B][ny+1][nx]; rho, rho_out, flags
+ * [B][ny][nx]; device memory. */
+hp_status hp_advect_step(const float *u, const float *v, const float *rho, const uint8_t *flags,
+                         float *u_out, float *v_out, float *rho_out, hp_shape shape,
+                         const hp_plume_params *params, void *stream);
+
 /* Allocation-free variant of hp_div_norms.  The paper has no counterpart; it
  * exists for callers that cannot call cudaMalloc: a host framework that owns
  * all device memory through its own pool and forbids other allocations, a

@@ -35,6 +35,12 @@ class hp_project_params(ctypes.Structure):
                 ("sweep_kernel", ctypes.c_int32)]
 
 
+class hp_plume_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_float), ("gravity", ctypes.c_float), ("rho_amb", ctypes.c_float),
+                ("rho_in", ctypes.c_float), ("inlet_x0", ctypes.c_int32),
+                ("inlet_x1", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "hp_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
@@ -48,6 +54,8 @@ _SIGS = {
                                   _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "hp_jacobi_sweeps": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P, hp_shape, _P]),
     "hp_div_norms_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
+    "hp_advect_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, hp_shape,
+                                      ctypes.POINTER(hp_plume_params), _P]),
 }
 
 
@@ -257,6 +265,40 @@ def hp_jacobi_sweeps(ctx: Context, phi_in, div, flags, n: int, phi_out=None, wit
                                            _ptr(phi_out), ctypes.c_int32(n), _ptr(e), s,
                                            _stream(stream)))
     return (phi_out, e) if with_e else phi_out
+
+
+@dataclass
+class PlumeParams:
+    dt: float = 0.1
+    gravity: float = -0.002
+    rho_amb: float = 1.0
+    rho_in: float = 1.1
+    inlet_x0: int = 0
+    inlet_x1: int = 0
+
+    def c(self):
+        return hp_plume_params(self.dt, self.gravity, self.rho_amb, self.rho_in, self.inlet_x0,
+                               self.inlet_x1)
+
+
+def hp_advect_step(u, v, rho, flags, params: PlumeParams, u_out=None, v_out=None, rho_out=None,
+                   stream=None):
+    """Driver step (inlet, semi-Lagrangian advection, buoyancy); returns
+    (u*, v*, rho) as new device tensors unless outputs are given."""
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(u, torch.float32, (B, ny, nx + 1), "u")
+    _check_dtype(v, torch.float32, (B, ny + 1, nx), "v")
+    _check_dtype(rho, torch.float32, (B, ny, nx), "rho")
+    u_out = torch.empty_like(u) if u_out is None else u_out
+    v_out = torch.empty_like(v) if v_out is None else v_out
+    rho_out = torch.empty_like(rho) if rho_out is None else rho_out
+    prm = params.c()
+    _check(load_library().hp_advect_step(_ptr(u), _ptr(v), _ptr(rho), _ptr(flags), _ptr(u_out),
+                                         _ptr(v_out), _ptr(rho_out), s, ctypes.byref(prm),
+                                         _stream(stream)))
+    return u_out, v_out, rho_out
 
 
 def exported_symbols():

@@ -113,5 +113,8 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
                        float* phi_copy_out);
 
 int ctas_per_grid(int ny, int nx, int T);
+hp_status launch_advect(const float* u, const float* v, const float* rho, const uint8_t* flags,
+                        float* u_out, float* v_out, float* rho_out, hp_shape s,
+                        const hp_plume_params& p, cudaStream_t st);
 
 }  // namespace hp

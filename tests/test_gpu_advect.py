@@ -1,0 +1,99 @@
+"""GPU parity of the plume driver step (hp_advect_step) and of the plume
+loop (advect + project, configuration: 128^2 closed box, 16-cell inlet with
+rho = 1.1, g = -0.002, dt = 0.1, 50 steps) against the FP64 oracle, with the
+oracle restarted from the GPU state every step (teacher forcing)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import advect as A
+from paper_2109_09363_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+hp = pytest.importorskip("paper_2109_09363_gb300")
+
+TOL = 1e-5  # relative to the field's max, per face / cell
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09363_gb300 import build
+    build.build()
+    oracle.build()
+    return torch.device("cuda:0")
+
+
+def t(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+@pytest.mark.parametrize("shape,dt", [((1, 16, 16), 0.1), ((2, 67, 130), 0.5), ((1, 128, 96), 2.5)])
+def test_advect_step_matches_oracle(dev, shape, dt):
+    B, ny, nx = shape
+    rng = np.random.default_rng(ny + nx)
+    us, vs, rs, fs = [], [], [], []
+    for b in range(B):
+        u, v = W.vortex_velocity(ny, nx, 7 + b, n_vortices=6, width=(3, 12))
+        us.append(u); vs.append(v)
+        rs.append(1.0 + 0.05 * rng.standard_normal((ny, nx)))
+        fs.append(W.random_obstacles(ny, nx, 9 + b, rect_side=(3, 12), disc_radius=(2, 6)))
+    u = np.stack(us).astype(np.float32); v = np.stack(vs).astype(np.float32)
+    rho = np.stack(rs).astype(np.float32); fl = np.stack(fs)
+    inlet = (nx // 2 - 4, nx // 2 + 4)
+    pp = hp.PlumeParams(dt=dt, inlet_x0=inlet[0], inlet_x1=inlet[1])
+    uo, vo, ro = hp.hp_advect_step(t(u, dev), t(v, dev), t(rho, dev), t(fl, dev), pp)
+    torch.cuda.synchronize()
+    uo, vo, ro = uo.cpu().numpy(), vo.cpu().numpy(), ro.cpu().numpy()
+    for b in range(B):
+        eu, ev, er = A.advect_step(u[b], v[b], rho[b], fl[b], dt, inlet=inlet)
+        umax = max(np.abs(eu).max(), np.abs(ev).max())
+        assert np.abs(uo[b] - eu).max() <= TOL * umax
+        assert np.abs(vo[b] - ev).max() <= TOL * umax
+        assert np.abs(ro[b] - er).max() <= TOL * np.abs(er).max()
+
+
+@pytest.mark.parametrize("threshold", [1e-3, 1e-7])
+def test_plume_128_teacher_forced(dev, threshold):
+    from paper_2109_09363_gb300.plume import Plume, PlumeConfig
+    n = 128
+    u0, v0, rho0 = W.plume_initial_state(n, seed=0)
+    fl = W.plume_flags(n)[None]
+    x0, x1 = W.inlet_columns(n)
+    cfg = PlumeConfig(ny=n, nx=n, dt=0.1, inlet=(x0, x1), threshold=threshold, max_iters=2000)
+    sim = Plume(cfg, t(u0[None].astype(np.float32), dev), t(v0[None].astype(np.float32), dev),
+                t(rho0[None].astype(np.float32), dev), t(fl, dev))
+    swept = 0
+    for step in range(50):
+        su, sv, sr = (x.cpu().numpy()[0].astype(np.float64) for x in (sim.u, sim.v, sim.rho))
+        sim.advect()
+        eu, ev, er = A.advect_step(su, sv, sr, fl[0], cfg.dt, inlet=(x0, x1))
+        gu, gv, gr = (x.cpu().numpy()[0] for x in (sim.u, sim.v, sim.rho))
+        umax = max(np.abs(eu).max(), np.abs(ev).max(), 1e-12)
+        assert np.abs(gu - eu).max() <= TOL * umax, step
+        assert np.abs(gv - ev).max() <= TOL * umax, step
+        assert np.abs(gr - er).max() <= TOL * np.abs(er).max(), step
+        ustar = (gu.astype(np.float64), gv.astype(np.float64))
+        out = sim.project()
+        torch.cuda.synchronize()
+        ref = oracle.project(ustar[0], ustar[1], fl, threshold, 2000, dt=cfg.dt,
+                             hist_len=2002)
+        kg = int(out["iters"].cpu()[0])
+        ko = int(ref["iters"][0])
+        swept += kg
+        if kg != ko:
+            eh = ref["e_hist"][0]
+            lo, hi = min(kg, ko), max(kg, ko)
+            assert np.all(np.abs(eh[lo:hi + 1] - threshold) / threshold <= 5e-5), (step, kg, ko)
+            ref = oracle.project(ustar[0], ustar[1], fl, threshold, 2000, dt=cfg.dt,
+                                 fixed_iters=kg)
+        pu, pv = sim.u.cpu().numpy()[0], sim.v.cpu().numpy()[0]
+        umax = max(np.abs(ref["u"]).max(), np.abs(ref["v"]).max(), 1e-12)
+        assert np.abs(pu - ref["u"][0]).max() <= TOL * umax, step
+        assert np.abs(pv - ref["v"][0]).max() <= TOL * umax, step
+    if threshold < 1e-5:
+        assert swept > 0
+    # the light fluid rises: negative v above the inlet
+    assert sim.v.cpu().numpy()[0][n - 2, n // 2] < 0

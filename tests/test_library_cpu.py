@@ -19,6 +19,7 @@ def test_header_declares_the_boundary():
     names = hp.exported_symbols()
     for n in ["hp_ctx_create", "hp_ctx_destroy", "hp_face_mask", "hp_divergence",
               "hp_div_norms", "hp_project", "hp_jacobi_sweeps", "hp_status_string",
+              "hp_advect_step",
               "hp_last_cuda_error"]:
         assert n in names
 
