@@ -1,0 +1,292 @@
+// 3x3 convolution with replicated borders as an implicit GEMM on the sm_103a
+// tensor cores (tcgen05): the dense contraction of the MultiScale CNN
+// (Sec. 3.1).  BF16 activations and weights, FP32 accumulation in tensor
+// memory, bias + optional ReLU + BF16 rounding in the epilogue.
+//
+// GEMM view of one tile: M = 128 output pixels (flattened over batch, rows
+// and columns), N = Cout, K = 9 taps x Cin.  For every tap the A operand is
+// the gathered neighbour pixel of each output pixel (replicated borders
+// handled by clamping the coordinates), written to shared memory in the
+// canonical no-swizzle K-major layout: core matrices of 8 rows x 16 bytes,
+// [tap][channel chunk of 8][row][8 channels].  The weights are packed the
+// same way once per CTA: [tap][chunk][cout][8 channels].  One thread issues
+// the 9 x Cin/16 MMAs (M = 128, N = Cout, K = 16) into one TMEM accumulator,
+// commits them to an mbarrier, and the 128 threads read their row back with
+// tcgen05.ld.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hproj_internal.cuh"
+
+namespace hp {
+
+namespace {
+
+constexpr int kConvThreads = 128;  // one thread per GEMM row (output pixel)
+constexpr int kTileM = 128;
+constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
+// byte offset (between core matrices along K), stride-dimension byte offset
+// (between core matrices along M or N), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n, M = m.
+__host__ __device__ constexpr uint32_t mma_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CIN, int COUT>
+struct ConvSmem {
+    static constexpr int kChunks = CIN / 8;
+    static constexpr int kABytes = 9 * kChunks * kTileM * 16;  // all taps of one tile
+    static constexpr int kBBytes = 9 * kChunks * COUT * 16;    // all weights
+    static constexpr int kBytes = kABytes + kBBytes;
+    static constexpr int kTmemCols = COUT < 32 ? 32 : COUT;
+};
+
+// x: [P][CIN] bf16 with P = B*H*W pixels (NHWC); w: [9][COUT][CIN] bf16 (tap
+// = 3*dy + dx, dy, dx in 0..2 for offsets -1..1); y: [P][COUT] bf16.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv3x3_tc_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
+                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int B,
+                      int H, int W, int relu, int ntiles, int* err)
+{
+    using S = ConvSmem<CIN, COUT>;
+    constexpr int NCH = S::kChunks;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + S::kABytes;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t mbar_a = smem_u32(&mbar);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"((uint32_t)S::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // weights -> [tap][chunk][cout][8]
+    for (int i = tid; i < 9 * COUT * NCH; i += kConvThreads) {
+        const int ch = i % NCH;
+        const int n = (i / NCH) % COUT;
+        const int tap = i / (NCH * COUT);
+        const uint4 v = w[(size_t)(tap * COUT + n) * NCH + ch];
+        *reinterpret_cast<uint4*>(sB + ((tap * NCH + ch) * COUT + n) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    const long P = (long)B * H * W;
+    const uint32_t idesc = mma_idesc(kTileM, COUT);
+    const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        // gather the 9 tap rows of this thread's output pixel
+        const long p = (long)tile * kTileM + tid;
+        const bool valid = p < P;
+        int b = 0, yy = 0, xx = 0;
+        if (valid) {
+            b = (int)(p / ((long)H * W));
+            const int r = (int)(p - (long)b * H * W);
+            yy = r / W;
+            xx = r - yy * W;
+        }
+#pragma unroll 1
+        for (int dy = 0; dy < 3; ++dy) {
+            const int sy = min(max(yy + dy - 1, 0), H - 1);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int sx = min(max(xx + dx - 1, 0), W - 1);
+                const uint4* src = x + (((size_t)b * H + sy) * W + sx) * NCH;
+                const int tap = dy * 3 + dx;
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const uint4 v = valid ? src[ch] : make_uint4(0u, 0u, 0u, 0u);
+                    *reinterpret_cast<uint4*>(sA + ((tap * NCH + ch) * kTileM + tid) * 16) = v;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+                for (int ks = 0; ks < NCH / 2; ++ks) {
+                    const uint64_t ad = smem_desc(a_base + (tap * NCH + 2 * ks) * kTileM * 16,
+                                                  kTileM * 16, 128);
+                    const uint64_t bd =
+                        smem_desc(b_base + (tap * NCH + 2 * ks) * COUT * 16, COUT * 16, 128);
+                    mma_bf16(tmem, ad, bd, idesc, (tap | ks) != 0);
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    mbar_a)
+                : "memory");
+        }
+        // a timed-out wait (never expected) ends the kernel on every thread
+        ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;
+        phase ^= 1u;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: this thread's row = TMEM lane tid
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 32) {
+            float acc[32];
+            tmem_ld32(lane_addr + c0, acc);
+            if (valid) {
+                __nv_bfloat16* out = y + (size_t)p * COUT + c0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float vq = acc[j + q] + bias[c0 + j + q];
+                        if (relu) vq = fmaxf(vq, 0.0f);
+                        o[q] = __float2bfloat16_rn(vq);
+                    }
+                    *reinterpret_cast<uint4*>(out + j) = *reinterpret_cast<const uint4*>(o);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && err) atomicExch(err, 1);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)S::kTmemCols));
+    }
+}
+
+template <int CIN, int COUT>
+hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y, int B, int H,
+                        int W, int relu, int* err, int nsm, cudaStream_t st)
+{
+    using S = ConvSmem<CIN, COUT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+        attr = true;
+    }
+    const long P = (long)B * H * W;
+    const int ntiles = (int)((P + kTileM - 1) / kTileM);
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    conv3x3_tc_kernel<CIN, COUT><<<grid, kConvThreads, S::kBytes, st>>>(
+        (const uint4*)x, (const uint4*)w, bias, (__nv_bfloat16*)y, B, H, W, relu, ntiles, err);
+    return check_launch();
+}
+
+}  // namespace
+
+hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
+                            int H, int W, int cin, int cout, int relu, int* err, int nsm,
+                            cudaStream_t st)
+{
+    if (cin == 32 && cout == 32) return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+    if (cin == 32 && cout == 64) return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+    if (cin == 64 && cout == 32) return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+    if (cin == 64 && cout == 64) return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+    return HP_ERR_UNSUPPORTED;
+}
+
+}  // namespace hp
+
+extern "C" hp_status hp_conv3x3_bf16(const uint16_t* x, const uint16_t* w, const float* bias,
+                                     uint16_t* y, int32_t batch, int32_t height, int32_t width,
+                                     int32_t cin, int32_t cout, int32_t relu, int32_t* err,
+                                     void* stream)
+{
+    if (!x || !w || !bias || !y || batch <= 0 || height <= 0 || width <= 0) return HP_ERR_INVALID_ARG;
+    if ((uintptr_t)x % 16 || (uintptr_t)w % 16 || (uintptr_t)y % 16) return HP_ERR_INVALID_ARG;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { hp::set_cuda_error(e); return HP_ERR_CUDA; }
+    return hp::launch_conv3x3_tc(x, w, bias, y, batch, height, width, cin, cout, relu, err, nsm,
+                                 (cudaStream_t)stream);
+}
