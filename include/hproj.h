@@ -169,6 +169,53 @@ hp_status hp_advect_step(const float *u, const float *v, const float *rho, const
                          float *u_out, float *v_out, float *rho_out, hp_shape shape,
                          const hp_plume_params *params, void *stream);
 
+/* 3 x 3 convolution with replicated borders (the convolutions of the
+ * MultiScale network, Sec. 3.1), on the tensor cores: BF16 inputs and weights,
+ * FP32 accumulation, y = [relu](conv(x, w) + bias) rounded to BF16.
+ *   x     bf16 [batch][height][width][cin]   (NHWC, 16-byte aligned)
+ *   w     bf16 [3][3][cout][cin]             (tap (dy, dx) for offsets -1..1)
+ *   bias  float [cout]
+ *   y     bf16 [batch][height][width][cout]  (16-byte aligned)
+ *   err   optional int32 device word set to 1 if a tensor-core completion
+ *         wait timed out (the call then leaves y incomplete)
+ * (cin, cout) in {32, 64} x {32, 64}; other sizes return HP_ERR_UNSUPPORTED.
+ * Device memory, stream-ordered; bf16 values are passed as their 16-bit
+ * patterns (uint16_t). */
+hp_status hp_conv3x3_bf16(const uint16_t *x, const uint16_t *w, const float *bias, uint16_t *y,
+                          int32_t batch, int32_t height, int32_t width, int32_t cin, int32_t cout,
+                          int32_t relu, int32_t *err, void *stream);
+
+/* MultiScale CNN of the hybrid method (Sec. 3.1): three branches at 1/4,
+ * 1/2 and full resolution, 3 x 3 convolutions with replicated borders, ReLU
+ * after every convolution of a branch except its last two, 2 x 2 / 4 x 4
+ * average pooling down, bilinear x 2 up; input [div / s, flags], s = mean
+ * |div| over fluid cells (1 if zero); 372,643 parameters.  BF16 weights and
+ * activations, FP32 accumulation (tensor cores for the 32/64-channel layers).
+ * An hp_cnn owns its device weights and a workspace for grids up to
+ * max_shape (ny, nx multiples of 4). */
+typedef struct hp_cnn hp_cnn;
+int64_t hp_cnn_param_count(void);
+hp_status hp_cnn_create(hp_cnn **cnn, hp_shape max_shape, int device);
+void hp_cnn_destroy(hp_cnn *cnn);
+/* params: HOST float [hp_cnn_param_count()], layers in the order scale 1/4
+ * (5 layers), 1/2 (7), 1 (7); per layer weights [cout][cin][3][3] then bias
+ * [cout].  Weights are rounded to BF16 on upload; synchronous. */
+hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
+hp_status hp_cnn_get_params(const hp_cnn *cnn, float *params, int64_t n);
+/* Network output phi_hat (float [B][ny][nx], device; the guess is s * phi_hat)
+ * and s (float [B], device, may be NULL) for the divergence div (float
+ * [B][ny][nx]) and flags. */
+hp_status hp_cnn_forward(hp_cnn *cnn, const float *div, const uint8_t *flags, float *phi_hat,
+                         float *s_out, hp_shape shape, void *stream);
+/* Hybrid projection (Sec. 3.3): phi_0 = s * CNN(div / s, flags) (0 on cells
+ * without an open face), then hp_project from phi_0.  Same arguments and
+ * outputs as hp_project. */
+hp_status hp_project_hybrid(hp_ctx *ctx, hp_cnn *cnn, float *u, float *v, const uint8_t *flags,
+                            hp_shape shape, const hp_project_params *params, float *p_out,
+                            int32_t *iters_out, double *e1_out, double *einf_out,
+                            uint8_t *converged_out, double *e_hist, int32_t hist_len,
+                            void *stream);
+
 /* Allocation-free variant of hp_div_norms.  The paper has no counterpart; it
  * exists for callers that cannot call cudaMalloc: a host framework that owns
  * all device memory through its own pool and forbids other allocations, a

@@ -133,12 +133,22 @@ def upsample2_backward(g):
 
 # --------------------------------------------------------------- network
 
-def forward(params, div, flags, keep=False):
+def round_bf16(x):
+    """Round to the nearest BF16 value (ties to even), returned as FP64."""
+    f = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params, div, flags, keep=False, act_round=None):
     """phi_hat = MultiScale([div_s, flags]) for one grid (H, W divisible by 4).
 
     div_s is the already scaled divergence (the caller divides by s and
     multiplies the output by s).  With keep=True returns (out, tape) for
-    backward."""
+    backward.  act_round (e.g. round_bf16) is applied to every branch input
+    and to every activation that feeds another convolution, to model a
+    reduced-precision storage of activations; the arithmetic stays FP64."""
+    rnd = act_round if act_round is not None else (lambda a: a)
     x0 = np.stack([np.asarray(div, np.float64), (np.asarray(flags) != 0).astype(np.float64)])
     xin = {1: x0, 2: avgpool2(x0)}
     xin[4] = avgpool2(xin[2])
@@ -147,14 +157,31 @@ def forward(params, div, flags, keep=False):
     prev = None
     for sc in SCALES:
         h = xin[sc] if prev is None else np.concatenate([xin[sc], upsample2(prev)], axis=0)
-        for l in range(len(BRANCH_WIDTHS[sc]) - 1):
+        h = rnd(h)
+        nl = len(BRANCH_WIDTHS[sc]) - 1
+        for l in range(nl):
             w, b = next(p)
             pre = conv3x3(h, w, b)
             out = np.maximum(pre, 0.0) if relu_after(sc, l) else pre
             tape.append((sc, l, h, pre))
-            h = out
+            h = rnd(out) if l < nl - 1 else out
         prev = h
     return (prev[0], tape) if keep else prev[0]
+
+
+def flatten(params):
+    """Flat FP32-order vector: per layer weights [cout][cin][3][3], then bias."""
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params])
+
+
+def unflatten(flat):
+    out, k = [], 0
+    for _, _, ws, bs in param_shapes():
+        nw, nb = int(np.prod(ws)), int(np.prod(bs))
+        out.append((np.asarray(flat[k:k + nw], np.float64).reshape(ws),
+                    np.asarray(flat[k + nw:k + nw + nb], np.float64)))
+        k += nw + nb
+    return out
 
 
 def backward(params, tape, g_out):

@@ -56,6 +56,18 @@ _SIGS = {
     "hp_div_norms_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
     "hp_advect_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, hp_shape,
                                       ctypes.POINTER(hp_plume_params), _P]),
+    "hp_conv3x3_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, _P, _P]),
+    "hp_cnn_param_count": (ctypes.c_int64, []),
+    "hp_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
+    "hp_cnn_destroy": (None, [_P]),
+    "hp_cnn_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "hp_cnn_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "hp_cnn_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
+    "hp_project_hybrid": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape,
+                                         ctypes.POINTER(hp_project_params), _P, _P, _P, _P, _P,
+                                         _P, ctypes.c_int32, _P]),
 }
 
 
@@ -301,10 +313,111 @@ def hp_advect_step(u, v, rho, flags, params: PlumeParams, u_out=None, v_out=None
     return u_out, v_out, rho_out
 
 
+def hp_conv3x3_bf16(x, w, bias, relu: bool, y=None, err=None, stream=None):
+    """y = [relu](conv3x3_replicate(x, w) + bias) on the tensor cores.
+    x: bf16 [B][H][W][Cin]; w: bf16 [3][3][Cout][Cin]; bias: float32 [Cout]."""
+    torch = _torch()
+    B, H, W, cin = x.shape
+    cout = w.shape[2]
+    if x.dtype != torch.bfloat16 or w.dtype != torch.bfloat16 or bias.dtype != torch.float32:
+        raise HprojError("x, w must be bfloat16 and bias float32")
+    if tuple(w.shape) != (3, 3, cout, cin):
+        raise HprojError("w must be [3][3][cout][cin]")
+    if y is None:
+        y = torch.empty((B, H, W, cout), dtype=torch.bfloat16, device=x.device)
+    _check(load_library().hp_conv3x3_bf16(_ptr(x), _ptr(w), _ptr(bias), _ptr(y), B, H, W, cin,
+                                          cout, int(bool(relu)), _ptr(err), _stream(stream)))
+    return y
+
+
+class CNN:
+    """MultiScale CNN weights and workspace on the device (hp_cnn)."""
+
+    def __init__(self, batch: int, ny: int, nx: int, device: int | None = None, params=None):
+        torch = _torch()
+        lib = load_library()
+        dev = torch.cuda.current_device() if device is None else device
+        self._h = _P()
+        _check(lib.hp_cnn_create(ctypes.byref(self._h), hp_shape(batch, ny, nx), dev))
+        if params is not None:
+            self.set_params(params)
+
+    @staticmethod
+    def param_count() -> int:
+        return int(load_library().hp_cnn_param_count())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(load_library().hp_cnn_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                a.size))
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.param_count(), dtype=np.float32)
+        _check(load_library().hp_cnn_get_params(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                a.size))
+        return a
+
+    def close(self):
+        if self._h:
+            load_library().hp_cnn_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hp_cnn_forward(cnn: CNN, div, flags, phi_hat=None, s_out=None, stream=None):
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(div, torch.float32, (B, ny, nx), "div")
+    phi_hat = torch.empty_like(div) if phi_hat is None else phi_hat
+    s_out = torch.empty(B, dtype=torch.float32, device=div.device) if s_out is None else s_out
+    _check(load_library().hp_cnn_forward(cnn.handle, _ptr(div), _ptr(flags), _ptr(phi_hat),
+                                         _ptr(s_out), s, _stream(stream)))
+    return phi_hat, s_out
+
+
+def hp_project_hybrid(ctx: Context, cnn: CNN, u, v, flags, params: ProjectParams, hist_len=0,
+                      stream=None, out=None):
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(u, torch.float32, (B, ny, nx + 1), "u")
+    _check_dtype(v, torch.float32, (B, ny + 1, nx), "v")
+    dev = u.device
+    if out is None:
+        out = {"p": torch.empty((B, ny, nx), dtype=torch.float32, device=dev),
+               "iters": torch.empty(B, dtype=torch.int32, device=dev),
+               "e1": torch.empty(B, dtype=torch.float64, device=dev),
+               "einf": torch.empty(B, dtype=torch.float64, device=dev),
+               "converged": torch.empty(B, dtype=torch.uint8, device=dev)}
+        if hist_len > 0:
+            out["e_hist"] = torch.full((B, hist_len), float("nan"), dtype=torch.float64,
+                                       device=dev)
+    prm = params.c()
+    hist = out.get("e_hist")
+    _check(load_library().hp_project_hybrid(
+        ctx.handle, cnn.handle, _ptr(u), _ptr(v), _ptr(flags), s, ctypes.byref(prm),
+        _ptr(out["p"]), _ptr(out["iters"]), _ptr(out["e1"]), _ptr(out["einf"]),
+        _ptr(out["converged"]), _ptr(hist), ctypes.c_int32(hist.shape[1] if hist is not None
+                                                           else 0), _stream(stream)))
+    return out
+
+
 def exported_symbols():
     """Names of the functions declared in include/hproj.h (parsed from the header)."""
     import re
     hdr = os.path.join(HERE, "..", "include", "hproj.h")
     txt = open(hdr).read()
-    return sorted(set(re.findall(r"^\s*(?:hp_status|void|const char \*)\s*(hp_\w+)\s*\(", txt,
-                                 re.M)))
+    return sorted(set(re.findall(r"^\s*(?:hp_status|void|int64_t|const char \*)\s*(hp_\w+)\s*\(",
+                                 txt, re.M)))

@@ -113,6 +113,9 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
                        float* phi_copy_out);
 
 int ctas_per_grid(int ny, int nx, int T);
+hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
+                            int H, int W, int cin, int cout, int relu, int* err, int nsm,
+                            cudaStream_t st);
 hp_status launch_advect(const float* u, const float* v, const float* rho, const uint8_t* flags,
                         float* u_out, float* v_out, float* rho_out, hp_shape s,
                         const hp_plume_params& p, cudaStream_t st);

@@ -19,7 +19,8 @@ def test_header_declares_the_boundary():
     names = hp.exported_symbols()
     for n in ["hp_ctx_create", "hp_ctx_destroy", "hp_face_mask", "hp_divergence",
               "hp_div_norms", "hp_project", "hp_jacobi_sweeps", "hp_status_string",
-              "hp_advect_step",
+              "hp_advect_step", "hp_conv3x3_bf16", "hp_cnn_create", "hp_cnn_forward",
+              "hp_project_hybrid", "hp_cnn_param_count",
               "hp_last_cuda_error"]:
         assert n in names
 
@@ -49,3 +50,8 @@ def test_binding_rejects_cpu_tensors():
     torch = pytest.importorskip("torch")
     with pytest.raises(hp.HprojError):
         hp.hp_face_mask(torch.zeros((1, 4, 4), dtype=torch.uint8))
+
+
+def test_cnn_parameter_count_matches_the_oracle(lib):
+    from oracle import cnn as C
+    assert int(lib.hp_cnn_param_count()) == C.param_count() == 372643
