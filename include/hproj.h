@@ -185,6 +185,20 @@ hp_status hp_conv3x3_bf16(const uint16_t *x, const uint16_t *w, const float *bia
                           int32_t batch, int32_t height, int32_t width, int32_t cin, int32_t cout,
                           int32_t relu, int32_t *err, void *stream);
 
+/* Adjoint of the fixed-count projection (the paper trains its networks through
+ * the solver and notes that the gradient of the correction is known,
+ * Sec. 3.2).  Forward map (hp_project with fixed_iters = k and a guess phi0):
+ * (u*, v*, phi_0) -> (u, v, p).  Given gu = dL/du, gv = dL/dv and gp = dL/dp
+ * (may be NULL), returns dL/du*, dL/dv* (0 on closed faces) and dL/dphi_0,
+ * using k transposed sweeps (no stored iterates: the map is affine).
+ * gu, gu_star float [B][ny][nx+1]; gv, gv_star [B][ny+1][nx]; gp, g_phi0
+ * [B][ny][nx]; device memory; outputs must not alias inputs.  Uses the
+ * context's workspaces. */
+hp_status hp_project_adjoint(hp_ctx *ctx, const float *gu, const float *gv, const float *gp,
+                             const uint8_t *flags, hp_shape shape, int32_t k, float dt,
+                             float rho0, float *gu_star, float *gv_star, float *g_phi0,
+                             void *stream);
+
 /* MultiScale CNN of the hybrid method (Sec. 3.1): three branches at 1/4,
  * 1/2 and full resolution, 3 x 3 convolutions with replicated borders, ReLU
  * after every convolution of a branch except its last two, 2 x 2 / 4 x 4

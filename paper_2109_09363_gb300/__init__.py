@@ -59,6 +59,8 @@ _SIGS = {
     "hp_conv3x3_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, _P, _P]),
+    "hp_project_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, ctypes.c_int32,
+                                          ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
     "hp_cnn_param_count": (ctypes.c_int64, []),
     "hp_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
     "hp_cnn_destroy": (None, [_P]),
@@ -328,6 +330,23 @@ def hp_conv3x3_bf16(x, w, bias, relu: bool, y=None, err=None, stream=None):
     _check(load_library().hp_conv3x3_bf16(_ptr(x), _ptr(w), _ptr(bias), _ptr(y), B, H, W, cin,
                                           cout, int(bool(relu)), _ptr(err), _stream(stream)))
     return y
+
+
+def hp_project_adjoint(ctx: Context, gu, gv, gp, flags, k: int, dt: float = 1.0,
+                       rho0: float = 1.0, stream=None):
+    """(dL/du*, dL/dv*, dL/dphi_0) of the fixed-count projection."""
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(gu, torch.float32, (B, ny, nx + 1), "gu")
+    _check_dtype(gv, torch.float32, (B, ny + 1, nx), "gv")
+    _check_dtype(gp, torch.float32, (B, ny, nx), "gp")
+    gus, gvs = torch.empty_like(gu), torch.empty_like(gv)
+    gphi = torch.empty((B, ny, nx), dtype=torch.float32, device=gu.device)
+    _check(load_library().hp_project_adjoint(ctx.handle, _ptr(gu), _ptr(gv), _ptr(gp),
+                                             _ptr(flags), s, int(k), float(dt), float(rho0),
+                                             _ptr(gus), _ptr(gvs), _ptr(gphi), _stream(stream)))
+    return gus, gvs, gphi
 
 
 class CNN:
