@@ -29,5 +29,8 @@ def project_fixed_adjoint(gu, gv, gp, flags, k, dt=1.0, rho0=1.0):
     if gp is not None:
         lam = lam + (rho0 / dt) * np.asarray(gp, np.float64).reshape(lam.shape)
     g_phi0, g_div = oracle.jacobi_adjoint(lam, flags, k)
+    # the forward sets phi_0 to zero on cells without an open face, so the
+    # gradient of those entries is zero (also for k = 0)
+    g_phi0 = g_phi0 * (oracle.face_mask(flags) > 0)
     gus, gvs = oracle.correct(gu, gv, g_div, flags)
     return gus, gvs, g_phi0
