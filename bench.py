@@ -205,6 +205,68 @@ def profile_sweep(batch: int, n: int, sweeps: int, host_loop: bool = False,
     return 0
 
 
+def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain, ws):
+    """CNN-hybrid projection of the same grids to the same threshold.
+
+    Untimed set-up: training pairs from the plain solver (128^2, vortex field +
+    divergence sources + 0-4 obstacles), Adam training on the GPU.  Timed: the
+    same per-step protocol as the plain arm (device restore of u*, L2 flush
+    between steps, CUDA events)."""
+    import torch
+    from paper_2109_09363_gb300 import training as T
+    t0 = time.perf_counter()
+    n_tr = 128
+    data = T.generate_pairs(2048, n_tr, seed0=0, threshold=1e-6, max_iters=8000,
+                            device=u0.device)
+    batch = 32
+    epochs = max(1, (args.train_steps * batch + 2047) // 2048)
+    cnn = hp.CNN(batch, n_tr, n_tr, params=T.init_params(seed=1))
+    losses = T.train(cnn, data, epochs=epochs, batch=batch, lr=1e-3, lambda_div=1.0)
+    t_train = time.perf_counter() - t0
+    del data
+    cnn_eval = hp.CNN(B, N, N, params=cnn.get_params())
+    cnn.close()
+    out = None
+
+    def step():
+        nonlocal out
+        u.copy_(u0)
+        v.copy_(v0)
+        out = hp.hp_project_hybrid(ctx, cnn_eval, u, v, fl, prm, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    iters = out["iters"].cpu().numpy()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for s_ in range(args.steps):
+        flush.fill_(float(s_))
+        ev[s_][0].record(stream)
+        step()
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    # inference alone (t_inf of the paper)
+    div = hp.hp_divergence(u0, v0, fl)
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hp.hp_cnn_forward(cnn_eval, div, fl)
+    a.record(stream)
+    for _ in range(5):
+        hp.hp_cnn_forward(cnn_eval, div, fl)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    t_inf = a.elapsed_time(b_) / 5
+    cnn_eval.close()
+    return {"value": ws * B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "speedup_vs_plain": ms_plain / ms, "iters_per_grid": iters.tolist(),
+            "converged": int(out["converged"].sum().item()),
+            "t_inf_ms_16_grids": t_inf,
+            "training": {"pairs": 2048, "grid": [n_tr, n_tr], "steps": len(losses),
+                         "batch": batch, "final_loss": float(np.mean(losses[-20:])),
+                         "seconds": t_train}}
+
+
 def main():
     global T_BLOCK
     ap = argparse.ArgumentParser()
@@ -220,6 +282,10 @@ def main():
                     help="sweeps per launch of the temporally blocked kernel (1..8)")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="0 = library choice, 1 = streaming, 2 = temporally blocked")
+    ap.add_argument("--no-hybrid", action="store_true",
+                    help="skip the CNN-hybrid arm (training + timing)")
+    ap.add_argument("--train-steps", type=int, default=1200,
+                    help="Adam steps of the network trained for the hybrid arm")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the sweep blocks from a host-polled loop instead of the "
                          "CUDA-graph conditional loop (same kernels; ncu cannot profile kernel "
@@ -364,6 +430,10 @@ def main():
     h2d = hu.nbytes + hv.nbytes + hf.nbytes
     d2h = ou.nbytes + ov.nbytes + op.nbytes + oi.nbytes
 
+    hybrid = None
+    if not args.no_hybrid:
+        hybrid = run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms, ws)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -394,6 +464,8 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
         }
+        if hybrid is not None:
+            line["hybrid"] = hybrid
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(u_np, v_np, fl_np)
         print(json.dumps(line), flush=True)

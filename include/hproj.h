@@ -230,6 +230,36 @@ hp_status hp_project_hybrid(hp_ctx *ctx, hp_cnn *cnn, float *u, float *v, const 
                             uint8_t *converged_out, double *e_hist, int32_t hist_len,
                             void *stream);
 
+/* Training of the MultiScale CNN (Sec. 3.2 trains the networks with a
+ * gradient-descent algorithm): FP32 master weights on the device, Adam,
+ * BF16 weights of the hp_cnn refreshed after every step.  Loss per grid,
+ * averaged over the batch, with t = target / s (target = the scaled pressure
+ * phi* of the plain solver), d = div / s and e = phi_hat - t:
+ * sum over fluid cells of (e - mean e)^2 / sum over fluid cells of
+ * (t - mean t)^2, plus lambda_div * sum r^2 / sum d^2 with r = d - L phi_hat
+ * on cells with an open face.  The trainer keeps every activation of a batch
+ * up to max_shape (ny, nx multiples of 4). */
+typedef struct hp_trainer hp_trainer;
+typedef struct {
+    float lr, beta1, beta2, eps;
+    float lambda_div;
+} hp_train_params;
+hp_status hp_trainer_create(hp_trainer **trainer, hp_cnn *cnn, hp_shape max_shape);
+void hp_trainer_destroy(hp_trainer *trainer);
+/* Loss (double [1], device, may be NULL) and its gradient w.r.t. every
+ * parameter (float [hp_cnn_param_count()], device, may be NULL; network
+ * parameter order) for one batch; div, target float [B][ny][nx], flags u8. */
+hp_status hp_trainer_gradient(hp_trainer *trainer, const float *div, const uint8_t *flags,
+                              const float *target, hp_shape shape, float lambda_div,
+                              float *grad_out, double *loss_out, void *stream);
+/* One Adam step on one batch; loss_out as above. */
+hp_status hp_trainer_step(hp_trainer *trainer, const float *div, const uint8_t *flags,
+                          const float *target, hp_shape shape, const hp_train_params *params,
+                          double *loss_out, void *stream);
+/* Copy the trained FP32 masters into the hp_cnn (hp_cnn_get_params then
+ * returns them); synchronises the device. */
+hp_status hp_trainer_sync_params(hp_trainer *trainer);
+
 /* Allocation-free variant of hp_div_norms.  The paper has no counterpart; it
  * exists for callers that cannot call cudaMalloc: a host framework that owns
  * all device memory through its own pool and forbids other allocations, a

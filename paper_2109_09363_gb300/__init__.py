@@ -61,6 +61,11 @@ _SIGS = {
                                        ctypes.c_int32, _P, _P]),
     "hp_project_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, ctypes.c_int32,
                                           ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
+    "hp_trainer_create": (ctypes.c_int, [ctypes.POINTER(_P), _P, hp_shape]),
+    "hp_trainer_destroy": (None, [_P]),
+    "hp_trainer_gradient": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_float, _P, _P, _P]),
+    "hp_trainer_step": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_void_p, _P, _P]),
+    "hp_trainer_sync_params": (ctypes.c_int, [_P]),
     "hp_cnn_param_count": (ctypes.c_int64, []),
     "hp_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
     "hp_cnn_destroy": (None, [_P]),
@@ -385,6 +390,57 @@ class CNN:
     def close(self):
         if self._h:
             load_library().hp_cnn_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class hp_train_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("lambda_div", ctypes.c_float)]
+
+
+class Trainer:
+    """Adam training of a CNN on the device (hp_trainer)."""
+
+    def __init__(self, cnn: CNN, batch: int, ny: int, nx: int):
+        self.cnn = cnn
+        self._h = _P()
+        _check(load_library().hp_trainer_create(ctypes.byref(self._h), cnn.handle,
+                                                hp_shape(batch, ny, nx)))
+
+    def gradient(self, div, flags, target, lambda_div=0.1, stream=None):
+        torch = _torch()
+        s = _shape_of_flags(flags)
+        g = torch.empty(CNN.param_count(), dtype=torch.float32, device=div.device)
+        loss = torch.empty(1, dtype=torch.float64, device=div.device)
+        _check(load_library().hp_trainer_gradient(self._h, _ptr(div), _ptr(flags), _ptr(target),
+                                                  s, float(lambda_div), _ptr(g), _ptr(loss),
+                                                  _stream(stream)))
+        return g, loss
+
+    def step(self, div, flags, target, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+             lambda_div=0.1, loss_out=None, stream=None):
+        torch = _torch()
+        s = _shape_of_flags(flags)
+        if loss_out is None:
+            loss_out = torch.empty(1, dtype=torch.float64, device=div.device)
+        prm = hp_train_params(lr, beta1, beta2, eps, lambda_div)
+        _check(load_library().hp_trainer_step(self._h, _ptr(div), _ptr(flags), _ptr(target), s,
+                                              ctypes.cast(ctypes.byref(prm), ctypes.c_void_p),
+                                              _ptr(loss_out), _stream(stream)))
+        return loss_out
+
+    def sync_params(self):
+        _check(load_library().hp_trainer_sync_params(self._h))
+
+    def close(self):
+        if self._h:
+            load_library().hp_trainer_destroy(self._h)
             self._h = _P()
 
     def __del__(self):

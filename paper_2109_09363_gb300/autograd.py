@@ -15,7 +15,10 @@ class ProjectFixed(torch.autograd.Function):
     def forward(ctx, u_star, v_star, phi0, flags, hctx, k, dt, rho0):
         u = u_star.detach().clone().contiguous()
         v = v_star.detach().clone().contiguous()
-        prm = hp.ProjectParams(fixed_iters=int(k), dt=float(dt), rho0=float(rho0))
+        if int(k) > 0:
+            prm = hp.ProjectParams(fixed_iters=int(k), dt=float(dt), rho0=float(rho0))
+        else:  # zero sweeps: the cap is reached at k = 0
+            prm = hp.ProjectParams(threshold=0.0, max_iters=0, dt=float(dt), rho0=float(rho0))
         out = hp.hp_project(hctx, u, v, flags, prm, phi0=phi0.detach().contiguous())
         ctx.save_for_backward(flags)
         ctx.hctx, ctx.k, ctx.dt, ctx.rho0 = hctx, int(k), float(dt), float(rho0)

@@ -117,7 +117,7 @@ struct BranchIn {
 // w: float [9][cin][32] (BF16-rounded values), bias float [32].
 __global__ void conv_first_kernel(BranchIn in, int cin, const float* __restrict__ w,
                                   const float* __restrict__ bias, __nv_bfloat16* __restrict__ y,
-                                  int B)
+                                  int B, float* __restrict__ xin_out)
 {
     __shared__ float sw[9 * 3 * 32];
     __shared__ float sb[32];
@@ -134,6 +134,12 @@ __global__ void conv_first_kernel(BranchIn in, int cin, const float* __restrict_
         float acc[32];
 #pragma unroll
         for (int o = 0; o < 32; ++o) acc[o] = 0.0f;
+        if (xin_out) {
+            // the branch input of this pixel, kept for the weight gradient
+            float xc[3];
+            in.at(b, i, j, xc);
+            for (int c = 0; c < cin; ++c) xin_out[(size_t)p * cin + c] = xc[c];
+        }
         for (int dy = 0; dy < 3; ++dy)
             for (int dx = 0; dx < 3; ++dx) {
                 float xv[3];
@@ -357,7 +363,7 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
         int cur = 0;
         const int blocks = (int)((P + 255) / 256 < 8L * c->num_sms ? (P + 255) / 256 : 8L * c->num_sms);
         conv_first_kernel<<<blocks, 256, 0, st>>>(in, kSpec[l].cin, (const float*)c->w[l],
-                                                  c->bias[l], c->act[cur], s.batch);
+                                                  c->bias[l], c->act[cur], s.batch, nullptr);
         if ((rc = check_launch()) != HP_OK) return rc;
         ++l;
         while (kSpec[l].cout != 1) {
@@ -401,6 +407,667 @@ hp_status hp_project_hybrid(hp_ctx* ctx, hp_cnn* cnn, float* u, float* v, const 
     if ((rc = check_launch()) != HP_OK) return rc;
     return hp_project(ctx, u, v, flags, s, prm, ctx->phi[1], p_out, iters_out, e1_out, einf_out,
                       conv_out, e_hist, hist_len, stream);
+}
+
+}  // extern "C"
+
+// ======================================================================
+// Training of the MultiScale CNN (Sec. 3.2: the networks are trained with a
+// gradient-descent algorithm; here the pairs come from the plain solver).
+// FP32 master weights, Adam, BF16 weights refreshed after every step; the
+// backward convolutions run on CUDA cores in FP32.
+//
+// Loss per grid (readings in the design notes), averaged over the batch; both
+// terms are relative (t = phi*/s, d = div/s, e = phi_hat - t):
+//   sup = sum_fluid (e - mean e)^2 / sum_fluid (t - mean t)^2
+//   div = lambda * sum r^2 / sum d^2,  r = d - L phi_hat on cells with an open
+//         face (the divergence of the corrected field of the scaled problem)
+// ======================================================================
+
+namespace hp {
+
+namespace {
+
+__global__ void relu_mask_kernel(float* __restrict__ g, const __nv_bfloat16* __restrict__ y,
+                                 size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(__bfloat162float(y[i]) > 0.0f)) g[i] = 0.0f;
+}
+
+// Input pixel i receives, through tap offset o in {-1, 0, 1}, from the output
+// rows y with clamp(y + o) == i: among {i-o-1, i-o, i-o+1}.
+__device__ __forceinline__ bool reads(int y, int o, int i, int n)
+{
+    return y >= 0 && y < n && min(max(y + o, 0), n - 1) == i;
+}
+
+// dL/dx of a 3 x 3 convolution with replicated borders: gx[p][ci] = sum over
+// taps and the output pixels that read p through that tap of
+// w[t][co][ci] * gy[o][co].  w: FP32 [9][CO][CI] (the BF16-rounded weights).
+template <int CI, int CO>
+__global__ void conv_dgrad_kernel(const float* __restrict__ gy, const float* __restrict__ w,
+                                  float* __restrict__ gx, int B, int H, int W)
+{
+    extern __shared__ float sw[];
+    for (int q = threadIdx.x; q < 9 * CO * CI; q += blockDim.x) sw[q] = w[q];
+    __syncthreads();
+    const long P = (long)B * H * W;
+    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+         p += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(p / ((long)H * W));
+        const int r = (int)(p - (long)b * H * W);
+        const int i = r / W, j = r - i * W;
+        float acc[CI];
+#pragma unroll
+        for (int c = 0; c < CI; ++c) acc[c] = 0.0f;
+        for (int t = 0; t < 9; ++t) {
+            const int oy = t / 3 - 1, ox = t % 3 - 1;
+            for (int yy = i - oy - 1; yy <= i - oy + 1; ++yy) {
+                if (!reads(yy, oy, i, H)) continue;
+                for (int xx = j - ox - 1; xx <= j - ox + 1; ++xx) {
+                    if (!reads(xx, ox, j, W)) continue;
+                    const float* g = gy + (((size_t)b * H + yy) * W + xx) * CO;
+                    const float* wt = sw + t * CO * CI;
+                    for (int co = 0; co < CO; ++co) {
+                        const float gv = g[co];
+#pragma unroll
+                        for (int c = 0; c < CI; ++c) acc[c] = fmaf(wt[co * CI + c], gv, acc[c]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CI; ++c) gx[(size_t)p * CI + c] = acc[c];
+    }
+}
+
+__device__ __forceinline__ float ld_act(const __nv_bfloat16* x, size_t i) { return __bfloat162float(x[i]); }
+__device__ __forceinline__ float ld_act(const float* x, size_t i) { return x[i]; }
+
+// Weight gradient partial sums over a chunk of pixels for one tap:
+// part[(chunk * 9 + t)][co][ci] = sum_p gy[p][co] * x[clamp(p + offset_t)][ci];
+// the centre tap also writes the bias partials partb[chunk][co] = sum_p gy.
+// Each thread owns a BCO x BCI block of (co, ci).
+template <int CI, int CO, int BCI, int BCO, typename XT>
+__global__ void conv_wgrad_kernel(const float* __restrict__ gy, const XT* __restrict__ x,
+                                  float* __restrict__ part, float* __restrict__ partb, int B,
+                                  int H, int W, int chunk)
+{
+    constexpr int TP = 32;  // pixels per shared-memory tile
+    __shared__ float sg[TP][CO];
+    __shared__ float sx[TP][CI];
+    const int t = blockIdx.y;
+    const int oy = t / 3 - 1, ox = t % 3 - 1;
+    const long P = (long)B * H * W;
+    const long p0 = (long)blockIdx.x * chunk;
+    const long p1 = min(P, p0 + chunk);
+    const int ncb = CI / BCI;
+    const int tco = (threadIdx.x / ncb) * BCO, tci = (threadIdx.x % ncb) * BCI;
+    float acc[BCO][BCI];
+    float accb[BCO];
+#pragma unroll
+    for (int a = 0; a < BCO; ++a) {
+        accb[a] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < BCI; ++c) acc[a][c] = 0.0f;
+    }
+    for (long pt = p0; pt < p1; pt += TP) {
+        for (int q = threadIdx.x; q < TP * CO; q += blockDim.x) {
+            const long p = pt + q / CO;
+            sg[q / CO][q % CO] = p < p1 ? gy[(size_t)p * CO + q % CO] : 0.0f;
+        }
+        for (int q = threadIdx.x; q < TP * CI; q += blockDim.x) {
+            const long p = pt + q / CI;
+            float v = 0.0f;
+            if (p < p1) {
+                const int b = (int)(p / ((long)H * W));
+                const int r = (int)(p - (long)b * H * W);
+                const int i = r / W, j = r - i * W;
+                const int si = min(max(i + oy, 0), H - 1), sj = min(max(j + ox, 0), W - 1);
+                v = ld_act(x, (((size_t)b * H + si) * W + sj) * CI + q % CI);
+            }
+            sx[q / CI][q % CI] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < (CO / BCO) * ncb) {
+            for (int k = 0; k < TP; ++k) {
+#pragma unroll
+                for (int a = 0; a < BCO; ++a) {
+                    const float g = sg[k][tco + a];
+                    accb[a] += g;
+#pragma unroll
+                    for (int c = 0; c < BCI; ++c) acc[a][c] = fmaf(g, sx[k][tci + c], acc[a][c]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < (CO / BCO) * ncb) {
+        float* dst = part + ((size_t)blockIdx.x * 9 + t) * CO * CI;
+#pragma unroll
+        for (int a = 0; a < BCO; ++a)
+#pragma unroll
+            for (int c = 0; c < BCI; ++c) dst[(tco + a) * CI + tci + c] = acc[a][c];
+        if (t == 4 && tci == 0)
+#pragma unroll
+            for (int a = 0; a < BCO; ++a) partb[(size_t)blockIdx.x * CO + tco + a] = accb[a];
+    }
+}
+
+// grad[co][ci][t] (oracle order) = sum over chunks, in order; bias likewise.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ partb,
+                                    int nchunks, int CI, int CO, float* __restrict__ gw,
+                                    float* __restrict__ gb)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = 9 * CO * CI;
+    if (q < nw) {
+        const int t = q % 9, ci = (q / 9) % CI, co = q / (9 * CI);
+        double s = 0.0;
+        for (int k = 0; k < nchunks; ++k) s += part[((size_t)k * 9 + t) * CO * CI + co * CI + ci];
+        gw[q] = (float)s;
+    } else if (q < nw + CO) {
+        const int co = q - nw;
+        double s = 0.0;
+        for (int k = 0; k < nchunks; ++k) s += partb[(size_t)k * CO + co];
+        gb[co] = (float)s;
+    }
+}
+
+// transpose of the bilinear x 2 up-sampling (gradient of the coarse output)
+// from channel `ch` of a fine-grid gradient with `stride` channels
+__device__ __forceinline__ float up_w(int f, int I, int n)
+{
+    const int c = f >> 1, a = f & 1;
+    const int nb = a ? min(c + 1, n - 1) : max(c - 1, 0);
+    return (c == I ? 0.75f : 0.0f) + (nb == I ? 0.25f : 0.0f);
+}
+
+__global__ void upsample_adjoint_kernel(const float* __restrict__ gfine, int stride, int ch,
+                                        float* __restrict__ gcoarse, int B, int hc, int wc)
+{
+    const long P = (long)B * hc * wc;
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int b = (int)(p / ((long)hc * wc));
+    const int r = (int)(p - (long)b * hc * wc);
+    const int J = r / wc, I = r - J * wc;
+    const int hf = 2 * hc, wf = 2 * wc;
+    float s = 0.0f;
+    for (int fy = 2 * J - 1; fy <= 2 * J + 2; ++fy) {
+        if (fy < 0 || fy >= hf) continue;
+        const float wy = up_w(fy, J, hc);
+        if (wy == 0.0f) continue;
+        for (int fx = 2 * I - 1; fx <= 2 * I + 2; ++fx) {
+            if (fx < 0 || fx >= wf) continue;
+            const float wx = up_w(fx, I, wc);
+            if (wx == 0.0f) continue;
+            s += wy * wx * gfine[(((size_t)b * hf + fy) * wf + fx) * stride + ch];
+        }
+    }
+    gcoarse[p] = s;
+}
+
+// residual of the scaled problem and per-grid loss sums (one CTA per grid):
+// stats[b] = {sum_f e, sum_f e^2, N_f, sum r^2, sum_f t, sum_f t^2, sum d^2}
+// with t = target/s, d = div/s, e = phi - t
+constexpr int kStats = 7;
+
+__global__ void loss_stats_kernel(const float* __restrict__ phi, const float* __restrict__ target,
+                                  const float* __restrict__ div, const uint8_t* __restrict__ mask,
+                                  const uint8_t* __restrict__ flags, const float* __restrict__ s,
+                                  float* __restrict__ rbuf, double* __restrict__ stats, int ny,
+                                  int nx)
+{
+    __shared__ double sh[kStats][32];
+    const int b = blockIdx.x;
+    const size_t cells = (size_t)ny * nx, base = (size_t)b * cells;
+    const float inv_s = 1.0f / s[b];
+    double v[kStats] = {0, 0, 0, 0, 0, 0, 0};
+    for (size_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        const uint32_t m = mask[base + c];
+        const float pc = phi[base + c];
+        const float dc = div[base + c] * inv_s;
+        float r = 0.0f;
+        if (m & 15u) {
+            float lap = 0.0f;
+            if (m & 1u) lap += phi[base + c - 1] - pc;
+            if (m & 2u) lap += phi[base + c + 1] - pc;
+            if (m & 4u) lap += phi[base + c - nx] - pc;
+            if (m & 8u) lap += phi[base + c + nx] - pc;
+            r = dc - lap;
+        }
+        rbuf[base + c] = r;
+        v[3] += (double)r * r;
+        v[6] += (double)dc * dc;
+        if (flags[base + c] == 0) {
+            const double t = (double)target[base + c] * inv_s;
+            const double e = (double)pc - t;
+            v[0] += e;
+            v[1] += e * e;
+            v[2] += 1.0;
+            v[4] += t;
+            v[5] += t * t;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < kStats; ++k) {
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+        if (lane == 0) sh[k][wid] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < kStats) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+        stats[(size_t)b * kStats + threadIdx.x] = t;
+    }
+}
+
+__device__ __forceinline__ double target_var(const double* st)
+{
+    return st[2] > 0.0 ? st[5] - st[4] * st[4] / st[2] : 0.0;
+}
+
+// dL/dphi_hat per cell
+__global__ void loss_grad_kernel(const float* __restrict__ phi, const float* __restrict__ target,
+                                 const float* __restrict__ rbuf, const uint8_t* __restrict__ mask,
+                                 const uint8_t* __restrict__ flags, const float* __restrict__ s,
+                                 const double* __restrict__ stats, float lambda,
+                                 float* __restrict__ g, int B, int ny, int nx)
+{
+    const size_t cells = (size_t)ny * nx;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)B * cells) return;
+    const int b = (int)(q / cells);
+    const double* st = stats + (size_t)b * kStats;
+    const double nf = st[2], vt = target_var(st), d2 = st[6];
+    float gv = 0.0f;
+    if (flags[q] == 0 && nf > 0.0 && vt > 0.0) {
+        const double e = (double)phi[q] - (double)target[q] / s[b];
+        gv = (float)(2.0 * (e - st[0] / nf) / (vt * B));
+    }
+    const uint32_t m = mask[q];
+    if ((m & 15u) && d2 > 0.0) {
+        const float rc = rbuf[q];
+        float lr = 0.0f;
+        if (m & 1u) lr += rbuf[q - 1] - rc;
+        if (m & 2u) lr += rbuf[q + 1] - rc;
+        if (m & 4u) lr += rbuf[q - nx] - rc;
+        if (m & 8u) lr += rbuf[q + nx] - rc;
+        gv -= (float)(2.0 * lambda / (d2 * B)) * lr;
+    }
+    g[q] = gv;
+}
+
+__global__ void loss_finish_kernel(const double* __restrict__ stats, int B, size_t cells,
+                                   float lambda, double* __restrict__ loss)
+{
+    double L = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double* st = stats + (size_t)b * kStats;
+        const double vt = target_var(st);
+        if (st[2] > 0.0 && vt > 0.0) L += (st[1] - st[0] * st[0] / st[2]) / vt;
+        if (st[6] > 0.0) L += lambda * st[3] / st[6];
+    }
+    (void)cells;
+    *loss = L / B;
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// masters (oracle order [co][ci][3][3] + bias) of one layer -> the layouts of
+// the forward kernels (BF16-rounded) and the FP32 [9][co][ci] copy for dgrad
+__global__ void pack_layer_kernel(const float* __restrict__ master, int ci, int co, int kind,
+                                  void* __restrict__ wfwd, float* __restrict__ bias,
+                                  float* __restrict__ wt)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = 9 * ci * co;
+    if (q < nw) {
+        const int t = q % 9, i = (q / 9) % ci, o = q / (9 * ci);
+        const __nv_bfloat16 h = __float2bfloat16_rn(master[q]);
+        const float f = __bfloat162float(h);
+        if (kind == 0) reinterpret_cast<__nv_bfloat16*>(wfwd)[((size_t)t * co + o) * ci + i] = h;
+        else if (kind == 1) reinterpret_cast<float*>(wfwd)[((size_t)t * ci + i) * co + o] = f;
+        else reinterpret_cast<float*>(wfwd)[(size_t)t * ci + i] = f;
+        wt[((size_t)t * co + o) * ci + i] = f;
+    } else if (q < nw + co) {
+        bias[q - nw] = master[q];
+    }
+}
+
+}  // namespace
+
+}  // namespace hp
+
+struct hp_trainer {
+    hp_cnn* cnn;
+    hp_shape max;
+    long param_count;
+    float *master, *grad, *m, *v;
+    float* wt[kLayers];
+    void* act[kLayers];   // layer outputs: bf16 [P][cout] or float [P] (cout == 1)
+    float* xin[3];        // first-layer inputs per branch, FP32 [P][cin]
+    float* g[2];          // gradient ping-pong, FP32 [P][64]
+    float* gsmall;        // first-layer input gradient, FP32 [P][3]
+    float *part, *partb;
+    size_t part_len, partb_len;
+    float* rbuf;
+    double* stats;
+    double* loss;
+    uint8_t* mask;
+    int step;
+};
+
+static long layer_offset(int l)
+{
+    long off = 0;
+    for (int k = 0; k < l; ++k) off += (long)layer_wcount(k) + kSpec[k].cout;
+    return off;
+}
+
+static int scale_of(int l) { return kSpec[l].scale; }
+
+static hp_status trainer_pack(hp_trainer* t, cudaStream_t st);
+
+extern "C" {
+
+void hp_trainer_destroy(hp_trainer* t)
+{
+    if (!t) return;
+    cudaFree(t->master); cudaFree(t->grad); cudaFree(t->m); cudaFree(t->v);
+    for (int l = 0; l < kLayers; ++l) { cudaFree(t->wt[l]); cudaFree(t->act[l]); }
+    for (int k = 0; k < 3; ++k) cudaFree(t->xin[k]);
+    cudaFree(t->g[0]); cudaFree(t->g[1]); cudaFree(t->gsmall);
+    cudaFree(t->part); cudaFree(t->partb); cudaFree(t->rbuf); cudaFree(t->stats);
+    cudaFree(t->loss); cudaFree(t->mask);
+    delete t;
+}
+
+static constexpr int kWgradChunk = 2048;
+
+hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
+{
+    if (!out || !cnn || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
+    *out = nullptr;
+    hp_trainer* t = new hp_trainer();
+    memset(t, 0, sizeof(*t));
+    t->cnn = cnn;
+    t->max = mx;
+    t->param_count = hp_cnn_param_count();
+    const size_t P = (size_t)mx.batch * mx.ny * mx.nx;
+    bool ok = true;
+    auto al = [&](void** p, size_t bytes) {
+        if (ok && cudaMalloc(p, bytes + 16) != cudaSuccess) ok = false;
+        if (ok) cudaMemset(*p, 0, bytes + 16);
+    };
+    al((void**)&t->master, t->param_count * 4);
+    al((void**)&t->grad, t->param_count * 4);
+    al((void**)&t->m, t->param_count * 4);
+    al((void**)&t->v, t->param_count * 4);
+    for (int l = 0; l < kLayers; ++l) {
+        const int sc = scale_of(l);
+        const size_t Pl = P / (sc * sc);
+        al(&t->act[l], kSpec[l].cout == 1 ? Pl * 4 : Pl * kSpec[l].cout * 2);
+        al((void**)&t->wt[l], layer_wcount(l) * 4);
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int sc = k == 0 ? 4 : k == 1 ? 2 : 1;
+        al((void**)&t->xin[k], P / (sc * sc) * 3 * 4);
+    }
+    al((void**)&t->g[0], P * 64 * 4);
+    al((void**)&t->g[1], P * 64 * 4);
+    al((void**)&t->gsmall, P * 3 * 4);
+    const size_t nchunks = (P + kWgradChunk - 1) / kWgradChunk;
+    t->part_len = nchunks * 9 * 64 * 64;
+    t->partb_len = nchunks * 64;
+    al((void**)&t->part, t->part_len * 4);
+    al((void**)&t->partb, t->partb_len * 4);
+    al((void**)&t->rbuf, P * 4);
+    al((void**)&t->stats, (size_t)mx.batch * kStats * 8);
+    al((void**)&t->loss, 8);
+    al((void**)&t->mask, P);
+    if (!ok) { set_cuda_error(cudaGetLastError()); hp_trainer_destroy(t); return HP_ERR_OOM; }
+    // masters from the network's current parameters
+    cudaError_t e = cudaMemcpy(t->master, cnn->master.data(), t->param_count * 4,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && trainer_pack(t, 0) != HP_OK) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { set_cuda_error(e); hp_trainer_destroy(t); return HP_ERR_CUDA; }
+    *out = t;
+    return HP_OK;
+}
+
+}  // extern "C"
+
+static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
+{
+    for (int l = 0; l < kLayers; ++l) {
+        const int ci = kSpec[l].cin, co = kSpec[l].cout;
+        const int kind = (ci >= 32 && co >= 32) ? 0 : (co == 1 ? 2 : 1);
+        const int n = 9 * ci * co + co;
+        pack_layer_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->master + layer_offset(l), ci, co,
+                                                          kind, t->cnn->w[l], t->cnn->bias[l],
+                                                          t->wt[l]);
+    }
+    return check_launch();
+}
+
+// forward keeping every layer output
+static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t* flags,
+                                 hp_shape s, cudaStream_t st)
+{
+    hp_cnn* c = t->cnn;
+    const size_t cells = (size_t)s.ny * s.nx;
+    cnn_scale_kernel<<<s.batch, 1024, 0, st>>>(div, flags, c->s, cells);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+    const float* prev = nullptr;
+    for (int k = 0, l = 0; k < 3; ++k) {
+        const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
+        const int H = s.ny / scale, W = s.nx / scale;
+        const long P = (long)s.batch * H * W;
+        const int blocks = (int)((P + 255) / 256 < 8L * c->num_sms ? (P + 255) / 256 : 8L * c->num_sms);
+        BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
+        conv_first_kernel<<<blocks, 256, 0, st>>>(in, kSpec[l].cin, (const float*)c->w[l],
+                                                  c->bias[l], (__nv_bfloat16*)t->act[l], s.batch,
+                                                  t->xin[k]);
+        if ((rc = check_launch()) != HP_OK) return rc;
+        ++l;
+        while (kSpec[l].cout != 1) {
+            rc = launch_conv3x3_tc(t->act[l - 1], c->w[l], c->bias[l], t->act[l], s.batch, H, W,
+                                   kSpec[l].cin, kSpec[l].cout, kSpec[l].relu, c->err, c->num_sms,
+                                   st);
+            if (rc != HP_OK) return rc;
+            ++l;
+        }
+        conv_last_kernel<<<blocks, 256, 0, st>>>((const __nv_bfloat16*)t->act[l - 1],
+                                                 (const float*)c->w[l], c->bias[l],
+                                                 (float*)t->act[l], s.batch, H, W);
+        if ((rc = check_launch()) != HP_OK) return rc;
+        prev = (const float*)t->act[l];
+        ++l;
+    }
+    return HP_OK;
+}
+
+template <int CI, int CO>
+static hp_status dgrad(const float* gy, const float* w, float* gx, int B, int H, int W, int nsm,
+                       cudaStream_t st)
+{
+    const size_t smem = (size_t)9 * CI * CO * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(conv_dgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    const long P = (long)B * H * W;
+    const int blocks = (int)((P + 127) / 128 < 4L * nsm ? (P + 127) / 128 : 4L * nsm);
+    conv_dgrad_kernel<CI, CO><<<blocks, 128, smem, st>>>(gy, w, gx, B, H, W);
+    return check_launch();
+}
+
+static hp_status dgrad_dispatch(int ci, int co, const float* gy, const float* w, float* gx, int B,
+                                int H, int W, int nsm, cudaStream_t st)
+{
+    if (ci == 64 && co == 64) return dgrad<64, 64>(gy, w, gx, B, H, W, nsm, st);
+    if (ci == 32 && co == 64) return dgrad<32, 64>(gy, w, gx, B, H, W, nsm, st);
+    if (ci == 64 && co == 32) return dgrad<64, 32>(gy, w, gx, B, H, W, nsm, st);
+    if (ci == 32 && co == 1) return dgrad<32, 1>(gy, w, gx, B, H, W, nsm, st);
+    if (ci == 3 && co == 32) return dgrad<3, 32>(gy, w, gx, B, H, W, nsm, st);
+    return HP_ERR_UNSUPPORTED;
+}
+
+template <int CI, int CO, int BCI, int BCO, typename XT>
+static hp_status wgrad_t(hp_trainer* t, const float* gy, const XT* x, float* gw, float* gb, int B,
+                         int H, int W, cudaStream_t st)
+{
+    const long P = (long)B * H * W;
+    const int nchunks = (int)((P + kWgradChunk - 1) / kWgradChunk);
+    if ((size_t)nchunks * 9 * CO * CI > t->part_len) return HP_ERR_INVALID_ARG;
+    const int threads = ((CO / BCO) * (CI / BCI) + 31) / 32 * 32;
+    conv_wgrad_kernel<CI, CO, BCI, BCO, XT><<<dim3(nchunks, 9), threads, 0, st>>>(
+        gy, x, t->part, t->partb, B, H, W, kWgradChunk);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+    const int n = 9 * CO * CI + CO;
+    wgrad_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->part, t->partb, nchunks, CI, CO, gw, gb);
+    return check_launch();
+}
+
+static hp_status wgrad_dispatch(hp_trainer* t, int l, const float* gy, const void* x, float* gw,
+                                float* gb, int B, int H, int W, cudaStream_t st)
+{
+    const int ci = kSpec[l].cin, co = kSpec[l].cout;
+    const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
+    if (ci == 64 && co == 64) return wgrad_t<64, 64, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
+    if (ci == 32 && co == 64) return wgrad_t<32, 64, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
+    if (ci == 64 && co == 32) return wgrad_t<64, 32, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
+    if (ci == 32 && co == 1) return wgrad_t<32, 1, 1, 1>(t, gy, xb, gw, gb, B, H, W, st);
+    const float* xf = (const float*)x;
+    if (ci == 3 && co == 32) return wgrad_t<3, 32, 1, 1>(t, gy, xf, gw, gb, B, H, W, st);
+    if (ci == 2 && co == 32) return wgrad_t<2, 32, 1, 1>(t, gy, xf, gw, gb, B, H, W, st);
+    return HP_ERR_UNSUPPORTED;
+}
+
+// dL/dparams for one batch into t->grad; loss (mean over the batch) into t->loss
+static hp_status trainer_grad(hp_trainer* t, const float* div, const uint8_t* flags,
+                              const float* target, hp_shape s, float lambda, cudaStream_t st)
+{
+    hp_cnn* c = t->cnn;
+    hp_status rc = trainer_forward(t, div, flags, s, st);
+    if (rc != HP_OK) return rc;
+    // loss and its gradient w.r.t. the full-resolution output
+    if ((rc = launch_mask(flags, t->mask, s, st)) != HP_OK) return rc;
+    const size_t cells = (size_t)s.ny * s.nx;
+    const float* phi = (const float*)t->act[kLayers - 1];
+    loss_stats_kernel<<<s.batch, 512, 0, st>>>(phi, target, div, t->mask, flags, c->s, t->rbuf,
+                                               t->stats, s.ny, s.nx);
+    loss_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
+        phi, target, t->rbuf, t->mask, flags, c->s, t->stats, lambda, t->g[0], s.batch, s.ny,
+        s.nx);
+    loss_finish_kernel<<<1, 1, 0, st>>>(t->stats, s.batch, cells, lambda, t->loss);
+    if ((rc = check_launch()) != HP_OK) return rc;
+    // backward, branch by branch from full resolution
+    int cur = 0;
+    for (int k = 2, l = kLayers - 1; k >= 0; --k) {
+        const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
+        const int H = s.ny / scale, W = s.nx / scale;
+        const long P = (long)s.batch * H * W;
+        const int lfirst = k == 0 ? 0 : k == 1 ? 5 : 12;
+        for (; l >= lfirst; --l) {
+            const int ci = kSpec[l].cin, co = kSpec[l].cout;
+            float* gy = t->g[cur];
+            if (kSpec[l].relu) {
+                const size_t n = (size_t)P * co;
+                relu_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                    gy, (const __nv_bfloat16*)t->act[l], n);
+            }
+            const void* x = l == lfirst ? (const void*)t->xin[k] : t->act[l - 1];
+            float* gw = t->grad + layer_offset(l);
+            rc = wgrad_dispatch(t, l, gy, x, gw, gw + layer_wcount(l), s.batch, H, W, st);
+            if (rc != HP_OK) return rc;
+            if (l > lfirst) {
+                rc = dgrad_dispatch(ci, co, gy, t->wt[l], t->g[cur ^ 1], s.batch, H, W, c->num_sms, st);
+                if (rc != HP_OK) return rc;
+                cur ^= 1;
+            } else if (k > 0) {
+                // gradient of the up-sampled coarser output (input channel 2)
+                rc = dgrad_dispatch(3, 32, gy, t->wt[l], t->gsmall, s.batch, H, W, c->num_sms, st);
+                if (rc != HP_OK) return rc;
+                const long Pc = P / 4;
+                upsample_adjoint_kernel<<<(unsigned)((Pc + 255) / 256), 256, 0, st>>>(
+                    t->gsmall, 3, 2, t->g[cur ^ 1], s.batch, H / 2, W / 2);
+                if ((rc = check_launch()) != HP_OK) return rc;
+                cur ^= 1;
+            }
+        }
+    }
+    return HP_OK;
+}
+
+extern "C" {
+
+hp_status hp_trainer_gradient(hp_trainer* t, const float* div, const uint8_t* flags,
+                              const float* target, hp_shape s, float lambda, float* grad_out,
+                              double* loss_out, void* stream)
+{
+    if (!t || !div || !flags || !target || !shape_ok(s) || s.batch > t->max.batch ||
+        s.ny > t->max.ny || s.nx > t->max.nx || s.ny % 4 || s.nx % 4)
+        return HP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    hp_status rc = trainer_grad(t, div, flags, target, s, lambda, st);
+    if (rc != HP_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (grad_out)
+        e = cudaMemcpyAsync(grad_out, t->grad, t->param_count * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && loss_out)
+        e = cudaMemcpyAsync(loss_out, t->loss, 8, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    return HP_OK;
+}
+
+hp_status hp_trainer_step(hp_trainer* t, const float* div, const uint8_t* flags,
+                          const float* target, hp_shape s, const hp_train_params* p,
+                          double* loss_out, void* stream)
+{
+    if (!p || !(p->lr > 0.0f)) return HP_ERR_INVALID_ARG;
+    hp_status rc = hp_trainer_gradient(t, div, flags, target, s, p->lambda_div, nullptr, loss_out,
+                                       stream);
+    if (rc != HP_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    t->step += 1;
+    const float c1 = 1.0f - powf(p->beta1, (float)t->step);
+    const float c2 = 1.0f - powf(p->beta2, (float)t->step);
+    adam_kernel<<<(unsigned)((t->param_count + 255) / 256), 256, 0, st>>>(
+        t->master, t->grad, t->m, t->v, t->param_count, p->lr, p->beta1, p->beta2, p->eps, c1, c2);
+    if ((rc = check_launch()) != HP_OK) return rc;
+    return trainer_pack(t, st);
+}
+
+// copy the FP32 masters back into the network object (host copy, synchronous)
+hp_status hp_trainer_sync_params(hp_trainer* t)
+{
+    if (!t) return HP_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->cnn->master.data(), t->master, t->param_count * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    return HP_OK;
 }
 
 }  // extern "C"

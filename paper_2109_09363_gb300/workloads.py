@@ -96,3 +96,41 @@ def plume_initial_state(n: int, seed: int = 0, noise_std: float = 1e-4):
     g = _rng(seed)
     rho = 1.0 + noise_std * g.standard_normal((n, n))
     return np.zeros((n, n + 1)), np.zeros((n + 1, n)), rho
+
+
+def source_velocity(ny: int, nx: int, seed: int, n_sources: int = 8, amp=(-1.0, 1.0),
+                    width=(2.0, 12.0)):
+    """Irrotational part with divergence: the face-sampled gradient of a sum of
+    Gaussian potential bumps, psi = sum A exp(-r^2 / 2 sigma^2) (FP64)."""
+    g = _rng(seed)
+    cx = g.uniform(0, nx, n_sources)
+    cy = g.uniform(0, ny, n_sources)
+    a = g.uniform(amp[0], amp[1], n_sources)
+    s = g.uniform(width[0], width[1], n_sources)
+    xu, yu = np.meshgrid(np.arange(nx + 1, dtype=np.float64), np.arange(ny) + 0.5)
+    xv, yv = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny + 1, dtype=np.float64))
+    u = np.zeros((ny, nx + 1))
+    v = np.zeros((ny + 1, nx))
+    for k in range(n_sources):
+        eu = np.exp(-((xu - cx[k]) ** 2 + (yu - cy[k]) ** 2) / (2 * s[k] ** 2))
+        ev = np.exp(-((xv - cx[k]) ** 2 + (yv - cy[k]) ** 2) / (2 * s[k] ** 2))
+        u += -a[k] * (xu - cx[k]) / s[k] ** 2 * eu
+        v += -a[k] * (yv - cy[k]) / s[k] ** 2 * ev
+    return u, v
+
+
+def training_case(batch: int, n: int, seed0: int = 0):
+    """Training inputs: vortex velocity plus Gaussian divergence sources, 0-4
+    obstacles (rectangles / discs sized to the grid); seeds seed0.. per grid.
+    Returns (u [B][n][n+1], v [B][n+1][n], flags [B][n][n]) FP64 / uint8."""
+    us, vs, fs = [], [], []
+    for b in range(batch):
+        sd = seed0 + b
+        u1, v1 = vortex_velocity(n, n, 5000 + sd, n_vortices=max(4, n // 8),
+                                 width=(n / 32, n / 8))
+        u2, v2 = source_velocity(n, n, 6000 + sd, n_sources=max(2, n // 16),
+                                 width=(n / 32, n / 8))
+        fl = random_obstacles(n, n, 8000 + sd, n_range=(0, 4), rect_side=(n / 16, n / 4),
+                              disc_radius=(n / 32, n / 8))
+        us.append(u1 + u2); vs.append(v1 + v2); fs.append(fl)
+    return np.stack(us), np.stack(vs), np.stack(fs)
