@@ -321,8 +321,8 @@ def main():
     prm = hp.ProjectParams(threshold=THR, max_iters=CAP, temporal_block=T_BLOCK,
                            use_graph=0 if args.host_loop else 1,
                            sweep_kernel=args.sweep_kernel)
-    stream = streaming_chosen(args.sweep_kernel, B * N * N)
-    per_launch = 1 if stream else T_BLOCK
+    streaming = streaming_chosen(args.sweep_kernel, B * N * N)
+    per_launch = 1 if streaming else T_BLOCK
     stream = torch.cuda.current_stream()
     out = None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -337,7 +337,7 @@ def main():
         step()
     torch.cuda.synchronize()
     iters = out["iters"].cpu().numpy()
-    if stream:
+    if streaming:
         # 8 sweep launches per graph-loop iteration, plus mask/div, init,
         # reset, correction, norms, finish
         launches_per_step = 6 + 8 * ((int(iters.max()) + 1 + 7) // 8)
@@ -399,7 +399,7 @@ def main():
     # workload (committed summary); null when the kernel changed since
     traffic = None
     tp = os.path.join(ROOT, "profiles", "dram_traffic_16x512.json")
-    kname = "sweep1_kernel" if stream else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>"
+    kname = "sweep1_kernel" if streaming else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>"
     if os.path.exists(tp):
         traffic = json.load(open(tp)).get(kname)
 
@@ -441,13 +441,13 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "method": "plain Jacobi", "grids_per_gpu": B,
                        "grid": [N, N], "threshold": THR, "cap": CAP,
-                       "sweep_kernel": "streaming" if stream else "temporally blocked",
-                       "temporal_block": None if stream else T_BLOCK,
+                       "sweep_kernel": "streaming" if streaming else "temporally blocked",
+                       "temporal_block": None if streaming else T_BLOCK,
                        "loop": "host-polled" if args.host_loop else "CUDA-graph conditional while",
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "iters_per_grid": iters.tolist()},
             "roofline": {"bound": "hbm",
-                         "kernel": kname if stream else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>",
+                         "kernel": kname,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
@@ -455,7 +455,7 @@ def main():
                          "launch_ms": t_launch_ms,
                          "note": ("13 B per cell-sweep x 4.19 M cells, one sweep per launch; "
                                   "the 54.5 MB working set is L2-resident between launches"
-                                  if stream else
+                                  if streaming else
                                   "13 B per cell-sweep x 4.19 M cells x 8 sweeps per launch; "
                                   "temporal blocking keeps 8 sweeps on chip, so frac is an "
                                   "effective HBM fraction")},

@@ -113,8 +113,8 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
                         : ctas_per_grid(mx.ny, mx.nx, 4);
     c->partial_len = (size_t)mx.batch * kMaxBlock * nct;
     {
-        // the streaming sweep keeps one partial per 8 x 128 block
-        const size_t s1 = (size_t)mx.batch * ((mx.nx + 127) / 128) * ((mx.ny + 7) / 8);
+        // the streaming sweep keeps two partials (sweep parity) per 16 x 128 block
+        const size_t s1 = (size_t)mx.batch * 2 * ((mx.nx + 127) / 128) * ((mx.ny + 15) / 16);
         if (s1 > c->partial_len) c->partial_len = s1;
     }
     c->partial2_len = (size_t)mx.batch * ((mx.nx + 255) / 256) * mx.ny;

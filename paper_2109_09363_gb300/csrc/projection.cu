@@ -413,28 +413,101 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
 
 // Rows and columns of one block of the streaming kernel: one warp per row,
 // four consecutive cells per lane.
-constexpr int kS1Rows = 8;
+constexpr int kS1Rows = 16;
 constexpr int kS1Cols = 128;
 
 int s1_blocks_x(int nx) { return (nx + kS1Cols - 1) / kS1Cols; }
 int s1_blocks_y(int ny) { return (ny + kS1Rows - 1) / kS1Rows; }
 
-// One Jacobi sweep of every active grid (phi_k -> phi_{k+1}, k = ls->k0) with
-// the E_1 of phi_k.  The last block of a grid sums the block partials in a
-// fixed order and takes the stop decision for k (the result phi_k is the
-// input buffer, no replay); the last grid to finish advances k and sets the
-// CUDA-graph conditional.  Neighbour rows come through L1/L2 (the working set
-// of a batch of 512^2 grids is L2-resident).
+// E of sweep k-1 of grid b from the CTA partials (fixed order, one warp).
+__device__ __forceinline__ double s1_grid_e(const SweepArgs& a, int b, int kprev, int nct)
+{
+    const int lane = threadIdx.x & 31;
+    const double* p = a.partial + ((size_t)b * 2 + (kprev & 1)) * nct;
+    double sum = 0.0;
+    for (int i = lane; i < nct; i += 32) sum += p[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+    return __shfl_sync(0xffffffffu, sum, 0) / ((double)a.nx * (double)a.ny);
+}
+
+__device__ __forceinline__ bool s1_stops(const SweepArgs& a, double e, int kprev)
+{
+    return e <= a.threshold || kprev >= a.max_iters;
+}
+
+// One Jacobi sweep per launch, no atomics on the data path.  Launch k (sweep
+// phi_k -> phi_{k+1} of every active grid) first decides the stop test of
+// E_{k-1}: every CTA of a grid sums the CTA partials of sweep k-1 in the same
+// fixed order and gets the same answer, so a grid that stopped leaves
+// phi_{k-1} untouched in its buffer; otherwise it sweeps and writes its
+// partial of E_k.  k per grid is the CTA arrival count of the grid divided by
+// its CTAs.  The extra control CTA (blockIdx.z == B) keeps the launch counter,
+// decides for all grids whether another launch is needed and sets the
+// CUDA-graph conditional.
 __global__ void __launch_bounds__(kS1Rows * 32) sweep1_kernel(SweepArgs a)
 {
     __shared__ float s_w[kS1Rows];
-    __shared__ int s_last;
+    __shared__ int s_k, s_stop;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nct = gridDim.x * gridDim.y;
     const int b = blockIdx.z;
+
+    if (b == a.B) {  // control CTA
+        if (blockIdx.x != 0 || blockIdx.y != 0) return;
+        LoopState* ls = a.ls;
+        const int k = ls->k0;
+        int any = 0;
+        if (k == 0) {
+            any = 1;
+        } else if (wid == 0) {
+            for (int bb = 0; bb < a.B; ++bb) {
+                if (!__ldcg(&a.gs[bb].active)) continue;
+                const double e = s1_grid_e(a, bb, k - 1, nct);
+                if (!s1_stops(a, e, k - 1)) any = 1;
+            }
+        }
+        any = __syncthreads_or(any);
+        if (threadIdx.x == 0) {
+            if (k > a.max_iters + 2) any = 0;
+            ls->k0 = k + 1;
+            ls->any_active = any;
+            if (a.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, any ? 1u : 0u);
+        }
+        return;
+    }
+
     GridState* g = a.gs + b;
     if (!g->active) return;
-    const int k = a.ls->k0;
-    const int src = a.ls->blk & 1;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) s_k = (int)(atomicAdd(&g->arrivals, 1u) / (uint32_t)nct);
+    __syncthreads();
+    const int k = s_k;
+    if (wid == 0) {
+        int stop = 0;
+        if (k > 0) {
+            const double e = s1_grid_e(a, b, k - 1, nct);
+            stop = s1_stops(a, e, k - 1);
+            if (lane == 0 && cta == 0) {
+                if (a.e_hist && k - 1 < a.hist_len) a.e_hist[(size_t)b * a.hist_len + k - 1] = e;
+                if (stop) {
+                    g->kstar = k - 1;
+                    g->k0_stop = k - 1;
+                    g->replay = 0;
+                    g->src = (k - 1) & 1;
+                    g->final_buf = (k - 1) & 1;
+                    g->converged = e <= a.threshold;
+                    g->e_stop = e;
+                    g->active = 0;
+                }
+            }
+        }
+        if (lane == 0) s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) return;
+
+    const int src = k & 1;
     const int nx = a.nx, ny = a.ny;
     const size_t gbase = (size_t)b * ny * nx;
     const float* __restrict__ pin = (src ? a.phi1 : a.phi0) + gbase;
@@ -461,8 +534,8 @@ __global__ void __launch_bounds__(kS1Rows * 32) sweep1_kernel(SweepArgs a)
             const float pw = q > 0 ? c[q - 1] : left;
             const float pe = q < 3 ? c[q + 1] : right;
             float res;
-            nv[q] = cell_update(c[q], pw, pe, up[q], dn[q], make_const(dd[q], (m4 >> (8 * q)) & 0xffu),
-                                res);
+            nv[q] = cell_update(c[q], pw, pe, up[q], dn[q],
+                                make_const(dd[q], (m4 >> (8 * q)) & 0xffu), res);
             acc = __fadd_rn(acc, fabsf(res));
         }
         float* orow = pout + (size_t)y * nx;
@@ -478,70 +551,11 @@ __global__ void __launch_bounds__(kS1Rows * 32) sweep1_kernel(SweepArgs a)
     for (int off = 16; off > 0; off >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, off));
     if (lane == 0) s_w[wid] = acc;
     __syncthreads();
-    const int nbx = gridDim.x, nblk = gridDim.x * gridDim.y;
     if (threadIdx.x == 0) {
         double sum = 0.0;
 #pragma unroll
         for (int w = 0; w < kS1Rows; ++w) sum += (double)s_w[w];
-        a.partial[(size_t)b * nblk + (size_t)blockIdx.y * nbx + blockIdx.x] = sum;
-        __threadfence();
-        s_last = atomicAdd(&g->arrivals, 1u) == (uint32_t)nblk - 1u;
-        if (s_last) __threadfence();
-    }
-    __syncthreads();
-    if (!s_last) return;
-
-    // last block of grid b: E_k and the stop decision
-    __shared__ int s_last_launch;
-    if (wid == 0) {
-        const double* p = a.partial + (size_t)b * nblk;
-        double sum = 0.0;
-        for (int i = lane; i < nblk; i += 32) sum += __ldcg(p + i);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
-        if (lane == 0) {
-            const double e = sum / ((double)nx * (double)ny);
-            if (a.e_hist && k < a.hist_len) a.e_hist[(size_t)b * a.hist_len + k] = e;
-            int stop = 0, conv = 0;
-            if (e <= a.threshold) { stop = 1; conv = 1; }
-            else if (k >= a.max_iters) { stop = 1; conv = 0; }
-            if (stop) {
-                g->active = 0;
-                g->kstar = k;
-                g->k0_stop = k;
-                g->replay = 0;
-                g->src = src;
-                g->final_buf = src;
-                g->converged = conv;
-                g->e_stop = e;
-            }
-            g->arrivals = 0u;
-            __threadfence();
-            s_last_launch = atomicAdd(&a.ls->arrivals, 1u) == (uint32_t)a.ls->n_active - 1u;
-            if (s_last_launch) __threadfence();
-        }
-    }
-    __syncthreads();
-    if (!s_last_launch) return;
-    // last grid of the launch: advance k, count the grids still sweeping
-    __shared__ int s_count;
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    int n = 0;
-    for (int bb = threadIdx.x; bb < a.B; bb += blockDim.x) n += __ldcg(&a.gs[bb].active) ? 1 : 0;
-    if (n) atomicAdd(&s_count, n);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = s_count;
-        LoopState* ls = a.ls;
-        if (k + 1 > a.max_iters + 1) tot = 0;
-        ls->k0 = k + 1;
-        ls->blk = ls->blk + 1;
-        ls->arrivals = 0u;
-        ls->n_active = tot;
-        ls->any_active = tot > 0;
-        __threadfence();
-        if (a.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)a.cond, tot > 0 ? 1u : 0u);
+        a.partial[((size_t)b * 2 + (k & 1)) * nct + cta] = sum;
     }
 }
 
@@ -748,7 +762,7 @@ static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H, bool stream)
             cudaKernelNodeParams kp = {};
             if (stream) {
                 kp.func = (void*)sweep1_kernel;
-                kp.gridDim = dim3(s1_blocks_x(a.nx), s1_blocks_y(a.ny), a.B);
+                kp.gridDim = dim3(s1_blocks_x(a.nx), s1_blocks_y(a.ny), a.B + 1);
                 kp.blockDim = dim3(kS1Rows * 32);
                 kp.sharedMemBytes = 0;
             } else {
@@ -780,7 +794,7 @@ static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H, bool stream)
 // to its exact stop index.  Expects ctx->mask, ctx->div and ctx->phi[0] ready.
 static hp_status launch_sweep1(const SweepArgs& a, cudaStream_t st)
 {
-    dim3 grd(s1_blocks_x(a.nx), s1_blocks_y(a.ny), a.B), blk(kS1Rows * 32);
+    dim3 grd(s1_blocks_x(a.nx), s1_blocks_y(a.ny), a.B + 1), blk(kS1Rows * 32);
     sweep1_kernel<<<grd, blk, 0, st>>>(a);
     return check_launch();
 }
@@ -792,7 +806,7 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, dou
     const int H = halo_for(T);
     const int nct = ctas_x(s.nx, H) * ctas_y(s.ny, H);
     if ((size_t)s.batch * kMaxBlock * nct > ctx->partial_len) return HP_ERR_INVALID_ARG;
-    if ((size_t)s.batch * s1_blocks_x(s.nx) * s1_blocks_y(s.ny) > ctx->partial_len)
+    if ((size_t)s.batch * 2 * s1_blocks_x(s.nx) * s1_blocks_y(s.ny) > ctx->partial_len)
         return HP_ERR_INVALID_ARG;
     SweepArgs a = {};
     a.phi0 = ctx->phi[0];
@@ -839,7 +853,7 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, dou
     } else {
         // host-polled: launch a few blocks, read the flag, repeat; bounded by
         // the cap (every grid stops at k = max_iters at the latest)
-        const int max_blocks = stream ? max_iters + 1 : max_iters / T + 2;
+        const int max_blocks = stream ? max_iters + 3 : max_iters / T + 2;
         int launched = 0;
         const int chunk = stream ? kStreamUnroll : 4;
         while (launched < max_blocks) {
