@@ -267,6 +267,63 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
                          "seconds": t_train}}
 
 
+def profile_conv(batch, h, w, cin, cout) -> int:
+    """Time and run one tensor-core convolution layer (FLOP/s printed)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((batch, h, w, cin), generator=g).to(torch.bfloat16).to(dev)
+    wt = (torch.randn((3, 3, cout, cin), generator=g) / (3 * cin ** 0.5)).to(torch.bfloat16).to(dev)
+    bias = torch.zeros(cout, dtype=torch.float32, device=dev)
+    y = torch.empty((batch, h, w, cout), dtype=torch.bfloat16, device=dev)
+    for _ in range(3):
+        hp.hp_conv3x3_bf16(x, wt, bias, True, y=y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        hp.hp_conv3x3_bf16(x, wt, bias, True, y=y)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 10
+    flop = 2.0 * batch * h * w * 9 * cin * cout
+    print(json.dumps({"profile_conv": [batch, h, w, cin, cout], "ms": ms,
+                      "tflops": flop / ms / 1e9}))
+    return 0
+
+
+def profile_cnn(batch, n) -> int:
+    """Time the CNN forward (t_inf) on BATCH vortex grids of N x N."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    from paper_2109_09363_gb300 import training as T
+    from paper_2109_09363_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    u, v, fl = W.batched_vortex_case(batch, n)
+    ud = torch.from_numpy(u.astype(np.float32)).to(dev)
+    vd = torch.from_numpy(v.astype(np.float32)).to(dev)
+    fd = torch.from_numpy(fl).to(dev)
+    cnn = hp.CNN(batch, n, n, params=T.init_params(seed=1))
+    div = hp.hp_divergence(ud, vd, fd)
+    for _ in range(3):
+        hp.hp_cnn_forward(cnn, div, fd)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        hp.hp_cnn_forward(cnn, div, fd)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 5
+    # MACs per full-resolution pixel: 148,608 + 148,608 / 4 + 74,592 / 16
+    flop = 2.0 * 190422 * batch * n * n
+    print(json.dumps({"profile_cnn": [batch, n], "ms": ms, "tflops": flop / ms / 1e9}))
+    return 0
+
+
 def main():
     global T_BLOCK
     ap = argparse.ArgumentParser()
@@ -282,6 +339,11 @@ def main():
                     help="sweeps per launch of the temporally blocked kernel (1..8)")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="0 = library choice, 1 = streaming, 2 = temporally blocked")
+    ap.add_argument("--profile-conv", nargs=5, type=int,
+                    metavar=("BATCH", "H", "W", "CIN", "COUT"),
+                    help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
+    ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
+                    help="only run the CNN forward on BATCH grids of N x N, 3 times")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the CNN-hybrid arm (training + timing)")
     ap.add_argument("--train-steps", type=int, default=1200,
@@ -297,6 +359,10 @@ def main():
     if args.profile_sweep:
         return profile_sweep(*args.profile_sweep, host_loop=args.host_loop,
                              kernel=args.sweep_kernel)
+    if args.profile_conv:
+        return profile_conv(*args.profile_conv)
+    if args.profile_cnn:
+        return profile_cnn(*args.profile_cnn)
 
     import torch
     import torch.distributed as dist

@@ -241,6 +241,164 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     }
 }
 
+// Row-walking variant for width >= 128: a CTA owns a 128-pixel column strip
+// of a band of rows.  Input rows live once in a 4-slot ring in shared memory,
+// [slot][chunk][130 pixels][8 channels] (pixels x0-1 .. x0+128, replicated
+// at the borders), so the A operand of tap (dy, dx) is a descriptor view of
+// ring slot (y + dy - 1) shifted by dx pixels (16 bytes): LBO = 130 * 16
+// bytes between channel chunks, SBO = 128 bytes between groups of 8 pixels.
+// While the MMAs of row y run, the threads prefetch row y + 2 into the free
+// slot with cp.async.
+constexpr int kHaloPx = kTileM + 2;
+
+template <int CIN, int COUT>
+struct RowSmem {
+    static constexpr int kChunks = CIN / 8;
+    static constexpr int kSlotBytes = kChunks * kHaloPx * 16;
+    static constexpr int kRingBytes = 4 * kSlotBytes;
+    static constexpr int kBBytes = 9 * kChunks * COUT * 16;
+    static constexpr int kBytes = kRingBytes + kBBytes;
+    static constexpr int kTmemCols = COUT < 32 ? 32 : COUT;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+}
+
+// copy input row r (clamped) of grid b, pixels x0-1 .. x0+128 (clamped), into
+// ring slot (r & 3)
+template <int CIN>
+__device__ __forceinline__ void load_halo_row(const uint4* __restrict__ x, uint8_t* ring, int b,
+                                              int r, int x0, int H, int W, int slot_bytes)
+{
+    constexpr int NCH = CIN / 8;
+    const int sr = min(max(r, 0), H - 1);
+    uint8_t* slot = ring + (r & 3) * slot_bytes;
+    const uint4* src_row = x + ((size_t)b * H + sr) * W * NCH;
+    for (int i = threadIdx.x; i < NCH * kHaloPx; i += kConvThreads) {
+        const int ch = i / kHaloPx, px = i - ch * kHaloPx;
+        const int sx = min(max(x0 - 1 + px, 0), W - 1);
+        cp_async16(smem_u32(slot + (ch * kHaloPx + px) * 16), src_row + (size_t)sx * NCH + ch);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv3x3_tc_rows_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
+                           const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int H,
+                           int W, int band, int relu, int* err)
+{
+    using S = RowSmem<CIN, COUT>;
+    constexpr int NCH = S::kChunks;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* ring = smem;
+    uint8_t* sB = smem + S::kRingBytes;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    const int b = blockIdx.z;
+    const int x0 = blockIdx.x * kTileM;
+    const int y0 = blockIdx.y * band;
+    const int y1 = min(H, y0 + band);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"((uint32_t)S::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    for (int i = tid; i < 9 * COUT * NCH; i += kConvThreads) {
+        const int ch = i % NCH;
+        const int n = (i / NCH) % COUT;
+        const int tap = i / (NCH * COUT);
+        const uint4 v = w[(size_t)(tap * COUT + n) * NCH + ch];
+        *reinterpret_cast<uint4*>(sB + ((tap * NCH + ch) * COUT + n) * 16) = v;
+    }
+    // first three rows of the band
+    for (int r = y0 - 1; r <= y0 + 1; ++r) load_halo_row<CIN>(x, ring, b, r, x0, H, W, S::kSlotBytes);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = mma_idesc(kTileM, COUT);
+    const uint32_t ring_a = smem_u32(ring), b_base = smem_u32(sB);
+    const int xo = x0 + tid;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int yy = y0; yy < y1; ++yy) {
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+                const uint32_t slot = (uint32_t)((yy + dy - 1) & 3) * S::kSlotBytes;
+#pragma unroll
+                for (int ks = 0; ks < NCH / 2; ++ks) {
+                    const uint64_t ad = smem_desc(ring_a + slot + ((2 * ks) * kHaloPx + dx) * 16,
+                                                  kHaloPx * 16, 128);
+                    const uint64_t bd =
+                        smem_desc(b_base + (tap * NCH + 2 * ks) * COUT * 16, COUT * 16, 128);
+                    mma_bf16(tmem, ad, bd, idesc, (tap | ks) != 0);
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    mbar_a)
+                : "memory");
+        }
+        // prefetch the row the next tile needs into the free slot
+        if (yy + 1 < y1) load_halo_row<CIN>(x, ring, b, yy + 2, x0, H, W, S::kSlotBytes);
+        ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;
+        phase ^= 1u;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 32) {
+            float acc[32];
+            tmem_ld32(lane_addr + c0, acc);
+            if (xo < W) {
+                __nv_bfloat16* out = y + (((size_t)b * H + yy) * W + xo) * COUT + c0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) {
+                    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float vq = acc[j + q] + bias[c0 + j + q];
+                        if (relu) vq = fmaxf(vq, 0.0f);
+                        o[q] = __float2bfloat16_rn(vq);
+                    }
+                    *reinterpret_cast<uint4*>(out + j) = *reinterpret_cast<const uint4*>(o);
+                }
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && err) atomicExch(err, 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)S::kTmemCols));
+    }
+}
+
 template <int CIN, int COUT>
 hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y, int B, int H,
                         int W, int relu, int* err, int nsm, cudaStream_t st)
@@ -252,6 +410,26 @@ hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
         if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
         attr = true;
+    }
+    if (W >= kTileM) {
+        // row-walking kernel: bands of rows sized for about two CTAs per SM
+        using R = RowSmem<CIN, COUT>;
+        static bool rattr = false;
+        if (!rattr) {
+            cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_rows_kernel<CIN, COUT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 R::kBytes);
+            if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+            rattr = true;
+        }
+        const int segs = (W + kTileM - 1) / kTileM;
+        long units = (long)segs * B;
+        int band = H;
+        while (band > 16 && units * ((H + band - 1) / band) < 2L * nsm) band = (band + 1) / 2;
+        dim3 grd(segs, (H + band - 1) / band, B);
+        conv3x3_tc_rows_kernel<CIN, COUT><<<grd, kConvThreads, R::kBytes, st>>>(
+            (const uint4*)x, (const uint4*)w, bias, (__nv_bfloat16*)y, H, W, band, relu, err);
+        return check_launch();
     }
     const long P = (long)B * H * W;
     const int ntiles = (int)((P + kTileM - 1) / kTileM);

@@ -21,7 +21,7 @@ def dev():
 
 
 @pytest.mark.parametrize("cin,cout", [(32, 32), (32, 64), (64, 32), (64, 64)])
-@pytest.mark.parametrize("shape", [(1, 8, 16), (2, 37, 53), (1, 128, 128)])
+@pytest.mark.parametrize("shape", [(1, 8, 16), (2, 37, 53), (1, 128, 128), (1, 20, 200), (2, 67, 256)])
 def test_conv3x3_tensor_core_matches_oracle(dev, cin, cout, shape):
     B, H, W = shape
     rng = np.random.default_rng(cin * 7 + cout + H)
