@@ -108,6 +108,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest value over all ranks (the step time of the slowest GPU);
+    timing only, nothing on the data path is exchanged."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(rank: int):
     from paper_2109_09363_gb300 import workloads as W
     u, v, fl = W.batched_vortex_case(B, N, seed0=rank * B)
@@ -258,10 +268,22 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     torch.cuda.synchronize()
     t_inf = a.elapsed_time(b_) / 5
     cnn_eval.close()
+    # MACs per full-resolution pixel of the network: 148,608 (scale 1) +
+    # 148,608 / 4 (scale 1/2) + 74,592 / 16 (scale 1/4)
+    flop = 2.0 * 190422 * B * N * N
+    tf = flop / (t_inf * 1e-3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    tpk = float(peaks.get("bf16_tflops", 1900.0))
     return {"value": ws * B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "speedup_vs_plain": ms_plain / ms, "iters_per_grid": iters.tolist(),
             "converged": int(out["converged"].sum().item()),
             "t_inf_ms_16_grids": t_inf,
+            "cnn_roofline": {"bound": "tensor", "achieved": tf, "peak": tpk,
+                             "unit": "TFLOP/s", "frac": tf / tpk,
+                             "peak_kind": "measured" if peaks else "fallback",
+                             "note": "whole network forward (BF16, FP32 accumulate), "
+                                     "380.8 kFLOP per full-resolution pixel"},
             "training": {"pairs": 2048, "grid": [n_tr, n_tr], "steps": len(losses),
                          "batch": batch, "final_loss": float(np.mean(losses[-20:])),
                          "seconds": t_train}}
@@ -337,8 +359,9 @@ def main():
                          "of N x N, three times (a small case for ncu)")
     ap.add_argument("--temporal-block", type=int, default=T_BLOCK,
                     help="sweeps per launch of the temporally blocked kernel (1..8)")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="0 = library choice, 1 = streaming, 2 = temporally blocked")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0 = library choice, 1 = streaming, 2 = temporally blocked "
+                         "(4 rows per thread), 3 = temporally blocked (2 rows per thread)")
     ap.add_argument("--profile-conv", nargs=5, type=int,
                     metavar=("BATCH", "H", "W", "CIN", "COUT"),
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
@@ -429,9 +452,7 @@ def main():
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
     value = ws * B / (ms * 1e-3)
 
     # dominant kernel: the temporally blocked sweep, per-launch duration from

@@ -65,9 +65,10 @@ typedef struct {
  *   use_graph      1 = run the sweep loop as a CUDA-graph conditional WHILE node
  *                  (no host round trip per block); 0 = host-polled loop
  *   sweep_kernel   0 = library choice, 1 = streaming (one sweep per launch,
- *                  exact stop per launch), 2 = temporally blocked (T sweeps
- *                  per launch, replay to the exact stop).  Both give the same
- *                  iterates bit for bit. */
+ *                  stop decided one launch later), 2 = temporally blocked (T
+ *                  sweeps per launch, replay to the exact stop; 4 rows per
+ *                  thread), 3 = temporally blocked with 2 rows per thread
+ *                  (twice the warps).  All give the same iterates bit for bit. */
 typedef struct {
     double threshold;
     int32_t max_iters;
@@ -116,6 +117,8 @@ hp_status hp_div_norms(hp_ctx *ctx, const float *u, const float *v, const uint8_
  *      are masked Jacobi on the open-face Laplacian, E_1 is summed in FP64
  *      after every sweep in a fixed order;
  *   4. u = u* - grad phi on open faces, 0 on closed faces; p = phi rho0 / dt.
+ * A grid whose E_1 is not finite (NaN or Inf in its input) stops at that k
+ * with converged = 0; the other grids of the batch are not affected.
  * Outputs (device): p_out float [B][ny][nx] (may be NULL), iters_out int32 [B],
  * e1_out / einf_out double [B] (norms of the CORRECTED velocity; may be NULL),
  * converged_out uint8 [B] (may be NULL).

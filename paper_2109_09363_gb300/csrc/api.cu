@@ -180,7 +180,7 @@ hp_status hp_project(hp_ctx* c, float* u, float* v, const uint8_t* flags, hp_sha
     if (!c || !u || !v || !flags || !prm || !iters_out || !fits(c, s)) return HP_ERR_INVALID_ARG;
     if (prm->max_iters < 0 || prm->fixed_iters < 0 || prm->temporal_block < 0 ||
         prm->temporal_block > kMaxBlock || !(prm->threshold >= 0.0) || !(prm->dt > 0.0f) ||
-        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 2)
+        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 3)
         return HP_ERR_INVALID_ARG;
     if ((e_hist == nullptr) != (hist_len <= 0)) return HP_ERR_INVALID_ARG;
     return project_impl(c, u, v, flags, s, prm, phi0, p_out, iters_out, e1_out, einf_out, conv_out,

@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     uint8_t* sB = smem + S::kABytes;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ float s_bias[COUT];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1u));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    for (int i = tid; i < COUT; i += kConvThreads) s_bias[i] = bias[i];
     // weights -> [tap][chunk][cout][8]
     for (int i = tid; i < 9 * COUT * NCH; i += kConvThreads) {
         const int ch = i % NCH;
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        float vq = acc[j + q] + bias[c0 + j + q];
+                        float vq = acc[j + q] + s_bias[c0 + j + q];
                         if (relu) vq = fmaxf(vq, 0.0f);
                         o[q] = __float2bfloat16_rn(vq);
                     }
@@ -297,6 +299,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     uint8_t* sB = smem + S::kRingBytes;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
+    __shared__ float s_bias[COUT];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -316,6 +319,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1u));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    for (int i = tid; i < COUT; i += kConvThreads) s_bias[i] = bias[i];
     for (int i = tid; i < 9 * COUT * NCH; i += kConvThreads) {
         const int ch = i % NCH;
         const int n = (i / NCH) % COUT;
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        float vq = acc[j + q] + bias[c0 + j + q];
+                        float vq = acc[j + q] + s_bias[c0 + j + q];
                         if (relu) vq = fmaxf(vq, 0.0f);
                         o[q] = __float2bfloat16_rn(vq);
                     }

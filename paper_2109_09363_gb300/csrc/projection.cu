@@ -203,7 +203,8 @@ __device__ void grid_decide(const SweepArgs& a, int b, int T, int k0, int src, i
             const double e = s_e[t];
             if (a.e_hist && k < a.hist_len) a.e_hist[(size_t)b * a.hist_len + k] = e;
             if (e <= a.threshold) { stop = t; conv = 1; break; }
-            if (k >= a.max_iters) { stop = t; conv = 0; break; }
+            // a non-finite E (NaN or Inf in the input) ends the grid at once
+            if (k >= a.max_iters || !isfinite(e)) { stop = t; conv = 0; break; }
         }
         if (stop >= 0) {
             g->active = 0;
@@ -268,14 +269,16 @@ __device__ __forceinline__ void launch_arrive(const SweepArgs& a, int T)
 //   counter advance by the last CTA of the launch.
 // mode 1 (replay): gs[b].replay sweeps from buffer gs[b].src into the other
 //   buffer, no reduction.
-template <int H>
-__global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs a)
+template <int H, int R>
+__global__ void __launch_bounds__((kTileRows / R) * 32, 1) sweep_tb_kernel(SweepArgs a)
 {
+    constexpr int NW = kTileRows / R;  // warps; warp w holds rows R*w .. R*w + R - 1
     constexpr int OW = TileGeom<H>::OW;
     constexpr int OH = TileGeom<H>::OH;
-    __shared__ float4 s_top[2][kTileWarps][32];
-    __shared__ float4 s_bot[2][kTileWarps][32];
-    __shared__ float s_wsum[kMaxBlock][kTileWarps];
+    static_assert(H % R == 0, "halo must hold whole thread rows");
+    // row exchange [parity][top/bottom][warp][lane], dynamic shared memory
+    extern __shared__ float4 s_xchg[];
+    __shared__ float s_wsum[kMaxBlock][NW];
 
     const int b = blockIdx.z;
     GridState* g = a.gs + b;
@@ -304,12 +307,12 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
     const bool vec = (nx & 3) == 0;
 
     const int x0 = blockIdx.x * OW - H + 4 * lane;
-    const int y0 = blockIdx.y * OH - H + 4 * wid;
+    const int y0 = blockIdx.y * OH - H + R * wid;
 
-    float phi[4][4];
-    CellConst kc[4][4];
+    float phi[R][4];
+    CellConst kc[R][4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < R; ++r) {
         const int y = y0 + r;
         if (y >= 0 && y < ny) {
             float dd[4];
@@ -327,21 +330,23 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
         }
     }
 
-    const bool own = lane >= H / 4 && lane < 32 - H / 4 && wid >= H / 4 && wid < kTileWarps - H / 4;
+    const bool own = lane >= H / 4 && lane < 32 - H / 4 && wid >= H / R && wid < NW - H / R;
 
     for (int t = 0; t < T; ++t) {
         const int p = t & 1;
-        s_top[p][wid][lane] = make_float4(phi[0][0], phi[0][1], phi[0][2], phi[0][3]);
-        s_bot[p][wid][lane] = make_float4(phi[3][0], phi[3][1], phi[3][2], phi[3][3]);
+        float4* top = s_xchg + (p * 2 + 0) * NW * 32;
+        float4* bot = s_xchg + (p * 2 + 1) * NW * 32;
+        top[wid * 32 + lane] = make_float4(phi[0][0], phi[0][1], phi[0][2], phi[0][3]);
+        bot[wid * 32 + lane] = make_float4(phi[R - 1][0], phi[R - 1][1], phi[R - 1][2], phi[R - 1][3]);
         __syncthreads();
-        const float4 nb = wid > 0 ? s_bot[p][wid - 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 nb = wid > 0 ? bot[(wid - 1) * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 sb =
-            wid < kTileWarps - 1 ? s_top[p][wid + 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            wid < NW - 1 ? top[(wid + 1) * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         float up[4] = {nb.x, nb.y, nb.z, nb.w};
         const float south[4] = {sb.x, sb.y, sb.z, sb.w};
         float acc = 0.0f;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < R; ++r) {
             const float left = __shfl_up_sync(0xffffffffu, phi[r][3], 1);
             const float right = __shfl_down_sync(0xffffffffu, phi[r][0], 1);
             float nw[4];
@@ -349,7 +354,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
             for (int q = 0; q < 4; ++q) {
                 const float pw = q > 0 ? phi[r][q - 1] : left;
                 const float pe = q < 3 ? phi[r][q + 1] : right;
-                const float ps = r < 3 ? phi[r + 1][q] : south[q];
+                const float ps = r < R - 1 ? phi[r + 1][q] : south[q];
                 float res;
                 nw[q] = cell_update(phi[r][q], pw, pe, up[q], ps, kc[r][q], res);
                 acc = __fadd_rn(acc, fabsf(res));
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
 
     if (own) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int y = y0 + r;
             if (y < ny) {
                 float* row = pout + (size_t)y * nx;
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 1) sweep_tb_kernel(SweepArgs 
     if (threadIdx.x < T) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < kTileWarps; ++w) s += (double)s_wsum[threadIdx.x][w];
+        for (int w = 0; w < NW; ++w) s += (double)s_wsum[threadIdx.x][w];
         a.partial[((size_t)b * kMaxBlock + threadIdx.x) * nct + cta] = s;
         __threadfence();
     }
@@ -433,7 +438,7 @@ __device__ __forceinline__ double s1_grid_e(const SweepArgs& a, int b, int kprev
 
 __device__ __forceinline__ bool s1_stops(const SweepArgs& a, double e, int kprev)
 {
-    return e <= a.threshold || kprev >= a.max_iters;
+    return e <= a.threshold || kprev >= a.max_iters || !isfinite(e);
 }
 
 // One Jacobi sweep per launch, no atomics on the data path.  Launch k (sweep
@@ -717,18 +722,42 @@ hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t
 
 // ------------------------------------------------------------- sweep loop
 
-static void* sweep_kernel_ptr(int H)
+// rows per thread of the blocked kernel: 4 (16 warps) or 2 (32 warps)
+static void* sweep_kernel_ptr(int H, int R)
 {
-    return H == 4 ? (void*)sweep_tb_kernel<4> : (void*)sweep_tb_kernel<8>;
+    if (R == 2) return H == 4 ? (void*)sweep_tb_kernel<4, 2> : (void*)sweep_tb_kernel<8, 2>;
+    return H == 4 ? (void*)sweep_tb_kernel<4, 4> : (void*)sweep_tb_kernel<8, 4>;
 }
 
-static hp_status launch_sweep(const SweepArgs& a, int H, cudaStream_t st)
+static int sweep_threads(int R) { return (kTileRows / R) * 32; }
+static size_t sweep_smem(int R) { return (size_t)4 * (kTileRows / R) * 32 * sizeof(float4); }
+
+static hp_status prepare_sweep_kernel(int H, int R)
 {
-    dim3 grd(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B), blk(kTileWarps * 32);
-    if (H == 4)
-        sweep_tb_kernel<4><<<grd, blk, 0, st>>>(a);
-    else
-        sweep_tb_kernel<8><<<grd, blk, 0, st>>>(a);
+    static bool done[2][2] = {{false, false}, {false, false}};
+    bool& d = done[H == 8][R == 2];
+    if (d) return HP_OK;
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel_ptr(H, R),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sweep_smem(R));
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    d = true;
+    return HP_OK;
+}
+
+static hp_status launch_sweep(const SweepArgs& a, int H, int R, cudaStream_t st)
+{
+    hp_status rc = prepare_sweep_kernel(H, R);
+    if (rc != HP_OK) return rc;
+    dim3 grd(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B), blk(sweep_threads(R));
+    const size_t sm = sweep_smem(R);
+    if (R == 2) {
+        if (H == 4) sweep_tb_kernel<4, 2><<<grd, blk, sm, st>>>(a);
+        else sweep_tb_kernel<8, 2><<<grd, blk, sm, st>>>(a);
+    } else {
+        if (H == 4) sweep_tb_kernel<4, 4><<<grd, blk, sm, st>>>(a);
+        else sweep_tb_kernel<8, 4><<<grd, blk, sm, st>>>(a);
+    }
     return check_launch();
 }
 
@@ -736,8 +765,12 @@ static hp_status launch_sweep(const SweepArgs& a, int H, cudaStream_t st)
 // (grids that stopped skip the remaining launches of the iteration).
 constexpr int kStreamUnroll = 8;
 
-static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H, bool stream)
+static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H, int R, bool stream)
 {
+    if (!stream) {
+        hp_status prc = prepare_sweep_kernel(H, R);
+        if (prc != HP_OK) return prc;
+    }
     if (ctx->graph_exec) {
         cudaGraphExecDestroy(ctx->graph_exec);
         ctx->graph_exec = nullptr;
@@ -766,10 +799,10 @@ static hp_status build_loop_graph(hp_ctx* ctx, SweepArgs a, int H, bool stream)
                 kp.blockDim = dim3(kS1Rows * 32);
                 kp.sharedMemBytes = 0;
             } else {
-                kp.func = sweep_kernel_ptr(H);
+                kp.func = sweep_kernel_ptr(H, R);
                 kp.gridDim = dim3(ctas_x(a.nx, H), ctas_y(a.ny, H), a.B);
-                kp.blockDim = dim3(kTileWarps * 32);
-                kp.sharedMemBytes = 0;
+                kp.blockDim = dim3(sweep_threads(R));
+                kp.sharedMemBytes = (unsigned)sweep_smem(R);
             }
             kp.kernelParams = args;
             cudaGraphNode_t prev = nullptr, knode = nullptr;
@@ -799,9 +832,9 @@ static hp_status launch_sweep1(const SweepArgs& a, cudaStream_t st)
     return check_launch();
 }
 
-static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, double threshold,
-                                int max_iters, double* e_hist, int hist_len, bool use_graph,
-                                cudaStream_t st)
+static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, int R, bool stream,
+                                double threshold, int max_iters, double* e_hist, int hist_len,
+                                bool use_graph, cudaStream_t st)
 {
     const int H = halo_for(T);
     const int nct = ctas_x(s.nx, H) * ctas_y(s.ny, H);
@@ -836,11 +869,12 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, dou
                           ctx->graph_shape.ny == s.ny && ctx->graph_shape.nx == s.nx &&
                           ctx->graph_T == T && ctx->graph_hist == hist_len &&
                           ctx->graph_hist_ptr == e_hist && ctx->graph_threshold == threshold &&
-                          ctx->graph_max_iters == max_iters && ctx->graph_kernel == (int)stream;
+                          ctx->graph_max_iters == max_iters &&
+                          ctx->graph_kernel == (stream ? 1 : 10 + R);
         if (!same) {
-            rc = build_loop_graph(ctx, a, H, stream);
+            rc = build_loop_graph(ctx, a, H, R, stream);
             if (rc != HP_OK) return rc;
-            ctx->graph_kernel = (int)stream;
+            ctx->graph_kernel = stream ? 1 : 10 + R;
             ctx->graph_shape = s;
             ctx->graph_T = T;
             ctx->graph_hist = hist_len;
@@ -858,7 +892,7 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, dou
         const int chunk = stream ? kStreamUnroll : 4;
         while (launched < max_blocks) {
             for (int c = 0; c < chunk && launched < max_blocks; ++c, ++launched) {
-                rc = stream ? launch_sweep1(a, st) : launch_sweep(a, H, st);
+                rc = stream ? launch_sweep1(a, st) : launch_sweep(a, H, R, st);
                 if (rc != HP_OK) return rc;
             }
             cudaError_t e = cudaMemcpyAsync(ctx->host_flag, &ctx->ls->any_active, sizeof(int32_t),
@@ -870,7 +904,7 @@ static hp_status run_sweep_loop(hp_ctx* ctx, hp_shape s, int T, bool stream, dou
     }
     if (stream) return HP_OK;  // the streaming kernel stops exactly, nothing to replay
     a.mode = 1;
-    return launch_sweep(a, H, st);
+    return launch_sweep(a, H, R, st);
 }
 
 static int pick_T(const hp_project_params* prm)
@@ -903,7 +937,8 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     // library choice: the temporally blocked kernel (measured faster than the
     // streaming one at 16 x 512^2 and above)
     const bool stream = prm->sweep_kernel == 1;
-    rc = run_sweep_loop(ctx, s, pick_T(prm), stream, thr, cap, e_hist, hist_len,
+    const int R = prm->sweep_kernel == 3 ? 2 : 4;
+    rc = run_sweep_loop(ctx, s, pick_T(prm), R, stream, thr, cap, e_hist, hist_len,
                         prm->use_graph != 0, st);
     if (rc != HP_OK) return rc;
 

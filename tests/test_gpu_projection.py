@@ -178,7 +178,8 @@ def test_project_matches_oracle(dev, shape, thr, cap):
 def test_sweep_kernel_block_size_and_loop_mode_do_not_change_results(dev):
     u, v, fl = vortex(3, 96, 160, seed=5)
     base = None
-    cases = [(1, 1, g) for g in (0, 1)] + [(2, T, g) for T in (1, 2, 3, 4, 5, 8) for g in (0, 1)]
+    cases = ([(1, 1, g) for g in (0, 1)] + [(2, T, g) for T in (1, 2, 3, 4, 5, 8) for g in (0, 1)]
+             + [(3, T, g) for T in (1, 4, 8) for g in (0, 1)])
     for kern, T, graph in cases:
         g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=700,
                                                     temporal_block=T, use_graph=graph,
@@ -190,7 +191,7 @@ def test_sweep_kernel_block_size_and_loop_mode_do_not_change_results(dev):
             assert np.array_equal(g[k], base[k]), (kern, T, graph, k)
 
 
-@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("kern", [1, 2, 3])
 def test_both_sweep_kernels_match_oracle(dev, kern):
     u, v, fl = vortex(3, 67, 130, seed=12)
     g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=2000,
@@ -198,7 +199,7 @@ def test_both_sweep_kernels_match_oracle(dev, kern):
     check_projection(g, u, v, fl, 1e-3, 2000)
 
 
-@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("kern", [1, 2, 3])
 def test_history_matches_oracle(dev, kern):
     u, v, fl = vortex(2, 64, 96, seed=9)
     thr, cap = 1e-3, 400
@@ -284,3 +285,20 @@ def test_full_size_vortex_benchmark_sampled(dev):
     sample = [0, 5, 10, 15]
     sub = {k: g[k][sample] for k in ["u", "v", "p", "iters", "converged", "e1"]}
     check_projection(sub, u[sample], v[sample], fl[sample], thr, cap)
+
+
+@pytest.mark.parametrize("kern", [1, 2])
+def test_nonfinite_input_stops_only_that_grid(dev, kern):
+    u, v, fl = vortex(3, 48, 64, seed=21)
+    good = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=900,
+                                                   sweep_kernel=kern))
+    u_bad = u.copy()
+    u_bad[1, 20, 30] = np.nan
+    fl_open = fl.copy()
+    fl_open[1, 20, 29:31] = 0   # make sure the poisoned face is open
+    g = run_gpu(dev, u_bad, v, fl_open, hp.ProjectParams(threshold=1e-3, max_iters=900,
+                                                          sweep_kernel=kern))
+    assert g["converged"][1] == 0 and g["iters"][1] <= 1
+    for b in (0, 2):
+        assert g["iters"][b] == good["iters"][b]
+        assert np.array_equal(g["u"][b], good["u"][b])
