@@ -12,7 +12,8 @@
 // same way once per CTA: [tap][chunk][cout][8 channels].  One thread issues
 // the 9 x Cin/16 MMAs (M = 128, N = Cout, K = 16) into one TMEM accumulator,
 // commits them to an mbarrier, and the 128 threads read their row back with
-// tcgen05.ld.
+// tcgen05.ld.  This gather form serves widths below 128; wider images use the
+// warp-specialised row walk further down.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -243,71 +244,119 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     }
 }
 
-// Row-walking variant for width >= 128: a CTA owns a 128-pixel column strip
-// of a band of rows.  Input rows live once in a 4-slot ring in shared memory,
-// [slot][chunk][130 pixels][8 channels] (pixels x0-1 .. x0+128, replicated
-// at the borders), so the A operand of tap (dy, dx) is a descriptor view of
-// ring slot (y + dy - 1) shifted by dx pixels (16 bytes): LBO = 130 * 16
+// Row-walking layout for width >= 128: a CTA walks a 128-pixel column strip
+// down a band of rows.  Input rows live once in a ring in shared memory,
+// [slot][chunk][130 pixels][8 channels] (pixels x0-1 .. x0+128, replicated at
+// the borders), so the A operand of tap (dy, dx) is a descriptor view of the
+// slot holding row y + dy - 1, shifted by dx pixels (16 bytes): LBO = 130 * 16
 // bytes between channel chunks, SBO = 128 bytes between groups of 8 pixels.
-// While the MMAs of row y run, the threads prefetch row y + 2 into the free
-// slot with cp.async.
 constexpr int kHaloPx = kTileM + 2;
-
-template <int CIN, int COUT>
-struct RowSmem {
-    static constexpr int kChunks = CIN / 8;
-    static constexpr int kSlotBytes = kChunks * kHaloPx * 16;
-    static constexpr int kRingBytes = 4 * kSlotBytes;
-    static constexpr int kBBytes = 9 * kChunks * COUT * 16;
-    static constexpr int kBytes = kRingBytes + kBBytes;
-    static constexpr int kTmemCols = COUT < 32 ? 32 : COUT;
-};
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
 
-// copy input row r (clamped) of grid b, pixels x0-1 .. x0+128 (clamped), into
-// ring slot (r & 3)
-template <int CIN>
-__device__ __forceinline__ void load_halo_row(const uint4* __restrict__ x, uint8_t* ring, int b,
-                                              int r, int x0, int H, int W, int slot_bytes)
+// Warp-specialised persistent row walk (width >= 128).  Each CTA loops over
+// work items (grid, 128-pixel column strip, band of rows); the input rows of
+// all its items form one stream through a kWsSlots-deep ring of halo rows in
+// shared memory (the layout and descriptor views above), and the output rows
+// alternate between two TMEM accumulators, so the three stages overlap:
+//   warp 5 (producer): cp.async of input row j into slot j % kWsSlots once the
+//     MMAs that read the slot's previous row have completed (mbarrier
+//     empty[slot], arrived by tcgen05.commit); completion signalled with
+//     cp.async.mbarrier.arrive on full[slot];
+//   warp 4, one thread (MMA): for output row i waits for its three input rows
+//     and for accumulator i & 1 to be drained, issues the 9 x Cin/16 MMAs,
+//     commits to acc_full[i & 1] and to empty[] of the row it no longer needs;
+//   warps 0-3 (epilogue): wait acc_full, tcgen05.ld their 32 TMEM lanes,
+//     release the accumulator (acc_empty), then bias, ReLU, BF16 and store,
+//     while the MMAs of the next row run.
+// The weights are staged once per CTA.  Every wait is bounded; on a timeout
+// the CTA raises the error flag and all roles leave their loops.
+constexpr int kWsSlots = 6;
+constexpr int kWsThreads = 192;
+constexpr uint32_t kWsSpinLimit = 1u << 22;
+
+template <int CIN, int COUT>
+struct WsSmem {
+    static constexpr int kChunks = CIN / 8;
+    static constexpr int kSlotBytes = kChunks * kHaloPx * 16;
+    static constexpr int kRingBytes = kWsSlots * kSlotBytes;
+    static constexpr int kBBytes = 9 * kChunks * COUT * 16;
+    static constexpr int kBytes = kRingBytes + kBBytes;
+    static constexpr int kAccCols = COUT < 32 ? 32 : COUT;
+    static constexpr int kTmemCols = 2 * kAccCols;
+};
+
+__device__ __forceinline__ bool mbar_wait_ws(uint32_t mbar, uint32_t parity,
+                                             const volatile int* abort_flag)
 {
-    constexpr int NCH = CIN / 8;
-    const int sr = min(max(r, 0), H - 1);
-    uint8_t* slot = ring + (r & 3) * slot_bytes;
-    const uint4* src_row = x + ((size_t)b * H + sr) * W * NCH;
-    for (int i = threadIdx.x; i < NCH * kHaloPx; i += kConvThreads) {
-        const int ch = i / kHaloPx, px = i - ch * kHaloPx;
-        const int sx = min(max(x0 - 1 + px, 0), W - 1);
-        cp_async16(smem_u32(slot + (ch * kHaloPx + px) * 16), src_row + (size_t)sx * NCH + ch);
+    for (uint32_t it = 0; it < kWsSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 1023u) == 1023u && *abort_flag) return false;
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+        : "memory");
+}
+
+struct WsItem {
+    int b, x0, y0, y1;
+};
+
+__device__ __forceinline__ WsItem ws_item(int w, int segs, int nbands, int band, int H)
+{
+    WsItem it;
+    const int seg = w % segs;
+    const int t = w / segs;
+    const int bi = t % nbands;
+    it.b = t / nbands;
+    it.x0 = seg * kTileM;
+    it.y0 = bi * band;
+    it.y1 = min(H, it.y0 + band);
+    return it;
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads, 1)
-    conv3x3_tc_rows_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
-                           const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int H,
-                           int W, int band, int relu, int* err)
+__global__ void __launch_bounds__(kWsThreads, 1)
+    conv3x3_tc_ws_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
+                         const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int H,
+                         int W, int segs, int nbands, int band, int items, int relu, int* err)
 {
-    using S = RowSmem<CIN, COUT>;
+    using S = WsSmem<CIN, COUT>;
     constexpr int NCH = S::kChunks;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem;
     uint8_t* sB = smem + S::kRingBytes;
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t full_bar[kWsSlots];
+    __shared__ __align__(8) uint64_t empty_bar[kWsSlots];
+    __shared__ __align__(8) uint64_t accf_bar[2];
+    __shared__ __align__(8) uint64_t acce_bar[2];
     __shared__ uint32_t tmem_base;
     __shared__ float s_bias[COUT];
+    __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
-    const uint32_t mbar_a = smem_u32(&mbar);
-    const int b = blockIdx.z;
-    const int x0 = blockIdx.x * kTileM;
-    const int y0 = blockIdx.y * band;
-    const int y1 = min(H, y0 + band);
+    const int lane = tid & 31;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -316,85 +365,161 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_a), "r"(1u));
+        for (int s = 0; s < kWsSlots; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[s])),
+                         "r"(32u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[s])),
+                         "r"(1u));
+        }
+        for (int k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf_bar[k])),
+                         "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce_bar[k])),
+                         "r"(4u));
+        }
+        s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    for (int i = tid; i < COUT; i += kConvThreads) s_bias[i] = bias[i];
-    for (int i = tid; i < 9 * COUT * NCH; i += kConvThreads) {
+    for (int i = tid; i < COUT; i += kWsThreads) s_bias[i] = bias[i];
+    for (int i = tid; i < 9 * COUT * NCH; i += kWsThreads) {
         const int ch = i % NCH;
         const int n = (i / NCH) % COUT;
         const int tap = i / (NCH * COUT);
         const uint4 v = w[(size_t)(tap * COUT + n) * NCH + ch];
         *reinterpret_cast<uint4*>(sB + ((tap * NCH + ch) * COUT + n) * 16) = v;
     }
-    // first three rows of the band
-    for (int r = y0 - 1; r <= y0 + 1; ++r) load_halo_row<CIN>(x, ring, b, r, x0, H, W, S::kSlotBytes);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = mma_idesc(kTileM, COUT);
-    const uint32_t ring_a = smem_u32(ring), b_base = smem_u32(sB);
-    const int xo = x0 + tid;
-    uint32_t phase = 0;
     bool ok = true;
 
-    for (int yy = y0; yy < y1; ++yy) {
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-                const uint32_t slot = (uint32_t)((yy + dy - 1) & 3) * S::kSlotBytes;
-#pragma unroll
-                for (int ks = 0; ks < NCH / 2; ++ks) {
-                    const uint64_t ad = smem_desc(ring_a + slot + ((2 * ks) * kHaloPx + dx) * 16,
-                                                  kHaloPx * 16, 128);
-                    const uint64_t bd =
-                        smem_desc(b_base + (tap * NCH + 2 * ks) * COUT * 16, COUT * 16, 128);
-                    mma_bf16(tmem, ad, bd, idesc, (tap | ks) != 0);
+    if (warp == 5) {
+        // ---------------------------------------------------------- producer
+        uint32_t jg = 0;
+        for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
+            const WsItem it = ws_item(wi, segs, nbands, band, H);
+            for (int r = it.y0 - 1; r <= it.y1 && ok; ++r, ++jg) {
+                const uint32_t s = jg % kWsSlots, u = jg / kWsSlots;
+                if (u > 0) ok = mbar_wait_ws(smem_u32(&empty_bar[s]), (u - 1) & 1u, &s_abort);
+                if (!ok) break;
+                const int sr = min(max(r, 0), H - 1);
+                uint8_t* slot = ring + s * S::kSlotBytes;
+                const uint4* src_row = x + ((size_t)it.b * H + sr) * W * NCH;
+                for (int i = lane; i < NCH * kHaloPx; i += 32) {
+                    const int px = i / NCH, ch = i - px * NCH;
+                    const int sx = min(max(it.x0 - 1 + px, 0), W - 1);
+                    cp_async16(smem_u32(slot + (ch * kHaloPx + px) * 16),
+                               src_row + (size_t)sx * NCH + ch);
                 }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                                 smem_u32(&full_bar[s]))
+                             : "memory");
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    mbar_a)
-                : "memory");
         }
-        // prefetch the row the next tile needs into the free slot
-        if (yy + 1 < y1) load_halo_row<CIN>(x, ring, b, yy + 2, x0, H, W, S::kSlotBytes);
-        ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;
-        phase ^= 1u;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == 4) {
+        // --------------------------------------------------------------- MMA
+        if (lane == 0) {
+            const uint32_t idesc = mma_idesc(kTileM, COUT);
+            const uint32_t ring_a = smem_u32(ring), b_base = smem_u32(sB);
+            uint32_t jg = 0, ig = 0;
+            int last_row = -1, last_out = -1;
+            for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
+                const WsItem it = ws_item(wi, segs, nbands, band, H);
+                const int nout = it.y1 - it.y0;
+                for (int i = 0; i < nout && ok; ++i, ++ig) {
+                    for (uint32_t j = (i == 0 ? jg : jg + i + 2); j <= jg + i + 2 && ok; ++j)
+                        ok = mbar_wait_ws(smem_u32(&full_bar[j % kWsSlots]),
+                                          (j / kWsSlots) & 1u, &s_abort);
+                    if (ok && ig >= 2)
+                        ok = mbar_wait_ws(smem_u32(&acce_bar[ig & 1]), ((ig >> 1) - 1) & 1u,
+                                          &s_abort);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t acc = tmem + (ig & 1) * S::kAccCols;
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 32) {
-            float acc[32];
-            tmem_ld32(lane_addr + c0, acc);
-            if (xo < W) {
-                __nv_bfloat16* out = y + (((size_t)b * H + yy) * W + xo) * COUT + c0;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+                        const uint32_t slot =
+                            (uint32_t)((jg + i + dy) % kWsSlots) * S::kSlotBytes;
 #pragma unroll
-                for (int j = 0; j < 32; j += 8) {
-                    __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float vq = acc[j + q] + s_bias[c0 + j + q];
-                        if (relu) vq = fmaxf(vq, 0.0f);
-                        o[q] = __float2bfloat16_rn(vq);
+                        for (int ks = 0; ks < NCH / 2; ++ks) {
+                            const uint64_t ad =
+                                smem_desc(ring_a + slot + ((2 * ks) * kHaloPx + dx) * 16,
+                                          kHaloPx * 16, 128);
+                            const uint64_t bd = smem_desc(
+                                b_base + (tap * NCH + 2 * ks) * COUT * 16, COUT * 16, 128);
+                            mma_bf16(acc, ad, bd, idesc, (tap | ks) != 0);
+                        }
                     }
-                    *reinterpret_cast<uint4*>(out + j) = *reinterpret_cast<const uint4*>(o);
+                    mma_commit(smem_u32(&accf_bar[ig & 1]));
+                    last_out = (int)ig;
+                    // input row i of the item is read by no later output
+                    mma_commit(smem_u32(&empty_bar[(jg + i) % kWsSlots]));
+                    last_row = (int)(jg + i);
+                    if (i == nout - 1) {
+                        mma_commit(smem_u32(&empty_bar[(jg + i + 1) % kWsSlots]));
+                        mma_commit(smem_u32(&empty_bar[(jg + i + 2) % kWsSlots]));
+                        last_row = (int)(jg + i + 2);
+                    }
+                }
+                jg += (uint32_t)(nout + 2);
+            }
+            // the MMAs and the arrivals of the last commits must have landed
+            // before the accumulators are freed and the CTA exits (also on
+            // the error path)
+            const volatile int no_abort = 0;
+            bool drained = true;
+            if (last_out >= 0)
+                drained = mbar_wait_ws(smem_u32(&accf_bar[last_out & 1]),
+                                       ((uint32_t)last_out >> 1) & 1u, &no_abort);
+            if (last_row >= 0 && drained)
+                drained = mbar_wait_ws(smem_u32(&empty_bar[last_row % kWsSlots]),
+                                       ((uint32_t)last_row / kWsSlots) & 1u, &no_abort);
+            ok = ok && drained;
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        uint32_t ig = 0;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
+            const WsItem it = ws_item(wi, segs, nbands, band, H);
+            const int xo = it.x0 + warp * 32 + lane;
+            for (int yy = it.y0; yy < it.y1; ++yy, ++ig) {
+                ok = mbar_wait_ws(smem_u32(&accf_bar[ig & 1]), (ig >> 1) & 1u, &s_abort);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float acc[S::kAccCols];
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 32)
+                    tmem_ld32(tmem + (ig & 1) * S::kAccCols + lane_off + c0, acc + c0);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acce_bar[ig & 1]));
+                if (xo < W) {
+                    __nv_bfloat16* out = y + (((size_t)it.b * H + yy) * W + xo) * COUT;
+#pragma unroll
+                    for (int j = 0; j < COUT; j += 8) {
+                        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            float vq = acc[j + q] + s_bias[j + q];
+                            if (relu) vq = fmaxf(vq, 0.0f);
+                            o[q] = __float2bfloat16_rn(vq);
+                        }
+                        *reinterpret_cast<uint4*>(out + j) = *reinterpret_cast<const uint4*>(o);
+                    }
                 }
             }
         }
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
     }
-    if (!ok && err) atomicExch(err, 1);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!ok) {
+        s_abort = 1;
+        if (err) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -416,23 +541,28 @@ hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y
         attr = true;
     }
     if (W >= kTileM) {
-        // row-walking kernel: bands of rows sized for about two CTAs per SM
-        using R = RowSmem<CIN, COUT>;
+        // warp-specialised row walk, one persistent CTA per SM; bands sized
+        // for about eight work items per CTA
+        using R = WsSmem<CIN, COUT>;
         static bool rattr = false;
         if (!rattr) {
-            cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_rows_kernel<CIN, COUT>,
+            cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_ws_kernel<CIN, COUT>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  R::kBytes);
             if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
             rattr = true;
         }
         const int segs = (W + kTileM - 1) / kTileM;
-        long units = (long)segs * B;
-        int band = H;
-        while (band > 16 && units * ((H + band - 1) / band) < 2L * nsm) band = (band + 1) / 2;
-        dim3 grd(segs, (H + band - 1) / band, B);
-        conv3x3_tc_rows_kernel<CIN, COUT><<<grd, kConvThreads, R::kBytes, st>>>(
-            (const uint4*)x, (const uint4*)w, bias, (__nv_bfloat16*)y, H, W, band, relu, err);
+        const long rows = (long)B * H * segs;
+        int band = (int)((rows + 8L * nsm - 1) / (8L * nsm));
+        band = band < 4 ? 4 : band > H ? H : band;
+        const int nbands = (H + band - 1) / band;
+        const long items = (long)B * segs * nbands;
+        if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
+        const int grid = items < nsm ? (int)items : nsm;
+        conv3x3_tc_ws_kernel<CIN, COUT><<<grid, kWsThreads, R::kBytes, st>>>(
+            (const uint4*)x, (const uint4*)w, bias, (__nv_bfloat16*)y, H, W, segs, nbands, band,
+            (int)items, relu, err);
         return check_launch();
     }
     const long P = (long)B * H * W;

@@ -27,16 +27,22 @@ def init_params(seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
-def generate_pairs(count: int, n: int, seed0: int = 0, threshold: float = 1e-6,
-                   max_iters: int = 5000, chunk: int = 1024, device=None):
+def generate_pairs(count: int, n: int, seed0: int = 0, sweeps: int = 40000,
+                   chunk: int = 1024, device=None):
     """(div, flags, target) on the device: div of a seeded velocity field with
-    obstacles, target = the scaled pressure phi of the plain projection, as
-    the mean of the last iterate and one more sweep (this cancels the
-    period-2 component that plain Jacobi never damps)."""
+    obstacles, target = the scaled pressure phi of the plain solver after a
+    fixed number of Jacobi sweeps from zero, as the mean of that iterate and
+    one more sweep (this cancels the period-2 component that plain Jacobi
+    never damps).
+
+    The sweep count sets how much of the smooth part of phi the target holds:
+    at 128^2, 8,000 sweeps leave 20-30 % relative L2 error against the exact
+    solve, 30,000 about 1 %, 60,000 below 0.1 %; the error falls with
+    sweeps / n^2."""
     dev = device or torch.device("cuda", torch.cuda.current_device())
     divs, fls, tgts = [], [], []
     ctx = hp.Context(min(chunk, count), n, n, device=dev.index)
-    prm = hp.ProjectParams(threshold=threshold, max_iters=max_iters)
+    prm = hp.ProjectParams(fixed_iters=sweeps)
     for c0 in range(0, count, chunk):
         B = min(chunk, count - c0)
         u, v, fl = W.training_case(B, n, seed0 + c0)

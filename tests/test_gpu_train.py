@@ -80,7 +80,7 @@ def test_gradient_matches_oracle_backward(dev, lam):
 def test_training_reduces_loss_and_jacobi_sweeps(dev):
     from paper_2109_09363_gb300 import training as T
     n = 64
-    data = T.generate_pairs(1024, n, seed0=0, threshold=1e-6, max_iters=8000, device=dev)
+    data = T.generate_pairs(1024, n, seed0=0, sweeps=16000, device=dev)
     cnn = hp.CNN(64, n, n, params=C.flatten(C.init_params(seed=1)))
     losses = T.train(cnn, data, epochs=30, batch=64, lr=1e-3, lambda_div=1.0)
     assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
