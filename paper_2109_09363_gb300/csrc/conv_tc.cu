@@ -260,21 +260,40 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
 // Warp-specialised persistent row walk (width >= 128).  Each CTA loops over
 // work items (grid, 128-pixel column strip, band of rows); the input rows of
 // all its items form one stream through a kWsSlots-deep ring of halo rows in
-// shared memory (the layout and descriptor views above), and the output rows
-// alternate between two TMEM accumulators, so the three stages overlap:
+// shared memory (the layout and descriptor views above).
+//
+// One input row r feeds three output rows: r + 1 through the kernel row
+// dy = 0, r through dy = 1 and r - 1 through dy = 2.  The weights are staged
+// as [dx][chunk][dy][cout][8 channels], so for each (dx, K step) the three
+// dy blocks are adjacent along N, and the accumulators of consecutive output
+// rows sit in adjacent TMEM column blocks of a ring of kAccSlots (output o of
+// the CTA's stream at columns Cout * (kAccSlots - 1 - o % kAccSlots)).  One
+// MMA with N = 3 Cout then adds row r's contribution to all three outputs:
+// the A operand (the 4 KB input view) is read once for three output rows,
+// and each input row needs 3 x Cin/16 MMAs.  At the first and last rows of a
+// band only the dy blocks whose output lies in the band are issued, and an
+// MMA whose column range would wrap around the ring is split in two; this
+// plan is made once per input row, so the unrolled issue loop costs two
+// descriptor additions per MMA.  Accumulator slots are pre-filled with the
+// bias, so every MMA accumulates.
+//
+// Roles, overlapping through mbarriers:
 //   warp 5 (producer): cp.async of input row j into slot j % kWsSlots once the
-//     MMAs that read the slot's previous row have completed (mbarrier
-//     empty[slot], arrived by tcgen05.commit); completion signalled with
+//     MMAs that read the slot's previous row have completed (empty[slot],
+//     arrived by tcgen05.commit); completion signalled with
 //     cp.async.mbarrier.arrive on full[slot];
-//   warp 4, one thread (MMA): for output row i waits for its three input rows
-//     and for accumulator i & 1 to be drained, issues the 9 x Cin/16 MMAs,
-//     commits to acc_full[i & 1] and to empty[] of the row it no longer needs;
-//   warps 0-3 (epilogue): wait acc_full, tcgen05.ld their 32 TMEM lanes,
-//     release the accumulator (acc_empty), then bias, ReLU, BF16 and store,
-//     while the MMAs of the next row run.
+//   warp 4, one thread (MMA): per input row waits for the row and, when it
+//     starts a new output row, for that accumulator slot to be refilled;
+//     issues the MMAs, commits to empty[] of the row and, when an output row
+//     is complete, to out_full[] of its slot;
+//   warps 0-3 (epilogue): wait out_full, tcgen05.ld their 32 TMEM lanes,
+//     refill the slot with the bias (tcgen05.st) and release it (slot_free),
+//     then ReLU + BF16 rounding in one conversion and a store staged through
+//     shared memory so that each warp writes contiguous 512-byte runs.
 // The weights are staged once per CTA.  Every wait is bounded; on a timeout
 // the CTA raises the error flag and all roles leave their loops.
 constexpr int kWsSlots = 6;
+constexpr int kAccSlots = 8;
 constexpr int kWsThreads = 192;
 constexpr uint32_t kWsSpinLimit = 1u << 22;
 
@@ -284,9 +303,11 @@ struct WsSmem {
     static constexpr int kSlotBytes = kChunks * kHaloPx * 16;
     static constexpr int kRingBytes = kWsSlots * kSlotBytes;
     static constexpr int kBBytes = 9 * kChunks * COUT * 16;
-    static constexpr int kBytes = kRingBytes + kBBytes;
-    static constexpr int kAccCols = COUT < 32 ? 32 : COUT;
-    static constexpr int kTmemCols = 2 * kAccCols;
+    // per epilogue warp: its 32 output pixels in BF16, 16-byte chunks XOR-swizzled
+    static constexpr int kStageBytes = 4 * 32 * COUT * 2;
+    static constexpr int kBytes = kRingBytes + kBBytes + kStageBytes;
+    static constexpr int kTmemCols = kAccSlots * COUT;  // 256 or 512
+    static_assert(COUT == 32 || COUT == 64, "accumulator ring sized for 32 or 64 channels");
 };
 
 __device__ __forceinline__ bool mbar_wait_ws(uint32_t mbar, uint32_t parity,
@@ -318,6 +339,49 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
         : "memory");
 }
 
+// 32 consecutive 32-bit TMEM columns of this thread's lane, without the wait.
+__device__ __forceinline__ void tmem_ld32_raw(uint32_t taddr, uint32_t* r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
+// Write 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+        "%27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// Two FP32 values to packed BF16 (lo in the low half), round to nearest even,
+// optionally with ReLU in the same conversion.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi, bool relu)
+{
+    uint32_t d;
+    if (relu)
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    else
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
 struct WsItem {
     int b, x0, y0, y1;
 };
@@ -335,6 +399,13 @@ __device__ __forceinline__ WsItem ws_item(int w, int segs, int nbands, int band,
     return it;
 }
 
+__device__ __forceinline__ uint32_t idesc_for_rows(int n_out, int cout)
+{
+    return n_out == 1 ? mma_idesc(kTileM, cout)
+           : n_out == 2 ? mma_idesc(kTileM, 2 * cout)
+                        : mma_idesc(kTileM, 3 * cout);
+}
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kWsThreads, 1)
     conv3x3_tc_ws_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
@@ -348,8 +419,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     uint8_t* sB = smem + S::kRingBytes;
     __shared__ __align__(8) uint64_t full_bar[kWsSlots];
     __shared__ __align__(8) uint64_t empty_bar[kWsSlots];
-    __shared__ __align__(8) uint64_t accf_bar[2];
-    __shared__ __align__(8) uint64_t acce_bar[2];
+    __shared__ __align__(8) uint64_t outf_bar[kAccSlots];
+    __shared__ __align__(8) uint64_t free_bar[kAccSlots];
     __shared__ uint32_t tmem_base;
     __shared__ float s_bias[COUT];
     __shared__ volatile int s_abort;
@@ -371,47 +442,75 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[s])),
                          "r"(1u));
         }
-        for (int k = 0; k < 2; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf_bar[k])),
+        for (int k = 0; k < kAccSlots; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&outf_bar[k])),
                          "r"(1u));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce_bar[k])),
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&free_bar[k])),
                          "r"(4u));
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     for (int i = tid; i < COUT; i += kWsThreads) s_bias[i] = bias[i];
+    // weights [tap = 3 dy + dx][cout][chunk] -> [dx][chunk][dy][cout] (16 B each)
     for (int i = tid; i < 9 * COUT * NCH; i += kWsThreads) {
         const int ch = i % NCH;
         const int n = (i / NCH) % COUT;
         const int tap = i / (NCH * COUT);
+        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
         const uint4 v = w[(size_t)(tap * COUT + n) * NCH + ch];
-        *reinterpret_cast<uint4*>(sB + ((tap * NCH + ch) * COUT + n) * 16) = v;
+        *reinterpret_cast<uint4*>(sB + (((dx * NCH + ch) * 3 + dy) * COUT + n) * 16) = v;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    // the bias as raw bits, the value every accumulator slot starts from
+    uint32_t bias_bits[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bias_bits[c] = __float_as_uint(s_bias[c]);
+    if (warp < 4) {
+#pragma unroll
+        for (int sl = 0; sl < kAccSlots; ++sl)
+#pragma unroll
+            for (int c0 = 0; c0 < COUT; c0 += 32)
+                tmem_st32(tmem + lane_off + (uint32_t)(sl * COUT + c0), bias_bits + c0);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     bool ok = true;
 
     if (warp == 5) {
         // ---------------------------------------------------------- producer
+        // lane: channel chunk ch of pixels p0, p0 + kPass, ...; a warp copies
+        // kPass whole pixels (512 contiguous bytes) per instruction
+        constexpr int kPass = 32 / NCH;
+        const int ch = lane % NCH, p0 = lane / NCH;
         uint32_t jg = 0;
         for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
             const WsItem it = ws_item(wi, segs, nbands, band, H);
+            const bool interior = it.x0 >= 1 && it.x0 + kHaloPx - 1 <= W;
             for (int r = it.y0 - 1; r <= it.y1 && ok; ++r, ++jg) {
                 const uint32_t s = jg % kWsSlots, u = jg / kWsSlots;
                 if (u > 0) ok = mbar_wait_ws(smem_u32(&empty_bar[s]), (u - 1) & 1u, &s_abort);
                 if (!ok) break;
                 const int sr = min(max(r, 0), H - 1);
-                uint8_t* slot = ring + s * S::kSlotBytes;
-                const uint4* src_row = x + ((size_t)it.b * H + sr) * W * NCH;
-                for (int i = lane; i < NCH * kHaloPx; i += 32) {
-                    const int px = i / NCH, ch = i - px * NCH;
-                    const int sx = min(max(it.x0 - 1 + px, 0), W - 1);
-                    cp_async16(smem_u32(slot + (ch * kHaloPx + px) * 16),
-                               src_row + (size_t)sx * NCH + ch);
+                const uint32_t dst = smem_u32(ring + s * S::kSlotBytes) + (uint32_t)(ch * kHaloPx * 16);
+                const uint4* src_row = x + ((size_t)it.b * H + sr) * W * NCH + ch;
+                if (interior) {
+                    const uint4* src = src_row + (size_t)(it.x0 - 1 + p0) * NCH;
+#pragma unroll 4
+                    for (int px = p0; px < kHaloPx; px += kPass, src += kPass * NCH)
+                        cp_async16(dst + (uint32_t)(px * 16), src);
+                } else {
+                    for (int px = p0; px < kHaloPx; px += kPass) {
+                        const int sx = min(max(it.x0 - 1 + px, 0), W - 1);
+                        cp_async16(dst + (uint32_t)(px * 16), src_row + (size_t)sx * NCH);
+                    }
                 }
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
                                  smem_u32(&full_bar[s]))
@@ -422,96 +521,132 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     } else if (warp == 4) {
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
-            const uint32_t idesc = mma_idesc(kTileM, COUT);
-            const uint32_t ring_a = smem_u32(ring), b_base = smem_u32(sB);
-            uint32_t jg = 0, ig = 0;
+            const uint64_t a_hi = smem_desc(0, kHaloPx * 16, 128);
+            const uint64_t bd_base = smem_desc(smem_u32(sB), 3 * COUT * 16, 128);
+            const uint32_t ring_a = smem_u32(ring);
+            uint32_t jg = 0, og = 0;
             int last_row = -1, last_out = -1;
             for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
                 const WsItem it = ws_item(wi, segs, nbands, band, H);
-                const int nout = it.y1 - it.y0;
-                for (int i = 0; i < nout && ok; ++i, ++ig) {
-                    for (uint32_t j = (i == 0 ? jg : jg + i + 2); j <= jg + i + 2 && ok; ++j)
-                        ok = mbar_wait_ws(smem_u32(&full_bar[j % kWsSlots]),
-                                          (j / kWsSlots) & 1u, &s_abort);
-                    if (ok && ig >= 2)
-                        ok = mbar_wait_ws(smem_u32(&acce_bar[ig & 1]), ((ig >> 1) - 1) & 1u,
-                                          &s_abort);
+                for (int r = it.y0 - 1; r <= it.y1 && ok; ++r, ++jg) {
+                    ok = mbar_wait_ws(smem_u32(&full_bar[jg % kWsSlots]),
+                                      (jg / kWsSlots) & 1u, &s_abort);
+                    // dy blocks whose output row r + 1 - dy lies in [y0, y1)
+                    const int dlo = max(0, r + 2 - it.y1), dhi = min(2, r + 1 - it.y0);
+                    const int nd = dhi - dlo + 1;
+                    const uint32_t o_first = og + (uint32_t)(r + 1 - dlo - it.y0);
+                    if (ok && dlo == 0 && o_first >= (uint32_t)kAccSlots)
+                        ok = mbar_wait_ws(smem_u32(&free_bar[o_first % kAccSlots]),
+                                          ((o_first / kAccSlots) - 1) & 1u, &s_abort);
                     if (!ok) break;
+                    // plan: outputs o_first, o_first - 1, ... in at most two
+                    // runs of adjacent TMEM column blocks (split at the wrap)
+                    const int m = (int)(o_first % kAccSlots);
+                    const int len0 = nd < m + 1 ? nd : m + 1;
+                    const int len1 = nd - len0;
+                    const uint32_t d0 = tmem + (uint32_t)(COUT * (kAccSlots - 1 - m));
+                    const uint32_t d1 = tmem;  // the run after the wrap starts at slot 0
+                    const uint32_t id0 = idesc_for_rows(len0, COUT);
+                    const uint32_t id1 = idesc_for_rows(len1 > 0 ? len1 : 1, COUT);
+                    // B row offsets (16-byte units) of the first dy block of each run
+                    const uint64_t b0 = bd_base + (uint64_t)(dlo * COUT);
+                    const uint64_t b1 = bd_base + (uint64_t)((dlo + len0) * COUT);
+                    const uint64_t ad_row =
+                        a_hi | (uint64_t)((ring_a + (jg % kWsSlots) * S::kSlotBytes) >> 4);
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t acc = tmem + (ig & 1) * S::kAccCols;
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-                        const uint32_t slot =
-                            (uint32_t)((jg + i + dy) % kWsSlots) * S::kSlotBytes;
+                    for (int dx = 0; dx < 3; ++dx) {
 #pragma unroll
                         for (int ks = 0; ks < NCH / 2; ++ks) {
-                            const uint64_t ad =
-                                smem_desc(ring_a + slot + ((2 * ks) * kHaloPx + dx) * 16,
-                                          kHaloPx * 16, 128);
-                            const uint64_t bd = smem_desc(
-                                b_base + (tap * NCH + 2 * ks) * COUT * 16, COUT * 16, 128);
-                            mma_bf16(acc, ad, bd, idesc, (tap | ks) != 0);
+                            // A: input view shifted by dx pixels, channel chunk 2 ks;
+                            // B: weights of (dx, chunk 2 ks)
+                            const uint64_t ad = ad_row + (uint64_t)(2 * ks * kHaloPx + dx);
+                            const uint64_t boff = (uint64_t)((dx * NCH + 2 * ks) * 3 * COUT);
+                            mma_bf16(d0, ad, b0 + boff, id0, 1u);
+                            if (len1 > 0) mma_bf16(d1, ad, b1 + boff, id1, 1u);
                         }
                     }
-                    mma_commit(smem_u32(&accf_bar[ig & 1]));
-                    last_out = (int)ig;
-                    // input row i of the item is read by no later output
-                    mma_commit(smem_u32(&empty_bar[(jg + i) % kWsSlots]));
-                    last_row = (int)(jg + i);
-                    if (i == nout - 1) {
-                        mma_commit(smem_u32(&empty_bar[(jg + i + 1) % kWsSlots]));
-                        mma_commit(smem_u32(&empty_bar[(jg + i + 2) % kWsSlots]));
-                        last_row = (int)(jg + i + 2);
+                    mma_commit(smem_u32(&empty_bar[jg % kWsSlots]));
+                    last_row = (int)jg;
+                    if (dhi == 2) {
+                        // output row r - 1 has all three contributions
+                        const uint32_t o_done = og + (uint32_t)(r - 1 - it.y0);
+                        mma_commit(smem_u32(&outf_bar[o_done % kAccSlots]));
+                        last_out = (int)o_done;
                     }
                 }
-                jg += (uint32_t)(nout + 2);
+                og += (uint32_t)(it.y1 - it.y0);
             }
             // the MMAs and the arrivals of the last commits must have landed
             // before the accumulators are freed and the CTA exits (also on
             // the error path)
             const volatile int no_abort = 0;
             bool drained = true;
-            if (last_out >= 0)
-                drained = mbar_wait_ws(smem_u32(&accf_bar[last_out & 1]),
-                                       ((uint32_t)last_out >> 1) & 1u, &no_abort);
-            if (last_row >= 0 && drained)
+            if (last_row >= 0)
                 drained = mbar_wait_ws(smem_u32(&empty_bar[last_row % kWsSlots]),
                                        ((uint32_t)last_row / kWsSlots) & 1u, &no_abort);
+            if (last_out >= 0 && drained)
+                drained = mbar_wait_ws(smem_u32(&outf_bar[last_out % kAccSlots]),
+                                       ((uint32_t)last_out / kAccSlots) & 1u, &no_abort);
             ok = ok && drained;
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        uint32_t ig = 0;
-        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        constexpr int CPP = COUT / 8;  // 16-byte chunks per pixel
+        auto stage_swz = [](int p) { return (p / (8 / CPP)) & (CPP - 1); };
+        uint8_t* stage = sB + S::kBBytes + warp * 32 * COUT * 2;
+        const bool do_relu = relu != 0;
+        uint32_t og = 0;
         for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
             const WsItem it = ws_item(wi, segs, nbands, band, H);
-            const int xo = it.x0 + warp * 32 + lane;
-            for (int yy = it.y0; yy < it.y1; ++yy, ++ig) {
-                ok = mbar_wait_ws(smem_u32(&accf_bar[ig & 1]), (ig >> 1) & 1u, &s_abort);
+            for (int yy = it.y0; yy < it.y1; ++yy, ++og) {
+                const uint32_t sl = og % kAccSlots;
+                ok = mbar_wait_ws(smem_u32(&outf_bar[sl]), (og / kAccSlots) & 1u, &s_abort);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float acc[S::kAccCols];
+                const uint32_t taddr =
+                    tmem + lane_off + (uint32_t)(COUT * (kAccSlots - 1 - (int)sl));
+                uint32_t acc[COUT];
 #pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 32)
-                    tmem_ld32(tmem + (ig & 1) * S::kAccCols + lane_off + c0, acc + c0);
+                for (int c0 = 0; c0 < COUT; c0 += 32) tmem_ld32_raw(taddr + c0, acc + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // refill the slot with the bias for the output row that reuses it
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 32) tmem_st32(taddr + c0, bias_bits + c0);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&acce_bar[ig & 1]));
-                if (xo < W) {
-                    __nv_bfloat16* out = y + (((size_t)it.b * H + yy) * W + xo) * COUT;
+                if (lane == 0) mbar_arrive(smem_u32(&free_bar[sl]));
+                // the warp's 32 pixels go through shared memory so that the
+                // global stores are contiguous: chunk c of pixel p (16 bytes,
+                // 8 channels) sits at position c ^ swz(p), conflict-free on
+                // both sides
 #pragma unroll
-                    for (int j = 0; j < COUT; j += 8) {
-                        __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            float vq = acc[j + q] + s_bias[j + q];
-                            if (relu) vq = fmaxf(vq, 0.0f);
-                            o[q] = __float2bfloat16_rn(vq);
-                        }
-                        *reinterpret_cast<uint4*>(out + j) = *reinterpret_cast<const uint4*>(o);
-                    }
+                for (int c = 0; c < CPP; ++c) {
+                    uint4 o;
+                    o.x = pack_bf16x2(__uint_as_float(acc[8 * c + 0]),
+                                      __uint_as_float(acc[8 * c + 1]), do_relu);
+                    o.y = pack_bf16x2(__uint_as_float(acc[8 * c + 2]),
+                                      __uint_as_float(acc[8 * c + 3]), do_relu);
+                    o.z = pack_bf16x2(__uint_as_float(acc[8 * c + 4]),
+                                      __uint_as_float(acc[8 * c + 5]), do_relu);
+                    o.w = pack_bf16x2(__uint_as_float(acc[8 * c + 6]),
+                                      __uint_as_float(acc[8 * c + 7]), do_relu);
+                    *reinterpret_cast<uint4*>(stage + lane * (COUT * 2) +
+                                              ((c ^ stage_swz(lane)) * 16)) = o;
                 }
+                __syncwarp();
+                __nv_bfloat16* row = y + (((size_t)it.b * H + yy) * W + it.x0 + warp * 32) * COUT;
+#pragma unroll
+                for (int i = 0; i < CPP; ++i) {
+                    const int k = lane + 32 * i;
+                    const int p = k / CPP, c = k % CPP;
+                    const uint4 v = *reinterpret_cast<const uint4*>(
+                        stage + p * (COUT * 2) + ((c ^ stage_swz(p)) * 16));
+                    if (it.x0 + warp * 32 + p < W)
+                        *reinterpret_cast<uint4*>(row + (size_t)p * COUT + 8 * c) = v;
+                }
+                __syncwarp();
             }
         }
     }
