@@ -461,7 +461,7 @@ def main():
                          "of N x N, three times (a small case for ncu)")
     ap.add_argument("--temporal-block", type=int, default=T_BLOCK,
                     help="sweeps per launch of the temporally blocked kernel (1..8)")
-    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="0 = library choice, 1 = streaming, 2 = temporally blocked "
                          "(4 rows per thread), 3 = temporally blocked (2 rows per thread)")
     ap.add_argument("--profile-conv", nargs=5, type=int,

@@ -68,7 +68,13 @@ typedef struct {
  *                  stop decided one launch later), 2 = temporally blocked (T
  *                  sweeps per launch, replay to the exact stop; 4 rows per
  *                  thread), 3 = temporally blocked with 2 rows per thread
- *                  (twice the warps).  All give the same iterates bit for bit. */
+ *                  (twice the warps), 4 = grid-resident: one thread-block
+ *                  cluster (up to 16 CTAs of 128 x 128 cells) keeps a whole
+ *                  grid on chip for all sweeps, falling back to 2 when the
+ *                  grid is larger than 512 x 512 cells or the cluster does
+ *                  not fit on the device.  All give the same iterates bit for
+ *                  bit; the FP64 E_k may differ in the last bits between
+ *                  kernels (their partial sums are grouped differently). */
 typedef struct {
     double threshold;
     int32_t max_iters;
@@ -139,6 +145,14 @@ hp_status hp_project(hp_ctx *ctx, float *u, float *v, const uint8_t *flags, hp_s
 hp_status hp_jacobi_sweeps(hp_ctx *ctx, const float *phi_in, const float *div,
                            const uint8_t *flags, float *phi_out, int32_t n, double *e_out,
                            hp_shape shape, void *stream);
+
+/* Number of grids of this shape that the grid-resident sweep kernel
+ * (sweep_kernel = 4) can hold on the device at once, one thread-block cluster
+ * of ceil(nx/128) x ceil(ny/128) CTAs per grid; 0 when that kernel cannot run
+ * the shape (grid above 512 x 512 cells, or the cluster does not fit), in
+ * which case hp_project falls back to the temporally blocked kernel.  Host
+ * query only (no kernel launch); 0 for a NULL context or an invalid shape. */
+int32_t hp_resident_clusters(hp_ctx *ctx, hp_shape shape);
 
 /* Parameters of the plume driver step (Sec. 2.2: semi-Lagrangian advection
  * of the density and of the velocity, then the external force by forward

@@ -54,6 +54,7 @@ _SIGS = {
                                   _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "hp_jacobi_sweeps": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P, hp_shape, _P]),
     "hp_div_norms_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
+    "hp_resident_clusters": (ctypes.c_int32, [_P, hp_shape]),
     "hp_advect_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, hp_shape,
                                       ctypes.POINTER(hp_plume_params), _P]),
     "hp_conv3x3_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
@@ -203,6 +204,13 @@ def hp_divergence(u, v, flags, div_out=None, stream=None):
     _check(load_library().hp_divergence(_ptr(u), _ptr(v), _ptr(flags), _ptr(div_out), s,
                                         _stream(stream)))
     return div_out
+
+
+def hp_resident_clusters(ctx: Context, batch: int, ny: int, nx: int) -> int:
+    """Grids of this shape the grid-resident sweep kernel (sweep_kernel = 4)
+    holds at once; 0 when it cannot run the shape (hp_project then uses the
+    temporally blocked kernel)."""
+    return int(load_library().hp_resident_clusters(ctx.handle, hp_shape(batch, ny, nx)))
 
 
 def hp_div_norms(ctx: Context, u, v, flags, stream=None):
@@ -494,5 +502,5 @@ def exported_symbols():
     import re
     hdr = os.path.join(HERE, "..", "include", "hproj.h")
     txt = open(hdr).read()
-    return sorted(set(re.findall(r"^\s*(?:hp_status|void|int64_t|const char \*)\s*(hp_\w+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:hp_status|void|int64_t|int32_t|const char \*)\s*(hp_\w+)\s*\(",
                                  txt, re.M)))

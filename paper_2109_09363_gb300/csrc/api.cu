@@ -78,6 +78,7 @@ void hp_ctx_destroy(hp_ctx* c)
     cudaFree(c->div);
     cudaFree(c->phi[0]);
     cudaFree(c->phi[1]);
+    cudaFree(c->ckpt);
     cudaFree(c->partial);
     cudaFree(c->partial2);
     cudaFree(c->gs);
@@ -123,6 +124,7 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
         (rc = dalloc(&c->div, c->max_cells)) != HP_OK ||
         (rc = dalloc(&c->phi[0], c->max_cells)) != HP_OK ||
         (rc = dalloc(&c->phi[1], c->max_cells)) != HP_OK ||
+        (rc = dalloc(&c->ckpt, c->max_cells)) != HP_OK ||
         (rc = dalloc(&c->partial, c->partial_len)) != HP_OK ||
         (rc = dalloc(&c->partial2, c->partial2_len)) != HP_OK ||
         (rc = dalloc(&c->gs, (size_t)mx.batch)) != HP_OK || (rc = dalloc(&c->ls, 1)) != HP_OK) {
@@ -180,7 +182,7 @@ hp_status hp_project(hp_ctx* c, float* u, float* v, const uint8_t* flags, hp_sha
     if (!c || !u || !v || !flags || !prm || !iters_out || !fits(c, s)) return HP_ERR_INVALID_ARG;
     if (prm->max_iters < 0 || prm->fixed_iters < 0 || prm->temporal_block < 0 ||
         prm->temporal_block > kMaxBlock || !(prm->threshold >= 0.0) || !(prm->dt > 0.0f) ||
-        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 3)
+        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 4)
         return HP_ERR_INVALID_ARG;
     if ((e_hist == nullptr) != (hist_len <= 0)) return HP_ERR_INVALID_ARG;
     return project_impl(c, u, v, flags, s, prm, phi0, p_out, iters_out, e1_out, einf_out, conv_out,

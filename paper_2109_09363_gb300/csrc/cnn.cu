@@ -13,10 +13,10 @@
 // is linear in div).  BF16 activations and weights, FP32 accumulation; the
 // 1-channel branch outputs are kept in FP32.
 //
-// Kernels: cnn_scale_kernel (s per grid), conv_first_kernel (2/3 -> 32 on
-// CUDA cores, pooling and up-sampling fused into its input read), the
-// tensor-core conv3x3 (conv_tc.cu) for the 32/64-channel layers,
-// conv_last_kernel (32 -> 1 on CUDA cores), phi0_kernel.
+// Kernels: cnn_scale_partial/finish_kernel (s per grid), branch_input_kernel
+// (pooling, up-sampling and scaling into the branch input), conv_first_kernel
+// (2/3 -> 32 on CUDA cores), the tensor-core conv3x3 (conv_tc.cu) for the
+// 32/64-channel layers, conv_last_kernel (32 -> 1 on CUDA cores), phi0_kernel.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -46,31 +46,64 @@ const LayerSpec kSpec[kLayers] = {
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // s[b] = mean |div| over fluid cells, 1 when there is none or it is zero.
-__global__ void cnn_scale_kernel(const float* __restrict__ div, const uint8_t* __restrict__ flags,
-                                 float* __restrict__ s, size_t cells)
+// s[b] = mean |div| over fluid cells, 1 when there is none or it is zero.
+// Pass 1: kScaleCtas CTAs per grid, each a contiguous slice of the cells;
+// FP32 sums per thread (at most a few dozen terms), FP64 across the warp and
+// the CTA.  Pass 2: one warp per grid adds the CTA partials in a fixed order.
+constexpr int kScaleCtas = 32;
+constexpr int kScaleThreads = 256;
+
+__global__ void cnn_scale_partial_kernel(const float* __restrict__ div,
+                                         const uint8_t* __restrict__ flags,
+                                         double* __restrict__ part_sum,
+                                         unsigned long long* __restrict__ part_cnt, size_t cells)
 {
-    __shared__ double sh_sum[32];
-    __shared__ unsigned long long sh_cnt[32];
-    const int b = blockIdx.x;
-    double sum = 0.0;
-    unsigned long long cnt = 0;
-    for (size_t q = threadIdx.x; q < cells; q += blockDim.x) {
-        if (flags[b * cells + q] == 0) {
-            sum += fabs((double)div[b * cells + q]);
+    __shared__ double sh_sum[kScaleThreads / 32];
+    __shared__ unsigned long long sh_cnt[kScaleThreads / 32];
+    const int b = blockIdx.y;
+    const size_t per = (cells + kScaleCtas - 1) / kScaleCtas;
+    const size_t q0 = (size_t)blockIdx.x * per;
+    const size_t q1 = q0 + per < cells ? q0 + per : cells;
+    const float* d = div + (size_t)b * cells;
+    const uint8_t* f = flags + (size_t)b * cells;
+    float sum = 0.0f;
+    unsigned cnt = 0;
+    for (size_t q = q0 + threadIdx.x; q < q1; q += kScaleThreads) {
+        if (f[q] == 0) {
+            sum += fabsf(d[q]);
             ++cnt;
         }
     }
+    double ds = (double)sum;
+    unsigned long long dc = cnt;
     for (int off = 16; off > 0; off >>= 1) {
-        sum += __shfl_down_sync(0xffffffffu, sum, off);
-        cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+        ds += __shfl_down_sync(0xffffffffu, ds, off);
+        dc += __shfl_down_sync(0xffffffffu, dc, off);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { sh_sum[wid] = sum; sh_cnt[wid] = cnt; }
+    if (lane == 0) { sh_sum[wid] = ds; sh_cnt[wid] = dc; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         unsigned long long c = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += sh_sum[w]; c += sh_cnt[w]; }
+        for (int w = 0; w < kScaleThreads / 32; ++w) { t += sh_sum[w]; c += sh_cnt[w]; }
+        part_sum[(size_t)b * kScaleCtas + blockIdx.x] = t;
+        part_cnt[(size_t)b * kScaleCtas + blockIdx.x] = c;
+    }
+}
+
+__global__ void cnn_scale_finish_kernel(const double* __restrict__ part_sum,
+                                        const unsigned long long* __restrict__ part_cnt,
+                                        float* __restrict__ s)
+{
+    const int b = blockIdx.x, lane = threadIdx.x;
+    double t = lane < kScaleCtas ? part_sum[(size_t)b * kScaleCtas + lane] : 0.0;
+    unsigned long long c = lane < kScaleCtas ? part_cnt[(size_t)b * kScaleCtas + lane] : 0ull;
+    for (int off = 16; off > 0; off >>= 1) {
+        t += __shfl_down_sync(0xffffffffu, t, off);
+        c += __shfl_down_sync(0xffffffffu, c, off);
+    }
+    if (lane == 0) {
         const double m = c ? t / (double)c : 0.0;
         s[b] = m > 0.0 ? (float)m : 1.0f;
     }
@@ -113,17 +146,10 @@ struct BranchIn {
     }
 };
 
-// First convolution of a branch: cin (2 or 3) -> 32, bias, ReLU, BF16 NHWC.
-// w: float [9][cin][32] (BF16-rounded values), bias float [32].
-__global__ void conv_first_kernel(BranchIn in, int cin, const float* __restrict__ w,
-                                  const float* __restrict__ bias, __nv_bfloat16* __restrict__ y,
-                                  int B, float* __restrict__ xin_out)
+// Branch input, once per pixel of the branch: xin [P][cin] FP32 holding the
+// BF16-rounded values [pool(div)/s, pool(flags)(, up(coarser output))].
+__global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xin, int B)
 {
-    __shared__ float sw[9 * 3 * 32];
-    __shared__ float sb[32];
-    for (int q = threadIdx.x; q < 9 * cin * 32; q += blockDim.x) sw[q] = w[q];
-    if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
-    __syncthreads();
     const int hs = in.H / in.scale, ws = in.W / in.scale;
     const long P = (long)B * hs * ws;
     for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
@@ -131,63 +157,153 @@ __global__ void conv_first_kernel(BranchIn in, int cin, const float* __restrict_
         const int b = (int)(p / ((long)hs * ws));
         const int r = (int)(p - (long)b * hs * ws);
         const int j = r / ws, i = r - j * ws;
-        float acc[32];
-#pragma unroll
-        for (int o = 0; o < 32; ++o) acc[o] = 0.0f;
-        if (xin_out) {
-            // the branch input of this pixel, kept for the weight gradient
-            float xc[3];
-            in.at(b, i, j, xc);
-            for (int c = 0; c < cin; ++c) xin_out[(size_t)p * cin + c] = xc[c];
-        }
-        for (int dy = 0; dy < 3; ++dy)
-            for (int dx = 0; dx < 3; ++dx) {
-                float xv[3];
-                in.at(b, min(max(i + dx - 1, 0), ws - 1), min(max(j + dy - 1, 0), hs - 1), xv);
-                const float* wt = sw + (dy * 3 + dx) * cin * 32;
-                for (int c = 0; c < cin; ++c)
-#pragma unroll
-                    for (int o = 0; o < 32; ++o) acc[o] = fmaf(wt[c * 32 + o], xv[c], acc[o]);
-            }
-        __align__(16) __nv_bfloat16 ob[32];
-#pragma unroll
-        for (int o = 0; o < 32; ++o) ob[o] = __float2bfloat16_rn(fmaxf(acc[o] + sb[o], 0.0f));
-        uint4* dst = reinterpret_cast<uint4*>(y + (size_t)p * 32);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(ob)[q];
+        float xc[3];
+        in.at(b, i, j, xc);
+        for (int c = 0; c < cin; ++c) xin[(size_t)p * cin + c] = xc[c];
     }
 }
 
-// Last convolution of a branch: 32 -> 1, bias, no ReLU, FP32 output.
-// w: float [9][32] (BF16-rounded), bias float [1].
-__global__ void conv_last_kernel(const __nv_bfloat16* __restrict__ x, const float* __restrict__ w,
-                                 const float* __restrict__ bias, float* __restrict__ y, int B, int H,
-                                 int W)
+// First convolution of a branch: cin (2 or 3) -> 32, bias, ReLU, BF16 NHWC,
+// from the branch input xin [P][cin].  Each thread computes two horizontally
+// adjacent pixels, so every weight read from shared memory (a broadcast) feeds
+// two FMAs.  w: float [9][cin][32] (BF16-rounded values), bias float [32].
+template <int CIN>
+__global__ void __launch_bounds__(128)
+    conv_first_kernel(const float* __restrict__ xin, const float* __restrict__ w,
+                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int B,
+                      int H, int W)
 {
-    __shared__ float sw[9 * 32];
+    __shared__ __align__(16) float sw[9 * CIN * 32];
+    __shared__ __align__(16) float sb[32];
+    for (int q = threadIdx.x; q < 9 * CIN * 32; q += blockDim.x) sw[q] = w[q];
+    if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const int W2 = (W + 1) / 2;
+    const long P2 = (long)B * H * W2;
+    for (long p2 = (long)blockIdx.x * blockDim.x + threadIdx.x; p2 < P2;
+         p2 += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(p2 / ((long)H * W2));
+        const int r = (int)(p2 - (long)b * H * W2);
+        const int j = r / W2, i0 = 2 * (r - j * W2);
+        const bool two = i0 + 1 < W;
+        float acc0[32], acc1[32];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) { acc0[o] = sb[o]; acc1[o] = sb[o]; }
+#pragma unroll 1
+        for (int dy = 0; dy < 3; ++dy) {
+            const int sy = min(max(j + dy - 1, 0), H - 1);
+            const float* xr = xin + ((size_t)b * H + sy) * W * CIN;
+#pragma unroll 1
+            for (int dx = 0; dx < 3; ++dx) {
+                // input columns of the two outputs for this tap (clamped)
+                const int sx0 = min(max(i0 - 1 + dx, 0), W - 1);
+                const int sx1 = min(max(i0 + dx, 0), W - 1);
+                const float* wt = sw + (dy * 3 + dx) * CIN * 32;
+#pragma unroll
+                for (int c = 0; c < CIN; ++c) {
+                    const float a0 = xr[(size_t)sx0 * CIN + c], a1 = xr[(size_t)sx1 * CIN + c];
+                    const float4* w4 = reinterpret_cast<const float4*>(wt + c * 32);
+#pragma unroll
+                    for (int o4 = 0; o4 < 8; ++o4) {
+                        const float4 wv = w4[o4];
+                        acc0[4 * o4 + 0] = fmaf(wv.x, a0, acc0[4 * o4 + 0]);
+                        acc0[4 * o4 + 1] = fmaf(wv.y, a0, acc0[4 * o4 + 1]);
+                        acc0[4 * o4 + 2] = fmaf(wv.z, a0, acc0[4 * o4 + 2]);
+                        acc0[4 * o4 + 3] = fmaf(wv.w, a0, acc0[4 * o4 + 3]);
+                        acc1[4 * o4 + 0] = fmaf(wv.x, a1, acc1[4 * o4 + 0]);
+                        acc1[4 * o4 + 1] = fmaf(wv.y, a1, acc1[4 * o4 + 1]);
+                        acc1[4 * o4 + 2] = fmaf(wv.z, a1, acc1[4 * o4 + 2]);
+                        acc1[4 * o4 + 3] = fmaf(wv.w, a1, acc1[4 * o4 + 3]);
+                    }
+                }
+            }
+        }
+        __align__(16) __nv_bfloat16 ob[32];
+        const size_t p = ((size_t)b * H + j) * W + i0;
+#pragma unroll
+        for (int o = 0; o < 32; ++o) ob[o] = __float2bfloat16_rn(fmaxf(acc0[o], 0.0f));
+        uint4* dst = reinterpret_cast<uint4*>(y + p * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(ob)[q];
+        if (two) {
+#pragma unroll
+            for (int o = 0; o < 32; ++o) ob[o] = __float2bfloat16_rn(fmaxf(acc1[o], 0.0f));
+            dst += 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(ob)[q];
+        }
+    }
+}
+
+// Last convolution of a branch: 32 -> 1, bias, no ReLU, FP32 output.  A
+// thread walks kLastRows output rows of one column: every input row (its
+// three clamped neighbours in that row) is loaded once and dotted with the
+// three kernel rows, adding to the outputs above, at and below it.  Lanes of
+// a warp take consecutive columns, so the loads are contiguous.
+// w: float [9][32] (BF16-rounded), bias float [1].
+constexpr int kLastRows = 8;
+
+__global__ void __launch_bounds__(128)
+    conv_last_kernel(const __nv_bfloat16* __restrict__ x, const float* __restrict__ w,
+                     const float* __restrict__ bias, float* __restrict__ y, int B, int H, int W)
+{
+    __shared__ __align__(16) float sw[9 * 32];
     for (int q = threadIdx.x; q < 9 * 32; q += blockDim.x) sw[q] = w[q];
     __syncthreads();
-    const long P = (long)B * H * W;
-    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-         p += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(p / ((long)H * W));
-        const int r = (int)(p - (long)b * H * W);
-        const int j = r / W, i = r - j * W;
-        float acc = 0.0f;
-        for (int dy = 0; dy < 3; ++dy)
+    const float b0 = bias[0];
+    const int strips = (H + kLastRows - 1) / kLastRows;
+    const long T = (long)B * strips * W;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % W);
+        const long bs = t / W;
+        const int b = (int)(bs / strips);
+        const int j0 = (int)(bs - (long)b * strips) * kLastRows;
+        const int j1 = min(H, j0 + kLastRows);
+        // a0: partial sum of output row r - 1, a1: of output row r
+        float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll 1
+        for (int r = j0 - 1; r <= j1; ++r) {  // input rows
+            const int sr = min(max(r, 0), H - 1);
+            float d[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
             for (int dx = 0; dx < 3; ++dx) {
-                const int sy = min(max(j + dy - 1, 0), H - 1), sx = min(max(i + dx - 1, 0), W - 1);
-                const uint4* src = reinterpret_cast<const uint4*>(x + (((size_t)b * H + sy) * W + sx) * 32);
-                const float* wt = sw + (dy * 3 + dx) * 32;
+                const int sx = min(max(i + dx - 1, 0), W - 1);
+                const uint4* src =
+                    reinterpret_cast<const uint4*>(x + (((size_t)b * H + sr) * W + sx) * 32);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const uint4 v = src[q];
-                    const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+                    const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v);
+                    float f[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc = fmaf(wt[q * 8 + k], __bfloat162float(e[k]), acc);
+                    for (int h = 0; h < 4; ++h) {
+                        const float2 t2 = __bfloat1622float2(e[h]);
+                        f[2 * h] = t2.x;
+                        f[2 * h + 1] = t2.y;
+                    }
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const float4* wq = reinterpret_cast<const float4*>(
+                            sw + (dy * 3 + dx) * 32 + q * 8);
+                        const float4 wa = wq[0], wb = wq[1];
+                        d[dy] = fmaf(wa.x, f[0], d[dy]);
+                        d[dy] = fmaf(wa.y, f[1], d[dy]);
+                        d[dy] = fmaf(wa.z, f[2], d[dy]);
+                        d[dy] = fmaf(wa.w, f[3], d[dy]);
+                        d[dy] = fmaf(wb.x, f[4], d[dy]);
+                        d[dy] = fmaf(wb.y, f[5], d[dy]);
+                        d[dy] = fmaf(wb.z, f[6], d[dy]);
+                        d[dy] = fmaf(wb.w, f[7], d[dy]);
+                    }
                 }
             }
-        y[p] = acc + bias[0];
+            // input row r is tap dy = 2 of output r - 1 (now complete), dy = 1
+            // of output r and dy = 0 of output r + 1
+            if (r - 1 >= j0) y[((size_t)b * H + (r - 1)) * W + i] = (a0 + d[2]) + b0;
+            a0 = a1 + d[1];
+            a1 = d[0];
+        }
     }
 }
 
@@ -219,9 +335,55 @@ struct hp_cnn {
     // workspace
     __nv_bfloat16* act[2];
     float* out[3];  // branch outputs at 1/4, 1/2, 1
+    float* xin;     // branch input [P][cin] FP32 (largest branch)
     float* s;
+    double* s_part;                // [B][kScaleCtas] partial sums of |div|
+    unsigned long long* s_cnt;     // [B][kScaleCtas] fluid-cell counts
     int* err;
 };
+
+static hp_status launch_scale(hp_cnn* c, const float* div, const uint8_t* flags, int B,
+                              size_t cells, cudaStream_t st)
+{
+    cnn_scale_partial_kernel<<<dim3(kScaleCtas, B), kScaleThreads, 0, st>>>(div, flags, c->s_part,
+                                                                          c->s_cnt, cells);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+    cnn_scale_finish_kernel<<<B, 32, 0, st>>>(c->s_part, c->s_cnt, c->s);
+    return check_launch();
+}
+
+// branch input (pooling / up-sampling) into xin, then the cin -> 32 convolution
+static hp_status launch_first(hp_cnn* c, const BranchIn& in, int cin, float* xin, const float* w,
+                              const float* bias, __nv_bfloat16* y, int B, int H, int W,
+                              cudaStream_t st)
+{
+    const long P = (long)B * H * W;
+    const long cap = 16L * c->num_sms;
+    const int blocks = (int)((P + 255) / 256 < cap ? (P + 255) / 256 : cap);
+    branch_input_kernel<<<blocks, 256, 0, st>>>(in, cin, xin, B);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+    const long P2 = (long)B * H * ((W + 1) / 2);
+    const int blocks2 = (int)((P2 + 127) / 128 < cap ? (P2 + 127) / 128 : cap);
+    if (cin == 2)
+        conv_first_kernel<2><<<blocks2, 128, 0, st>>>(xin, w, bias, y, B, H, W);
+    else if (cin == 3)
+        conv_first_kernel<3><<<blocks2, 128, 0, st>>>(xin, w, bias, y, B, H, W);
+    else
+        return HP_ERR_UNSUPPORTED;
+    return check_launch();
+}
+
+static hp_status launch_last(hp_cnn* c, const __nv_bfloat16* x, const float* w, const float* bias,
+                             float* y, int B, int H, int W, cudaStream_t st)
+{
+    const long T = (long)B * ((H + kLastRows - 1) / kLastRows) * W;
+    const long cap = 16L * c->num_sms;
+    const int blocks = (int)((T + 127) / 128 < cap ? (T + 127) / 128 : cap);
+    conv_last_kernel<<<blocks, 128, 0, st>>>(x, w, bias, y, B, H, W);
+    return check_launch();
+}
 
 static size_t layer_wcount(int l) { return (size_t)9 * kSpec[l].cin * kSpec[l].cout; }
 
@@ -244,6 +406,9 @@ void hp_cnn_destroy(hp_cnn* c)
     cudaFree(c->act[0]);
     cudaFree(c->act[1]);
     for (int k = 0; k < 3; ++k) cudaFree(c->out[k]);
+    cudaFree(c->xin);
+    cudaFree(c->s_part);
+    cudaFree(c->s_cnt);
     cudaFree(c->s);
     cudaFree(c->err);
     delete c;
@@ -278,6 +443,11 @@ hp_status hp_cnn_create(hp_cnn** out, hp_shape mx, int device)
           cudaMalloc((void**)&c->out[0], px / 16 * 4 + 16) == cudaSuccess &&
           cudaMalloc((void**)&c->out[1], px / 4 * 4 + 16) == cudaSuccess &&
           cudaMalloc((void**)&c->out[2], px * 4) == cudaSuccess &&
+          cudaMalloc((void**)&c->xin, px * 3 * sizeof(float)) == cudaSuccess &&
+          cudaMalloc((void**)&c->s_part, (size_t)mx.batch * kScaleCtas * sizeof(double)) ==
+              cudaSuccess &&
+          cudaMalloc((void**)&c->s_cnt,
+                     (size_t)mx.batch * kScaleCtas * sizeof(unsigned long long)) == cudaSuccess &&
           cudaMalloc((void**)&c->s, mx.batch * sizeof(float)) == cudaSuccess &&
           cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
     if (!okm) {
@@ -350,21 +520,18 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
         return HP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cells = (size_t)s.ny * s.nx;
-    cnn_scale_kernel<<<s.batch, 1024, 0, st>>>(div, flags, c->s, cells);
-    hp_status rc = check_launch();
+    hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
     if (rc != HP_OK) return rc;
     int l = 0;
     const float* prev = nullptr;
     for (int k = 0; k < 3; ++k) {
         const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
         const int H = s.ny / scale, W = s.nx / scale;
-        const long P = (long)s.batch * H * W;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
         int cur = 0;
-        const int blocks = (int)((P + 255) / 256 < 8L * c->num_sms ? (P + 255) / 256 : 8L * c->num_sms);
-        conv_first_kernel<<<blocks, 256, 0, st>>>(in, kSpec[l].cin, (const float*)c->w[l],
-                                                  c->bias[l], c->act[cur], s.batch, nullptr);
-        if ((rc = check_launch()) != HP_OK) return rc;
+        rc = launch_first(c, in, kSpec[l].cin, c->xin, (const float*)c->w[l], c->bias[l],
+                          c->act[cur], s.batch, H, W, st);
+        if (rc != HP_OK) return rc;
         ++l;
         while (kSpec[l].cout != 1) {
             rc = launch_conv3x3_tc(c->act[cur], c->w[l], c->bias[l], c->act[cur ^ 1], s.batch, H,
@@ -375,9 +542,8 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
             ++l;
         }
         float* o = (k == 2 && phi_hat) ? phi_hat : c->out[k];
-        conv_last_kernel<<<blocks, 256, 0, st>>>(c->act[cur], (const float*)c->w[l], c->bias[l],
-                                                 o, s.batch, H, W);
-        if ((rc = check_launch()) != HP_OK) return rc;
+        rc = launch_last(c, c->act[cur], (const float*)c->w[l], c->bias[l], o, s.batch, H, W, st);
+        if (rc != HP_OK) return rc;
         ++l;
         prev = o;
     }
@@ -872,20 +1038,16 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
 {
     hp_cnn* c = t->cnn;
     const size_t cells = (size_t)s.ny * s.nx;
-    cnn_scale_kernel<<<s.batch, 1024, 0, st>>>(div, flags, c->s, cells);
-    hp_status rc = check_launch();
+    hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
     if (rc != HP_OK) return rc;
     const float* prev = nullptr;
     for (int k = 0, l = 0; k < 3; ++k) {
         const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
         const int H = s.ny / scale, W = s.nx / scale;
-        const long P = (long)s.batch * H * W;
-        const int blocks = (int)((P + 255) / 256 < 8L * c->num_sms ? (P + 255) / 256 : 8L * c->num_sms);
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
-        conv_first_kernel<<<blocks, 256, 0, st>>>(in, kSpec[l].cin, (const float*)c->w[l],
-                                                  c->bias[l], (__nv_bfloat16*)t->act[l], s.batch,
-                                                  t->xin[k]);
-        if ((rc = check_launch()) != HP_OK) return rc;
+        rc = launch_first(c, in, kSpec[l].cin, t->xin[k], (const float*)c->w[l], c->bias[l],
+                          (__nv_bfloat16*)t->act[l], s.batch, H, W, st);
+        if (rc != HP_OK) return rc;
         ++l;
         while (kSpec[l].cout != 1) {
             rc = launch_conv3x3_tc(t->act[l - 1], c->w[l], c->bias[l], t->act[l], s.batch, H, W,
@@ -894,10 +1056,9 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
             if (rc != HP_OK) return rc;
             ++l;
         }
-        conv_last_kernel<<<blocks, 256, 0, st>>>((const __nv_bfloat16*)t->act[l - 1],
-                                                 (const float*)c->w[l], c->bias[l],
-                                                 (float*)t->act[l], s.batch, H, W);
-        if ((rc = check_launch()) != HP_OK) return rc;
+        rc = launch_last(c, (const __nv_bfloat16*)t->act[l - 1], (const float*)c->w[l],
+                         c->bias[l], (float*)t->act[l], s.batch, H, W, st);
+        if (rc != HP_OK) return rc;
         prev = (const float*)t->act[l];
         ++l;
     }

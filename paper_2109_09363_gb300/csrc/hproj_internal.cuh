@@ -78,6 +78,8 @@ struct hp_ctx {
     size_t partial2_len;
     hp::GridState* gs;
     hp::LoopState* ls;
+    float* ckpt;         // [max_cells] checkpoint buffer of the resident sweep kernel
+    int res_clusters[17];  // per cluster size: 0 unknown, else 1 + clusters that fit
     int32_t* host_flag;  // pinned
     // cached conditional-graph loop
     cudaGraphExec_t graph_exec;
@@ -92,7 +94,76 @@ struct hp_ctx {
 
 namespace hp {
 
+// ------------------------------------------------------------ cell update
+
+// Per-cell constants derived from the open-face bits m:
+//   inv = 1/n (0 when n = 0), c = 4 - n, w = (n > 0).
+struct CellConst {
+    float d, inv, c, w;
+};
+
+__device__ __forceinline__ CellConst make_const(float d, uint32_t m)
+{
+    const int n = __popc(m & 15u);
+    CellConst k;
+    k.d = d;
+    k.inv = n == 4 ? 0.25f : n == 3 ? (1.0f / 3.0f) : n == 2 ? 0.5f : n == 1 ? 1.0f : 0.0f;
+    k.c = (float)(4 - n);
+    k.w = n > 0 ? 1.0f : 0.0f;
+    return k;
+}
+
+// One Jacobi update of one cell; returns phi' and writes the residual of phi.
+// Every operation is an explicitly rounded intrinsic so that all kernels that
+// use it produce bit-identical iterates.
+__device__ __forceinline__ float cell_update(float pc, float pw, float pe, float pn, float ps,
+                                             const CellConst& k, float& res)
+{
+    const float dw = __fsub_rn(pw, pc);
+    const float de = __fsub_rn(pe, pc);
+    const float dn = __fsub_rn(pn, pc);
+    const float ds = __fsub_rn(ps, pc);
+    const float lapd = __fadd_rn(__fadd_rn(dw, de), __fadd_rn(dn, ds));
+    const float lap = __fmaf_rn(k.c, pc, lapd);
+    const float r = __fmaf_rn(-k.w, lap, k.d);
+    res = r;
+    return __fmaf_rn(-r, k.inv, pc);
+}
+
+// Loads four consecutive cells of a row (float), zero outside [0, nx).
+__device__ __forceinline__ void load_row4(const float* __restrict__ row, int x0, int nx, bool vec,
+                                          float out[4])
+{
+    if (vec && x0 >= 0 && x0 + 3 < nx) {
+        const float4 t = *reinterpret_cast<const float4*>(row + x0);
+        out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int x = x0 + q;
+            out[q] = (x >= 0 && x < nx) ? row[x] : 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t load_mask4(const uint8_t* __restrict__ row, int x0, int nx,
+                                               bool vec)
+{
+    if (vec && x0 >= 0 && x0 + 3 < nx) return *reinterpret_cast<const uint32_t*>(row + x0);
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int x = x0 + q;
+        if (x >= 0 && x < nx) m |= (uint32_t)row[x] << (8 * q);
+    }
+    return m;
+}
+
 void set_cuda_error(cudaError_t e);
+int resident_tiles(hp_shape s);
+int resident_capacity(hp_ctx* ctx, hp_shape s);
+hp_status launch_resident(hp_ctx* ctx, hp_shape s, double threshold, int max_iters,
+                          double* e_hist, int hist_len, cudaStream_t st, bool* launched);
 hp_status check_launch();
 bool shape_ok(hp_shape s);
 

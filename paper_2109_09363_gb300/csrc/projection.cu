@@ -24,42 +24,6 @@
 
 namespace hp {
 
-// ------------------------------------------------------------ cell update
-
-// Per-cell constants derived from the open-face bits m:
-//   inv = 1/n (0 when n = 0), c = 4 - n, w = (n > 0).
-struct CellConst {
-    float d, inv, c, w;
-};
-
-__device__ __forceinline__ CellConst make_const(float d, uint32_t m)
-{
-    const int n = __popc(m & 15u);
-    CellConst k;
-    k.d = d;
-    k.inv = n == 4 ? 0.25f : n == 3 ? (1.0f / 3.0f) : n == 2 ? 0.5f : n == 1 ? 1.0f : 0.0f;
-    k.c = (float)(4 - n);
-    k.w = n > 0 ? 1.0f : 0.0f;
-    return k;
-}
-
-// One Jacobi update of one cell; returns phi' and writes the residual of phi.
-// Every operation is an explicitly rounded intrinsic so that all kernels that
-// use it produce bit-identical iterates.
-__device__ __forceinline__ float cell_update(float pc, float pw, float pe, float pn, float ps,
-                                             const CellConst& k, float& res)
-{
-    const float dw = __fsub_rn(pw, pc);
-    const float de = __fsub_rn(pe, pc);
-    const float dn = __fsub_rn(pn, pc);
-    const float ds = __fsub_rn(ps, pc);
-    const float lapd = __fadd_rn(__fadd_rn(dw, de), __fadd_rn(dn, ds));
-    const float lap = __fmaf_rn(k.c, pc, lapd);
-    const float r = __fmaf_rn(-k.w, lap, k.d);
-    res = r;
-    return __fmaf_rn(-r, k.inv, pc);
-}
-
 // --------------------------------------------------------- mask + divergence
 
 // One thread per cell.  mask (optional) receives the open-face bits, div
@@ -148,35 +112,6 @@ int ctas_per_grid(int ny, int nx, int T)
 {
     const int H = halo_for(T);
     return ctas_x(nx, H) * ctas_y(ny, H);
-}
-
-// Loads four consecutive cells of a row (float), zero outside [0, nx).
-__device__ __forceinline__ void load_row4(const float* __restrict__ row, int x0, int nx, bool vec,
-                                          float out[4])
-{
-    if (vec && x0 >= 0 && x0 + 3 < nx) {
-        const float4 t = *reinterpret_cast<const float4*>(row + x0);
-        out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int x = x0 + q;
-            out[q] = (x >= 0 && x < nx) ? row[x] : 0.0f;
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t load_mask4(const uint8_t* __restrict__ row, int x0, int nx,
-                                               bool vec)
-{
-    if (vec && x0 >= 0 && x0 + 3 < nx) return *reinterpret_cast<const uint32_t*>(row + x0);
-    uint32_t m = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int x = x0 + q;
-        if (x >= 0 && x < nx) m |= (uint32_t)row[x] << (8 * q);
-    }
-    return m;
 }
 
 // Called by the last CTA of grid b after all its CTAs wrote their per-sweep
@@ -938,9 +873,20 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     // streaming one at 16 x 512^2 and above)
     const bool stream = prm->sweep_kernel == 1;
     const int R = prm->sweep_kernel == 3 ? 2 : 4;
-    rc = run_sweep_loop(ctx, s, pick_T(prm), R, stream, thr, cap, e_hist, hist_len,
-                        prm->use_graph != 0, st);
-    if (rc != HP_OK) return rc;
+    bool resident = false;
+    if (prm->sweep_kernel == 4) {
+        // whole grid on chip, one cluster per grid; the blocked loop when a
+        // cluster of that size does not fit
+        reset_state_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(ctx->gs, ctx->ls, s.batch);
+        if ((rc = check_launch()) != HP_OK) return rc;
+        rc = launch_resident(ctx, s, thr, cap, e_hist, hist_len, st, &resident);
+        if (rc != HP_OK) return rc;
+    }
+    if (!resident) {
+        rc = run_sweep_loop(ctx, s, pick_T(prm), R, stream, thr, cap, e_hist, hist_len,
+                            prm->use_graph != 0, st);
+        if (rc != HP_OK) return rc;
+    }
 
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
     const float scale = prm->rho0 / prm->dt;

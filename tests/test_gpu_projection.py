@@ -191,7 +191,7 @@ def test_sweep_kernel_block_size_and_loop_mode_do_not_change_results(dev):
             assert np.array_equal(g[k], base[k]), (kern, T, graph, k)
 
 
-@pytest.mark.parametrize("kern", [1, 2, 3])
+@pytest.mark.parametrize("kern", [1, 2, 3, 4])
 def test_both_sweep_kernels_match_oracle(dev, kern):
     u, v, fl = vortex(3, 67, 130, seed=12)
     g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=2000,
@@ -199,7 +199,7 @@ def test_both_sweep_kernels_match_oracle(dev, kern):
     check_projection(g, u, v, fl, 1e-3, 2000)
 
 
-@pytest.mark.parametrize("kern", [1, 2, 3])
+@pytest.mark.parametrize("kern", [1, 2, 3, 4])
 def test_history_matches_oracle(dev, kern):
     u, v, fl = vortex(2, 64, 96, seed=9)
     thr, cap = 1e-3, 400
@@ -212,30 +212,32 @@ def test_history_matches_oracle(dev, kern):
         assert np.allclose(g["e_hist"][b, :k + 1], ref["e_hist"][b, :k + 1], rtol=2e-5)
 
 
-def test_edge_cases(dev):
+@pytest.mark.parametrize("kern", [2, 4])
+def test_edge_cases(dev, kern):
+    P = lambda *a, **k: hp.ProjectParams(*a, sweep_kernel=kern, **k)
     u, v, fl = vortex(3, 40, 56, seed=2)
     # threshold above E_0: zero sweeps, u is only zeroed on closed faces
-    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e9, max_iters=100))
+    g = run_gpu(dev, u, v, fl, P(threshold=1e9, max_iters=100))
     assert np.all(g["iters"] == 0) and np.all(g["converged"] == 1)
     uz, vz = oracle.zero_closed_faces(u.astype(np.float64), v.astype(np.float64), fl)
     assert np.array_equal(g["u"], f32(uz)) and np.array_equal(g["v"], f32(vz))
     assert np.all(g["p"] == 0)
     # cap 0 with an unreachable threshold
-    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=0.0, max_iters=0))
+    g = run_gpu(dev, u, v, fl, P(threshold=0.0, max_iters=0))
     assert np.all(g["iters"] == 0) and np.all(g["converged"] == 0)
     # cap reached
-    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=0.0, max_iters=37))
+    g = run_gpu(dev, u, v, fl, P(threshold=0.0, max_iters=37))
     assert np.all(g["iters"] == 37) and np.all(g["converged"] == 0)
     check_projection(g, u, v, fl, 0.0, 37)
     # fixed count
-    g = run_gpu(dev, u, v, fl, hp.ProjectParams(fixed_iters=13))
+    g = run_gpu(dev, u, v, fl, P(fixed_iters=13))
     assert np.all(g["iters"] == 13) and np.all(g["converged"] == 1)
     # all-solid grid and a single-cell grid
     fs = np.ones((1, 16, 16), np.uint8)
-    g = run_gpu(dev, u[:1, :16, :17], v[:1, :17, :16], fs, hp.ProjectParams(1e-3, 50))
+    g = run_gpu(dev, u[:1, :16, :17], v[:1, :17, :16], fs, P(1e-3, 50))
     assert g["iters"][0] == 0 and np.all(g["u"] == 0) and np.all(g["v"] == 0)
     g = run_gpu(dev, f32(np.ones((1, 1, 2))), f32(np.ones((1, 2, 1))), np.zeros((1, 1, 1), np.uint8),
-                hp.ProjectParams(1e-3, 50))
+                P(1e-3, 50))
     assert g["iters"][0] == 0 and np.all(g["u"] == 0)
 
 
@@ -281,13 +283,18 @@ def test_full_size_vortex_benchmark_sampled(dev):
     assert np.all(g["iters"] > 0)
     g2 = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap, sweep_kernel=2))
     assert np.array_equal(g2["u"], g["u"]) and np.array_equal(g2["iters"], g["iters"])
+    # the grid-resident kernel (one 16-CTA cluster per grid): same stops here,
+    # then the same iterates bit for bit
+    g4 = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap, sweep_kernel=4))
+    assert np.array_equal(g4["iters"], g["iters"])
+    assert np.array_equal(g4["u"], g["u"]) and np.array_equal(g4["p"], g["p"])
     oracle.set_threads(0)
     sample = [0, 5, 10, 15]
     sub = {k: g[k][sample] for k in ["u", "v", "p", "iters", "converged", "e1"]}
     check_projection(sub, u[sample], v[sample], fl[sample], thr, cap)
 
 
-@pytest.mark.parametrize("kern", [1, 2])
+@pytest.mark.parametrize("kern", [1, 2, 4])
 def test_nonfinite_input_stops_only_that_grid(dev, kern):
     u, v, fl = vortex(3, 48, 64, seed=21)
     good = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=900,
@@ -302,3 +309,35 @@ def test_nonfinite_input_stops_only_that_grid(dev, kern):
     for b in (0, 2):
         assert g["iters"][b] == good["iters"][b]
         assert np.array_equal(g["u"][b], good["u"][b])
+
+
+@pytest.mark.parametrize("shape", [(5, 128, 128), (3, 67, 130), (2, 129, 257), (2, 300, 260),
+                                   (1, 512, 512), (4, 1, 1), (2, 9, 500)])
+def test_resident_kernel_matches_blocked_kernel(dev, shape):
+    """sweep_kernel = 4 keeps each grid on chip in one cluster (1, 2, 6, 9
+    and 16 CTAs here) and replays from a checkpoint to the exact stop: the
+    iterates equal the blocked kernel's bit for bit; stops agree except at a
+    near tie of E (the kernels group the partial sums differently)."""
+    B, ny, nx = shape
+    assert hp.hp_resident_clusters(hp.Context(B, ny, nx), B, ny, nx) > 0
+    u, v, fl = vortex(B, ny, nx, seed=ny + nx)
+    for thr, cap, fixed in [(1e-3, 1500, 0), (0.0, 45, 0), (0.0, 0, 31), (0.0, 0, 16)]:
+        prm = dict(threshold=thr, max_iters=cap, fixed_iters=fixed)
+        a = run_gpu(dev, u, v, fl, hp.ProjectParams(sweep_kernel=2, **prm), hist_len=cap + 2)
+        b = run_gpu(dev, u, v, fl, hp.ProjectParams(sweep_kernel=4, **prm), hist_len=cap + 2)
+        assert np.array_equal(a["converged"], b["converged"])
+        for i in range(B):
+            if a["iters"][i] == b["iters"][i]:
+                for k in ("u", "v", "p"):
+                    assert np.array_equal(a[k][i], b[k][i]), (shape, thr, cap, fixed, i, k)
+                kk = int(a["iters"][i])
+                # FP32 per-thread partial sums over 16 vs 32 cells: E agrees to
+                # a few FP32 roundings
+                assert np.allclose(a["e_hist"][i, :kk + 1], b["e_hist"][i, :kk + 1],
+                                   rtol=1e-6, atol=0)
+            else:
+                lo, hi = sorted((int(a["iters"][i]), int(b["iters"][i])))
+                eh = a["e_hist"][i, lo:hi + 1]
+                assert np.all(np.abs(eh - thr) / thr <= 1e-6), (shape, i, lo, hi)
+    g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=1500, sweep_kernel=4))
+    check_projection(g, u, v, fl, 1e-3, 1500)
