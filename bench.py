@@ -42,6 +42,7 @@ TRAIN_SWEEPS = 40000
 IN_DIST_GRIDS, IN_DIST_SEED = 256, 100000
 T_BLOCK = 8
 BYTES_PER_CELL_SWEEP = 13  # read phi 4, div 4, mask 1; write phi 4
+OPS_PER_CELL_UPDATE = 11   # FP32 operations of one masked Jacobi cell update
 WORKLOAD = ("16 x 512^2 MAC grids, 32 Gaussian vortices + 1-6 obstacles each, plain Jacobi "
             "to mean|div| <= 1e-4 (cap 5000), FP32 sweeps, FP64 stop test")
 
@@ -463,7 +464,8 @@ def main():
                     help="sweeps per launch of the temporally blocked kernel (1..8)")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="0 = library choice, 1 = streaming, 2 = temporally blocked "
-                         "(4 rows per thread), 3 = temporally blocked (2 rows per thread)")
+                         "(4 rows per thread), 3 = temporally blocked (2 rows per thread), "
+                         "4 = grid-resident")
     ap.add_argument("--profile-conv", nargs=5, type=int,
                     metavar=("BATCH", "H", "W", "CIN", "COUT"),
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
@@ -512,7 +514,10 @@ def main():
     prm = hp.ProjectParams(threshold=THR, max_iters=CAP, temporal_block=T_BLOCK,
                            use_graph=0 if args.host_loop else 1,
                            sweep_kernel=args.sweep_kernel)
-    streaming = streaming_chosen(args.sweep_kernel, B * N * N)
+    # the grid-resident kernel runs when the library picks it (0) or it is
+    # asked for (4) and one cluster per grid fits on this device
+    resident = args.sweep_kernel in (0, 4) and hp.hp_resident_clusters(ctx, B, N, N) > 0
+    streaming = not resident and streaming_chosen(args.sweep_kernel, B * N * N)
     per_launch = 1 if streaming else T_BLOCK
     stream = torch.cuda.current_stream()
     out = None
@@ -528,7 +533,10 @@ def main():
         step()
     torch.cuda.synchronize()
     iters = out["iters"].cpu().numpy()
-    if streaming:
+    if resident:
+        # mask/div, init, reset, the resident sweep loop, correction, norms (2)
+        launches_per_step = 7
+    elif streaming:
         # 8 sweep launches per graph-loop iteration, plus mask/div, init,
         # reset, correction, norms, finish
         launches_per_step = 6 + 8 * ((int(iters.max()) + 1 + 7) // 8)
@@ -557,9 +565,9 @@ def main():
         ms = max_over_ranks(ms, dev)
     value = ws * B / (ms * 1e-3)
 
-    # dominant kernel: the temporally blocked sweep, per-launch duration from
-    # the difference of two fixed-length sweep runs (same shape, same T, all
-    # 16 grids active), CUDA events on the launching stream
+    # dominant kernel: the sweep kernel; its time per sweep of the batch from
+    # the difference of two fixed-length sweep runs (same shape, all 16 grids
+    # active), CUDA events on the launching stream
     n1, n2 = 8 * 20, 8 * 220
     fprm = [hp.ProjectParams(fixed_iters=n, temporal_block=T_BLOCK, use_graph=1,
                              sweep_kernel=args.sweep_kernel) for n in (n1, n2)]
@@ -580,6 +588,7 @@ def main():
         torch.cuda.synchronize()
         tl.append(a.elapsed_time(b_))
     t_launch_ms = (tl[1] - tl[0]) / ((n2 - n1) / per_launch)
+    t_sweep_ms = (tl[1] - tl[0]) / (n2 - n1)
     cells = B * N * N
     alg_bytes = BYTES_PER_CELL_SWEEP * cells * per_launch
     peak, peak_kind = load_peaks()
@@ -588,9 +597,47 @@ def main():
     # workload (committed summary); null when the kernel changed since
     traffic = None
     tp = os.path.join(ROOT, "profiles", "dram_traffic_16x512.json")
-    kname = "sweep1_kernel" if streaming else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>"
+    kname = ("sweep_resident_kernel" if resident else "sweep1_kernel" if streaming
+             else f"sweep_tb_kernel<{8 if T_BLOCK > 4 else 4}>")
     if os.path.exists(tp):
         traffic = json.load(open(tp)).get(kname)
+    if resident:
+        # on-chip for all sweeps: bound by FP32 issue, not by HBM.  11 FP32
+        # operations per cell update (4 neighbour differences, 3 adds, the
+        # closed-face, residual and update FMAs, the |r| add) against the
+        # FP32 lane rate (SMs x 128 lanes x maximum SM clock)
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        max_mhz = clk.get("sm_max_mhz") or 2070.0
+        alu_peak = sm_count * 128 * max_mhz * 1e6 / 1e12
+        alu_achieved = OPS_PER_CELL_UPDATE * cells / (t_sweep_ms * 1e-3) / 1e12
+        hbm_eff = BYTES_PER_CELL_SWEEP * cells / (t_sweep_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": kname, "achieved": alu_achieved,
+                    "peak": alu_peak, "unit": "TOP/s", "frac": alu_achieved / alu_peak,
+                    "traffic": traffic, "peak_kind": "derived: SMs x 128 FP32 lanes x max clock",
+                    "ops_per_cell_update": OPS_PER_CELL_UPDATE, "sweep_ms_batch": t_sweep_ms,
+                    "clusters_resident": hp.hp_resident_clusters(ctx, B, N, N),
+                    "hbm_effective": {"achieved": hbm_eff, "peak": peak, "unit": "GB/s",
+                                      "frac": hbm_eff / peak, "peak_kind": peak_kind,
+                                      "note": "13 B per cell-sweep of a sweep that streams "
+                                              "from HBM; the resident kernel reads the grid "
+                                              "once per projection"},
+                    "note": "one cluster of 16 CTAs per 512^2 grid keeps phi on chip for all "
+                            "sweeps; per-sweep time of the 16-grid batch from two fixed-length "
+                            "runs"}
+    else:
+        roofline = {"bound": "hbm",
+                    "kernel": kname,
+                    "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "launch_ms": t_launch_ms,
+                    "note": ("13 B per cell-sweep x 4.19 M cells, one sweep per launch; "
+                             "the 54.5 MB working set is L2-resident between launches"
+                             if streaming else
+                             "13 B per cell-sweep x 4.19 M cells x 8 sweeps per launch; "
+                             "temporal blocking keeps 8 sweeps on chip, so frac is an "
+                             "effective HBM fraction")}
 
     # end to end through the public API with host buffers: H2D of u*, v*, flags
     # from pinned memory, projection, D2H of u, v, p, iterations
@@ -630,24 +677,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "method": "plain Jacobi", "grids_per_gpu": B,
                        "grid": [N, N], "threshold": THR, "cap": CAP,
-                       "sweep_kernel": "streaming" if streaming else "temporally blocked",
-                       "temporal_block": None if streaming else T_BLOCK,
-                       "loop": "host-polled" if args.host_loop else "CUDA-graph conditional while",
+                       "sweep_kernel": ("grid-resident (one cluster per grid)" if resident
+                                        else "streaming" if streaming else "temporally blocked"),
+                       "temporal_block": None if (streaming or resident) else T_BLOCK,
+                       "loop": ("one launch per projection" if resident else "host-polled"
+                                if args.host_loop else "CUDA-graph conditional while"),
                        "l2": "flushed between steps (256 MB write, untimed)",
                        "iters_per_grid": iters.tolist()},
-            "roofline": {"bound": "hbm",
-                         "kernel": kname,
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "launch_ms": t_launch_ms,
-                         "note": ("13 B per cell-sweep x 4.19 M cells, one sweep per launch; "
-                                  "the 54.5 MB working set is L2-resident between launches"
-                                  if streaming else
-                                  "13 B per cell-sweep x 4.19 M cells x 8 sweeps per launch; "
-                                  "temporal blocking keeps 8 sweeps on chip, so frac is an "
-                                  "effective HBM fraction")},
+            "roofline": roofline,
             "e2e": {"value": ws * B / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,

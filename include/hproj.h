@@ -64,8 +64,9 @@ typedef struct {
  *                  (0 = library default)
  *   use_graph      1 = run the sweep loop as a CUDA-graph conditional WHILE node
  *                  (no host round trip per block); 0 = host-polled loop
- *   sweep_kernel   0 = library choice, 1 = streaming (one sweep per launch,
- *                  stop decided one launch later), 2 = temporally blocked (T
+ *   sweep_kernel   0 = library choice (4 where it runs, else 2), 1 = streaming
+ *                  (one sweep per launch, stop decided one launch later),
+ *                  2 = temporally blocked (T
  *                  sweeps per launch, replay to the exact stop; 4 rows per
  *                  thread), 3 = temporally blocked with 2 rows per thread
  *                  (twice the warps), 4 = grid-resident: one thread-block

@@ -3,8 +3,8 @@
 //
 // One thread-block cluster holds one whole grid on chip for all of its sweeps:
 // each CTA owns a 128 x 128 tile (16 warps; thread (w, l) holds rows 8w..8w+7,
-// columns 4l..4l+3), phi and div live in registers, 1/n and 4 - n in shared
-// memory, the open-face flag n > 0 as a bit mask.  A cluster has up to 16 CTAs
+// columns 4l..4l+3), phi lives in registers, div, 1/n and 4 - n (as BF16,
+// exact for 0..4) in shared memory, the open-face flag n > 0 as a bit mask.  A cluster has up to 16 CTAs
 // (a 512 x 512 grid), a grid of at most 128 x 128 runs as a single CTA.  Per
 // sweep k:
 //   1. every warp publishes its top and bottom rows of phi_k in shared memory;
@@ -44,7 +44,7 @@ constexpr int kResWarps = 16;
 constexpr int kResRows = 8;  // rows per thread
 constexpr int kResThreads = kResWarps * 32;
 constexpr int kResTile = 128;  // tile side per CTA
-constexpr int kCkptEvery = 16;
+constexpr int kCkptEvery = 32;  // > kResLag: the two latest checkpoints cover k*
 // E book-keeping in rounds of kBatch sweeps (every kBatch-th sweep, 8 lanes
 // of warp 0 per sweep); the stop decision of sweep j is read at sweep j + kResLag
 constexpr int kBatch = 4;
@@ -56,8 +56,9 @@ constexpr int kResMaxCluster = 16;
 
 // dynamic shared memory (bytes)
 constexpr int kOffInv = 0;                                            // [128][128] float
-constexpr int kOffC = kOffInv + kResTile * kResTile * 4;              // [128][128] float
-constexpr int kOffXch = kOffC + kResTile * kResTile * 4;              // [2][2][16][32] float4
+constexpr int kOffD = kOffInv + kResTile * kResTile * 4;              // [128][128] float
+constexpr int kOffC = kOffD + kResTile * kResTile * 4;                // [128][128] bf16 (exact)
+constexpr int kOffXch = kOffC + kResTile * kResTile * 2;              // [2][2][16][32] float4
 constexpr int kOffHRow = kOffXch + 2 * 2 * kResWarps * 32 * 16;       // [2][2][32] float4
 constexpr int kOffHCol = kOffHRow + 2 * 2 * 32 * 16;                  // [2][2][16][8] float
 constexpr int kOffWsum = kOffHCol + 2 * 2 * kResWarps * kResRows * 4; // [8][16] float
@@ -194,10 +195,10 @@ __device__ __forceinline__ void res_publish(const ResGeom& g, const float (&phi)
 // of the first four rows.
 template <bool WITH_E, bool BOOK>
 __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResRows][4],
-                                            const float (&d)[kResRows][4], uint32_t wbits, int p,
-                                            const float4* s_xch, const float4* s_hrow,
-                                            const float* s_hcol, const float4* s_inv4,
-                                            const float4* s_c4, double& t0, double& t1)
+                                            uint32_t wbits, int p, const float4* s_xch,
+                                            const float4* s_hrow, const float* s_hcol,
+                                            const float4* s_inv4, const float4* s_d4,
+                                            const uint2* s_c2, double& t0, double& t1)
 {
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 nb = g.wid > 0 ? s_xch[((p * 2 + 1) * kResWarps + g.wid - 1) * 32 + g.lane]
@@ -218,10 +219,14 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
         float right = __shfl_down_sync(0xffffffffu, phi[r][0], 1);
         if (g.lane == 0) left = g.left ? hl[r] : 0.0f;
         if (g.lane == 31) right = g.right ? hr[r] : 0.0f;
-        const float4 iv = s_inv4[(g.wid * kResRows + r) * 32 + g.lane];
-        const float4 cv = s_c4[(g.wid * kResRows + r) * 32 + g.lane];
+        const int slot = (g.wid * kResRows + r) * 32 + g.lane;
+        const float4 iv = s_inv4[slot];
+        const float4 dv = s_d4[slot];
+        const uint2 cb = s_c2[slot];
         const float inv[4] = {iv.x, iv.y, iv.z, iv.w};
-        const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+        const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
+        const float cc[4] = {__uint_as_float(cb.x << 16), __uint_as_float(cb.x & 0xffff0000u),
+                             __uint_as_float(cb.y << 16), __uint_as_float(cb.y & 0xffff0000u)};
         float nw[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -229,7 +234,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             const float pe = q < 3 ? phi[r][q + 1] : right;
             const float ps = r < kResRows - 1 ? phi[r + 1][q] : south[q];
             CellConst kc;
-            kc.d = d[r][q];
+            kc.d = dd[q];
             kc.inv = inv[q];
             kc.c = cc[q];
             kc.w = (wbits >> (4 * r + q)) & 1u ? 1.0f : 0.0f;
@@ -261,7 +266,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
 {
     extern __shared__ __align__(16) uint8_t sm[];
     float4* s_inv4 = reinterpret_cast<float4*>(sm + kOffInv);
-    float4* s_c4 = reinterpret_cast<float4*>(sm + kOffC);
+    float4* s_d4 = reinterpret_cast<float4*>(sm + kOffD);
+    uint2* s_c2 = reinterpret_cast<uint2*>(sm + kOffC);
     float4* s_xch = reinterpret_cast<float4*>(sm + kOffXch);
     float4* s_hrow = reinterpret_cast<float4*>(sm + kOffHRow);
     float* s_hcol = reinterpret_cast<float*>(sm + kOffHCol);
@@ -288,31 +294,35 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
     const bool vec = (nx & 3) == 0;
 
     // ---- load phi_0, div and the per-cell constants
-    float phi[kResRows][4], d[kResRows][4];
+    float phi[kResRows][4];
     uint32_t wbits = 0;
 #pragma unroll
     for (int r = 0; r < kResRows; ++r) {
         const int y = y0 + r;
         uint32_t m4 = 0;
+        float dr[4];
         if (y < ny) {
             load_row4(a.phi + gbase + (size_t)y * nx, x0, nx, vec, phi[r]);
-            load_row4(a.div + gbase + (size_t)y * nx, x0, nx, vec, d[r]);
+            load_row4(a.div + gbase + (size_t)y * nx, x0, nx, vec, dr);
             m4 = load_mask4(a.mask + gbase + (size_t)y * nx, x0, nx, vec);
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) phi[r][q] = d[r][q] = 0.0f;
+            for (int q = 0; q < 4; ++q) phi[r][q] = dr[q] = 0.0f;
         }
-        float iv[4], cv[4];
+        float iv[4], dv[4];
+        uint32_t cb[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const CellConst k = make_const(d[r][q], (m4 >> (8 * q)) & 0xffu);
-            d[r][q] = k.d;
+            const CellConst k = make_const(dr[q], (m4 >> (8 * q)) & 0xffu);
+            dv[q] = k.d;
             iv[q] = k.inv;
-            cv[q] = k.c;
+            cb[q] = __float_as_uint(k.c) >> 16;  // 0..4: exact in the upper half
             if (k.w != 0.0f) wbits |= 1u << (4 * r + q);
         }
-        s_inv4[(g.wid * kResRows + r) * 32 + g.lane] = make_float4(iv[0], iv[1], iv[2], iv[3]);
-        s_c4[(g.wid * kResRows + r) * 32 + g.lane] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+        const int slot = (g.wid * kResRows + r) * 32 + g.lane;
+        s_inv4[slot] = make_float4(iv[0], iv[1], iv[2], iv[3]);
+        s_d4[slot] = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        s_c2[slot] = make_uint2(cb[0] | (cb[1] << 16), cb[2] | (cb[3] << 16));
     }
     if (threadIdx.x < kDecRing) s_dec[threadIdx.x] = 0;
 
@@ -411,8 +421,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             }
         }
         double t0 = 0.0, t1 = 0.0;
-        const float acc = res_update<true, false>(g, phi, d, wbits, p, s_xch, s_hrow, s_hcol,
-                                                  s_inv4, s_c4, t0, t1);
+        const float acc = res_update<true, false>(g, phi, wbits, p, s_xch, s_hrow, s_hcol,
+                                                  s_inv4, s_d4, s_c2, t0, t1);
         float t = acc;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
@@ -438,8 +448,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
         res_publish<CLUSTER>(g, phi, p, s_xch, s_hrow, s_hcol);
         sweep_barrier<CLUSTER>();
         double t0 = 0.0, t1 = 0.0;
-        res_update<false, false>(g, phi, d, wbits, p, s_xch, s_hrow, s_hcol, s_inv4, s_c4, t0,
-                                 t1);
+        res_update<false, false>(g, phi, wbits, p, s_xch, s_hrow, s_hcol, s_inv4, s_d4, s_c2,
+                                 t0, t1);
     }
     store_cells(a.phi);
     if (threadIdx.x == 0 && g.rank == 0) {
