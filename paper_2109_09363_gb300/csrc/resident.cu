@@ -7,9 +7,10 @@
 // exact for 0..4) in shared memory, the open-face flag n > 0 as a bit mask.  A cluster has up to 16 CTAs
 // (a 512 x 512 grid), a grid of at most 128 x 128 runs as a single CTA.  Per
 // sweep k:
-//   1. every warp publishes its top and bottom rows of phi_k in shared memory;
-//      the edge warps and lanes also store the tile's boundary rows / columns
-//      into the neighbouring CTAs' halo buffers (distributed shared memory);
+//   1. the boundary values of phi_k are out: every warp's top and bottom rows
+//      in shared memory, the tile's boundary rows / columns in the
+//      neighbouring CTAs' halo buffers (distributed shared memory); sweep k-1
+//      stored each of them as soon as it had computed it;
 //   2. one cluster barrier (release / acquire), split in arrive and wait;
 //   3. every kBatch-th sweep, between arrive and wait and on data visible
 //      since the previous barrier, warp 0 runs one round of the E
@@ -193,13 +194,18 @@ __device__ __forceinline__ void res_publish(const ResGeom& g, const float (&phi)
 // thread's FP32 sum of |r(phi_k)| when WITH_E.  With BOOK (warp 0), the two
 // FP64 reduction trees t0, t1 over lanes 0..15 advance one level after each
 // of the first four rows.
-template <bool WITH_E, bool BOOK>
+template <bool CLUSTER, bool WITH_E, bool BOOK>
 __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResRows][4],
-                                            uint32_t wbits, int p, const float4* s_xch,
-                                            const float4* s_hrow, const float* s_hcol,
+                                            uint32_t wbits, int p, float4* s_xch,
+                                            float4* s_hrow, float* s_hcol,
                                             const float4* s_inv4, const float4* s_d4,
                                             const uint2* s_c2, double& t0, double& t1)
 {
+    // boundary values of phi_{k+1} go out (parity p ^ 1) as soon as they are
+    // computed, so that the stores have landed by the next barrier; those
+    // buffers were last read in the previous sweep, before the barrier this
+    // thread has passed
+    const int q1 = p ^ 1;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 nb = g.wid > 0 ? s_xch[((p * 2 + 1) * kResWarps + g.wid - 1) * 32 + g.lane]
                       : g.up    ? s_hrow[(p * 2 + 0) * 32 + g.lane]
@@ -241,6 +247,26 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             float res;
             nw[q] = cell_update(phi[r][q], pw, pe, up[q], ps, kc, res);
             if (WITH_E) acc = __fadd_rn(acc, fabsf(res));
+        }
+        if (r == 0 || r == kResRows - 1) {
+            const float4 v4 = make_float4(nw[0], nw[1], nw[2], nw[3]);
+            s_xch[((q1 * 2 + (r == 0 ? 0 : 1)) * kResWarps + g.wid) * 32 + g.lane] = v4;
+            if (CLUSTER) {
+                if (r == 0 && g.wid == 0 && g.up)
+                    st_cluster(remote(&s_hrow[(q1 * 2 + 1) * 32 + g.lane], g.rank - g.cx), v4);
+                if (r == kResRows - 1 && g.wid == kResWarps - 1 && g.down)
+                    st_cluster(remote(&s_hrow[(q1 * 2 + 0) * 32 + g.lane], g.rank + g.cx), v4);
+            }
+        }
+        if (CLUSTER) {
+            if (g.lane == 0 && g.left)
+                st_cluster(remote(&s_hcol[((q1 * 2 + 1) * kResWarps + g.wid) * kResRows + r],
+                                  g.rank - 1),
+                           nw[0]);
+            if (g.lane == 31 && g.right)
+                st_cluster(remote(&s_hcol[((q1 * 2 + 0) * kResWarps + g.wid) * kResRows + r],
+                                  g.rank + 1),
+                           nw[3]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -347,11 +373,13 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
     bool decided = false;  // thread 0: a stop was decided (no more history writes)
     int kstar = 0, dec = 0;
     double estar = 0.0;
-    // ---- main loop; registers hold phi_k at the top of sweep k
+    // ---- main loop; registers hold phi_k at the top of sweep k, its
+    // boundary values are in the parity-(k & 1) buffers (sweep k - 1 wrote
+    // them during its update; phi_0's go out here)
+    res_publish<CLUSTER>(g, phi, 0, s_xch, s_hrow, s_hcol);
     for (int k = 0;; ++k) {
         const int p = k & 1;
         if (k > 0 && k % kCkptEvery == 0) store_cells(ckpt_buf(a, k / kCkptEvery));
-        res_publish<CLUSTER>(g, phi, p, s_xch, s_hrow, s_hcol);
         sweep_arrive<CLUSTER>();
         if (g.wid == 0 && k % kBatch == 0) {
             // one round, between arrive and wait, on data visible since the
@@ -421,8 +449,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             }
         }
         double t0 = 0.0, t1 = 0.0;
-        const float acc = res_update<true, false>(g, phi, wbits, p, s_xch, s_hrow, s_hcol,
-                                                  s_inv4, s_d4, s_c2, t0, t1);
+        const float acc = res_update<CLUSTER, true, false>(g, phi, wbits, p, s_xch, s_hrow,
+                                                           s_hcol, s_inv4, s_d4, s_c2, t0, t1);
         float t = acc;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
@@ -443,13 +471,15 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             }
         }
     }
+    // nobody reads a halo buffer after the main loop's last barrier, so the
+    // checkpoint's boundary values can go out at once
+    res_publish<CLUSTER>(g, phi, (m * kCkptEvery) & 1, s_xch, s_hrow, s_hcol);
     for (int j = m * kCkptEvery; j < kstar; ++j) {
         const int p = j & 1;
-        res_publish<CLUSTER>(g, phi, p, s_xch, s_hrow, s_hcol);
         sweep_barrier<CLUSTER>();
         double t0 = 0.0, t1 = 0.0;
-        res_update<false, false>(g, phi, wbits, p, s_xch, s_hrow, s_hcol, s_inv4, s_d4, s_c2,
-                                 t0, t1);
+        res_update<CLUSTER, false, false>(g, phi, wbits, p, s_xch, s_hrow, s_hcol, s_inv4, s_d4,
+                                          s_c2, t0, t1);
     }
     store_cells(a.phi);
     if (threadIdx.x == 0 && g.rank == 0) {
