@@ -148,7 +148,8 @@ struct BranchIn {
 
 // Branch input, once per pixel of the branch: xin [P][cin] FP32 holding the
 // BF16-rounded values [pool(div)/s, pool(flags)(, up(coarser output))].
-__global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xin, int B)
+__global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xin,
+                                    __nv_bfloat16* __restrict__ x16, int B)
 {
     const int hs = in.H / in.scale, ws = in.W / in.scale;
     const long P = (long)B * hs * ws;
@@ -159,8 +160,39 @@ __global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xi
         const int j = r / ws, i = r - j * ws;
         float xc[3];
         in.at(b, i, j, xc);
-        for (int c = 0; c < cin; ++c) xin[(size_t)p * cin + c] = xc[c];
+        if (xin)
+            for (int c = 0; c < cin; ++c) xin[(size_t)p * cin + c] = xc[c];
+        if (x16) {
+            // the tensor-core first layer: 16 channels, the inputs then zeros
+            // (the values are BF16-rounded already, so this is exact)
+            __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < cin ? xc[c] : 0.0f);
+            uint4* dst = reinterpret_cast<uint4*>(x16 + (size_t)p * 16);
+            dst[0] = reinterpret_cast<const uint4*>(v)[0];
+            dst[1] = reinterpret_cast<const uint4*>(v)[1];
+        }
     }
+}
+
+// BF16 tensor-core copies of a branch's first and last layer from their
+// CUDA-core (FP32, BF16-rounded) weights: first [tap][cin][32] ->
+// [tap][32][16] with zero channels cin..15; last [tap][32] -> [tap][16][32]
+// with zero output channels 1..15, bias -> 16 floats.
+__global__ void pack_edge_layers_kernel(const float* __restrict__ wf, int cin,
+                                        __nv_bfloat16* __restrict__ wf16,
+                                        const float* __restrict__ wl,
+                                        const float* __restrict__ bl,
+                                        __nv_bfloat16* __restrict__ wl16, float* __restrict__ bl16)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 9 * 32 * 16) {
+        const int c = i % 16, o = (i / 16) % 32, t = i / (16 * 32);
+        wf16[i] = __float2bfloat16_rn(c < cin ? wf[(t * cin + c) * 32 + o] : 0.0f);
+        const int c2 = i % 32, o2 = (i / 32) % 16, t2 = i / (32 * 16);
+        wl16[i] = __float2bfloat16_rn(o2 == 0 ? wl[t2 * 32 + c2] : 0.0f);
+    }
+    if (i < 16) bl16[i] = i == 0 ? bl[0] : 0.0f;
 }
 
 // First convolution of a branch: cin (2 or 3) -> 32, bias, ReLU, BF16 NHWC,
@@ -336,6 +368,11 @@ struct hp_cnn {
     __nv_bfloat16* act[2];
     float* out[3];  // branch outputs at 1/4, 1/2, 1
     float* xin;     // branch input [P][cin] FP32 (largest branch)
+    __nv_bfloat16* x16;  // branch input [P][16] BF16 for the tensor-core first layer
+    // tensor-core copies of the first / last layer of each branch (0: 1/4, 1: 1/2, 2: 1)
+    __nv_bfloat16* wtc_first[3];  // [9][32][16]
+    __nv_bfloat16* wtc_last[3];   // [9][16][32]
+    float* btc_last[3];           // [16]
     float* s;
     double* s_part;                // [B][kScaleCtas] partial sums of |div|
     unsigned long long* s_cnt;     // [B][kScaleCtas] fluid-cell counts
@@ -353,17 +390,26 @@ static hp_status launch_scale(hp_cnn* c, const float* div, const uint8_t* flags,
     return check_launch();
 }
 
-// branch input (pooling / up-sampling) into xin, then the cin -> 32 convolution
-static hp_status launch_first(hp_cnn* c, const BranchIn& in, int cin, float* xin, const float* w,
-                              const float* bias, __nv_bfloat16* y, int B, int H, int W,
-                              cudaStream_t st)
+// branch input (pooling / up-sampling) and the cin -> 32 convolution: on the
+// tensor cores (input padded to 16 BF16 channels) from the width the
+// warp-specialised kernel serves, else on CUDA cores from the FP32 input.
+// xin_keep (may be null) receives the FP32 branch input for the weight
+// gradient of training.
+static hp_status launch_first(hp_cnn* c, int k, const BranchIn& in, int cin, float* xin_keep,
+                              const float* w, const float* bias, __nv_bfloat16* y, int B, int H,
+                              int W, cudaStream_t st)
 {
+    const bool tc = W >= conv_tc_min_width();
+    float* xin = xin_keep ? xin_keep : (tc ? nullptr : c->xin);
     const long P = (long)B * H * W;
     const long cap = 16L * c->num_sms;
     const int blocks = (int)((P + 255) / 256 < cap ? (P + 255) / 256 : cap);
-    branch_input_kernel<<<blocks, 256, 0, st>>>(in, cin, xin, B);
+    branch_input_kernel<<<blocks, 256, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
+    if (tc)
+        return launch_conv3x3_tc(c->x16, c->wtc_first[k], bias, y, B, H, W, 16, 32, 1, c->err,
+                                 c->num_sms, st);
     const long P2 = (long)B * H * ((W + 1) / 2);
     const int blocks2 = (int)((P2 + 127) / 128 < cap ? (P2 + 127) / 128 : cap);
     if (cin == 2)
@@ -375,14 +421,36 @@ static hp_status launch_first(hp_cnn* c, const BranchIn& in, int cin, float* xin
     return check_launch();
 }
 
-static hp_status launch_last(hp_cnn* c, const __nv_bfloat16* x, const float* w, const float* bias,
-                             float* y, int B, int H, int W, cudaStream_t st)
+// the 32 -> 1 convolution: tensor cores from the width the warp-specialised
+// kernel serves, else CUDA cores
+static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const float* w,
+                             const float* bias, float* y, int B, int H, int W, cudaStream_t st)
 {
+    if (W >= conv_tc_min_width())
+        return launch_conv3x3_tc_out1(x, c->wtc_last[k], c->btc_last[k], y, B, H, W, c->err,
+                                      c->num_sms, st);
     const long T = (long)B * ((H + kLastRows - 1) / kLastRows) * W;
     const long cap = 16L * c->num_sms;
     const int blocks = (int)((T + 127) / 128 < cap ? (T + 127) / 128 : cap);
     conv_last_kernel<<<blocks, 128, 0, st>>>(x, w, bias, y, B, H, W);
     return check_launch();
+}
+
+// first and last layer (network order) of branch k, and their tensor-core copies
+static const int kFirstLayer[3] = {0, 5, 12};
+static const int kLastLayer[3] = {4, 11, 18};
+
+static hp_status pack_edge_layers(hp_cnn* c, cudaStream_t st)
+{
+    for (int k = 0; k < 3; ++k) {
+        const int lf = kFirstLayer[k], ll = kLastLayer[k];
+        pack_edge_layers_kernel<<<(9 * 32 * 16 + 255) / 256, 256, 0, st>>>(
+            (const float*)c->w[lf], kSpec[lf].cin, c->wtc_first[k], (const float*)c->w[ll],
+            c->bias[ll], c->wtc_last[k], c->btc_last[k]);
+        hp_status rc = check_launch();
+        if (rc != HP_OK) return rc;
+    }
+    return HP_OK;
 }
 
 static size_t layer_wcount(int l) { return (size_t)9 * kSpec[l].cin * kSpec[l].cout; }
@@ -407,6 +475,12 @@ void hp_cnn_destroy(hp_cnn* c)
     cudaFree(c->act[1]);
     for (int k = 0; k < 3; ++k) cudaFree(c->out[k]);
     cudaFree(c->xin);
+    cudaFree(c->x16);
+    for (int k = 0; k < 3; ++k) {
+        cudaFree(c->wtc_first[k]);
+        cudaFree(c->wtc_last[k]);
+        cudaFree(c->btc_last[k]);
+    }
     cudaFree(c->s_part);
     cudaFree(c->s_cnt);
     cudaFree(c->s);
@@ -444,12 +518,17 @@ hp_status hp_cnn_create(hp_cnn** out, hp_shape mx, int device)
           cudaMalloc((void**)&c->out[1], px / 4 * 4 + 16) == cudaSuccess &&
           cudaMalloc((void**)&c->out[2], px * 4) == cudaSuccess &&
           cudaMalloc((void**)&c->xin, px * 3 * sizeof(float)) == cudaSuccess &&
+          cudaMalloc((void**)&c->x16, px * 16 * 2) == cudaSuccess &&
           cudaMalloc((void**)&c->s_part, (size_t)mx.batch * kScaleCtas * sizeof(double)) ==
               cudaSuccess &&
           cudaMalloc((void**)&c->s_cnt,
                      (size_t)mx.batch * kScaleCtas * sizeof(unsigned long long)) == cudaSuccess &&
           cudaMalloc((void**)&c->s, mx.batch * sizeof(float)) == cudaSuccess &&
           cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
+    for (int k = 0; k < 3 && okm; ++k)
+        okm = cudaMalloc((void**)&c->wtc_first[k], 9 * 32 * 16 * 2) == cudaSuccess &&
+              cudaMalloc((void**)&c->wtc_last[k], 9 * 16 * 32 * 2) == cudaSuccess &&
+              cudaMalloc((void**)&c->btc_last[k], 16 * sizeof(float)) == cudaSuccess;
     if (!okm) {
         set_cuda_error(cudaGetLastError());
         hp_cnn_destroy(c);
@@ -499,6 +578,11 @@ hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
         if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
         p += co;
     }
+    // the tensor-core copies of the first and last layers
+    hp_status rc = pack_edge_layers(c, nullptr);
+    if (rc != HP_OK) return rc;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return HP_OK;
 }
 
@@ -529,7 +613,7 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
         const int H = s.ny / scale, W = s.nx / scale;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
         int cur = 0;
-        rc = launch_first(c, in, kSpec[l].cin, c->xin, (const float*)c->w[l], c->bias[l],
+        rc = launch_first(c, k, in, kSpec[l].cin, nullptr, (const float*)c->w[l], c->bias[l],
                           c->act[cur], s.batch, H, W, st);
         if (rc != HP_OK) return rc;
         ++l;
@@ -542,7 +626,8 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
             ++l;
         }
         float* o = (k == 2 && phi_hat) ? phi_hat : c->out[k];
-        rc = launch_last(c, c->act[cur], (const float*)c->w[l], c->bias[l], o, s.batch, H, W, st);
+        rc = launch_last(c, k, c->act[cur], (const float*)c->w[l], c->bias[l], o, s.batch, H, W,
+                         st);
         if (rc != HP_OK) return rc;
         ++l;
         prev = o;
@@ -1029,7 +1114,9 @@ static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
                                                           kind, t->cnn->w[l], t->cnn->bias[l],
                                                           t->wt[l]);
     }
-    return check_launch();
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+    return pack_edge_layers(t->cnn, st);
 }
 
 // forward keeping every layer output
@@ -1045,7 +1132,7 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
         const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
         const int H = s.ny / scale, W = s.nx / scale;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
-        rc = launch_first(c, in, kSpec[l].cin, t->xin[k], (const float*)c->w[l], c->bias[l],
+        rc = launch_first(c, k, in, kSpec[l].cin, t->xin[k], (const float*)c->w[l], c->bias[l],
                           (__nv_bfloat16*)t->act[l], s.batch, H, W, st);
         if (rc != HP_OK) return rc;
         ++l;
@@ -1056,7 +1143,7 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
             if (rc != HP_OK) return rc;
             ++l;
         }
-        rc = launch_last(c, (const __nv_bfloat16*)t->act[l - 1], (const float*)c->w[l],
+        rc = launch_last(c, k, (const __nv_bfloat16*)t->act[l - 1], (const float*)c->w[l],
                          c->bias[l], (float*)t->act[l], s.batch, H, W, st);
         if (rc != HP_OK) return rc;
         prev = (const float*)t->act[l];

@@ -300,17 +300,22 @@ constexpr int kAccSlots = 8;
 constexpr int kWsThreads = 192;
 constexpr uint32_t kWsSpinLimit = 1u << 22;
 
-template <int CIN, int COUT>
+// OUT1: the layer has one output channel (the last convolution of a
+// branch), computed as channel 0 of COUT = 16 (the other weights are zero)
+// and stored as FP32 [P] without rounding.
+template <int CIN, int COUT, bool OUT1 = false>
 struct WsSmem {
     static constexpr int kChunks = CIN / 8;
     static constexpr int kSlotBytes = kChunks * kHaloPx * 16;
     static constexpr int kRingBytes = kWsSlots * kSlotBytes;
     static constexpr int kBBytes = 9 * kChunks * COUT * 16;
     // per epilogue warp: its 32 output pixels in BF16, 16-byte chunks XOR-swizzled
-    static constexpr int kStageBytes = 4 * 32 * COUT * 2;
+    static constexpr int kStageBytes = OUT1 ? 0 : 4 * 32 * COUT * 2;
     static constexpr int kBytes = kRingBytes + kBBytes + kStageBytes;
-    static constexpr int kTmemCols = kAccSlots * COUT;  // 256 or 512
-    static_assert(COUT == 32 || COUT == 64, "accumulator ring sized for 32 or 64 channels");
+    static constexpr int kTmemCols = kAccSlots * COUT;  // 128, 256 or 512
+    static_assert(COUT == 32 || COUT == 64 || (COUT == 16 && OUT1),
+                  "accumulator ring sized for 32 or 64 channels (16 for one output)");
+    static_assert(CIN % 16 == 0, "K steps of 16 channels");
 };
 
 __device__ __forceinline__ bool mbar_wait_ws(uint32_t mbar, uint32_t parity,
@@ -373,6 +378,38 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r)
         : "memory");
 }
 
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+        "%10, %11, %12, %13, %14, %15, %16};\n" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
+        : "memory");
+}
+
+// One 32-bit TMEM column of this thread's lane, without the wait.
+__device__ __forceinline__ uint32_t tmem_ld1_raw(uint32_t taddr)
+{
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(r) : "r"(taddr));
+    return r;
+}
+
+// An accumulator slot (COUT columns) set to the given 32-bit values.
+template <int COUT>
+__device__ __forceinline__ void tmem_fill(uint32_t taddr, const uint32_t* bits)
+{
+    if (COUT % 32 == 0) {
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 32) tmem_st32(taddr + c0, bits + c0);
+    } else {
+        tmem_st16(taddr, bits);
+    }
+}
+
 // Two FP32 values to packed BF16 (lo in the low half), round to nearest even,
 // optionally with ReLU in the same conversion.
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi, bool relu)
@@ -409,13 +446,14 @@ __device__ __forceinline__ uint32_t idesc_for_rows(int n_out, int cout)
                         : mma_idesc(kTileM, 3 * cout);
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool OUT1>
 __global__ void __launch_bounds__(kWsThreads, 1)
     conv3x3_tc_ws_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
-                         const float* __restrict__ bias, __nv_bfloat16* __restrict__ y, int H,
-                         int W, int segs, int nbands, int band, int items, int relu, int* err)
+                         const float* __restrict__ bias, void* __restrict__ yout, int H, int W,
+                         int segs, int nbands, int band, int items, int relu, int* err)
 {
-    using S = WsSmem<CIN, COUT>;
+    using S = WsSmem<CIN, COUT, OUT1>;
+    __nv_bfloat16* __restrict__ y = reinterpret_cast<__nv_bfloat16*>(yout);
     constexpr int NCH = S::kChunks;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem;
@@ -477,9 +515,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     if (warp < 4) {
 #pragma unroll
         for (int sl = 0; sl < kAccSlots; ++sl)
-#pragma unroll
-            for (int c0 = 0; c0 < COUT; c0 += 32)
-                tmem_st32(tmem + lane_off + (uint32_t)(sl * COUT + c0), bias_bits + c0);
+            tmem_fill<COUT>(tmem + lane_off + (uint32_t)(sl * COUT), bias_bits);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -609,13 +645,27 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t taddr =
                     tmem + lane_off + (uint32_t)(COUT * (kAccSlots - 1 - (int)sl));
+                if constexpr (OUT1) {
+                    // channel 0 only, FP32 (bias included by the slot's fill)
+                    const uint32_t v = tmem_ld1_raw(taddr);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tmem_fill<COUT>(taddr, bias_bits);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&free_bar[sl]));
+                    const int xo = it.x0 + warp * 32 + lane;
+                    if (xo < W)
+                        reinterpret_cast<float*>(yout)[((size_t)it.b * H + yy) * W + xo] =
+                            __uint_as_float(v);
+                    continue;
+                } else {
                 uint32_t acc[COUT];
 #pragma unroll
                 for (int c0 = 0; c0 < COUT; c0 += 32) tmem_ld32_raw(taddr + c0, acc + c0);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 // refill the slot with the bias for the output row that reuses it
-#pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 32) tmem_st32(taddr + c0, bias_bits + c0);
+                tmem_fill<COUT>(taddr, bias_bits);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
@@ -650,6 +700,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                         *reinterpret_cast<uint4*>(row + (size_t)p * COUT + 8 * c) = v;
                 }
                 __syncwarp();
+                }
             }
         }
     }
@@ -666,10 +717,42 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
 }
 
+// warp-specialised row walk, one persistent CTA per SM; bands sized for about
+// eight work items per CTA (an image narrower than 128 pixels is one strip
+// whose pixels past its width are clamped on load and not stored)
+template <int CIN, int COUT, bool OUT1>
+hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, int B, int H,
+                    int W, int relu, int* err, int nsm, cudaStream_t st)
+{
+    using R = WsSmem<CIN, COUT, OUT1>;
+    static bool rattr = false;
+    if (!rattr) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_ws_kernel<CIN, COUT, OUT1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             R::kBytes);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+        rattr = true;
+    }
+    const int segs = (W + kTileM - 1) / kTileM;
+    const long rows = (long)B * H * segs;
+    int band = (int)((rows + 8L * nsm - 1) / (8L * nsm));
+    band = band < 4 ? 4 : band > H ? H : band;
+    const int nbands = (H + band - 1) / band;
+    const long items = (long)B * segs * nbands;
+    if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
+    const int grid = items < nsm ? (int)items : nsm;
+    conv3x3_tc_ws_kernel<CIN, COUT, OUT1><<<grid, kWsThreads, R::kBytes, st>>>(
+        (const uint4*)x, (const uint4*)w, bias, y, H, W, segs, nbands, band, (int)items, relu,
+        err);
+    return check_launch();
+}
+
 template <int CIN, int COUT>
 hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y, int B, int H,
                         int W, int relu, int* err, int nsm, cudaStream_t st)
 {
+    if (W >= kWsMinWidth) return launch_ws<CIN, COUT, false>(x, w, bias, y, B, H, W, relu, err,
+                                                            nsm, st);
     using S = ConvSmem<CIN, COUT>;
     static bool attr = false;
     if (!attr) {
@@ -677,33 +760,6 @@ hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
         if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
         attr = true;
-    }
-    if (W >= kWsMinWidth) {
-        // warp-specialised row walk, one persistent CTA per SM; bands sized
-        // for about eight work items per CTA (an image narrower than 128
-        // pixels is one strip whose pixels past its width are clamped on
-        // load and not stored)
-        using R = WsSmem<CIN, COUT>;
-        static bool rattr = false;
-        if (!rattr) {
-            cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_ws_kernel<CIN, COUT>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 R::kBytes);
-            if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
-            rattr = true;
-        }
-        const int segs = (W + kTileM - 1) / kTileM;
-        const long rows = (long)B * H * segs;
-        int band = (int)((rows + 8L * nsm - 1) / (8L * nsm));
-        band = band < 4 ? 4 : band > H ? H : band;
-        const int nbands = (H + band - 1) / band;
-        const long items = (long)B * segs * nbands;
-        if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
-        const int grid = items < nsm ? (int)items : nsm;
-        conv3x3_tc_ws_kernel<CIN, COUT><<<grid, kWsThreads, R::kBytes, st>>>(
-            (const uint4*)x, (const uint4*)w, bias, (__nv_bfloat16*)y, H, W, segs, nbands, band,
-            (int)items, relu, err);
-        return check_launch();
     }
     const long P = (long)B * H * W;
     const int ntiles = (int)((P + kTileM - 1) / kTileM);
@@ -723,7 +779,24 @@ hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, voi
     if (cin == 32 && cout == 64) return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st);
     if (cin == 64 && cout == 32) return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st);
     if (cin == 64 && cout == 64) return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+    // first layer of a branch, input padded to 16 channels (warp-specialised
+    // kernel only; narrower images take the CUDA-core layer)
+    if (cin == 16 && cout == 32 && W >= kWsMinWidth)
+        return launch_ws<16, 32, false>(x, w, bias, y, B, H, W, relu, err, nsm, st);
     return HP_ERR_UNSUPPORTED;
+}
+
+int conv_tc_min_width() { return kWsMinWidth; }
+
+// Last layer of a branch, 32 -> 1, as channel 0 of a 32 -> 16 convolution
+// (w: BF16 [9][16][32], rows 1..15 zero; bias: 16 floats) written as FP32
+// [B][H][W] without rounding; HP_ERR_UNSUPPORTED below the width the
+// warp-specialised kernel serves.
+hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias, float* y,
+                                 int B, int H, int W, int* err, int nsm, cudaStream_t st)
+{
+    if (W < kWsMinWidth) return HP_ERR_UNSUPPORTED;
+    return launch_ws<32, 16, true>(x, w, bias, y, B, H, W, 0, err, nsm, st);
 }
 
 }  // namespace hp

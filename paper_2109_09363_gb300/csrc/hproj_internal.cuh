@@ -187,6 +187,11 @@ int ctas_per_grid(int ny, int nx, int T);
 hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
                             int H, int W, int cin, int cout, int relu, int* err, int nsm,
                             cudaStream_t st);
+// narrowest image the warp-specialised convolution (and the tensor-core first
+// and last layers of a branch) serves
+int conv_tc_min_width();
+hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias, float* y,
+                                 int B, int H, int W, int* err, int nsm, cudaStream_t st);
 hp_status launch_advect(const float* u, const float* v, const float* rho, const uint8_t* flags,
                         float* u_out, float* v_out, float* rho_out, hp_shape s,
                         const hp_plume_params& p, cudaStream_t st);
