@@ -4,7 +4,7 @@
 // One thread-block cluster holds one whole grid on chip for all of its sweeps:
 // each CTA owns a 128 x 128 tile (16 warps; thread (w, l) holds rows 8w..8w+7,
 // columns 4l..4l+3), phi lives in registers, div, 1/n and 4 - n (as BF16,
-// exact for 0..4) in shared memory, the open-face flag n > 0 as a bit mask.  A cluster has up to 16 CTAs
+// exact for 0..4) in shared memory; the open-face flag n > 0 follows from 1/n.  A cluster has up to 16 CTAs
 // (a 512 x 512 grid), a grid of at most 128 x 128 runs as a single CTA.  Per
 // sweep k:
 //   1. the boundary values of phi_k are out: every warp's top and bottom rows
@@ -196,7 +196,7 @@ __device__ __forceinline__ void res_publish(const ResGeom& g, const float (&phi)
 // of the first four rows.
 template <bool CLUSTER, bool WITH_E, bool BOOK>
 __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResRows][4],
-                                            uint32_t wbits, int p, float4* s_xch,
+                                            int p, float4* s_xch,
                                             float4* s_hrow, float* s_hcol,
                                             const float4* s_inv4, const float4* s_d4,
                                             const uint2* s_c2, double& t0, double& t1)
@@ -243,7 +243,8 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             kc.d = dd[q];
             kc.inv = inv[q];
             kc.c = cc[q];
-            kc.w = (wbits >> (4 * r + q)) & 1u ? 1.0f : 0.0f;
+            // [n > 0] from 1/n in {0, 1/4, 1/3, 1/2, 1}: saturate(4/n) is exactly 0 or 1
+            kc.w = __saturatef(inv[q] * 4.0f);
             float res;
             nw[q] = cell_update(phi[r][q], pw, pe, up[q], ps, kc, res);
             if (WITH_E) acc = __fadd_rn(acc, fabsf(res));
@@ -321,7 +322,6 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
 
     // ---- load phi_0, div and the per-cell constants
     float phi[kResRows][4];
-    uint32_t wbits = 0;
 #pragma unroll
     for (int r = 0; r < kResRows; ++r) {
         const int y = y0 + r;
@@ -343,7 +343,6 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             dv[q] = k.d;
             iv[q] = k.inv;
             cb[q] = __float_as_uint(k.c) >> 16;  // 0..4: exact in the upper half
-            if (k.w != 0.0f) wbits |= 1u << (4 * r + q);
         }
         const int slot = (g.wid * kResRows + r) * 32 + g.lane;
         s_inv4[slot] = make_float4(iv[0], iv[1], iv[2], iv[3]);
@@ -449,7 +448,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             }
         }
         double t0 = 0.0, t1 = 0.0;
-        const float acc = res_update<CLUSTER, true, false>(g, phi, wbits, p, s_xch, s_hrow,
+        const float acc = res_update<CLUSTER, true, false>(g, phi, p, s_xch, s_hrow,
                                                            s_hcol, s_inv4, s_d4, s_c2, t0, t1);
         float t = acc;
 #pragma unroll
@@ -478,7 +477,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
         const int p = j & 1;
         sweep_barrier<CLUSTER>();
         double t0 = 0.0, t1 = 0.0;
-        res_update<CLUSTER, false, false>(g, phi, wbits, p, s_xch, s_hrow, s_hcol, s_inv4, s_d4,
+        res_update<CLUSTER, false, false>(g, phi, p, s_xch, s_hrow, s_hcol, s_inv4, s_d4,
                                           s_c2, t0, t1);
     }
     store_cells(a.phi);
