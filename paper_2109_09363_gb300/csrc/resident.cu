@@ -4,9 +4,9 @@
 // One thread-block cluster holds one whole grid on chip for all of its sweeps:
 // each CTA owns a 128 x 128 tile (16 warps; thread (w, l) holds rows 8w..8w+7,
 // columns 4l..4l+3), phi lives in registers, div, 1/n and 4 - n (as BF16,
-// exact for 0..4) in shared memory; the open-face flag n > 0 follows from 1/n.  A cluster has up to 16 CTAs
-// (a 512 x 512 grid), a grid of at most 128 x 128 runs as a single CTA.  Per
-// sweep k:
+// exact for 0..4) in shared memory; the open-face flag n > 0 follows from
+// 1/n.  A cluster has up to 16 CTAs (a 512 x 512 grid), a grid of at most
+// 128 x 128 runs as a single CTA.  Per sweep k:
 //   1. the boundary values of phi_k are out: every warp's top and bottom rows
 //      in shared memory, the tile's boundary rows / columns in the
 //      neighbouring CTAs' halo buffers (distributed shared memory); sweep k-1
@@ -27,11 +27,12 @@
 //      warp sums of |r(phi_k)|.
 // Buffers rotate with the sweep parity (halos) or in rings indexed by sweep
 // (warp sums, CTA partials, decisions), sized so that the one barrier per
-// sweep keeps them race-free.  The decision arrives kResLag sweeps late; phi is checkpointed to global
-// memory every kCkptEvery sweeps, and after the stop the cluster reloads the
-// checkpoint at or below k* and replays the sweeps up to k* exactly.  All
-// CTAs of a cluster execute the same number of barriers: the decision is
-// computed from the same values in the same order everywhere.
+// sweep keeps them race-free.  The decision arrives kResLag sweeps late; phi
+// is checkpointed to global memory every kCkptEvery sweeps, and after the
+// stop the cluster reloads the checkpoint at or below k* and replays the
+// sweeps up to k* exactly.  All CTAs of a cluster execute the same number of
+// barriers: the decision is computed from the same values in the same order
+// everywhere.
 #include <cuda_runtime.h>
 #include <math.h>
 
