@@ -1,5 +1,8 @@
-"""FP64 oracle of the training loss of the MultiScale CNN, numpy.
+"""FP64 oracle of the training losses of the MultiScale CNN, numpy.
 TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+1. loss_and_grad: the supervised loss with a divergence term (below).
+2. pdnn_loss_and_grad: the physics-driven loss of Sec. 3.2 (Eq. 4).
 
 Reading (the paper trains on the divergence of the corrected field, Sec. 3.2,
 and this build also supervises on pressures from the plain solver); both terms
@@ -14,6 +17,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from oracle import adjoint as AD
 
 
 def loss_and_grad(phi_hat, target, div, flags, s, lam):
@@ -39,3 +43,52 @@ def loss_and_grad(phi_hat, target, div, flags, s, lam):
         lr = -oracle.residual(r, np.zeros_like(r), flags)[0]
         g += -2.0 * lam / d2 * lr
     return loss, g
+
+
+def forward_divergence(u, v):
+    """Forward-difference divergence of every cell from all of its faces."""
+    return (u[..., :, 1:] - u[..., :, :-1]) + (v[..., 1:, :] - v[..., :-1, :])
+
+
+def forward_divergence_adjoint(g, nx, ny):
+    """Transpose of forward_divergence for a cell field g [ny][nx]."""
+    gu = np.zeros((ny, nx + 1))
+    gv = np.zeros((ny + 1, nx))
+    gu[:, 1:] += g
+    gu[:, :-1] -= g
+    gv[1:, :] += g
+    gv[:-1, :] -= g
+    return gu, gv
+
+
+def pdnn_loss_and_grad(phi_hat, u_star, v_star, flags, s, weight, norm):
+    """(loss, dloss/dphi_hat) of the physics-driven loss (Sec. 3.2, Eq. 4) for
+    one grid whose network output is phi_hat.
+
+    During training the network alone solves the Poisson problem: its guess
+    phi = s * phi_hat (s the input scale of the network) corrects u* by Eq. 2
+    without any Jacobi sweep, and the loss is the mean over all nx * ny cells
+    of |div u|^norm times weight; norm = 1 is the printed Eq. 4, norm = 2 the
+    mean squared error that the text names.  Here u comes from the projection
+    oracle (zero closed faces, correct) and div u from all faces; the gradient
+    runs the chain backwards: divergence transpose, the adjoint of the
+    zero-sweep projection, the factor s.  sign(0) is taken as 0."""
+    if norm not in (1, 2):
+        raise ValueError("norm must be 1 or 2")
+    fl = np.asarray(flags)[None]
+    ny, nx = fl.shape[1:]
+    phi0 = s * np.asarray(phi_hat, np.float64).reshape(1, ny, nx)
+    u, v, _ = AD.project_fixed(np.asarray(u_star, np.float64).reshape(1, ny, nx + 1),
+                               np.asarray(v_star, np.float64).reshape(1, ny + 1, nx),
+                               phi0, fl, 0)
+    d = forward_divergence(u[0], v[0])
+    cells = nx * ny
+    if norm == 1:
+        loss = weight * np.abs(d).sum() / cells
+        gd = weight * np.sign(d) / cells
+    else:
+        loss = weight * (d ** 2).sum() / cells
+        gd = 2.0 * weight * d / cells
+    gu, gv = forward_divergence_adjoint(gd, nx, ny)
+    _, _, g_phi0 = AD.project_fixed_adjoint(gu[None], gv[None], None, fl, 0)
+    return loss, s * g_phi0[0]
