@@ -392,6 +392,53 @@ def compare_in_distribution(hp, params, flush, stream, dev, ws):
     return res
 
 
+def run_pdnn_arm(hp, dev, steps: int = 10, warmup: int = 3, batch: int = 64, n: int = 128):
+    """Physics-driven training (Sec. 3.2, Eq. 4) at the paper's training
+    resolution: one Adam step = the rollout of the training solver over
+    n_roll - 1 steps (network-only projection + advection) from a batch of
+    velocity states, then the loss gradient on 2 x batch grids (t and
+    t + n_roll - 1) and the update.  Timed with CUDA events per step for
+    n_roll = 4 and 16 (the paper draws 4 nine times in ten); inputs resident,
+    a fixed random network."""
+    import torch
+    from paper_2109_09363_gb300 import training as T
+    from paper_2109_09363_gb300 import workloads as W
+    u_np, v_np, f_np = W.training_case(batch, n, seed0=IN_DIST_SEED + 4096)
+    u = torch.from_numpy(u_np.astype(np.float32)).to(dev)
+    v = torch.from_numpy(v_np.astype(np.float32)).to(dev)
+    fl = torch.from_numpy(f_np).to(dev)
+    cnn = hp.CNN(2 * batch, n, n, params=T.init_params(seed=5))
+    ctx = hp.Context(batch, n, n, device=dev.index)
+    tr = hp.Trainer(cnn, 2 * batch, n, n)
+    stream = torch.cuda.current_stream()
+    res = {"workload": f"{batch} x {n}^2 training-distribution grids (vortex field + divergence "
+                       "sources + 0-4 obstacles), random network, norm 1, alpha = beta = 1",
+           "batch": batch, "grid": [n, n]}
+    for n_roll in (4, 16):
+        def one():
+            div, f2, w = T.pdnn_batch(cnn, ctx, u, v, fl, n_roll)
+            tr.pdnn_step(div, f2, w, norm=1, lr=1e-5)
+        for _ in range(warmup):
+            one()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            ev[k][0].record(stream)
+            one()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        res[f"ms_per_step_n{n_roll}"] = ms
+    ms_mean = 0.9 * res["ms_per_step_n4"] + 0.1 * res["ms_per_step_n16"]
+    res["ms_per_step_mean"] = ms_mean
+    res["samples_per_s"] = batch / (ms_mean * 1e-3)
+    tr.close()
+    ctx.close()
+    cnn.close()
+    return res
+
+
 def profile_conv(batch, h, w, cin, cout) -> int:
     """Time and run one tensor-core convolution layer (FLOP/s printed)."""
     import torch
@@ -473,6 +520,8 @@ def main():
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the CNN-hybrid arm (training + timing)")
+    ap.add_argument("--no-pdnn", action="store_true",
+                    help="skip the timing of physics-driven training steps")
     ap.add_argument("--train-steps", type=int, default=1200,
                     help="Adam steps of the network trained for the hybrid arm")
     ap.add_argument("--host-loop", action="store_true",
@@ -669,6 +718,7 @@ def main():
     hybrid = None
     if not args.no_hybrid:
         hybrid = run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms, ws)
+    pdnn = None if args.no_pdnn else run_pdnn_arm(hp, dev)
 
     if rank == 0:
         line = {
@@ -692,6 +742,8 @@ def main():
         }
         if hybrid is not None:
             line["hybrid"] = hybrid
+        if pdnn is not None:
+            line["pdnn_training"] = pdnn
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(u_np, v_np, fl_np)
         print(json.dumps(line), flush=True)

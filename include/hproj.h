@@ -262,6 +262,7 @@ typedef struct {
     float lr, beta1, beta2, eps;
     float lambda_div;
 } hp_train_params;
+/* max_shape may not exceed the network's own (HP_ERR_INVALID_ARG). */
 hp_status hp_trainer_create(hp_trainer **trainer, hp_cnn *cnn, hp_shape max_shape);
 void hp_trainer_destroy(hp_trainer *trainer);
 /* Loss (double [1], device, may be NULL) and its gradient w.r.t. every
@@ -274,6 +275,26 @@ hp_status hp_trainer_gradient(hp_trainer *trainer, const float *div, const uint8
 hp_status hp_trainer_step(hp_trainer *trainer, const float *div, const uint8_t *flags,
                           const float *target, hp_shape shape, const hp_train_params *params,
                           double *loss_out, void *stream);
+/* Physics-driven (unsupervised) loss of Sec. 3.2, Eq. 4: no target pressure.
+ * During training the network alone solves the Poisson problem: its guess
+ * s_b * phi_hat_b corrects the velocity u*_b whose divergence is div (Eq. 2,
+ * no Jacobi sweep), and the loss is
+ *     sum over grids b of weight[b] / (nx ny) * sum over cells |div u_b|^norm
+ * with norm = 1 (the printed Eq. 4) or 2 (the mean squared error the text
+ * names).  div u_b equals s_b times the residual of the scaled problem, so
+ * only div and flags are needed.  The paper's short- and long-term terms
+ * (alpha at t + 1, beta at t + n) are two sets of grids of one batch with
+ * weights alpha / B and beta / B.
+ * div float [B][ny][nx], flags u8, weight float [B]: device memory.
+ * grad_out, loss_out as for hp_trainer_gradient.  norm other than 1 or 2
+ * returns HP_ERR_INVALID_ARG. */
+hp_status hp_trainer_pdnn_gradient(hp_trainer *trainer, const float *div, const uint8_t *flags,
+                                   const float *weight, hp_shape shape, int32_t norm,
+                                   float *grad_out, double *loss_out, void *stream);
+/* One Adam step on the physics-driven loss (params->lambda_div unused). */
+hp_status hp_trainer_pdnn_step(hp_trainer *trainer, const float *div, const uint8_t *flags,
+                               const float *weight, hp_shape shape, int32_t norm,
+                               const hp_train_params *params, double *loss_out, void *stream);
 /* Copy the trained FP32 masters into the hp_cnn (hp_cnn_get_params then
  * returns them); synchronises the device. */
 hp_status hp_trainer_sync_params(hp_trainer *trainer);

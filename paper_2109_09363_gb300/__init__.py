@@ -67,6 +67,10 @@ _SIGS = {
     "hp_trainer_gradient": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_float, _P, _P, _P]),
     "hp_trainer_step": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_void_p, _P, _P]),
     "hp_trainer_sync_params": (ctypes.c_int, [_P]),
+    "hp_trainer_pdnn_gradient": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_int32, _P,
+                                                _P, _P]),
+    "hp_trainer_pdnn_step": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_int32,
+                                            ctypes.c_void_p, _P, _P]),
     "hp_cnn_param_count": (ctypes.c_int64, []),
     "hp_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
     "hp_cnn_destroy": (None, [_P]),
@@ -441,6 +445,33 @@ class Trainer:
         _check(load_library().hp_trainer_step(self._h, _ptr(div), _ptr(flags), _ptr(target), s,
                                               ctypes.cast(ctypes.byref(prm), ctypes.c_void_p),
                                               _ptr(loss_out), _stream(stream)))
+        return loss_out
+
+    def pdnn_gradient(self, div, flags, weight, norm=1, stream=None):
+        """Gradient and value of the physics-driven loss (Sec. 3.2, Eq. 4):
+        sum_b weight[b] * mean |div u_b|^norm, u_b corrected by the network."""
+        torch = _torch()
+        s = _shape_of_flags(flags)
+        _check_dtype(weight, torch.float32, (flags.shape[0],), "weight")
+        g = torch.empty(CNN.param_count(), dtype=torch.float32, device=div.device)
+        loss = torch.empty(1, dtype=torch.float64, device=div.device)
+        _check(load_library().hp_trainer_pdnn_gradient(self._h, _ptr(div), _ptr(flags),
+                                                       _ptr(weight), s, int(norm), _ptr(g),
+                                                       _ptr(loss), _stream(stream)))
+        return g, loss
+
+    def pdnn_step(self, div, flags, weight, norm=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                  loss_out=None, stream=None):
+        torch = _torch()
+        s = _shape_of_flags(flags)
+        _check_dtype(weight, torch.float32, (flags.shape[0],), "weight")
+        if loss_out is None:
+            loss_out = torch.empty(1, dtype=torch.float64, device=div.device)
+        prm = hp_train_params(lr, beta1, beta2, eps, 0.0)
+        _check(load_library().hp_trainer_pdnn_step(self._h, _ptr(div), _ptr(flags), _ptr(weight),
+                                                   s, int(norm),
+                                                   ctypes.cast(ctypes.byref(prm), ctypes.c_void_p),
+                                                   _ptr(loss_out), _stream(stream)))
         return loss_out
 
     def sync_params(self):

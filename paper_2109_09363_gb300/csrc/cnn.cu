@@ -965,6 +965,86 @@ __global__ void loss_finish_kernel(const double* __restrict__ stats, int B, size
     *loss = L / B;
 }
 
+// physics-driven loss (Sec. 3.2, Eq. 4) of the network-corrected field: the
+// guess s * phi_hat removes the divergence s * r with r = d - L phi_hat, the
+// residual of the scaled problem (0 on cells without an open face).  One CTA
+// per grid: rbuf <- dloss/dr = weight * norm * s^norm * |r|^(norm-1) sign(r)
+// / cells, stats[b] <- sum |s r|^norm
+__global__ void pdnn_stats_kernel(const float* __restrict__ phi, const float* __restrict__ div,
+                                  const uint8_t* __restrict__ mask, const float* __restrict__ s,
+                                  const float* __restrict__ weight, int norm,
+                                  float* __restrict__ rbuf, double* __restrict__ stats, int ny,
+                                  int nx)
+{
+    __shared__ double sh[32];
+    const int b = blockIdx.x;
+    const size_t cells = (size_t)ny * nx, base = (size_t)b * cells;
+    const float sb = s[b], inv_s = 1.0f / sb;
+    const float coef = norm == 1 ? weight[b] * sb / (float)cells
+                                 : 2.0f * weight[b] * sb * sb / (float)cells;
+    double acc = 0.0;
+    for (size_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        const uint32_t m = mask[base + c];
+        float r = 0.0f;
+        if (m & 15u) {
+            const float pc = phi[base + c];
+            float lap = 0.0f;
+            if (m & 1u) lap += phi[base + c - 1] - pc;
+            if (m & 2u) lap += phi[base + c + 1] - pc;
+            if (m & 4u) lap += phi[base + c - nx] - pc;
+            if (m & 8u) lap += phi[base + c + nx] - pc;
+            r = div[base + c] * inv_s - lap;
+        }
+        const double sr = (double)sb * (double)r;
+        float g;
+        if (norm == 1) {
+            acc += fabs(sr);
+            g = r > 0.0f ? coef : r < 0.0f ? -coef : 0.0f;
+        } else {
+            acc += sr * sr;
+            g = coef * r;
+        }
+        rbuf[base + c] = g;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) sh[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        stats[b] = t;
+    }
+}
+
+// dL/dphi_hat = -L^T dL/dr = -L (dL/dr): the masked Laplacian is symmetric
+__global__ void pdnn_grad_kernel(const float* __restrict__ rbuf, const uint8_t* __restrict__ mask,
+                                 float* __restrict__ g, int B, int ny, int nx)
+{
+    const size_t cells = (size_t)ny * nx;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (size_t)B * cells) return;
+    const uint32_t m = mask[q];
+    float lr = 0.0f;
+    if (m & 15u) {
+        const float rc = rbuf[q];
+        if (m & 1u) lr += rbuf[q - 1] - rc;
+        if (m & 2u) lr += rbuf[q + 1] - rc;
+        if (m & 4u) lr += rbuf[q - nx] - rc;
+        if (m & 8u) lr += rbuf[q + nx] - rc;
+    }
+    g[q] = -lr;
+}
+
+__global__ void pdnn_finish_kernel(const double* __restrict__ stats,
+                                   const float* __restrict__ weight, int B, size_t cells,
+                                   double* __restrict__ loss)
+{
+    double L = 0.0;
+    for (int b = 0; b < B; ++b) L += (double)weight[b] * stats[b] / (double)cells;
+    *loss = L;
+}
+
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long n, float lr, float b1, float b2, float eps,
                             float c1, float c2)
@@ -1053,6 +1133,11 @@ static constexpr int kWgradChunk = 2048;
 hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
 {
     if (!out || !cnn || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
+    // the forward pass of training runs in the network's own input workspace
+    // (scale, BF16 branch input), sized for its max_shape
+    if (mx.batch > cnn->max_shape.batch || mx.ny > cnn->max_shape.ny ||
+        mx.nx > cnn->max_shape.nx)
+        return HP_ERR_INVALID_ARG;
     *out = nullptr;
     hp_trainer* t = new hp_trainer();
     memset(t, 0, sizeof(*t));
@@ -1212,24 +1297,12 @@ static hp_status wgrad_dispatch(hp_trainer* t, int l, const float* gy, const voi
     return HP_ERR_UNSUPPORTED;
 }
 
-// dL/dparams for one batch into t->grad; loss (mean over the batch) into t->loss
-static hp_status trainer_grad(hp_trainer* t, const float* div, const uint8_t* flags,
-                              const float* target, hp_shape s, float lambda, cudaStream_t st)
+// dL/dparams into t->grad from dL/dphi_hat in t->g[0] (the activations of
+// the last trainer_forward)
+static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
 {
     hp_cnn* c = t->cnn;
-    hp_status rc = trainer_forward(t, div, flags, s, st);
-    if (rc != HP_OK) return rc;
-    // loss and its gradient w.r.t. the full-resolution output
-    if ((rc = launch_mask(flags, t->mask, s, st)) != HP_OK) return rc;
-    const size_t cells = (size_t)s.ny * s.nx;
-    const float* phi = (const float*)t->act[kLayers - 1];
-    loss_stats_kernel<<<s.batch, 512, 0, st>>>(phi, target, div, t->mask, flags, c->s, t->rbuf,
-                                               t->stats, s.ny, s.nx);
-    loss_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
-        phi, target, t->rbuf, t->mask, flags, c->s, t->stats, lambda, t->g[0], s.batch, s.ny,
-        s.nx);
-    loss_finish_kernel<<<1, 1, 0, st>>>(t->stats, s.batch, cells, lambda, t->loss);
-    if ((rc = check_launch()) != HP_OK) return rc;
+    hp_status rc = HP_OK;
     // backward, branch by branch from full resolution
     int cur = 0;
     for (int k = 2, l = kLayers - 1; k >= 0; --k) {
@@ -1268,18 +1341,50 @@ static hp_status trainer_grad(hp_trainer* t, const float* div, const uint8_t* fl
     return HP_OK;
 }
 
-extern "C" {
-
-hp_status hp_trainer_gradient(hp_trainer* t, const float* div, const uint8_t* flags,
-                              const float* target, hp_shape s, float lambda, float* grad_out,
-                              double* loss_out, void* stream)
+// dL/dparams for one batch into t->grad; loss (mean over the batch) into t->loss
+static hp_status trainer_grad(hp_trainer* t, const float* div, const uint8_t* flags,
+                              const float* target, hp_shape s, float lambda, cudaStream_t st)
 {
-    if (!t || !div || !flags || !target || !shape_ok(s) || s.batch > t->max.batch ||
-        s.ny > t->max.ny || s.nx > t->max.nx || s.ny % 4 || s.nx % 4)
-        return HP_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    hp_status rc = trainer_grad(t, div, flags, target, s, lambda, st);
+    hp_cnn* c = t->cnn;
+    hp_status rc = trainer_forward(t, div, flags, s, st);
     if (rc != HP_OK) return rc;
+    // loss and its gradient w.r.t. the full-resolution output
+    if ((rc = launch_mask(flags, t->mask, s, st)) != HP_OK) return rc;
+    const size_t cells = (size_t)s.ny * s.nx;
+    const float* phi = (const float*)t->act[kLayers - 1];
+    loss_stats_kernel<<<s.batch, 512, 0, st>>>(phi, target, div, t->mask, flags, c->s, t->rbuf,
+                                               t->stats, s.ny, s.nx);
+    loss_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
+        phi, target, t->rbuf, t->mask, flags, c->s, t->stats, lambda, t->g[0], s.batch, s.ny,
+        s.nx);
+    loss_finish_kernel<<<1, 1, 0, st>>>(t->stats, s.batch, cells, lambda, t->loss);
+    if ((rc = check_launch()) != HP_OK) return rc;
+    return trainer_backward(t, s, st);
+}
+
+// the same for the physics-driven loss: sum over grids of weight_b * mean
+// |div u_b|^norm, u_b the input velocity corrected by s_b * phi_hat_b
+static hp_status trainer_pdnn_grad(hp_trainer* t, const float* div, const uint8_t* flags,
+                                   const float* weight, hp_shape s, int norm, cudaStream_t st)
+{
+    hp_cnn* c = t->cnn;
+    hp_status rc = trainer_forward(t, div, flags, s, st);
+    if (rc != HP_OK) return rc;
+    if ((rc = launch_mask(flags, t->mask, s, st)) != HP_OK) return rc;
+    const size_t cells = (size_t)s.ny * s.nx;
+    const float* phi = (const float*)t->act[kLayers - 1];
+    pdnn_stats_kernel<<<s.batch, 512, 0, st>>>(phi, div, t->mask, c->s, weight, norm, t->rbuf,
+                                               t->stats, s.ny, s.nx);
+    pdnn_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
+        t->rbuf, t->mask, t->g[0], s.batch, s.ny, s.nx);
+    pdnn_finish_kernel<<<1, 1, 0, st>>>(t->stats, weight, s.batch, cells, t->loss);
+    if ((rc = check_launch()) != HP_OK) return rc;
+    return trainer_backward(t, s, st);
+}
+
+static hp_status trainer_copy_out(hp_trainer* t, float* grad_out, double* loss_out,
+                                  cudaStream_t st)
+{
     cudaError_t e = cudaSuccess;
     if (grad_out)
         e = cudaMemcpyAsync(grad_out, t->grad, t->param_count * 4, cudaMemcpyDeviceToDevice, st);
@@ -1287,6 +1392,38 @@ hp_status hp_trainer_gradient(hp_trainer* t, const float* div, const uint8_t* fl
         e = cudaMemcpyAsync(loss_out, t->loss, 8, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return HP_OK;
+}
+
+// Adam on the masters from t->grad, then the BF16 / FP32 copies of the network
+static hp_status trainer_adam(hp_trainer* t, const hp_train_params* p, cudaStream_t st)
+{
+    t->step += 1;
+    const float c1 = 1.0f - powf(p->beta1, (float)t->step);
+    const float c2 = 1.0f - powf(p->beta2, (float)t->step);
+    adam_kernel<<<(unsigned)((t->param_count + 255) / 256), 256, 0, st>>>(
+        t->master, t->grad, t->m, t->v, t->param_count, p->lr, p->beta1, p->beta2, p->eps, c1, c2);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
+    return trainer_pack(t, st);
+}
+
+static bool trainer_shape_ok(const hp_trainer* t, hp_shape s)
+{
+    return shape_ok(s) && s.batch <= t->max.batch && s.ny <= t->max.ny && s.nx <= t->max.nx &&
+           s.ny % 4 == 0 && s.nx % 4 == 0;
+}
+
+extern "C" {
+
+hp_status hp_trainer_gradient(hp_trainer* t, const float* div, const uint8_t* flags,
+                              const float* target, hp_shape s, float lambda, float* grad_out,
+                              double* loss_out, void* stream)
+{
+    if (!t || !div || !flags || !target || !trainer_shape_ok(t, s)) return HP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    hp_status rc = trainer_grad(t, div, flags, target, s, lambda, st);
+    if (rc != HP_OK) return rc;
+    return trainer_copy_out(t, grad_out, loss_out, st);
 }
 
 hp_status hp_trainer_step(hp_trainer* t, const float* div, const uint8_t* flags,
@@ -1297,14 +1434,30 @@ hp_status hp_trainer_step(hp_trainer* t, const float* div, const uint8_t* flags,
     hp_status rc = hp_trainer_gradient(t, div, flags, target, s, p->lambda_div, nullptr, loss_out,
                                        stream);
     if (rc != HP_OK) return rc;
+    return trainer_adam(t, p, (cudaStream_t)stream);
+}
+
+hp_status hp_trainer_pdnn_gradient(hp_trainer* t, const float* div, const uint8_t* flags,
+                                   const float* weight, hp_shape s, int32_t norm,
+                                   float* grad_out, double* loss_out, void* stream)
+{
+    if (!t || !div || !flags || !weight || !trainer_shape_ok(t, s) || (norm != 1 && norm != 2))
+        return HP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    t->step += 1;
-    const float c1 = 1.0f - powf(p->beta1, (float)t->step);
-    const float c2 = 1.0f - powf(p->beta2, (float)t->step);
-    adam_kernel<<<(unsigned)((t->param_count + 255) / 256), 256, 0, st>>>(
-        t->master, t->grad, t->m, t->v, t->param_count, p->lr, p->beta1, p->beta2, p->eps, c1, c2);
-    if ((rc = check_launch()) != HP_OK) return rc;
-    return trainer_pack(t, st);
+    hp_status rc = trainer_pdnn_grad(t, div, flags, weight, s, norm, st);
+    if (rc != HP_OK) return rc;
+    return trainer_copy_out(t, grad_out, loss_out, st);
+}
+
+hp_status hp_trainer_pdnn_step(hp_trainer* t, const float* div, const uint8_t* flags,
+                               const float* weight, hp_shape s, int32_t norm,
+                               const hp_train_params* p, double* loss_out, void* stream)
+{
+    if (!p || !(p->lr > 0.0f)) return HP_ERR_INVALID_ARG;
+    hp_status rc = hp_trainer_pdnn_gradient(t, div, flags, weight, s, norm, nullptr, loss_out,
+                                            stream);
+    if (rc != HP_OK) return rc;
+    return trainer_adam(t, p, (cudaStream_t)stream);
 }
 
 // copy the FP32 masters back into the network object (host copy, synchronous)

@@ -80,3 +80,73 @@ def train(cnn: hp.CNN, data, epochs: int = 20, batch: int = 64, lr: float = 1e-3
     trainer.sync_params()
     trainer.close()
     return losses[:k_step].cpu().numpy().tolist()
+
+
+# Physics-driven training (Sec. 3.2, Eq. 4)
+#
+# Reading: the short-term term is the divergence left by the network at
+# t + 1, the long-term term the one it leaves at t + n after the training
+# solver (network-only projection, then advection) has run n - 1 steps from
+# the same state; n = 4 nine times in ten, else 16.  Advection is not
+# differentiated and the rolled-out state is an input of the long-term term,
+# so both terms are one-step losses through the same network, on the state at
+# t and on the state reached at t + n - 1.
+
+def pdnn_rollout(cnn: hp.CNN, ctx: hp.Context, u, v, flags, steps: int, dt: float = 0.1,
+                 trace: list | None = None):
+    """The intermediate velocity u*_{t+steps} reached from u*_t = (u, v) by
+    `steps` steps of the training solver: the network-only projection (guess
+    s * CNN(div / s, flags), Eq. 2, no Jacobi sweep), then semi-Lagrangian
+    self-advection without buoyancy (the training flows carry no density
+    variation).  The inputs are not modified.  With a list as `trace`, every
+    step appends (u*, v*, projected u, projected v) before advecting."""
+    prm = hp.ProjectParams(threshold=0.0, max_iters=0, dt=dt)
+    adv = hp.PlumeParams(dt=dt, gravity=0.0)
+    rho = torch.ones(flags.shape, dtype=torch.float32, device=flags.device)
+    cu, cv = u.clone(), v.clone()
+    for _ in range(steps):
+        before = (cu.clone(), cv.clone()) if trace is not None else None
+        hp.hp_project_hybrid(ctx, cnn, cu, cv, flags, prm)
+        if trace is not None:
+            trace.append((*before, cu.clone(), cv.clone()))
+        cu, cv, rho = hp.hp_advect_step(cu, cv, rho, flags, adv)
+    return cu, cv
+
+
+def pdnn_batch(cnn: hp.CNN, ctx: hp.Context, u, v, flags, n: int, alpha: float = 1.0,
+               beta: float = 1.0, dt: float = 0.1):
+    """(div, flags, weight) of one physics-driven step on B grids: the grids
+    at t with weight alpha / B and the same grids rolled out to t + n - 1
+    with weight beta / B (2B grids, for Trainer.pdnn_step)."""
+    B = flags.shape[0]
+    ul, vl = pdnn_rollout(cnn, ctx, u, v, flags, n - 1, dt)
+    div = torch.cat([hp.hp_divergence(u, v, flags), hp.hp_divergence(ul, vl, flags)])
+    w = torch.cat([torch.full((B,), alpha / B), torch.full((B,), beta / B)])
+    return div, torch.cat([flags, flags]), w.to(device=flags.device, dtype=torch.float32)
+
+
+def train_pdnn(cnn: hp.CNN, data, steps: int, batch: int = 32, lr: float = 1e-3,
+               alpha: float = 1.0, beta: float = 1.0, norm: int = 1, dt: float = 0.1,
+               p_long: float = 0.1, n_short: int = 4, n_long: int = 16, seed: int = 0):
+    """Adam on the physics-driven loss over random mini-batches of velocity
+    states (u, v, flags on the device, u and v with divergence); the network
+    object must hold 2 * batch grids.  Returns the per-step losses and the
+    rollout lengths drawn."""
+    u, v, fl = data
+    N, ny, nx = fl.shape
+    ctx = hp.Context(batch, ny, nx, device=fl.device.index)
+    trainer = hp.Trainer(cnn, 2 * batch, ny, nx)
+    g = np.random.default_rng(seed)
+    losses = torch.empty(max(steps, 1), dtype=torch.float64, device=fl.device)
+    ns = []
+    for k in range(steps):
+        idx = torch.from_numpy(g.choice(N, batch, replace=False)).to(fl.device)
+        n = n_long if g.random() < p_long else n_short
+        ns.append(n)
+        div, f2, w = pdnn_batch(cnn, ctx, u[idx].contiguous(), v[idx].contiguous(),
+                                fl[idx].contiguous(), n, alpha, beta, dt)
+        trainer.pdnn_step(div, f2, w, norm=norm, lr=lr, loss_out=losses[k:k + 1])
+    trainer.sync_params()
+    trainer.close()
+    ctx.close()
+    return losses[:steps].cpu().numpy().tolist(), ns
