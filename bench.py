@@ -496,6 +496,39 @@ def profile_cnn(batch, n) -> int:
     return 0
 
 
+def profile_train(batch, n, norm=1) -> int:
+    """Time the physics-driven loss gradient (network forward, loss, backward)
+    on BATCH training-distribution grids of N x N, after 3 untimed calls."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    from paper_2109_09363_gb300 import training as T
+    from paper_2109_09363_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    u, v, fl = W.training_case(batch, n, seed0=IN_DIST_SEED + 8192)
+    ud = torch.from_numpy(u.astype(np.float32)).to(dev)
+    vd = torch.from_numpy(v.astype(np.float32)).to(dev)
+    fd = torch.from_numpy(fl).to(dev)
+    cnn = hp.CNN(batch, n, n, params=T.init_params(seed=1))
+    tr = hp.Trainer(cnn, batch, n, n)
+    div = hp.hp_divergence(ud, vd, fd)
+    w = torch.full((batch,), 1.0 / batch, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        tr.pdnn_gradient(div, fd, w, norm=norm)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        tr.pdnn_gradient(div, fd, w, norm=norm)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 5
+    # forward + two backward contractions (data and weight gradients)
+    flop = 3 * 2.0 * 190422 * batch * n * n
+    print(json.dumps({"profile_train": [batch, n], "ms": ms, "tflops": flop / ms / 1e9}))
+    return 0
+
+
 def main():
     global T_BLOCK
     ap = argparse.ArgumentParser()
@@ -518,6 +551,9 @@ def main():
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
     ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
+    ap.add_argument("--profile-train", nargs=2, type=int, metavar=("BATCH", "N"),
+                    help="only run the physics-driven loss gradient on BATCH grids of N x N, "
+                         "8 times (a small case for ncu)")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the CNN-hybrid arm (training + timing)")
     ap.add_argument("--no-pdnn", action="store_true",
@@ -539,6 +575,8 @@ def main():
         return profile_conv(*args.profile_conv)
     if args.profile_cnn:
         return profile_cnn(*args.profile_cnn)
+    if args.profile_train:
+        return profile_train(*args.profile_train)
 
     import torch
     import torch.distributed as dist

@@ -693,12 +693,20 @@ __device__ __forceinline__ bool reads(int y, int o, int i, int n)
     return y >= 0 && y < n && min(max(y + o, 0), n - 1) == i;
 }
 
+__device__ __forceinline__ float ld_act(const __nv_bfloat16* x, size_t i) { return __bfloat162float(x[i]); }
+__device__ __forceinline__ float ld_act(const float* x, size_t i) { return x[i]; }
+__device__ __forceinline__ void st_val(float* y, size_t i, float v) { y[i] = v; }
+__device__ __forceinline__ void st_val(__nv_bfloat16* y, size_t i, float v) { y[i] = __float2bfloat16_rn(v); }
+
 // dL/dx of a 3 x 3 convolution with replicated borders: gx[p][ci] = sum over
 // taps and the output pixels that read p through that tap of
 // w[t][co][ci] * gy[o][co].  w: FP32 [9][CO][CI] (the BF16-rounded weights).
-template <int CI, int CO>
-__global__ void conv_dgrad_kernel(const float* __restrict__ gy, const float* __restrict__ w,
-                                  float* __restrict__ gx, int B, int H, int W)
+// With act (BF16 [P][CI]) the result is zeroed where act is not positive
+// (the ReLU derivative of the layer that produced the input).
+template <int CI, int CO, typename GT = float, typename OT = float>
+__global__ void conv_dgrad_kernel(const GT* __restrict__ gy, const float* __restrict__ w,
+                                  OT* __restrict__ gx, int B, int H, int W,
+                                  const __nv_bfloat16* __restrict__ act = nullptr)
 {
     extern __shared__ float sw[];
     for (int q = threadIdx.x; q < 9 * CO * CI; q += blockDim.x) sw[q] = w[q];
@@ -718,10 +726,10 @@ __global__ void conv_dgrad_kernel(const float* __restrict__ gy, const float* __r
                 if (!reads(yy, oy, i, H)) continue;
                 for (int xx = j - ox - 1; xx <= j - ox + 1; ++xx) {
                     if (!reads(xx, ox, j, W)) continue;
-                    const float* g = gy + (((size_t)b * H + yy) * W + xx) * CO;
+                    const size_t g = (((size_t)b * H + yy) * W + xx) * CO;
                     const float* wt = sw + t * CO * CI;
                     for (int co = 0; co < CO; ++co) {
-                        const float gv = g[co];
+                        const float gv = ld_act(gy, g + co);
 #pragma unroll
                         for (int c = 0; c < CI; ++c) acc[c] = fmaf(wt[co * CI + c], gv, acc[c]);
                     }
@@ -729,19 +737,19 @@ __global__ void conv_dgrad_kernel(const float* __restrict__ gy, const float* __r
             }
         }
 #pragma unroll
-        for (int c = 0; c < CI; ++c) gx[(size_t)p * CI + c] = acc[c];
+        for (int c = 0; c < CI; ++c) {
+            const bool keep = !act || __bfloat162float(act[(size_t)p * CI + c]) > 0.0f;
+            st_val(gx, (size_t)p * CI + c, keep ? acc[c] : 0.0f);
+        }
     }
 }
-
-__device__ __forceinline__ float ld_act(const __nv_bfloat16* x, size_t i) { return __bfloat162float(x[i]); }
-__device__ __forceinline__ float ld_act(const float* x, size_t i) { return x[i]; }
 
 // Weight gradient partial sums over a chunk of pixels for one tap:
 // part[(chunk * 9 + t)][co][ci] = sum_p gy[p][co] * x[clamp(p + offset_t)][ci];
 // the centre tap also writes the bias partials partb[chunk][co] = sum_p gy.
 // Each thread owns a BCO x BCI block of (co, ci).
-template <int CI, int CO, int BCI, int BCO, typename XT>
-__global__ void conv_wgrad_kernel(const float* __restrict__ gy, const XT* __restrict__ x,
+template <int CI, int CO, int BCI, int BCO, typename XT, typename GT = float>
+__global__ void conv_wgrad_kernel(const GT* __restrict__ gy, const XT* __restrict__ x,
                                   float* __restrict__ part, float* __restrict__ partb, int B,
                                   int H, int W, int chunk)
 {
@@ -766,7 +774,7 @@ __global__ void conv_wgrad_kernel(const float* __restrict__ gy, const XT* __rest
     for (long pt = p0; pt < p1; pt += TP) {
         for (int q = threadIdx.x; q < TP * CO; q += blockDim.x) {
             const long p = pt + q / CO;
-            sg[q / CO][q % CO] = p < p1 ? gy[(size_t)p * CO + q % CO] : 0.0f;
+            sg[q / CO][q % CO] = p < p1 ? ld_act(gy, (size_t)p * CO + q % CO) : 0.0f;
         }
         for (int q = threadIdx.x; q < TP * CI; q += blockDim.x) {
             const long p = pt + q / CI;
@@ -823,6 +831,104 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float*
         double s = 0.0;
         for (int k = 0; k < nchunks; ++k) s += partb[(size_t)k * CO + co];
         gb[co] = (float)s;
+    }
+}
+
+// Border terms of the input gradient of a 3 x 3 convolution with replicated
+// borders.  The forward reads x at clamp(p + d); extended by a ring of ghost
+// pixels holding the replicated values, it is a plain convolution, whose
+// transpose puts w[d]^T gy[q - d] on every extended pixel q.  The tensor-core
+// pass computes that transpose with zero padding on the image itself; an
+// input pixel j on the border also collects the ghost pixels q outside the
+// image with clamp(q) = j.  One warp per border pixel, lanes over the input
+// channels; the ghost terms get the ReLU derivative of act (may be null) and
+// are added to gx (BF16 [P][CI], rounded again).  w: FP32 [9][CO][CI].
+template <int CI, int CO>
+__global__ void dgrad_border_kernel(const __nv_bfloat16* __restrict__ gy,
+                                    const float* __restrict__ w,
+                                    const __nv_bfloat16* __restrict__ act,
+                                    __nv_bfloat16* __restrict__ gx, int B, int H, int W)
+{
+    constexpr int PER = CI / 32;
+    const int ncol = W > 1 ? 2 : 1;
+    const int nrow_px = H > 1 ? 2 * W : W;
+    const long per_img = nrow_px + (long)max(H - 2, 0) * ncol;
+    const long e_all = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e_all >= (long)B * per_img) return;
+    const int b = (int)(e_all / per_img);
+    const int e = (int)(e_all - (long)b * per_img);
+    int jy, jx;
+    if (e < W) { jy = 0; jx = e; }
+    else if (e < nrow_px) { jy = H - 1; jx = e - W; }
+    else { const int e2 = e - nrow_px; jy = 1 + e2 / ncol; jx = (e2 % ncol) ? W - 1 : 0; }
+    float acc[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
+    const int gys[3] = {jy, jy == 0 ? -1 : jy, jy == H - 1 ? H : jy};
+    const int gxs[3] = {jx, jx == 0 ? -1 : jx, jx == W - 1 ? W : jx};
+    for (int a = 0; a < 3; ++a) {
+        const int qy = gys[a];
+        if (a > 0 && qy == jy) continue;
+        for (int c = 0; c < 3; ++c) {
+            const int qx = gxs[c];
+            if (c > 0 && qx == jx) continue;
+            if (qy == jy && qx == jx) continue;  // inside: the tensor-core pass has it
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int py = qy - dy;
+                if (py < 0 || py >= H) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int px = qx - dx;
+                    if (px < 0 || px >= W) continue;
+                    const __nv_bfloat16* g = gy + (((size_t)b * H + py) * W + px) * CO;
+                    const float* wt = w + (size_t)(3 * (dy + 1) + dx + 1) * CO * CI;
+                    for (int co = 0; co < CO; ++co) {
+                        const float gv = __bfloat162float(g[co]);
+#pragma unroll
+                        for (int k = 0; k < PER; ++k)
+                            acc[k] = fmaf(wt[co * CI + lane + 32 * k], gv, acc[k]);
+                    }
+                }
+            }
+        }
+    }
+    const size_t q = (((size_t)b * H + jy) * W + jx) * CI;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int ci = lane + 32 * k;
+        if (act && !(__bfloat162float(act[q + ci]) > 0.0f)) continue;
+        gx[q + ci] = __float2bfloat16_rn(__bfloat162float(gx[q + ci]) + acc[k]);
+    }
+}
+
+// Bias gradient partial sums: partb[g][co] = sum of gy[p][co] (BF16 [P][CO])
+// over the g-th of G equal pixel ranges, in a fixed order.
+template <int CO>
+__global__ void __launch_bounds__(256) bias_grad_kernel(const uint4* __restrict__ gy, long P,
+                                                        float* __restrict__ partb)
+{
+    constexpr int NCH = CO / 8, PAR = 256 / NCH;
+    __shared__ float sh[PAR][CO + 1];
+    const int G = gridDim.x, g = blockIdx.x;
+    const long p0 = P * g / G, p1 = P * (g + 1) / G;
+    const int ch = threadIdx.x % NCH, pl = threadIdx.x / NCH;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long p = p0 + pl; p < p1; p += PAR) {
+        const uint4 v = gy[(size_t)p * NCH + ch];
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[2 * k] += __uint_as_float(u[k] << 16);
+            acc[2 * k + 1] += __uint_as_float(u[k] & 0xFFFF0000u);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[pl][ch * 8 + k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < CO) {
+        float t = 0.0f;
+        for (int i = 0; i < PAR; ++i) t += sh[i][threadIdx.x];
+        partb[(size_t)g * CO + threadIdx.x] = t;
     }
 }
 
@@ -1061,9 +1167,11 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
 
 // masters (oracle order [co][ci][3][3] + bias) of one layer -> the layouts of
 // the forward kernels (BF16-rounded) and the FP32 [9][co][ci] copy for dgrad
+// and, for the tensor-core layers, the BF16 weights of the input-gradient
+// convolution: flipped taps, input and output swapped, wdg[8 - t][ci][co]
 __global__ void pack_layer_kernel(const float* __restrict__ master, int ci, int co, int kind,
                                   void* __restrict__ wfwd, float* __restrict__ bias,
-                                  float* __restrict__ wt)
+                                  float* __restrict__ wt, __nv_bfloat16* __restrict__ wdg)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int nw = 9 * ci * co;
@@ -1075,6 +1183,7 @@ __global__ void pack_layer_kernel(const float* __restrict__ master, int ci, int 
         else if (kind == 1) reinterpret_cast<float*>(wfwd)[((size_t)t * ci + i) * co + o] = f;
         else reinterpret_cast<float*>(wfwd)[(size_t)t * ci + i] = f;
         wt[((size_t)t * co + o) * ci + i] = f;
+        if (wdg) wdg[((size_t)(8 - t) * ci + i) * co + o] = h;
     } else if (q < nw + co) {
         bias[q - nw] = master[q];
     }
@@ -1094,6 +1203,8 @@ struct hp_trainer {
     float* xin[3];        // first-layer inputs per branch, FP32 [P][cin]
     float* g[2];          // gradient ping-pong, FP32 [P][64]
     float* gsmall;        // first-layer input gradient, FP32 [P][3]
+    __nv_bfloat16* wdg[kLayers];  // input-gradient weights of the tensor-core layers
+    float* zero_bias;     // 64 zeros: the bias of an input-gradient convolution
     float *part, *partb;
     size_t part_len, partb_len;
     float* rbuf;
@@ -1112,6 +1223,10 @@ static long layer_offset(int l)
 
 static int scale_of(int l) { return kSpec[l].scale; }
 
+// layers whose backward runs on the tensor cores (at widths from
+// conv_tc_min_width() up): 32 or 64 channels on both sides
+static bool tc_layer(int l) { return kSpec[l].cin >= 32 && kSpec[l].cout >= 32; }
+
 static hp_status trainer_pack(hp_trainer* t, cudaStream_t st);
 
 extern "C" {
@@ -1120,7 +1235,10 @@ void hp_trainer_destroy(hp_trainer* t)
 {
     if (!t) return;
     cudaFree(t->master); cudaFree(t->grad); cudaFree(t->m); cudaFree(t->v);
-    for (int l = 0; l < kLayers; ++l) { cudaFree(t->wt[l]); cudaFree(t->act[l]); }
+    for (int l = 0; l < kLayers; ++l) {
+        cudaFree(t->wt[l]); cudaFree(t->act[l]); cudaFree(t->wdg[l]);
+    }
+    cudaFree(t->zero_bias);
     for (int k = 0; k < 3; ++k) cudaFree(t->xin[k]);
     cudaFree(t->g[0]); cudaFree(t->g[1]); cudaFree(t->gsmall);
     cudaFree(t->part); cudaFree(t->partb); cudaFree(t->rbuf); cudaFree(t->stats);
@@ -1159,7 +1277,9 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
         const size_t Pl = P / (sc * sc);
         al(&t->act[l], kSpec[l].cout == 1 ? Pl * 4 : Pl * kSpec[l].cout * 2);
         al((void**)&t->wt[l], layer_wcount(l) * 4);
+        if (tc_layer(l)) al((void**)&t->wdg[l], layer_wcount(l) * 2);
     }
+    al((void**)&t->zero_bias, 64 * 4);
     for (int k = 0; k < 3; ++k) {
         const int sc = k == 0 ? 4 : k == 1 ? 2 : 1;
         al((void**)&t->xin[k], P / (sc * sc) * 3 * 4);
@@ -1167,7 +1287,10 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     al((void**)&t->g[0], P * 64 * 4);
     al((void**)&t->g[1], P * 64 * 4);
     al((void**)&t->gsmall, P * 3 * 4);
-    const size_t nchunks = (P + kWgradChunk - 1) / kWgradChunk;
+    // partial sums: one per pixel chunk (CUDA-core weight gradient) or per
+    // CTA (tensor-core weight gradient, at most one CTA per SM)
+    size_t nchunks = (P + kWgradChunk - 1) / kWgradChunk;
+    if (nchunks < (size_t)cnn->num_sms) nchunks = (size_t)cnn->num_sms;
     t->part_len = nchunks * 9 * 64 * 64;
     t->partb_len = nchunks * 64;
     al((void**)&t->part, t->part_len * 4);
@@ -1197,7 +1320,7 @@ static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
         const int n = 9 * ci * co + co;
         pack_layer_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->master + layer_offset(l), ci, co,
                                                           kind, t->cnn->w[l], t->cnn->bias[l],
-                                                          t->wt[l]);
+                                                          t->wt[l], t->wdg[l]);
     }
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
@@ -1237,20 +1360,20 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
     return HP_OK;
 }
 
-template <int CI, int CO>
-static hp_status dgrad(const float* gy, const float* w, float* gx, int B, int H, int W, int nsm,
-                       cudaStream_t st)
+template <int CI, int CO, typename GT = float, typename OT = float>
+static hp_status dgrad(const GT* gy, const float* w, OT* gx, int B, int H, int W, int nsm,
+                       cudaStream_t st, const __nv_bfloat16* act = nullptr)
 {
     const size_t smem = (size_t)9 * CI * CO * 4;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(conv_dgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+        cudaFuncSetAttribute(conv_dgrad_kernel<CI, CO, GT, OT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     const long P = (long)B * H * W;
     const int blocks = (int)((P + 127) / 128 < 4L * nsm ? (P + 127) / 128 : 4L * nsm);
-    conv_dgrad_kernel<CI, CO><<<blocks, 128, smem, st>>>(gy, w, gx, B, H, W);
+    conv_dgrad_kernel<CI, CO, GT, OT><<<blocks, 128, smem, st>>>(gy, w, gx, B, H, W, act);
     return check_launch();
 }
 
@@ -1265,15 +1388,15 @@ static hp_status dgrad_dispatch(int ci, int co, const float* gy, const float* w,
     return HP_ERR_UNSUPPORTED;
 }
 
-template <int CI, int CO, int BCI, int BCO, typename XT>
-static hp_status wgrad_t(hp_trainer* t, const float* gy, const XT* x, float* gw, float* gb, int B,
+template <int CI, int CO, int BCI, int BCO, typename XT, typename GT = float>
+static hp_status wgrad_t(hp_trainer* t, const GT* gy, const XT* x, float* gw, float* gb, int B,
                          int H, int W, cudaStream_t st)
 {
     const long P = (long)B * H * W;
     const int nchunks = (int)((P + kWgradChunk - 1) / kWgradChunk);
     if ((size_t)nchunks * 9 * CO * CI > t->part_len) return HP_ERR_INVALID_ARG;
     const int threads = ((CO / BCO) * (CI / BCI) + 31) / 32 * 32;
-    conv_wgrad_kernel<CI, CO, BCI, BCO, XT><<<dim3(nchunks, 9), threads, 0, st>>>(
+    conv_wgrad_kernel<CI, CO, BCI, BCO, XT, GT><<<dim3(nchunks, 9), threads, 0, st>>>(
         gy, x, t->part, t->partb, B, H, W, kWgradChunk);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
@@ -1297,6 +1420,78 @@ static hp_status wgrad_dispatch(hp_trainer* t, int l, const float* gy, const voi
     return HP_ERR_UNSUPPORTED;
 }
 
+// first layer of a branch (2 or 3 -> 32) from a BF16 gradient: weight
+// gradient, and for the finer branches the gradient of the up-sampled coarser
+// output (input channel 2) into gsmall
+static hp_status first_layer_bf16(hp_trainer* t, int k, int l, const __nv_bfloat16* gy, int B,
+                                  int H, int W, cudaStream_t st)
+{
+    float* gw = t->grad + layer_offset(l);
+    float* gb = gw + layer_wcount(l);
+    hp_status rc = kSpec[l].cin == 3
+                       ? wgrad_t<3, 32, 1, 1>(t, gy, (const float*)t->xin[k], gw, gb, B, H, W, st)
+                       : wgrad_t<2, 32, 1, 1>(t, gy, (const float*)t->xin[k], gw, gb, B, H, W, st);
+    if (rc != HP_OK || k == 0) return rc;
+    return dgrad<3, 32>(gy, t->wt[l], t->gsmall, B, H, W, t->cnn->num_sms, st);
+}
+
+// One branch on the tensor cores (width >= conv_tc_min_width()): gradients
+// in BF16 [P][C], the ReLU derivative applied by the layer that produces each
+// gradient.  gout: FP32 [P] gradient of the branch's 1-channel output.
+static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast, float* gout,
+                                    __nv_bfloat16* gbuf[2], int B, int H, int W, cudaStream_t st)
+{
+    hp_cnn* c = t->cnn;
+    const long P = (long)B * H * W;
+    // last layer (32 -> 1, CUDA cores): weight gradient from the FP32 output
+    // gradient, input gradient into BF16
+    float* gw = t->grad + layer_offset(llast);
+    hp_status rc = wgrad_t<32, 1, 1, 1>(t, gout, (const __nv_bfloat16*)t->act[llast - 1], gw,
+                                        gw + layer_wcount(llast), B, H, W, st);
+    if (rc != HP_OK) return rc;
+    const __nv_bfloat16* mask_last =
+        kSpec[llast - 1].relu ? (const __nv_bfloat16*)t->act[llast - 1] : nullptr;
+    rc = dgrad<32, 1, float, __nv_bfloat16>(gout, t->wt[llast], gbuf[0], B, H, W, c->num_sms, st,
+                                            mask_last);
+    if (rc != HP_OK) return rc;
+    int cur = 0;
+    for (int l = llast - 1; l > lfirst; --l) {
+        const int ci = kSpec[l].cin, co = kSpec[l].cout;
+        const __nv_bfloat16* gy = gbuf[cur];
+        const __nv_bfloat16* x = (const __nv_bfloat16*)t->act[l - 1];
+        int grid = 0;
+        rc = launch_conv3x3_tc_wgrad(x, gy, t->part, t->part_len, B, H, W, ci, co, c->err,
+                                     c->num_sms, &grid, st);
+        if (rc != HP_OK) return rc;
+        if (co == 64)
+            bias_grad_kernel<64><<<grid, 256, 0, st>>>((const uint4*)gy, P, t->partb);
+        else
+            bias_grad_kernel<32><<<grid, 256, 0, st>>>((const uint4*)gy, P, t->partb);
+        gw = t->grad + layer_offset(l);
+        const int n = 9 * co * ci + co;
+        wgrad_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->part, t->partb, grid, ci, co, gw,
+                                                             gw + layer_wcount(l));
+        if ((rc = check_launch()) != HP_OK) return rc;
+        // input gradient with the ReLU derivative of layer l - 1
+        const __nv_bfloat16* act = kSpec[l - 1].relu ? x : nullptr;
+        __nv_bfloat16* gx = gbuf[cur ^ 1];
+        rc = launch_conv3x3_tc_dgrad(gy, t->wdg[l], t->zero_bias, act, gx, B, H, W, ci, co,
+                                     c->err, c->num_sms, st);
+        if (rc != HP_OK) return rc;
+        const long nb = (long)B * ((H > 1 ? 2 * W : W) + (long)(H > 2 ? H - 2 : 0) * (W > 1 ? 2 : 1));
+        const unsigned blocks = (unsigned)((nb * 32 + 255) / 256);
+        if (ci == 64 && co == 64)
+            dgrad_border_kernel<64, 64><<<blocks, 256, 0, st>>>(gy, t->wt[l], act, gx, B, H, W);
+        else if (ci == 32 && co == 64)
+            dgrad_border_kernel<32, 64><<<blocks, 256, 0, st>>>(gy, t->wt[l], act, gx, B, H, W);
+        else
+            dgrad_border_kernel<64, 32><<<blocks, 256, 0, st>>>(gy, t->wt[l], act, gx, B, H, W);
+        if ((rc = check_launch()) != HP_OK) return rc;
+        cur ^= 1;
+    }
+    return first_layer_bf16(t, k, lfirst, gbuf[cur], B, H, W, st);
+}
+
 // dL/dparams into t->grad from dL/dphi_hat in t->g[0] (the activations of
 // the last trainer_forward)
 static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
@@ -1310,6 +1505,23 @@ static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
         const int H = s.ny / scale, W = s.nx / scale;
         const long P = (long)s.batch * H * W;
         const int lfirst = k == 0 ? 0 : k == 1 ? 5 : 12;
+        if (W >= conv_tc_min_width()) {
+            // the FP32 gradient of the branch output stays in g[cur]; the
+            // BF16 gradients use g[cur ^ 1] and the unused half of g[cur]
+            __nv_bfloat16* gbuf[2] = {(__nv_bfloat16*)t->g[cur ^ 1],
+                                      (__nv_bfloat16*)(t->g[cur ^ 1]) + (size_t)P * 64};
+            rc = branch_backward_tc(t, k, lfirst, l, t->g[cur], gbuf, s.batch, H, W, st);
+            if (rc != HP_OK) return rc;
+            if (k > 0) {
+                const long Pc = P / 4;
+                upsample_adjoint_kernel<<<(unsigned)((Pc + 255) / 256), 256, 0, st>>>(
+                    t->gsmall, 3, 2, t->g[cur ^ 1], s.batch, H / 2, W / 2);
+                if ((rc = check_launch()) != HP_OK) return rc;
+                cur ^= 1;
+            }
+            l = lfirst - 1;
+            continue;
+        }
         for (; l >= lfirst; --l) {
             const int ci = kSpec[l].cin, co = kSpec[l].cout;
             float* gy = t->g[cur];

@@ -257,6 +257,13 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
 
+// 16 bytes from global memory, or 16 zero bytes when !valid (src is not read)
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16u : 0u));
+}
+
 // Warp-specialised persistent row walk (width >= 128).  Each CTA loops over
 // work items (grid, 128-pixel column strip, band of rows); the input rows of
 // all its items form one stream through a kWsSlots-deep ring of halo rows in
@@ -422,6 +429,16 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi, bool relu)
     return d;
 }
 
+// Two packed BF16 values v kept where the matching BF16 value of a is
+// positive, zeroed elsewhere.
+__device__ __forceinline__ uint32_t relu_mask2(uint32_t v, uint32_t a)
+{
+    uint32_t m = 0;
+    if ((a & 0xFFFFu) != 0u && !(a & 0x8000u)) m |= 0xFFFFu;
+    if ((a >> 16) != 0u && !(a & 0x80000000u)) m |= 0xFFFF0000u;
+    return v & m;
+}
+
 struct WsItem {
     int b, x0, y0, y1;
 };
@@ -446,11 +463,18 @@ __device__ __forceinline__ uint32_t idesc_for_rows(int n_out, int cout)
                         : mma_idesc(kTileM, 3 * cout);
 }
 
-template <int CIN, int COUT, bool OUT1>
+// DGRAD: the input gradient of a convolution as the convolution of the output
+// gradient x with the flipped, transposed weights w: zero padding instead of
+// replicated borders (the border terms of the replicated padding are added
+// by a separate pass), and in the epilogue every value whose activation in
+// act (same layout as the output) is not positive is zeroed (the ReLU
+// derivative of the layer that produced act; act may be null).
+template <int CIN, int COUT, bool OUT1, bool DGRAD = false>
 __global__ void __launch_bounds__(kWsThreads, 1)
     conv3x3_tc_ws_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
                          const float* __restrict__ bias, void* __restrict__ yout, int H, int W,
-                         int segs, int nbands, int band, int items, int relu, int* err)
+                         int segs, int nbands, int band, int items, int relu, int* err,
+                         const uint4* __restrict__ act = nullptr)
 {
     using S = WsSmem<CIN, COUT, OUT1>;
     __nv_bfloat16* __restrict__ y = reinterpret_cast<__nv_bfloat16*>(yout);
@@ -540,7 +564,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 const int sr = min(max(r, 0), H - 1);
                 const uint32_t dst = smem_u32(ring + s * S::kSlotBytes) + (uint32_t)(ch * kHaloPx * 16);
                 const uint4* src_row = x + ((size_t)it.b * H + sr) * W * NCH + ch;
-                if (interior) {
+                if constexpr (DGRAD) {
+                    // zero outside the image
+                    const bool row_in = r >= 0 && r < H;
+                    for (int px = p0; px < kHaloPx; px += kPass) {
+                        const int gx = it.x0 - 1 + px;
+                        const int sx = min(max(gx, 0), W - 1);
+                        cp_async16_zfill(dst + (uint32_t)(px * 16), src_row + (size_t)sx * NCH,
+                                         row_in && gx >= 0 && gx < W);
+                    }
+                } else if (interior) {
                     const uint4* src = src_row + (size_t)(it.x0 - 1 + p0) * NCH;
 #pragma unroll 4
                     for (int px = p0; px < kHaloPx; px += kPass, src += kPass * NCH)
@@ -694,10 +727,22 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 for (int i = 0; i < CPP; ++i) {
                     const int k = lane + 32 * i;
                     const int p = k / CPP, c = k % CPP;
-                    const uint4 v = *reinterpret_cast<const uint4*>(
+                    uint4 v = *reinterpret_cast<const uint4*>(
                         stage + p * (COUT * 2) + ((c ^ stage_swz(p)) * 16));
-                    if (it.x0 + warp * 32 + p < W)
+                    if (it.x0 + warp * 32 + p < W) {
+                        if constexpr (DGRAD) {
+                            if (act) {
+                                const size_t q = (((size_t)it.b * H + yy) * W + it.x0 + warp * 32 +
+                                                  p) * CPP + c;
+                                const uint4 a = act[q];
+                                v.x = relu_mask2(v.x, a.x);
+                                v.y = relu_mask2(v.y, a.y);
+                                v.z = relu_mask2(v.z, a.z);
+                                v.w = relu_mask2(v.w, a.w);
+                            }
+                        }
                         *reinterpret_cast<uint4*>(row + (size_t)p * COUT + 8 * c) = v;
+                    }
                 }
                 __syncwarp();
                 }
@@ -720,14 +765,15 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 // warp-specialised row walk, one persistent CTA per SM; bands sized for about
 // eight work items per CTA (an image narrower than 128 pixels is one strip
 // whose pixels past its width are clamped on load and not stored)
-template <int CIN, int COUT, bool OUT1>
+template <int CIN, int COUT, bool OUT1, bool DGRAD = false>
 hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, int B, int H,
-                    int W, int relu, int* err, int nsm, cudaStream_t st)
+                    int W, int relu, int* err, int nsm, cudaStream_t st,
+                    const void* act = nullptr)
 {
     using R = WsSmem<CIN, COUT, OUT1>;
     static bool rattr = false;
     if (!rattr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_ws_kernel<CIN, COUT, OUT1>,
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              R::kBytes);
         if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
@@ -741,9 +787,293 @@ hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, in
     const long items = (long)B * segs * nbands;
     if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
     const int grid = items < nsm ? (int)items : nsm;
-    conv3x3_tc_ws_kernel<CIN, COUT, OUT1><<<grid, kWsThreads, R::kBytes, st>>>(
+    conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD><<<grid, kWsThreads, R::kBytes, st>>>(
         (const uint4*)x, (const uint4*)w, bias, y, H, W, segs, nbands, band, (int)items, relu,
-        err);
+        err, (const uint4*)act);
+    return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3 x 3 convolution with replicated borders on the
+// tensor cores:
+//     gW[dy][dx][co][ci] = sum over pixels p of gy[p][co] * x[clamp(p + (dy, dx))][ci]
+// Per 128-pixel row segment of an output-gradient row r this is a GEMM over
+// K = the 130 input pixels x0 - 1 .. x0 + 128 (padded to 144, 9 steps of 16):
+//   A = input rows (M = 128 = kRows rows x CI channels), taken MN-major straight
+//       from an input-row ring laid out [row][channel chunk][pixel][8 channels]
+//       with replicated halo pixels; consecutive rows are adjacent in shared
+//       memory (the first kRows - 1 ring slots are mirrored after the last),
+//       so one descriptor spans kRows rows;
+//   B = the gradient row in three copies shifted by dx (pixel q of copy dx
+//       holds gy[q - dx], zero outside the segment), N = 3 CO, MN-major;
+//   D = TMEM, lane (row i of the tile, ci), column (dx, co), accumulating over
+//       every row and segment the CTA visits.
+// CI = 64: two tiles per gradient row, input rows (r-1, r) and (r, r+1) (the
+// second tile's r half repeats the first and is not read out); CI = 32: one
+// tile of rows r-1 .. r+2 (the r+2 quarter is not read out and may hold any
+// row).  Warps 0-3 load (cp.async) and finally read the accumulators out to
+// per-CTA partial sums part[cta][3 dy + dx][co][ci]; warp 4 issues the MMAs.
+constexpr int kWgPx = 144;
+constexpr int kWgThreads = 160;
+
+template <int CI, int CO>
+struct WgSmem {
+    static constexpr int kChunksX = CI / 8, kChunksG = CO / 8;
+    static constexpr int kStride = kWgPx * 16;  // bytes per channel chunk of a row
+    static constexpr int kSlotBytes = kChunksX * kStride;
+    static constexpr int kRows = 128 / CI;
+    static constexpr int kSlots = kRows == 2 ? 4 : 5;
+    static constexpr int kMirror = kRows - 1;
+    static constexpr int kRingBytes = (kSlots + kMirror) * kSlotBytes;
+    static constexpr int kGBytes = 3 * kChunksG * kStride;
+    static constexpr int kTiles = kRows == 2 ? 2 : 1;
+    static constexpr int kN = 3 * CO;
+    static constexpr int kBytes = kRingBytes + 2 * kGBytes;
+    static constexpr int kTmemCols = kTiles * kN <= 128 ? 128 : kTiles * kN <= 256 ? 256 : 512;
+    static_assert(CI == 32 || CI == 64, "input channels 32 or 64");
+    static_assert(CO == 32 || CO == 64, "output channels 32 or 64");
+    static_assert(kBytes <= 227 * 1024, "shared memory");
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(kWgThreads, 1)
+    conv3x3_wgrad_tc_kernel(const uint4* __restrict__ x, const uint4* __restrict__ gy,
+                            float* __restrict__ part, int H, int W, int segs, int nbands,
+                            int band, int items, int* err)
+{
+    using S = WgSmem<CI, CO>;
+    constexpr int NX = S::kChunksX, NG = S::kChunksG;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* ring = smem;
+    uint8_t* gbuf = smem + S::kRingBytes;
+    __shared__ __align__(8) uint64_t xfull[S::kSlots];
+    __shared__ __align__(8) uint64_t xempty[S::kSlots];
+    __shared__ __align__(8) uint64_t gfull[2];
+    __shared__ __align__(8) uint64_t gempty[2];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"((uint32_t)S::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < S::kSlots; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&xfull[i])),
+                         "r"(128u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&xempty[i])),
+                         "r"(1u));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&gfull[i])),
+                         "r"(128u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&gempty[i])),
+                         "r"(1u));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done_bar)),
+                     "r"(1u));
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // pixels 130..143 of every input row are never loaded: zero them once so
+    // that the MMAs read finite values there (the gradient copies are zero
+    // at those pixels)
+    for (int i = tid; i < (S::kSlots + S::kMirror) * NX * (kWgPx - kHaloPx); i += kWgThreads) {
+        const int px = kHaloPx + i % (kWgPx - kHaloPx);
+        const int ch = (i / (kWgPx - kHaloPx)) % NX;
+        const int sl = i / ((kWgPx - kHaloPx) * NX);
+        *reinterpret_cast<uint4*>(ring + sl * S::kSlotBytes + ch * S::kStride + px * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+
+    if (warp < 4) {
+        // ---------------------------------------------------------- producer
+        uint32_t xpos = 0, gcnt = 0;
+        auto load_x = [&](int b, int x0, int r, uint32_t pos) -> bool {
+            const uint32_t sl = pos % S::kSlots, u = pos / S::kSlots;
+            if (u > 0 && !mbar_wait_ws(smem_u32(&xempty[sl]), (u - 1) & 1u, &s_abort))
+                return false;
+            const int sr = min(max(r, 0), H - 1);
+            const uint4* src_row = x + ((size_t)b * H + sr) * W * NX;
+            const uint32_t dst = smem_u32(ring + sl * S::kSlotBytes);
+            const uint32_t dst2 = smem_u32(ring + (S::kSlots + sl) * S::kSlotBytes);
+            for (int q = tid; q < kHaloPx * NX; q += 128) {
+                const int ch = q % NX, px = q / NX;
+                const int sx = min(max(x0 - 1 + px, 0), W - 1);
+                const uint4* src = src_row + (size_t)sx * NX + ch;
+                const uint32_t off = (uint32_t)(ch * S::kStride + px * 16);
+                cp_async16(dst + off, src);
+                if (sl < (uint32_t)S::kMirror) cp_async16(dst2 + off, src);
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                             smem_u32(&xfull[sl]))
+                         : "memory");
+            return true;
+        };
+        auto load_g = [&](int b, int x0, int r, uint32_t cnt) -> bool {
+            const uint32_t bb = cnt & 1u, u = cnt >> 1;
+            if (u > 0 && !mbar_wait_ws(smem_u32(&gempty[bb]), (u - 1) & 1u, &s_abort))
+                return false;
+            const uint4* src_row = gy + ((size_t)b * H + r) * W * NG;
+            const uint32_t dst = smem_u32(gbuf + bb * S::kGBytes);
+            const int xend = min(x0 + kTileM, W);
+            for (int q = tid; q < 3 * kWgPx * NG; q += 128) {
+                const int ch = q % NG, k = (q / NG) % kWgPx, dx = q / (NG * kWgPx);
+                const int col = x0 + k - dx;  // gradient pixel at input pixel x0 - 1 + k
+                const bool valid = col >= x0 && col < xend;
+                const uint4* src = src_row + (size_t)(valid ? col : x0) * NG + ch;
+                cp_async16_zfill(dst + (uint32_t)(((dx * NG + ch) * kWgPx + k) * 16), src, valid);
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                             smem_u32(&gfull[bb]))
+                         : "memory");
+            return true;
+        };
+        for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
+            const WsItem it = ws_item(wi, segs, nbands, band, H);
+            ok = load_x(it.b, it.x0, it.y0 - 1, xpos++) && load_x(it.b, it.x0, it.y0, xpos++);
+            for (int r = it.y0; r < it.y1 && ok; ++r) {
+                ok = load_x(it.b, it.x0, r + 1, xpos++) && load_g(it.b, it.x0, r, gcnt++);
+            }
+        }
+        if (!ok) s_abort = 1;  // the MMA thread stops waiting for rows
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (lane == 0) {
+        // --------------------------------------------------------------- MMA
+        constexpr uint32_t idesc = mma_idesc(128, S::kN) | (1u << 15) | (1u << 16);
+        const uint32_t ring_a = smem_u32(ring), g_a = smem_u32(gbuf);
+        uint32_t xpos = 0, gcnt = 0;
+        bool first = true;
+        for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
+            const WsItem it = ws_item(wi, segs, nbands, band, H);
+            const uint32_t p0 = xpos;
+            const int nb = it.y1 - it.y0;
+            for (int i = 0; i < nb && ok; ++i) {
+                // input rows at positions p0 + i .. p0 + i + 2 (the first two
+                // were waited for by the previous row unless i == 0)
+                for (uint32_t pos = p0 + (i == 0 ? 0u : (uint32_t)i + 2u);
+                     pos <= p0 + (uint32_t)i + 2u && ok; ++pos)
+                    ok = mbar_wait_ws(smem_u32(&xfull[pos % S::kSlots]),
+                                      (pos / S::kSlots) & 1u, &s_abort);
+                if (ok)
+                    ok = mbar_wait_ws(smem_u32(&gfull[gcnt & 1u]), (gcnt >> 1) & 1u, &s_abort);
+                if (!ok) break;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t gb_a = g_a + (gcnt & 1u) * S::kGBytes;
+#pragma unroll
+                for (int t = 0; t < S::kTiles; ++t) {
+                    const uint32_t a0 = ring_a + ((p0 + (uint32_t)(i + t)) % S::kSlots) * S::kSlotBytes;
+#pragma unroll
+                    for (int ks = 0; ks < kWgPx / 16; ++ks) {
+                        const uint64_t ad = smem_desc(a0 + ks * 256, 128, S::kStride);
+                        const uint64_t bd = smem_desc(gb_a + ks * 256, 128, S::kStride);
+                        mma_bf16(tmem + (uint32_t)(t * S::kN), ad, bd, idesc,
+                                 (first && ks == 0) ? 0u : 1u);
+                    }
+                }
+                first = false;
+                mma_commit(smem_u32(&gempty[gcnt & 1u]));
+                ++gcnt;
+                // input row p0 + i is not read again; after the last row of the
+                // item neither are the two after it
+                mma_commit(smem_u32(&xempty[(p0 + (uint32_t)i) % S::kSlots]));
+                if (i == nb - 1) {
+                    mma_commit(smem_u32(&xempty[(p0 + (uint32_t)i + 1u) % S::kSlots]));
+                    mma_commit(smem_u32(&xempty[(p0 + (uint32_t)i + 2u) % S::kSlots]));
+                }
+            }
+            xpos = p0 + (uint32_t)nb + 2u;
+        }
+        if (!ok) s_abort = 1;
+        // every MMA issued must have landed before the accumulators are read
+        // or freed, also on the error path
+        mma_commit(smem_u32(&done_bar));
+        const volatile int no_abort = 0;
+        if (!mbar_wait_ws(smem_u32(&done_bar), 0u, &no_abort)) ok = false;
+    }
+    // ------------------------------------------------------------- epilogue
+    if (warp < 4) {
+        // the MMA thread commits done_bar on every path, so this wait ends
+        // once its MMAs have landed (abort only shortens the error path)
+        const volatile int no_abort = 0;
+        const bool landed = mbar_wait_ws(smem_u32(&done_bar), 0u, &no_abort);
+        if (!landed) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int L = warp * 32 + lane;  // TMEM lane = GEMM row
+        const int ci = L % CI, ri = L / CI;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        float* dst = part + (size_t)blockIdx.x * 9 * CO * CI;
+#pragma unroll
+        for (int t = 0; t < S::kTiles; ++t) {
+            // tile t row ri is input row r - 1 + t + ri, i.e. dy index t + ri
+            const int dyi = t + ri;
+            const bool keep = landed && (S::kTiles == 2 ? (t == 0 || ri == 1) : ri < 3);
+#pragma unroll
+            for (int c0 = 0; c0 < S::kN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32_raw(tmem + lane_off + (uint32_t)(t * S::kN + c0), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (keep) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int n = c0 + j, dxi = n / CO, co = n % CO;
+                        dst[((size_t)(3 * dyi + dxi) * CO + co) * CI + ci] = __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        s_abort = 1;
+        if (err) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)S::kTmemCols));
+    }
+}
+
+template <int CI, int CO>
+hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part_len, int B,
+                         int H, int W, int* err, int nsm, int* grid_out, cudaStream_t st)
+{
+    using S = WgSmem<CI, CO>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<CI, CO>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+        attr = true;
+    }
+    const int segs = (W + kTileM - 1) / kTileM;
+    const long rows = (long)B * H * segs;
+    int band = (int)((rows + 4L * nsm - 1) / (4L * nsm));
+    band = band < 2 ? 2 : band > H ? H : band;
+    const int nbands = (H + band - 1) / band;
+    const long items = (long)B * segs * nbands;
+    if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
+    const int grid = items < nsm ? (int)items : nsm;
+    if ((size_t)grid * 9 * CO * CI > part_len) return HP_ERR_INVALID_ARG;
+    conv3x3_wgrad_tc_kernel<CI, CO><<<grid, kWgThreads, S::kBytes, st>>>(
+        (const uint4*)x, (const uint4*)gy, part, H, W, segs, nbands, band, (int)items, err);
+    *grid_out = grid;
     return check_launch();
 }
 
@@ -787,6 +1117,42 @@ hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, voi
 }
 
 int conv_tc_min_width() { return kWsMinWidth; }
+
+// Input gradient of a tensor-core layer (cin -> cout): the convolution of the
+// output gradient gy (BF16 [P][cout]) with wdg = the flipped, transposed
+// weights (BF16 [9][cin][cout], tap 8 - t of the forward's tap t), zero
+// padding, zero bias (cout floats), the ReLU derivative of act (BF16
+// [P][cin], may be null) applied; gx BF16 [P][cin].  Widths from
+// conv_tc_min_width() up.
+hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* zero_bias,
+                                  const void* act, void* gx, int B, int H, int W, int cin,
+                                  int cout, int* err, int nsm, cudaStream_t st)
+{
+    if (W < kWsMinWidth) return HP_ERR_UNSUPPORTED;
+    if (cin == 64 && cout == 64)
+        return launch_ws<64, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+    if (cin == 32 && cout == 64)
+        return launch_ws<64, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+    if (cin == 64 && cout == 32)
+        return launch_ws<32, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+    return HP_ERR_UNSUPPORTED;
+}
+
+// Weight-gradient partial sums of a tensor-core layer (cin -> cout) into
+// part[g][9][cout][cin] for g < *grid_out (one per CTA); x BF16 [P][cin],
+// gy BF16 [P][cout].
+hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, size_t part_len,
+                                  int B, int H, int W, int cin, int cout, int* err, int nsm,
+                                  int* grid_out, cudaStream_t st)
+{
+    if (cin == 64 && cout == 64)
+        return launch_wgrad_t<64, 64>(x, gy, part, part_len, B, H, W, err, nsm, grid_out, st);
+    if (cin == 32 && cout == 64)
+        return launch_wgrad_t<32, 64>(x, gy, part, part_len, B, H, W, err, nsm, grid_out, st);
+    if (cin == 64 && cout == 32)
+        return launch_wgrad_t<64, 32>(x, gy, part, part_len, B, H, W, err, nsm, grid_out, st);
+    return HP_ERR_UNSUPPORTED;
+}
 
 // Last layer of a branch, 32 -> 1, as channel 0 of a 32 -> 16 convolution
 // (w: BF16 [9][16][32], rows 1..15 zero; bias: 16 floats) written as FP32

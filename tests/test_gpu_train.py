@@ -77,6 +77,49 @@ def test_gradient_matches_oracle_backward(dev, lam):
         k += nw + nb
 
 
+@pytest.mark.parametrize("B,ny,nx", [(2, 128, 128), (1, 64, 160)])
+def test_tensor_core_backward_matches_oracle(dev, B, ny, nx):
+    """Sizes where every branch is at least 32 pixels wide, so that every
+    32/64-channel layer takes the tensor-core backward (BF16 gradients, the
+    replicated-border terms added separately); 160 = one full and one partial
+    128-pixel segment."""
+    rng = np.random.default_rng(B + nx)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in C.init_params(seed=13)]
+    u, v, fl = W.training_case(1, max(ny, nx), 700)
+    u, v, fl = u[:, :ny, :nx + 1], v[:, :ny + 1, :nx], fl[:, :ny, :nx]
+    u, v, fl = np.repeat(u, B, 0), np.repeat(v, B, 0), np.ascontiguousarray(np.repeat(fl, B, 0))
+    if B > 1:  # a different field on the second grid
+        u[1] = np.roll(u[1], 17, axis=1)
+        v[1] = np.roll(v[1], 29, axis=0)
+    ud = torch.from_numpy(np.ascontiguousarray(u, np.float32)).to(dev)
+    vd = torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev)
+    fd = torch.from_numpy(fl).to(dev)
+    div = hp.hp_divergence(ud, vd, fd)
+    tgt = torch.from_numpy(rng.standard_normal((B, ny, nx)).astype(np.float32)).to(dev)
+    cnn = hp.CNN(B, ny, nx, params=C.flatten(params))
+    tr = hp.Trainer(cnn, B, ny, nx)
+    lam = 1.0
+    g, loss = tr.gradient(div, fd, tgt, lambda_div=lam)
+    phi_gpu, s = hp.hp_cnn_forward(cnn, div, fd)
+    torch.cuda.synchronize()
+    args = (phi_gpu.cpu().numpy(), div.cpu().numpy(), fl, tgt.cpu().numpy(),
+            [float(x) for x in s.cpu()], lam)
+    L, ref = oracle_gradient(params, *args, act_round=C.round_bf16)
+    assert np.isclose(float(loss.item()), L, rtol=1e-4)
+    _, ref64 = oracle_gradient(params, *args, act_round=None)
+    flat = g.cpu().numpy()
+    k = 0
+    for (w, b), (w64, b64) in zip(ref, ref64):
+        nw, nb = w.size, b.size
+        gw, gb = flat[k:k + nw], flat[k + nw:k + nw + nb]
+        scale = max(np.abs(w).max(), np.abs(b).max())
+        sens = max(np.abs(w - w64).max(), np.abs(b - b64).max())
+        bar = max(5e-2 * scale, 3.0 * sens) + 1e-9
+        assert np.abs(gw - w.ravel()).max() <= bar, (k, np.abs(gw - w.ravel()).max(), scale, sens)
+        assert np.abs(gb - b.ravel()).max() <= bar, (k, np.abs(gb - b.ravel()).max(), scale)
+        k += nw + nb
+
+
 def test_training_reduces_loss_and_jacobi_sweeps(dev):
     from paper_2109_09363_gb300 import training as T
     n = 64
