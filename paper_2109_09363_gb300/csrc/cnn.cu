@@ -814,24 +814,239 @@ __global__ void conv_wgrad_kernel(const GT* __restrict__ gy, const XT* __restric
     }
 }
 
-// grad[co][ci][t] (oracle order) = sum over chunks, in order; bias likewise.
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ partb,
-                                    int nchunks, int CI, int CO, float* __restrict__ gw,
-                                    float* __restrict__ gb)
+// grad[co][ci][t] (oracle order) = sum over chunks; bias likewise.  A block
+// of 256 threads serves 32 outputs; thread group j (of 8) sums the chunks
+// k = j (mod 8) in FP64, and the 8 group sums are added in a fixed order.
+// Launch with ceil((9 CO CI + CO) / 32) blocks of 256 threads.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ part,
+                                                           const float* __restrict__ partb,
+                                                           int nchunks, int CI, int CO,
+                                                           float* __restrict__ gw,
+                                                           float* __restrict__ gb)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double sh[8][32];
+    const int o = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + o;
     const int nw = 9 * CO * CI;
+    double s = 0.0;
     if (q < nw) {
         const int t = q % 9, ci = (q / 9) % CI, co = q / (9 * CI);
-        double s = 0.0;
-        for (int k = 0; k < nchunks; ++k) s += part[((size_t)k * 9 + t) * CO * CI + co * CI + ci];
-        gw[q] = (float)s;
+        const size_t off = (size_t)t * CO * CI + co * CI + ci, step = (size_t)9 * CO * CI;
+        for (int k = j; k < nchunks; k += 8) s += part[(size_t)k * step + off];
     } else if (q < nw + CO) {
         const int co = q - nw;
-        double s = 0.0;
-        for (int k = 0; k < nchunks; ++k) s += partb[(size_t)k * CO + co];
-        gb[co] = (float)s;
+        for (int k = j; k < nchunks; k += 8) s += partb[(size_t)k * CO + co];
     }
+    sh[j][o] = s;
+    __syncthreads();
+    if (j == 0) {
+        double t = 0.0;
+        for (int g = 0; g < 8; ++g) t += sh[g][o];
+        if (q < nw) gw[q] = (float)t;
+        else if (q < nw + CO) gb[q - nw] = (float)t;
+    }
+}
+
+static unsigned reduce_blocks(int ci, int co) { return (unsigned)((9 * co * ci + co + 31) / 32); }
+
+// The three (position p, tap offset d) pairs through which a 3-tap
+// convolution with replicated borders along an axis of length n reads
+// position j: clamp(p + d) == j (interior: p = j - d; at an end one tap is
+// clamped onto j; n == 1: every tap).
+struct AxisPairs {
+    int p[3], d[3];
+};
+
+__device__ __forceinline__ AxisPairs axis_pairs(int j, int n)
+{
+    AxisPairs a;
+    if (n == 1) {
+        a.p[0] = 0; a.d[0] = -1; a.p[1] = 0; a.d[1] = 0; a.p[2] = 0; a.d[2] = 1;
+    } else if (j == 0) {
+        a.p[0] = 1; a.d[0] = -1; a.p[1] = 0; a.d[1] = 0; a.p[2] = 0; a.d[2] = -1;
+    } else if (j == n - 1) {
+        a.p[0] = n - 1; a.d[0] = 1; a.p[1] = n - 1; a.d[1] = 0; a.p[2] = n - 2; a.d[2] = 1;
+    } else {
+        a.p[0] = j + 1; a.d[0] = -1; a.p[1] = j; a.d[1] = 0; a.p[2] = j - 1; a.d[2] = 1;
+    }
+    return a;
+}
+
+// Input gradient of the last layer of a branch (32 -> 1): gx[j][ci] = sum
+// over the 9 pairs of w[tap][ci] * gy[p], optionally zeroed where act (BF16
+// [P][32]) is not positive.  Thread = (pixel, chunk of 8 channels), so that
+// a warp stores 8 whole pixels.  w: FP32 [9][32].
+template <typename OT>
+__global__ void dgrad_last_kernel(const float* __restrict__ gy, const float* __restrict__ w,
+                                  OT* __restrict__ gx, int B, int H, int W,
+                                  const __nv_bfloat16* __restrict__ act)
+{
+    __shared__ float sw[9 * 32];
+    for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) sw[i] = w[i];
+    __syncthreads();
+    const long P = (long)B * H * W;
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P * 4) return;
+    const long pix = q >> 2;
+    const int c = (int)(q & 3);
+    const int b = (int)(pix / ((long)H * W));
+    const int rem = (int)(pix - (long)b * H * W);
+    const int jy = rem / W, jx = rem - jy * W;
+    const AxisPairs ay = axis_pairs(jy, H), ax = axis_pairs(jx, W);
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float* g = gy + (size_t)b * H * W;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float gv = g[(size_t)ay.p[u] * W + ax.p[v]];
+            const float* wt = sw + (3 * (ay.d[u] + 1) + ax.d[v] + 1) * 32 + 8 * c;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = fmaf(wt[k], gv, acc[k]);
+        }
+    const size_t o = (size_t)pix * 32 + 8 * c;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool keep = !act || __bfloat162float(act[o + k]) > 0.0f;
+        st_val(gx, o + k, keep ? acc[k] : 0.0f);
+    }
+}
+
+// Gradient of input channel 2 (the up-sampled coarser output) of the first
+// layer of a branch (3 -> 32): gx2[j] = sum over the 9 pairs of
+// sum_co w[tap][co][2] * gy[p][co].  w: FP32 [9][32][3]; gx2 FP32 [P].
+template <typename GT>
+__global__ void dgrad_first_ch2_kernel(const GT* __restrict__ gy, const float* __restrict__ w,
+                                       float* __restrict__ gx2, int B, int H, int W)
+{
+    __shared__ float sw[9 * 32];
+    for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) sw[i] = w[i * 3 + 2];
+    __syncthreads();
+    const long P = (long)B * H * W;
+    const long pix = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= P) return;
+    const int b = (int)(pix / ((long)H * W));
+    const int rem = (int)(pix - (long)b * H * W);
+    const int jy = rem / W, jx = rem - jy * W;
+    const AxisPairs ay = axis_pairs(jy, H), ax = axis_pairs(jx, W);
+    float acc = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const size_t src = (((size_t)b * H + ay.p[u]) * W + ax.p[v]) * 32;
+            const float* wt = sw + (3 * (ay.d[u] + 1) + ax.d[v] + 1) * 32;
+            if constexpr (sizeof(GT) == 2) {
+                const uint4* g4 = reinterpret_cast<const uint4*>(gy + src);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint4 t = g4[k];
+                    const uint32_t e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        acc = fmaf(wt[8 * k + 2 * h], __uint_as_float(e[h] << 16), acc);
+                        acc = fmaf(wt[8 * k + 2 * h + 1], __uint_as_float(e[h] & 0xFFFF0000u), acc);
+                    }
+                }
+            } else {
+#pragma unroll 8
+                for (int co = 0; co < 32; ++co) acc = fmaf(wt[co], ld_act(gy, src + co), acc);
+            }
+        }
+    gx2[pix] = acc;
+}
+
+// Weight and bias gradient of the last layer of a branch (32 -> 1) over the
+// g-th of G equal ranges of image rows: part[g][tap][ci], partb[g].  Warp
+// = row offset dy, lane = input channel; every input pixel is read once per
+// warp and feeds the three column taps through a sliding window of the
+// output gradient (with the replicated-border terms at both row ends).
+__global__ void __launch_bounds__(96) wgrad_last_kernel(const float* __restrict__ gy,
+                                                        const __nv_bfloat16* __restrict__ x,
+                                                        float* __restrict__ part,
+                                                        float* __restrict__ partb, int B, int H,
+                                                        int W)
+{
+    const int dyo = (int)(threadIdx.x >> 5) - 1, ci = threadIdx.x & 31;
+    const long R = (long)B * H;
+    const long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+    float am = 0.0f, a0 = 0.0f, ap = 0.0f, bsum = 0.0f;
+    for (long r = r0; r < r1; ++r) {
+        const int b = (int)(r / H), y = (int)(r - (long)b * H);
+        const int ys = min(max(y + dyo, 0), H - 1);
+        const float* g = gy + (size_t)r * W;
+        const __nv_bfloat16* xr = x + ((size_t)b * H + ys) * W * 32 + ci;
+        float gl = 0.0f, gc = g[0];
+#pragma unroll 4
+        for (int xs = 0; xs < W; ++xs) {
+            const float gr = xs + 1 < W ? g[xs + 1] : 0.0f;
+            const float X = __bfloat162float(xr[(size_t)xs * 32]);
+            am = fmaf(gr + (xs == 0 ? gc : 0.0f), X, am);
+            a0 = fmaf(gc, X, a0);
+            ap = fmaf(gl + (xs == W - 1 ? gc : 0.0f), X, ap);
+            bsum += gc;
+            gl = gc;
+            gc = gr;
+        }
+    }
+    float* dst = part + (size_t)blockIdx.x * 9 * 32;
+    const int t0 = 3 * (dyo + 1);
+    dst[(t0 + 0) * 32 + ci] = am;
+    dst[(t0 + 1) * 32 + ci] = a0;
+    dst[(t0 + 2) * 32 + ci] = ap;
+    if (dyo == 0 && ci == 0) partb[blockIdx.x] = bsum;
+}
+
+// Weight and bias gradient of the first layer of a branch (CX -> 32, input
+// FP32 [P][CX]) over the g-th of G row ranges: part[g][tap][co][ci],
+// partb[g][co].  Warp = row offset dy, lane = output channel; sliding window
+// of the output gradient as in wgrad_last_kernel.
+template <int CX, typename GT>
+__global__ void __launch_bounds__(96) wgrad_first_kernel(const GT* __restrict__ gy,
+                                                         const float* __restrict__ x,
+                                                         float* __restrict__ part,
+                                                         float* __restrict__ partb, int B, int H,
+                                                         int W)
+{
+    const int dyo = (int)(threadIdx.x >> 5) - 1, co = threadIdx.x & 31;
+    const long R = (long)B * H;
+    const long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+    float am[CX], a0[CX], ap[CX];
+#pragma unroll
+    for (int c = 0; c < CX; ++c) am[c] = a0[c] = ap[c] = 0.0f;
+    float bsum = 0.0f;
+    for (long r = r0; r < r1; ++r) {
+        const int b = (int)(r / H), y = (int)(r - (long)b * H);
+        const int ys = min(max(y + dyo, 0), H - 1);
+        const size_t g0 = (size_t)r * W * 32 + co;
+        const float* xr = x + ((size_t)b * H + ys) * W * CX;
+        float gl = 0.0f, gc = ld_act(gy, g0);
+#pragma unroll 4
+        for (int xs = 0; xs < W; ++xs) {
+            const float gr = xs + 1 < W ? ld_act(gy, g0 + (size_t)(xs + 1) * 32) : 0.0f;
+            const float gm = gr + (xs == 0 ? gc : 0.0f);
+            const float gq = gl + (xs == W - 1 ? gc : 0.0f);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const float X = xr[(size_t)xs * CX + c];
+                am[c] = fmaf(gm, X, am[c]);
+                a0[c] = fmaf(gc, X, a0[c]);
+                ap[c] = fmaf(gq, X, ap[c]);
+            }
+            bsum += gc;
+            gl = gc;
+            gc = gr;
+        }
+    }
+    float* dst = part + (size_t)blockIdx.x * 9 * 32 * CX;
+    const int t0 = 3 * (dyo + 1);
+#pragma unroll
+    for (int c = 0; c < CX; ++c) {
+        dst[((t0 + 0) * 32 + co) * CX + c] = am[c];
+        dst[((t0 + 1) * 32 + co) * CX + c] = a0[c];
+        dst[((t0 + 2) * 32 + co) * CX + c] = ap[c];
+    }
+    if (dyo == 0) partb[(size_t)blockIdx.x * 32 + co] = bsum;
 }
 
 // Border terms of the input gradient of a 3 x 3 convolution with replicated
@@ -1292,7 +1507,8 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     size_t nchunks = (P + kWgradChunk - 1) / kWgradChunk;
     if (nchunks < (size_t)cnn->num_sms) nchunks = (size_t)cnn->num_sms;
     t->part_len = nchunks * 9 * 64 * 64;
-    t->partb_len = nchunks * 64;
+    // bias partials of up to 16 row blocks per SM (sliding-window kernels)
+    t->partb_len = (nchunks > 16 * (size_t)cnn->num_sms ? nchunks : 16 * (size_t)cnn->num_sms) * 64;
     al((void**)&t->part, t->part_len * 4);
     al((void**)&t->partb, t->partb_len * 4);
     al((void**)&t->rbuf, P * 4);
@@ -1383,8 +1599,6 @@ static hp_status dgrad_dispatch(int ci, int co, const float* gy, const float* w,
     if (ci == 64 && co == 64) return dgrad<64, 64>(gy, w, gx, B, H, W, nsm, st);
     if (ci == 32 && co == 64) return dgrad<32, 64>(gy, w, gx, B, H, W, nsm, st);
     if (ci == 64 && co == 32) return dgrad<64, 32>(gy, w, gx, B, H, W, nsm, st);
-    if (ci == 32 && co == 1) return dgrad<32, 1>(gy, w, gx, B, H, W, nsm, st);
-    if (ci == 3 && co == 32) return dgrad<3, 32>(gy, w, gx, B, H, W, nsm, st);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1400,23 +1614,81 @@ static hp_status wgrad_t(hp_trainer* t, const GT* gy, const XT* x, float* gw, fl
         gy, x, t->part, t->partb, B, H, W, kWgradChunk);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
-    const int n = 9 * CO * CI + CO;
-    wgrad_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->part, t->partb, nchunks, CI, CO, gw, gb);
+    wgrad_reduce_kernel<<<reduce_blocks(CI, CO), 256, 0, st>>>(t->part, t->partb, nchunks, CI, CO,
+                                                             gw, gb);
     return check_launch();
 }
 
-static hp_status wgrad_dispatch(hp_trainer* t, int l, const float* gy, const void* x, float* gw,
-                                float* gb, int B, int H, int W, cudaStream_t st)
+// row ranges of the sliding-window weight gradients: 16 blocks of 3 warps
+// per SM (a block scans its rows serially; the latency of one scan is hidden
+// by the others)
+static int row_blocks(hp_trainer* t, long rows)
+{
+    const long g = 16L * t->cnn->num_sms;
+    return (int)(rows < g ? rows : g);
+}
+
+// weight and bias gradient of the last layer of a branch (32 -> 1)
+static hp_status wgrad_last(hp_trainer* t, int l, const float* gy, float* gw, float* gb, int B,
+                            int H, int W, cudaStream_t st)
+{
+    const int G = row_blocks(t, (long)B * H);
+    if ((size_t)G * 9 * 32 > t->part_len || (size_t)G > t->partb_len) return HP_ERR_INVALID_ARG;
+    wgrad_last_kernel<<<G, 96, 0, st>>>(gy, (const __nv_bfloat16*)t->act[l - 1], t->part,
+                                        t->partb, B, H, W);
+    wgrad_reduce_kernel<<<reduce_blocks(32, 1), 256, 0, st>>>(t->part, t->partb, G, 32, 1, gw, gb);
+    return check_launch();
+}
+
+// weight and bias gradient of the first layer of a branch (2 or 3 -> 32)
+template <typename GT>
+static hp_status wgrad_first(hp_trainer* t, int k, int l, const GT* gy, float* gw, float* gb,
+                             int B, int H, int W, cudaStream_t st)
+{
+    const int cx = kSpec[l].cin;
+    const int G = row_blocks(t, (long)B * H);
+    if ((size_t)G * 9 * 32 * cx > t->part_len || (size_t)G * 32 > t->partb_len)
+        return HP_ERR_INVALID_ARG;
+    if (cx == 3)
+        wgrad_first_kernel<3, GT><<<G, 96, 0, st>>>(gy, t->xin[k], t->part, t->partb, B, H, W);
+    else
+        wgrad_first_kernel<2, GT><<<G, 96, 0, st>>>(gy, t->xin[k], t->part, t->partb, B, H, W);
+    wgrad_reduce_kernel<<<reduce_blocks(cx, 32), 256, 0, st>>>(t->part, t->partb, G, cx, 32, gw,
+                                                              gb);
+    return check_launch();
+}
+
+// gradient of input channel 2 of a first layer into t->gsmall (FP32 [P])
+template <typename GT>
+static hp_status dgrad_first_ch2(hp_trainer* t, int l, const GT* gy, int B, int H, int W,
+                                 cudaStream_t st)
+{
+    const long P = (long)B * H * W;
+    dgrad_first_ch2_kernel<GT><<<(unsigned)((P + 255) / 256), 256, 0, st>>>(gy, t->wt[l],
+                                                                          t->gsmall, B, H, W);
+    return check_launch();
+}
+
+template <typename OT>
+static hp_status dgrad_last(hp_trainer* t, int l, const float* gy, OT* gx, int B, int H, int W,
+                            const __nv_bfloat16* act, cudaStream_t st)
+{
+    const long n = (long)B * H * W * 4;
+    dgrad_last_kernel<OT><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gy, t->wt[l], gx, B, H, W,
+                                                                      act);
+    return check_launch();
+}
+
+static hp_status wgrad_dispatch(hp_trainer* t, int k, int l, const float* gy, const void* x,
+                                float* gw, float* gb, int B, int H, int W, cudaStream_t st)
 {
     const int ci = kSpec[l].cin, co = kSpec[l].cout;
     const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
     if (ci == 64 && co == 64) return wgrad_t<64, 64, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
     if (ci == 32 && co == 64) return wgrad_t<32, 64, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
     if (ci == 64 && co == 32) return wgrad_t<64, 32, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
-    if (ci == 32 && co == 1) return wgrad_t<32, 1, 1, 1>(t, gy, xb, gw, gb, B, H, W, st);
-    const float* xf = (const float*)x;
-    if (ci == 3 && co == 32) return wgrad_t<3, 32, 1, 1>(t, gy, xf, gw, gb, B, H, W, st);
-    if (ci == 2 && co == 32) return wgrad_t<2, 32, 1, 1>(t, gy, xf, gw, gb, B, H, W, st);
+    if (ci == 32 && co == 1) return wgrad_last(t, l, gy, gw, gb, B, H, W, st);
+    if (co == 32 && (ci == 3 || ci == 2)) return wgrad_first(t, k, l, gy, gw, gb, B, H, W, st);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1427,12 +1699,9 @@ static hp_status first_layer_bf16(hp_trainer* t, int k, int l, const __nv_bfloat
                                   int H, int W, cudaStream_t st)
 {
     float* gw = t->grad + layer_offset(l);
-    float* gb = gw + layer_wcount(l);
-    hp_status rc = kSpec[l].cin == 3
-                       ? wgrad_t<3, 32, 1, 1>(t, gy, (const float*)t->xin[k], gw, gb, B, H, W, st)
-                       : wgrad_t<2, 32, 1, 1>(t, gy, (const float*)t->xin[k], gw, gb, B, H, W, st);
+    hp_status rc = wgrad_first(t, k, l, gy, gw, gw + layer_wcount(l), B, H, W, st);
     if (rc != HP_OK || k == 0) return rc;
-    return dgrad<3, 32>(gy, t->wt[l], t->gsmall, B, H, W, t->cnn->num_sms, st);
+    return dgrad_first_ch2(t, l, gy, B, H, W, st);
 }
 
 // One branch on the tensor cores (width >= conv_tc_min_width()): gradients
@@ -1446,13 +1715,11 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
     // last layer (32 -> 1, CUDA cores): weight gradient from the FP32 output
     // gradient, input gradient into BF16
     float* gw = t->grad + layer_offset(llast);
-    hp_status rc = wgrad_t<32, 1, 1, 1>(t, gout, (const __nv_bfloat16*)t->act[llast - 1], gw,
-                                        gw + layer_wcount(llast), B, H, W, st);
+    hp_status rc = wgrad_last(t, llast, gout, gw, gw + layer_wcount(llast), B, H, W, st);
     if (rc != HP_OK) return rc;
     const __nv_bfloat16* mask_last =
         kSpec[llast - 1].relu ? (const __nv_bfloat16*)t->act[llast - 1] : nullptr;
-    rc = dgrad<32, 1, float, __nv_bfloat16>(gout, t->wt[llast], gbuf[0], B, H, W, c->num_sms, st,
-                                            mask_last);
+    rc = dgrad_last(t, llast, gout, gbuf[0], B, H, W, mask_last, st);
     if (rc != HP_OK) return rc;
     int cur = 0;
     for (int l = llast - 1; l > lfirst; --l) {
@@ -1468,9 +1735,8 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
         else
             bias_grad_kernel<32><<<grid, 256, 0, st>>>((const uint4*)gy, P, t->partb);
         gw = t->grad + layer_offset(l);
-        const int n = 9 * co * ci + co;
-        wgrad_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->part, t->partb, grid, ci, co, gw,
-                                                             gw + layer_wcount(l));
+        wgrad_reduce_kernel<<<reduce_blocks(ci, co), 256, 0, st>>>(t->part, t->partb, grid, ci, co,
+                                                                   gw, gw + layer_wcount(l));
         if ((rc = check_launch()) != HP_OK) return rc;
         // input gradient with the ReLU derivative of layer l - 1
         const __nv_bfloat16* act = kSpec[l - 1].relu ? x : nullptr;
@@ -1515,7 +1781,7 @@ static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
             if (k > 0) {
                 const long Pc = P / 4;
                 upsample_adjoint_kernel<<<(unsigned)((Pc + 255) / 256), 256, 0, st>>>(
-                    t->gsmall, 3, 2, t->g[cur ^ 1], s.batch, H / 2, W / 2);
+                    t->gsmall, 1, 0, t->g[cur ^ 1], s.batch, H / 2, W / 2);
                 if ((rc = check_launch()) != HP_OK) return rc;
                 cur ^= 1;
             }
@@ -1532,19 +1798,21 @@ static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
             }
             const void* x = l == lfirst ? (const void*)t->xin[k] : t->act[l - 1];
             float* gw = t->grad + layer_offset(l);
-            rc = wgrad_dispatch(t, l, gy, x, gw, gw + layer_wcount(l), s.batch, H, W, st);
+            rc = wgrad_dispatch(t, k, l, gy, x, gw, gw + layer_wcount(l), s.batch, H, W, st);
             if (rc != HP_OK) return rc;
             if (l > lfirst) {
-                rc = dgrad_dispatch(ci, co, gy, t->wt[l], t->g[cur ^ 1], s.batch, H, W, c->num_sms, st);
+                rc = co == 1 ? dgrad_last(t, l, gy, t->g[cur ^ 1], s.batch, H, W, nullptr, st)
+                             : dgrad_dispatch(ci, co, gy, t->wt[l], t->g[cur ^ 1], s.batch, H, W,
+                                              c->num_sms, st);
                 if (rc != HP_OK) return rc;
                 cur ^= 1;
             } else if (k > 0) {
                 // gradient of the up-sampled coarser output (input channel 2)
-                rc = dgrad_dispatch(3, 32, gy, t->wt[l], t->gsmall, s.batch, H, W, c->num_sms, st);
+                rc = dgrad_first_ch2(t, l, gy, s.batch, H, W, st);
                 if (rc != HP_OK) return rc;
                 const long Pc = P / 4;
                 upsample_adjoint_kernel<<<(unsigned)((Pc + 255) / 256), 256, 0, st>>>(
-                    t->gsmall, 3, 2, t->g[cur ^ 1], s.batch, H / 2, W / 2);
+                    t->gsmall, 1, 0, t->g[cur ^ 1], s.batch, H / 2, W / 2);
                 if ((rc = check_launch()) != HP_OK) return rc;
                 cur ^= 1;
             }

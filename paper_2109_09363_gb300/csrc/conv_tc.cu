@@ -673,6 +673,21 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             const WsItem it = ws_item(wi, segs, nbands, band, H);
             for (int yy = it.y0; yy < it.y1; ++yy, ++og) {
                 const uint32_t sl = og % kAccSlots;
+                // DGRAD: this lane's activation chunks of the row, loaded while
+                // the MMAs of the row are still running
+                uint4 act_r[DGRAD ? CPP : 1];
+                if constexpr (DGRAD) {
+                    if (act) {
+#pragma unroll
+                        for (int i = 0; i < CPP; ++i) {
+                            const int k = lane + 32 * i;
+                            const int p = k / CPP, c = k % CPP;
+                            const int xo = it.x0 + warp * 32 + p;
+                            act_r[i] = xo < W ? act[(((size_t)it.b * H + yy) * W + xo) * CPP + c]
+                                              : make_uint4(0u, 0u, 0u, 0u);
+                        }
+                    }
+                }
                 ok = mbar_wait_ws(smem_u32(&outf_bar[sl]), (og / kAccSlots) & 1u, &s_abort);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -732,9 +747,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     if (it.x0 + warp * 32 + p < W) {
                         if constexpr (DGRAD) {
                             if (act) {
-                                const size_t q = (((size_t)it.b * H + yy) * W + it.x0 + warp * 32 +
-                                                  p) * CPP + c;
-                                const uint4 a = act[q];
+                                const uint4 a = act_r[i];
                                 v.x = relu_mask2(v.x, a.x);
                                 v.y = relu_mask2(v.y, a.y);
                                 v.z = relu_mask2(v.z, a.z);
