@@ -956,22 +956,27 @@ __global__ void dgrad_first_ch2_kernel(const GT* __restrict__ gy, const float* _
     gx2[pix] = acc;
 }
 
+// Row groups per block of the sliding-window weight gradients.
+constexpr int kRowGroups = 8;
+
 // Weight and bias gradient of the last layer of a branch (32 -> 1) over the
-// g-th of G equal ranges of image rows: part[g][tap][ci], partb[g].  Warp
-// = row offset dy, lane = input channel; every input pixel is read once per
-// warp and feeds the three column taps through a sliding window of the
-// output gradient (with the replicated-border terms at both row ends).
-__global__ void __launch_bounds__(96) wgrad_last_kernel(const float* __restrict__ gy,
-                                                        const __nv_bfloat16* __restrict__ x,
-                                                        float* __restrict__ part,
-                                                        float* __restrict__ partb, int B, int H,
-                                                        int W)
+// g-th of G equal ranges of image rows: part[g][tap][ci], partb[g].  Block =
+// kRowGroups x 3 warps: row group rg takes every kRowGroups-th row of the
+// range, warp = row offset dy, lane = input channel; every input pixel is
+// read once per warp and feeds the three column taps through a sliding
+// window of the output gradient (with the replicated-border terms at both row
+// ends); the row groups are added in a fixed order.
+__global__ void __launch_bounds__(96 * kRowGroups) wgrad_last_kernel(
+    const float* __restrict__ gy, const __nv_bfloat16* __restrict__ x, float* __restrict__ part,
+    float* __restrict__ partb, int B, int H, int W)
 {
-    const int dyo = (int)(threadIdx.x >> 5) - 1, ci = threadIdx.x & 31;
+    __shared__ float sh[kRowGroups][4][96];
+    const int rg = threadIdx.x / 96, tw = threadIdx.x % 96;
+    const int dyo = tw / 32 - 1, ci = tw & 31;
     const long R = (long)B * H;
     const long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
     float am = 0.0f, a0 = 0.0f, ap = 0.0f, bsum = 0.0f;
-    for (long r = r0; r < r1; ++r) {
+    for (long r = r0 + rg; r < r1; r += kRowGroups) {
         const int b = (int)(r / H), y = (int)(r - (long)b * H);
         const int ys = min(max(y + dyo, 0), H - 1);
         const float* g = gy + (size_t)r * W;
@@ -989,33 +994,45 @@ __global__ void __launch_bounds__(96) wgrad_last_kernel(const float* __restrict_
             gc = gr;
         }
     }
-    float* dst = part + (size_t)blockIdx.x * 9 * 32;
-    const int t0 = 3 * (dyo + 1);
-    dst[(t0 + 0) * 32 + ci] = am;
-    dst[(t0 + 1) * 32 + ci] = a0;
-    dst[(t0 + 2) * 32 + ci] = ap;
-    if (dyo == 0 && ci == 0) partb[blockIdx.x] = bsum;
+    sh[rg][0][tw] = am;
+    sh[rg][1][tw] = a0;
+    sh[rg][2][tw] = ap;
+    sh[rg][3][tw] = bsum;
+    __syncthreads();
+    if (rg == 0) {
+        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int k = 0; k < kRowGroups; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] += sh[k][c][tw];
+        float* dst = part + (size_t)blockIdx.x * 9 * 32;
+        const int t0 = 3 * (dyo + 1);
+        dst[(t0 + 0) * 32 + ci] = v[0];
+        dst[(t0 + 1) * 32 + ci] = v[1];
+        dst[(t0 + 2) * 32 + ci] = v[2];
+        if (dyo == 0 && ci == 0) partb[blockIdx.x] = v[3];
+    }
 }
 
 // Weight and bias gradient of the first layer of a branch (CX -> 32, input
 // FP32 [P][CX]) over the g-th of G row ranges: part[g][tap][co][ci],
-// partb[g][co].  Warp = row offset dy, lane = output channel; sliding window
-// of the output gradient as in wgrad_last_kernel.
+// partb[g][co].  Same organisation as wgrad_last_kernel with lane = output
+// channel.
 template <int CX, typename GT>
-__global__ void __launch_bounds__(96) wgrad_first_kernel(const GT* __restrict__ gy,
-                                                         const float* __restrict__ x,
-                                                         float* __restrict__ part,
-                                                         float* __restrict__ partb, int B, int H,
-                                                         int W)
+__global__ void __launch_bounds__(96 * kRowGroups) wgrad_first_kernel(
+    const GT* __restrict__ gy, const float* __restrict__ x, float* __restrict__ part,
+    float* __restrict__ partb, int B, int H, int W)
 {
-    const int dyo = (int)(threadIdx.x >> 5) - 1, co = threadIdx.x & 31;
+    constexpr int NV = 3 * CX + 1;
+    __shared__ float sh[kRowGroups][NV][96];
+    const int rg = threadIdx.x / 96, tw = threadIdx.x % 96;
+    const int dyo = tw / 32 - 1, co = tw & 31;
     const long R = (long)B * H;
     const long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
     float am[CX], a0[CX], ap[CX];
 #pragma unroll
     for (int c = 0; c < CX; ++c) am[c] = a0[c] = ap[c] = 0.0f;
     float bsum = 0.0f;
-    for (long r = r0; r < r1; ++r) {
+    for (long r = r0 + rg; r < r1; r += kRowGroups) {
         const int b = (int)(r / H), y = (int)(r - (long)b * H);
         const int ys = min(max(y + dyo, 0), H - 1);
         const size_t g0 = (size_t)r * W * 32 + co;
@@ -1038,26 +1055,44 @@ __global__ void __launch_bounds__(96) wgrad_first_kernel(const GT* __restrict__ 
             gc = gr;
         }
     }
-    float* dst = part + (size_t)blockIdx.x * 9 * 32 * CX;
-    const int t0 = 3 * (dyo + 1);
 #pragma unroll
     for (int c = 0; c < CX; ++c) {
-        dst[((t0 + 0) * 32 + co) * CX + c] = am[c];
-        dst[((t0 + 1) * 32 + co) * CX + c] = a0[c];
-        dst[((t0 + 2) * 32 + co) * CX + c] = ap[c];
+        sh[rg][3 * c + 0][tw] = am[c];
+        sh[rg][3 * c + 1][tw] = a0[c];
+        sh[rg][3 * c + 2][tw] = ap[c];
     }
-    if (dyo == 0) partb[(size_t)blockIdx.x * 32 + co] = bsum;
+    sh[rg][3 * CX][tw] = bsum;
+    __syncthreads();
+    if (rg == 0) {
+        float v[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[c] = 0.0f;
+        for (int k = 0; k < kRowGroups; ++k)
+#pragma unroll
+            for (int c = 0; c < NV; ++c) v[c] += sh[k][c][tw];
+        float* dst = part + (size_t)blockIdx.x * 9 * 32 * CX;
+        const int t0 = 3 * (dyo + 1);
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            dst[((t0 + 0) * 32 + co) * CX + c] = v[3 * c + 0];
+            dst[((t0 + 1) * 32 + co) * CX + c] = v[3 * c + 1];
+            dst[((t0 + 2) * 32 + co) * CX + c] = v[3 * c + 2];
+        }
+        if (dyo == 0) partb[(size_t)blockIdx.x * 32 + co] = v[3 * CX];
+    }
 }
 
 // Border terms of the input gradient of a 3 x 3 convolution with replicated
 // borders.  The forward reads x at clamp(p + d); extended by a ring of ghost
 // pixels holding the replicated values, it is a plain convolution, whose
-// transpose puts w[d]^T gy[q - d] on every extended pixel q.  The tensor-core
-// pass computes that transpose with zero padding on the image itself; an
-// input pixel j on the border also collects the ghost pixels q outside the
-// image with clamp(q) = j.  One warp per border pixel, lanes over the input
-// channels; the ghost terms get the ReLU derivative of act (may be null) and
-// are added to gx (BF16 [P][CI], rounded again).  w: FP32 [9][CO][CI].
+// transpose puts w[d]^T gy[q - d] on every extended pixel q, and an input
+// pixel j collects the ghost pixels q with clamp(q) = j.  The tensor-core
+// pass computes the transpose with zero padding on the image and folds the
+// ghost rows -1 and H into rows 0 and H - 1; this kernel adds the ghost
+// pixels in columns -1 and W (corner ghosts included) to the first and last
+// column.  One warp per pixel, lanes over the input channels; the terms get
+// the ReLU derivative of act (may be null) and are added to gx (BF16 [P][CI],
+// rounded again).  w: FP32 [9][CO][CI].
 template <int CI, int CO>
 __global__ void dgrad_border_kernel(const __nv_bfloat16* __restrict__ gy,
                                     const float* __restrict__ w,
@@ -1066,17 +1101,13 @@ __global__ void dgrad_border_kernel(const __nv_bfloat16* __restrict__ gy,
 {
     constexpr int PER = CI / 32;
     const int ncol = W > 1 ? 2 : 1;
-    const int nrow_px = H > 1 ? 2 * W : W;
-    const long per_img = nrow_px + (long)max(H - 2, 0) * ncol;
+    const long per_img = (long)H * ncol;
     const long e_all = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (e_all >= (long)B * per_img) return;
     const int b = (int)(e_all / per_img);
     const int e = (int)(e_all - (long)b * per_img);
-    int jy, jx;
-    if (e < W) { jy = 0; jx = e; }
-    else if (e < nrow_px) { jy = H - 1; jx = e - W; }
-    else { const int e2 = e - nrow_px; jy = 1 + e2 / ncol; jx = (e2 % ncol) ? W - 1 : 0; }
+    const int jy = e / ncol, jx = (e % ncol) ? W - 1 : 0;
     float acc[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
@@ -1085,10 +1116,9 @@ __global__ void dgrad_border_kernel(const __nv_bfloat16* __restrict__ gy,
     for (int a = 0; a < 3; ++a) {
         const int qy = gys[a];
         if (a > 0 && qy == jy) continue;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 1; c < 3; ++c) {
             const int qx = gxs[c];
-            if (c > 0 && qx == jx) continue;
-            if (qy == jy && qx == jx) continue;  // inside: the tensor-core pass has it
+            if (qx == jx) continue;  // only ghost columns; the rest is the tensor-core pass
             for (int dy = -1; dy <= 1; ++dy) {
                 const int py = qy - dy;
                 if (py < 0 || py >= H) continue;
@@ -1113,37 +1143,6 @@ __global__ void dgrad_border_kernel(const __nv_bfloat16* __restrict__ gy,
         const int ci = lane + 32 * k;
         if (act && !(__bfloat162float(act[q + ci]) > 0.0f)) continue;
         gx[q + ci] = __float2bfloat16_rn(__bfloat162float(gx[q + ci]) + acc[k]);
-    }
-}
-
-// Bias gradient partial sums: partb[g][co] = sum of gy[p][co] (BF16 [P][CO])
-// over the g-th of G equal pixel ranges, in a fixed order.
-template <int CO>
-__global__ void __launch_bounds__(256) bias_grad_kernel(const uint4* __restrict__ gy, long P,
-                                                        float* __restrict__ partb)
-{
-    constexpr int NCH = CO / 8, PAR = 256 / NCH;
-    __shared__ float sh[PAR][CO + 1];
-    const int G = gridDim.x, g = blockIdx.x;
-    const long p0 = P * g / G, p1 = P * (g + 1) / G;
-    const int ch = threadIdx.x % NCH, pl = threadIdx.x / NCH;
-    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (long p = p0 + pl; p < p1; p += PAR) {
-        const uint4 v = gy[(size_t)p * NCH + ch];
-        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            acc[2 * k] += __uint_as_float(u[k] << 16);
-            acc[2 * k + 1] += __uint_as_float(u[k] & 0xFFFF0000u);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sh[pl][ch * 8 + k] = acc[k];
-    __syncthreads();
-    if (threadIdx.x < CO) {
-        float t = 0.0f;
-        for (int i = 0; i < PAR; ++i) t += sh[i][threadIdx.x];
-        partb[(size_t)g * CO + threadIdx.x] = t;
     }
 }
 
@@ -1619,12 +1618,12 @@ static hp_status wgrad_t(hp_trainer* t, const GT* gy, const XT* x, float* gw, fl
     return check_launch();
 }
 
-// row ranges of the sliding-window weight gradients: 16 blocks of 3 warps
-// per SM (a block scans its rows serially; the latency of one scan is hidden
-// by the others)
+// row ranges of the sliding-window weight gradients: two blocks of
+// kRowGroups x 3 warps per SM (each warp scans its rows serially; the
+// latency of one scan is hidden by the others)
 static int row_blocks(hp_trainer* t, long rows)
 {
-    const long g = 16L * t->cnn->num_sms;
+    const long g = 2L * t->cnn->num_sms;
     return (int)(rows < g ? rows : g);
 }
 
@@ -1634,8 +1633,8 @@ static hp_status wgrad_last(hp_trainer* t, int l, const float* gy, float* gw, fl
 {
     const int G = row_blocks(t, (long)B * H);
     if ((size_t)G * 9 * 32 > t->part_len || (size_t)G > t->partb_len) return HP_ERR_INVALID_ARG;
-    wgrad_last_kernel<<<G, 96, 0, st>>>(gy, (const __nv_bfloat16*)t->act[l - 1], t->part,
-                                        t->partb, B, H, W);
+    wgrad_last_kernel<<<G, 96 * kRowGroups, 0, st>>>(gy, (const __nv_bfloat16*)t->act[l - 1],
+                                                     t->part, t->partb, B, H, W);
     wgrad_reduce_kernel<<<reduce_blocks(32, 1), 256, 0, st>>>(t->part, t->partb, G, 32, 1, gw, gb);
     return check_launch();
 }
@@ -1650,9 +1649,11 @@ static hp_status wgrad_first(hp_trainer* t, int k, int l, const GT* gy, float* g
     if ((size_t)G * 9 * 32 * cx > t->part_len || (size_t)G * 32 > t->partb_len)
         return HP_ERR_INVALID_ARG;
     if (cx == 3)
-        wgrad_first_kernel<3, GT><<<G, 96, 0, st>>>(gy, t->xin[k], t->part, t->partb, B, H, W);
+        wgrad_first_kernel<3, GT><<<G, 96 * kRowGroups, 0, st>>>(gy, t->xin[k], t->part,
+                                                                 t->partb, B, H, W);
     else
-        wgrad_first_kernel<2, GT><<<G, 96, 0, st>>>(gy, t->xin[k], t->part, t->partb, B, H, W);
+        wgrad_first_kernel<2, GT><<<G, 96 * kRowGroups, 0, st>>>(gy, t->xin[k], t->part,
+                                                                 t->partb, B, H, W);
     wgrad_reduce_kernel<<<reduce_blocks(cx, 32), 256, 0, st>>>(t->part, t->partb, G, cx, 32, gw,
                                                               gb);
     return check_launch();
@@ -1692,6 +1693,18 @@ static hp_status wgrad_dispatch(hp_trainer* t, int k, int l, const float* gy, co
     return HP_ERR_UNSUPPORTED;
 }
 
+// replicated-border terms of a tensor-core input gradient in the first and
+// last column (the ghost rows are folded in by the tensor-core pass)
+template <int CI, int CO>
+static hp_status border_terms(const __nv_bfloat16* gy, const float* w, const __nv_bfloat16* act,
+                              __nv_bfloat16* gx, int B, int H, int W, cudaStream_t st)
+{
+    const long nb = (long)B * H * (W > 1 ? 2 : 1);
+    dgrad_border_kernel<CI, CO><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(gy, w, act, gx,
+                                                                                  B, H, W);
+    return check_launch();
+}
+
 // first layer of a branch (2 or 3 -> 32) from a BF16 gradient: weight
 // gradient, and for the finer branches the gradient of the up-sampled coarser
 // output (input channel 2) into gsmall
@@ -1711,7 +1724,6 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
                                     __nv_bfloat16* gbuf[2], int B, int H, int W, cudaStream_t st)
 {
     hp_cnn* c = t->cnn;
-    const long P = (long)B * H * W;
     // last layer (32 -> 1, CUDA cores): weight gradient from the FP32 output
     // gradient, input gradient into BF16
     float* gw = t->grad + layer_offset(llast);
@@ -1727,13 +1739,9 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
         const __nv_bfloat16* gy = gbuf[cur];
         const __nv_bfloat16* x = (const __nv_bfloat16*)t->act[l - 1];
         int grid = 0;
-        rc = launch_conv3x3_tc_wgrad(x, gy, t->part, t->part_len, B, H, W, ci, co, c->err,
-                                     c->num_sms, &grid, st);
+        rc = launch_conv3x3_tc_wgrad(x, gy, t->part, t->part_len, t->partb, t->partb_len, B, H, W,
+                                     ci, co, c->err, c->num_sms, &grid, st);
         if (rc != HP_OK) return rc;
-        if (co == 64)
-            bias_grad_kernel<64><<<grid, 256, 0, st>>>((const uint4*)gy, P, t->partb);
-        else
-            bias_grad_kernel<32><<<grid, 256, 0, st>>>((const uint4*)gy, P, t->partb);
         gw = t->grad + layer_offset(l);
         wgrad_reduce_kernel<<<reduce_blocks(ci, co), 256, 0, st>>>(t->part, t->partb, grid, ci, co,
                                                                    gw, gw + layer_wcount(l));
@@ -1744,15 +1752,13 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
         rc = launch_conv3x3_tc_dgrad(gy, t->wdg[l], t->zero_bias, act, gx, B, H, W, ci, co,
                                      c->err, c->num_sms, st);
         if (rc != HP_OK) return rc;
-        const long nb = (long)B * ((H > 1 ? 2 * W : W) + (long)(H > 2 ? H - 2 : 0) * (W > 1 ? 2 : 1));
-        const unsigned blocks = (unsigned)((nb * 32 + 255) / 256);
         if (ci == 64 && co == 64)
-            dgrad_border_kernel<64, 64><<<blocks, 256, 0, st>>>(gy, t->wt[l], act, gx, B, H, W);
+            rc = border_terms<64, 64>(gy, t->wt[l], act, gx, B, H, W, st);
         else if (ci == 32 && co == 64)
-            dgrad_border_kernel<32, 64><<<blocks, 256, 0, st>>>(gy, t->wt[l], act, gx, B, H, W);
+            rc = border_terms<32, 64>(gy, t->wt[l], act, gx, B, H, W, st);
         else
-            dgrad_border_kernel<64, 32><<<blocks, 256, 0, st>>>(gy, t->wt[l], act, gx, B, H, W);
-        if ((rc = check_launch()) != HP_OK) return rc;
+            rc = border_terms<64, 32>(gy, t->wt[l], act, gx, B, H, W, st);
+        if (rc != HP_OK) return rc;
         cur ^= 1;
     }
     return first_layer_bf16(t, k, lfirst, gbuf[cur], B, H, W, st);

@@ -638,6 +638,32 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                             if (len1 > 0) mma_bf16(d1, ad, b1 + boff, id1, 1u);
                         }
                     }
+                    if constexpr (DGRAD) {
+                        // ghost output rows -1 and H of the zero-padded
+                        // transpose, folded into rows 0 and H - 1 (the
+                        // replicated border); both are still accumulating
+                        // while input rows 0 and H - 1 are issued
+                        for (int f = 0; f < 2; ++f) {
+                            const bool fold = f == 0 ? (r == 0 && it.y0 == 0)
+                                                     : (r == H - 1 && it.y1 == H);
+                            if (!fold) continue;
+                            const int o = f == 0 ? 0 : H - 1;
+                            const int dsrc = f == 0 ? 2 : 0;  // block of output row -1 / H
+                            const uint32_t sl =
+                                (og + (uint32_t)(o - it.y0)) % (uint32_t)kAccSlots;
+                            const uint32_t dd = tmem + (uint32_t)(COUT * (kAccSlots - 1 - (int)sl));
+                            const uint32_t idf = idesc_for_rows(1, COUT);
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                                for (int ks = 0; ks < NCH / 2; ++ks) {
+                                    const uint64_t ad = ad_row + (uint64_t)(2 * ks * kHaloPx + dx);
+                                    const uint64_t boff =
+                                        (uint64_t)((dx * NCH + 2 * ks) * 3 * COUT + dsrc * COUT);
+                                    mma_bf16(dd, ad, bd_base + boff, idf, 1u);
+                                }
+                        }
+                    }
                     mma_commit(smem_u32(&empty_bar[jg % kWsSlots]));
                     last_row = (int)jg;
                     if (dhi == 2) {
@@ -851,8 +877,8 @@ struct WgSmem {
 template <int CI, int CO>
 __global__ void __launch_bounds__(kWgThreads, 1)
     conv3x3_wgrad_tc_kernel(const uint4* __restrict__ x, const uint4* __restrict__ gy,
-                            float* __restrict__ part, int H, int W, int segs, int nbands,
-                            int band, int items, int* err)
+                            float* __restrict__ part, float* __restrict__ partb, int H, int W,
+                            int segs, int nbands, int band, int items, int* err)
 {
     using S = WgSmem<CI, CO>;
     constexpr int NX = S::kChunksX, NG = S::kChunksG;
@@ -866,10 +892,14 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_abort;
+    __shared__ float s_bias[128][8];
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
+    // bias-gradient partial sums of the producer threads: channels 8 (tid % NG)
+    // .. + 7 over the pixels of every gradient row this CTA loads
+    float bacc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -915,6 +945,21 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     if (warp < 4) {
         // ---------------------------------------------------------- producer
         uint32_t xpos = 0, gcnt = 0;
+        uint4 pend[NG];
+#pragma unroll
+        for (int i = 0; i < NG; ++i) pend[i] = make_uint4(0u, 0u, 0u, 0u);
+        auto add_pend = [&]() {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const uint32_t e[4] = {pend[i].x, pend[i].y, pend[i].z, pend[i].w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    bacc[2 * h] += __uint_as_float(e[h] << 16);
+                    bacc[2 * h + 1] += __uint_as_float(e[h] & 0xFFFF0000u);
+                }
+                pend[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
         auto load_x = [&](int b, int x0, int r, uint32_t pos) -> bool {
             const uint32_t sl = pos % S::kSlots, u = pos / S::kSlots;
             if (u > 0 && !mbar_wait_ws(smem_u32(&xempty[sl]), (u - 1) & 1u, &s_abort))
@@ -953,6 +998,16 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
                              smem_u32(&gfull[bb]))
                          : "memory");
+            // bias sums: the previous row's values (loaded one row earlier, so
+            // that their latency overlaps) are added, this row's are loaded
+            add_pend();
+            const int chb = tid % NG;
+#pragma unroll
+            for (int i = 0; i < NG; ++i) {
+                const int j = tid / NG + i * (128 / NG);
+                pend[i] = x0 + j < xend ? src_row[(size_t)(x0 + j) * NG + chb]
+                                        : make_uint4(0u, 0u, 0u, 0u);
+            }
             return true;
         };
         for (int wi = blockIdx.x; wi < items && ok; wi += gridDim.x) {
@@ -962,6 +1017,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 ok = load_x(it.b, it.x0, r + 1, xpos++) && load_g(it.b, it.x0, r, gcnt++);
             }
         }
+        add_pend();
         if (!ok) s_abort = 1;  // the MMA thread stops waiting for rows
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (lane == 0) {
@@ -1054,6 +1110,10 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         s_abort = 1;
         if (err) atomicExch(err, 1);
     }
+    if (warp < 4) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s_bias[tid][k] = bacc[k];
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -1061,11 +1121,20 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"((uint32_t)S::kTmemCols));
     }
+    // bias partial of the CTA: the producer threads of each channel chunk,
+    // in a fixed order
+    if (tid < CO) {
+        const int chb = tid / 8, k = tid % 8;
+        float t = 0.0f;
+        for (int q = chb; q < 128; q += NG) t += s_bias[q][k];
+        partb[(size_t)blockIdx.x * CO + tid] = t;
+    }
 }
 
 template <int CI, int CO>
-hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part_len, int B,
-                         int H, int W, int* err, int nsm, int* grid_out, cudaStream_t st)
+hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part_len,
+                         float* partb, size_t partb_len, int B, int H, int W, int* err, int nsm,
+                         int* grid_out, cudaStream_t st)
 {
     using S = WgSmem<CI, CO>;
     static bool attr = false;
@@ -1083,9 +1152,10 @@ hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part
     const long items = (long)B * segs * nbands;
     if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
     const int grid = items < nsm ? (int)items : nsm;
-    if ((size_t)grid * 9 * CO * CI > part_len) return HP_ERR_INVALID_ARG;
+    if ((size_t)grid * 9 * CO * CI > part_len || (size_t)grid * CO > partb_len)
+        return HP_ERR_INVALID_ARG;
     conv3x3_wgrad_tc_kernel<CI, CO><<<grid, kWgThreads, S::kBytes, st>>>(
-        (const uint4*)x, (const uint4*)gy, part, H, W, segs, nbands, band, (int)items, err);
+        (const uint4*)x, (const uint4*)gy, part, partb, H, W, segs, nbands, band, (int)items, err);
     *grid_out = grid;
     return check_launch();
 }
@@ -1151,19 +1221,22 @@ hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* 
     return HP_ERR_UNSUPPORTED;
 }
 
-// Weight-gradient partial sums of a tensor-core layer (cin -> cout) into
-// part[g][9][cout][cin] for g < *grid_out (one per CTA); x BF16 [P][cin],
-// gy BF16 [P][cout].
+// Weight- and bias-gradient partial sums of a tensor-core layer (cin ->
+// cout) into part[g][9][cout][cin] and partb[g][cout] for g < *grid_out (one
+// per CTA); x BF16 [P][cin], gy BF16 [P][cout].
 hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, size_t part_len,
-                                  int B, int H, int W, int cin, int cout, int* err, int nsm,
-                                  int* grid_out, cudaStream_t st)
+                                  float* partb, size_t partb_len, int B, int H, int W, int cin,
+                                  int cout, int* err, int nsm, int* grid_out, cudaStream_t st)
 {
     if (cin == 64 && cout == 64)
-        return launch_wgrad_t<64, 64>(x, gy, part, part_len, B, H, W, err, nsm, grid_out, st);
+        return launch_wgrad_t<64, 64>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
+                                      grid_out, st);
     if (cin == 32 && cout == 64)
-        return launch_wgrad_t<32, 64>(x, gy, part, part_len, B, H, W, err, nsm, grid_out, st);
+        return launch_wgrad_t<32, 64>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
+                                      grid_out, st);
     if (cin == 64 && cout == 32)
-        return launch_wgrad_t<64, 32>(x, gy, part, part_len, B, H, W, err, nsm, grid_out, st);
+        return launch_wgrad_t<64, 32>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
+                                      grid_out, st);
     return HP_ERR_UNSUPPORTED;
 }
 

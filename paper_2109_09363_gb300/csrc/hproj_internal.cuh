@@ -195,14 +195,15 @@ hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias
 // backward of a tensor-core layer cin -> cout (32 or 64 channels each):
 // input gradient (BF16, zero-padded transposed convolution with the flipped
 // weights wdg BF16 [9][cin][cout], ReLU derivative of act applied; the
-// replicated-border terms are added separately) and per-CTA weight-gradient
-// partial sums part[g][9][cout][cin], g < *grid_out
+// replicated-border terms are added separately) and per-CTA weight- and
+// bias-gradient partial sums part[g][9][cout][cin], partb[g][cout],
+// g < *grid_out
 hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* zero_bias,
                                   const void* act, void* gx, int B, int H, int W, int cin,
                                   int cout, int* err, int nsm, cudaStream_t st);
 hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, size_t part_len,
-                                  int B, int H, int W, int cin, int cout, int* err, int nsm,
-                                  int* grid_out, cudaStream_t st);
+                                  float* partb, size_t partb_len, int B, int H, int W, int cin,
+                                  int cout, int* err, int nsm, int* grid_out, cudaStream_t st);
 hp_status launch_advect(const float* u, const float* v, const float* rho, const uint8_t* flags,
                         float* u_out, float* v_out, float* rho_out, hp_shape s,
                         const hp_plume_params& p, cudaStream_t st);
