@@ -858,7 +858,10 @@ constexpr int kWgThreads = 160;
 template <int CI, int CO>
 struct WgSmem {
     static constexpr int kChunksX = CI / 8, kChunksG = CO / 8;
-    static constexpr int kStride = kWgPx * 16;  // bytes per channel chunk of a row
+    // bytes per channel chunk of a row: 144 pixels plus 16 bytes, so that the
+    // chunks of one pixel fall in different shared-memory banks (the
+    // producers write them together)
+    static constexpr int kStride = kWgPx * 16 + 16;
     static constexpr int kSlotBytes = kChunksX * kStride;
     static constexpr int kRows = 128 / CI;
     static constexpr int kSlots = kRows == 2 ? 4 : 5;
@@ -993,7 +996,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 const int col = x0 + k - dx;  // gradient pixel at input pixel x0 - 1 + k
                 const bool valid = col >= x0 && col < xend;
                 const uint4* src = src_row + (size_t)(valid ? col : x0) * NG + ch;
-                cp_async16_zfill(dst + (uint32_t)(((dx * NG + ch) * kWgPx + k) * 16), src, valid);
+                cp_async16_zfill(dst + (uint32_t)((dx * NG + ch) * S::kStride + k * 16), src, valid);
             }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
                              smem_u32(&gfull[bb]))
