@@ -1271,18 +1271,27 @@ __global__ void loss_grad_kernel(const float* __restrict__ phi, const float* __r
     g[q] = gv;
 }
 
+// sum of 32 lanes' values in a fixed order (lane 0 gets the result)
+__device__ __forceinline__ double warp_sum_fixed(double v)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// one warp: lane l takes the grids b = l (mod 32) in order
 __global__ void loss_finish_kernel(const double* __restrict__ stats, int B, size_t cells,
                                    float lambda, double* __restrict__ loss)
 {
     double L = 0.0;
-    for (int b = 0; b < B; ++b) {
+    for (int b = threadIdx.x; b < B; b += 32) {
         const double* st = stats + (size_t)b * kStats;
         const double vt = target_var(st);
         if (st[2] > 0.0 && vt > 0.0) L += (st[1] - st[0] * st[0] / st[2]) / vt;
         if (st[6] > 0.0) L += lambda * st[3] / st[6];
     }
     (void)cells;
-    *loss = L / B;
+    L = warp_sum_fixed(L);
+    if (threadIdx.x == 0) *loss = L / B;
 }
 
 // physics-driven loss (Sec. 3.2, Eq. 4) of the network-corrected field: the
@@ -1356,13 +1365,15 @@ __global__ void pdnn_grad_kernel(const float* __restrict__ rbuf, const uint8_t* 
     g[q] = -lr;
 }
 
+// one warp, as loss_finish_kernel
 __global__ void pdnn_finish_kernel(const double* __restrict__ stats,
                                    const float* __restrict__ weight, int B, size_t cells,
                                    double* __restrict__ loss)
 {
     double L = 0.0;
-    for (int b = 0; b < B; ++b) L += (double)weight[b] * stats[b] / (double)cells;
-    *loss = L;
+    for (int b = threadIdx.x; b < B; b += 32) L += (double)weight[b] * stats[b] / (double)cells;
+    L = warp_sum_fixed(L);
+    if (threadIdx.x == 0) *loss = L;
 }
 
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
@@ -1843,7 +1854,7 @@ static hp_status trainer_grad(hp_trainer* t, const float* div, const uint8_t* fl
     loss_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
         phi, target, t->rbuf, t->mask, flags, c->s, t->stats, lambda, t->g[0], s.batch, s.ny,
         s.nx);
-    loss_finish_kernel<<<1, 1, 0, st>>>(t->stats, s.batch, cells, lambda, t->loss);
+    loss_finish_kernel<<<1, 32, 0, st>>>(t->stats, s.batch, cells, lambda, t->loss);
     if ((rc = check_launch()) != HP_OK) return rc;
     return trainer_backward(t, s, st);
 }
@@ -1863,7 +1874,7 @@ static hp_status trainer_pdnn_grad(hp_trainer* t, const float* div, const uint8_
                                                t->stats, s.ny, s.nx);
     pdnn_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
         t->rbuf, t->mask, t->g[0], s.batch, s.ny, s.nx);
-    pdnn_finish_kernel<<<1, 1, 0, st>>>(t->stats, weight, s.batch, cells, t->loss);
+    pdnn_finish_kernel<<<1, 32, 0, st>>>(t->stats, weight, s.batch, cells, t->loss);
     if ((rc = check_launch()) != HP_OK) return rc;
     return trainer_backward(t, s, st);
 }
