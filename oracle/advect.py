@@ -20,6 +20,13 @@ Boussinesq buoyancy of the plume case:
 Positions: cell (i, j) centred at (i + 1/2, j + 1/2); u face (j, i) at
 (i, j + 1/2); v face (j, i) at (i + 1/2, j); row 0 is the top of the image,
 so a negative v points up.
+
+With scheme="maccormack" step 2 is the MacCormack semi-Lagrangian method the
+paper names (Sec. 2.2, after Selle et al. 2008) for rho, u and v alike: the
+forward semi-Lagrangian result q_f, the backward semi-Lagrangian result q_b
+(q_f sampled at x + dt * vel(x)), q_f + (q - q_b) / 2, clamped to the
+smallest and largest of the four samples of q that the forward step
+interpolated (the limiter that keeps the scheme stable).
 """
 from __future__ import annotations
 
@@ -45,16 +52,46 @@ def bilinear(q, x, y, ox, oy):
     return top * (1.0 - fy) + bot * fy
 
 
+def stencil_range(q, x, y, ox, oy):
+    """(min, max) of the four samples of q that bilinear(q, x, y, ox, oy)
+    interpolates."""
+    My, Mx = q.shape
+    tx = np.clip(x - ox, 0.0, Mx - 1.0)
+    ty = np.clip(y - oy, 0.0, My - 1.0)
+    i0 = np.minimum(np.floor(tx).astype(np.int64), max(Mx - 2, 0))
+    j0 = np.minimum(np.floor(ty).astype(np.int64), max(My - 2, 0))
+    i1 = np.minimum(i0 + 1, Mx - 1)
+    j1 = np.minimum(j0 + 1, My - 1)
+    c = np.stack([q[j0, i0], q[j0, i1], q[j1, i0], q[j1, i1]])
+    return c.min(axis=0), c.max(axis=0)
+
+
+def advect_quantity(q, x, y, ox, oy, vx, vy, dt, scheme):
+    """q [My][Mx] (sample (j, i) at (i + ox, j + oy)) advected to its own
+    sample points (x, y) with the velocity (vx, vy) there."""
+    xd, yd = x - dt * vx, y - dt * vy
+    fwd = bilinear(q, xd, yd, ox, oy)
+    if scheme == "sl":
+        return fwd
+    if scheme != "maccormack":
+        raise ValueError(scheme)
+    back = bilinear(fwd, x + dt * vx, y + dt * vy, ox, oy)
+    lo, hi = stencil_range(q, xd, yd, ox, oy)
+    return np.clip(fwd + 0.5 * (q - back), lo, hi)
+
+
 def velocity_at(u, v, x, y):
     """(u, v) at points (x, y): each component interpolated on its own faces."""
     return bilinear(u, x, y, 0.0, 0.5), bilinear(v, x, y, 0.5, 0.0)
 
 
-def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, inlet=None):
+def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, inlet=None,
+                scheme="sl"):
     """One driver step on one grid; returns (u*, v*, rho) in FP64.
 
     u [ny][nx+1], v [ny+1][nx], rho, flags [ny][nx]; inlet = (x0, x1) columns
-    of the bottom-row density source or None.
+    of the bottom-row density source or None; scheme "sl" (first-order
+    semi-Lagrangian) or "maccormack".
     """
     u = np.asarray(u, np.float64)
     v = np.asarray(v, np.float64)
@@ -71,11 +108,11 @@ def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, i
     xv, yv = iv + 0.5, jv.astype(np.float64)
 
     vx, vy = velocity_at(u, v, xc, yc)
-    rho_new = bilinear(rho, xc - dt * vx, yc - dt * vy, 0.5, 0.5)
+    rho_new = advect_quantity(rho, xc, yc, 0.5, 0.5, vx, vy, dt, scheme)
     vx, vy = velocity_at(u, v, xu, yu)
-    u_new = bilinear(u, xu - dt * vx, yu - dt * vy, 0.0, 0.5)
+    u_new = advect_quantity(u, xu, yu, 0.0, 0.5, vx, vy, dt, scheme)
     vx, vy = velocity_at(u, v, xv, yv)
-    v_new = bilinear(v, xv - dt * vx, yv - dt * vy, 0.5, 0.0)
+    v_new = advect_quantity(v, xv, yv, 0.5, 0.0, vx, vy, dt, scheme)
     # Boussinesq buoyancy on interior v faces (forward Euler)
     rho_face = 0.5 * (rho_new[:-1, :] + rho_new[1:, :])
     v_new[1:ny, :] += dt * gravity * (rho_face - rho_amb)
