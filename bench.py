@@ -439,6 +439,42 @@ def run_pdnn_arm(hp, dev, steps: int = 10, warmup: int = 3, batch: int = 64, n: 
     return res
 
 
+def run_driver_timing(hp, u0, v0, fl, reps: int = 10):
+    """Driver step (a8 and the f3 MacCormack scheme) on the bench grids: one
+    hp_advect_step with first-order semi-Lagrangian and with MacCormack
+    advection, and the plume-head reduction, CUDA events over `reps` calls
+    each (inputs resident)."""
+    import torch
+    B_, ny, nx = fl.shape
+    g = torch.Generator(device="cpu").manual_seed(7)
+    rho = (1.0 + 1e-4 * torch.randn((B_, ny, nx), generator=g)).to(u0.device)
+    outs = (torch.empty_like(u0), torch.empty_like(v0), torch.empty_like(rho))
+    res = {"workload": f"{B_} x {ny}x{nx} bench grids, rho = 1 + N(0, 1e-4^2), dt = 0.1"}
+    for name, scheme in (("sl", 0), ("maccormack", 1)):
+        pp = hp.PlumeParams(dt=0.1, inlet_x0=nx // 2 - nx // 16, inlet_x1=nx // 2 + nx // 16,
+                            scheme=scheme)
+        for _ in range(3):
+            hp.hp_advect_step(u0, v0, rho, fl, pp, *outs)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            hp.hp_advect_step(u0, v0, rho, fl, pp, *outs)
+        b.record()
+        torch.cuda.synchronize()
+        res[f"{name}_ms"] = a.elapsed_time(b) / reps
+    head = torch.empty((B_, 3), dtype=torch.int32, device=u0.device)
+    for _ in range(3):
+        hp.hp_plume_head(outs[2], 1.0, 0.01, out=head)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        hp.hp_plume_head(outs[2], 1.0, 0.01, out=head)
+    b.record()
+    torch.cuda.synchronize()
+    res["plume_head_ms"] = a.elapsed_time(b) / reps
+    return res
+
+
 def profile_conv(batch, h, w, cin, cout) -> int:
     """Time and run one tensor-core convolution layer (FLOP/s printed)."""
     import torch
@@ -757,6 +793,7 @@ def main():
     if not args.no_hybrid:
         hybrid = run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms, ws)
     pdnn = None if args.no_pdnn else run_pdnn_arm(hp, dev)
+    driver = run_driver_timing(hp, u0, v0, fl)
 
     if rank == 0:
         line = {
@@ -782,6 +819,7 @@ def main():
             line["hybrid"] = hybrid
         if pdnn is not None:
             line["pdnn_training"] = pdnn
+        line["driver_step"] = driver
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(u_np, v_np, fl_np)
         print(json.dumps(line), flush=True)

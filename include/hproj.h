@@ -163,7 +163,13 @@ int32_t hp_resident_clusters(hp_ctx *ctx, hp_shape shape);
  *             row 0 is the top, so g < 0 makes light fluid rise
  *   rho_amb   ambient density
  *   rho_in    density imposed on the inlet cells before the step
- *   inlet_x0, inlet_x1  inlet columns [x0, x1) of the bottom row (x1 <= x0: no inlet) */
+ *   inlet_x0, inlet_x1  inlet columns [x0, x1) of the bottom row (x1 <= x0: no inlet)
+ *   scheme    0: first-order semi-Lagrangian; 1: MacCormack (the scheme of
+ *             Sec. 2.2, after Selle et al. 2008): the forward semi-Lagrangian
+ *             value q_f, the forward field sampled backwards at x + dt vel(x)
+ *             (q_b), and q_f + (q - q_b) / 2 clamped to the range of the four
+ *             samples the forward step interpolated; for rho, u and v alike.
+ *             Other values return HP_ERR_INVALID_ARG. */
 typedef struct {
     float dt;
     float gravity;
@@ -171,6 +177,7 @@ typedef struct {
     float rho_in;
     int32_t inlet_x0;
     int32_t inlet_x1;
+    int32_t scheme;
 } hp_plume_params;
 
 /* One driver step on B grids, out of place (outputs must not alias inputs):
@@ -186,6 +193,17 @@ typedef struct {
 hp_status hp_advect_step(const float *u, const float *v, const float *rho, const uint8_t *flags,
                          float *u_out, float *v_out, float *rho_out, hp_shape shape,
                          const hp_plume_params *params, void *stream);
+
+/* Plume head of the paper's diagnostics (Sec. 4.1: the highest point of the
+ * plume, and its horizontal extent on both sides around an obstacle): for
+ * each grid, over the cells with |rho - rho_amb| >= contrast (compared in
+ * FP32), out[b] = {smallest row index (row 0 is the top), smallest column,
+ * largest column}; {ny, nx, -1} when no cell qualifies.  The normalised
+ * positions follow on the host: h_y = (ny - row) / ny, left and right extent
+ * (nx / 2 - col_min) / nx and (col_max + 1 - nx / 2) / nx.  rho float
+ * [B][ny][nx], out int32 [B][3]: device memory; contrast >= 0. */
+hp_status hp_plume_head(const float *rho, hp_shape shape, float rho_amb, float contrast,
+                        int32_t *out, void *stream);
 
 /* 3 x 3 convolution with replicated borders (the convolutions of the
  * MultiScale network, Sec. 3.1), on the tensor cores: BF16 inputs and weights,

@@ -118,3 +118,18 @@ def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, i
     v_new[1:ny, :] += dt * gravity * (rho_face - rho_amb)
     uz, vz = oracle.zero_closed_faces(u_new, v_new, flags)
     return uz[0], vz[0], rho_new
+
+
+def plume_head(rho, rho_amb=1.0, contrast=0.01):
+    """Plume head of one grid (Sec. 4.1: the highest point of the plume and
+    its horizontal extent): (smallest row, smallest column, largest column) of
+    the cells with |rho - rho_amb| >= contrast, (ny, nx, -1) if there is none.
+    The comparison is made in FP32, as in the library, so that both take the
+    same decision for every cell."""
+    r = np.asarray(rho, np.float32)
+    m = np.abs(r - np.float32(rho_amb)) >= np.float32(contrast)
+    ny, nx = r.shape
+    if not m.any():
+        return ny, nx, -1
+    rows, cols = np.nonzero(m)
+    return int(rows.min()), int(cols.min()), int(cols.max())

@@ -38,7 +38,7 @@ class hp_project_params(ctypes.Structure):
 class hp_plume_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_float), ("gravity", ctypes.c_float), ("rho_amb", ctypes.c_float),
                 ("rho_in", ctypes.c_float), ("inlet_x0", ctypes.c_int32),
-                ("inlet_x1", ctypes.c_int32)]
+                ("inlet_x1", ctypes.c_int32), ("scheme", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -57,6 +57,7 @@ _SIGS = {
     "hp_resident_clusters": (ctypes.c_int32, [_P, hp_shape]),
     "hp_advect_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, hp_shape,
                                       ctypes.POINTER(hp_plume_params), _P]),
+    "hp_plume_head": (ctypes.c_int, [_P, hp_shape, ctypes.c_float, ctypes.c_float, _P, _P]),
     "hp_conv3x3_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, _P, _P]),
@@ -306,10 +307,11 @@ class PlumeParams:
     rho_in: float = 1.1
     inlet_x0: int = 0
     inlet_x1: int = 0
+    scheme: int = 0  # 0 first-order semi-Lagrangian, 1 MacCormack
 
     def c(self):
         return hp_plume_params(self.dt, self.gravity, self.rho_amb, self.rho_in, self.inlet_x0,
-                               self.inlet_x1)
+                               self.inlet_x1, self.scheme)
 
 
 def hp_advect_step(u, v, rho, flags, params: PlumeParams, u_out=None, v_out=None, rho_out=None,
@@ -330,6 +332,21 @@ def hp_advect_step(u, v, rho, flags, params: PlumeParams, u_out=None, v_out=None
                                          _ptr(v_out), _ptr(rho_out), s, ctypes.byref(prm),
                                          _stream(stream)))
     return u_out, v_out, rho_out
+
+
+def hp_plume_head(rho, rho_amb: float = 1.0, contrast: float = 0.01, out=None, stream=None):
+    """Plume head per grid: int32 [B][3] = (smallest row, smallest column,
+    largest column) of the cells with |rho - rho_amb| >= contrast; (ny, nx, -1)
+    when there is none."""
+    torch = _torch()
+    if rho.dim() != 3:
+        raise HprojError("rho must be [B][ny][nx]")
+    _check_dtype(rho, torch.float32, tuple(rho.shape), "rho")
+    B, ny, nx = rho.shape
+    out = torch.empty((B, 3), dtype=torch.int32, device=rho.device) if out is None else out
+    _check(load_library().hp_plume_head(_ptr(rho), hp_shape(B, ny, nx), float(rho_amb),
+                                        float(contrast), _ptr(out), _stream(stream)))
+    return out
 
 
 def hp_conv3x3_bf16(x, w, bias, relu: bool, y=None, err=None, stream=None):

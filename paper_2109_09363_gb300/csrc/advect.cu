@@ -1,8 +1,15 @@
-// Plume driver step for sm_103a: inlet source, first-order semi-Lagrangian
-// advection of rho (cell centres) and u, v (faces) with the start-of-step
-// velocity, Boussinesq buoyancy on the v faces (forward Euler), closed faces
-// zeroed.  This produces u* for the projection (Sec. 2.2: advection, then
-// external forces, then the pressure projection).
+// Plume driver step for sm_103a: inlet source, semi-Lagrangian advection of
+// rho (cell centres) and u, v (faces) with the start-of-step velocity,
+// first order or MacCormack, Boussinesq buoyancy on the v faces (forward
+// Euler), closed faces zeroed.  This produces u* for the projection
+// (Sec. 2.2: advection, then external forces, then the pressure projection).
+//
+// MacCormack (the scheme Sec. 2.2 names, after Selle et al. 2008): q_f, the
+// forward semi-Lagrangian value, q_b, the forward field sampled backwards at
+// x + dt vel(x), and q_f + (q - q_b) / 2 clamped to the range of the four
+// samples the forward step interpolated.  The forward field is not stored:
+// the backward sample recomputes it at its four corners, so the step needs
+// no workspace.
 //
 // Positions: cell (i, j) centred at (i + 1/2, j + 1/2); u face (j, i) at
 // (i, j + 1/2); v face (j, i) at (i + 1/2, j); row 0 is the top of the image.
@@ -19,6 +26,7 @@ struct Field {
     const float* q;  // [My][Mx]
     int Mx, My;
     float ox, oy;    // position of sample (0, 0)
+    __device__ float at(int i, int j) const { return q[(size_t)j * Mx + i]; }
 };
 
 // Bilinear sample at (x, y); the position is clamped to the sample span.
@@ -49,6 +57,76 @@ struct Rho {
     }
 };
 
+// Generic quantity view: Mx x My samples, sample (0, 0) at (ox, oy).
+template <class Q>
+struct View {
+    const Q& q;
+    int Mx, My;
+    float ox, oy;
+};
+
+// Bilinear sample of a view at (x, y) (position clamped to the sample span),
+// with the range of the four samples it interpolates.
+template <class V>
+__device__ __forceinline__ float sample_range(const V& f, float x, float y, float* lo, float* hi)
+{
+    const float tx = fminf(fmaxf(x - f.ox, 0.0f), (float)(f.Mx - 1));
+    const float ty = fminf(fmaxf(y - f.oy, 0.0f), (float)(f.My - 1));
+    int i0 = (int)floorf(tx), j0 = (int)floorf(ty);
+    i0 = min(i0, max(f.Mx - 2, 0));
+    j0 = min(j0, max(f.My - 2, 0));
+    const float fx = tx - (float)i0, fy = ty - (float)j0;
+    const int i1 = min(i0 + 1, f.Mx - 1), j1 = min(j0 + 1, f.My - 1);
+    const float q00 = f.q.at(i0, j0), q01 = f.q.at(i1, j0);
+    const float q10 = f.q.at(i0, j1), q11 = f.q.at(i1, j1);
+    if (lo) {
+        *lo = fminf(fminf(q00, q01), fminf(q10, q11));
+        *hi = fmaxf(fmaxf(q00, q01), fmaxf(q10, q11));
+    }
+    const float top = q00 * (1.0f - fx) + q01 * fx;
+    const float bot = q10 * (1.0f - fx) + q11 * fx;
+    return top * (1.0f - fy) + bot * fy;
+}
+
+// The forward semi-Lagrangian field of a quantity, evaluated on demand at
+// its own samples.
+template <class Q>
+struct Forward {
+    const Q& q;
+    const Field& fu;
+    const Field& fv;
+    int Mx, My;
+    float ox, oy, dt;
+    __device__ float at(int i, int j) const
+    {
+        const float x = (float)i + ox, y = (float)j + oy;
+        const float vx = sample(fu, x, y), vy = sample(fv, x, y);
+        const View<Q> w = {q, Mx, My, ox, oy};
+        return sample_range(w, x - dt * vx, y - dt * vy, nullptr, nullptr);
+    }
+};
+
+// New value of sample (i, j) of quantity q (Mx x My samples at (ox, oy)).
+template <bool MC, class Q>
+__device__ __forceinline__ float advected(const Q& q, int Mx, int My, float ox, float oy,
+                                          const Field& fu, const Field& fv, float dt, int i,
+                                          int j)
+{
+    const float x = (float)i + ox, y = (float)j + oy;
+    const float vx = sample(fu, x, y), vy = sample(fv, x, y);
+    const View<Q> w = {q, Mx, My, ox, oy};
+    if constexpr (!MC) {
+        return sample_range(w, x - dt * vx, y - dt * vy, nullptr, nullptr);
+    } else {
+        float lo, hi;
+        const float qf = sample_range(w, x - dt * vx, y - dt * vy, &lo, &hi);
+        const Forward<Q> fwd = {q, fu, fv, Mx, My, ox, oy, dt};
+        const View<Forward<Q>> wf = {fwd, Mx, My, ox, oy};
+        const float qb = sample_range(wf, x + dt * vx, y + dt * vy, nullptr, nullptr);
+        return fminf(fmaxf(qf + 0.5f * (q.at(i, j) - qb), lo), hi);
+    }
+}
+
 __device__ __forceinline__ float sample_rho(const Rho& r, float x, float y)
 {
     const float tx = fminf(fmaxf(x - 0.5f, 0.0f), (float)(r.nx - 1));
@@ -69,16 +147,22 @@ __device__ __forceinline__ bool fluid(const uint8_t* fl, int nx, int i, int j)
 }
 
 // New density of cell (i, j).
+template <bool MC>
 __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const Field& fv,
                                             float dt, int i, int j)
 {
-    const float x = i + 0.5f, y = j + 0.5f;
-    const float vx = sample(fu, x, y), vy = sample(fv, x, y);
-    return sample_rho(r, x - dt * vx, y - dt * vy);
+    if constexpr (!MC) {
+        const float x = i + 0.5f, y = j + 0.5f;
+        const float vx = sample(fu, x, y), vy = sample(fv, x, y);
+        return sample_rho(r, x - dt * vx, y - dt * vy);
+    } else {
+        return advected<true>(r, r.nx, r.ny, 0.5f, 0.5f, fu, fv, dt, i, j);
+    }
 }
 
 // One thread per (i, j) in [0, nx] x [0, ny]: cell (i, j) density, u face
 // (j, i), v face (j, i) with buoyancy.
+template <bool MC>
 __global__ void advect_kernel(const float* __restrict__ u, const float* __restrict__ v,
                               const float* __restrict__ rho, const uint8_t* __restrict__ flags,
                               float* __restrict__ u_out, float* __restrict__ v_out,
@@ -95,30 +179,81 @@ __global__ void advect_kernel(const float* __restrict__ u, const float* __restri
     const uint8_t* fl = flags + b * cells;
     const float dt = p.dt;
 
-    if (i < nx && j < ny) rho_out[b * cells + (size_t)j * nx + i] = rho_new_at(r, fu, fv, dt, i, j);
+    if (i < nx && j < ny)
+        rho_out[b * cells + (size_t)j * nx + i] = rho_new_at<MC>(r, fu, fv, dt, i, j);
 
     if (j < ny) {
         const bool open = i > 0 && i < nx && fluid(fl, nx, i - 1, j) && fluid(fl, nx, i, j);
         float val = 0.0f;
-        if (open) {
-            const float x = (float)i, y = j + 0.5f;
-            const float vx = sample(fu, x, y), vy = sample(fv, x, y);
-            val = sample(fu, x - dt * vx, y - dt * vy);
-        }
+        if (open) val = advected<MC>(fu, nx + 1, ny, 0.0f, 0.5f, fu, fv, dt, i, j);
         u_out[(size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1) + i] = val;
     }
     if (i < nx) {
         const bool open = j > 0 && j < ny && fluid(fl, nx, i, j - 1) && fluid(fl, nx, i, j);
         float val = 0.0f;
         if (open) {
-            const float x = i + 0.5f, y = (float)j;
-            const float vx = sample(fu, x, y), vy = sample(fv, x, y);
-            val = sample(fv, x - dt * vx, y - dt * vy);
-            const float rf = 0.5f * (rho_new_at(r, fu, fv, dt, i, j - 1) +
-                                     rho_new_at(r, fu, fv, dt, i, j));
+            val = advected<MC>(fv, nx, ny + 1, 0.5f, 0.0f, fu, fv, dt, i, j);
+            const float rf = 0.5f * (rho_new_at<MC>(r, fu, fv, dt, i, j - 1) +
+                                     rho_new_at<MC>(r, fu, fv, dt, i, j));
             val += dt * p.gravity * (rf - p.rho_amb);
         }
         v_out[(size_t)b * (ny + 1) * nx + (size_t)j * nx + i] = val;
+    }
+}
+
+__global__ void plume_head_init_kernel(int32_t* __restrict__ out, int B, int ny, int nx)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    out[3 * b + 0] = ny;
+    out[3 * b + 1] = nx;
+    out[3 * b + 2] = -1;
+}
+
+// Smallest row, smallest and largest column of the cells whose density
+// contrast reaches the threshold: CTA (slice, grid) reduces its slice of
+// rows and merges with atomicMin / atomicMax (integers: order independent).
+__global__ void __launch_bounds__(512) plume_head_kernel(const float* __restrict__ rho, int ny,
+                                                         int nx, float rho_amb, float contrast,
+                                                         int32_t* __restrict__ out)
+{
+    __shared__ int s_min_row[16], s_min_col[16], s_max_col[16];
+    const int b = blockIdx.y;
+    const int r0 = (int)((long)ny * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long)ny * (blockIdx.x + 1) / gridDim.x);
+    const float* r = rho + (size_t)b * ny * nx;
+    int min_row = ny, min_col = nx, max_col = -1;
+    for (long c = (long)r0 * nx + threadIdx.x; c < (long)r1 * nx; c += blockDim.x) {
+        if (fabsf(r[c] - rho_amb) >= contrast) {
+            const int j = (int)(c / nx), i = (int)(c - (long)j * nx);
+            min_row = min(min_row, j);
+            min_col = min(min_col, i);
+            max_col = max(max_col, i);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        min_row = min(min_row, __shfl_down_sync(0xffffffffu, min_row, off));
+        min_col = min(min_col, __shfl_down_sync(0xffffffffu, min_col, off));
+        max_col = max(max_col, __shfl_down_sync(0xffffffffu, max_col, off));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_min_row[warp] = min_row;
+        s_min_col[warp] = min_col;
+        s_max_col[warp] = max_col;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            min_row = min(min_row, s_min_row[w]);
+            min_col = min(min_col, s_min_col[w]);
+            max_col = max(max_col, s_max_col[w]);
+        }
+        if (max_col >= 0) {
+            atomicMin(&out[3 * b + 0], min_row);
+            atomicMin(&out[3 * b + 1], min_col);
+            atomicMax(&out[3 * b + 2], max_col);
+        }
     }
 }
 
@@ -129,7 +264,12 @@ hp_status launch_advect(const float* u, const float* v, const float* rho, const 
                         const hp_plume_params& p, cudaStream_t st)
 {
     dim3 blk(128), grd((s.nx + 1 + 127) / 128, s.ny + 1, s.batch);
-    advect_kernel<<<grd, blk, 0, st>>>(u, v, rho, flags, u_out, v_out, rho_out, s.ny, s.nx, p);
+    if (p.scheme == 1)
+        advect_kernel<true><<<grd, blk, 0, st>>>(u, v, rho, flags, u_out, v_out, rho_out, s.ny,
+                                                 s.nx, p);
+    else
+        advect_kernel<false><<<grd, blk, 0, st>>>(u, v, rho, flags, u_out, v_out, rho_out, s.ny,
+                                                  s.nx, p);
     return check_launch();
 }
 
@@ -143,5 +283,19 @@ extern "C" hp_status hp_advect_step(const float* u, const float* v, const float*
     if (!u || !v || !rho || !flags || !u_out || !v_out || !rho_out || !p || !hp::shape_ok(s))
         return HP_ERR_INVALID_ARG;
     if (u_out == u || v_out == v || rho_out == rho || !(p->dt >= 0.0f)) return HP_ERR_INVALID_ARG;
+    if (p->scheme != 0 && p->scheme != 1) return HP_ERR_INVALID_ARG;
     return hp::launch_advect(u, v, rho, flags, u_out, v_out, rho_out, s, *p, (cudaStream_t)stream);
+}
+
+extern "C" hp_status hp_plume_head(const float* rho, hp_shape s, float rho_amb, float contrast,
+                                   int32_t* out, void* stream)
+{
+    if (!rho || !out || !hp::shape_ok(s) || !(contrast >= 0.0f)) return HP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    hp::plume_head_init_kernel<<<(s.batch + 127) / 128, 128, 0, st>>>(out, s.batch, s.ny, s.nx);
+    // about 16 rows per CTA, at most 64 CTAs per grid
+    const int slices = s.ny < 16 ? 1 : (s.ny / 16 < 64 ? s.ny / 16 : 64);
+    hp::plume_head_kernel<<<dim3(slices, s.batch), 512, 0, st>>>(rho, s.ny, s.nx, rho_amb,
+                                                                  contrast, out);
+    return hp::check_launch();
 }

@@ -91,6 +91,17 @@ def inlet_columns(n: int, width: int | None = None):
     return n // 2 - w // 2, n // 2 - w // 2 + w
 
 
+def paper_plume_geometry(n: int, cylinder: bool = True):
+    """The plume cases of Sec. 2.1 on an n x n box: an inlet centred in the
+    bottom face whose width is 0.29 n (the paper's D_in, which its R = 74.25
+    at n = 512 makes a diameter), and optionally a solid disc of diameter
+    0.312 n centred horizontally, its centre 0.625 n above the bottom wall.
+    Returns (flags [n][n], (x0, x1) inlet columns)."""
+    fl = plume_flags(n, cylinder_radius=0.156 * n if cylinder else 0.0,
+                     cylinder_height=0.625 * n - 0.5)
+    return fl, inlet_columns(n, width=int(round(0.29 * n)))
+
+
 def plume_initial_state(n: int, seed: int = 0, noise_std: float = 1e-4):
     """rho = 1 + N(0, noise_std^2) per cell, u = v = 0 (FP64)."""
     g = _rng(seed)

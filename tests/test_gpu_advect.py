@@ -97,3 +97,77 @@ def test_plume_128_teacher_forced(dev, threshold):
         assert swept > 0
     # the light fluid rises: negative v above the inlet
     assert sim.v.cpu().numpy()[0][n - 2, n // 2] < 0
+
+
+@pytest.mark.parametrize("shape,dt", [((1, 16, 16), 0.1), ((2, 67, 130), 0.5), ((1, 128, 96), 2.5)])
+def test_maccormack_step_matches_oracle(dev, shape, dt):
+    B, ny, nx = shape
+    rng = np.random.default_rng(ny + nx + 1)
+    us, vs, rs, fs = [], [], [], []
+    for b in range(B):
+        u, v = W.vortex_velocity(ny, nx, 17 + b, n_vortices=6, width=(3, 12))
+        us.append(u); vs.append(v)
+        rs.append(1.0 + 0.05 * rng.standard_normal((ny, nx)))
+        fs.append(W.random_obstacles(ny, nx, 19 + b, rect_side=(3, 12), disc_radius=(2, 6)))
+    u = np.stack(us).astype(np.float32); v = np.stack(vs).astype(np.float32)
+    rho = np.stack(rs).astype(np.float32); fl = np.stack(fs)
+    inlet = (nx // 2 - 4, nx // 2 + 4)
+    pp = hp.PlumeParams(dt=dt, inlet_x0=inlet[0], inlet_x1=inlet[1], scheme=1)
+    uo, vo, ro = hp.hp_advect_step(t(u, dev), t(v, dev), t(rho, dev), t(fl, dev), pp)
+    torch.cuda.synchronize()
+    uo, vo, ro = uo.cpu().numpy(), vo.cpu().numpy(), ro.cpu().numpy()
+    for b in range(B):
+        eu, ev, er = A.advect_step(u[b], v[b], rho[b], fl[b], dt, inlet=inlet,
+                                   scheme="maccormack")
+        umax = max(np.abs(eu).max(), np.abs(ev).max())
+        assert np.abs(uo[b] - eu).max() <= TOL * umax
+        assert np.abs(vo[b] - ev).max() <= TOL * umax
+        assert np.abs(ro[b] - er).max() <= TOL * np.abs(er).max()
+        # and it is not the first-order result
+        su, sv, sr = A.advect_step(u[b], v[b], rho[b], fl[b], dt, inlet=inlet)
+        assert np.abs(er - sr).max() > 100 * TOL * np.abs(er).max()
+    with pytest.raises(hp.HprojError):
+        hp.hp_advect_step(t(u, dev), t(v, dev), t(rho, dev), t(fl, dev),
+                          hp.PlumeParams(dt=dt, scheme=2))
+
+
+def test_plume_head_matches_oracle(dev):
+    n = 96
+    rng = np.random.default_rng(4)
+    rho = np.ones((3, n, n), np.float32)
+    rho[0] += (0.02 * rng.standard_normal((n, n))).astype(np.float32)
+    rho[1, 60:90, 20:31] = 1.1
+    rho[1, 40, 70] = 0.9
+    g = torch.from_numpy(rho).to(dev)
+    for contrast in (0.0, 0.01, 0.03, 0.05, 0.2):
+        got = hp.hp_plume_head(g, 1.0, contrast).cpu().numpy()
+        for b in range(3):
+            assert tuple(got[b]) == A.plume_head(rho[b], 1.0, contrast), (contrast, b)
+
+
+def test_plume_maccormack_paper_geometry_teacher_forced(dev):
+    """The paper's plume with the cylinder (Sec. 2.1) at 128^2, MacCormack
+    advection, every step checked against the oracle from the GPU state."""
+    from paper_2109_09363_gb300.plume import Plume, PlumeConfig
+    n, thr = 128, 1e-7
+    fl, (x0, x1) = W.paper_plume_geometry(n)
+    fl = fl[None]
+    u0, v0, rho0 = W.plume_initial_state(n, seed=1)
+    cfg = PlumeConfig(ny=n, nx=n, dt=0.5, gravity=-0.05, inlet=(x0, x1), threshold=thr,
+                      max_iters=3000, scheme=1)
+    sim = Plume(cfg, t(u0[None].astype(np.float32), dev), t(v0[None].astype(np.float32), dev),
+                t(rho0[None].astype(np.float32), dev), t(fl, dev))
+    for step in range(12):
+        su, sv, sr = (x.cpu().numpy()[0].astype(np.float64) for x in (sim.u, sim.v, sim.rho))
+        sim.advect()
+        eu, ev, er = A.advect_step(su, sv, sr, fl[0], cfg.dt, gravity=cfg.gravity,
+                                   inlet=(x0, x1), scheme="maccormack")
+        gu, gv, gr = (x.cpu().numpy()[0] for x in (sim.u, sim.v, sim.rho))
+        umax = max(np.abs(eu).max(), np.abs(ev).max(), 1e-12)
+        assert np.abs(gu - eu).max() <= TOL * umax, step
+        assert np.abs(gv - ev).max() <= TOL * umax, step
+        assert np.abs(gr - er).max() <= TOL * np.abs(er).max(), step
+        sim.project()
+        torch.cuda.synchronize()
+    hy, _, _ = sim.head()
+    assert float(hy[0]) > 0.0

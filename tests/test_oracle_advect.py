@@ -163,3 +163,20 @@ def test_maccormack_limiter_creates_no_new_extrema():
     jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     lo, hi = A.stencil_range(rho, ii + 0.5 - 0.43, jj + 0.5 - 0.19, 0.5, 0.5)
     assert np.all(r_mc >= lo - 1e-15) and np.all(r_mc <= hi + 1e-15)
+
+
+def test_plume_head_of_constructed_fields():
+    n = 40
+    rho = np.ones((n, n))
+    assert A.plume_head(rho, 1.0, 0.01) == (n, n, -1)
+    # a light blob: rows 12..20, columns 7..30 (a disc clipped by a box)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    blob = ((ii - 18.5) ** 2 / 12.0 ** 2 + (jj - 16.0) ** 2 / 4.5 ** 2 <= 1.0)
+    rho[blob] = 1.05
+    rows, cols = np.nonzero(blob)
+    assert A.plume_head(rho, 1.0, 0.01) == (rows.min(), cols.min(), cols.max())
+    # heavier fluid counts by its contrast too; below the contrast it does not
+    rho[35, 2] = 0.98
+    assert A.plume_head(rho, 1.0, 0.01) == (rows.min(), 2, cols.max())
+    assert A.plume_head(rho, 1.0, 0.03) == (rows.min(), cols.min(), cols.max())
+    assert A.plume_head(rho, 1.0, 0.06) == (n, n, -1)
