@@ -46,7 +46,8 @@ typedef enum {
     HP_ERR_CUDA = 2,        /* a CUDA call or launch failed */
     HP_ERR_NONFINITE = 3,   /* the input velocity holds NaN or Inf */
     HP_ERR_OOM = 5,         /* device allocation failed */
-    HP_ERR_UNSUPPORTED = 6  /* the requested combination is not built */
+    HP_ERR_UNSUPPORTED = 6, /* the requested combination is not built */
+    HP_ERR_TIMEOUT = 7      /* a tensor-core completion wait gave up (hp_cnn_check) */
 } hp_status;
 
 typedef struct {
@@ -251,6 +252,14 @@ void hp_cnn_destroy(hp_cnn *cnn);
  * (5 layers), 1/2 (7), 1 (7); per layer weights [cout][cin][3][3] then bias
  * [cout].  Weights are rounded to BF16 on upload; synchronous. */
 hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
+/* Device-side status of a network: every wait of its tensor-core kernels on
+ * the completion of MMAs or copies is bounded; one that gives up leaves that
+ * kernel's output incomplete, sets an error word of the network and lets the
+ * kernel return instead of hanging.  This call synchronises the device, reads
+ * and clears that word: HP_ERR_TIMEOUT if it was set since the last check (by
+ * hp_cnn_forward, hp_project_hybrid or a trainer built on the network),
+ * else HP_OK. */
+hp_status hp_cnn_check(hp_cnn *cnn);
 hp_status hp_cnn_get_params(const hp_cnn *cnn, float *params, int64_t n);
 /* Network output phi_hat (float [B][ny][nx], device; the guess is s * phi_hat)
  * and s (float [B], device, may be NULL) for the divergence div (float
@@ -314,7 +323,8 @@ hp_status hp_trainer_pdnn_step(hp_trainer *trainer, const float *div, const uint
                                const float *weight, hp_shape shape, int32_t norm,
                                const hp_train_params *params, double *loss_out, void *stream);
 /* Copy the trained FP32 masters into the hp_cnn (hp_cnn_get_params then
- * returns them); synchronises the device. */
+ * returns them); synchronises the device and then reports the network's
+ * device status as hp_cnn_check does (the masters are copied either way). */
 hp_status hp_trainer_sync_params(hp_trainer *trainer);
 
 /* Allocation-free variant of hp_div_norms.  The paper has no counterpart; it

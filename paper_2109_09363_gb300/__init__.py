@@ -76,6 +76,7 @@ _SIGS = {
     "hp_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
     "hp_cnn_destroy": (None, [_P]),
     "hp_cnn_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    "hp_cnn_check": (ctypes.c_int, [_P]),
     "hp_cnn_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "hp_cnn_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
     "hp_project_hybrid": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape,
@@ -408,6 +409,11 @@ class CNN:
         a = np.ascontiguousarray(flat, dtype=np.float32)
         _check(load_library().hp_cnn_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p),
                                                 a.size))
+
+    def check(self):
+        """Raise if a tensor-core wait of this network's kernels timed out
+        since the last check (synchronises the device)."""
+        _check(load_library().hp_cnn_check(self._h))
 
     def get_params(self):
         import numpy as np

@@ -61,6 +61,7 @@ const char* hp_status_string(hp_status s)
     case HP_ERR_NONFINITE: return "non-finite input";
     case HP_ERR_OOM: return "out of device memory";
     case HP_ERR_UNSUPPORTED: return "unsupported";
+    case HP_ERR_TIMEOUT: return "a tensor-core wait timed out";
     }
     return "unknown status";
 }

@@ -1965,7 +1965,18 @@ hp_status hp_trainer_sync_params(hp_trainer* t)
     if (e == cudaSuccess)
         e = cudaMemcpy(t->cnn->master.data(), t->master, t->param_count * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
-    return HP_OK;
+    return hp_cnn_check(t->cnn);
+}
+
+hp_status hp_cnn_check(hp_cnn* c)
+{
+    if (!c) return HP_ERR_INVALID_ARG;
+    int flag = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(c->err, 0, sizeof(int));
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    return flag ? HP_ERR_TIMEOUT : HP_OK;
 }
 
 }  // extern "C"
