@@ -153,7 +153,17 @@ struct ResGeom {
     uint32_t rank;
     bool up, down, left, right;  // neighbouring tiles exist in the cluster
     int cx;
+    // cluster addresses of this thread's halo slots (parity 0) in the
+    // neighbouring CTAs, computed once: up / down row slot of this lane,
+    // left / right column slots of this warp (row 0); parity p adds
+    // p * kParityBytes, row r of a column adds 4 r
+    uint32_t r_up, r_down, r_left, r_right;
 };
+
+// byte offset between the parity-0 and parity-1 halo buffers (rows and columns)
+constexpr uint32_t kParityBytes = 2 * 32 * 16;
+static_assert(2 * kResWarps * kResRows * 4 == (int)kParityBytes,
+              "row and column halo buffers share the parity stride");
 
 // Step 1: this thread's boundary values of phi into the parity-p buffers.
 template <bool CLUSTER>
@@ -168,25 +178,19 @@ __device__ __forceinline__ void res_publish(const ResGeom& g, const float (&phi)
     if (CLUSTER) {
         // the tile above receives our top row as its row "from below" (slot 1),
         // the tile below our bottom row as "from above" (slot 0)
-        if (g.wid == 0 && g.up)
-            st_cluster(remote(&s_hrow[(p * 2 + 1) * 32 + g.lane], g.rank - g.cx), top);
-        if (g.wid == kResWarps - 1 && g.down)
-            st_cluster(remote(&s_hrow[(p * 2 + 0) * 32 + g.lane], g.rank + g.cx), bot);
+        if (g.wid == 0 && g.up) st_cluster(g.r_up + p * kParityBytes, top);
+        if (g.wid == kResWarps - 1 && g.down) st_cluster(g.r_down + p * kParityBytes, bot);
         // the tile to the left receives our left column as "from right" (slot
         // 1), the tile to the right our right column as "from left" (slot 0)
         if (g.lane == 0 && g.left) {
 #pragma unroll
             for (int r = 0; r < kResRows; ++r)
-                st_cluster(remote(&s_hcol[((p * 2 + 1) * kResWarps + g.wid) * kResRows + r],
-                                  g.rank - 1),
-                           phi[r][0]);
+                st_cluster(g.r_left + p * kParityBytes + 4 * r, phi[r][0]);
         }
         if (g.lane == 31 && g.right) {
 #pragma unroll
             for (int r = 0; r < kResRows; ++r)
-                st_cluster(remote(&s_hcol[((p * 2 + 0) * kResWarps + g.wid) * kResRows + r],
-                                  g.rank + 1),
-                           phi[r][3]);
+                st_cluster(g.r_right + p * kParityBytes + 4 * r, phi[r][3]);
         }
     }
 }
@@ -254,21 +258,14 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             const float4 v4 = make_float4(nw[0], nw[1], nw[2], nw[3]);
             s_xch[((q1 * 2 + (r == 0 ? 0 : 1)) * kResWarps + g.wid) * 32 + g.lane] = v4;
             if (CLUSTER) {
-                if (r == 0 && g.wid == 0 && g.up)
-                    st_cluster(remote(&s_hrow[(q1 * 2 + 1) * 32 + g.lane], g.rank - g.cx), v4);
+                if (r == 0 && g.wid == 0 && g.up) st_cluster(g.r_up + q1 * kParityBytes, v4);
                 if (r == kResRows - 1 && g.wid == kResWarps - 1 && g.down)
-                    st_cluster(remote(&s_hrow[(q1 * 2 + 0) * 32 + g.lane], g.rank + g.cx), v4);
+                    st_cluster(g.r_down + q1 * kParityBytes, v4);
             }
         }
         if (CLUSTER) {
-            if (g.lane == 0 && g.left)
-                st_cluster(remote(&s_hcol[((q1 * 2 + 1) * kResWarps + g.wid) * kResRows + r],
-                                  g.rank - 1),
-                           nw[0]);
-            if (g.lane == 31 && g.right)
-                st_cluster(remote(&s_hcol[((q1 * 2 + 0) * kResWarps + g.wid) * kResRows + r],
-                                  g.rank + 1),
-                           nw[3]);
+            if (g.lane == 0 && g.left) st_cluster(g.r_left + q1 * kParityBytes + 4 * r, nw[0]);
+            if (g.lane == 31 && g.right) st_cluster(g.r_right + q1 * kParityBytes + 4 * r, nw[3]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -314,6 +311,13 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
     g.down = ty < a.cy - 1;
     g.left = tx > 0;
     g.right = tx < a.cx - 1;
+    g.r_up = g.r_down = g.r_left = g.r_right = 0u;
+    if (CLUSTER) {
+        if (g.up) g.r_up = remote(&s_hrow[1 * 32 + g.lane], g.rank - g.cx);
+        if (g.down) g.r_down = remote(&s_hrow[0 * 32 + g.lane], g.rank + g.cx);
+        if (g.left) g.r_left = remote(&s_hcol[(1 * kResWarps + g.wid) * kResRows], g.rank - 1);
+        if (g.right) g.r_right = remote(&s_hcol[(0 * kResWarps + g.wid) * kResRows], g.rank + 1);
+    }
     const int nranks = a.cx * a.cy;
     const int nx = a.nx, ny = a.ny;
     const size_t gbase = (size_t)b * ny * nx;
