@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "hproj_internal.cuh"
 
 namespace hp {
@@ -199,9 +201,9 @@ __device__ __forceinline__ void res_publish(const ResGeom& g, const float (&phi)
 // thread's FP32 sum of |r(phi_k)| when WITH_E.  With BOOK (warp 0), the two
 // FP64 reduction trees t0, t1 over lanes 0..15 advance one level after each
 // of the first four rows.
-template <bool CLUSTER, bool WITH_E, bool BOOK>
+template <bool CLUSTER, bool WITH_E, bool BOOK, int p>
 __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResRows][4],
-                                            int p, float4* s_xch,
+                                            float4* s_xch,
                                             float4* s_hrow, float* s_hcol,
                                             const float4* s_inv4, const float4* s_d4,
                                             const uint2* s_c2, double& t0, double& t1)
@@ -210,7 +212,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
     // computed, so that the stores have landed by the next barrier; those
     // buffers were last read in the previous sweep, before the barrier this
     // thread has passed
-    const int q1 = p ^ 1;
+    constexpr int q1 = p ^ 1;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 nb = g.wid > 0 ? s_xch[((p * 2 + 1) * kResWarps + g.wid - 1) * 32 + g.lane]
                       : g.up    ? s_hrow[(p * 2 + 0) * 32 + g.lane]
@@ -381,11 +383,14 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
     // boundary values are in the parity-(k & 1) buffers (sweep k - 1 wrote
     // them during its update; phi_0's go out here)
     res_publish<CLUSTER>(g, phi, 0, s_xch, s_hrow, s_hcol);
-    for (int k = 0;; ++k) {
-        const int p = k & 1;
-        if (k > 0 && k % kCkptEvery == 0) store_cells(ckpt_buf(a, k / kCkptEvery));
+    // one sweep k of parity P (the loop below runs them in pairs so that the
+    // halo buffers' parity is a compile-time constant); true: stop
+    auto sweep = [&](auto parity, int k) -> bool {
+        constexpr int P = decltype(parity)::value;
+        // checkpoints (every 32nd sweep) and E rounds (every 4th) fall on even k
+        if (P == 0 && k > 0 && k % kCkptEvery == 0) store_cells(ckpt_buf(a, k / kCkptEvery));
         sweep_arrive<CLUSTER>();
-        if (g.wid == 0 && k % kBatch == 0) {
+        if (P == 0 && g.wid == 0 && k % kBatch == 0) {
             // one round, between arrive and wait, on data visible since the
             // previous barrier; lane group gi (8 lanes) takes sweep
             // jc = k - kBatch - 1 + gi for the CTA partial (its 16 warp sums)
@@ -449,16 +454,21 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
                 kstar = j;
                 dec = dj;
                 estar = s_edec[j % kDecRing];
-                break;
+                return true;
             }
         }
         double t0 = 0.0, t1 = 0.0;
-        const float acc = res_update<CLUSTER, true, false>(g, phi, p, s_xch, s_hrow,
-                                                           s_hcol, s_inv4, s_d4, s_c2, t0, t1);
+        const float acc = res_update<CLUSTER, true, false, P>(g, phi, s_xch, s_hrow, s_hcol,
+                                                              s_inv4, s_d4, s_c2, t0, t1);
         float t = acc;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
         if (g.lane == 0) s_wsum[(k % kWsumRing) * kResWarps + g.wid] = t;
+        return false;
+    };
+    for (int k = 0;; k += 2) {
+        if (sweep(std::integral_constant<int, 0>{}, k)) break;
+        if (sweep(std::integral_constant<int, 1>{}, k + 1)) break;
     }
 
     // ---- replay from the checkpoint at or below k* to phi_{k*}
@@ -479,11 +489,14 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
     // checkpoint's boundary values can go out at once
     res_publish<CLUSTER>(g, phi, (m * kCkptEvery) & 1, s_xch, s_hrow, s_hcol);
     for (int j = m * kCkptEvery; j < kstar; ++j) {
-        const int p = j & 1;
         sweep_barrier<CLUSTER>();
         double t0 = 0.0, t1 = 0.0;
-        res_update<CLUSTER, false, false>(g, phi, p, s_xch, s_hrow, s_hcol, s_inv4, s_d4,
-                                          s_c2, t0, t1);
+        if (j & 1)
+            res_update<CLUSTER, false, false, 1>(g, phi, s_xch, s_hrow, s_hcol, s_inv4, s_d4,
+                                                 s_c2, t0, t1);
+        else
+            res_update<CLUSTER, false, false, 0>(g, phi, s_xch, s_hrow, s_hcol, s_inv4, s_d4,
+                                                 s_c2, t0, t1);
     }
     store_cells(a.phi);
     if (threadIdx.x == 0 && g.rank == 0) {
