@@ -42,7 +42,10 @@ TRAIN_SWEEPS = 40000
 IN_DIST_GRIDS, IN_DIST_SEED = 256, 100000
 T_BLOCK = 8
 BYTES_PER_CELL_SWEEP = 13  # read phi 4, div 4, mask 1; write phi 4
-OPS_PER_CELL_UPDATE = 11   # FP32 operations of one masked Jacobi cell update
+# FP32 operations of one masked Jacobi cell update in increment form: the two
+# neighbour differences it owns (each difference serves two cells), 3 adds,
+# the closed-face, residual and update FMAs, the |r| add
+OPS_PER_CELL_UPDATE = 9
 WORKLOAD = ("16 x 512^2 MAC grids, 32 Gaussian vortices + 1-6 obstacles each, plain Jacobi "
             "to mean|div| <= 1e-4 (cap 5000), FP32 sweeps, FP64 stop test")
 
@@ -725,10 +728,9 @@ def main():
     if os.path.exists(tp):
         traffic = json.load(open(tp)).get(kname)
     if resident:
-        # on-chip for all sweeps: bound by FP32 issue, not by HBM.  11 FP32
-        # operations per cell update (4 neighbour differences, 3 adds, the
-        # closed-face, residual and update FMAs, the |r| add) against the
-        # FP32 lane rate (SMs x 128 lanes x maximum SM clock)
+        # on-chip for all sweeps: bound by FP32 issue, not by HBM.
+        # OPS_PER_CELL_UPDATE FP32 operations per cell update against the FP32
+        # lane rate (SMs x 128 lanes x maximum SM clock)
         sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
         max_mhz = clk.get("sm_max_mhz") or 2070.0
         alu_peak = sm_count * 128 * max_mhz * 1e6 / 1e12

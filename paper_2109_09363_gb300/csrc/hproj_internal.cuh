@@ -130,6 +130,19 @@ __device__ __forceinline__ float cell_update(float pc, float pw, float pe, float
     return __fmaf_rn(-r, k.inv, pc);
 }
 
+// The same update from the four neighbour differences dw = pw - pc, ...;
+// a caller that forms each difference between two cells once and negates it
+// for the other cell (x - y == -(y - x) exactly) gets identical results.
+__device__ __forceinline__ float cell_update_diff(float pc, float dw, float de, float dn,
+                                                  float ds, const CellConst& k, float& res)
+{
+    const float lapd = __fadd_rn(__fadd_rn(dw, de), __fadd_rn(dn, ds));
+    const float lap = __fmaf_rn(k.c, pc, lapd);
+    const float r = __fmaf_rn(-k.w, lap, k.d);
+    res = r;
+    return __fmaf_rn(-r, k.inv, pc);
+}
+
 // Loads four consecutive cells of a row (float), zero outside [0, nx).
 __device__ __forceinline__ void load_row4(const float* __restrict__ row, int x0, int nx, bool vec,
                                           float out[4])

@@ -223,8 +223,14 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
                                : zero;
     const float* hl = s_hcol + ((p * 2 + 0) * kResWarps + g.wid) * kResRows;
     const float* hr = s_hcol + ((p * 2 + 1) * kResWarps + g.wid) * kResRows;
-    float up[4] = {nb.x, nb.y, nb.z, nb.w};
+    const float north[4] = {nb.x, nb.y, nb.z, nb.w};
     const float south[4] = {sb.x, sb.y, sb.z, sb.w};
+    // each difference between two cells is formed once: the south difference
+    // of row r is minus the north difference of row r + 1, the east
+    // difference of a cell minus the west difference of the next
+    float dn[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dn[q] = __fsub_rn(north[q], phi[0][q]);
     float acc = 0.0f;
 #pragma unroll
     for (int r = 0; r < kResRows; ++r) {
@@ -240,12 +246,17 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
         const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
         const float cc[4] = {__uint_as_float(cb.x << 16), __uint_as_float(cb.x & 0xffff0000u),
                              __uint_as_float(cb.y << 16), __uint_as_float(cb.y & 0xffff0000u)};
-        float nw[4];
+        // east differences: ex[0] = phi[0] - left, ex[q + 1] = east of cell q
+        float ex[5];
+        ex[0] = __fsub_rn(phi[r][0], left);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ex[q + 1] = __fsub_rn(phi[r][q + 1], phi[r][q]);
+        ex[4] = __fsub_rn(right, phi[r][3]);
+        float nw[4], ds[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float pw = q > 0 ? phi[r][q - 1] : left;
-            const float pe = q < 3 ? phi[r][q + 1] : right;
             const float ps = r < kResRows - 1 ? phi[r + 1][q] : south[q];
+            ds[q] = __fsub_rn(ps, phi[r][q]);
             CellConst kc;
             kc.d = dd[q];
             kc.inv = inv[q];
@@ -253,7 +264,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             // [n > 0] from 1/n in {0, 1/4, 1/3, 1/2, 1}: saturate(4/n) is exactly 0 or 1
             kc.w = __saturatef(inv[q] * 4.0f);
             float res;
-            nw[q] = cell_update(phi[r][q], pw, pe, up[q], ps, kc, res);
+            nw[q] = cell_update_diff(phi[r][q], -ex[q], ex[q + 1], dn[q], ds[q], kc, res);
             if (WITH_E) acc = __fadd_rn(acc, fabsf(res));
         }
         if (r == 0 || r == kResRows - 1) {
@@ -271,7 +282,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            up[q] = phi[r][q];
+            dn[q] = -ds[q];
             phi[r][q] = nw[q];
         }
         if (BOOK && r < 4) {
