@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
         s_c2[slot] = make_uint2(cb[0] | (cb[1] << 16), cb[2] | (cb[3] << 16));
     }
     if (threadIdx.x < kDecRing) s_dec[threadIdx.x] = 0;
+    // every CTA of the cluster is running before any CTA stores into
+    // another's shared memory
+    sweep_barrier<CLUSTER>();
 
     auto store_cells = [&](float* dst) {
 #pragma unroll
