@@ -231,7 +231,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
     float dn[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) dn[q] = __fsub_rn(north[q], phi[0][q]);
-    float acc = 0.0f;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // one |r| sum per column: short chains
 #pragma unroll
     for (int r = 0; r < kResRows; ++r) {
         float left = __shfl_up_sync(0xffffffffu, phi[r][3], 1);
@@ -265,7 +265,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             kc.w = __saturatef(inv[q] * 4.0f);
             float res;
             nw[q] = cell_update_diff(phi[r][q], -ex[q], ex[q + 1], dn[q], ds[q], kc, res);
-            if (WITH_E) acc = __fadd_rn(acc, fabsf(res));
+            if (WITH_E) acc[q] = __fadd_rn(acc[q], fabsf(res));
         }
         if (r == 0 || r == kResRows - 1) {
             const float4 v4 = make_float4(nw[0], nw[1], nw[2], nw[3]);
@@ -290,7 +290,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
             t1 += __shfl_down_sync(0xffffffffu, t1, 8 >> r);
         }
     }
-    return acc;
+    return __fadd_rn(__fadd_rn(acc[0], acc[1]), __fadd_rn(acc[2], acc[3]));
 }
 
 __device__ __forceinline__ float* ckpt_buf(const ResArgs& a, int m)
@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
     // boundary values are in the parity-(k & 1) buffers (sweep k - 1 wrote
     // them during its update; phi_0's go out here)
     res_publish<CLUSTER>(g, phi, 0, s_xch, s_hrow, s_hcol);
+    float pending = 0.0f;  // this thread's sum of |r| of the previous sweep
     // one sweep k of parity P (the loop below runs them in pairs so that the
     // halo buffers' parity is a compile-time constant); true: stop
     auto sweep = [&](auto parity, int k) -> bool {
@@ -404,6 +405,15 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
         // checkpoints (every 32nd sweep) and E rounds (every 4th) fall on even k
         if (P == 0 && k > 0 && k % kCkptEvery == 0) store_cells(ckpt_buf(a, k / kCkptEvery));
         sweep_arrive<CLUSTER>();
+        if (k > 0) {
+            // warp sum of sweep k - 1, reduced while the barrier completes; the
+            // book-keeping reads warp sums two or more sweeps old
+            float t = pending;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
+            if (g.lane == 0) s_wsum[((k - 1) % kWsumRing) * kResWarps + g.wid] = t;
+        }
         if (P == 0 && g.wid == 0 && k % kBatch == 0) {
             // one round, between arrive and wait, on data visible since the
             // previous barrier; lane group gi (8 lanes) takes sweep
@@ -472,12 +482,8 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             }
         }
         double t0 = 0.0, t1 = 0.0;
-        const float acc = res_update<CLUSTER, true, false, P>(g, phi, s_xch, s_hrow, s_hcol,
-                                                              s_inv4, s_d4, s_c2, t0, t1);
-        float t = acc;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, off));
-        if (g.lane == 0) s_wsum[(k % kWsumRing) * kResWarps + g.wid] = t;
+        pending = res_update<CLUSTER, true, false, P>(g, phi, s_xch, s_hrow, s_hcol, s_inv4,
+                                                      s_d4, s_c2, t0, t1);
         return false;
     };
     for (int k = 0;; k += 2) {
