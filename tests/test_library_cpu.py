@@ -55,3 +55,57 @@ def test_binding_rejects_cpu_tensors():
 def test_cnn_parameter_count_matches_the_oracle(lib):
     from oracle import cnn as C
     assert int(lib.hp_cnn_param_count()) == C.param_count() == 372643
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """The binding's structures have the sizes and field offsets the C compiler
+    gives the header's (the ABI the Python names marshal into)."""
+    import os
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "hproj.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu\\n", sizeof(hp_shape), sizeof(hp_project_params),\n'
+        "         sizeof(hp_plume_params), sizeof(hp_train_params));\n"
+        '  printf("%zu %zu %zu\\n", offsetof(hp_plume_params, scheme),\n'
+        "         offsetof(hp_project_params, fixed_iters), offsetof(hp_train_params, lambda_div));\n"
+        "  return 0; }\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()
+    sizes = [int(x) for x in out[:4]]
+    offs = [int(x) for x in out[4:]]
+    assert sizes == [ctypes.sizeof(hp.hp_shape), ctypes.sizeof(hp.hp_project_params),
+                     ctypes.sizeof(hp.hp_plume_params), ctypes.sizeof(hp.hp_train_params)]
+    assert offs == [hp.hp_plume_params.scheme.offset, hp.hp_project_params.fixed_iters.offset,
+                    hp.hp_train_params.lambda_div.offset]
+
+
+def test_new_entry_points_reject_null_arguments(lib):
+    s = hp.hp_shape(1, 4, 4)
+    assert lib.hp_plume_head(None, s, 1.0, 0.01, None, None) == 1
+    assert lib.hp_cnn_check(None) == 1
+    assert lib.hp_trainer_pdnn_gradient(None, None, None, None, s, 1, None, None, None) == 1
+    assert lib.hp_status_string(7) == b"a tensor-core wait timed out"
+    pp = hp.PlumeParams(scheme=1).c()
+    assert lib.hp_advect_step(None, None, None, None, None, None, None, s, ctypes.byref(pp),
+                              None) == 1
+
+
+def test_paper_plume_geometry():
+    import numpy as np
+    from paper_2109_09363_gb300 import workloads as W
+    n = 512
+    fl, (x0, x1) = W.paper_plume_geometry(n)
+    assert x1 - x0 == round(0.29 * n) and (x0 + x1) / 2 == n / 2
+    # disc of diameter 0.312 n, centre 0.625 n above the bottom wall
+    r, cy = 0.156 * n, n - 0.625 * n
+    assert fl[int(cy), n // 2] == 1 and fl.sum() == pytest.approx(np.pi * r * r, rel=0.01)
+    rows = np.nonzero(fl.any(axis=1))[0]
+    assert (rows.min() + rows.max() + 1) / 2 == pytest.approx(cy, abs=1.0)
+    fl0, _ = W.paper_plume_geometry(n, cylinder=False)
+    assert fl0.sum() == 0
