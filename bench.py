@@ -317,6 +317,7 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     uncapped["speedup"] = uncapped["plain"]["ms_per_step"] / uncapped["hybrid"]["ms_per_step"]
     cnn_eval.close()
     in_dist = compare_in_distribution(hp, trained, flush, stream, u0.device, ws)
+    plume = compare_plume_same_threshold(hp, trained, u0.device)
     # MACs per full-resolution pixel of the network: 148,608 (scale 1) +
     # 148,608 / 4 (scale 1/2) + 74,592 / 16 (scale 1/4)
     flop = 2.0 * 190422 * B * N * N
@@ -335,10 +336,60 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
                                      "380.8 kFLOP per full-resolution pixel"},
             "equal_threshold_uncapped": uncapped,
             "in_distribution_128": in_dist,
+            "plume_same_threshold": plume,
             "training": {"pairs": 2048, "grid": [n_tr, n_tr], "target_sweeps": TRAIN_SWEEPS,
                          "steps": len(losses),
                          "batch": batch, "final_loss": float(np.mean(losses[-20:])),
                          "seconds": t_train}}
+
+
+def compare_plume_same_threshold(hp, params, dev, n=128, steps=300, thr=1e-5, cap=20000):
+    """The paper's plume with the cylinder (Sec. 2.1 geometry) at 128^2,
+    MacCormack advection, buoyancy g = -0.5 (the plume rises about 20 cells in
+    300 steps of dt = 0.5), every projection stopped by the same mean |div|
+    threshold: plain Jacobi from zero against the hybrid with the trained
+    network.  Reports the sweeps and time of each run and how far apart the
+    two plume-head trajectories are (Sec. 4.2: the same E_1 should give the
+    same plume)."""
+    import torch
+    from paper_2109_09363_gb300 import workloads as W
+    from paper_2109_09363_gb300.plume import Plume, PlumeConfig
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    fl, (x0, x1) = W.paper_plume_geometry(n)
+    fl = t(fl[None])
+    u0, v0, rho0 = W.plume_initial_state(n, seed=2)
+    cfg = PlumeConfig(ny=n, nx=n, dt=0.5, gravity=-0.5, inlet=(x0, x1), threshold=thr,
+                      max_iters=cap, scheme=1)
+    res = {"workload": f"{n}^2 plume, inlet 0.29 n, cylinder 0.312 n at 0.625 n, MacCormack, "
+                       f"g = -0.5, dt = 0.5, {steps} steps, E_t = {thr}, cap {cap}"}
+    heads = {}
+    for mode in ("plain", "hybrid"):
+        cnn = hp.CNN(1, n, n, params=params) if mode == "hybrid" else None
+        sim = Plume(cfg, t(u0[None].astype(np.float32)), t(v0[None].astype(np.float32)),
+                    t(rho0[None].astype(np.float32)), fl, cnn=cnn)
+        it = torch.zeros(steps, dtype=torch.int32, device=dev)
+        cv = torch.zeros(steps, dtype=torch.uint8, device=dev)
+        hd = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            out = sim.step()
+            it[k:k + 1].copy_(out["iters"])
+            cv[k:k + 1].copy_(out["converged"])
+            hd.append(torch.stack(sim.head()).view(-1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        heads[mode] = torch.stack(hd).cpu().numpy() * n
+        res[mode] = {"sweeps": int(it.sum().item()), "converged_steps": int(cv.sum().item()),
+                     "seconds": wall, "final_head_cells": heads[mode][-1].tolist()}
+        if cnn is not None:
+            cnn.check()
+            cnn.close()
+    d = np.abs(heads["plain"] - heads["hybrid"]).max(axis=0)
+    res["max_head_difference_cells"] = {"h_y": float(d[0]), "left": float(d[1]),
+                                        "right": float(d[2])}
+    res["sweep_ratio"] = res["plain"]["sweeps"] / max(res["hybrid"]["sweeps"], 1)
+    return res
 
 
 def compare_in_distribution(hp, params, flush, stream, dev, ws):
