@@ -277,26 +277,35 @@ __global__ void __launch_bounds__((kTileRows / R) * 32, 1) sweep_tb_kernel(Sweep
         const float4 nb = wid > 0 ? bot[(wid - 1) * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 sb =
             wid < NW - 1 ? top[(wid + 1) * 32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float up[4] = {nb.x, nb.y, nb.z, nb.w};
+        const float north[4] = {nb.x, nb.y, nb.z, nb.w};
         const float south[4] = {sb.x, sb.y, sb.z, sb.w};
+        // each difference between two cells is formed once and negated for
+        // the other cell (exact), as in the grid-resident kernel
+        float dn[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dn[q] = __fsub_rn(north[q], phi[0][q]);
         float acc = 0.0f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float left = __shfl_up_sync(0xffffffffu, phi[r][3], 1);
             const float right = __shfl_down_sync(0xffffffffu, phi[r][0], 1);
-            float nw[4];
+            float ex[5];
+            ex[0] = __fsub_rn(phi[r][0], left);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ex[q + 1] = __fsub_rn(phi[r][q + 1], phi[r][q]);
+            ex[4] = __fsub_rn(right, phi[r][3]);
+            float nw[4], ds[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float pw = q > 0 ? phi[r][q - 1] : left;
-                const float pe = q < 3 ? phi[r][q + 1] : right;
                 const float ps = r < R - 1 ? phi[r + 1][q] : south[q];
+                ds[q] = __fsub_rn(ps, phi[r][q]);
                 float res;
-                nw[q] = cell_update(phi[r][q], pw, pe, up[q], ps, kc[r][q], res);
+                nw[q] = cell_update_diff(phi[r][q], -ex[q], ex[q + 1], dn[q], ds[q], kc[r][q], res);
                 acc = __fadd_rn(acc, fabsf(res));
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                up[q] = phi[r][q];
+                dn[q] = -ds[q];
                 phi[r][q] = nw[q];
             }
         }
