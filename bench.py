@@ -208,6 +208,7 @@ def profile_sweep(batch: int, n: int, sweeps: int, host_loop: bool = False,
     v = torch.from_numpy(np.stack(vs).astype(np.float32)).to(dev)
     fl = torch.from_numpy(np.stack(fs)).to(dev)
     ctx = hp.Context(batch, n, n)
+    times = []
     if host_loop:
         prm = hp.ProjectParams(fixed_iters=sweeps, temporal_block=T_BLOCK, use_graph=0,
                                sweep_kernel=kernel)
@@ -215,14 +216,29 @@ def profile_sweep(batch: int, n: int, sweeps: int, host_loop: bool = False,
         for _ in range(3):
             uw.copy_(u)
             vw.copy_(v)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             hp.hp_project(ctx, uw, vw, fl, prm)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
     else:
         div = hp.hp_divergence(u, v, fl)
         phi = torch.zeros_like(div)
         for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             hp.hp_jacobi_sweeps(ctx, phi, div, fl, sweeps)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
     torch.cuda.synchronize()
-    print(json.dumps({"profile_sweep": [batch, n, sweeps], "ok": True}))
+    # the last call, whole projection (host loop) or sweeps only; effective
+    # bandwidth = 13 B per cell-sweep
+    ms = times[-1]
+    print(json.dumps({"profile_sweep": [batch, n, sweeps], "ok": True, "ms_last_call": ms,
+                      "effective_gbs": BYTES_PER_CELL_SWEEP * batch * n * n * sweeps /
+                      (ms * 1e-3) / 1e9}))
     ctx.close()
     return 0
 
