@@ -341,3 +341,38 @@ def test_resident_kernel_matches_blocked_kernel(dev, shape):
                 assert np.all(np.abs(eh - thr) / thr <= 1e-6), (shape, i, lo, hi)
     g = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=1e-3, max_iters=1500, sweep_kernel=4))
     check_projection(g, u, v, fl, 1e-3, 1500)
+
+
+def test_resident_kernel_matches_blocked_kernel_on_random_shapes(dev):
+    """24 seeded random cases: shapes 1..512 on either side (clusters of 1 to
+    16 CTAs in every aspect ratio, ragged tiles), 1-5 grids, thresholds
+    1e-5..1e-2 and caps 0..1199: the same bits as the blocked kernel, or a
+    stop that differs only at a near tie of E."""
+    rng = np.random.default_rng(2026)
+    for trial in range(24):
+        ny, nx = int(rng.integers(1, 513)), int(rng.integers(1, 513))
+        B = int(rng.integers(1, 6))
+        us, vs, fs = [], [], []
+        for b in range(B):
+            u1, v1 = W.vortex_velocity(ny, nx, 9000 + 10 * trial + b,
+                                       n_vortices=int(rng.integers(2, 12)),
+                                       width=(1.0, max(2.0, min(ny, nx) / 6)))
+            us.append(u1); vs.append(v1)
+            fs.append(W.random_obstacles(ny, nx, 7000 + 10 * trial + b,
+                                         rect_side=(1, max(2, min(ny, nx) / 5)),
+                                         disc_radius=(1, max(2, min(ny, nx) / 10))))
+        u, v, fl = f32(np.stack(us)), f32(np.stack(vs)), np.stack(fs)
+        thr, cap = float(10 ** rng.uniform(-5, -2)), int(rng.integers(0, 1200))
+        a = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap, sweep_kernel=2),
+                    hist_len=cap + 2)
+        b_ = run_gpu(dev, u, v, fl, hp.ProjectParams(threshold=thr, max_iters=cap, sweep_kernel=4),
+                     hist_len=cap + 2)
+        for i in range(B):
+            case = (trial, (B, ny, nx), i, thr, cap)
+            if a["iters"][i] == b_["iters"][i]:
+                assert np.array_equal(a["u"][i], b_["u"][i]), case
+                assert np.array_equal(a["v"][i], b_["v"][i]), case
+            else:
+                lo, hi = sorted((int(a["iters"][i]), int(b_["iters"][i])))
+                eh = a["e_hist"][i, lo:hi + 1]
+                assert np.all(np.abs(eh - thr) / thr <= 1e-6), case
