@@ -957,7 +957,7 @@ __global__ void dgrad_first_ch2_kernel(const GT* __restrict__ gy, const float* _
 }
 
 // Row groups per block of the sliding-window weight gradients.
-constexpr int kRowGroups = 8;
+constexpr int kRowGroups = 4;
 
 // Weight and bias gradient of the last layer of a branch (32 -> 1) over the
 // g-th of G equal ranges of image rows: part[g][tap][ci], partb[g].  Block =
@@ -1629,12 +1629,12 @@ static hp_status wgrad_t(hp_trainer* t, const GT* gy, const XT* x, float* gw, fl
     return check_launch();
 }
 
-// row ranges of the sliding-window weight gradients: two blocks of
+// row ranges of the sliding-window weight gradients: four blocks of
 // kRowGroups x 3 warps per SM (each warp scans its rows serially; the
 // latency of one scan is hidden by the others)
 static int row_blocks(hp_trainer* t, long rows)
 {
-    const long g = 2L * t->cnn->num_sms;
+    const long g = 4L * t->cnn->num_sms;
     return (int)(rows < g ? rows : g);
 }
 
