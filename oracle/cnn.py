@@ -1,4 +1,5 @@
-"""FP64 oracle of the MultiScale CNN (Sec. 3.1, MultiScale architecture), numpy.
+"""FP64 oracle of the MultiScale CNN and of its narrower SmallScale variant
+(Sec. 3.1, network architectures), numpy.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -11,6 +12,11 @@ after every convolution of a branch except its last two; down-sampling is 2 x
 half-pixel centres; up-sampling is bilinear x 2 at half-pixel centres with the
 edge sample repeated.  372,643 parameters.
 
+SmallScale (Sec. 3.1): the same structure with fewer filters per layer, about
+three times fewer parameters.  Reading: every 64-channel layer has 32
+channels, 2 -> 32 -> 32 -> 32 -> 32 -> 1 and 3 -> 32 -> 32 -> 32 -> 32 -> 32
+-> 32 -> 1; 123,491 parameters (3.02 times fewer).
+
 Layout: activations [C][H][W] (one grid), weights [Cout][Cin][3][3].
 """
 from __future__ import annotations
@@ -22,33 +28,40 @@ BRANCH_WIDTHS = {
     2: [3, 32, 64, 64, 64, 64, 32, 1],       # scale 1/2
     1: [3, 32, 64, 64, 64, 64, 32, 1],       # full scale
 }
+SMALL_WIDTHS = {
+    4: [2, 32, 32, 32, 32, 1],
+    2: [3, 32, 32, 32, 32, 32, 32, 1],
+    1: [3, 32, 32, 32, 32, 32, 32, 1],
+}
+ARCHS = {"multiscale": BRANCH_WIDTHS, "smallscale": SMALL_WIDTHS}
 SCALES = (4, 2, 1)
 
 
-def param_shapes():
+def param_shapes(arch="multiscale"):
     """[(scale, layer, (Cout, Cin, 3, 3), (Cout,))] in network order."""
     out = []
     for sc in SCALES:
-        w = BRANCH_WIDTHS[sc]
+        w = ARCHS[arch][sc]
         for l in range(len(w) - 1):
             out.append((sc, l, (w[l + 1], w[l], 3, 3), (w[l + 1],)))
     return out
 
 
-def param_count():
-    return sum(int(np.prod(ws)) + int(np.prod(bs)) for _, _, ws, bs in param_shapes())
+def param_count(arch="multiscale"):
+    return sum(int(np.prod(ws)) + int(np.prod(bs)) for _, _, ws, bs in param_shapes(arch))
 
 
 def relu_after(sc, l):
-    """ReLU after every convolution of a branch except its last two."""
+    """ReLU after every convolution of a branch except its last two (both
+    architectures have the same number of layers per branch)."""
     return l < len(BRANCH_WIDTHS[sc]) - 3
 
 
-def init_params(seed=0):
+def init_params(seed=0, arch="multiscale"):
     """He-uniform weights, zero biases (a deterministic starting point)."""
     g = np.random.Generator(np.random.PCG64(seed))
     params = []
-    for sc, l, ws, bs in param_shapes():
+    for sc, l, ws, bs in param_shapes(arch):
         fan_in = ws[1] * 9
         lim = np.sqrt(6.0 / fan_in)
         params.append((g.uniform(-lim, lim, ws), np.zeros(bs)))
@@ -174,9 +187,9 @@ def flatten(params):
     return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params])
 
 
-def unflatten(flat):
+def unflatten(flat, arch="multiscale"):
     out, k = [], 0
-    for _, _, ws, bs in param_shapes():
+    for _, _, ws, bs in param_shapes(arch):
         nw, nb = int(np.prod(ws)), int(np.prod(bs))
         out.append((np.asarray(flat[k:k + nw], np.float64).reshape(ws),
                     np.asarray(flat[k + nw:k + nw + nb], np.float64)))

@@ -1,6 +1,7 @@
-"""Pins of the FP64 MultiScale CNN oracle (Sec. 3.1): library special cases
+"""Pins of the FP64 MultiScale and SmallScale CNN oracle (Sec. 3.1): library special cases
 (torch conv2d / pooling / interpolation in FP64 on CPU, used only here to pin
-the oracle), adjointness, finite differences and the parameter count."""
+the oracle), adjointness, finite differences, the parameter counts and the
+embedding of the SmallScale in a zero-padded MultiScale."""
 import numpy as np
 import pytest
 
@@ -104,3 +105,73 @@ def test_forward_shapes_and_scale_structure():
     assert len(params) == 5 + 7 + 7
     out = C.forward(params, np.zeros((16, 16)), np.zeros((16, 16), np.uint8))
     assert out.shape == (16, 16)
+
+
+def test_smallscale_parameter_count():
+    # about three times fewer parameters than the MultiScale (Sec. 3.1)
+    assert C.param_count("smallscale") == 123491
+    assert 2.5 < C.param_count() / C.param_count("smallscale") < 3.5
+    shapes = C.param_shapes("smallscale")
+    assert len(shapes) == len(C.param_shapes()) == 19
+    assert max(ws[0] for _, _, ws, _ in shapes) == 32
+
+
+def embed_small_in_multiscale(small):
+    """MultiScale parameters that compute the SmallScale network: its weights
+    in the first channels of every layer, zeros on the extra channels (their
+    pre-activations are 0, ReLU keeps them 0, and no later weight reads them)."""
+    out = []
+    for (_, _, ws, bs), (w, b) in zip(C.param_shapes(), small):
+        W_ = np.zeros(ws)
+        B_ = np.zeros(bs)
+        W_[:w.shape[0], :w.shape[1]] = w
+        B_[:b.shape[0]] = b
+        out.append((W_, B_))
+    return out
+
+
+def test_smallscale_is_a_zero_padded_multiscale():
+    rng = np.random.default_rng(7)
+    small = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in
+             C.init_params(seed=3, arch="smallscale")]
+    big = embed_small_in_multiscale(small)
+    n = 16
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    gout = rng.standard_normal((n, n))
+    o_s, tape_s = C.forward(small, div, fl, keep=True)
+    o_b, tape_b = C.forward(big, div, fl, keep=True)
+    assert np.array_equal(o_s, o_b)
+    g_s = C.backward(small, tape_s, gout)
+    g_b = C.backward(big, tape_b, gout)
+    for (gw, gb), (hw, hb) in zip(g_s, g_b):
+        assert np.allclose(gw, hw[:gw.shape[0], :gw.shape[1]], rtol=1e-12, atol=1e-14)
+        assert np.allclose(gb, hb[:gb.shape[0]], rtol=1e-12, atol=1e-14)
+    # flatten / unflatten round trip in the SmallScale layout
+    flat = C.flatten(small)
+    assert flat.size == C.param_count("smallscale")
+    back = C.unflatten(flat, "smallscale")
+    assert all(np.array_equal(a, c) and np.array_equal(b, d)
+               for (a, b), (c, d) in zip(small, back))
+
+
+def test_smallscale_gradients_by_central_differences():
+    rng = np.random.default_rng(8)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in
+              C.init_params(seed=4, arch="smallscale")]
+    n = 8
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    gout = rng.standard_normal((n, n))
+    _, tape = C.forward(params, div, fl, keep=True)
+    grads = C.backward(params, tape, gout)
+    eps = 1e-6
+    for li in [1, 2, 7, 14]:
+        w = params[li][0]
+        idx = tuple(rng.integers(0, s) for s in w.shape)
+        wp = [(ww.copy(), bb) for ww, bb in params]
+        wm = [(ww.copy(), bb) for ww, bb in params]
+        wp[li][0][idx] += eps
+        wm[li][0][idx] -= eps
+        fd = (np.sum(C.forward(wp, div, fl) * gout) - np.sum(C.forward(wm, div, fl) * gout)) / (2 * eps)
+        assert np.isclose(grads[li][0][idx], fd, rtol=1e-5, atol=1e-8), (li, idx)
