@@ -38,6 +38,11 @@ CAP_UNCAPPED, UNCAPPED_STEPS = 40000, 3
 # fixed Jacobi sweeps behind each 128^2 training target (about 0.5 % relative
 # L2 error against the exact solve)
 TRAIN_SWEEPS = 40000
+# multiply-adds per full-resolution pixel of each network: the scale-1 branch,
+# a quarter of the scale-1/2 branch, a sixteenth of the scale-1/4 branch
+# (MultiScale 148,608 + 148,608 / 4 + 74,592 / 16; SmallScale 47,232 +
+# 47,232 / 4 + 28,512 / 16)
+CNN_MACS_PER_PIXEL = {"multiscale": 190422, "smallscale": 60822}
 # held-out grids of the training distribution for the in-distribution comparison
 IN_DIST_GRIDS, IN_DIST_SEED = 256, 100000
 T_BLOCK = 8
@@ -269,74 +274,83 @@ def profile_sweep(batch: int, n: int, sweeps: int, host_loop: bool = False,
 
 
 def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain, ws):
-    """CNN-hybrid projection of the same grids to the same threshold.
+    """CNN-hybrid projection of the same grids to the same threshold, with the
+    MultiScale and with the SmallScale network (Sec. 3.1).
 
     Untimed set-up: training pairs from the plain solver (128^2, vortex field +
-    divergence sources + 0-4 obstacles), Adam training on the GPU.  Timed: the
-    same per-step protocol as the plain arm (device restore of u*, L2 flush
-    between steps, CUDA events)."""
+    divergence sources + 0-4 obstacles), Adam training of each network on the
+    GPU with the same pairs and schedule.  Timed: the same per-step protocol
+    as the plain arm (device restore of u*, L2 flush between steps, CUDA
+    events)."""
     import torch
     from paper_2109_09363_gb300 import training as T
     t0 = time.perf_counter()
     n_tr = 128
     data = T.generate_pairs(2048, n_tr, seed0=0, sweeps=TRAIN_SWEEPS, device=u0.device)
+    t_pairs = time.perf_counter() - t0
     batch = 32
     epochs = max(1, (args.train_steps * batch + 2047) // 2048)
-    cnn = hp.CNN(batch, n_tr, n_tr, params=T.init_params(seed=1))
-    losses = T.train(cnn, data, epochs=epochs, batch=batch, lr=1e-3, lambda_div=1.0)
-    t_train = time.perf_counter() - t0
+    trained, train_info = {}, {}
+    for arch in ("multiscale", "smallscale"):
+        t1 = time.perf_counter()
+        cnn = hp.CNN(batch, n_tr, n_tr, params=T.init_params(seed=1, arch=arch), arch=arch)
+        losses = T.train(cnn, data, epochs=epochs, batch=batch, lr=1e-3, lambda_div=1.0)
+        trained[arch] = cnn.get_params()
+        cnn.close()
+        train_info[arch] = {"steps": len(losses), "final_loss": float(np.mean(losses[-20:])),
+                            "seconds": time.perf_counter() - t1}
     del data
-    trained = cnn.get_params()
-    cnn_eval = hp.CNN(B, N, N, params=trained)
-    cnn.close()
-    out = None
 
-    def step():
-        nonlocal out
-        u.copy_(u0)
-        v.copy_(v0)
-        out = hp.hp_project_hybrid(ctx, cnn_eval, u, v, fl, prm, out=out)
+    def time_capped(net):
+        res = None
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    iters = out["iters"].cpu().numpy()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for s_ in range(args.steps):
-        flush.fill_(float(s_))
-        ev[s_][0].record(stream)
-        step()
-        ev[s_][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    # inference alone (t_inf of the paper)
-    div = hp.hp_divergence(u0, v0, fl)
-    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    hp.hp_cnn_forward(cnn_eval, div, fl)
-    a.record(stream)
-    for _ in range(5):
-        hp.hp_cnn_forward(cnn_eval, div, fl)
-    b_.record(stream)
-    torch.cuda.synchronize()
-    t_inf = a.elapsed_time(b_) / 5
+        def step():
+            nonlocal res
+            u.copy_(u0)
+            v.copy_(v0)
+            res = hp.hp_project_hybrid(ctx, net, u, v, fl, prm, out=res)
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for s_ in range(args.steps):
+            flush.fill_(float(s_))
+            ev[s_][0].record(stream)
+            step()
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a_.elapsed_time(b2) for a_, b2 in ev) / args.steps, res
+
+    def time_inference(net):
+        # inference alone (t_inf of the paper)
+        div = hp.hp_divergence(u0, v0, fl)
+        a_, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hp.hp_cnn_forward(net, div, fl)
+        a_.record(stream)
+        for _ in range(5):
+            hp.hp_cnn_forward(net, div, fl)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        return a_.elapsed_time(b2) / 5
 
     # the same grids and threshold with the cap lifted far enough that every
     # grid converges in both arms: projections/s at equal mean|div|
     prm_u = hp.ProjectParams(threshold=THR, max_iters=CAP_UNCAPPED, temporal_block=T_BLOCK,
                              use_graph=prm.use_graph, sweep_kernel=prm.sweep_kernel)
-    uncapped = {}
-    for arm in ("plain", "hybrid"):
+
+    def time_uncapped(net):
         res = None
 
         def ustep():
             nonlocal res
             u.copy_(u0)
             v.copy_(v0)
-            if arm == "plain":
+            if net is None:
                 res = hp.hp_project(ctx, u, v, fl, prm_u, out=res)
             else:
-                res = hp.hp_project_hybrid(ctx, cnn_eval, u, v, fl, prm_u, out=res)
+                res = hp.hp_project_hybrid(ctx, net, u, v, fl, prm_u, out=res)
 
         ustep()
         torch.cuda.synchronize()
@@ -349,39 +363,54 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
             e1.record(stream)
         torch.cuda.synchronize()
         ms_u = sum(a_.elapsed_time(b2) for a_, b2 in ev_u) / UNCAPPED_STEPS
-        uncapped[arm] = {"value": ws * B / (ms_u * 1e-3), "ms_per_step": ms_u,
-                         "iters_per_grid": res["iters"].cpu().numpy().tolist(),
-                         "converged": int(res["converged"].sum().item()),
-                         "e1_max": float(res["e1"].max().item())}
-    uncapped["cap"] = CAP_UNCAPPED
-    uncapped["steps"] = UNCAPPED_STEPS
-    uncapped["speedup"] = uncapped["plain"]["ms_per_step"] / uncapped["hybrid"]["ms_per_step"]
-    cnn_eval.close()
-    in_dist = compare_in_distribution(hp, trained, flush, stream, u0.device, ws)
-    plume = compare_plume_same_threshold(hp, trained, u0.device)
-    # MACs per full-resolution pixel of the network: 148,608 (scale 1) +
-    # 148,608 / 4 (scale 1/2) + 74,592 / 16 (scale 1/4)
-    flop = 2.0 * 190422 * B * N * N
-    tf = flop / (t_inf * 1e-3) / 1e12
+        return {"value": ws * B / (ms_u * 1e-3), "ms_per_step": ms_u,
+                "iters_per_grid": res["iters"].cpu().numpy().tolist(),
+                "converged": int(res["converged"].sum().item()),
+                "e1_max": float(res["e1"].max().item())}
+
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     tpk = float(peaks.get("bf16_tflops", 1900.0))
-    return {"value": ws * B / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "speedup_vs_plain": ms_plain / ms, "iters_per_grid": iters.tolist(),
+    uncapped_plain = time_uncapped(None)
+    arms = {}
+    for arch in ("multiscale", "smallscale"):
+        net = hp.CNN(B, N, N, params=trained[arch], arch=arch)
+        ms, out = time_capped(net)
+        t_inf = time_inference(net)
+        unc = time_uncapped(net)
+        # MACs per full-resolution pixel: the scale-1 branch, a quarter of the
+        # scale-1/2 branch and a sixteenth of the scale-1/4 branch
+        flop = 2.0 * CNN_MACS_PER_PIXEL[arch] * B * N * N
+        tf = flop / (t_inf * 1e-3) / 1e12
+        arms[arch] = {
+            "params": net.n_params, "value": ws * B / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "speedup_vs_plain": ms_plain / ms,
+            "iters_per_grid": out["iters"].cpu().numpy().tolist(),
             "converged": int(out["converged"].sum().item()),
             "t_inf_ms_16_grids": t_inf,
-            "cnn_roofline": {"bound": "tensor", "achieved": tf, "peak": tpk,
-                             "unit": "TFLOP/s", "frac": tf / tpk,
+            "cnn_roofline": {"bound": "tensor", "achieved": tf, "peak": tpk, "unit": "TFLOP/s",
+                             "frac": tf / tpk,
                              "peak_kind": "measured" if peaks else "fallback",
                              "note": "whole network forward (BF16, FP32 accumulate), "
-                                     "380.8 kFLOP per full-resolution pixel"},
-            "equal_threshold_uncapped": uncapped,
-            "in_distribution_128": in_dist,
-            "plume_same_threshold": plume,
-            "training": {"pairs": 2048, "grid": [n_tr, n_tr], "target_sweeps": TRAIN_SWEEPS,
-                         "steps": len(losses),
-                         "batch": batch, "final_loss": float(np.mean(losses[-20:])),
-                         "seconds": t_train}}
+                                     f"{2 * CNN_MACS_PER_PIXEL[arch] / 1e3:.1f} kFLOP per "
+                                     "full-resolution pixel"},
+            "equal_threshold_uncapped": {"hybrid": unc, "plain": uncapped_plain,
+                                         "cap": CAP_UNCAPPED, "steps": UNCAPPED_STEPS,
+                                         "speedup": uncapped_plain["ms_per_step"] /
+                                         unc["ms_per_step"]},
+            "training": dict(train_info[arch], pairs=2048, grid=[n_tr, n_tr],
+                             target_sweeps=TRAIN_SWEEPS, batch=batch,
+                             pair_generation_seconds=t_pairs)}
+        net.close()
+    ms_arm = arms.pop("multiscale")
+    in_dist = compare_in_distribution(hp, trained["multiscale"], flush, stream, u0.device, ws)
+    plume = compare_plume_same_threshold(hp, trained["multiscale"], u0.device)
+    ms_arm["in_distribution_128"] = in_dist
+    ms_arm["plume_same_threshold"] = plume
+    ms_arm["smallscale"] = arms["smallscale"]
+    ms_arm["smallscale"]["t_inf_ratio_multiscale_over_smallscale"] = (
+        ms_arm["t_inf_ms_16_grids"] / arms["smallscale"]["t_inf_ms_16_grids"])
+    return ms_arm
 
 
 def compare_plume_same_threshold(hp, params, dev, n=128, steps=300, thr=1e-5, cap=20000):
@@ -597,7 +626,7 @@ def profile_conv(batch, h, w, cin, cout) -> int:
     return 0
 
 
-def profile_cnn(batch, n) -> int:
+def profile_cnn(batch, n, arch="multiscale") -> int:
     """Time the CNN forward (t_inf) on BATCH vortex grids of N x N."""
     import torch
     import __graft_entry__
@@ -610,7 +639,7 @@ def profile_cnn(batch, n) -> int:
     ud = torch.from_numpy(u.astype(np.float32)).to(dev)
     vd = torch.from_numpy(v.astype(np.float32)).to(dev)
     fd = torch.from_numpy(fl).to(dev)
-    cnn = hp.CNN(batch, n, n, params=T.init_params(seed=1))
+    cnn = hp.CNN(batch, n, n, params=T.init_params(seed=1, arch=arch), arch=arch)
     div = hp.hp_divergence(ud, vd, fd)
     for _ in range(3):
         hp.hp_cnn_forward(cnn, div, fd)
@@ -621,9 +650,9 @@ def profile_cnn(batch, n) -> int:
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 5
-    # MACs per full-resolution pixel: 148,608 + 148,608 / 4 + 74,592 / 16
-    flop = 2.0 * 190422 * batch * n * n
-    print(json.dumps({"profile_cnn": [batch, n], "ms": ms, "tflops": flop / ms / 1e9}))
+    flop = 2.0 * CNN_MACS_PER_PIXEL[arch] * batch * n * n
+    print(json.dumps({"profile_cnn": [batch, n], "arch": arch, "ms": ms,
+                      "tflops": flop / ms / 1e9}))
     return 0
 
 
@@ -682,6 +711,8 @@ def main():
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
     ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
+    ap.add_argument("--arch", default="multiscale", choices=["multiscale", "smallscale"],
+                    help="network of --profile-cnn")
     ap.add_argument("--profile-train", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the physics-driven loss gradient on BATCH grids of N x N, "
                          "8 times (a small case for ncu)")
@@ -705,7 +736,7 @@ def main():
     if args.profile_conv:
         return profile_conv(*args.profile_conv)
     if args.profile_cnn:
-        return profile_cnn(*args.profile_cnn)
+        return profile_cnn(*args.profile_cnn, arch=args.arch)
     if args.profile_train:
         return profile_train(*args.profile_train)
 

@@ -245,10 +245,21 @@ hp_status hp_project_adjoint(hp_ctx *ctx, const float *gu, const float *gv, cons
  * An hp_cnn owns its device weights and a workspace for grids up to
  * max_shape (ny, nx multiples of 4). */
 typedef struct hp_cnn hp_cnn;
+/* Architectures (Sec. 3.1).  SmallScale: the MultiScale graph with fewer
+ * filters, every 64-channel layer at 32 channels, 123,491 parameters. */
+typedef enum { HP_CNN_MULTISCALE = 0, HP_CNN_SMALLSCALE = 1 } hp_cnn_arch;
+/* Parameter count of the MultiScale; of the architecture arch (-1 if arch is
+ * not one of hp_cnn_arch). */
 int64_t hp_cnn_param_count(void);
+int64_t hp_cnn_arch_param_count(int32_t arch);
+/* A MultiScale network (hp_cnn_create) or one of architecture arch;
+ * HP_ERR_INVALID_ARG for an unknown arch or a bad shape. */
 hp_status hp_cnn_create(hp_cnn **cnn, hp_shape max_shape, int device);
+hp_status hp_cnn_create_arch(hp_cnn **cnn, int32_t arch, hp_shape max_shape, int device);
+/* The architecture of cnn (-1 for NULL). */
+int32_t hp_cnn_get_arch(const hp_cnn *cnn);
 void hp_cnn_destroy(hp_cnn *cnn);
-/* params: HOST float [hp_cnn_param_count()], layers in the order scale 1/4
+/* params: HOST float [hp_cnn_arch_param_count(arch)], layers in the order scale 1/4
  * (5 layers), 1/2 (7), 1 (7); per layer weights [cout][cin][3][3] then bias
  * [cout].  Weights are rounded to BF16 on upload; synchronous. */
 hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
@@ -293,7 +304,7 @@ typedef struct {
 hp_status hp_trainer_create(hp_trainer **trainer, hp_cnn *cnn, hp_shape max_shape);
 void hp_trainer_destroy(hp_trainer *trainer);
 /* Loss (double [1], device, may be NULL) and its gradient w.r.t. every
- * parameter (float [hp_cnn_param_count()], device, may be NULL; network
+ * parameter (float [the network's parameter count], device, may be NULL; network
  * parameter order) for one batch; div, target float [B][ny][nx], flags u8. */
 hp_status hp_trainer_gradient(hp_trainer *trainer, const float *div, const uint8_t *flags,
                               const float *target, hp_shape shape, float lambda_div,

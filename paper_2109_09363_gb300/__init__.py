@@ -73,7 +73,11 @@ _SIGS = {
     "hp_trainer_pdnn_step": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_int32,
                                             ctypes.c_void_p, _P, _P]),
     "hp_cnn_param_count": (ctypes.c_int64, []),
+    "hp_cnn_arch_param_count": (ctypes.c_int64, [ctypes.c_int32]),
     "hp_cnn_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
+    "hp_cnn_create_arch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, hp_shape,
+                                          ctypes.c_int]),
+    "hp_cnn_get_arch": (ctypes.c_int32, [_P]),
     "hp_cnn_destroy": (None, [_P]),
     "hp_cnn_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "hp_cnn_check": (ctypes.c_int, [_P]),
@@ -384,21 +388,33 @@ def hp_project_adjoint(ctx: Context, gu, gv, gp, flags, k: int, dt: float = 1.0,
     return gus, gvs, gphi
 
 
-class CNN:
-    """MultiScale CNN weights and workspace on the device (hp_cnn)."""
+CNN_ARCHS = {"multiscale": 0, "smallscale": 1}  # hp_cnn_arch
 
-    def __init__(self, batch: int, ny: int, nx: int, device: int | None = None, params=None):
+
+class CNN:
+    """CNN weights and workspace on the device (hp_cnn): the MultiScale or
+    its narrower SmallScale variant (Sec. 3.1)."""
+
+    def __init__(self, batch: int, ny: int, nx: int, device: int | None = None, params=None,
+                 arch: str = "multiscale"):
         torch = _torch()
         lib = load_library()
+        if arch not in CNN_ARCHS:
+            raise ValueError(f"arch must be one of {sorted(CNN_ARCHS)}")
         dev = torch.cuda.current_device() if device is None else device
+        self.arch = arch
+        self.n_params = CNN.param_count(arch)
         self._h = _P()
-        _check(lib.hp_cnn_create(ctypes.byref(self._h), hp_shape(batch, ny, nx), dev))
+        _check(lib.hp_cnn_create_arch(ctypes.byref(self._h), CNN_ARCHS[arch],
+                                      hp_shape(batch, ny, nx), dev))
         if params is not None:
             self.set_params(params)
 
     @staticmethod
-    def param_count() -> int:
-        return int(load_library().hp_cnn_param_count())
+    def param_count(arch: str = "multiscale") -> int:
+        if arch not in CNN_ARCHS:
+            raise ValueError(f"arch must be one of {sorted(CNN_ARCHS)}")
+        return int(load_library().hp_cnn_arch_param_count(CNN_ARCHS[arch]))
 
     @property
     def handle(self):
@@ -417,7 +433,7 @@ class CNN:
 
     def get_params(self):
         import numpy as np
-        a = np.empty(self.param_count(), dtype=np.float32)
+        a = np.empty(self.n_params, dtype=np.float32)
         _check(load_library().hp_cnn_get_params(self._h, a.ctypes.data_as(ctypes.c_void_p),
                                                 a.size))
         return a
@@ -451,7 +467,7 @@ class Trainer:
     def gradient(self, div, flags, target, lambda_div=0.1, stream=None):
         torch = _torch()
         s = _shape_of_flags(flags)
-        g = torch.empty(CNN.param_count(), dtype=torch.float32, device=div.device)
+        g = torch.empty(self.cnn.n_params, dtype=torch.float32, device=div.device)
         loss = torch.empty(1, dtype=torch.float64, device=div.device)
         _check(load_library().hp_trainer_gradient(self._h, _ptr(div), _ptr(flags), _ptr(target),
                                                   s, float(lambda_div), _ptr(g), _ptr(loss),
@@ -476,7 +492,7 @@ class Trainer:
         torch = _torch()
         s = _shape_of_flags(flags)
         _check_dtype(weight, torch.float32, (flags.shape[0],), "weight")
-        g = torch.empty(CNN.param_count(), dtype=torch.float32, device=div.device)
+        g = torch.empty(self.cnn.n_params, dtype=torch.float32, device=div.device)
         loss = torch.empty(1, dtype=torch.float64, device=div.device)
         _check(load_library().hp_trainer_pdnn_gradient(self._h, _ptr(div), _ptr(flags),
                                                        _ptr(weight), s, int(norm), _ptr(g),

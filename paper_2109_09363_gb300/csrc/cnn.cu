@@ -37,11 +37,24 @@ struct LayerSpec {
 
 // network order: scale 1/4, then 1/2, then 1
 constexpr int kLayers = 19;
-const LayerSpec kSpec[kLayers] = {
+const LayerSpec kSpecMulti[kLayers] = {
     {4, 2, 32, 1},  {4, 32, 64, 1}, {4, 64, 64, 1}, {4, 64, 32, 0}, {4, 32, 1, 0},
     {2, 3, 32, 1},  {2, 32, 64, 1}, {2, 64, 64, 1}, {2, 64, 64, 1}, {2, 64, 64, 1},
     {2, 64, 32, 0}, {2, 32, 1, 0},  {1, 3, 32, 1},  {1, 32, 64, 1}, {1, 64, 64, 1},
     {1, 64, 64, 1}, {1, 64, 64, 1}, {1, 64, 32, 0}, {1, 32, 1, 0}};
+// SmallScale (Sec. 3.1): the same graph with fewer filters, every 64-channel
+// layer at 32 channels (123,491 parameters, about three times fewer)
+const LayerSpec kSpecSmall[kLayers] = {
+    {4, 2, 32, 1},  {4, 32, 32, 1}, {4, 32, 32, 1}, {4, 32, 32, 0}, {4, 32, 1, 0},
+    {2, 3, 32, 1},  {2, 32, 32, 1}, {2, 32, 32, 1}, {2, 32, 32, 1}, {2, 32, 32, 1},
+    {2, 32, 32, 0}, {2, 32, 1, 0},  {1, 3, 32, 1},  {1, 32, 32, 1}, {1, 32, 32, 1},
+    {1, 32, 32, 1}, {1, 32, 32, 1}, {1, 32, 32, 0}, {1, 32, 1, 0}};
+
+const LayerSpec* spec_for(int arch)
+{
+    return arch == HP_CNN_MULTISCALE ? kSpecMulti : arch == HP_CNN_SMALLSCALE ? kSpecSmall
+                                                                              : nullptr;
+}
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
@@ -357,6 +370,8 @@ __global__ void phi0_kernel(const float* __restrict__ out, const float* __restri
 using namespace hp;
 
 struct hp_cnn {
+    int arch;               // hp_cnn_arch
+    const LayerSpec* spec;  // its layer table
     int device;
     int num_sms;
     hp_shape max_shape;
@@ -445,7 +460,7 @@ static hp_status pack_edge_layers(hp_cnn* c, cudaStream_t st)
     for (int k = 0; k < 3; ++k) {
         const int lf = kFirstLayer[k], ll = kLastLayer[k];
         pack_edge_layers_kernel<<<(9 * 32 * 16 + 255) / 256, 256, 0, st>>>(
-            (const float*)c->w[lf], kSpec[lf].cin, c->wtc_first[k], (const float*)c->w[ll],
+            (const float*)c->w[lf], c->spec[lf].cin, c->wtc_first[k], (const float*)c->w[ll],
             c->bias[ll], c->wtc_last[k], c->btc_last[k]);
         hp_status rc = check_launch();
         if (rc != HP_OK) return rc;
@@ -453,16 +468,25 @@ static hp_status pack_edge_layers(hp_cnn* c, cudaStream_t st)
     return HP_OK;
 }
 
-static size_t layer_wcount(int l) { return (size_t)9 * kSpec[l].cin * kSpec[l].cout; }
+static size_t layer_wcount(const LayerSpec* sp, int l)
+{
+    return (size_t)9 * sp[l].cin * sp[l].cout;
+}
 
 extern "C" {
 
-int64_t hp_cnn_param_count(void)
+int64_t hp_cnn_arch_param_count(int32_t arch)
 {
+    const LayerSpec* sp = spec_for(arch);
+    if (!sp) return -1;
     int64_t n = 0;
-    for (int l = 0; l < kLayers; ++l) n += (int64_t)layer_wcount(l) + kSpec[l].cout;
+    for (int l = 0; l < kLayers; ++l) n += (int64_t)layer_wcount(sp, l) + sp[l].cout;
     return n;
 }
+
+int64_t hp_cnn_param_count(void) { return hp_cnn_arch_param_count(HP_CNN_MULTISCALE); }
+
+int32_t hp_cnn_get_arch(const hp_cnn* c) { return c ? c->arch : -1; }
 
 void hp_cnn_destroy(hp_cnn* c)
 {
@@ -488,28 +512,32 @@ void hp_cnn_destroy(hp_cnn* c)
     delete c;
 }
 
-hp_status hp_cnn_create(hp_cnn** out, hp_shape mx, int device)
+hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device)
 {
-    if (!out || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
+    if (!out) return HP_ERR_INVALID_ARG;
     *out = nullptr;
+    if (!spec_for(arch) || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     hp_cnn* c = new hp_cnn();
+    c->arch = arch;
+    c->spec = spec_for(arch);
     memset(c->w, 0, sizeof(c->w));
     memset(c->bias, 0, sizeof(c->bias));
     c->device = device;
     c->max_shape = mx;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    c->master.assign((size_t)hp_cnn_param_count(), 0.0f);
+    c->master.assign((size_t)hp_cnn_arch_param_count(arch), 0.0f);
     const size_t px = (size_t)mx.batch * mx.ny * mx.nx;
     bool okm = true;
     for (int l = 0; l < kLayers && okm; ++l) {
-        const size_t wb = layer_wcount(l) * (kSpec[l].cin >= 32 && kSpec[l].cout >= 32 ? 2 : 4);
+        const LayerSpec& ls = c->spec[l];
+        const size_t wb = layer_wcount(c->spec, l) * (ls.cin >= 32 && ls.cout >= 32 ? 2 : 4);
         okm = cudaMalloc(&c->w[l], wb) == cudaSuccess &&
-              cudaMalloc((void**)&c->bias[l], kSpec[l].cout * sizeof(float)) == cudaSuccess;
+              cudaMalloc((void**)&c->bias[l], c->spec[l].cout * sizeof(float)) == cudaSuccess;
         if (okm) {
             cudaMemset(c->w[l], 0, wb);
-            cudaMemset(c->bias[l], 0, kSpec[l].cout * sizeof(float));
+            cudaMemset(c->bias[l], 0, c->spec[l].cout * sizeof(float));
         }
     }
     okm = okm && cudaMalloc((void**)&c->act[0], px * 64 * 2) == cudaSuccess &&
@@ -541,20 +569,26 @@ hp_status hp_cnn_create(hp_cnn** out, hp_shape mx, int device)
     return HP_OK;
 }
 
+hp_status hp_cnn_create(hp_cnn** out, hp_shape mx, int device)
+{
+    return hp_cnn_create_arch(out, HP_CNN_MULTISCALE, mx, device);
+}
+
 // params: host FP32 in the order of the network (scale 1/4, 1/2, 1), each
 // layer weights [cout][cin][3][3] then bias [cout].  Weights are rounded to
 // BF16 on upload.
 hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
 {
-    if (!c || !params || n != hp_cnn_param_count()) return HP_ERR_INVALID_ARG;
+    if (!c || !params || n != hp_cnn_arch_param_count(c->arch)) return HP_ERR_INVALID_ARG;
     memcpy(c->master.data(), params, (size_t)n * sizeof(float));
     const float* p = params;
     for (int l = 0; l < kLayers; ++l) {
-        const int ci = kSpec[l].cin, co = kSpec[l].cout;
+        const int ci = c->spec[l].cin, co = c->spec[l].cout;
         const bool tc = ci >= 32 && co >= 32;
         std::vector<uint16_t> wb;
         std::vector<float> wf;
-        if (tc) wb.assign(layer_wcount(l), 0); else wf.assign(layer_wcount(l), 0.0f);
+        const size_t nw = layer_wcount(c->spec, l);
+        if (tc) wb.assign(nw, 0); else wf.assign(nw, 0.0f);
         for (int o = 0; o < co; ++o)
             for (int i = 0; i < ci; ++i)
                 for (int t = 0; t < 9; ++t) {
@@ -570,7 +604,7 @@ hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
                         wf[((size_t)t * ci + i) * co + o] = __bfloat162float(h);  // [tap][cin][cout]
                     }
                 }
-        p += layer_wcount(l);
+        p += layer_wcount(c->spec, l);
         cudaError_t e = tc ? cudaMemcpy(c->w[l], wb.data(), wb.size() * 2, cudaMemcpyHostToDevice)
                            : cudaMemcpy(c->w[l], wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -588,7 +622,7 @@ hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
 
 hp_status hp_cnn_get_params(const hp_cnn* c, float* params, int64_t n)
 {
-    if (!c || !params || n != hp_cnn_param_count()) return HP_ERR_INVALID_ARG;
+    if (!c || !params || n != hp_cnn_arch_param_count(c->arch)) return HP_ERR_INVALID_ARG;
     memcpy(params, c->master.data(), (size_t)n * sizeof(float));
     return HP_OK;
 }
@@ -613,13 +647,13 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
         const int H = s.ny / scale, W = s.nx / scale;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
         int cur = 0;
-        rc = launch_first(c, k, in, kSpec[l].cin, nullptr, (const float*)c->w[l], c->bias[l],
+        rc = launch_first(c, k, in, c->spec[l].cin, nullptr, (const float*)c->w[l], c->bias[l],
                           c->act[cur], s.batch, H, W, st);
         if (rc != HP_OK) return rc;
         ++l;
-        while (kSpec[l].cout != 1) {
+        while (c->spec[l].cout != 1) {
             rc = launch_conv3x3_tc(c->act[cur], c->w[l], c->bias[l], c->act[cur ^ 1], s.batch, H,
-                                   W, kSpec[l].cin, kSpec[l].cout, kSpec[l].relu, c->err,
+                                   W, c->spec[l].cin, c->spec[l].cout, c->spec[l].relu, c->err,
                                    c->num_sms, st);
             if (rc != HP_OK) return rc;
             cur ^= 1;
@@ -1439,18 +1473,16 @@ struct hp_trainer {
     int step;
 };
 
-static long layer_offset(int l)
+static long layer_offset(const LayerSpec* sp, int l)
 {
     long off = 0;
-    for (int k = 0; k < l; ++k) off += (long)layer_wcount(k) + kSpec[k].cout;
+    for (int k = 0; k < l; ++k) off += (long)layer_wcount(sp, k) + sp[k].cout;
     return off;
 }
 
-static int scale_of(int l) { return kSpec[l].scale; }
-
 // layers whose backward runs on the tensor cores (at widths from
 // conv_tc_min_width() up): 32 or 64 channels on both sides
-static bool tc_layer(int l) { return kSpec[l].cin >= 32 && kSpec[l].cout >= 32; }
+static bool tc_layer(const LayerSpec* sp, int l) { return sp[l].cin >= 32 && sp[l].cout >= 32; }
 
 static hp_status trainer_pack(hp_trainer* t, cudaStream_t st);
 
@@ -1486,7 +1518,8 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     memset(t, 0, sizeof(*t));
     t->cnn = cnn;
     t->max = mx;
-    t->param_count = hp_cnn_param_count();
+    t->param_count = hp_cnn_arch_param_count(cnn->arch);
+    const LayerSpec* sp = cnn->spec;
     const size_t P = (size_t)mx.batch * mx.ny * mx.nx;
     bool ok = true;
     auto al = [&](void** p, size_t bytes) {
@@ -1498,11 +1531,11 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     al((void**)&t->m, t->param_count * 4);
     al((void**)&t->v, t->param_count * 4);
     for (int l = 0; l < kLayers; ++l) {
-        const int sc = scale_of(l);
+        const int sc = sp[l].scale;
         const size_t Pl = P / (sc * sc);
-        al(&t->act[l], kSpec[l].cout == 1 ? Pl * 4 : Pl * kSpec[l].cout * 2);
-        al((void**)&t->wt[l], layer_wcount(l) * 4);
-        if (tc_layer(l)) al((void**)&t->wdg[l], layer_wcount(l) * 2);
+        al(&t->act[l], sp[l].cout == 1 ? Pl * 4 : Pl * sp[l].cout * 2);
+        al((void**)&t->wt[l], layer_wcount(sp, l) * 4);
+        if (tc_layer(sp, l)) al((void**)&t->wdg[l], layer_wcount(sp, l) * 2);
     }
     al((void**)&t->zero_bias, 64 * 4);
     for (int k = 0; k < 3; ++k) {
@@ -1540,11 +1573,12 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
 
 static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
 {
+    const LayerSpec* sp = t->cnn->spec;
     for (int l = 0; l < kLayers; ++l) {
-        const int ci = kSpec[l].cin, co = kSpec[l].cout;
+        const int ci = sp[l].cin, co = sp[l].cout;
         const int kind = (ci >= 32 && co >= 32) ? 0 : (co == 1 ? 2 : 1);
         const int n = 9 * ci * co + co;
-        pack_layer_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->master + layer_offset(l), ci, co,
+        pack_layer_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->master + layer_offset(sp, l), ci, co,
                                                           kind, t->cnn->w[l], t->cnn->bias[l],
                                                           t->wt[l], t->wdg[l]);
     }
@@ -1557,6 +1591,7 @@ static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
 static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t* flags,
                                  hp_shape s, cudaStream_t st)
 {
+    const LayerSpec* sp = t->cnn->spec;
     hp_cnn* c = t->cnn;
     const size_t cells = (size_t)s.ny * s.nx;
     hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
@@ -1566,13 +1601,13 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
         const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
         const int H = s.ny / scale, W = s.nx / scale;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
-        rc = launch_first(c, k, in, kSpec[l].cin, t->xin[k], (const float*)c->w[l], c->bias[l],
+        rc = launch_first(c, k, in, sp[l].cin, t->xin[k], (const float*)c->w[l], c->bias[l],
                           (__nv_bfloat16*)t->act[l], s.batch, H, W, st);
         if (rc != HP_OK) return rc;
         ++l;
-        while (kSpec[l].cout != 1) {
+        while (sp[l].cout != 1) {
             rc = launch_conv3x3_tc(t->act[l - 1], c->w[l], c->bias[l], t->act[l], s.batch, H, W,
-                                   kSpec[l].cin, kSpec[l].cout, kSpec[l].relu, c->err, c->num_sms,
+                                   sp[l].cin, sp[l].cout, sp[l].relu, c->err, c->num_sms,
                                    st);
             if (rc != HP_OK) return rc;
             ++l;
@@ -1609,6 +1644,7 @@ static hp_status dgrad_dispatch(int ci, int co, const float* gy, const float* w,
     if (ci == 64 && co == 64) return dgrad<64, 64>(gy, w, gx, B, H, W, nsm, st);
     if (ci == 32 && co == 64) return dgrad<32, 64>(gy, w, gx, B, H, W, nsm, st);
     if (ci == 64 && co == 32) return dgrad<64, 32>(gy, w, gx, B, H, W, nsm, st);
+    if (ci == 32 && co == 32) return dgrad<32, 32>(gy, w, gx, B, H, W, nsm, st);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1655,7 +1691,8 @@ template <typename GT>
 static hp_status wgrad_first(hp_trainer* t, int k, int l, const GT* gy, float* gw, float* gb,
                              int B, int H, int W, cudaStream_t st)
 {
-    const int cx = kSpec[l].cin;
+    const LayerSpec* sp = t->cnn->spec;
+    const int cx = sp[l].cin;
     const int G = row_blocks(t, (long)B * H);
     if ((size_t)G * 9 * 32 * cx > t->part_len || (size_t)G * 32 > t->partb_len)
         return HP_ERR_INVALID_ARG;
@@ -1694,11 +1731,13 @@ static hp_status dgrad_last(hp_trainer* t, int l, const float* gy, OT* gx, int B
 static hp_status wgrad_dispatch(hp_trainer* t, int k, int l, const float* gy, const void* x,
                                 float* gw, float* gb, int B, int H, int W, cudaStream_t st)
 {
-    const int ci = kSpec[l].cin, co = kSpec[l].cout;
+    const LayerSpec* sp = t->cnn->spec;
+    const int ci = sp[l].cin, co = sp[l].cout;
     const __nv_bfloat16* xb = (const __nv_bfloat16*)x;
     if (ci == 64 && co == 64) return wgrad_t<64, 64, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
     if (ci == 32 && co == 64) return wgrad_t<32, 64, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
     if (ci == 64 && co == 32) return wgrad_t<64, 32, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
+    if (ci == 32 && co == 32) return wgrad_t<32, 32, 4, 4>(t, gy, xb, gw, gb, B, H, W, st);
     if (ci == 32 && co == 1) return wgrad_last(t, l, gy, gw, gb, B, H, W, st);
     if (co == 32 && (ci == 3 || ci == 2)) return wgrad_first(t, k, l, gy, gw, gb, B, H, W, st);
     return HP_ERR_UNSUPPORTED;
@@ -1722,8 +1761,9 @@ static hp_status border_terms(const __nv_bfloat16* gy, const float* w, const __n
 static hp_status first_layer_bf16(hp_trainer* t, int k, int l, const __nv_bfloat16* gy, int B,
                                   int H, int W, cudaStream_t st)
 {
-    float* gw = t->grad + layer_offset(l);
-    hp_status rc = wgrad_first(t, k, l, gy, gw, gw + layer_wcount(l), B, H, W, st);
+    const LayerSpec* sp = t->cnn->spec;
+    float* gw = t->grad + layer_offset(sp, l);
+    hp_status rc = wgrad_first(t, k, l, gy, gw, gw + layer_wcount(sp, l), B, H, W, st);
     if (rc != HP_OK || k == 0) return rc;
     return dgrad_first_ch2(t, l, gy, B, H, W, st);
 }
@@ -1734,31 +1774,32 @@ static hp_status first_layer_bf16(hp_trainer* t, int k, int l, const __nv_bfloat
 static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast, float* gout,
                                     __nv_bfloat16* gbuf[2], int B, int H, int W, cudaStream_t st)
 {
+    const LayerSpec* sp = t->cnn->spec;
     hp_cnn* c = t->cnn;
     // last layer (32 -> 1, CUDA cores): weight gradient from the FP32 output
     // gradient, input gradient into BF16
-    float* gw = t->grad + layer_offset(llast);
-    hp_status rc = wgrad_last(t, llast, gout, gw, gw + layer_wcount(llast), B, H, W, st);
+    float* gw = t->grad + layer_offset(sp, llast);
+    hp_status rc = wgrad_last(t, llast, gout, gw, gw + layer_wcount(sp, llast), B, H, W, st);
     if (rc != HP_OK) return rc;
     const __nv_bfloat16* mask_last =
-        kSpec[llast - 1].relu ? (const __nv_bfloat16*)t->act[llast - 1] : nullptr;
+        sp[llast - 1].relu ? (const __nv_bfloat16*)t->act[llast - 1] : nullptr;
     rc = dgrad_last(t, llast, gout, gbuf[0], B, H, W, mask_last, st);
     if (rc != HP_OK) return rc;
     int cur = 0;
     for (int l = llast - 1; l > lfirst; --l) {
-        const int ci = kSpec[l].cin, co = kSpec[l].cout;
+        const int ci = sp[l].cin, co = sp[l].cout;
         const __nv_bfloat16* gy = gbuf[cur];
         const __nv_bfloat16* x = (const __nv_bfloat16*)t->act[l - 1];
         int grid = 0;
         rc = launch_conv3x3_tc_wgrad(x, gy, t->part, t->part_len, t->partb, t->partb_len, B, H, W,
                                      ci, co, c->err, c->num_sms, &grid, st);
         if (rc != HP_OK) return rc;
-        gw = t->grad + layer_offset(l);
+        gw = t->grad + layer_offset(sp, l);
         wgrad_reduce_kernel<<<reduce_blocks(ci, co), 256, 0, st>>>(t->part, t->partb, grid, ci, co,
-                                                                   gw, gw + layer_wcount(l));
+                                                                   gw, gw + layer_wcount(sp, l));
         if ((rc = check_launch()) != HP_OK) return rc;
         // input gradient with the ReLU derivative of layer l - 1
-        const __nv_bfloat16* act = kSpec[l - 1].relu ? x : nullptr;
+        const __nv_bfloat16* act = sp[l - 1].relu ? x : nullptr;
         __nv_bfloat16* gx = gbuf[cur ^ 1];
         rc = launch_conv3x3_tc_dgrad(gy, t->wdg[l], t->zero_bias, act, gx, B, H, W, ci, co,
                                      c->err, c->num_sms, st);
@@ -1767,8 +1808,10 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
             rc = border_terms<64, 64>(gy, t->wt[l], act, gx, B, H, W, st);
         else if (ci == 32 && co == 64)
             rc = border_terms<32, 64>(gy, t->wt[l], act, gx, B, H, W, st);
-        else
+        else if (ci == 64 && co == 32)
             rc = border_terms<64, 32>(gy, t->wt[l], act, gx, B, H, W, st);
+        else
+            rc = border_terms<32, 32>(gy, t->wt[l], act, gx, B, H, W, st);
         if (rc != HP_OK) return rc;
         cur ^= 1;
     }
@@ -1779,6 +1822,7 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
 // the last trainer_forward)
 static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
 {
+    const LayerSpec* sp = t->cnn->spec;
     hp_cnn* c = t->cnn;
     hp_status rc = HP_OK;
     // backward, branch by branch from full resolution
@@ -1806,16 +1850,16 @@ static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
             continue;
         }
         for (; l >= lfirst; --l) {
-            const int ci = kSpec[l].cin, co = kSpec[l].cout;
+            const int ci = sp[l].cin, co = sp[l].cout;
             float* gy = t->g[cur];
-            if (kSpec[l].relu) {
+            if (sp[l].relu) {
                 const size_t n = (size_t)P * co;
                 relu_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
                     gy, (const __nv_bfloat16*)t->act[l], n);
             }
             const void* x = l == lfirst ? (const void*)t->xin[k] : t->act[l - 1];
-            float* gw = t->grad + layer_offset(l);
-            rc = wgrad_dispatch(t, k, l, gy, x, gw, gw + layer_wcount(l), s.batch, H, W, st);
+            float* gw = t->grad + layer_offset(sp, l);
+            rc = wgrad_dispatch(t, k, l, gy, x, gw, gw + layer_wcount(sp, l), s.batch, H, W, st);
             if (rc != HP_OK) return rc;
             if (l > lfirst) {
                 rc = co == 1 ? dgrad_last(t, l, gy, t->g[cur ^ 1], s.batch, H, W, nullptr, st)

@@ -1221,6 +1221,8 @@ hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* 
         return launch_ws<64, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
     if (cin == 64 && cout == 32)
         return launch_ws<32, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+    if (cin == 32 && cout == 32)
+        return launch_ws<32, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1239,6 +1241,9 @@ hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, si
                                       grid_out, st);
     if (cin == 64 && cout == 32)
         return launch_wgrad_t<64, 32>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
+                                      grid_out, st);
+    if (cin == 32 && cout == 32)
+        return launch_wgrad_t<32, 32>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
                                       grid_out, st);
     return HP_ERR_UNSUPPORTED;
 }

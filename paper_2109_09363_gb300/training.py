@@ -13,14 +13,18 @@ from paper_2109_09363_gb300 import workloads as W
 # (cin, cout) of the 19 convolutions in network order: scale 1/4, 1/2, 1
 LAYERS = ([(2, 32), (32, 64), (64, 64), (64, 32), (32, 1)] +
           2 * [(3, 32), (32, 64), (64, 64), (64, 64), (64, 64), (64, 32), (32, 1)])
+# the SmallScale: every 64-channel layer at 32 channels
+SMALL_LAYERS = ([(2, 32), (32, 32), (32, 32), (32, 32), (32, 1)] +
+                2 * [(3, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1)])
+ARCH_LAYERS = {"multiscale": LAYERS, "smallscale": SMALL_LAYERS}
 
 
-def init_params(seed: int = 0) -> np.ndarray:
+def init_params(seed: int = 0, arch: str = "multiscale") -> np.ndarray:
     """Initial parameters in the network's flat order (per layer weights
     [cout][cin][3][3] He-uniform, then zero biases), FP32."""
     g = np.random.Generator(np.random.PCG64(seed))
     parts = []
-    for cin, cout in LAYERS:
+    for cin, cout in ARCH_LAYERS[arch]:
         lim = np.sqrt(6.0 / (9 * cin))
         parts.append(g.uniform(-lim, lim, 9 * cin * cout))
         parts.append(np.zeros(cout))

@@ -1,0 +1,187 @@
+"""The SmallScale network (Sec. 3.1: the MultiScale with fewer filters, every
+64-channel layer at 32 channels) on the GPU against the FP64 oracle:
+1. the forward (hp_cnn_forward), under the bar of the MultiScale forward test;
+2. the hybrid projection from the same guess;
+3. the training gradient (hand-written backward, the 32 -> 32 layers on the
+   tensor cores from a width of 32 pixels, on CUDA cores below) against the
+   oracle backward, under the bar of the MultiScale gradient tests;
+4. a few Adam steps lower the loss;
+5. the architecture is kept and checked (parameter counts of the other
+   architecture are rejected)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn as C
+from oracle import train as TR
+from paper_2109_09363_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+hp = pytest.importorskip("paper_2109_09363_gb300")
+
+ARCH = "smallscale"
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09363_gb300 import build
+    build.build()
+    oracle.build()
+    return torch.device("cuda:0")
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    return [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in C.init_params(seed, ARCH)]
+
+
+def bf16_weights(params):
+    return [(C.round_bf16(w), b.astype(np.float32).astype(np.float64)) for w, b in params]
+
+
+def case(B, n, seed):
+    us, vs, fs = [], [], []
+    for b in range(B):
+        u, v = W.vortex_velocity(n, n, 40 + seed + b, n_vortices=8, width=(n / 32, n / 8))
+        fs.append(W.random_obstacles(n, n, 50 + seed + b, rect_side=(n / 16, n / 4),
+                                     disc_radius=(n / 32, n / 8)))
+        us.append(u); vs.append(v)
+    return (np.stack(us).astype(np.float32), np.stack(vs).astype(np.float32), np.stack(fs))
+
+
+@pytest.mark.parametrize("B,n", [(2, 64), (1, 128), (3, 32)])
+def test_smallscale_forward_matches_oracle(dev, B, n):
+    params = random_params(3)
+    u, v, fl = case(B, n, 1)
+    cnn = hp.CNN(B, n, n, params=C.flatten(params), arch=ARCH)
+    assert cnn.arch == ARCH and cnn.n_params == C.param_count(ARCH)
+    assert hp.load_library().hp_cnn_get_arch(cnn.handle) == 1
+    ud, vd, fd = (torch.from_numpy(a).to(dev) for a in (u, v, fl))
+    div = hp.hp_divergence(ud, vd, fd)
+    phi_hat, s = hp.hp_cnn_forward(cnn, div, fd)
+    torch.cuda.synchronize()
+    cnn.check()
+    pw = bf16_weights(params)
+    for b in range(B):
+        d = div[b].cpu().numpy().astype(np.float64)
+        sb = float(s[b].cpu())
+        ref = C.forward(pw, d / sb, fl[b], act_round=C.round_bf16)
+        got = phi_hat[b].cpu().numpy()
+        assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), np.abs(got - ref).max()
+
+
+def test_smallscale_hybrid_projection_matches_oracle_from_the_same_guess(dev):
+    B, n, thr, cap = 2, 64, 1e-3, 3000
+    params = random_params(5)
+    u, v, fl = case(B, n, 7)
+    cnn = hp.CNN(B, n, n, params=C.flatten(params), arch=ARCH)
+    ctx = hp.Context(B, n, n)
+    ud, vd, fd = (torch.from_numpy(a).to(dev) for a in (u, v, fl))
+    div = hp.hp_divergence(ud, vd, fd)
+    phi_hat, s = hp.hp_cnn_forward(cnn, div, fd)
+    phi0 = (phi_hat.cpu().numpy() * s.cpu().numpy()[:, None, None]).astype(np.float64)
+    out = hp.hp_project_hybrid(ctx, cnn, ud, vd, fd, hp.ProjectParams(threshold=thr, max_iters=cap))
+    torch.cuda.synchronize()
+    ref = oracle.project(u.astype(np.float64), v.astype(np.float64), fl, thr, cap, phi0=phi0,
+                         hist_len=cap + 2)
+    gi = out["iters"].cpu().numpy()
+    for b in range(B):
+        if gi[b] != ref["iters"][b]:
+            eh = ref["e_hist"][b]
+            lo, hi = sorted((int(gi[b]), int(ref["iters"][b])))
+            assert np.all(np.abs(eh[lo:hi + 1] - thr) / thr <= 5e-5)
+        else:
+            umax = np.abs(ref["u"][b]).max()
+            assert np.abs(ud.cpu().numpy()[b] - ref["u"][b]).max() <= 1e-5 * umax
+
+
+def oracle_gradient(params, phi_gpu, div, fl, tgt, s, lam, act_round):
+    B = div.shape[0]
+    pw = bf16_weights(params)
+    total = [(np.zeros_like(w), np.zeros_like(b)) for w, b in pw]
+    L = 0.0
+    for b in range(B):
+        d = div[b].astype(np.float64)
+        _, tape = C.forward(pw, d / s[b], fl[b], keep=True, act_round=act_round)
+        lb, gphi = TR.loss_and_grad(phi_gpu[b], tgt[b], d, fl[b], s[b], lam)
+        L += lb / B
+        gr = C.backward(pw, tape, gphi / B)
+        total = [(tw + gw, tb + gb) for (tw, tb), (gw, gb) in zip(total, gr)]
+    return L, total
+
+
+@pytest.mark.parametrize("B,ny,nx", [(2, 32, 32), (2, 128, 128), (1, 64, 160)])
+def test_smallscale_gradient_matches_oracle_backward(dev, B, ny, nx):
+    """32 x 32: the coarse branches (8 and 16 pixels wide) on CUDA cores, the
+    full-resolution one on the tensor cores; the larger sizes on the tensor
+    cores throughout (160 = a full and a partial 128-pixel segment)."""
+    rng = np.random.default_rng(B + nx + 1)
+    params = random_params(13)
+    u, v, fl = W.training_case(1, max(ny, nx), 710)
+    u, v, fl = u[:, :ny, :nx + 1], v[:, :ny + 1, :nx], fl[:, :ny, :nx]
+    u, v, fl = np.repeat(u, B, 0), np.repeat(v, B, 0), np.ascontiguousarray(np.repeat(fl, B, 0))
+    if B > 1:
+        u[1] = np.roll(u[1], 11, axis=1)
+        v[1] = np.roll(v[1], 7, axis=0)
+    ud = torch.from_numpy(np.ascontiguousarray(u, np.float32)).to(dev)
+    vd = torch.from_numpy(np.ascontiguousarray(v, np.float32)).to(dev)
+    fd = torch.from_numpy(fl).to(dev)
+    div = hp.hp_divergence(ud, vd, fd)
+    tgt = torch.from_numpy(rng.standard_normal((B, ny, nx)).astype(np.float32)).to(dev)
+    cnn = hp.CNN(B, ny, nx, params=C.flatten(params), arch=ARCH)
+    tr = hp.Trainer(cnn, B, ny, nx)
+    lam = 1.0
+    g, loss = tr.gradient(div, fd, tgt, lambda_div=lam)
+    assert g.numel() == C.param_count(ARCH)
+    phi_gpu, s = hp.hp_cnn_forward(cnn, div, fd)
+    torch.cuda.synchronize()
+    cnn.check()
+    args = (phi_gpu.cpu().numpy(), div.cpu().numpy(), fl, tgt.cpu().numpy(),
+            [float(x) for x in s.cpu()], lam)
+    L, ref = oracle_gradient(params, *args, act_round=C.round_bf16)
+    assert np.isclose(float(loss.item()), L, rtol=1e-4)
+    _, ref64 = oracle_gradient(params, *args, act_round=None)
+    flat = g.cpu().numpy()
+    k = 0
+    for (w, b), (w64, b64) in zip(ref, ref64):
+        nw, nb = w.size, b.size
+        gw, gb = flat[k:k + nw], flat[k + nw:k + nw + nb]
+        scale = max(np.abs(w).max(), np.abs(b).max())
+        sens = max(np.abs(w - w64).max(), np.abs(b - b64).max())
+        bar = max(5e-2 * scale, 3.0 * sens) + 1e-9
+        assert np.abs(gw - w.ravel()).max() <= bar, (k, np.abs(gw - w.ravel()).max(), scale, sens)
+        assert np.abs(gb - b.ravel()).max() <= bar, (k, np.abs(gb - b.ravel()).max(), scale)
+        k += nw + nb
+    assert k == flat.size
+
+
+def test_smallscale_adam_steps_lower_the_loss(dev):
+    B, n = 8, 64
+    rng = np.random.default_rng(21)
+    u, v, fl = W.training_case(B, n, 720)
+    ud = torch.from_numpy(u.astype(np.float32)).to(dev)
+    vd = torch.from_numpy(v.astype(np.float32)).to(dev)
+    fd = torch.from_numpy(fl).to(dev)
+    div = hp.hp_divergence(ud, vd, fd)
+    tgt = torch.from_numpy(rng.standard_normal((B, n, n)).astype(np.float32)).to(dev)
+    from paper_2109_09363_gb300 import training as T
+    cnn = hp.CNN(B, n, n, params=T.init_params(seed=2, arch=ARCH), arch=ARCH)
+    tr = hp.Trainer(cnn, B, n, n)
+    losses = [float(tr.step(div, fd, tgt, lr=1e-3, lambda_div=0.0).item()) for _ in range(30)]
+    assert all(np.isfinite(losses))
+    assert losses[-1] < losses[0], (losses[0], losses[-1])
+    tr.sync_params()
+    p = cnn.get_params()
+    assert p.size == C.param_count(ARCH) and np.all(np.isfinite(p))
+
+
+def test_smallscale_parameter_counts_are_checked(dev):
+    B, n = 1, 32
+    cnn = hp.CNN(B, n, n, arch=ARCH)
+    with pytest.raises(hp.HprojError):
+        cnn.set_params(C.flatten(C.init_params(1)))  # MultiScale-sized vector
+    with pytest.raises(ValueError):
+        hp.CNN(B, n, n, arch="unet")

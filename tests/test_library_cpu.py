@@ -55,6 +55,23 @@ def test_binding_rejects_cpu_tensors():
 def test_cnn_parameter_count_matches_the_oracle(lib):
     from oracle import cnn as C
     assert int(lib.hp_cnn_param_count()) == C.param_count() == 372643
+    assert int(lib.hp_cnn_arch_param_count(0)) == C.param_count("multiscale")
+    assert int(lib.hp_cnn_arch_param_count(1)) == C.param_count("smallscale") == 123491
+    assert hp.CNN.param_count("smallscale") == 123491
+    assert int(lib.hp_cnn_arch_param_count(2)) == -1
+    assert int(lib.hp_cnn_arch_param_count(-1)) == -1
+
+
+def test_cnn_architecture_argument_checks(lib):
+    out = hp._P()
+    # unknown architecture, bad shape, null handle: rejected before any device call
+    assert lib.hp_cnn_create_arch(ctypes.byref(out), 5, hp.hp_shape(1, 64, 64), 0) == 1
+    assert not out
+    assert lib.hp_cnn_create_arch(ctypes.byref(out), 1, hp.hp_shape(1, 62, 64), 0) == 1
+    assert lib.hp_cnn_create_arch(None, 1, hp.hp_shape(1, 64, 64), 0) == 1
+    assert lib.hp_cnn_get_arch(None) == -1
+    with pytest.raises(ValueError):
+        hp.CNN.param_count("unet")
 
 
 def test_ctypes_structures_match_the_header(tmp_path):
