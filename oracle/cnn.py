@@ -17,6 +17,11 @@ three times fewer parameters.  Reading: every 64-channel layer has 32
 channels, 2 -> 32 -> 32 -> 32 -> 32 -> 1 and 3 -> 32 -> 32 -> 32 -> 32 -> 32
 -> 32 -> 1; 123,491 parameters (3.02 times fewer).
 
+MonoScale (Sec. 3.1): one feed-forward branch of 9 convolutions at full
+resolution with replicated borders on [div/s, flags].  Reading: 3 x 3 kernels
+only, 2 -> 32 -> 64 -> 64 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1, ReLU after every
+convolution except the last two; 222,497 parameters.
+
 Layout: activations [C][H][W] (one grid), weights [Cout][Cin][3][3].
 """
 from __future__ import annotations
@@ -33,15 +38,21 @@ SMALL_WIDTHS = {
     2: [3, 32, 32, 32, 32, 32, 32, 1],
     1: [3, 32, 32, 32, 32, 32, 32, 1],
 }
-ARCHS = {"multiscale": BRANCH_WIDTHS, "smallscale": SMALL_WIDTHS}
 SCALES = (4, 2, 1)
+# every architecture as its branches in network order: (scale, widths); the
+# input of a branch is [div_s, flags] at its scale, followed by the
+# up-sampled output of the branch before it when there is one
+ARCHS = {
+    "multiscale": [(sc, BRANCH_WIDTHS[sc]) for sc in SCALES],
+    "smallscale": [(sc, SMALL_WIDTHS[sc]) for sc in SCALES],
+    "monoscale": [(1, [2, 32, 64, 64, 64, 64, 64, 64, 32, 1])],
+}
 
 
 def param_shapes(arch="multiscale"):
     """[(scale, layer, (Cout, Cin, 3, 3), (Cout,))] in network order."""
     out = []
-    for sc in SCALES:
-        w = ARCHS[arch][sc]
+    for sc, w in ARCHS[arch]:
         for l in range(len(w) - 1):
             out.append((sc, l, (w[l + 1], w[l], 3, 3), (w[l + 1],)))
     return out
@@ -51,10 +62,19 @@ def param_count(arch="multiscale"):
     return sum(int(np.prod(ws)) + int(np.prod(bs)) for _, _, ws, bs in param_shapes(arch))
 
 
-def relu_after(sc, l):
-    """ReLU after every convolution of a branch except its last two (both
-    architectures have the same number of layers per branch)."""
-    return l < len(BRANCH_WIDTHS[sc]) - 3
+def arch_of(params):
+    """The architecture whose layer shapes the parameter list has."""
+    shapes = [(tuple(np.shape(w)), tuple(np.shape(b))) for w, b in params]
+    for name in ARCHS:
+        if shapes == [(ws, bs) for _, _, ws, bs in param_shapes(name)]:
+            return name
+    raise ValueError("parameters of no known architecture")
+
+
+def relu_after(l, nl):
+    """ReLU after every convolution of a branch of nl layers except its last
+    two."""
+    return l < nl - 2
 
 
 def init_params(seed=0, arch="multiscale"):
@@ -154,7 +174,8 @@ def round_bf16(x):
 
 
 def forward(params, div, flags, keep=False, act_round=None):
-    """phi_hat = MultiScale([div_s, flags]) for one grid (H, W divisible by 4).
+    """phi_hat = network([div_s, flags]) for one grid (H, W divisible by 4);
+    the architecture is the one the parameters have.
 
     div_s is the already scaled divergence (the caller divides by s and
     multiplies the output by s).  With keep=True returns (out, tape) for
@@ -168,14 +189,14 @@ def forward(params, div, flags, keep=False, act_round=None):
     tape = []
     p = iter(params)
     prev = None
-    for sc in SCALES:
+    for sc, widths in ARCHS[arch_of(params)]:
         h = xin[sc] if prev is None else np.concatenate([xin[sc], upsample2(prev)], axis=0)
         h = rnd(h)
-        nl = len(BRANCH_WIDTHS[sc]) - 1
+        nl = len(widths) - 1
         for l in range(nl):
             w, b = next(p)
             pre = conv3x3(h, w, b)
-            out = np.maximum(pre, 0.0) if relu_after(sc, l) else pre
+            out = np.maximum(pre, 0.0) if relu_after(l, nl) else pre
             tape.append((sc, l, h, pre))
             h = rnd(out) if l < nl - 1 else out
         prev = h
@@ -204,18 +225,19 @@ def backward(params, tape, g_out):
     g = g_out[None].astype(np.float64)
     idx = len(params) - 1
     g_prev_up = None
-    for sc in reversed(SCALES):
-        nl = len(BRANCH_WIDTHS[sc]) - 1
+    branches = ARCHS[arch_of(params)]
+    for k in reversed(range(len(branches))):
+        nl = len(branches[k][1]) - 1
         if g_prev_up is not None:
             g = g_prev_up
         for l in reversed(range(nl)):
             _, _, h, pre = tape[idx]
-            if relu_after(sc, l):
+            if relu_after(l, nl):
                 g = g * (pre > 0)
             gx, gw, gb = conv3x3_backward(h, params[idx][0], g)
             grads[idx] = (gw, gb)
             g = gx
             idx -= 1
         # g is the gradient of this branch's input [x_sc(, upsampled coarser)]
-        g_prev_up = upsample2_backward(g[2:3]) if sc != 4 else None
+        g_prev_up = upsample2_backward(g[2:3]) if k > 0 else None
     return grads

@@ -1,4 +1,4 @@
-"""Pins of the FP64 MultiScale and SmallScale CNN oracle (Sec. 3.1): library special cases
+"""Pins of the FP64 MultiScale, SmallScale and MonoScale CNN oracle (Sec. 3.1): library special cases
 (torch conv2d / pooling / interpolation in FP64 on CPU, used only here to pin
 the oracle), adjointness, finite differences, the parameter counts and the
 embedding of the SmallScale in a zero-padded MultiScale."""
@@ -175,3 +175,59 @@ def test_smallscale_gradients_by_central_differences():
         wm[li][0][idx] -= eps
         fd = (np.sum(C.forward(wp, div, fl) * gout) - np.sum(C.forward(wm, div, fl) * gout)) / (2 * eps)
         assert np.isclose(grads[li][0][idx], fd, rtol=1e-5, atol=1e-8), (li, idx)
+
+
+def test_monoscale_parameter_count_and_structure():
+    shapes = C.param_shapes("monoscale")
+    assert len(shapes) == 9 and all(sc == 1 for sc, _, _, _ in shapes)
+    assert C.param_count("monoscale") == 222497
+    assert shapes[0][2][1] == 2 and shapes[-1][2][0] == 1
+    with pytest.raises(ValueError):
+        C.arch_of([(np.zeros((4, 2, 3, 3)), np.zeros(4))])
+
+
+def test_monoscale_is_a_chain_of_library_convolutions():
+    """The MonoScale is a plain feed-forward chain: replicate padding,
+    convolution, ReLU except after the last two (torch FP64 on CPU)."""
+    rng = np.random.default_rng(9)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in
+              C.init_params(seed=5, arch="monoscale")]
+    n = 12
+    div = rng.standard_normal((n, 2 * n))
+    fl = (rng.random((n, 2 * n)) < 0.2).astype(np.uint8)
+    h = torch.stack([T(div), T(fl.astype(np.float64))])[None]
+    for l, (w, b) in enumerate(params):
+        h = F.conv2d(F.pad(h, (1, 1, 1, 1), mode="replicate"), T(w), T(b))
+        if l < len(params) - 2:
+            h = torch.relu(h)
+    assert C.arch_of(params) == "monoscale"
+    assert np.allclose(C.forward(params, div, fl), h[0, 0].numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_monoscale_gradients_by_central_differences():
+    rng = np.random.default_rng(10)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in
+              C.init_params(seed=6, arch="monoscale")]
+    n = 8
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    gout = rng.standard_normal((n, n))
+    _, tape = C.forward(params, div, fl, keep=True)
+    grads = C.backward(params, tape, gout)
+    eps = 1e-6
+    for li in [0, 3, 6, 8]:
+        w, b = params[li]
+        idx = tuple(rng.integers(0, s) for s in w.shape)
+        wp = [(ww.copy(), bb) for ww, bb in params]
+        wm = [(ww.copy(), bb) for ww, bb in params]
+        wp[li][0][idx] += eps
+        wm[li][0][idx] -= eps
+        fd = (np.sum(C.forward(wp, div, fl) * gout) - np.sum(C.forward(wm, div, fl) * gout)) / (2 * eps)
+        assert np.isclose(grads[li][0][idx], fd, rtol=1e-5, atol=1e-8), (li, idx)
+        j = int(rng.integers(0, b.shape[0]))
+        bp = [(ww, bb.copy()) for ww, bb in params]
+        bm = [(ww, bb.copy()) for ww, bb in params]
+        bp[li][1][j] += eps
+        bm[li][1][j] -= eps
+        fd = (np.sum(C.forward(bp, div, fl) * gout) - np.sum(C.forward(bm, div, fl) * gout)) / (2 * eps)
+        assert np.isclose(grads[li][1][j], fd, rtol=1e-5, atol=1e-8)
