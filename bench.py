@@ -41,8 +41,9 @@ TRAIN_SWEEPS = 40000
 # multiply-adds per full-resolution pixel of each network: the scale-1 branch,
 # a quarter of the scale-1/2 branch, a sixteenth of the scale-1/4 branch
 # (MultiScale 148,608 + 148,608 / 4 + 74,592 / 16; SmallScale 47,232 +
-# 47,232 / 4 + 28,512 / 16)
-CNN_MACS_PER_PIXEL = {"multiscale": 190422, "smallscale": 60822}
+# 47,232 / 4 + 28,512 / 16); the MonoScale's one branch 222,048
+CNN_MACS_PER_PIXEL = {"multiscale": 190422, "smallscale": 60822, "monoscale": 222048}
+NETWORKS = ("multiscale", "smallscale", "monoscale")
 # held-out grids of the training distribution for the in-distribution comparison
 IN_DIST_GRIDS, IN_DIST_SEED = 256, 100000
 T_BLOCK = 8
@@ -275,7 +276,7 @@ def profile_sweep(batch: int, n: int, sweeps: int, host_loop: bool = False,
 
 def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain, ws):
     """CNN-hybrid projection of the same grids to the same threshold, with the
-    MultiScale and with the SmallScale network (Sec. 3.1).
+    MultiScale, the SmallScale and the MonoScale network (Sec. 3.1).
 
     Untimed set-up: training pairs from the plain solver (128^2, vortex field +
     divergence sources + 0-4 obstacles), Adam training of each network on the
@@ -291,7 +292,7 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     batch = 32
     epochs = max(1, (args.train_steps * batch + 2047) // 2048)
     trained, train_info = {}, {}
-    for arch in ("multiscale", "smallscale"):
+    for arch in NETWORKS:
         t1 = time.perf_counter()
         cnn = hp.CNN(batch, n_tr, n_tr, params=T.init_params(seed=1, arch=arch), arch=arch)
         losses = T.train(cnn, data, epochs=epochs, batch=batch, lr=1e-3, lambda_div=1.0)
@@ -373,7 +374,7 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     tpk = float(peaks.get("bf16_tflops", 1900.0))
     uncapped_plain = time_uncapped(None)
     arms = {}
-    for arch in ("multiscale", "smallscale"):
+    for arch in NETWORKS:
         net = hp.CNN(B, N, N, params=trained[arch], arch=arch)
         ms, out = time_capped(net)
         t_inf = time_inference(net)
@@ -407,9 +408,10 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     plume = compare_plume_same_threshold(hp, trained["multiscale"], u0.device)
     ms_arm["in_distribution_128"] = in_dist
     ms_arm["plume_same_threshold"] = plume
-    ms_arm["smallscale"] = arms["smallscale"]
-    ms_arm["smallscale"]["t_inf_ratio_multiscale_over_smallscale"] = (
-        ms_arm["t_inf_ms_16_grids"] / arms["smallscale"]["t_inf_ms_16_grids"])
+    for arch in NETWORKS[1:]:
+        ms_arm[arch] = arms[arch]
+        ms_arm[arch]["t_inf_over_multiscale"] = (arms[arch]["t_inf_ms_16_grids"] /
+                                                 ms_arm["t_inf_ms_16_grids"])
     return ms_arm
 
 
@@ -711,7 +713,7 @@ def main():
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
     ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
-    ap.add_argument("--arch", default="multiscale", choices=["multiscale", "smallscale"],
+    ap.add_argument("--arch", default="multiscale", choices=list(NETWORKS),
                     help="network of --profile-cnn")
     ap.add_argument("--profile-train", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the physics-driven loss gradient on BATCH grids of N x N, "

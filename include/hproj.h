@@ -246,8 +246,16 @@ hp_status hp_project_adjoint(hp_ctx *ctx, const float *gu, const float *gv, cons
  * max_shape (ny, nx multiples of 4). */
 typedef struct hp_cnn hp_cnn;
 /* Architectures (Sec. 3.1).  SmallScale: the MultiScale graph with fewer
- * filters, every 64-channel layer at 32 channels, 123,491 parameters. */
-typedef enum { HP_CNN_MULTISCALE = 0, HP_CNN_SMALLSCALE = 1 } hp_cnn_arch;
+ * filters, every 64-channel layer at 32 channels, 123,491 parameters.
+ * MonoScale: one feed-forward branch at full resolution on [div / s, flags],
+ * 2 -> 32 -> 64 -> 64 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1 (3 x 3, replicated
+ * borders, ReLU after all but the last two), 222,497 parameters; its params
+ * vector holds its 9 layers in that order. */
+typedef enum {
+    HP_CNN_MULTISCALE = 0,
+    HP_CNN_SMALLSCALE = 1,
+    HP_CNN_MONOSCALE = 2
+} hp_cnn_arch;
 /* Parameter count of the MultiScale; of the architecture arch (-1 if arch is
  * not one of hp_cnn_arch). */
 int64_t hp_cnn_param_count(void);

@@ -388,12 +388,12 @@ def hp_project_adjoint(ctx: Context, gu, gv, gp, flags, k: int, dt: float = 1.0,
     return gus, gvs, gphi
 
 
-CNN_ARCHS = {"multiscale": 0, "smallscale": 1}  # hp_cnn_arch
+CNN_ARCHS = {"multiscale": 0, "smallscale": 1, "monoscale": 2}  # hp_cnn_arch
 
 
 class CNN:
-    """CNN weights and workspace on the device (hp_cnn): the MultiScale or
-    its narrower SmallScale variant (Sec. 3.1)."""
+    """CNN weights and workspace on the device (hp_cnn): the MultiScale, its
+    narrower SmallScale variant or the feed-forward MonoScale (Sec. 3.1)."""
 
     def __init__(self, batch: int, ny: int, nx: int, device: int | None = None, params=None,
                  arch: str = "multiscale"):

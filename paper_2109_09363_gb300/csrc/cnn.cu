@@ -36,7 +36,9 @@ struct LayerSpec {
 };
 
 // network order: scale 1/4, then 1/2, then 1
-constexpr int kLayers = 19;
+constexpr int kLayers = 19;      // MultiScale and SmallScale
+constexpr int kMaxLayers = 19;   // the most of any architecture
+constexpr int kMaxBranches = 3;
 const LayerSpec kSpecMulti[kLayers] = {
     {4, 2, 32, 1},  {4, 32, 64, 1}, {4, 64, 64, 1}, {4, 64, 32, 0}, {4, 32, 1, 0},
     {2, 3, 32, 1},  {2, 32, 64, 1}, {2, 64, 64, 1}, {2, 64, 64, 1}, {2, 64, 64, 1},
@@ -50,10 +52,44 @@ const LayerSpec kSpecSmall[kLayers] = {
     {2, 32, 32, 0}, {2, 32, 1, 0},  {1, 3, 32, 1},  {1, 32, 32, 1}, {1, 32, 32, 1},
     {1, 32, 32, 1}, {1, 32, 32, 1}, {1, 32, 32, 0}, {1, 32, 1, 0}};
 
+// MonoScale (Sec. 3.1): one feed-forward branch of 9 convolutions at full
+// resolution on [div/s, flags]
+constexpr int kLayersMono = 9;
+const LayerSpec kSpecMono[kLayersMono] = {
+    {1, 2, 32, 1},  {1, 32, 64, 1}, {1, 64, 64, 1}, {1, 64, 64, 1}, {1, 64, 64, 1},
+    {1, 64, 64, 1}, {1, 64, 64, 1}, {1, 64, 32, 0}, {1, 32, 1, 0}};
+
 const LayerSpec* spec_for(int arch)
 {
-    return arch == HP_CNN_MULTISCALE ? kSpecMulti : arch == HP_CNN_SMALLSCALE ? kSpecSmall
-                                                                              : nullptr;
+    return arch == HP_CNN_MULTISCALE   ? kSpecMulti
+           : arch == HP_CNN_SMALLSCALE ? kSpecSmall
+           : arch == HP_CNN_MONOSCALE  ? kSpecMono
+                                       : nullptr;
+}
+
+int layers_for(int arch) { return arch == HP_CNN_MONOSCALE ? kLayersMono : kLayers; }
+
+// The branches of a network in order: consecutive layers up to a 1-channel
+// output.  A branch after the first takes the up-sampled output of the one
+// before it as its third input channel.
+struct Branches {
+    int n;
+    int first[kMaxBranches], last[kMaxBranches], scale[kMaxBranches];
+};
+
+Branches branches_of(const LayerSpec* sp, int nl)
+{
+    Branches br = {};
+    int start = 0;
+    for (int l = 0; l < nl && br.n < kMaxBranches; ++l)
+        if (sp[l].cout == 1) {
+            br.first[br.n] = start;
+            br.last[br.n] = l;
+            br.scale[br.n] = sp[l].scale;
+            ++br.n;
+            start = l + 1;
+        }
+    return br;
 }
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
@@ -372,22 +408,24 @@ using namespace hp;
 struct hp_cnn {
     int arch;               // hp_cnn_arch
     const LayerSpec* spec;  // its layer table
+    int nlayers;
+    Branches br;
     int device;
     int num_sms;
     hp_shape max_shape;
     // per layer: weights in the layout of its kernel, FP32 bias
-    void* w[kLayers];
-    float* bias[kLayers];
+    void* w[kMaxLayers];
+    float* bias[kMaxLayers];
     std::vector<float> master;  // FP32 parameters, oracle order
     // workspace
     __nv_bfloat16* act[2];
-    float* out[3];  // branch outputs at 1/4, 1/2, 1
+    float* out[kMaxBranches];  // branch outputs (FP32, one channel at the branch's scale)
     float* xin;     // branch input [P][cin] FP32 (largest branch)
     __nv_bfloat16* x16;  // branch input [P][16] BF16 for the tensor-core first layer
-    // tensor-core copies of the first / last layer of each branch (0: 1/4, 1: 1/2, 2: 1)
-    __nv_bfloat16* wtc_first[3];  // [9][32][16]
-    __nv_bfloat16* wtc_last[3];   // [9][16][32]
-    float* btc_last[3];           // [16]
+    // tensor-core copies of the first / last layer of each branch
+    __nv_bfloat16* wtc_first[kMaxBranches];  // [9][32][16]
+    __nv_bfloat16* wtc_last[kMaxBranches];   // [9][16][32]
+    float* btc_last[kMaxBranches];           // [16]
     float* s;
     double* s_part;                // [B][kScaleCtas] partial sums of |div|
     unsigned long long* s_cnt;     // [B][kScaleCtas] fluid-cell counts
@@ -451,14 +489,11 @@ static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const flo
     return check_launch();
 }
 
-// first and last layer (network order) of branch k, and their tensor-core copies
-static const int kFirstLayer[3] = {0, 5, 12};
-static const int kLastLayer[3] = {4, 11, 18};
-
+// tensor-core copies of the first and last layer of every branch
 static hp_status pack_edge_layers(hp_cnn* c, cudaStream_t st)
 {
-    for (int k = 0; k < 3; ++k) {
-        const int lf = kFirstLayer[k], ll = kLastLayer[k];
+    for (int k = 0; k < c->br.n; ++k) {
+        const int lf = c->br.first[k], ll = c->br.last[k];
         pack_edge_layers_kernel<<<(9 * 32 * 16 + 255) / 256, 256, 0, st>>>(
             (const float*)c->w[lf], c->spec[lf].cin, c->wtc_first[k], (const float*)c->w[ll],
             c->bias[ll], c->wtc_last[k], c->btc_last[k]);
@@ -480,7 +515,7 @@ int64_t hp_cnn_arch_param_count(int32_t arch)
     const LayerSpec* sp = spec_for(arch);
     if (!sp) return -1;
     int64_t n = 0;
-    for (int l = 0; l < kLayers; ++l) n += (int64_t)layer_wcount(sp, l) + sp[l].cout;
+    for (int l = 0; l < layers_for(arch); ++l) n += (int64_t)layer_wcount(sp, l) + sp[l].cout;
     return n;
 }
 
@@ -491,16 +526,16 @@ int32_t hp_cnn_get_arch(const hp_cnn* c) { return c ? c->arch : -1; }
 void hp_cnn_destroy(hp_cnn* c)
 {
     if (!c) return;
-    for (int l = 0; l < kLayers; ++l) {
+    for (int l = 0; l < kMaxLayers; ++l) {
         cudaFree(c->w[l]);
         cudaFree(c->bias[l]);
     }
     cudaFree(c->act[0]);
     cudaFree(c->act[1]);
-    for (int k = 0; k < 3; ++k) cudaFree(c->out[k]);
+    for (int k = 0; k < kMaxBranches; ++k) cudaFree(c->out[k]);
     cudaFree(c->xin);
     cudaFree(c->x16);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kMaxBranches; ++k) {
         cudaFree(c->wtc_first[k]);
         cudaFree(c->wtc_last[k]);
         cudaFree(c->btc_last[k]);
@@ -522,7 +557,10 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
     hp_cnn* c = new hp_cnn();
     c->arch = arch;
     c->spec = spec_for(arch);
+    c->nlayers = layers_for(arch);
+    c->br = branches_of(c->spec, c->nlayers);
     memset(c->w, 0, sizeof(c->w));
+    memset(c->out, 0, sizeof(c->out));
     memset(c->bias, 0, sizeof(c->bias));
     c->device = device;
     c->max_shape = mx;
@@ -530,7 +568,7 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
     c->master.assign((size_t)hp_cnn_arch_param_count(arch), 0.0f);
     const size_t px = (size_t)mx.batch * mx.ny * mx.nx;
     bool okm = true;
-    for (int l = 0; l < kLayers && okm; ++l) {
+    for (int l = 0; l < c->nlayers && okm; ++l) {
         const LayerSpec& ls = c->spec[l];
         const size_t wb = layer_wcount(c->spec, l) * (ls.cin >= 32 && ls.cout >= 32 ? 2 : 4);
         okm = cudaMalloc(&c->w[l], wb) == cudaSuccess &&
@@ -542,9 +580,7 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
     }
     okm = okm && cudaMalloc((void**)&c->act[0], px * 64 * 2) == cudaSuccess &&
           cudaMalloc((void**)&c->act[1], px * 64 * 2) == cudaSuccess &&
-          cudaMalloc((void**)&c->out[0], px / 16 * 4 + 16) == cudaSuccess &&
-          cudaMalloc((void**)&c->out[1], px / 4 * 4 + 16) == cudaSuccess &&
-          cudaMalloc((void**)&c->out[2], px * 4) == cudaSuccess &&
+
           cudaMalloc((void**)&c->xin, px * 3 * sizeof(float)) == cudaSuccess &&
           cudaMalloc((void**)&c->x16, px * 16 * 2) == cudaSuccess &&
           cudaMalloc((void**)&c->s_part, (size_t)mx.batch * kScaleCtas * sizeof(double)) ==
@@ -553,8 +589,11 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
                      (size_t)mx.batch * kScaleCtas * sizeof(unsigned long long)) == cudaSuccess &&
           cudaMalloc((void**)&c->s, mx.batch * sizeof(float)) == cudaSuccess &&
           cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
-    for (int k = 0; k < 3 && okm; ++k)
-        okm = cudaMalloc((void**)&c->wtc_first[k], 9 * 32 * 16 * 2) == cudaSuccess &&
+    for (int k = 0; k < c->br.n && okm; ++k)
+        okm = cudaMalloc((void**)&c->out[k],
+                         px / ((size_t)c->br.scale[k] * c->br.scale[k]) * 4 + 16) ==
+                  cudaSuccess &&
+              cudaMalloc((void**)&c->wtc_first[k], 9 * 32 * 16 * 2) == cudaSuccess &&
               cudaMalloc((void**)&c->wtc_last[k], 9 * 16 * 32 * 2) == cudaSuccess &&
               cudaMalloc((void**)&c->btc_last[k], 16 * sizeof(float)) == cudaSuccess;
     if (!okm) {
@@ -582,7 +621,7 @@ hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
     if (!c || !params || n != hp_cnn_arch_param_count(c->arch)) return HP_ERR_INVALID_ARG;
     memcpy(c->master.data(), params, (size_t)n * sizeof(float));
     const float* p = params;
-    for (int l = 0; l < kLayers; ++l) {
+    for (int l = 0; l < c->nlayers; ++l) {
         const int ci = c->spec[l].cin, co = c->spec[l].cout;
         const bool tc = ci >= 32 && co >= 32;
         std::vector<uint16_t> wb;
@@ -642,8 +681,8 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
     if (rc != HP_OK) return rc;
     int l = 0;
     const float* prev = nullptr;
-    for (int k = 0; k < 3; ++k) {
-        const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
+    for (int k = 0; k < c->br.n; ++k) {
+        const int scale = c->br.scale[k];
         const int H = s.ny / scale, W = s.nx / scale;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
         int cur = 0;
@@ -659,7 +698,7 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
             cur ^= 1;
             ++l;
         }
-        float* o = (k == 2 && phi_hat) ? phi_hat : c->out[k];
+        float* o = (k == c->br.n - 1 && phi_hat) ? phi_hat : c->out[k];
         rc = launch_last(c, k, c->act[cur], (const float*)c->w[l], c->bias[l], o, s.batch, H, W,
                          st);
         if (rc != HP_OK) return rc;
@@ -684,11 +723,12 @@ hp_status hp_project_hybrid(hp_ctx* ctx, hp_cnn* cnn, float* u, float* v, const 
     // divergence into the context, CNN guess into the second phi buffer
     hp_status rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st);
     if (rc != HP_OK) return rc;
-    rc = hp_cnn_forward(cnn, ctx->div, flags, cnn->out[2], nullptr, s, stream);
+    float* phi_hat = cnn->out[cnn->br.n - 1];
+    rc = hp_cnn_forward(cnn, ctx->div, flags, phi_hat, nullptr, s, stream);
     if (rc != HP_OK) return rc;
     const size_t cells = (size_t)s.ny * s.nx;
     phi0_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
-        cnn->out[2], cnn->s, ctx->mask, ctx->phi[1], s.batch, cells);
+        phi_hat, cnn->s, ctx->mask, ctx->phi[1], s.batch, cells);
     if ((rc = check_launch()) != HP_OK) return rc;
     return hp_project(ctx, u, v, flags, s, prm, ctx->phi[1], p_out, iters_out, e1_out, einf_out,
                       conv_out, e_hist, hist_len, stream);
@@ -1457,12 +1497,12 @@ struct hp_trainer {
     hp_shape max;
     long param_count;
     float *master, *grad, *m, *v;
-    float* wt[kLayers];
-    void* act[kLayers];   // layer outputs: bf16 [P][cout] or float [P] (cout == 1)
-    float* xin[3];        // first-layer inputs per branch, FP32 [P][cin]
+    float* wt[kMaxLayers];
+    void* act[kMaxLayers];   // layer outputs: bf16 [P][cout] or float [P] (cout == 1)
+    float* xin[kMaxBranches];  // first-layer inputs per branch, FP32 [P][cin]
     float* g[2];          // gradient ping-pong, FP32 [P][64]
     float* gsmall;        // first-layer input gradient, FP32 [P][3]
-    __nv_bfloat16* wdg[kLayers];  // input-gradient weights of the tensor-core layers
+    __nv_bfloat16* wdg[kMaxLayers];  // input-gradient weights of the tensor-core layers
     float* zero_bias;     // 64 zeros: the bias of an input-gradient convolution
     float *part, *partb;
     size_t part_len, partb_len;
@@ -1492,11 +1532,11 @@ void hp_trainer_destroy(hp_trainer* t)
 {
     if (!t) return;
     cudaFree(t->master); cudaFree(t->grad); cudaFree(t->m); cudaFree(t->v);
-    for (int l = 0; l < kLayers; ++l) {
+    for (int l = 0; l < kMaxLayers; ++l) {
         cudaFree(t->wt[l]); cudaFree(t->act[l]); cudaFree(t->wdg[l]);
     }
     cudaFree(t->zero_bias);
-    for (int k = 0; k < 3; ++k) cudaFree(t->xin[k]);
+    for (int k = 0; k < kMaxBranches; ++k) cudaFree(t->xin[k]);
     cudaFree(t->g[0]); cudaFree(t->g[1]); cudaFree(t->gsmall);
     cudaFree(t->part); cudaFree(t->partb); cudaFree(t->rbuf); cudaFree(t->stats);
     cudaFree(t->loss); cudaFree(t->mask);
@@ -1530,7 +1570,7 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     al((void**)&t->grad, t->param_count * 4);
     al((void**)&t->m, t->param_count * 4);
     al((void**)&t->v, t->param_count * 4);
-    for (int l = 0; l < kLayers; ++l) {
+    for (int l = 0; l < cnn->nlayers; ++l) {
         const int sc = sp[l].scale;
         const size_t Pl = P / (sc * sc);
         al(&t->act[l], sp[l].cout == 1 ? Pl * 4 : Pl * sp[l].cout * 2);
@@ -1538,8 +1578,8 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
         if (tc_layer(sp, l)) al((void**)&t->wdg[l], layer_wcount(sp, l) * 2);
     }
     al((void**)&t->zero_bias, 64 * 4);
-    for (int k = 0; k < 3; ++k) {
-        const int sc = k == 0 ? 4 : k == 1 ? 2 : 1;
+    for (int k = 0; k < cnn->br.n; ++k) {
+        const int sc = cnn->br.scale[k];
         al((void**)&t->xin[k], P / (sc * sc) * 3 * 4);
     }
     al((void**)&t->g[0], P * 64 * 4);
@@ -1574,7 +1614,7 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
 static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
 {
     const LayerSpec* sp = t->cnn->spec;
-    for (int l = 0; l < kLayers; ++l) {
+    for (int l = 0; l < t->cnn->nlayers; ++l) {
         const int ci = sp[l].cin, co = sp[l].cout;
         const int kind = (ci >= 32 && co >= 32) ? 0 : (co == 1 ? 2 : 1);
         const int n = 9 * ci * co + co;
@@ -1597,8 +1637,8 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
     hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
     if (rc != HP_OK) return rc;
     const float* prev = nullptr;
-    for (int k = 0, l = 0; k < 3; ++k) {
-        const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
+    for (int k = 0, l = 0; k < c->br.n; ++k) {
+        const int scale = c->br.scale[k];
         const int H = s.ny / scale, W = s.nx / scale;
         BranchIn in = {div, flags, c->s, prev, s.ny, s.nx, scale};
         rc = launch_first(c, k, in, sp[l].cin, t->xin[k], (const float*)c->w[l], c->bias[l],
@@ -1827,11 +1867,11 @@ static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
     hp_status rc = HP_OK;
     // backward, branch by branch from full resolution
     int cur = 0;
-    for (int k = 2, l = kLayers - 1; k >= 0; --k) {
-        const int scale = k == 0 ? 4 : k == 1 ? 2 : 1;
+    for (int k = c->br.n - 1, l = c->nlayers - 1; k >= 0; --k) {
+        const int scale = c->br.scale[k];
         const int H = s.ny / scale, W = s.nx / scale;
         const long P = (long)s.batch * H * W;
-        const int lfirst = k == 0 ? 0 : k == 1 ? 5 : 12;
+        const int lfirst = c->br.first[k];
         if (W >= conv_tc_min_width()) {
             // the FP32 gradient of the branch output stays in g[cur]; the
             // BF16 gradients use g[cur ^ 1] and the unused half of g[cur]
@@ -1892,7 +1932,7 @@ static hp_status trainer_grad(hp_trainer* t, const float* div, const uint8_t* fl
     // loss and its gradient w.r.t. the full-resolution output
     if ((rc = launch_mask(flags, t->mask, s, st)) != HP_OK) return rc;
     const size_t cells = (size_t)s.ny * s.nx;
-    const float* phi = (const float*)t->act[kLayers - 1];
+    const float* phi = (const float*)t->act[c->nlayers - 1];
     loss_stats_kernel<<<s.batch, 512, 0, st>>>(phi, target, div, t->mask, flags, c->s, t->rbuf,
                                                t->stats, s.ny, s.nx);
     loss_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
@@ -1913,7 +1953,7 @@ static hp_status trainer_pdnn_grad(hp_trainer* t, const float* div, const uint8_
     if (rc != HP_OK) return rc;
     if ((rc = launch_mask(flags, t->mask, s, st)) != HP_OK) return rc;
     const size_t cells = (size_t)s.ny * s.nx;
-    const float* phi = (const float*)t->act[kLayers - 1];
+    const float* phi = (const float*)t->act[c->nlayers - 1];
     pdnn_stats_kernel<<<s.batch, 512, 0, st>>>(phi, div, t->mask, c->s, weight, norm, t->rbuf,
                                                t->stats, s.ny, s.nx);
     pdnn_grad_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(

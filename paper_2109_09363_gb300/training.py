@@ -16,7 +16,9 @@ LAYERS = ([(2, 32), (32, 64), (64, 64), (64, 32), (32, 1)] +
 # the SmallScale: every 64-channel layer at 32 channels
 SMALL_LAYERS = ([(2, 32), (32, 32), (32, 32), (32, 32), (32, 1)] +
                 2 * [(3, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1)])
-ARCH_LAYERS = {"multiscale": LAYERS, "smallscale": SMALL_LAYERS}
+# the MonoScale: one full-resolution branch of nine convolutions
+MONO_LAYERS = [(2, 32), (32, 64)] + 5 * [(64, 64)] + [(64, 32), (32, 1)]
+ARCH_LAYERS = {"multiscale": LAYERS, "smallscale": SMALL_LAYERS, "monoscale": MONO_LAYERS}
 
 
 def init_params(seed: int = 0, arch: str = "multiscale") -> np.ndarray:

@@ -58,7 +58,8 @@ def test_cnn_parameter_count_matches_the_oracle(lib):
     assert int(lib.hp_cnn_arch_param_count(0)) == C.param_count("multiscale")
     assert int(lib.hp_cnn_arch_param_count(1)) == C.param_count("smallscale") == 123491
     assert hp.CNN.param_count("smallscale") == 123491
-    assert int(lib.hp_cnn_arch_param_count(2)) == -1
+    assert int(lib.hp_cnn_arch_param_count(2)) == C.param_count("monoscale") == 222497
+    assert int(lib.hp_cnn_arch_param_count(3)) == -1
     assert int(lib.hp_cnn_arch_param_count(-1)) == -1
 
 
