@@ -404,8 +404,8 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
                              pair_generation_seconds=t_pairs)}
         net.close()
     ms_arm = arms.pop("multiscale")
-    in_dist = compare_in_distribution(hp, trained["multiscale"], flush, stream, u0.device, ws)
-    plume = compare_plume_same_threshold(hp, trained["multiscale"], u0.device)
+    in_dist = compare_in_distribution(hp, trained, flush, stream, u0.device, ws)
+    plume = compare_plume_same_threshold(hp, trained, u0.device)
     ms_arm["in_distribution_128"] = in_dist
     ms_arm["plume_same_threshold"] = plume
     for arch in NETWORKS[1:]:
@@ -415,14 +415,15 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     return ms_arm
 
 
-def compare_plume_same_threshold(hp, params, dev, n=128, steps=300, thr=1e-5, cap=20000):
+def compare_plume_same_threshold(hp, nets, dev, n=128, steps=300, thr=1e-5, cap=20000):
     """The paper's plume with the cylinder (Sec. 2.1 geometry) at 128^2,
     MacCormack advection, buoyancy g = -0.5 (the plume rises about 20 cells in
     300 steps of dt = 0.5), every projection stopped by the same mean |div|
-    threshold: plain Jacobi from zero against the hybrid with the trained
-    network.  Reports the sweeps and time of each run and how far apart the
-    two plume-head trajectories are (Sec. 4.2: the same E_1 should give the
-    same plume)."""
+    threshold: plain Jacobi from zero against the hybrid with each trained
+    network (nets: architecture -> parameters).  Reports the sweeps and time
+    of each run and how far each hybrid's plume-head trajectory is from the
+    plain solver's (Sec. 4.2: the same E_1 should give the same plume, whatever
+    the network)."""
     import torch
     from paper_2109_09363_gb300 import workloads as W
     from paper_2109_09363_gb300.plume import Plume, PlumeConfig
@@ -435,8 +436,11 @@ def compare_plume_same_threshold(hp, params, dev, n=128, steps=300, thr=1e-5, ca
     res = {"workload": f"{n}^2 plume, inlet 0.29 n, cylinder 0.312 n at 0.625 n, MacCormack, "
                        f"g = -0.5, dt = 0.5, {steps} steps, E_t = {thr}, cap {cap}"}
     heads = {}
-    for mode in ("plain", "hybrid"):
-        cnn = hp.CNN(1, n, n, params=params) if mode == "hybrid" else None
+    # the MultiScale run keeps the key "hybrid"
+    modes = {"plain": None}
+    modes.update({("hybrid" if a == "multiscale" else "hybrid_" + a): a for a in nets})
+    for mode, arch in modes.items():
+        cnn = hp.CNN(1, n, n, params=nets[arch], arch=arch) if arch else None
         sim = Plume(cfg, t(u0[None].astype(np.float32)), t(v0[None].astype(np.float32)),
                     t(rho0[None].astype(np.float32)), fl, cnn=cnn)
         it = torch.zeros(steps, dtype=torch.int32, device=dev)
@@ -457,19 +461,26 @@ def compare_plume_same_threshold(hp, params, dev, n=128, steps=300, thr=1e-5, ca
         if cnn is not None:
             cnn.check()
             cnn.close()
-    d = np.abs(heads["plain"] - heads["hybrid"]).max(axis=0)
-    res["max_head_difference_cells"] = {"h_y": float(d[0]), "left": float(d[1]),
-                                        "right": float(d[2])}
-    res["sweep_ratio"] = res["plain"]["sweeps"] / max(res["hybrid"]["sweeps"], 1)
+    for mode in modes:
+        if mode == "plain":
+            continue
+        d = np.abs(heads["plain"] - heads[mode]).max(axis=0)
+        res[mode]["max_head_difference_cells"] = {"h_y": float(d[0]), "left": float(d[1]),
+                                                  "right": float(d[2])}
+        res[mode]["sweep_ratio"] = res["plain"]["sweeps"] / max(res[mode]["sweeps"], 1)
+    res["max_head_difference_cells"] = res["hybrid"]["max_head_difference_cells"]
+    res["sweep_ratio"] = res["hybrid"]["sweep_ratio"]
     return res
 
 
-def compare_in_distribution(hp, params, flush, stream, dev, ws):
-    """Plain vs hybrid on held-out grids of the training distribution at the
-    training resolution (256 x 128^2, vortex field + divergence sources + 0-4
-    obstacles, seeds disjoint from the training pairs), E_t = 1e-3, cap 5000:
-    the regime where the network sees most of the domain.  Same protocol as
-    the plain arm: device restore of u*, L2 flush between steps, CUDA events."""
+def compare_in_distribution(hp, nets, flush, stream, dev, ws):
+    """Plain vs hybrid with each trained network (nets: architecture ->
+    parameters; the MultiScale's run keeps the key "hybrid") on held-out grids
+    of the training distribution at the training resolution (256 x 128^2,
+    vortex field + divergence sources + 0-4 obstacles, seeds disjoint from the
+    training pairs), E_t = 1e-3, cap 5000: the regime where the network sees
+    most of the domain.  Same protocol as the plain arm: device restore of u*,
+    L2 flush between steps, CUDA events."""
     import torch
     from paper_2109_09363_gb300 import workloads as W
     nb, n, thr, cap = IN_DIST_GRIDS, 128, 1e-3, 5000
@@ -479,17 +490,19 @@ def compare_in_distribution(hp, params, flush, stream, dev, ws):
     fd = torch.from_numpy(f_np).to(dev)
     ud, vd = torch.empty_like(uh), torch.empty_like(vh)
     ctx = hp.Context(nb, n, n, device=dev.index)
-    cnn = hp.CNN(nb, n, n, params=params)
     prm = hp.ProjectParams(threshold=thr, max_iters=cap, temporal_block=T_BLOCK)
     res = {}
-    for arm in ("plain", "hybrid"):
+    arms = {"plain": None}
+    arms.update({("hybrid" if a == "multiscale" else "hybrid_" + a): a for a in nets})
+    for arm, arch in arms.items():
         out = None
+        cnn = hp.CNN(nb, n, n, params=nets[arch], arch=arch) if arch else None
 
         def step():
             nonlocal out
             ud.copy_(uh)
             vd.copy_(vh)
-            if arm == "plain":
+            if cnn is None:
                 out = hp.hp_project(ctx, ud, vd, fd, prm, out=out)
             else:
                 out = hp.hp_project_hybrid(ctx, cnn, ud, vd, fd, prm, out=out)
@@ -510,9 +523,11 @@ def compare_in_distribution(hp, params, flush, stream, dev, ws):
         res[arm] = {"value": ws * nb / (ms * 1e-3), "ms_per_step": ms,
                     "iters_mean": float(it.mean()), "iters_max": int(it.max()),
                     "converged": int(out["converged"].sum().item())}
-    cnn.close()
+        if cnn is not None:
+            res[arm]["speedup"] = res["plain"]["ms_per_step"] / ms
+            cnn.close()
     ctx.close()
-    res["speedup"] = res["plain"]["ms_per_step"] / res["hybrid"]["ms_per_step"]
+    res["speedup"] = res["hybrid"]["speedup"]
     res["workload"] = (f"{nb} x {n}^2 held-out training-distribution grids (seeds "
                        f"{IN_DIST_SEED}..), E_t = {thr}, cap {cap}")
     return res
