@@ -236,14 +236,14 @@ hp_status hp_project_adjoint(hp_ctx *ctx, const float *gu, const float *gv, cons
                              float rho0, float *gu_star, float *gv_star, float *g_phi0,
                              void *stream);
 
-/* MultiScale CNN of the hybrid method (Sec. 3.1): three branches at 1/4,
- * 1/2 and full resolution, 3 x 3 convolutions with replicated borders, ReLU
- * after every convolution of a branch except its last two, 2 x 2 / 4 x 4
+/* CNNs of the hybrid method (Sec. 3.1).  The MultiScale: three branches at
+ * 1/4, 1/2 and full resolution, 3 x 3 convolutions with replicated borders,
+ * ReLU after every convolution of a branch except its last two, 2 x 2 / 4 x 4
  * average pooling down, bilinear x 2 up; input [div / s, flags], s = mean
- * |div| over fluid cells (1 if zero); 372,643 parameters.  BF16 weights and
- * activations, FP32 accumulation (tensor cores for the 32/64-channel layers).
- * An hp_cnn owns its device weights and a workspace for grids up to
- * max_shape (ny, nx multiples of 4). */
+ * |div| over fluid cells (1 if zero); 372,643 parameters.  The SmallScale and
+ * the MonoScale below.  BF16 weights and activations, FP32 accumulation
+ * (tensor cores for the 32/64-channel layers).  An hp_cnn owns its device
+ * weights and a workspace for grids up to max_shape (ny, nx multiples of 4). */
 typedef struct hp_cnn hp_cnn;
 /* Architectures (Sec. 3.1).  SmallScale: the MultiScale graph with fewer
  * filters, every 64-channel layer at 32 channels, 123,491 parameters.
@@ -267,9 +267,10 @@ hp_status hp_cnn_create_arch(hp_cnn **cnn, int32_t arch, hp_shape max_shape, int
 /* The architecture of cnn (-1 for NULL). */
 int32_t hp_cnn_get_arch(const hp_cnn *cnn);
 void hp_cnn_destroy(hp_cnn *cnn);
-/* params: HOST float [hp_cnn_arch_param_count(arch)], layers in the order scale 1/4
- * (5 layers), 1/2 (7), 1 (7); per layer weights [cout][cin][3][3] then bias
- * [cout].  Weights are rounded to BF16 on upload; synchronous. */
+/* params: HOST float [hp_cnn_arch_param_count(arch)], layers in network
+ * order (MultiScale and SmallScale: scale 1/4 (5 layers), 1/2 (7), 1 (7));
+ * per layer weights [cout][cin][3][3] then bias [cout].  Weights are rounded
+ * to BF16 on upload; synchronous. */
 hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
 /* Device-side status of a network: every wait of its tensor-core kernels on
  * the completion of MMAs or copies is bounded; one that gives up leaves that

@@ -1,12 +1,16 @@
-// MultiScale CNN (Sec. 3.1) on sm_103a and the hybrid projection (Sec. 3.3):
-// the network predicts the scaled pressure from [div/s, flags] and hands it to
+// The CNNs of Sec. 3.1 on sm_103a and the hybrid projection (Sec. 3.3): the
+// network predicts the scaled pressure from [div/s, flags] and hands it to
 // the Jacobi sweeps as the initial guess.
 //
-// Network (3 x 3 convolutions, replicated borders; ReLU after every
+// MultiScale (3 x 3 convolutions, replicated borders; ReLU after every
 // convolution of a branch except its last two):
 //   scale 1/4: [pool4(div/s), pool4(flags)]          2 -> 32 -> 64 -> 64 -> 32 -> 1
 //   scale 1/2: [pool2(div/s), pool2(flags), up(o4)]  3 -> 32 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1
 //   scale 1  : [div/s, flags, up(o2)]                3 -> 32 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1
+// SmallScale: the same with every 64-channel layer at 32 channels.
+// MonoScale: one branch, [div/s, flags] 2 -> 32 -> 64 x 6 -> 32 -> 1 at full
+// resolution.  A network is its layer table; its branches are the runs of
+// layers that end in one output channel.
 // pool = average pooling (2 x 2 / 4 x 4), up = bilinear x 2 at half-pixel
 // centres with the edge repeated.  s = mean |div| over the fluid cells (1 if
 // zero); phi_0 = s * output on cells with an open face (the Poisson equation
