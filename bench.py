@@ -673,6 +673,42 @@ def profile_cnn(batch, n, arch="multiscale") -> int:
     return 0
 
 
+def profile_cnn_scaling(sizes=(32, 64, 128, 256, 512, 1024, 2048)) -> int:
+    """t_inf of one grid against its size for every network (the paper's
+    Fig. 15): CUDA events over 20 forwards after 5 untimed ones, one JSON line
+    per network and size."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    from paper_2109_09363_gb300 import training as T
+    from paper_2109_09363_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    for n in sizes:
+        u, v, fl = W.batched_vortex_case(1, n)
+        ud = torch.from_numpy(u.astype(np.float32)).to(dev)
+        vd = torch.from_numpy(v.astype(np.float32)).to(dev)
+        fd = torch.from_numpy(fl).to(dev)
+        div = hp.hp_divergence(ud, vd, fd)
+        for arch in NETWORKS:
+            cnn = hp.CNN(1, n, n, params=T.init_params(seed=1, arch=arch), arch=arch)
+            for _ in range(5):
+                hp.hp_cnn_forward(cnn, div, fd)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(20):
+                hp.hp_cnn_forward(cnn, div, fd)
+            b.record()
+            torch.cuda.synchronize()
+            cnn.check()
+            ms = a.elapsed_time(b) / 20
+            flop = 2.0 * CNN_MACS_PER_PIXEL[arch] * n * n
+            print(json.dumps({"profile_cnn_scaling": arch, "n": n, "ms": ms,
+                              "tflops": flop / ms / 1e9}), flush=True)
+            cnn.close()
+    return 0
+
+
 def profile_train(batch, n, norm=1) -> int:
     """Time the physics-driven loss gradient (network forward, loss, backward)
     on BATCH training-distribution grids of N x N, after 3 untimed calls."""
@@ -728,6 +764,8 @@ def main():
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
     ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
+    ap.add_argument("--profile-cnn-scaling", action="store_true",
+                    help="only time one forward of every network on one grid of 32^2 .. 2048^2")
     ap.add_argument("--arch", default="multiscale", choices=list(NETWORKS),
                     help="network of --profile-cnn")
     ap.add_argument("--profile-train", nargs=2, type=int, metavar=("BATCH", "N"),
@@ -754,6 +792,8 @@ def main():
         return profile_conv(*args.profile_conv)
     if args.profile_cnn:
         return profile_cnn(*args.profile_cnn, arch=args.arch)
+    if args.profile_cnn_scaling:
+        return profile_cnn_scaling()
     if args.profile_train:
         return profile_train(*args.profile_train)
 
