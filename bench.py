@@ -406,8 +406,11 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     ms_arm = arms.pop("multiscale")
     in_dist = compare_in_distribution(hp, trained, flush, stream, u0.device, ws)
     plume = compare_plume_same_threshold(hp, trained, u0.device)
+    # the paper's size (Sec. 2.1, 512^2), networks trained at 128^2 as in Sec. 3.2
+    plume512 = compare_plume_same_threshold(hp, trained, u0.device, n=512, steps=300)
     ms_arm["in_distribution_128"] = in_dist
     ms_arm["plume_same_threshold"] = plume
+    ms_arm["plume_same_threshold_512"] = plume512
     for arch in NETWORKS[1:]:
         ms_arm[arch] = arms[arch]
         ms_arm[arch]["t_inf_over_multiscale"] = (arms[arch]["t_inf_ms_16_grids"] /
@@ -468,6 +471,8 @@ def compare_plume_same_threshold(hp, nets, dev, n=128, steps=300, thr=1e-5, cap=
         res[mode]["max_head_difference_cells"] = {"h_y": float(d[0]), "left": float(d[1]),
                                                   "right": float(d[2])}
         res[mode]["sweep_ratio"] = res["plain"]["sweeps"] / max(res[mode]["sweeps"], 1)
+        # the paper's eta: time of the plain solver over the hybrid's (Sec. 5)
+        res[mode]["eta"] = res["plain"]["seconds"] / res[mode]["seconds"]
     res["max_head_difference_cells"] = res["hybrid"]["max_head_difference_cells"]
     res["sweep_ratio"] = res["hybrid"]["sweep_ratio"]
     return res
