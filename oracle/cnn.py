@@ -22,6 +22,15 @@ resolution with replicated borders on [div/s, flags].  Reading: 3 x 3 kernels
 only, 2 -> 32 -> 64 -> 64 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1, ReLU after every
 convolution except the last two; 222,497 parameters.
 
+Unet (Sec. 3.1: five scales, max pooling down, bilinear up, skip connections,
+3 x 3 and 1 x 1 kernels; the widths are in a figure that is not recoverable).
+Reading: encoder levels at n, n/2, n/4, n/8 end in 32 channels (the skip
+features): 2 -> 32 -> 32, then after each 2 x 2 max pooling 32 -> 64 -> 32;
+the bottom (n/16) 32 -> 64 -> 64 -> 32; each decoder level takes
+[up(coarser), skip] (64 channels) through 64 -> 64 -> 32, the last one
+64 -> 32 -> 32 and a 1 x 1 convolution 32 -> 1.  ReLU after every
+convolution except the last two; 388,545 parameters.
+
 Layout: activations [C][H][W] (one grid), weights [Cout][Cin][3][3].
 """
 from __future__ import annotations
@@ -49,8 +58,18 @@ ARCHS = {
 }
 
 
+# the Unet's layers in network order: (scale, cin, cout, kernel size)
+UNET_LAYERS = ([(1, 2, 32, 3), (1, 32, 32, 3)] +
+               [(sc, c, o, 3) for sc in (2, 4, 8) for c, o in ((32, 64), (64, 32))] +
+               [(16, 32, 64, 3), (16, 64, 64, 3), (16, 64, 32, 3)] +
+               [(sc, c, o, 3) for sc in (8, 4, 2) for c, o in ((64, 64), (64, 32))] +
+               [(1, 64, 32, 3), (1, 32, 32, 3), (1, 32, 1, 1)])
+
+
 def param_shapes(arch="multiscale"):
-    """[(scale, layer, (Cout, Cin, 3, 3), (Cout,))] in network order."""
+    """[(scale, layer, (Cout, Cin, k, k), (Cout,))] in network order."""
+    if arch == "unet":
+        return [(sc, l, (o, c, k, k), (o,)) for l, (sc, c, o, k) in enumerate(UNET_LAYERS)]
     out = []
     for sc, w in ARCHS[arch]:
         for l in range(len(w) - 1):
@@ -65,7 +84,7 @@ def param_count(arch="multiscale"):
 def arch_of(params):
     """The architecture whose layer shapes the parameter list has."""
     shapes = [(tuple(np.shape(w)), tuple(np.shape(b))) for w, b in params]
-    for name in ARCHS:
+    for name in list(ARCHS) + ["unet"]:
         if shapes == [(ws, bs) for _, _, ws, bs in param_shapes(name)]:
             return name
     raise ValueError("parameters of no known architecture")
@@ -82,7 +101,7 @@ def init_params(seed=0, arch="multiscale"):
     g = np.random.Generator(np.random.PCG64(seed))
     params = []
     for sc, l, ws, bs in param_shapes(arch):
-        fan_in = ws[1] * 9
+        fan_in = ws[1] * ws[2] * ws[3]
         lim = np.sqrt(6.0 / fan_in)
         params.append((g.uniform(-lim, lim, ws), np.zeros(bs)))
     return params
@@ -118,6 +137,17 @@ def conv3x3_backward(x, w, gy):
     gxp[:, :, 1] += gxp[:, :, 0]
     gxp[:, :, W] += gxp[:, :, W + 1]
     return gxp[:, 1:H + 1, 1:W + 1], gw, gy.sum(axis=(1, 2))
+
+
+def maxpool2(x):
+    """2 x 2 max pooling of [C][H][W] (H, W even)."""
+    return np.maximum(np.maximum(x[:, 0::2, 0::2], x[:, 0::2, 1::2]),
+                      np.maximum(x[:, 1::2, 0::2], x[:, 1::2, 1::2]))
+
+
+def conv1x1(x, w, b):
+    """y[o] = b[o] + sum_i w[o, i] x[i]; w [Cout][Cin][1][1]."""
+    return np.einsum("oi,ihw->ohw", w[:, :, 0, 0], x) + b[:, None, None]
 
 
 def avgpool2(x):
@@ -184,6 +214,10 @@ def forward(params, div, flags, keep=False, act_round=None):
     reduced-precision storage of activations; the arithmetic stays FP64."""
     rnd = act_round if act_round is not None else (lambda a: a)
     x0 = np.stack([np.asarray(div, np.float64), (np.asarray(flags) != 0).astype(np.float64)])
+    if arch_of(params) == "unet":
+        if keep:
+            raise NotImplementedError("the Unet's backward is not built")
+        return _forward_unet(params, x0, rnd)
     xin = {1: x0, 2: avgpool2(x0)}
     xin[4] = avgpool2(xin[2])
     tape = []
@@ -201,6 +235,31 @@ def forward(params, div, flags, keep=False, act_round=None):
             h = rnd(out) if l < nl - 1 else out
         prev = h
     return (prev[0], tape) if keep else prev[0]
+
+
+def _forward_unet(params, x0, rnd):
+    """The Unet of the reading above on x0 = [div_s, flags] (H, W divisible by
+    16); rnd models the storage rounding of every stored activation."""
+    nl = len(params)
+    it = iter(enumerate(params))
+
+    def conv(h):
+        l, (w, b) = next(it)
+        pre = conv1x1(h, w, b) if w.shape[2] == 1 else conv3x3(h, w, b)
+        out = np.maximum(pre, 0.0) if relu_after(l, nl) else pre
+        return rnd(out) if l < nl - 1 else out
+
+    h = rnd(x0)
+    skips = []
+    for level in range(4):
+        if level > 0:
+            h = maxpool2(h)
+        h = conv(conv(h))
+        skips.append(h)
+    h = conv(conv(conv(maxpool2(h))))
+    for level in (3, 2, 1, 0):
+        h = conv(conv(np.concatenate([rnd(upsample2(h)), skips[level]], axis=0)))
+    return conv(h)[0]
 
 
 def flatten(params):

@@ -231,3 +231,53 @@ def test_monoscale_gradients_by_central_differences():
         bm[li][1][j] -= eps
         fd = (np.sum(C.forward(bp, div, fl) * gout) - np.sum(C.forward(bm, div, fl) * gout)) / (2 * eps)
         assert np.isclose(grads[li][1][j], fd, rtol=1e-5, atol=1e-8)
+
+
+def test_unet_parameter_count_and_structure():
+    shapes = C.param_shapes("unet")
+    assert len(shapes) == 20 and C.param_count("unet") == 388545
+    # five scales; the last layer is the 1 x 1 convolution 32 -> 1
+    assert sorted({sc for sc, _, _, _ in shapes}) == [1, 2, 4, 8, 16]
+    assert shapes[-1][2] == (1, 32, 1, 1)
+    assert C.arch_of(C.init_params(0, "unet")) == "unet"
+
+
+def test_maxpool_matches_library():
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((3, 8, 12))
+    assert np.array_equal(C.maxpool2(x), F.max_pool2d(T(x)[None], 2)[0].numpy())
+
+
+def test_unet_is_a_chain_of_library_operations():
+    """Encoder (replicate-padded 3 x 3 convolutions, ReLU, 2 x 2 max pooling),
+    decoder ([bilinear x 2 of the coarser features, skip features], 3 x 3
+    convolutions), 1 x 1 output; ReLU after every convolution except the last
+    two (torch FP64 on CPU)."""
+    rng = np.random.default_rng(12)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in C.init_params(6, "unet")]
+    n = 32
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    ws = iter(enumerate(params))
+
+    def conv(h):
+        l, (w, b) = next(ws)
+        pad = (1, 1, 1, 1) if w.shape[2] == 3 else (0, 0, 0, 0)
+        h = F.conv2d(F.pad(h, pad, mode="replicate"), T(w), T(b))
+        return torch.relu(h) if l < len(params) - 2 else h
+
+    h = torch.stack([T(div), T(fl.astype(np.float64))])[None]
+    skips = []
+    for level in range(4):
+        if level > 0:
+            h = F.max_pool2d(h, 2)
+        h = conv(conv(h))
+        skips.append(h)
+    h = conv(conv(conv(F.max_pool2d(h, 2))))
+    for level in (3, 2, 1, 0):
+        up = F.interpolate(h, scale_factor=2, mode="bilinear", align_corners=False)
+        h = conv(conv(torch.cat([up, skips[level]], dim=1)))
+    h = conv(h)
+    assert np.allclose(C.forward(params, div, fl), h[0, 0].numpy(), rtol=1e-12, atol=1e-12)
+    with pytest.raises(NotImplementedError):
+        C.forward(params, div, fl, keep=True)
