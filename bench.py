@@ -41,9 +41,12 @@ TRAIN_SWEEPS = 40000
 # multiply-adds per full-resolution pixel of each network: the scale-1 branch,
 # a quarter of the scale-1/2 branch, a sixteenth of the scale-1/4 branch
 # (MultiScale 148,608 + 148,608 / 4 + 74,592 / 16; SmallScale 47,232 +
-# 47,232 / 4 + 28,512 / 16); the MonoScale's one branch 222,048
-CNN_MACS_PER_PIXEL = {"multiscale": 190422, "smallscale": 60822, "monoscale": 222048}
-NETWORKS = ("multiscale", "smallscale", "monoscale")
+# 47,232 / 4 + 28,512 / 16); the MonoScale's one branch 222,048; the Unet's
+# levels n .. n/16 weighted by 1, 1/4, .., 1/256
+CNN_MACS_PER_PIXEL = {"multiscale": 190422, "smallscale": 60822, "monoscale": 222048,
+                      "unet": 68000}
+NETWORKS = ("multiscale", "smallscale", "monoscale")  # trained in the hybrid arm
+FORWARD_NETWORKS = NETWORKS + ("unet",)  # forward only (no trainer for the Unet)
 # held-out grids of the training distribution for the in-distribution comparison
 IN_DIST_GRIDS, IN_DIST_SEED = 256, 100000
 T_BLOCK = 8
@@ -697,7 +700,7 @@ def profile_cnn_scaling(sizes=(32, 64, 128, 256, 512, 1024, 2048)) -> int:
         vd = torch.from_numpy(v.astype(np.float32)).to(dev)
         fd = torch.from_numpy(fl).to(dev)
         div = hp.hp_divergence(ud, vd, fd)
-        for arch in NETWORKS:
+        for arch in FORWARD_NETWORKS:
             cnn = hp.CNN(1, n, n, params=T.init_params(seed=1, arch=arch), arch=arch)
             for _ in range(5):
                 hp.hp_cnn_forward(cnn, div, fd)
@@ -773,7 +776,7 @@ def main():
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
     ap.add_argument("--profile-cnn-scaling", action="store_true",
                     help="only time one forward of every network on one grid of 32^2 .. 2048^2")
-    ap.add_argument("--arch", default="multiscale", choices=list(NETWORKS),
+    ap.add_argument("--arch", default="multiscale", choices=list(FORWARD_NETWORKS),
                     help="network of --profile-cnn")
     ap.add_argument("--profile-train", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the physics-driven loss gradient on BATCH grids of N x N, "

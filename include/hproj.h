@@ -250,11 +250,19 @@ typedef struct hp_cnn hp_cnn;
  * MonoScale: one feed-forward branch at full resolution on [div / s, flags],
  * 2 -> 32 -> 64 -> 64 -> 64 -> 64 -> 64 -> 64 -> 32 -> 1 (3 x 3, replicated
  * borders, ReLU after all but the last two), 222,497 parameters; its params
- * vector holds its 9 layers in that order. */
+ * vector holds its 9 layers in that order.
+ * Unet: encoder levels n, n/2, n/4, n/8 ending in 32-channel skip features
+ * (2 -> 32 -> 32, then after each 2 x 2 max pooling 32 -> 64 -> 32), bottom
+ * n/16 32 -> 64 -> 64 -> 32, decoder levels on [bilinear x 2 of the coarser
+ * features, skip features] 64 -> 64 -> 32, the last 64 -> 32 -> 32 and a
+ * 1 x 1 32 -> 1 (its weights [1][32][1][1] in params); ReLU after all but
+ * the last two; 388,545 parameters; grid sizes multiples of 16.  Forward and
+ * hybrid projection only: hp_trainer_create returns HP_ERR_UNSUPPORTED. */
 typedef enum {
     HP_CNN_MULTISCALE = 0,
     HP_CNN_SMALLSCALE = 1,
-    HP_CNN_MONOSCALE = 2
+    HP_CNN_MONOSCALE = 2,
+    HP_CNN_UNET = 3
 } hp_cnn_arch;
 /* Parameter count of the MultiScale; of the architecture arch (-1 if arch is
  * not one of hp_cnn_arch). */
@@ -269,8 +277,8 @@ int32_t hp_cnn_get_arch(const hp_cnn *cnn);
 void hp_cnn_destroy(hp_cnn *cnn);
 /* params: HOST float [hp_cnn_arch_param_count(arch)], layers in network
  * order (MultiScale and SmallScale: scale 1/4 (5 layers), 1/2 (7), 1 (7));
- * per layer weights [cout][cin][3][3] then bias [cout].  Weights are rounded
- * to BF16 on upload; synchronous. */
+ * per layer weights [cout][cin][k][k] (k = 3, the Unet's output layer 1)
+ * then bias [cout].  Weights are rounded to BF16 on upload; synchronous. */
 hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
 /* Device-side status of a network: every wait of its tensor-core kernels on
  * the completion of MMAs or copies is bounded; one that gives up leaves that

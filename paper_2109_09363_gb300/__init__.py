@@ -388,12 +388,13 @@ def hp_project_adjoint(ctx: Context, gu, gv, gp, flags, k: int, dt: float = 1.0,
     return gus, gvs, gphi
 
 
-CNN_ARCHS = {"multiscale": 0, "smallscale": 1, "monoscale": 2}  # hp_cnn_arch
+CNN_ARCHS = {"multiscale": 0, "smallscale": 1, "monoscale": 2, "unet": 3}  # hp_cnn_arch
 
 
 class CNN:
     """CNN weights and workspace on the device (hp_cnn): the MultiScale, its
-    narrower SmallScale variant or the feed-forward MonoScale (Sec. 3.1)."""
+    narrower SmallScale variant, the feed-forward MonoScale or the Unet (Sec.
+    3.1; forward and hybrid projection only, grid sizes multiples of 16)."""
 
     def __init__(self, batch: int, ny: int, nx: int, device: int | None = None, params=None,
                  arch: str = "multiscale"):

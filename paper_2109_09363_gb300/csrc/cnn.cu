@@ -37,11 +37,12 @@ namespace {
 
 struct LayerSpec {
     int scale, cin, cout, relu;
+    int ks = 3;  // kernel size: 3, or 1 (run as a 3 x 3 with only the centre tap)
 };
 
 // network order: scale 1/4, then 1/2, then 1
 constexpr int kLayers = 19;      // MultiScale and SmallScale
-constexpr int kMaxLayers = 19;   // the most of any architecture
+constexpr int kMaxLayers = 20;   // the most of any architecture (the Unet)
 constexpr int kMaxBranches = 3;
 const LayerSpec kSpecMulti[kLayers] = {
     {4, 2, 32, 1},  {4, 32, 64, 1}, {4, 64, 64, 1}, {4, 64, 32, 0}, {4, 32, 1, 0},
@@ -63,15 +64,33 @@ const LayerSpec kSpecMono[kLayersMono] = {
     {1, 2, 32, 1},  {1, 32, 64, 1}, {1, 64, 64, 1}, {1, 64, 64, 1}, {1, 64, 64, 1},
     {1, 64, 64, 1}, {1, 64, 64, 1}, {1, 64, 32, 0}, {1, 32, 1, 0}};
 
+// Unet (Sec. 3.1): encoder levels n, n/2, n/4, n/8 ending in 32-channel skip
+// features (2 -> 32 -> 32, then 2 x 2 max pooling and 32 -> 64 -> 32), the
+// bottom n/16 32 -> 64 -> 64 -> 32, decoder levels on [up(coarser), skip]
+// (64 channels) 64 -> 64 -> 32, the last 64 -> 32 -> 32 and a 1 x 1 32 -> 1
+constexpr int kLayersUnet = 20;
+const LayerSpec kSpecUnet[kLayersUnet] = {
+    {1, 2, 32, 1},   {1, 32, 32, 1},  {2, 32, 64, 1},  {2, 64, 32, 1},  {4, 32, 64, 1},
+    {4, 64, 32, 1},  {8, 32, 64, 1},  {8, 64, 32, 1},  {16, 32, 64, 1}, {16, 64, 64, 1},
+    {16, 64, 32, 1}, {8, 64, 64, 1},  {8, 64, 32, 1},  {4, 64, 64, 1},  {4, 64, 32, 1},
+    {2, 64, 64, 1},  {2, 64, 32, 1},  {1, 64, 32, 1},  {1, 32, 32, 0},  {1, 32, 1, 0, 1}};
+
 const LayerSpec* spec_for(int arch)
 {
     return arch == HP_CNN_MULTISCALE   ? kSpecMulti
            : arch == HP_CNN_SMALLSCALE ? kSpecSmall
            : arch == HP_CNN_MONOSCALE  ? kSpecMono
+           : arch == HP_CNN_UNET       ? kSpecUnet
                                        : nullptr;
 }
 
-int layers_for(int arch) { return arch == HP_CNN_MONOSCALE ? kLayersMono : kLayers; }
+int layers_for(int arch)
+{
+    return arch == HP_CNN_MONOSCALE ? kLayersMono : arch == HP_CNN_UNET ? kLayersUnet : kLayers;
+}
+
+// grid sizes a network accepts: multiples of 4 (16 for the Unet's five scales)
+int size_multiple(int arch) { return arch == HP_CNN_UNET ? 16 : 4; }
 
 // The branches of a network in order: consecutive layers up to a 1-channel
 // output.  A branch after the first takes the up-sampled output of the one
@@ -225,6 +244,84 @@ __global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xi
             dst[0] = reinterpret_cast<const uint4*>(v)[0];
             dst[1] = reinterpret_cast<const uint4*>(v)[1];
         }
+    }
+}
+
+// 2 x 2 max pooling of BF16 [B][H][W][C] (H, W even) into [B][H/2][W/2][C],
+// one thread per output pixel and 8-channel chunk (c8 chunks per pixel); the
+// maximum of BF16 values is exact.
+__global__ void maxpool2_kernel(const uint4* __restrict__ x, uint4* __restrict__ y, int B, int H,
+                                int W, int c8)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long n = (long)B * Ho * Wo * c8;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(q % c8);
+        const long p = q / c8;
+        const int j = (int)(p % Wo);
+        const long t = p / Wo;
+        const int i = (int)(t % Ho);
+        const int b = (int)(t / Ho);
+        const size_t r0 = (((size_t)b * H + 2 * i) * W + 2 * j) * c8 + c;
+        const size_t r1 = r0 + (size_t)W * c8;
+        uint4 v[4] = {x[r0], x[r0 + c8], x[r1], x[r1 + c8]};
+        uint4 m = v[0];
+        uint32_t* mw = reinterpret_cast<uint32_t*>(&m);
+        for (int k = 1; k < 4; ++k) {
+            const uint32_t* vw = reinterpret_cast<const uint32_t*>(&v[k]);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                __nv_bfloat162 a, bb;
+                memcpy(&a, &mw[h], 4);
+                memcpy(&bb, &vw[h], 4);
+                a = __hmax2(a, bb);
+                memcpy(&mw[h], &a, 4);
+            }
+        }
+        y[q] = m;
+    }
+}
+
+// Decoder input of the Unet, BF16 [B][H][W][64]: channels 0-31 the bilinear
+// x 2 up-sampling (half-pixel centres, edge sample repeated, FP32 then
+// rounded to BF16) of coarse [B][H/2][W/2][32], channels 32-63 the skip
+// features [B][H][W][32]; one thread per pixel and 8-channel chunk.
+__global__ void up_concat_kernel(const uint4* __restrict__ coarse, const uint4* __restrict__ skip,
+                                 uint4* __restrict__ y, int B, int H, int W)
+{
+    const int Hc = H / 2, Wc = W / 2;
+    const long n = (long)B * H * W * 8;
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(q % 8);
+        const long p = q / 8;
+        if (c >= 4) {
+            y[q] = skip[p * 4 + (c - 4)];
+            continue;
+        }
+        const int i = (int)(p % W);  // column
+        const long t = p / W;
+        const int j = (int)(t % H);  // row
+        const int b = (int)(t / H);
+        const int ci = i >> 1, cj = j >> 1;
+        const int ni = (i & 1) ? min(ci + 1, Wc - 1) : max(ci - 1, 0);
+        const int nj = (j & 1) ? min(cj + 1, Hc - 1) : max(cj - 1, 0);
+        const uint4* base = coarse + (size_t)b * Hc * Wc * 4 + c;
+        const uint4 q00 = base[((size_t)cj * Wc + ci) * 4], q01 = base[((size_t)cj * Wc + ni) * 4];
+        const uint4 q10 = base[((size_t)nj * Wc + ci) * 4], q11 = base[((size_t)nj * Wc + ni) * 4];
+        const __nv_bfloat16* a00 = reinterpret_cast<const __nv_bfloat16*>(&q00);
+        const __nv_bfloat16* a01 = reinterpret_cast<const __nv_bfloat16*>(&q01);
+        const __nv_bfloat16* a10 = reinterpret_cast<const __nv_bfloat16*>(&q10);
+        const __nv_bfloat16* a11 = reinterpret_cast<const __nv_bfloat16*>(&q11);
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float rx0 = 0.75f * __bfloat162float(a00[k]) + 0.25f * __bfloat162float(a01[k]);
+            const float rx1 = 0.75f * __bfloat162float(a10[k]) + 0.25f * __bfloat162float(a11[k]);
+            o[k] = __float2bfloat16_rn(0.75f * rx0 + 0.25f * rx1);
+        }
+        y[q] = *reinterpret_cast<const uint4*>(o);
     }
 }
 
@@ -430,6 +527,7 @@ struct hp_cnn {
     __nv_bfloat16* wtc_first[kMaxBranches];  // [9][32][16]
     __nv_bfloat16* wtc_last[kMaxBranches];   // [9][16][32]
     float* btc_last[kMaxBranches];           // [16]
+    __nv_bfloat16* skip[4];  // Unet: the encoder's skip features per level, BF16 [P_level][32]
     float* s;
     double* s_part;                // [B][kScaleCtas] partial sums of |div|
     unsigned long long* s_cnt;     // [B][kScaleCtas] fluid-cell counts
@@ -493,6 +591,84 @@ static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const flo
     return check_launch();
 }
 
+static int ew_blocks(const hp_cnn* c, long n)
+{
+    const long cap = 16L * c->num_sms;
+    const long b = (n + 255) / 256;
+    return (int)(b < cap ? b : cap);
+}
+
+// The Unet's forward: its 20 layers in order on the stream (tensor-core
+// convolutions from a width of 32 pixels, the gather kernel or CUDA cores
+// below), skip features kept per level, decoder inputs built by
+// up_concat_kernel.  Activations ping-pong between act[0] and act[1].
+static hp_status unet_forward(hp_cnn* c, const float* div, const uint8_t* flags, float* phi_hat,
+                              hp_shape s, cudaStream_t st)
+{
+    const LayerSpec* sp = c->spec;
+    const int B = s.batch;
+    int l = 0;
+    hp_status rc = HP_OK;
+    auto conv = [&](const void* x, void* y, int H, int W) {
+        if (rc == HP_OK)
+            rc = launch_conv3x3_tc(x, c->w[l], c->bias[l], y, B, H, W, sp[l].cin, sp[l].cout,
+                                   sp[l].relu, c->err, c->num_sms, st);
+        ++l;
+    };
+    auto pool = [&](const __nv_bfloat16* x, __nv_bfloat16* y, int H, int W) {
+        if (rc != HP_OK) return;
+        const long n = (long)B * (H / 2) * (W / 2) * 4;
+        maxpool2_kernel<<<ew_blocks(c, n), 256, 0, st>>>((const uint4*)x, (uint4*)y, B, H, W, 4);
+        rc = check_launch();
+    };
+    auto up_concat = [&](const __nv_bfloat16* coarse, const __nv_bfloat16* sk, __nv_bfloat16* y,
+                         int H, int W) {
+        if (rc != HP_OK) return;
+        const long n = (long)B * H * W * 8;
+        up_concat_kernel<<<ew_blocks(c, n), 256, 0, st>>>((const uint4*)coarse, (const uint4*)sk,
+                                                           (uint4*)y, B, H, W);
+        rc = check_launch();
+    };
+    __nv_bfloat16* a = c->act[0];
+    __nv_bfloat16* b = c->act[1];
+    // encoder level 0: [div/s, flags] -> 32 -> 32
+    BranchIn in = {div, flags, c->s, nullptr, s.ny, s.nx, 1};
+    rc = launch_first(c, 0, in, sp[0].cin, nullptr, (const float*)c->w[0], c->bias[0], a, B, s.ny,
+                      s.nx, st);
+    l = 1;
+    conv(a, c->skip[0], s.ny, s.nx);
+    // levels 1-3: max pooling, 32 -> 64 -> 32
+    for (int lev = 1; lev < 4; ++lev) {
+        const int H = s.ny >> lev, W = s.nx >> lev;
+        pool(c->skip[lev - 1], a, 2 * H, 2 * W);
+        conv(a, b, H, W);
+        conv(b, c->skip[lev], H, W);
+    }
+    // bottom: 32 -> 64 -> 64 -> 32, the result in b
+    {
+        const int H = s.ny >> 4, W = s.nx >> 4;
+        pool(c->skip[3], a, 2 * H, 2 * W);
+        conv(a, b, H, W);
+        conv(b, a, H, W);
+        conv(a, b, H, W);
+    }
+    // decoder: [up(coarser), skip] -> two convolutions; the result ends in cur
+    __nv_bfloat16* cur = b;
+    __nv_bfloat16* other = a;
+    for (int lev = 3; lev >= 0; --lev) {
+        const int H = s.ny >> lev, W = s.nx >> lev;
+        up_concat(cur, c->skip[lev], other, H, W);
+        conv(other, cur, H, W);
+        conv(cur, other, H, W);
+        __nv_bfloat16* t = cur;
+        cur = other;
+        other = t;
+    }
+    if (rc != HP_OK) return rc;
+    // the 1 x 1 output convolution 32 -> 1 (FP32)
+    return launch_last(c, 0, cur, (const float*)c->w[l], c->bias[l], phi_hat, B, s.ny, s.nx, st);
+}
+
 // tensor-core copies of the first and last layer of every branch
 static hp_status pack_edge_layers(hp_cnn* c, cudaStream_t st)
 {
@@ -507,10 +683,14 @@ static hp_status pack_edge_layers(hp_cnn* c, cudaStream_t st)
     return HP_OK;
 }
 
+// weights of layer l in the parameter vector (ks x ks taps) and on the device
+// (always 9 taps; a 1 x 1 layer has only the centre tap non-zero)
 static size_t layer_wcount(const LayerSpec* sp, int l)
 {
-    return (size_t)9 * sp[l].cin * sp[l].cout;
+    return (size_t)sp[l].ks * sp[l].ks * sp[l].cin * sp[l].cout;
 }
+
+static size_t dev_wcount(const LayerSpec* sp, int l) { return (size_t)9 * sp[l].cin * sp[l].cout; }
 
 extern "C" {
 
@@ -544,6 +724,7 @@ void hp_cnn_destroy(hp_cnn* c)
         cudaFree(c->wtc_last[k]);
         cudaFree(c->btc_last[k]);
     }
+    for (int k = 0; k < 4; ++k) cudaFree(c->skip[k]);
     cudaFree(c->s_part);
     cudaFree(c->s_cnt);
     cudaFree(c->s);
@@ -555,7 +736,9 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
 {
     if (!out) return HP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!spec_for(arch) || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
+    if (!spec_for(arch) || !shape_ok(mx) || mx.ny % size_multiple(arch) ||
+        mx.nx % size_multiple(arch))
+        return HP_ERR_INVALID_ARG;
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     hp_cnn* c = new hp_cnn();
@@ -565,6 +748,7 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
     c->br = branches_of(c->spec, c->nlayers);
     memset(c->w, 0, sizeof(c->w));
     memset(c->out, 0, sizeof(c->out));
+    memset(c->skip, 0, sizeof(c->skip));
     memset(c->bias, 0, sizeof(c->bias));
     c->device = device;
     c->max_shape = mx;
@@ -574,7 +758,7 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
     bool okm = true;
     for (int l = 0; l < c->nlayers && okm; ++l) {
         const LayerSpec& ls = c->spec[l];
-        const size_t wb = layer_wcount(c->spec, l) * (ls.cin >= 32 && ls.cout >= 32 ? 2 : 4);
+        const size_t wb = dev_wcount(c->spec, l) * (ls.cin >= 32 && ls.cout >= 32 ? 2 : 4);
         okm = cudaMalloc(&c->w[l], wb) == cudaSuccess &&
               cudaMalloc((void**)&c->bias[l], c->spec[l].cout * sizeof(float)) == cudaSuccess;
         if (okm) {
@@ -600,6 +784,9 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
               cudaMalloc((void**)&c->wtc_first[k], 9 * 32 * 16 * 2) == cudaSuccess &&
               cudaMalloc((void**)&c->wtc_last[k], 9 * 16 * 32 * 2) == cudaSuccess &&
               cudaMalloc((void**)&c->btc_last[k], 16 * sizeof(float)) == cudaSuccess;
+    if (arch == HP_CNN_UNET)
+        for (int k = 0; k < 4 && okm; ++k)
+            okm = cudaMalloc((void**)&c->skip[k], (px >> (2 * k)) * 32 * 2) == cudaSuccess;
     if (!okm) {
         set_cuda_error(cudaGetLastError());
         hp_cnn_destroy(c);
@@ -617,9 +804,9 @@ hp_status hp_cnn_create(hp_cnn** out, hp_shape mx, int device)
     return hp_cnn_create_arch(out, HP_CNN_MULTISCALE, mx, device);
 }
 
-// params: host FP32 in the order of the network (scale 1/4, 1/2, 1), each
-// layer weights [cout][cin][3][3] then bias [cout].  Weights are rounded to
-// BF16 on upload.
+// params: host FP32 in the order of the network, each layer weights
+// [cout][cin][ks][ks] then bias [cout].  Weights are rounded to BF16 on
+// upload; a 1 x 1 layer is stored as a 3 x 3 with zero outer taps.
 hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
 {
     if (!c || !params || n != hp_cnn_arch_param_count(c->arch)) return HP_ERR_INVALID_ARG;
@@ -630,12 +817,14 @@ hp_status hp_cnn_set_params(hp_cnn* c, const float* params, int64_t n)
         const bool tc = ci >= 32 && co >= 32;
         std::vector<uint16_t> wb;
         std::vector<float> wf;
-        const size_t nw = layer_wcount(c->spec, l);
+        const size_t nw = dev_wcount(c->spec, l);
+        const bool k1 = c->spec[l].ks == 1;
         if (tc) wb.assign(nw, 0); else wf.assign(nw, 0.0f);
         for (int o = 0; o < co; ++o)
             for (int i = 0; i < ci; ++i)
                 for (int t = 0; t < 9; ++t) {
-                    const float v = p[((size_t)o * ci + i) * 9 + t];
+                    const float v = k1 ? (t == 4 ? p[(size_t)o * ci + i] : 0.0f)
+                                       : p[((size_t)o * ci + i) * 9 + t];
                     const __nv_bfloat16 h = __float2bfloat16_rn(v);
                     if (tc) {
                         uint16_t bits;
@@ -674,15 +863,25 @@ hp_status hp_cnn_get_params(const hp_cnn* c, float* params, int64_t n)
 hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, float* phi_hat,
                          float* s_out, hp_shape s, void* stream)
 {
-    if (!c || !div || !flags || !shape_ok(s) || s.ny % 4 || s.nx % 4 ||
-        s.batch > c->max_shape.batch || (size_t)s.batch * s.ny * s.nx >
-                                            (size_t)c->max_shape.batch * c->max_shape.ny *
-                                                c->max_shape.nx)
+    if (!c || !div || !flags || !shape_ok(s) || s.ny % size_multiple(c->arch) ||
+        s.nx % size_multiple(c->arch) || s.batch > c->max_shape.batch ||
+        (size_t)s.batch * s.ny * s.nx >
+            (size_t)c->max_shape.batch * c->max_shape.ny * c->max_shape.nx)
         return HP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cells = (size_t)s.ny * s.nx;
     hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
     if (rc != HP_OK) return rc;
+    if (c->arch == HP_CNN_UNET) {
+        rc = unet_forward(c, div, flags, phi_hat ? phi_hat : c->out[0], s, st);
+        if (rc != HP_OK) return rc;
+        if (s_out) {
+            cudaError_t e = cudaMemcpyAsync(s_out, c->s, s.batch * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+        }
+        return HP_OK;
+    }
     int l = 0;
     const float* prev = nullptr;
     for (int k = 0; k < c->br.n; ++k) {
@@ -1552,6 +1751,8 @@ static constexpr int kWgradChunk = 2048;
 hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
 {
     if (!out || !cnn || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
+    // the Unet's backward (max pooling, concatenated skips) is not built
+    if (cnn->arch == HP_CNN_UNET) return HP_ERR_UNSUPPORTED;
     // the forward pass of training runs in the network's own input workspace
     // (scale, BF16 branch input), sized for its max_shape
     if (mx.batch > cnn->max_shape.batch || mx.ny > cnn->max_shape.ny ||

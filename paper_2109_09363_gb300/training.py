@@ -18,7 +18,11 @@ SMALL_LAYERS = ([(2, 32), (32, 32), (32, 32), (32, 32), (32, 1)] +
                 2 * [(3, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1)])
 # the MonoScale: one full-resolution branch of nine convolutions
 MONO_LAYERS = [(2, 32), (32, 64)] + 5 * [(64, 64)] + [(64, 32), (32, 1)]
-ARCH_LAYERS = {"multiscale": LAYERS, "smallscale": SMALL_LAYERS, "monoscale": MONO_LAYERS}
+# the Unet (forward only): (cin, cout, kernel size), the last layer 1 x 1
+UNET_LAYERS = ([(2, 32), (32, 32)] + 3 * [(32, 64), (64, 32)] + [(32, 64), (64, 64), (64, 32)]
+               + 3 * [(64, 64), (64, 32)] + [(64, 32), (32, 32), (32, 1, 1)])
+ARCH_LAYERS = {"multiscale": LAYERS, "smallscale": SMALL_LAYERS, "monoscale": MONO_LAYERS,
+               "unet": UNET_LAYERS}
 
 
 def init_params(seed: int = 0, arch: str = "multiscale") -> np.ndarray:
@@ -26,9 +30,11 @@ def init_params(seed: int = 0, arch: str = "multiscale") -> np.ndarray:
     [cout][cin][3][3] He-uniform, then zero biases), FP32."""
     g = np.random.Generator(np.random.PCG64(seed))
     parts = []
-    for cin, cout in ARCH_LAYERS[arch]:
-        lim = np.sqrt(6.0 / (9 * cin))
-        parts.append(g.uniform(-lim, lim, 9 * cin * cout))
+    for layer in ARCH_LAYERS[arch]:
+        cin, cout = layer[:2]
+        taps = layer[2] ** 2 if len(layer) > 2 else 9
+        lim = np.sqrt(6.0 / (taps * cin))
+        parts.append(g.uniform(-lim, lim, taps * cin * cout))
         parts.append(np.zeros(cout))
     return np.concatenate(parts).astype(np.float32)
 

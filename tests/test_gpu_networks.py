@@ -1,6 +1,7 @@
 """The SmallScale network (Sec. 3.1: the MultiScale with fewer filters, every
-64-channel layer at 32 channels) and the MonoScale (one feed-forward branch of
-nine convolutions at full resolution) on the GPU against the FP64 oracle:
+64-channel layer at 32 channels), the MonoScale (one feed-forward branch of
+nine convolutions at full resolution) and the Unet (five scales, max pooling,
+concatenated skip features; forward only) on the GPU against the FP64 oracle:
 1. the forward (hp_cnn_forward), under the bar of the MultiScale forward test;
 2. the hybrid projection from the same guess;
 3. the training gradient (hand-written backward: on the tensor cores from a
@@ -21,7 +22,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 hp = pytest.importorskip("paper_2109_09363_gb300")
 
-ARCHS = ["smallscale", "monoscale"]
+ARCHS = ["smallscale", "monoscale"]   # forward and training
+FORWARD_ARCHS = ARCHS + ["unet"]     # forward and hybrid projection
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +55,7 @@ def case(B, n, seed):
     return (np.stack(us).astype(np.float32), np.stack(vs).astype(np.float32), np.stack(fs))
 
 
-@pytest.mark.parametrize("arch", ARCHS)
+@pytest.mark.parametrize("arch", FORWARD_ARCHS)
 @pytest.mark.parametrize("B,n", [(2, 64), (1, 128), (3, 32), (2, 16)])
 def test_network_forward_matches_oracle(dev, arch, B, n):
     params = random_params(3, arch)
@@ -83,7 +85,7 @@ def test_network_forward_matches_oracle(dev, arch, B, n):
 E_ULPS = 256
 
 
-@pytest.mark.parametrize("arch", ARCHS)
+@pytest.mark.parametrize("arch", FORWARD_ARCHS)
 def test_hybrid_projection_matches_oracle_from_the_same_guess(dev, arch):
     """The GPU stops where its own E history first reaches E_t; that history
     tracks the oracle's (same guess, same sweeps) within the FP32 bound above;
@@ -209,4 +211,30 @@ def test_parameter_counts_are_checked(dev, arch):
     with pytest.raises(hp.HprojError):
         cnn.set_params(C.flatten(C.init_params(1)))  # MultiScale-sized vector
     with pytest.raises(ValueError):
-        hp.CNN(B, n, n, arch="unet")
+        hp.CNN(B, n, n, arch="resnet")
+
+
+def test_unet_at_the_tensor_core_widths_and_argument_checks(dev):
+    """512 x 256: every level from 32 pixels wide up on the tensor cores, the
+    n/16 bottom (32 x 16) on the gather kernel; the Unet has no trainer and
+    wants sizes that are multiples of 16."""
+    B, ny, nx = 1, 256, 512
+    params = random_params(9, "unet")
+    u, v = W.vortex_velocity(ny, nx, 61, n_vortices=12, width=(4, 24))
+    fl = W.random_obstacles(ny, nx, 62, rect_side=(16, 64), disc_radius=(8, 32))
+    ud = torch.from_numpy(u[None].astype(np.float32)).to(dev)
+    vd = torch.from_numpy(v[None].astype(np.float32)).to(dev)
+    fd = torch.from_numpy(fl[None]).to(dev)
+    cnn = hp.CNN(B, ny, nx, params=C.flatten(params), arch="unet")
+    div = hp.hp_divergence(ud, vd, fd)
+    phi_hat, s = hp.hp_cnn_forward(cnn, div, fd)
+    torch.cuda.synchronize()
+    cnn.check()
+    d = div[0].cpu().numpy().astype(np.float64)
+    ref = C.forward(bf16_weights(params), d / float(s[0].cpu()), fl, act_round=C.round_bf16)
+    got = phi_hat[0].cpu().numpy()
+    assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), np.abs(got - ref).max()
+    with pytest.raises(hp.HprojError):
+        hp.Trainer(cnn, B, ny, nx)
+    with pytest.raises(hp.HprojError):
+        hp.CNN(1, 40, 48, arch="unet")

@@ -59,7 +59,8 @@ def test_cnn_parameter_count_matches_the_oracle(lib):
     assert int(lib.hp_cnn_arch_param_count(1)) == C.param_count("smallscale") == 123491
     assert hp.CNN.param_count("smallscale") == 123491
     assert int(lib.hp_cnn_arch_param_count(2)) == C.param_count("monoscale") == 222497
-    assert int(lib.hp_cnn_arch_param_count(3)) == -1
+    assert int(lib.hp_cnn_arch_param_count(3)) == C.param_count("unet") == 388545
+    assert int(lib.hp_cnn_arch_param_count(4)) == -1
     assert int(lib.hp_cnn_arch_param_count(-1)) == -1
 
 
@@ -70,9 +71,11 @@ def test_cnn_architecture_argument_checks(lib):
     assert not out
     assert lib.hp_cnn_create_arch(ctypes.byref(out), 1, hp.hp_shape(1, 62, 64), 0) == 1
     assert lib.hp_cnn_create_arch(None, 1, hp.hp_shape(1, 64, 64), 0) == 1
+    # the Unet's five scales need sizes that are multiples of 16
+    assert lib.hp_cnn_create_arch(ctypes.byref(out), 3, hp.hp_shape(1, 40, 48), 0) == 1
     assert lib.hp_cnn_get_arch(None) == -1
     with pytest.raises(ValueError):
-        hp.CNN.param_count("unet")
+        hp.CNN.param_count("resnet")
 
 
 def test_ctypes_structures_match_the_header(tmp_path):
