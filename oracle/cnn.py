@@ -215,9 +215,8 @@ def forward(params, div, flags, keep=False, act_round=None):
     rnd = act_round if act_round is not None else (lambda a: a)
     x0 = np.stack([np.asarray(div, np.float64), (np.asarray(flags) != 0).astype(np.float64)])
     if arch_of(params) == "unet":
-        if keep:
-            raise NotImplementedError("the Unet's backward is not built")
-        return _forward_unet(params, x0, rnd)
+        out, tape = _forward_unet(params, x0, rnd)
+        return (out, tape) if keep else out
     xin = {1: x0, 2: avgpool2(x0)}
     xin[4] = avgpool2(xin[2])
     tape = []
@@ -239,13 +238,17 @@ def forward(params, div, flags, keep=False, act_round=None):
 
 def _forward_unet(params, x0, rnd):
     """The Unet of the reading above on x0 = [div_s, flags] (H, W divisible by
-    16); rnd models the storage rounding of every stored activation."""
+    16); rnd models the storage rounding of every stored activation.  Returns
+    (output, tape): per layer its input and pre-activation, and the skip
+    features (the inputs of the max poolings)."""
     nl = len(params)
     it = iter(enumerate(params))
+    convs = []
 
     def conv(h):
         l, (w, b) = next(it)
         pre = conv1x1(h, w, b) if w.shape[2] == 1 else conv3x3(h, w, b)
+        convs.append((h, pre))
         out = np.maximum(pre, 0.0) if relu_after(l, nl) else pre
         return rnd(out) if l < nl - 1 else out
 
@@ -259,7 +262,61 @@ def _forward_unet(params, x0, rnd):
     h = conv(conv(conv(maxpool2(h))))
     for level in (3, 2, 1, 0):
         h = conv(conv(np.concatenate([rnd(upsample2(h)), skips[level]], axis=0)))
-    return conv(h)[0]
+    out = conv(h)[0]
+    return out, {"unet": True, "convs": convs, "skips": skips}
+
+
+def maxpool2_backward(x, g):
+    """Transpose of maxpool2 at x: each gradient goes to the first maximum of
+    its window in the order (0, 0), (0, 1), (1, 0), (1, 1)."""
+    gx = np.zeros_like(x)
+    m = maxpool2(x)
+    taken = np.zeros(m.shape, bool)
+    for dy in (0, 1):
+        for dx in (0, 1):
+            hit = (x[:, dy::2, dx::2] == m) & ~taken
+            gx[:, dy::2, dx::2] = np.where(hit, g, 0.0)
+            taken |= hit
+    return gx
+
+
+def conv1x1_backward(x, w, gy):
+    """(gx, gw, gb) of conv1x1."""
+    gx = np.einsum("oi,ohw->ihw", w[:, :, 0, 0], gy)
+    gw = np.einsum("ohw,ihw->oi", gy, x)[:, :, None, None]
+    return gx, gw, gy.sum(axis=(1, 2))
+
+
+def _backward_unet(params, tape, g_out):
+    """Gradients of the Unet's output w.r.t. every parameter (the forward's
+    rounding taken as the identity, as for the other networks)."""
+    nl = len(params)
+    convs, skips = tape["convs"], tape["skips"]
+    grads = [None] * nl
+    state = {"l": nl - 1}
+
+    def conv_back(g):
+        l = state["l"]
+        h, pre = convs[l]
+        if relu_after(l, nl):
+            g = g * (pre > 0)
+        w = params[l][0]
+        gx, gw, gb = conv1x1_backward(h, w, g) if w.shape[2] == 1 else conv3x3_backward(h, w, g)
+        grads[l] = (gw, gb)
+        state["l"] = l - 1
+        return gx
+
+    g = conv_back(g_out[None].astype(np.float64))
+    g_skip = [None] * 4
+    for level in (0, 1, 2, 3):
+        g_cat = conv_back(conv_back(g))
+        g_skip[level] = g_cat[32:]
+        g = upsample2_backward(g_cat[:32])
+    g = conv_back(conv_back(conv_back(g)))  # bottom, down to the pooled skip 3
+    for level in (3, 2, 1, 0):
+        g = g_skip[level] + maxpool2_backward(skips[level], g)
+        g = conv_back(conv_back(g))
+    return grads
 
 
 def flatten(params):
@@ -280,6 +337,8 @@ def unflatten(flat, arch="multiscale"):
 def backward(params, tape, g_out):
     """Gradients of the network output (given dL/dphi_hat) w.r.t. every
     parameter, as a list aligned with params: [(gw, gb), ...]."""
+    if isinstance(tape, dict) and tape.get("unet"):
+        return _backward_unet(params, tape, g_out)
     grads = [None] * len(params)
     g = g_out[None].astype(np.float64)
     idx = len(params) - 1

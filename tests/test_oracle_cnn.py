@@ -279,5 +279,70 @@ def test_unet_is_a_chain_of_library_operations():
         h = conv(conv(torch.cat([up, skips[level]], dim=1)))
     h = conv(h)
     assert np.allclose(C.forward(params, div, fl), h[0, 0].numpy(), rtol=1e-12, atol=1e-12)
-    with pytest.raises(NotImplementedError):
-        C.forward(params, div, fl, keep=True)
+
+
+def test_unet_gradients_match_library_autograd():
+    """The oracle backward of the Unet against torch autograd of the same
+    chain of library operations (FP64 on CPU; random inputs, so no ties in the
+    max pooling)."""
+    rng = np.random.default_rng(13)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in C.init_params(7, "unet")]
+    n = 32
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    gout = rng.standard_normal((n, n))
+    tw = [(T(w).requires_grad_(), T(b).requires_grad_()) for w, b in params]
+    ws = iter(enumerate(tw))
+
+    def conv(h):
+        l, (w, b) = next(ws)
+        pad = (1, 1, 1, 1) if w.shape[2] == 3 else (0, 0, 0, 0)
+        h = F.conv2d(F.pad(h, pad, mode="replicate"), w, b)
+        return torch.relu(h) if l < len(tw) - 2 else h
+
+    h = torch.stack([T(div), T(fl.astype(np.float64))])[None]
+    skips = []
+    for level in range(4):
+        if level > 0:
+            h = F.max_pool2d(h, 2)
+        h = conv(conv(h))
+        skips.append(h)
+    h = conv(conv(conv(F.max_pool2d(h, 2))))
+    for level in (3, 2, 1, 0):
+        up = F.interpolate(h, scale_factor=2, mode="bilinear", align_corners=False)
+        h = conv(conv(torch.cat([up, skips[level]], dim=1)))
+    (conv(h)[0, 0] * T(gout)).sum().backward()
+    out, tape = C.forward(params, div, fl, keep=True)
+    grads = C.backward(params, tape, gout)
+    for (gw, gb), (w, b) in zip(grads, tw):
+        assert np.allclose(gw, w.grad.numpy(), rtol=1e-10, atol=1e-12)
+        assert np.allclose(gb, b.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_unet_gradients_by_central_differences():
+    rng = np.random.default_rng(14)
+    params = [(w, 0.05 * rng.standard_normal(b.shape)) for w, b in C.init_params(8, "unet")]
+    n = 16
+    div = rng.standard_normal((n, n))
+    fl = (rng.random((n, n)) < 0.2).astype(np.uint8)
+    gout = rng.standard_normal((n, n))
+    _, tape = C.forward(params, div, fl, keep=True)
+    grads = C.backward(params, tape, gout)
+    eps = 1e-6
+    for li in [0, 5, 9, 12, 17, 19]:
+        w = params[li][0]
+        idx = tuple(rng.integers(0, s) for s in w.shape)
+        wp = [(ww.copy(), bb) for ww, bb in params]
+        wm = [(ww.copy(), bb) for ww, bb in params]
+        wp[li][0][idx] += eps
+        wm[li][0][idx] -= eps
+        fd = (np.sum(C.forward(wp, div, fl) * gout) - np.sum(C.forward(wm, div, fl) * gout)) / (2 * eps)
+        assert np.isclose(grads[li][0][idx], fd, rtol=1e-5, atol=1e-8), (li, idx)
+
+
+def test_maxpool_backward_routes_to_the_first_maximum():
+    x = np.array([[[1.0, 3.0, 2.0, 2.0], [3.0, 0.0, 2.0, 2.0]]])
+    g = np.array([[[5.0, 7.0]]])
+    gx = C.maxpool2_backward(x, g)
+    # ties go to the first maximum in the order (0, 0), (0, 1), (1, 0), (1, 1)
+    assert np.array_equal(gx, [[[0.0, 5.0, 7.0, 0.0], [0.0, 0.0, 0.0, 0.0]]])
