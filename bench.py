@@ -408,12 +408,16 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
         net.close()
     ms_arm = arms.pop("multiscale")
     in_dist = compare_in_distribution(hp, trained, flush, stream, u0.device, ws)
-    plume = compare_plume_same_threshold(hp, trained, u0.device)
+    heads128 = {}
+    plume = compare_plume_same_threshold(hp, trained, u0.device, heads_out=heads128)
     # the paper's size (Sec. 2.1, 512^2), networks trained at 128^2 as in Sec. 3.2
     plume512 = compare_plume_same_threshold(hp, trained, u0.device, n=512, steps=300)
+    plume_min = compare_plume_min_threshold(hp, trained, u0.device,
+                                            reference=heads128.get("plain"))
     ms_arm["in_distribution_128"] = in_dist
     ms_arm["plume_same_threshold"] = plume
     ms_arm["plume_same_threshold_512"] = plume512
+    ms_arm["plume_min_threshold"] = plume_min
     for arch in NETWORKS[1:]:
         ms_arm[arch] = arms[arch]
         ms_arm[arch]["t_inf_over_multiscale"] = (arms[arch]["t_inf_ms_16_grids"] /
@@ -421,7 +425,8 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     return ms_arm
 
 
-def compare_plume_same_threshold(hp, nets, dev, n=128, steps=300, thr=1e-5, cap=20000):
+def compare_plume_same_threshold(hp, nets, dev, n=128, steps=300, thr=1e-5, cap=20000,
+                                 heads_out=None):
     """The paper's plume with the cylinder (Sec. 2.1 geometry) at 128^2,
     MacCormack advection, buoyancy g = -0.5 (the plume rises about 20 cells in
     300 steps of dt = 0.5), every projection stopped by the same mean |div|
@@ -480,6 +485,84 @@ def compare_plume_same_threshold(hp, nets, dev, n=128, steps=300, thr=1e-5, cap=
         res[mode]["eta"] = res["plain"]["seconds"] / res[mode]["seconds"]
     res["max_head_difference_cells"] = res["hybrid"]["max_head_difference_cells"]
     res["sweep_ratio"] = res["hybrid"]["sweep_ratio"]
+    if heads_out is not None:
+        heads_out.update(heads)
+    return res
+
+
+def compare_plume_min_threshold(hp, nets, dev, n=128, steps=300, cap=20000, reference=None):
+    """The paper's threshold rule (Sec. 4.2): first every network runs the
+    plume alone (its guess is the projection, no Jacobi sweep) and records E_1
+    per step; the threshold of step k is the smallest of those E_1.  Then
+    plain Jacobi and the hybrid with each network run the same plume with that
+    per-step threshold.  Reports the threshold's range, and per run the sweeps,
+    time, eta against plain Jacobi and the plume-head distance to the plain
+    solver's trajectory (for the networks alone too) and, with reference (the
+    head trajectory [steps][3] of an accurate run of the same plume), to that."""
+    import torch
+    from paper_2109_09363_gb300 import workloads as W
+    from paper_2109_09363_gb300.plume import Plume, PlumeConfig
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    fl, (x0, x1) = W.paper_plume_geometry(n)
+    fl = t(fl[None])
+    u0, v0, rho0 = W.plume_initial_state(n, seed=2)
+
+    def run(arch, thresholds, max_iters):
+        cfg = PlumeConfig(ny=n, nx=n, dt=0.5, gravity=-0.5, inlet=(x0, x1),
+                          threshold=float(thresholds[0]), max_iters=max_iters, scheme=1)
+        cnn = hp.CNN(1, n, n, params=nets[arch], arch=arch) if arch else None
+        sim = Plume(cfg, t(u0[None].astype(np.float32)), t(v0[None].astype(np.float32)),
+                    t(rho0[None].astype(np.float32)), fl, cnn=cnn)
+        it = torch.zeros(steps, dtype=torch.int32, device=dev)
+        cv = torch.zeros(steps, dtype=torch.uint8, device=dev)
+        e1 = torch.zeros(steps, dtype=torch.float64, device=dev)
+        hd = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            sim.prm.threshold = float(thresholds[k])
+            out = sim.step()
+            it[k:k + 1].copy_(out["iters"])
+            cv[k:k + 1].copy_(out["converged"])
+            e1[k:k + 1].copy_(out["e1"])
+            hd.append(torch.stack(sim.head()).view(-1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if cnn is not None:
+            cnn.check()
+            cnn.close()
+        return {"sweeps": int(it.sum().item()), "converged_steps": int(cv.sum().item()),
+                "seconds": wall, "e1": e1.cpu().numpy(),
+                "heads": torch.stack(hd).cpu().numpy() * n}
+
+    alone = {a: run(a, np.zeros(steps), 0) for a in nets}
+    e_t = np.min(np.stack([r["e1"] for r in alone.values()]), axis=0)
+    res = {"workload": f"{n}^2 plume, inlet 0.29 n, cylinder 0.312 n at 0.625 n, MacCormack, "
+                       f"g = -0.5, dt = 0.5, {steps} steps, E_t(step) = min over the networks "
+                       f"alone, cap {cap}",
+           "threshold": {"min": float(e_t.min()), "median": float(np.median(e_t)),
+                         "max": float(e_t.max()),
+                         "set_by": {a: int(np.sum(r["e1"] == e_t)) for a, r in alone.items()}}}
+    runs = {"plain": run(None, e_t, cap)}
+    runs.update({"hybrid_" + a: run(a, e_t, cap) for a in nets})
+    runs.update({"alone_" + a: r for a, r in alone.items()})
+    ref = runs["plain"]["heads"]
+    for mode, r in runs.items():
+        out = {"sweeps": r["sweeps"], "converged_steps": r["converged_steps"],
+               "seconds": r["seconds"], "final_head_cells": r["heads"][-1].tolist()}
+        if mode != "plain":
+            d = np.abs(r["heads"] - ref).max(axis=0)
+            out["max_head_difference_cells"] = {"h_y": float(d[0]), "left": float(d[1]),
+                                                "right": float(d[2])}
+        if mode.startswith("hybrid_"):
+            out["eta"] = runs["plain"]["seconds"] / r["seconds"]
+        if reference is not None:
+            d = np.abs(r["heads"] - reference).max(axis=0)
+            out["max_head_difference_to_reference_cells"] = {
+                "h_y": float(d[0]), "left": float(d[1]), "right": float(d[2])}
+        res[mode] = out
+    if reference is not None:
+        res["reference"] = "plain Jacobi with every projection stopped at E_t = 1e-5 (cap 20,000)"
     return res
 
 
