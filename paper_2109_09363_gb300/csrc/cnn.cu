@@ -247,82 +247,79 @@ __global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xi
     }
 }
 
-// 2 x 2 max pooling of BF16 [B][H][W][C] (H, W even) into [B][H/2][W/2][C],
-// one thread per output pixel and 8-channel chunk (c8 chunks per pixel); the
-// maximum of BF16 values is exact.
-__global__ void maxpool2_kernel(const uint4* __restrict__ x, uint4* __restrict__ y, int B, int H,
-                                int W, int c8)
+// 2 x 2 max pooling of BF16 [B][H][W][C] (H, W even) into [B][H/2][W/2][C].
+// Block x = one output row (b, i); its threads cover the row's (pixel,
+// 8-channel chunk) items, c8 chunks per pixel.  The maximum of BF16 values is
+// exact.
+__global__ void maxpool2_kernel(const uint4* __restrict__ x, uint4* __restrict__ y, int H, int W,
+                                int c8)
 {
     const int Ho = H / 2, Wo = W / 2;
-    const long n = (long)B * Ho * Wo * c8;
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(q % c8);
-        const long p = q / c8;
-        const int j = (int)(p % Wo);
-        const long t = p / Wo;
-        const int i = (int)(t % Ho);
-        const int b = (int)(t / Ho);
-        const size_t r0 = (((size_t)b * H + 2 * i) * W + 2 * j) * c8 + c;
-        const size_t r1 = r0 + (size_t)W * c8;
-        uint4 v[4] = {x[r0], x[r0 + c8], x[r1], x[r1 + c8]};
-        uint4 m = v[0];
-        uint32_t* mw = reinterpret_cast<uint32_t*>(&m);
-        for (int k = 1; k < 4; ++k) {
-            const uint32_t* vw = reinterpret_cast<const uint32_t*>(&v[k]);
+    const int xi = blockIdx.y * blockDim.x + threadIdx.x;
+    if (xi >= Wo * c8) return;
+    const int c = xi % c8, j = xi / c8;
+    const int row = blockIdx.x;
+    const int i = row % Ho, b = row / Ho;
+    const size_t q = ((size_t)row * Wo + j) * c8 + c;
+    const size_t r0 = (((size_t)b * H + 2 * i) * W + 2 * j) * c8 + c;
+    const size_t r1 = r0 + (size_t)W * c8;
+    uint4 v[4] = {x[r0], x[r0 + c8], x[r1], x[r1 + c8]};
+    uint4 m = v[0];
+    uint32_t* mw = reinterpret_cast<uint32_t*>(&m);
+    for (int k = 1; k < 4; ++k) {
+        const uint32_t* vw = reinterpret_cast<const uint32_t*>(&v[k]);
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                __nv_bfloat162 a, bb;
-                memcpy(&a, &mw[h], 4);
-                memcpy(&bb, &vw[h], 4);
-                a = __hmax2(a, bb);
-                memcpy(&mw[h], &a, 4);
-            }
+        for (int h = 0; h < 4; ++h) {
+            __nv_bfloat162 a, bb;
+            memcpy(&a, &mw[h], 4);
+            memcpy(&bb, &vw[h], 4);
+            a = __hmax2(a, bb);
+            memcpy(&mw[h], &a, 4);
         }
-        y[q] = m;
     }
+    y[q] = m;
 }
 
 // Decoder input of the Unet, BF16 [B][H][W][64]: channels 0-31 the bilinear
 // x 2 up-sampling (half-pixel centres, edge sample repeated, FP32 then
 // rounded to BF16) of coarse [B][H/2][W/2][32], channels 32-63 the skip
-// features [B][H][W][32]; one thread per pixel and 8-channel chunk.
+// features [B][H][W][32].  Block x = one output row (b, j); its threads cover
+// the row's (pixel, 8-channel chunk) items.
 __global__ void up_concat_kernel(const uint4* __restrict__ coarse, const uint4* __restrict__ skip,
-                                 uint4* __restrict__ y, int B, int H, int W)
+                                 uint4* __restrict__ y, int H, int W)
 {
     const int Hc = H / 2, Wc = W / 2;
-    const long n = (long)B * H * W * 8;
-    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(q % 8);
-        const long p = q / 8;
-        if (c >= 4) {
-            y[q] = skip[p * 4 + (c - 4)];
-            continue;
-        }
-        const int i = (int)(p % W);  // column
-        const long t = p / W;
-        const int j = (int)(t % H);  // row
-        const int b = (int)(t / H);
-        const int ci = i >> 1, cj = j >> 1;
-        const int ni = (i & 1) ? min(ci + 1, Wc - 1) : max(ci - 1, 0);
-        const int nj = (j & 1) ? min(cj + 1, Hc - 1) : max(cj - 1, 0);
-        const uint4* base = coarse + (size_t)b * Hc * Wc * 4 + c;
-        const uint4 q00 = base[((size_t)cj * Wc + ci) * 4], q01 = base[((size_t)cj * Wc + ni) * 4];
-        const uint4 q10 = base[((size_t)nj * Wc + ci) * 4], q11 = base[((size_t)nj * Wc + ni) * 4];
-        const __nv_bfloat16* a00 = reinterpret_cast<const __nv_bfloat16*>(&q00);
-        const __nv_bfloat16* a01 = reinterpret_cast<const __nv_bfloat16*>(&q01);
-        const __nv_bfloat16* a10 = reinterpret_cast<const __nv_bfloat16*>(&q10);
-        const __nv_bfloat16* a11 = reinterpret_cast<const __nv_bfloat16*>(&q11);
-        __align__(16) __nv_bfloat16 o[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const float rx0 = 0.75f * __bfloat162float(a00[k]) + 0.25f * __bfloat162float(a01[k]);
-            const float rx1 = 0.75f * __bfloat162float(a10[k]) + 0.25f * __bfloat162float(a11[k]);
-            o[k] = __float2bfloat16_rn(0.75f * rx0 + 0.25f * rx1);
-        }
-        y[q] = *reinterpret_cast<const uint4*>(o);
+    const int xi = blockIdx.y * blockDim.x + threadIdx.x;
+    if (xi >= W * 8) return;
+    const int c = xi & 7;
+    const int i = xi >> 3;  // column
+    const int row = blockIdx.x;
+    const size_t p = (size_t)row * W + i;
+    const size_t q = p * 8 + c;
+    if (c >= 4) {
+        y[q] = skip[p * 4 + (c - 4)];
+        return;
     }
+    const int j = row % H;  // row within the grid
+    const int b = row / H;
+    const int ci = i >> 1, cj = j >> 1;
+    const int ni = (i & 1) ? min(ci + 1, Wc - 1) : max(ci - 1, 0);
+    const int nj = (j & 1) ? min(cj + 1, Hc - 1) : max(cj - 1, 0);
+    const uint4* base = coarse + (size_t)b * Hc * Wc * 4 + c;
+    const uint4 q00 = base[((size_t)cj * Wc + ci) * 4], q01 = base[((size_t)cj * Wc + ni) * 4];
+    const uint4 q10 = base[((size_t)nj * Wc + ci) * 4], q11 = base[((size_t)nj * Wc + ni) * 4];
+    const __nv_bfloat16* a00 = reinterpret_cast<const __nv_bfloat16*>(&q00);
+    const __nv_bfloat16* a01 = reinterpret_cast<const __nv_bfloat16*>(&q01);
+    const __nv_bfloat16* a10 = reinterpret_cast<const __nv_bfloat16*>(&q10);
+    const __nv_bfloat16* a11 = reinterpret_cast<const __nv_bfloat16*>(&q11);
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float rx0 = 0.75f * __bfloat162float(a00[k]) + 0.25f * __bfloat162float(a01[k]);
+        const float rx1 = 0.75f * __bfloat162float(a10[k]) + 0.25f * __bfloat162float(a11[k]);
+        o[k] = __float2bfloat16_rn(0.75f * rx0 + 0.25f * rx1);
+    }
+    y[q] = *reinterpret_cast<const uint4*>(o);
 }
 
 // BF16 tensor-core copies of a branch's first and last layer from their
@@ -591,13 +588,6 @@ static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const flo
     return check_launch();
 }
 
-static int ew_blocks(const hp_cnn* c, long n)
-{
-    const long cap = 16L * c->num_sms;
-    const long b = (n + 255) / 256;
-    return (int)(b < cap ? b : cap);
-}
-
 // The Unet's forward: its 20 layers in order on the stream (tensor-core
 // convolutions from a width of 32 pixels, the gather kernel or CUDA cores
 // below), skip features kept per level, decoder inputs built by
@@ -615,18 +605,19 @@ static hp_status unet_forward(hp_cnn* c, const float* div, const uint8_t* flags,
                                    sp[l].relu, c->err, c->num_sms, st);
         ++l;
     };
+    // one block row per output row, the row's items across blockIdx.y
     auto pool = [&](const __nv_bfloat16* x, __nv_bfloat16* y, int H, int W) {
         if (rc != HP_OK) return;
-        const long n = (long)B * (H / 2) * (W / 2) * 4;
-        maxpool2_kernel<<<ew_blocks(c, n), 256, 0, st>>>((const uint4*)x, (uint4*)y, B, H, W, 4);
+        const dim3 grid((unsigned)(B * (H / 2)), (unsigned)((W / 2 * 4 + 255) / 256));
+        maxpool2_kernel<<<grid, 256, 0, st>>>((const uint4*)x, (uint4*)y, H, W, 4);
         rc = check_launch();
     };
     auto up_concat = [&](const __nv_bfloat16* coarse, const __nv_bfloat16* sk, __nv_bfloat16* y,
                          int H, int W) {
         if (rc != HP_OK) return;
-        const long n = (long)B * H * W * 8;
-        up_concat_kernel<<<ew_blocks(c, n), 256, 0, st>>>((const uint4*)coarse, (const uint4*)sk,
-                                                           (uint4*)y, B, H, W);
+        const dim3 grid((unsigned)(B * H), (unsigned)((W * 8 + 255) / 256));
+        up_concat_kernel<<<grid, 256, 0, st>>>((const uint4*)coarse, (const uint4*)sk, (uint4*)y,
+                                               H, W);
         rc = check_launch();
     };
     __nv_bfloat16* a = c->act[0];
