@@ -106,6 +106,33 @@ def test_ctypes_structures_match_the_header(tmp_path):
                     hp.hp_train_params.lambda_div.offset]
 
 
+def test_architecture_numbers_match_the_header(tmp_path):
+    """The binding's architecture names map to the header's hp_cnn_arch values,
+    and the initial parameters of every architecture have the oracle's size."""
+    import os
+    import subprocess
+    from oracle import cnn as C
+    from paper_2109_09363_gb300 import training as T
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "arch.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "hproj.h"\n'
+        "int main(void) {\n"
+        '  printf("%d %d %d %d\\n", HP_CNN_MULTISCALE, HP_CNN_SMALLSCALE, HP_CNN_MONOSCALE,\n'
+        "         HP_CNN_UNET);\n"
+        "  return 0; }\n")
+    exe = tmp_path / "arch"
+    r = subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals == [hp.CNN_ARCHS[a] for a in ("multiscale", "smallscale", "monoscale", "unet")]
+    for arch in hp.CNN_ARCHS:
+        n = C.param_count(arch)
+        assert hp.CNN.param_count(arch) == n
+        assert T.init_params(seed=0, arch=arch).size == n
+
+
 def test_new_entry_points_reject_null_arguments(lib):
     s = hp.hp_shape(1, 4, 4)
     assert lib.hp_plume_head(None, s, 1.0, 0.01, None, None) == 1
