@@ -1741,6 +1741,7 @@ static constexpr int kWgradChunk = 2048;
 
 hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
 {
+    if (out) *out = nullptr;
     if (!out || !cnn || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
     // the Unet's backward (max pooling, concatenated skips) is not built
     if (cnn->arch == HP_CNN_UNET) return HP_ERR_UNSUPPORTED;
