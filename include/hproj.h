@@ -317,7 +317,8 @@ typedef struct {
     float lr, beta1, beta2, eps;
     float lambda_div;
 } hp_train_params;
-/* max_shape may not exceed the network's own (HP_ERR_INVALID_ARG). */
+/* max_shape may not exceed the network's own (HP_ERR_INVALID_ARG); a Unet has
+ * no trainer (HP_ERR_UNSUPPORTED).  *trainer is NULL on every error. */
 hp_status hp_trainer_create(hp_trainer **trainer, hp_cnn *cnn, hp_shape max_shape);
 void hp_trainer_destroy(hp_trainer *trainer);
 /* Loss (double [1], device, may be NULL) and its gradient w.r.t. every
