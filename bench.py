@@ -1120,8 +1120,29 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
         }
+        # how many grids of the last timed step reached E_t before the cap
+        line["converged"] = {"grids": int(out["converged"].sum().item()), "of": B}
         if hybrid is not None:
             line["hybrid"] = hybrid
+            # the headline comparison: CNN-hybrid against plain Jacobi on the
+            # same grids, both at the same E_t; under BASELINE's cap, and with
+            # the cap lifted so that every grid of both arms converges (the
+            # paper's comparison at equal mean|div|)
+            unc = hybrid["equal_threshold_uncapped"]
+            line["hybrid_vs_plain"] = {
+                "network": "multiscale",
+                "equal_threshold": {
+                    "speedup": unc["speedup"], "threshold": THR, "cap": unc["cap"],
+                    "converged_hybrid": unc["hybrid"]["converged"],
+                    "converged_plain": unc["plain"]["converged"], "of": B,
+                    "all_converged": unc["hybrid"]["converged"] == B and
+                    unc["plain"]["converged"] == B},
+                "capped": {"speedup": hybrid["speedup_vs_plain"], "threshold": THR, "cap": CAP,
+                           "converged_hybrid": hybrid["converged"],
+                           "converged_plain": int(out["converged"].sum().item()), "of": B},
+                "others": {a: {"equal_threshold": hybrid[a]["equal_threshold_uncapped"]["speedup"],
+                               "capped": hybrid[a]["speedup_vs_plain"]}
+                           for a in NETWORKS[1:] if a in hybrid}}
         if pdnn is not None:
             line["pdnn_training"] = pdnn
         line["driver_step"] = driver

@@ -47,9 +47,21 @@ typedef enum {
     HP_ERR_NONFINITE = 3,   /* the input velocity holds NaN or Inf */
     HP_ERR_OOM = 5,         /* device allocation failed */
     HP_ERR_UNSUPPORTED = 6, /* the requested combination is not built */
-    HP_ERR_TIMEOUT = 7      /* a tensor-core completion wait gave up (hp_cnn_check) */
+    HP_ERR_TIMEOUT = 7,     /* a tensor-core completion wait gave up (hp_cnn_check) */
+    HP_ERR_IO = 8,          /* a checkpoint file could not be written, or is missing,
+                               truncated, corrupted or of another format version */
+    /* not an error: the network's guess of some grid was not finite, and the
+     * hybrid projection started that grid's sweeps from zero (hp_cnn_check) */
+    HP_WARN_CNN_NONFINITE = 100
 } hp_status;
 
+/* Shape of a batch of grids.  Every call rejects a shape with a non-positive
+ * size, or with batch > HP_MAX_BATCH or ny > HP_MAX_NY, with
+ * HP_ERR_INVALID_ARG before it launches anything: the kernels cover rows and
+ * grids with one CUDA grid dimension each (65535 blocks at most), some of
+ * them with one more (the ny + 1 rows of v faces). */
+#define HP_MAX_BATCH 65534
+#define HP_MAX_NY 65534
 typedef struct {
     int32_t batch; /* number of independent grids B */
     int32_t ny;    /* rows */
@@ -147,6 +159,18 @@ hp_status hp_project(hp_ctx *ctx, float *u, float *v, const uint8_t *flags, hp_s
 hp_status hp_jacobi_sweeps(hp_ctx *ctx, const float *phi_in, const float *div,
                            const uint8_t *flags, float *phi_out, int32_t n, double *e_out,
                            hp_shape shape, void *stream);
+
+/* Pressure target of a training pair from the plain solver (the networks are
+ * trained on pairs of divergence and pressure, Sec. 3.2): n masked Jacobi
+ * sweeps from phi_0 = 0 on the right-hand side div (n >= 0), then
+ *     target_out = (phi_n + phi_{n+1}) / 2,
+ * the mean of the last iterate and one more sweep; the mean cancels the
+ * period-2 (checkerboard) component that plain Jacobi never damps.  The
+ * iterates are those of hp_jacobi_sweeps bit for bit.  div, target_out float
+ * [B][ny][nx], flags uint8, device memory; target_out must not alias div.
+ * Uses the context's workspaces. */
+hp_status hp_jacobi_target(hp_ctx *ctx, const float *div, const uint8_t *flags, int32_t n,
+                           float *target_out, hp_shape shape, void *stream);
 
 /* Number of grids of this shape that the grid-resident sweep kernel
  * (sweep_kernel = 4) can hold on the device at once, one thread-block cluster
@@ -283,11 +307,22 @@ hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
 /* Device-side status of a network: every wait of its tensor-core kernels on
  * the completion of MMAs or copies is bounded; one that gives up leaves that
  * kernel's output incomplete, sets an error word of the network and lets the
- * kernel return instead of hanging.  This call synchronises the device, reads
- * and clears that word: HP_ERR_TIMEOUT if it was set since the last check (by
- * hp_cnn_forward, hp_project_hybrid or a trainer built on the network),
- * else HP_OK. */
+ * kernel return instead of hanging.  hp_project_hybrid also records there
+ * that it replaced a non-finite guess.  This call synchronises the device,
+ * reads and clears that word: HP_ERR_TIMEOUT if a wait gave up since the last
+ * check (in hp_cnn_forward, hp_project_hybrid or a trainer built on the
+ * network), else HP_WARN_CNN_NONFINITE if a hybrid projection fell back to a
+ * zero guess, else HP_OK. */
 hp_status hp_cnn_check(hp_cnn *cnn);
+/* Polls of each bounded pipeline wait (copies and MMAs of the warp-
+ * specialised convolution and weight-gradient kernels, images from 32 pixels
+ * wide) before it gives up; 0 restores the compiled limit (2^22 polls, far
+ * above any wait of a healthy kernel).  A small value makes those waits give
+ * up on purpose: the kernels then still wait (with the compiled limit) for
+ * the MMAs they issued, free their tensor memory and return, and
+ * hp_cnn_check reports HP_ERR_TIMEOUT; the outputs of such calls are
+ * incomplete.  Host only, no synchronisation; HP_ERR_INVALID_ARG for NULL. */
+hp_status hp_cnn_set_wait_limit(hp_cnn *cnn, uint32_t polls);
 hp_status hp_cnn_get_params(const hp_cnn *cnn, float *params, int64_t n);
 /* Network output phi_hat (float [B][ny][nx], device; the guess is s * phi_hat)
  * and s (float [B], device, may be NULL) for the divergence div (float
@@ -296,7 +331,13 @@ hp_status hp_cnn_forward(hp_cnn *cnn, const float *div, const uint8_t *flags, fl
                          float *s_out, hp_shape shape, void *stream);
 /* Hybrid projection (Sec. 3.3): phi_0 = s * CNN(div / s, flags) (0 on cells
  * without an open face), then hp_project from phi_0.  Same arguments and
- * outputs as hp_project. */
+ * outputs as hp_project; the batch and grid must also fit the network (its
+ * max_shape, sides multiples of 4, of 16 for the Unet); every argument is
+ * checked before anything is launched.  The Jacobi sweeps always follow and
+ * judge the guess: a grid whose guess is not finite (NaN or Inf on a cell
+ * with an open face) starts from phi_0 = 0 instead, i.e. it is the plain
+ * projection, while the other grids keep their guesses; hp_cnn_check then
+ * returns HP_WARN_CNN_NONFINITE. */
 hp_status hp_project_hybrid(hp_ctx *ctx, hp_cnn *cnn, float *u, float *v, const uint8_t *flags,
                             hp_shape shape, const hp_project_params *params, float *p_out,
                             int32_t *iters_out, double *e1_out, double *einf_out,
@@ -356,6 +397,39 @@ hp_status hp_trainer_pdnn_step(hp_trainer *trainer, const float *div, const uint
  * device status as hp_cnn_check does (the masters are copied either way). */
 hp_status hp_trainer_sync_params(hp_trainer *trainer);
 
+/* Optimiser state of a trainer, copied to HOST memory (synchronous): the FP32
+ * masters, the first and second Adam moments (float [the network's parameter
+ * count] each, network parameter order) and the number of Adam steps taken;
+ * any pointer may be NULL. */
+hp_status hp_trainer_get_state(hp_trainer *trainer, float *master, float *m, float *v,
+                               int64_t *step);
+
+/* Checkpoint files (a training run that stops resumes from one; the format
+ * is versioned and checksummed; little-endian):
+ *   magic "HPCNNCK1", uint32 version 1, int32 arch, int64 n (the
+ *   architecture's parameter count), int64 step, uint32 moments (0/1),
+ *   uint32 0, float32 parameters[n] (network order, as hp_cnn_set_params),
+ *   when moments = 1 float32 m[n] and v[n] (Adam moments), then the FNV-1a
+ *   64-bit checksum of all bytes before it.
+ * Files are written under path + ".tmp" and renamed; host I/O only, the
+ * trainer calls synchronise the device.  Unreadable, truncated, foreign or
+ * corrupted files give HP_ERR_IO and change nothing.
+ * hp_cnn_save: the network's architecture and parameters (those last set
+ * with hp_cnn_set_params or copied back by hp_trainer_sync_params), step 0,
+ * no moments.
+ * hp_cnn_load: a new network of the file's architecture for grids up to
+ * max_shape on `device`, with the file's parameters (as hp_cnn_create_arch
+ * followed by hp_cnn_set_params); *cnn is NULL on every error.
+ * hp_trainer_save: the trainer's masters, Adam moments and step.
+ * hp_trainer_load: restores them into a trainer whose network has the
+ * file's architecture (else HP_ERR_IO) and refreshes the network's BF16
+ * weights and its host copy of the parameters; a file without moments
+ * restarts Adam from step 0 with zero moments. */
+hp_status hp_cnn_save(const hp_cnn *cnn, const char *path);
+hp_status hp_cnn_load(hp_cnn **cnn, const char *path, hp_shape max_shape, int device);
+hp_status hp_trainer_save(hp_trainer *trainer, const char *path);
+hp_status hp_trainer_load(hp_trainer *trainer, const char *path);
+
 /* Allocation-free variant of hp_div_norms.  The paper has no counterpart; it
  * exists for callers that cannot call cudaMalloc: a host framework that owns
  * all device memory through its own pool and forbids other allocations, a
@@ -369,12 +443,17 @@ hp_status hp_trainer_sync_params(hp_trainer *trainer);
  * grid) is a fixed array inside libhproj.so: every GPU that loads the library
  * holds it (about 2.1 MB) until the process exits.  Limits: batch <=
  * HP_NOALLOC_MAX_BATCH and batch * ny * ceil(nx / 256) <= HP_NOALLOC_MAX_BLOCKS
- * (16 grids of 2048 x 2048 fit); larger shapes return HP_ERR_INVALID_ARG and
- * launch nothing.  The call works on the device that is current; its first
- * call on each device looks up the array's device address with that device
- * current (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU
- * (other streams, other host threads) race and give wrong results.  Each call
+ * (16 grids of 2048 x 2048 fit), and batch, ny within HP_MAX_BATCH,
+ * HP_MAX_NY like every call; larger shapes return HP_ERR_INVALID_ARG and
+ * launch nothing.  The call works on the device and CUDA context that are
+ * current.  The array's device address belongs to the context that loaded
+ * the library's kernels: the first call in each context (the device's
+ * primary context, again after a cudaDeviceReset, or a context the caller
+ * made current through the driver API) looks it up with that context current
+ * (cudaGetSymbolAddress) and caches it per context, so make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and give wrong
+ * results.  Each call
  * clears the max words it uses before the reduction and overwrites the
  * partial sums it reads; no cudaMalloc, cudaFree or allocating library
  * routine is called.  u, v, flags, e1_out, einf_out as in hp_div_norms. */

@@ -5,9 +5,10 @@ CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA library in ``paper_2109_09363_gb300`` and never imports it.
 
 The projection itself (mask, divergence, Jacobi to threshold, correction) is
-plain C in ``oracle.c`` (built by :func:`build`); the MultiScale CNN, the
-advection step and the dense direct solve are plain numpy (``cnn.py``,
-``advect.py``, ``dense.py``).  All arithmetic is FP64.
+plain C in ``oracle.c`` (built by :func:`build`); the networks, the advection
+step, the adjoint and the training losses and optimiser are plain numpy
+(``cnn.py``, ``advect.py``, ``adjoint.py``, ``train.py``).  All arithmetic is
+FP64.
 
 Functions that have no independent pin say so in their docstring ("parity
 unpinned"); every other function is pinned by ``tests/test_oracle_*.py``.

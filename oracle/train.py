@@ -3,6 +3,10 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 1. loss_and_grad: the supervised loss with a divergence term (below).
 2. pdnn_loss_and_grad: the physics-driven loss of Sec. 3.2 (Eq. 4).
+3. adam_step: the optimiser (Sec. 3.2 trains with a gradient-descent
+   algorithm; Adam as published by Kingma and Ba, 2015, Algorithm 1).
+4. training_target: the pressure target of a training pair (the plain
+   solver's iterates, reading below).
 
 Reading (the paper trains on the divergence of the corrected field, Sec. 3.2,
 and this build also supervises on pressures from the plain solver); both terms
@@ -92,3 +96,32 @@ def pdnn_loss_and_grad(phi_hat, u_star, v_star, flags, s, weight, norm):
     gu, gv = forward_divergence_adjoint(gd, nx, ny)
     _, _, g_phi0 = AD.project_fixed_adjoint(gu[None], gv[None], None, fl, 0)
     return loss, s * g_phi0[0]
+
+
+def adam_step(theta, m, v, g, t, lr, beta1, beta2, eps):
+    """One Adam update at step t >= 1 (Kingma and Ba, 2015, Algorithm 1), in
+    FP64; returns the new (theta, m, v):
+        m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2
+        m_hat = m / (1 - beta1^t),     v_hat = v / (1 - beta2^t)
+        theta <- theta - lr m_hat / (sqrt(v_hat) + eps)
+    (eps outside the square root, both moments bias-corrected)."""
+    theta, m, v, g = (np.asarray(a, np.float64) for a in (theta, m, v, g))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def training_target(div, flags, n):
+    """Pressure target of a training pair: n masked Jacobi sweeps (Sec. 2.2)
+    from phi_0 = 0 on the right-hand side div, then the mean of phi_n and
+    phi_{n+1} (reading: the mean cancels the period-2 component that plain
+    Jacobi never damps, so the networks do not learn it).  div, flags
+    [B][ny][nx] or [ny][nx]; returns FP64 of the same shape."""
+    div = np.asarray(div, np.float64)
+    phi = np.zeros_like(div)
+    for _ in range(n):
+        phi = oracle.jacobi_sweep(phi, div, flags).reshape(div.shape)
+    nxt = oracle.jacobi_sweep(phi, div, flags).reshape(div.shape)
+    return 0.5 * (phi + nxt)

@@ -24,6 +24,10 @@ class HprojError(RuntimeError):
     pass
 
 
+HP_ERR_TIMEOUT = 7
+HP_WARN_CNN_NONFINITE = 100
+
+
 class hp_shape(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("ny", ctypes.c_int32), ("nx", ctypes.c_int32)]
 
@@ -53,6 +57,7 @@ _SIGS = {
     "hp_project": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.POINTER(hp_project_params),
                                   _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "hp_jacobi_sweeps": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, _P, hp_shape, _P]),
+    "hp_jacobi_target": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, hp_shape, _P]),
     "hp_div_norms_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
     "hp_resident_clusters": (ctypes.c_int32, [_P, hp_shape]),
     "hp_advect_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, hp_shape,
@@ -68,6 +73,11 @@ _SIGS = {
     "hp_trainer_gradient": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_float, _P, _P, _P]),
     "hp_trainer_step": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_void_p, _P, _P]),
     "hp_trainer_sync_params": (ctypes.c_int, [_P]),
+    "hp_trainer_get_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "hp_trainer_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "hp_trainer_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "hp_cnn_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "hp_cnn_load": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_char_p, hp_shape, ctypes.c_int]),
     "hp_trainer_pdnn_gradient": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_int32, _P,
                                                 _P, _P]),
     "hp_trainer_pdnn_step": (ctypes.c_int, [_P, _P, _P, _P, hp_shape, ctypes.c_int32,
@@ -81,6 +91,7 @@ _SIGS = {
     "hp_cnn_destroy": (None, [_P]),
     "hp_cnn_set_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "hp_cnn_check": (ctypes.c_int, [_P]),
+    "hp_cnn_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "hp_cnn_get_params": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "hp_cnn_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape, _P]),
     "hp_project_hybrid": (ctypes.c_int, [_P, _P, _P, _P, _P, hp_shape,
@@ -304,6 +315,20 @@ def hp_jacobi_sweeps(ctx: Context, phi_in, div, flags, n: int, phi_out=None, wit
     return (phi_out, e) if with_e else phi_out
 
 
+def hp_jacobi_target(ctx: Context, div, flags, n: int, target_out=None, stream=None):
+    """Training target of the plain solver: n Jacobi sweeps from zero on the
+    right-hand side div, then the mean of phi_n and phi_{n+1}."""
+    torch = _torch()
+    s = _shape_of_flags(flags)
+    B, ny, nx = flags.shape
+    _check_dtype(div, torch.float32, (B, ny, nx), "div")
+    if target_out is None:
+        target_out = torch.empty_like(div)
+    _check(load_library().hp_jacobi_target(ctx.handle, _ptr(div), _ptr(flags), ctypes.c_int32(n),
+                                           _ptr(target_out), s, _stream(stream)))
+    return target_out
+
+
 @dataclass
 class PlumeParams:
     dt: float = 0.1
@@ -397,19 +422,31 @@ class CNN:
     3.1; forward and hybrid projection only, grid sizes multiples of 16)."""
 
     def __init__(self, batch: int, ny: int, nx: int, device: int | None = None, params=None,
-                 arch: str = "multiscale"):
+                 arch: str = "multiscale", path: str | None = None):
+        """A new network; with `path`, the architecture and parameters of a
+        checkpoint file (hp_cnn_load) instead of `arch` and `params`."""
         torch = _torch()
         lib = load_library()
-        if arch not in CNN_ARCHS:
-            raise ValueError(f"arch must be one of {sorted(CNN_ARCHS)}")
         dev = torch.cuda.current_device() if device is None else device
+        self._h = _P()
+        if path is not None:
+            _check(lib.hp_cnn_load(ctypes.byref(self._h), os.fsencode(path),
+                                   hp_shape(batch, ny, nx), dev))
+            code = int(lib.hp_cnn_get_arch(self._h))
+            arch = next(a for a, c in CNN_ARCHS.items() if c == code)
+        elif arch not in CNN_ARCHS:
+            raise ValueError(f"arch must be one of {sorted(CNN_ARCHS)}")
+        else:
+            _check(lib.hp_cnn_create_arch(ctypes.byref(self._h), CNN_ARCHS[arch],
+                                          hp_shape(batch, ny, nx), dev))
         self.arch = arch
         self.n_params = CNN.param_count(arch)
-        self._h = _P()
-        _check(lib.hp_cnn_create_arch(ctypes.byref(self._h), CNN_ARCHS[arch],
-                                      hp_shape(batch, ny, nx), dev))
         if params is not None:
             self.set_params(params)
+
+    def save(self, path: str):
+        """Checkpoint file of the architecture and parameters (hp_cnn_save)."""
+        _check(load_library().hp_cnn_save(self._h, os.fsencode(path)))
 
     @staticmethod
     def param_count(arch: str = "multiscale") -> int:
@@ -429,8 +466,19 @@ class CNN:
 
     def check(self):
         """Raise if a tensor-core wait of this network's kernels timed out
-        since the last check (synchronises the device)."""
-        _check(load_library().hp_cnn_check(self._h))
+        since the last check (synchronises the device).  Returns
+        HP_WARN_CNN_NONFINITE (100) when a hybrid projection replaced a
+        non-finite guess by zero since the last check, else 0."""
+        rc = load_library().hp_cnn_check(self._h)
+        if rc == HP_WARN_CNN_NONFINITE:
+            return rc
+        _check(rc)
+        return 0
+
+    def set_wait_limit(self, polls: int):
+        """Polls of each bounded pipeline wait of the tensor-core kernels
+        (0 = the compiled limit)."""
+        _check(load_library().hp_cnn_set_wait_limit(self._h, int(polls)))
 
     def get_params(self):
         import numpy as np
@@ -516,6 +564,26 @@ class Trainer:
 
     def sync_params(self):
         _check(load_library().hp_trainer_sync_params(self._h))
+
+    def state(self):
+        """(masters, m, v, step): the FP32 masters, the Adam moments (numpy,
+        network parameter order) and the number of Adam steps taken."""
+        import numpy as np
+        n = self.cnn.n_params
+        w, m, v = (np.empty(n, dtype=np.float32) for _ in range(3))
+        step = ctypes.c_int64(0)
+        _check(load_library().hp_trainer_get_state(
+            self._h, w.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p),
+            v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(step)))
+        return w, m, v, int(step.value)
+
+    def save(self, path: str):
+        """Checkpoint file of the masters, Adam moments and step (hp_trainer_save)."""
+        _check(load_library().hp_trainer_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Restore masters, moments and step from a checkpoint (hp_trainer_load)."""
+        _check(load_library().hp_trainer_load(self._h, os.fsencode(path)))
 
     def close(self):
         if self._h:

@@ -26,12 +26,29 @@ hp_status check_launch()
     return HP_OK;
 }
 
-bool shape_ok(hp_shape s) { return s.batch > 0 && s.ny > 0 && s.nx > 0; }
+// Kernels cover rows and grids with one CUDA grid dimension each (at most
+// 65535 blocks), some with one row or grid more than the shape.
+bool shape_ok(hp_shape s)
+{
+    return s.batch > 0 && s.ny > 0 && s.nx > 0 && s.batch <= HP_MAX_BATCH && s.ny <= HP_MAX_NY;
+}
 
 static bool fits(const hp_ctx* c, hp_shape s)
 {
     return shape_ok(s) && s.batch <= c->max_shape.batch && s.ny <= c->max_shape.ny &&
            s.nx <= c->max_shape.nx;
+}
+
+bool project_args_ok(const hp_ctx* c, const float* u, const float* v, const uint8_t* flags,
+                     hp_shape s, const hp_project_params* prm, const int32_t* iters_out,
+                     const double* e_hist, int32_t hist_len)
+{
+    if (!c || !u || !v || !flags || !prm || !iters_out || !fits(c, s)) return false;
+    if (prm->max_iters < 0 || prm->fixed_iters < 0 || prm->temporal_block < 0 ||
+        prm->temporal_block > kMaxBlock || !(prm->threshold >= 0.0) || !(prm->dt > 0.0f) ||
+        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 4)
+        return false;
+    return (e_hist == nullptr) == (hist_len <= 0);
 }
 
 template <typename T>
@@ -62,6 +79,9 @@ const char* hp_status_string(hp_status s)
     case HP_ERR_OOM: return "out of device memory";
     case HP_ERR_UNSUPPORTED: return "unsupported";
     case HP_ERR_TIMEOUT: return "a tensor-core wait timed out";
+    case HP_ERR_IO: return "checkpoint file error";
+    case HP_WARN_CNN_NONFINITE:
+        return "warning: a network guess was not finite; its grids started from zero";
     }
     return "unknown status";
 }
@@ -180,12 +200,8 @@ hp_status hp_project(hp_ctx* c, float* u, float* v, const uint8_t* flags, hp_sha
                      int32_t* iters_out, double* e1_out, double* einf_out, uint8_t* conv_out,
                      double* e_hist, int32_t hist_len, void* stream)
 {
-    if (!c || !u || !v || !flags || !prm || !iters_out || !fits(c, s)) return HP_ERR_INVALID_ARG;
-    if (prm->max_iters < 0 || prm->fixed_iters < 0 || prm->temporal_block < 0 ||
-        prm->temporal_block > kMaxBlock || !(prm->threshold >= 0.0) || !(prm->dt > 0.0f) ||
-        !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 4)
+    if (!project_args_ok(c, u, v, flags, s, prm, iters_out, e_hist, hist_len))
         return HP_ERR_INVALID_ARG;
-    if ((e_hist == nullptr) != (hist_len <= 0)) return HP_ERR_INVALID_ARG;
     return project_impl(c, u, v, flags, s, prm, phi0, p_out, iters_out, e1_out, einf_out, conv_out,
                         e_hist, hist_len, (cudaStream_t)stream, nullptr);
 }
@@ -210,6 +226,33 @@ hp_status hp_jacobi_sweeps(hp_ctx* c, const float* phi_in, const float* div,
     prm.use_graph = 1;
     return project_impl(c, nullptr, nullptr, flags, s, &prm, phi_in, nullptr, nullptr, nullptr,
                         nullptr, nullptr, e_out, e_out ? n : 0, st, phi_out);
+}
+
+hp_status hp_jacobi_target(hp_ctx* c, const float* div, const uint8_t* flags, int32_t n,
+                           float* target_out, hp_shape s, void* stream)
+{
+    if (!c || !div || !flags || !target_out || n < 0 || !fits(c, s)) return HP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cells = (size_t)s.batch * s.ny * s.nx;
+    hp_status rc = launch_mask(flags, c->mask, s, st);
+    if (rc != HP_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->div, div, cells * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    // phi_n into the checkpoint workspace (free once the sweeps are done)
+    if (n > 0) {
+        hp_project_params prm = {};
+        prm.fixed_iters = n;
+        prm.dt = 1.0f;
+        prm.rho0 = 1.0f;
+        prm.use_graph = 1;
+        rc = project_impl(c, nullptr, nullptr, flags, s, &prm, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, nullptr, nullptr, 0, st, c->ckpt);
+        if (rc != HP_OK) return rc;
+    } else {
+        e = cudaMemsetAsync(c->ckpt, 0, cells * sizeof(float), st);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    }
+    return launch_mean_sweep(c->ckpt, c->div, c->mask, target_out, s, st);
 }
 
 }  // extern "C"

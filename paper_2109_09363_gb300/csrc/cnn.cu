@@ -486,15 +486,33 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// phi_0 = s * out on cells with an open face, 0 elsewhere.
+// bad[b] = 1 when the guess s * out of grid b is not finite on some cell
+// with an open face (bad cleared beforehand; every writer stores 1).
+__global__ void guess_check_kernel(const float* __restrict__ out, const float* __restrict__ s,
+                                   const uint8_t* __restrict__ mask, int32_t* __restrict__ bad,
+                                   int B, size_t cells)
+{
+    const size_t n = (size_t)B * cells;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(q / cells);
+        if ((mask[q] & 15u) && !isfinite(s[b] * out[q])) bad[b] = 1;
+    }
+}
+
+// phi_0 = s * out on cells with an open face, 0 elsewhere; the whole grid 0
+// when its guess is not finite (the Jacobi sweeps then start from zero, the
+// plain method).  The first cell of such a grid raises bit 1 of *err.
 __global__ void phi0_kernel(const float* __restrict__ out, const float* __restrict__ s,
-                            const uint8_t* __restrict__ mask, float* __restrict__ phi, int B,
-                            size_t cells)
+                            const uint8_t* __restrict__ mask, const int32_t* __restrict__ bad,
+                            float* __restrict__ phi, int* err, int B, size_t cells)
 {
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= (size_t)B * cells) return;
     const int b = (int)(q / cells);
-    phi[q] = (mask[q] & 15u) ? s[b] * out[q] : 0.0f;
+    const bool fallback = bad[b] != 0;
+    phi[q] = ((mask[q] & 15u) && !fallback) ? s[b] * out[q] : 0.0f;
+    if (fallback && q == (size_t)b * cells) atomicOr(err, 2);
 }
 
 }  // namespace
@@ -528,8 +546,21 @@ struct hp_cnn {
     float* s;
     double* s_part;                // [B][kScaleCtas] partial sums of |div|
     unsigned long long* s_cnt;     // [B][kScaleCtas] fluid-cell counts
+    // device status word: bit 0 a tensor-core wait gave up, bit 1 a grid's
+    // guess was not finite and the hybrid projection started it from zero
     int* err;
+    uint32_t wait_limit;  // polls per bounded pipeline wait (0 = compiled limit)
+    int32_t* guess_bad;   // [max batch] per grid: the network's guess is not finite
 };
+
+// a batch this network's workspace holds, with sides its architecture takes
+static bool cnn_shape_ok(const hp_cnn* c, hp_shape s)
+{
+    return shape_ok(s) && s.ny % size_multiple(c->arch) == 0 &&
+           s.nx % size_multiple(c->arch) == 0 && s.batch <= c->max_shape.batch &&
+           (size_t)s.batch * s.ny * s.nx <=
+               (size_t)c->max_shape.batch * c->max_shape.ny * c->max_shape.nx;
+}
 
 static hp_status launch_scale(hp_cnn* c, const float* div, const uint8_t* flags, int B,
                               size_t cells, cudaStream_t st)
@@ -561,7 +592,7 @@ static hp_status launch_first(hp_cnn* c, int k, const BranchIn& in, int cin, flo
     if (rc != HP_OK) return rc;
     if (tc)
         return launch_conv3x3_tc(c->x16, c->wtc_first[k], bias, y, B, H, W, 16, 32, 1, c->err,
-                                 c->num_sms, st);
+                                 c->num_sms, st, c->wait_limit);
     const long P2 = (long)B * H * ((W + 1) / 2);
     const int blocks2 = (int)((P2 + 127) / 128 < cap ? (P2 + 127) / 128 : cap);
     if (cin == 2)
@@ -580,7 +611,7 @@ static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const flo
 {
     if (W >= conv_tc_min_width())
         return launch_conv3x3_tc_out1(x, c->wtc_last[k], c->btc_last[k], y, B, H, W, c->err,
-                                      c->num_sms, st);
+                                      c->num_sms, st, c->wait_limit);
     const long T = (long)B * ((H + kLastRows - 1) / kLastRows) * W;
     const long cap = 16L * c->num_sms;
     const int blocks = (int)((T + 127) / 128 < cap ? (T + 127) / 128 : cap);
@@ -602,7 +633,7 @@ static hp_status unet_forward(hp_cnn* c, const float* div, const uint8_t* flags,
     auto conv = [&](const void* x, void* y, int H, int W) {
         if (rc == HP_OK)
             rc = launch_conv3x3_tc(x, c->w[l], c->bias[l], y, B, H, W, sp[l].cin, sp[l].cout,
-                                   sp[l].relu, c->err, c->num_sms, st);
+                                   sp[l].relu, c->err, c->num_sms, st, c->wait_limit);
         ++l;
     };
     // one block row per output row, the row's items across blockIdx.y
@@ -720,6 +751,7 @@ void hp_cnn_destroy(hp_cnn* c)
     cudaFree(c->s_cnt);
     cudaFree(c->s);
     cudaFree(c->err);
+    cudaFree(c->guess_bad);
     delete c;
 }
 
@@ -767,7 +799,8 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
           cudaMalloc((void**)&c->s_cnt,
                      (size_t)mx.batch * kScaleCtas * sizeof(unsigned long long)) == cudaSuccess &&
           cudaMalloc((void**)&c->s, mx.batch * sizeof(float)) == cudaSuccess &&
-          cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
+          cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess &&
+          cudaMalloc((void**)&c->guess_bad, mx.batch * sizeof(int32_t)) == cudaSuccess;
     for (int k = 0; k < c->br.n && okm; ++k)
         okm = cudaMalloc((void**)&c->out[k],
                          px / ((size_t)c->br.scale[k] * c->br.scale[k]) * 4 + 16) ==
@@ -854,11 +887,7 @@ hp_status hp_cnn_get_params(const hp_cnn* c, float* params, int64_t n)
 hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, float* phi_hat,
                          float* s_out, hp_shape s, void* stream)
 {
-    if (!c || !div || !flags || !shape_ok(s) || s.ny % size_multiple(c->arch) ||
-        s.nx % size_multiple(c->arch) || s.batch > c->max_shape.batch ||
-        (size_t)s.batch * s.ny * s.nx >
-            (size_t)c->max_shape.batch * c->max_shape.ny * c->max_shape.nx)
-        return HP_ERR_INVALID_ARG;
+    if (!c || !div || !flags || !cnn_shape_ok(c, s)) return HP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cells = (size_t)s.ny * s.nx;
     hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
@@ -887,7 +916,7 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
         while (c->spec[l].cout != 1) {
             rc = launch_conv3x3_tc(c->act[cur], c->w[l], c->bias[l], c->act[cur ^ 1], s.batch, H,
                                    W, c->spec[l].cin, c->spec[l].cout, c->spec[l].relu, c->err,
-                                   c->num_sms, st);
+                                   c->num_sms, st, c->wait_limit);
             if (rc != HP_OK) return rc;
             cur ^= 1;
             ++l;
@@ -912,7 +941,10 @@ hp_status hp_project_hybrid(hp_ctx* ctx, hp_cnn* cnn, float* u, float* v, const 
                             int32_t* iters_out, double* e1_out, double* einf_out,
                             uint8_t* conv_out, double* e_hist, int32_t hist_len, void* stream)
 {
-    if (!ctx || !cnn || !u || !v || !flags || !prm || !iters_out) return HP_ERR_INVALID_ARG;
+    // every argument of both halves is checked before anything is launched
+    if (!cnn || !project_args_ok(ctx, u, v, flags, s, prm, iters_out, e_hist, hist_len) ||
+        !cnn_shape_ok(cnn, s))
+        return HP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     // divergence into the context, CNN guess into the second phi buffer
     hp_status rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st);
@@ -920,12 +952,30 @@ hp_status hp_project_hybrid(hp_ctx* ctx, hp_cnn* cnn, float* u, float* v, const 
     float* phi_hat = cnn->out[cnn->br.n - 1];
     rc = hp_cnn_forward(cnn, ctx->div, flags, phi_hat, nullptr, s, stream);
     if (rc != HP_OK) return rc;
+    // a grid whose guess is not finite starts from zero (the network's guess
+    // is always followed and judged by the Jacobi sweeps, Sec. 3.3)
     const size_t cells = (size_t)s.ny * s.nx;
-    phi0_kernel<<<(unsigned)(((size_t)s.batch * cells + 255) / 256), 256, 0, st>>>(
-        phi_hat, cnn->s, ctx->mask, ctx->phi[1], s.batch, cells);
+    cudaError_t e = cudaMemsetAsync(cnn->guess_bad, 0, s.batch * sizeof(int32_t), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    const size_t n = (size_t)s.batch * cells;
+    const size_t cap = (size_t)8 * cnn->num_sms;
+    guess_check_kernel<<<(unsigned)((n + 255) / 256 < cap ? (n + 255) / 256 : cap), 256, 0, st>>>(
+        phi_hat, cnn->s, ctx->mask, cnn->guess_bad, s.batch, cells);
     if ((rc = check_launch()) != HP_OK) return rc;
-    return hp_project(ctx, u, v, flags, s, prm, ctx->phi[1], p_out, iters_out, e1_out, einf_out,
-                      conv_out, e_hist, hist_len, stream);
+    phi0_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(phi_hat, cnn->s, ctx->mask,
+                                                             cnn->guess_bad, ctx->phi[1],
+                                                             cnn->err, s.batch, cells);
+    if ((rc = check_launch()) != HP_OK) return rc;
+    // the mask and divergence of the context are those of this velocity
+    return project_impl(ctx, u, v, flags, s, prm, ctx->phi[1], p_out, iters_out, e1_out,
+                        einf_out, conv_out, e_hist, hist_len, st, nullptr, true);
+}
+
+hp_status hp_cnn_set_wait_limit(hp_cnn* c, uint32_t polls)
+{
+    if (!c) return HP_ERR_INVALID_ARG;
+    c->wait_limit = polls;
+    return HP_OK;
 }
 
 }  // extern "C"
@@ -1845,7 +1895,7 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
         while (sp[l].cout != 1) {
             rc = launch_conv3x3_tc(t->act[l - 1], c->w[l], c->bias[l], t->act[l], s.batch, H, W,
                                    sp[l].cin, sp[l].cout, sp[l].relu, c->err, c->num_sms,
-                                   st);
+                                   st, c->wait_limit);
             if (rc != HP_OK) return rc;
             ++l;
         }
@@ -2029,7 +2079,7 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
         const __nv_bfloat16* x = (const __nv_bfloat16*)t->act[l - 1];
         int grid = 0;
         rc = launch_conv3x3_tc_wgrad(x, gy, t->part, t->part_len, t->partb, t->partb_len, B, H, W,
-                                     ci, co, c->err, c->num_sms, &grid, st);
+                                     ci, co, c->err, c->num_sms, &grid, st, c->wait_limit);
         if (rc != HP_OK) return rc;
         gw = t->grad + layer_offset(sp, l);
         wgrad_reduce_kernel<<<reduce_blocks(ci, co), 256, 0, st>>>(t->part, t->partb, grid, ci, co,
@@ -2039,7 +2089,7 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
         const __nv_bfloat16* act = sp[l - 1].relu ? x : nullptr;
         __nv_bfloat16* gx = gbuf[cur ^ 1];
         rc = launch_conv3x3_tc_dgrad(gy, t->wdg[l], t->zero_bias, act, gx, B, H, W, ci, co,
-                                     c->err, c->num_sms, st);
+                                     c->err, c->num_sms, st, c->wait_limit);
         if (rc != HP_OK) return rc;
         if (ci == 64 && co == 64)
             rc = border_terms<64, 64>(gy, t->wt[l], act, gx, B, H, W, st);
@@ -2249,6 +2299,92 @@ hp_status hp_trainer_sync_params(hp_trainer* t)
     return hp_cnn_check(t->cnn);
 }
 
+hp_status hp_trainer_get_state(hp_trainer* t, float* master, float* m, float* v, int64_t* step)
+{
+    if (!t) return HP_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    const size_t bytes = (size_t)t->param_count * 4;
+    if (e == cudaSuccess && master) e = cudaMemcpy(master, t->master, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && m) e = cudaMemcpy(m, t->m, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v) e = cudaMemcpy(v, t->v, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    if (step) *step = t->step;
+    return HP_OK;
+}
+
+hp_status hp_cnn_save(const hp_cnn* c, const char* path)
+{
+    if (!c || !path) return HP_ERR_INVALID_ARG;
+    CkptData d;
+    d.arch = c->arch;
+    d.w = c->master;
+    return ckpt_write(path, d);
+}
+
+hp_status hp_cnn_load(hp_cnn** out, const char* path, hp_shape mx, int device)
+{
+    if (!out || !path) return HP_ERR_INVALID_ARG;
+    *out = nullptr;
+    CkptData d;
+    hp_status rc = ckpt_read(path, &d);
+    if (rc != HP_OK) return rc;
+    if (!spec_for(d.arch) || (int64_t)d.w.size() != hp_cnn_arch_param_count(d.arch))
+        return HP_ERR_IO;
+    hp_cnn* c = nullptr;
+    if ((rc = hp_cnn_create_arch(&c, d.arch, mx, device)) != HP_OK) return rc;
+    if ((rc = hp_cnn_set_params(c, d.w.data(), (int64_t)d.w.size())) != HP_OK) {
+        hp_cnn_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HP_OK;
+}
+
+hp_status hp_trainer_save(hp_trainer* t, const char* path)
+{
+    if (!t || !path) return HP_ERR_INVALID_ARG;
+    CkptData d;
+    d.arch = t->cnn->arch;
+    d.has_moments = true;
+    d.w.assign((size_t)t->param_count, 0.0f);
+    d.m.assign((size_t)t->param_count, 0.0f);
+    d.v.assign((size_t)t->param_count, 0.0f);
+    int64_t step = 0;
+    hp_status rc = hp_trainer_get_state(t, d.w.data(), d.m.data(), d.v.data(), &step);
+    if (rc != HP_OK) return rc;
+    d.step = step;
+    return ckpt_write(path, d);
+}
+
+hp_status hp_trainer_load(hp_trainer* t, const char* path)
+{
+    if (!t || !path) return HP_ERR_INVALID_ARG;
+    CkptData d;
+    hp_status rc = ckpt_read(path, &d);
+    if (rc != HP_OK) return rc;
+    if (d.arch != t->cnn->arch || (int64_t)d.w.size() != t->param_count) return HP_ERR_IO;
+    const size_t bytes = (size_t)t->param_count * 4;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(t->master, d.w.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (d.has_moments) {
+            e = cudaMemcpy(t->m, d.m.data(), bytes, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(t->v, d.v.data(), bytes, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemset(t->m, 0, bytes);
+            if (e == cudaSuccess) e = cudaMemset(t->v, 0, bytes);
+        }
+    }
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    t->step = d.has_moments ? (int)d.step : 0;
+    memcpy(t->cnn->master.data(), d.w.data(), bytes);
+    // the network's BF16 weights from the restored masters, as after a step
+    if ((rc = trainer_pack(t, nullptr)) != HP_OK) return rc;
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
+    return HP_OK;
+}
+
 hp_status hp_cnn_check(hp_cnn* c)
 {
     if (!c) return HP_ERR_INVALID_ARG;
@@ -2257,7 +2393,7 @@ hp_status hp_cnn_check(hp_cnn* c)
     if (e == cudaSuccess) e = cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && flag) e = cudaMemset(c->err, 0, sizeof(int));
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
-    return flag ? HP_ERR_TIMEOUT : HP_OK;
+    return (flag & 1) ? HP_ERR_TIMEOUT : (flag & 2) ? HP_WARN_CNN_NONFINITE : HP_OK;
 }
 
 }  // extern "C"

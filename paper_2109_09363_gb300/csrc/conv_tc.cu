@@ -208,8 +208,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         }
         // a timed-out wait (never expected) ends the kernel on every thread
         ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;
+        if (!ok) {
+            // the MMAs must land before their accumulator is freed: wait once
+            // more (bounded) before leaving
+            mbar_wait(mbar_a, phase);
+            __syncthreads();
+            break;
+        }
         phase ^= 1u;
-        if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // epilogue: this thread's row = TMEM lane tid
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    if (!ok && err) atomicExch(err, 1);
+    if (!ok && err) atomicOr(err, 1);
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -325,10 +331,13 @@ struct WsSmem {
     static_assert(CIN % 16 == 0, "K steps of 16 channels");
 };
 
+// A bounded wait on an mbarrier phase: gives up after `limit` polls, or
+// earlier once another role of the CTA has raised abort_flag.
 __device__ __forceinline__ bool mbar_wait_ws(uint32_t mbar, uint32_t parity,
-                                             const volatile int* abort_flag)
+                                             const volatile int* abort_flag,
+                                             uint32_t limit = kWsSpinLimit)
 {
-    for (uint32_t it = 0; it < kWsSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -474,9 +483,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     conv3x3_tc_ws_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
                          const float* __restrict__ bias, void* __restrict__ yout, int H, int W,
                          int segs, int nbands, int band, int items, int relu, int* err,
-                         const uint4* __restrict__ act = nullptr)
+                         uint32_t wait_limit, const uint4* __restrict__ act = nullptr)
 {
     using S = WsSmem<CIN, COUT, OUT1>;
+    // polls of each pipeline wait before it gives up (0: the compiled limit);
+    // the final waits for issued MMAs always use the compiled limit
+    const uint32_t lim = wait_limit ? wait_limit : kWsSpinLimit;
     __nv_bfloat16* __restrict__ y = reinterpret_cast<__nv_bfloat16*>(yout);
     constexpr int NCH = S::kChunks;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -559,7 +571,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             const bool interior = it.x0 >= 1 && it.x0 + kHaloPx - 1 <= W;
             for (int r = it.y0 - 1; r <= it.y1 && ok; ++r, ++jg) {
                 const uint32_t s = jg % kWsSlots, u = jg / kWsSlots;
-                if (u > 0) ok = mbar_wait_ws(smem_u32(&empty_bar[s]), (u - 1) & 1u, &s_abort);
+                // the lanes take one decision (no lane runs ahead of the others)
+                if (u > 0)
+                    ok = __all_sync(0xffffffffu,
+                                    mbar_wait_ws(smem_u32(&empty_bar[s]), (u - 1) & 1u, &s_abort,
+                                                 lim));
                 if (!ok) break;
                 const int sr = min(max(r, 0), H - 1);
                 const uint32_t dst = smem_u32(ring + s * S::kSlotBytes) + (uint32_t)(ch * kHaloPx * 16);
@@ -602,14 +618,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 const WsItem it = ws_item(wi, segs, nbands, band, H);
                 for (int r = it.y0 - 1; r <= it.y1 && ok; ++r, ++jg) {
                     ok = mbar_wait_ws(smem_u32(&full_bar[jg % kWsSlots]),
-                                      (jg / kWsSlots) & 1u, &s_abort);
+                                      (jg / kWsSlots) & 1u, &s_abort, lim);
                     // dy blocks whose output row r + 1 - dy lies in [y0, y1)
                     const int dlo = max(0, r + 2 - it.y1), dhi = min(2, r + 1 - it.y0);
                     const int nd = dhi - dlo + 1;
                     const uint32_t o_first = og + (uint32_t)(r + 1 - dlo - it.y0);
                     if (ok && dlo == 0 && o_first >= (uint32_t)kAccSlots)
                         ok = mbar_wait_ws(smem_u32(&free_bar[o_first % kAccSlots]),
-                                          ((o_first / kAccSlots) - 1) & 1u, &s_abort);
+                                          ((o_first / kAccSlots) - 1) & 1u, &s_abort, lim);
                     if (!ok) break;
                     // plan: outputs o_first, o_first - 1, ... in at most two
                     // runs of adjacent TMEM column blocks (split at the wrap)
@@ -714,7 +730,9 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                         }
                     }
                 }
-                ok = mbar_wait_ws(smem_u32(&outf_bar[sl]), (og / kAccSlots) & 1u, &s_abort);
+                // one decision per warp: the tcgen05.ld below is warp-collective
+                ok = __all_sync(0xffffffffu, mbar_wait_ws(smem_u32(&outf_bar[sl]),
+                                                          (og / kAccSlots) & 1u, &s_abort, lim));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t taddr =
@@ -790,7 +808,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     }
     if (!ok) {
         s_abort = 1;
-        if (err) atomicExch(err, 1);
+        if (err) atomicOr(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -807,7 +825,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
 template <int CIN, int COUT, bool OUT1, bool DGRAD = false>
 hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, int B, int H,
                     int W, int relu, int* err, int nsm, cudaStream_t st,
-                    const void* act = nullptr)
+                    const void* act = nullptr, uint32_t wait_limit = 0)
 {
     using R = WsSmem<CIN, COUT, OUT1>;
     static bool rattr = false;
@@ -828,7 +846,7 @@ hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, in
     const int grid = items < nsm ? (int)items : nsm;
     conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD><<<grid, kWsThreads, R::kBytes, st>>>(
         (const uint4*)x, (const uint4*)w, bias, y, H, W, segs, nbands, band, (int)items, relu,
-        err, (const uint4*)act);
+        err, wait_limit, (const uint4*)act);
     return check_launch();
 }
 
@@ -881,9 +899,13 @@ template <int CI, int CO>
 __global__ void __launch_bounds__(kWgThreads, 1)
     conv3x3_wgrad_tc_kernel(const uint4* __restrict__ x, const uint4* __restrict__ gy,
                             float* __restrict__ part, float* __restrict__ partb, int H, int W,
-                            int segs, int nbands, int band, int items, int* err)
+                            int segs, int nbands, int band, int items, int* err,
+                            uint32_t wait_limit)
 {
     using S = WgSmem<CI, CO>;
+    // polls of each pipeline wait before it gives up (0: the compiled limit);
+    // the waits for the issued MMAs (done_bar) always use the compiled limit
+    const uint32_t lim = wait_limit ? wait_limit : kWsSpinLimit;
     constexpr int NX = S::kChunksX, NG = S::kChunksG;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ring = smem;
@@ -965,7 +987,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         };
         auto load_x = [&](int b, int x0, int r, uint32_t pos) -> bool {
             const uint32_t sl = pos % S::kSlots, u = pos / S::kSlots;
-            if (u > 0 && !mbar_wait_ws(smem_u32(&xempty[sl]), (u - 1) & 1u, &s_abort))
+            if (u > 0 && !mbar_wait_ws(smem_u32(&xempty[sl]), (u - 1) & 1u, &s_abort, lim))
                 return false;
             const int sr = min(max(r, 0), H - 1);
             const uint4* src_row = x + ((size_t)b * H + sr) * W * NX;
@@ -986,7 +1008,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         };
         auto load_g = [&](int b, int x0, int r, uint32_t cnt) -> bool {
             const uint32_t bb = cnt & 1u, u = cnt >> 1;
-            if (u > 0 && !mbar_wait_ws(smem_u32(&gempty[bb]), (u - 1) & 1u, &s_abort))
+            if (u > 0 && !mbar_wait_ws(smem_u32(&gempty[bb]), (u - 1) & 1u, &s_abort, lim))
                 return false;
             const uint4* src_row = gy + ((size_t)b * H + r) * W * NG;
             const uint32_t dst = smem_u32(gbuf + bb * S::kGBytes);
@@ -1039,9 +1061,10 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 for (uint32_t pos = p0 + (i == 0 ? 0u : (uint32_t)i + 2u);
                      pos <= p0 + (uint32_t)i + 2u && ok; ++pos)
                     ok = mbar_wait_ws(smem_u32(&xfull[pos % S::kSlots]),
-                                      (pos / S::kSlots) & 1u, &s_abort);
+                                      (pos / S::kSlots) & 1u, &s_abort, lim);
                 if (ok)
-                    ok = mbar_wait_ws(smem_u32(&gfull[gcnt & 1u]), (gcnt >> 1) & 1u, &s_abort);
+                    ok = mbar_wait_ws(smem_u32(&gfull[gcnt & 1u]), (gcnt >> 1) & 1u, &s_abort,
+                                      lim);
                 if (!ok) break;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1111,7 +1134,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     }
     if (!ok) {
         s_abort = 1;
-        if (err) atomicExch(err, 1);
+        if (err) atomicOr(err, 1);
     }
     if (warp < 4) {
 #pragma unroll
@@ -1137,7 +1160,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
 template <int CI, int CO>
 hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part_len,
                          float* partb, size_t partb_len, int B, int H, int W, int* err, int nsm,
-                         int* grid_out, cudaStream_t st)
+                         int* grid_out, cudaStream_t st, uint32_t wait_limit)
 {
     using S = WgSmem<CI, CO>;
     static bool attr = false;
@@ -1158,17 +1181,18 @@ hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part
     if ((size_t)grid * 9 * CO * CI > part_len || (size_t)grid * CO > partb_len)
         return HP_ERR_INVALID_ARG;
     conv3x3_wgrad_tc_kernel<CI, CO><<<grid, kWgThreads, S::kBytes, st>>>(
-        (const uint4*)x, (const uint4*)gy, part, partb, H, W, segs, nbands, band, (int)items, err);
+        (const uint4*)x, (const uint4*)gy, part, partb, H, W, segs, nbands, band, (int)items, err,
+        wait_limit);
     *grid_out = grid;
     return check_launch();
 }
 
 template <int CIN, int COUT>
 hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y, int B, int H,
-                        int W, int relu, int* err, int nsm, cudaStream_t st)
+                        int W, int relu, int* err, int nsm, cudaStream_t st, uint32_t wait_limit)
 {
     if (W >= kWsMinWidth) return launch_ws<CIN, COUT, false>(x, w, bias, y, B, H, W, relu, err,
-                                                            nsm, st);
+                                                            nsm, st, nullptr, wait_limit);
     using S = ConvSmem<CIN, COUT>;
     static bool attr = false;
     if (!attr) {
@@ -1189,16 +1213,17 @@ hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y
 
 hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
                             int H, int W, int cin, int cout, int relu, int* err, int nsm,
-                            cudaStream_t st)
+                            cudaStream_t st, uint32_t wait_limit)
 {
-    if (cin == 32 && cout == 32) return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st);
-    if (cin == 32 && cout == 64) return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st);
-    if (cin == 64 && cout == 32) return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st);
-    if (cin == 64 && cout == 64) return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+    if (cin == 32 && cout == 32) return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 32 && cout == 64) return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 64 && cout == 32) return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 64 && cout == 64) return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
     // first layer of a branch, input padded to 16 channels (warp-specialised
     // kernel only; narrower images take the CUDA-core layer)
     if (cin == 16 && cout == 32 && W >= kWsMinWidth)
-        return launch_ws<16, 32, false>(x, w, bias, y, B, H, W, relu, err, nsm, st);
+        return launch_ws<16, 32, false>(x, w, bias, y, B, H, W, relu, err, nsm, st, nullptr,
+                                        wait_limit);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1212,17 +1237,22 @@ int conv_tc_min_width() { return kWsMinWidth; }
 // conv_tc_min_width() up.
 hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* zero_bias,
                                   const void* act, void* gx, int B, int H, int W, int cin,
-                                  int cout, int* err, int nsm, cudaStream_t st)
+                                  int cout, int* err, int nsm, cudaStream_t st,
+                                  uint32_t wait_limit)
 {
     if (W < kWsMinWidth) return HP_ERR_UNSUPPORTED;
     if (cin == 64 && cout == 64)
-        return launch_ws<64, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+        return launch_ws<64, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act,
+                                               wait_limit);
     if (cin == 32 && cout == 64)
-        return launch_ws<64, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+        return launch_ws<64, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act,
+                                               wait_limit);
     if (cin == 64 && cout == 32)
-        return launch_ws<32, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+        return launch_ws<32, 64, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act,
+                                               wait_limit);
     if (cin == 32 && cout == 32)
-        return launch_ws<32, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act);
+        return launch_ws<32, 32, false, true>(gy, wdg, zero_bias, gx, B, H, W, 0, err, nsm, st, act,
+                                               wait_limit);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1231,20 +1261,21 @@ hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* 
 // per CTA); x BF16 [P][cin], gy BF16 [P][cout].
 hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, size_t part_len,
                                   float* partb, size_t partb_len, int B, int H, int W, int cin,
-                                  int cout, int* err, int nsm, int* grid_out, cudaStream_t st)
+                                  int cout, int* err, int nsm, int* grid_out, cudaStream_t st,
+                                  uint32_t wait_limit)
 {
     if (cin == 64 && cout == 64)
         return launch_wgrad_t<64, 64>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
-                                      grid_out, st);
+                                      grid_out, st, wait_limit);
     if (cin == 32 && cout == 64)
         return launch_wgrad_t<32, 64>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
-                                      grid_out, st);
+                                      grid_out, st, wait_limit);
     if (cin == 64 && cout == 32)
         return launch_wgrad_t<64, 32>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
-                                      grid_out, st);
+                                      grid_out, st, wait_limit);
     if (cin == 32 && cout == 32)
         return launch_wgrad_t<32, 32>(x, gy, part, part_len, partb, partb_len, B, H, W, err, nsm,
-                                      grid_out, st);
+                                      grid_out, st, wait_limit);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1253,10 +1284,11 @@ hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, si
 // [B][H][W] without rounding; HP_ERR_UNSUPPORTED below the width the
 // warp-specialised kernel serves.
 hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias, float* y,
-                                 int B, int H, int W, int* err, int nsm, cudaStream_t st)
+                                 int B, int H, int W, int* err, int nsm, cudaStream_t st,
+                                 uint32_t wait_limit)
 {
     if (W < kWsMinWidth) return HP_ERR_UNSUPPORTED;
-    return launch_ws<32, 16, true>(x, w, bias, y, B, H, W, 0, err, nsm, st);
+    return launch_ws<32, 16, true>(x, w, bias, y, B, H, W, 0, err, nsm, st, nullptr, wait_limit);
 }
 
 }  // namespace hp

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/hproj.h"
 
 namespace hp {
@@ -61,6 +63,17 @@ struct SweepArgs {
     int32_t mode;                // 0 = loop block, 1 = replay
     unsigned long long cond;     // CUDA-graph conditional handle (0 = none)
 };
+
+// Contents of a network checkpoint file (checkpoint.cu).
+struct CkptData {
+    int32_t arch = -1;
+    int64_t step = 0;
+    bool has_moments = false;
+    std::vector<float> w, m, v;
+};
+hp_status ckpt_write(const char* path, const CkptData& d);
+// HP_ERR_IO for a missing, short, foreign or corrupted file
+hp_status ckpt_read(const char* path, CkptData* d);
 
 }  // namespace hp
 
@@ -184,27 +197,39 @@ bool shape_ok(hp_shape s);
 hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
                           float* div, hp_shape s, cudaStream_t st);
 hp_status launch_mask(const uint8_t* flags, uint8_t* mask, hp_shape s, cudaStream_t st);
+// out = (phi + J(phi)) / 2, J one masked Jacobi sweep on the right-hand side div
+hp_status launch_mean_sweep(const float* phi, const float* div, const uint8_t* mask, float* out,
+                            hp_shape s, cudaStream_t st);
 hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
                            double* partial, int nblk_cap, GridState* gs, double* e1,
                            double* einf, hp_shape s, cudaStream_t st);
 hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t* flags,
                                    double* partial, uint32_t* einf_bits, size_t stride,
                                    double* e1, double* einf, hp_shape s, cudaStream_t st);
+// have_div: ctx->mask and ctx->div already hold this velocity's open faces
+// and divergence (no second pass over u, v)
 hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp_shape s,
                        const hp_project_params* prm, const float* phi0, float* p_out,
                        int32_t* iters_out, double* e1_out, double* einf_out,
                        uint8_t* conv_out, double* e_hist, int32_t hist_len, cudaStream_t st,
-                       float* phi_copy_out);
+                       float* phi_copy_out, bool have_div = false);
+// the argument checks of hp_project
+bool project_args_ok(const hp_ctx* c, const float* u, const float* v, const uint8_t* flags,
+                     hp_shape s, const hp_project_params* prm, const int32_t* iters_out,
+                     const double* e_hist, int32_t hist_len);
 
 int ctas_per_grid(int ny, int nx, int T);
+// wait_limit: polls of each bounded pipeline wait of the tensor-core kernels
+// before it gives up and raises bit 0 of *err (0 = the compiled limit)
 hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
                             int H, int W, int cin, int cout, int relu, int* err, int nsm,
-                            cudaStream_t st);
+                            cudaStream_t st, uint32_t wait_limit = 0);
 // narrowest image the warp-specialised convolution (and the tensor-core first
 // and last layers of a branch) serves
 int conv_tc_min_width();
 hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias, float* y,
-                                 int B, int H, int W, int* err, int nsm, cudaStream_t st);
+                                 int B, int H, int W, int* err, int nsm, cudaStream_t st,
+                                 uint32_t wait_limit = 0);
 // backward of a tensor-core layer cin -> cout (32 or 64 channels each):
 // input gradient (BF16, zero-padded transposed convolution with the flipped
 // weights wdg BF16 [9][cin][cout], ReLU derivative of act applied; the
@@ -213,10 +238,12 @@ hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias
 // g < *grid_out
 hp_status launch_conv3x3_tc_dgrad(const void* gy, const void* wdg, const float* zero_bias,
                                   const void* act, void* gx, int B, int H, int W, int cin,
-                                  int cout, int* err, int nsm, cudaStream_t st);
+                                  int cout, int* err, int nsm, cudaStream_t st,
+                                  uint32_t wait_limit = 0);
 hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, size_t part_len,
                                   float* partb, size_t partb_len, int B, int H, int W, int cin,
-                                  int cout, int* err, int nsm, int* grid_out, cudaStream_t st);
+                                  int cout, int* err, int nsm, int* grid_out, cudaStream_t st,
+                                  uint32_t wait_limit = 0);
 hp_status launch_advect(const float* u, const float* v, const float* rho, const uint8_t* flags,
                         float* u_out, float* v_out, float* rho_out, hp_shape s,
                         const hp_plume_params& p, cudaStream_t st);

@@ -97,6 +97,38 @@ __global__ void init_phi_kernel(const float* __restrict__ phi0, const uint8_t* _
     out[q] = (phi0 && (mask[q] & 15u)) ? phi0[q] : 0.0f;
 }
 
+// One more masked Jacobi sweep of phi (the same cell update as every sweep
+// kernel, so phi' is bit-identical to theirs) and the mean of phi and phi'
+// (the target of the training pairs: the mean cancels the period-2
+// component that plain Jacobi never damps).
+__global__ void mean_sweep_kernel(const float* __restrict__ phi, const float* __restrict__ div,
+                                  const uint8_t* __restrict__ mask, float* __restrict__ out,
+                                  int ny, int nx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const size_t gb = (size_t)blockIdx.z * ny * nx;
+    if (i >= nx) return;
+    const size_t c = gb + (size_t)j * nx + i;
+    const float* ph = phi + gb;
+    const float pc = phi[c];
+    const float pw = i > 0 ? ph[(size_t)j * nx + i - 1] : 0.0f;
+    const float pe = i < nx - 1 ? ph[(size_t)j * nx + i + 1] : 0.0f;
+    const float pn = j > 0 ? ph[(size_t)(j - 1) * nx + i] : 0.0f;
+    const float ps = j < ny - 1 ? ph[(size_t)(j + 1) * nx + i] : 0.0f;
+    float res;
+    const float nxt = cell_update(pc, pw, pe, pn, ps, make_const(div[c], mask[c]), res);
+    out[c] = __fmul_rn(0.5f, __fadd_rn(pc, nxt));
+}
+
+hp_status launch_mean_sweep(const float* phi, const float* div, const uint8_t* mask, float* out,
+                            hp_shape s, cudaStream_t st)
+{
+    dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
+    mean_sweep_kernel<<<grd, blk, 0, st>>>(phi, div, mask, out, s.ny, s.nx);
+    return check_launch();
+}
+
 // ----------------------------------------------------- blocked Jacobi sweeps
 
 template <int H>
@@ -639,8 +671,11 @@ hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
     uint32_t* einf_bits = &gs[0].einf_bits;
     const size_t stride = sizeof(GridState) / sizeof(uint32_t);
     clear_einf_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(einf_bits, stride, s.batch);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
     div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, nullptr, partial, einf_bits, stride, s.ny,
                                           s.nx);
+    if ((rc = check_launch()) != HP_OK) return rc;
     norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
         partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
         1.0 / ((double)s.nx * (double)s.ny));
@@ -656,8 +691,11 @@ hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
     const int nblk = grd.x * grd.y;
     clear_einf_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(einf_bits, stride, s.batch);
+    hp_status rc = check_launch();
+    if (rc != HP_OK) return rc;
     div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, nullptr, partial, einf_bits, stride, s.ny,
                                           s.nx);
+    if ((rc = check_launch()) != HP_OK) return rc;
     norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
         partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
         1.0 / ((double)s.nx * (double)s.ny));
@@ -862,11 +900,12 @@ static int pick_T(const hp_project_params* prm)
 hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp_shape s,
                        const hp_project_params* prm, const float* phi0, float* p_out,
                        int32_t* iters_out, double* e1_out, double* einf_out, uint8_t* conv_out,
-                       double* e_hist, int32_t hist_len, cudaStream_t st, float* phi_copy_out)
+                       double* e_hist, int32_t hist_len, cudaStream_t st, float* phi_copy_out,
+                       bool have_div)
 {
     const size_t cells = (size_t)s.batch * s.ny * s.nx;
     hp_status rc = HP_OK;
-    if (u) {
+    if (u && !have_div) {
         // without a velocity the caller has prepared ctx->mask and ctx->div
         rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st);
         if (rc != HP_OK) return rc;

@@ -54,7 +54,6 @@ def generate_pairs(count: int, n: int, seed0: int = 0, sweeps: int = 40000,
     dev = device or torch.device("cuda", torch.cuda.current_device())
     divs, fls, tgts = [], [], []
     ctx = hp.Context(min(chunk, count), n, n, device=dev.index)
-    prm = hp.ProjectParams(fixed_iters=sweeps)
     for c0 in range(0, count, chunk):
         B = min(chunk, count - c0)
         u, v, fl = W.training_case(B, n, seed0 + c0)
@@ -62,10 +61,7 @@ def generate_pairs(count: int, n: int, seed0: int = 0, sweeps: int = 40000,
         vd = torch.from_numpy(v.astype(np.float32)).to(dev)
         fd = torch.from_numpy(fl).to(dev)
         div = hp.hp_divergence(ud, vd, fd)
-        out = hp.hp_project(ctx, ud, vd, fd, prm)
-        phi = out["p"].clone()
-        nxt = hp.hp_jacobi_sweeps(ctx, phi, div, fd, 1)
-        divs.append(div); fls.append(fd); tgts.append(0.5 * (phi + nxt))
+        divs.append(div); fls.append(fd); tgts.append(hp.hp_jacobi_target(ctx, div, fd, sweeps))
     ctx.close()
     return torch.cat(divs), torch.cat(fls), torch.cat(tgts)
 

@@ -1,0 +1,238 @@
+"""The boundary's behaviour around the hot path, through the C ABI:
+
+- the hybrid projection's fallback for a non-finite network guess (the
+  Jacobi sweeps always follow and judge the guess, Sec. 3.3): the grid starts
+  from zero, the others keep their guesses, hp_cnn_check warns;
+- a bounded tensor-core wait made to run out (hp_cnn_set_wait_limit): the
+  kernels return, hp_cnn_check reports HP_ERR_TIMEOUT, and the network works
+  again afterwards with the same output bits;
+- checkpoint files of networks and trainers (save -> load is bit-exact);
+- the Adam update of the trainer against the FP64 oracle's Adam;
+- the training-pair target hp_jacobi_target against the oracle's sweeps."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn as C
+from oracle import train as TR
+from paper_2109_09363_gb300 import training as T
+from paper_2109_09363_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+hp = pytest.importorskip("paper_2109_09363_gb300")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_09363_gb300 import build
+    build.build()
+    oracle.build()
+    return torch.device("cuda:0")
+
+
+def to_dev(dev, *arrays):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrays]
+
+
+# ------------------------------------------------------ non-finite guesses
+
+def test_nonfinite_guess_falls_back_to_zero_for_that_grid_only(dev):
+    # grid 0 has no obstacle, grid 1 has a disc; a huge weight on the flags
+    # channel of the first layer of every branch makes the guess of grid 1
+    # overflow to Inf/NaN while grid 0 (flags channel 0 everywhere) keeps a
+    # finite guess
+    B, n = 2, 64
+    u, v = [], []
+    for b in range(B):
+        ub, vb = W.vortex_velocity(n, n, 70 + b, n_vortices=8, width=(2.0, 8.0))
+        u.append(ub); v.append(vb)
+    u = np.stack(u).astype(np.float32)
+    v = np.stack(v).astype(np.float32)
+    fl = np.zeros((B, n, n), np.uint8)
+    yy, xx = np.mgrid[:n, :n]
+    fl[1][(yy - 30) ** 2 + (xx - 34) ** 2 < 100] = 1
+    params = C.init_params(seed=5)
+    first = {0, 5, 12}  # first layer of the 1/4, 1/2 and full-resolution branch
+    params = [(w.copy(), b) for w, b in params]
+    for l in first:
+        params[l][0][:, 1] = 1e38
+    cnn = hp.CNN(B, n, n, params=C.flatten(params))
+    ctx = hp.Context(B, n, n)
+    prm = hp.ProjectParams(threshold=1e-3, max_iters=3000)
+    ud, vd, fd = to_dev(dev, u, v, fl)
+    div = hp.hp_divergence(ud, vd, fd)
+    phi_hat, s = hp.hp_cnn_forward(cnn, div, fd)
+    torch.cuda.synchronize()
+    ph = phi_hat.cpu().numpy()
+    assert np.isfinite(ph[0]).all() and not np.isfinite(ph[1][fl[1] == 0]).all()
+    assert cnn.check() == 0
+    out = hp.hp_project_hybrid(ctx, cnn, ud, vd, fd, prm)
+    torch.cuda.synchronize()
+    assert cnn.check() == hp.HP_WARN_CNN_NONFINITE
+    assert cnn.check() == 0  # the warning is cleared by reading it
+    # reference: grid 0 from its network guess, grid 1 from zero
+    phi0 = (phi_hat * s[:, None, None]).contiguous()
+    phi0[1] = 0.0
+    ur, vr, _ = to_dev(dev, u, v, fl)
+    ref = hp.hp_project(ctx, ur, vr, fd, prm, phi0=phi0)
+    torch.cuda.synchronize()
+    assert np.array_equal(out["iters"].cpu().numpy(), ref["iters"].cpu().numpy())
+    assert torch.equal(ud, ur) and torch.equal(vd, vr)
+    assert torch.equal(out["p"], ref["p"])
+    # and grid 1 is the plain projection: the oracle from zero, run to the
+    # GPU's sweep count
+    k1 = int(out["iters"][1])
+    o = oracle.project(u[1:].astype(np.float64), v[1:].astype(np.float64), fl[1:], 0.0, 0,
+                       fixed_iters=k1)
+    umax = np.abs(o["u"]).max()
+    assert np.abs(ud[1:].cpu().numpy() - o["u"]).max() <= 1e-5 * umax
+
+
+# --------------------------------------------------- bounded wait runs out
+
+def test_a_wait_that_runs_out_returns_timeout_and_the_network_recovers(dev):
+    B, n = 1, 128
+    u, v, fl = W.training_case(B, n, 300)
+    ud, vd, fd = to_dev(dev, u.astype(np.float32), v.astype(np.float32), fl)
+    div = hp.hp_divergence(ud, vd, fd)
+    cnn = hp.CNN(B, n, n, params=T.init_params(seed=2))
+    ref, _ = hp.hp_cnn_forward(cnn, div, fd)
+    ref = ref.clone()
+    torch.cuda.synchronize()
+    assert cnn.check() == 0
+    # one poll per pipeline wait: the copies and MMAs of a 128-wide image
+    # cannot all complete within it, so the waits give up
+    cnn.set_wait_limit(1)
+    hp.hp_cnn_forward(cnn, div, fd)
+    with pytest.raises(hp.HprojError, match="status 7"):
+        cnn.check()
+    # the device and the network are usable again, with the same output bits
+    cnn.set_wait_limit(0)
+    again, _ = hp.hp_cnn_forward(cnn, div, fd)
+    torch.cuda.synchronize()
+    assert cnn.check() == 0
+    assert torch.equal(again, ref)
+
+
+# ---------------------------------------------------------- checkpoints
+
+def test_network_checkpoint_round_trip_is_bit_exact(dev, tmp_path):
+    B, n = 2, 64
+    u, v, fl = W.training_case(B, n, 310)
+    ud, vd, fd = to_dev(dev, u.astype(np.float32), v.astype(np.float32), fl)
+    div = hp.hp_divergence(ud, vd, fd)
+    for arch in ("multiscale", "monoscale"):
+        a = hp.CNN(B, n, n, params=T.init_params(seed=3, arch=arch), arch=arch)
+        path = str(tmp_path / f"{arch}.hpcnn")
+        a.save(path)
+        b = hp.CNN(B, n, n, path=path)
+        assert b.arch == arch
+        assert np.array_equal(b.get_params(), a.get_params())
+        ya, _ = hp.hp_cnn_forward(a, div, fd)
+        ya = ya.clone()
+        yb, _ = hp.hp_cnn_forward(b, div, fd)
+        torch.cuda.synchronize()
+        assert torch.equal(ya, yb)
+    # a corrupted file is refused
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 1
+    bad = str(tmp_path / "bad.hpcnn")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(hp.HprojError, match="status 8"):
+        hp.CNN(B, n, n, path=bad)
+
+
+def test_trainer_checkpoint_resumes_bit_exactly(dev, tmp_path):
+    B, n = 4, 64
+    data = T.generate_pairs(8, n, seed0=320, sweeps=400, chunk=8, device=dev)
+    div, fl, tgt = data
+    batches = [(div[i:i + B].contiguous(), fl[i:i + B].contiguous(), tgt[i:i + B].contiguous())
+               for i in (0, 4, 0)]
+    cnn_a = hp.CNN(B, n, n, params=T.init_params(seed=4))
+    tr_a = hp.Trainer(cnn_a, B, n, n)
+    for d, f, t in batches[:2]:
+        tr_a.step(d, f, t, lr=1e-3, lambda_div=1.0)
+    path = str(tmp_path / "trainer.hpcnn")
+    tr_a.save(path)
+    cnn_b = hp.CNN(B, n, n, params=T.init_params(seed=99))
+    tr_b = hp.Trainer(cnn_b, B, n, n)
+    tr_b.load(path)
+    wa, ma, va, sa = tr_a.state()
+    wb, mb, vb, sb = tr_b.state()
+    assert sa == sb == 2
+    assert np.array_equal(wa, wb) and np.array_equal(ma, mb) and np.array_equal(va, vb)
+    d, f, t = batches[2]
+    la = tr_a.step(d, f, t, lr=1e-3, lambda_div=1.0).clone()
+    lb = tr_b.step(d, f, t, lr=1e-3, lambda_div=1.0).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(la, lb)
+    wa, ma, va, sa = tr_a.state()
+    wb, mb, vb, sb = tr_b.state()
+    assert sa == sb == 3
+    assert np.array_equal(wa, wb) and np.array_equal(ma, mb) and np.array_equal(va, vb)
+    # the network object of the loaded trainer forwards with the new weights
+    tr_b.sync_params()
+    tr_a.sync_params()
+    assert np.array_equal(cnn_a.get_params(), cnn_b.get_params())
+
+
+# ----------------------------------------------------------------- Adam
+
+@pytest.mark.parametrize("arch", ["multiscale", "smallscale"])
+def test_adam_matches_the_oracle_update(dev, arch):
+    # three steps; the oracle takes the GPU's own gradient of each step (the
+    # gradient itself is checked against the oracle backward elsewhere) and
+    # applies Adam in FP64 to FP64 copies of the state
+    B, n = 2, 64
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    data = T.generate_pairs(6, n, seed0=330, sweeps=300, chunk=6, device=dev)
+    cnn = hp.CNN(B, n, n, params=T.init_params(seed=6, arch=arch), arch=arch)
+    tr = hp.Trainer(cnn, B, n, n)
+    w0, m0, v0, st0 = tr.state()
+    assert st0 == 0 and not m0.any() and not v0.any()
+    th = w0.astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for k in range(3):
+        d, f, t = (x[2 * k:2 * k + 2].contiguous() for x in data)
+        g, _ = tr.gradient(d, f, t, lambda_div=1.0)
+        tr.step(d, f, t, lr=lr, beta1=b1, beta2=b2, eps=eps, lambda_div=1.0)
+        th, m, v = TR.adam_step(th, m, v, g.cpu().numpy().astype(np.float64), k + 1, lr, b1,
+                                b2, eps)
+    w, mg, vg, st = tr.state()
+    assert st == 3
+    assert np.abs(mg - m).max() <= 1e-5 * np.abs(m).max()
+    assert np.abs(vg - v).max() <= 1e-5 * np.abs(v).max()
+    # FP32 rounding of the stored weight plus a tolerance far below what a
+    # wrong bias correction or epsilon placement changes (of order lr)
+    err = np.abs(w - th) - 4e-7 * np.abs(th)
+    assert err.max() <= 1e-4 * lr, err.max()
+    assert np.abs(w - w0).max() > 0.5 * lr  # the weights did move
+
+
+# ----------------------------------------------------- training target
+
+@pytest.mark.parametrize("B,ny,nx,n", [(3, 64, 64, 200), (2, 67, 130, 57), (1, 1, 1, 3),
+                                       (2, 40, 24, 0)])
+def test_jacobi_target_matches_the_oracle(dev, B, ny, nx, n):
+    rng = np.random.default_rng(ny * nx + n)
+    fl = (rng.random((B, ny, nx)) < 0.1).astype(np.uint8)
+    div = (rng.standard_normal((B, ny, nx)) * (fl == 0)).astype(np.float32)
+    ctx = hp.Context(B, ny, nx)
+    dd, fd = to_dev(dev, div, fl)
+    got = hp.hp_jacobi_target(ctx, dd, fd, n)
+    # the iterates are those of hp_jacobi_sweeps
+    if n > 0:
+        phi = hp.hp_jacobi_sweeps(ctx, torch.zeros_like(dd), dd, fd, n)
+        nxt = hp.hp_jacobi_sweeps(ctx, phi, dd, fd, 1)
+        torch.cuda.synchronize()
+        mean = ((phi.cpu().numpy().astype(np.float64) + nxt.cpu().numpy()) * 0.5)
+        assert np.abs(got.cpu().numpy() - mean).max() <= 1e-6 * max(np.abs(mean).max(), 1e-30)
+    exp = TR.training_target(div.astype(np.float64), fl, n)
+    g = got.cpu().numpy()
+    scale = max(np.abs(exp).max(), 1e-30)
+    assert np.abs(g - exp).max() <= 1e-5 * scale

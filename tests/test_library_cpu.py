@@ -157,3 +157,62 @@ def test_paper_plume_geometry():
     assert (rows.min() + rows.max() + 1) / 2 == pytest.approx(cy, abs=1.0)
     fl0, _ = W.paper_plume_geometry(n, cylinder=False)
     assert fl0.sum() == 0
+
+
+def test_shapes_beyond_the_launch_limits_are_rejected_on_the_host(lib):
+    # batch and ny each map to one CUDA grid dimension (65535 blocks); larger
+    # shapes return HP_ERR_INVALID_ARG before any CUDA call, so stand-in
+    # pointers that are never dereferenced suffice here
+    fake = ctypes.c_void_p(256)
+    for shape in [(1, 70000, 1), (70000, 1, 1), (1, 65535, 4), (65535, 4, 4)]:
+        s = hp.hp_shape(*shape)
+        assert lib.hp_divergence(fake, fake, fake, fake, s, None) == 1
+        assert lib.hp_face_mask(fake, fake, s, None) == 1
+        assert lib.hp_div_norms_noalloc(fake, fake, fake, fake, fake, s, None) == 1
+        pp = hp.PlumeParams().c()
+        assert lib.hp_advect_step(fake, fake, fake, fake, fake, fake, fake, s,
+                                  ctypes.byref(pp), None) == 1
+
+
+def _checkpoint_bytes(arch, n, step=0, moments=False, seed=0):
+    """A checkpoint in the layout include/hproj.h documents, written here."""
+    import struct
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    body = struct.pack("<8sIiqqII", b"HPCNNCK1", 1, arch, n, step, int(moments), 0)
+    body += rng.standard_normal(n).astype("<f4").tobytes()
+    if moments:
+        body += rng.standard_normal(2 * n).astype("<f4").tobytes()
+    h = 1469598103934665603
+    for byte in body:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return body + struct.pack("<Q", h)
+
+
+def test_checkpoint_reader_errors_need_no_gpu(lib, tmp_path):
+    out = ctypes.c_void_p()
+    s = hp.hp_shape(1, 64, 64)
+    assert lib.hp_cnn_load(ctypes.byref(out), str(tmp_path / "missing").encode(), s, 0) == 8
+    assert not out.value
+    assert lib.hp_cnn_load(None, b"x", s, 0) == 1
+    assert lib.hp_trainer_load(None, b"x") == 1
+    assert lib.hp_status_string(8) == b"checkpoint file error"
+    n = int(lib.hp_cnn_arch_param_count(1))
+    good = _checkpoint_bytes(1, n)
+    for bad in (good[:-1], good[:50], good + b"\0",
+                good[:60] + bytes([good[60] ^ 4]) + good[61:],      # a parameter bit
+                _checkpoint_bytes(1, n - 1),                        # wrong count
+                _checkpoint_bytes(7, n)):                           # unknown arch
+        p = tmp_path / "bad.hpcnn"
+        p.write_bytes(bad)
+        assert lib.hp_cnn_load(ctypes.byref(out), str(p).encode(), s, 0) == 8
+        assert not out.value
+    # the documented layout passes the reader: creating the network is the
+    # first step that needs a GPU (HP_ERR_CUDA here, without one)
+    p = tmp_path / "good.hpcnn"
+    p.write_bytes(good)
+    rc = lib.hp_cnn_load(ctypes.byref(out), str(p).encode(), s, 0)
+    torch = pytest.importorskip("torch")
+    assert rc == (0 if torch.cuda.is_available() else 2)
+    if rc == 0:
+        lib.hp_cnn_destroy(out)

@@ -75,3 +75,85 @@ def test_adjoint_is_the_dense_jacobian_transpose(k):
     exp = J.T @ g
     # including phi_0 on cells without an open face, whose column is zero
     assert np.allclose(got, exp, atol=1e-10)
+
+
+def _dense_divergence(fl):
+    """D (cells x faces, u faces then v faces in row-major order) of the
+    open-face divergence, and the open-face indicator; built here by loops."""
+    ny, nx = fl.shape
+    nu = ny * (nx + 1)
+    D = np.zeros((ny * nx, nu + (ny + 1) * nx))
+    open_f = np.zeros(D.shape[1], bool)
+    for j in range(ny):
+        for i in range(1, nx):
+            if fl[j, i - 1] == 0 and fl[j, i] == 0:
+                f = j * (nx + 1) + i
+                D[j * nx + i - 1, f] += 1.0   # east face of the left cell
+                D[j * nx + i, f] -= 1.0       # west face of the right cell
+                open_f[f] = True
+    for j in range(1, ny):
+        for i in range(nx):
+            if fl[j - 1, i] == 0 and fl[j, i] == 0:
+                f = nu + j * nx + i
+                D[(j - 1) * nx + i, f] += 1.0
+                D[j * nx + i, f] -= 1.0
+                open_f[f] = True
+    return D, open_f
+
+
+def _components(fl):
+    """Connected fluid components (4-neighbour flood fill) as cell lists."""
+    ny, nx = fl.shape
+    seen = np.zeros_like(fl, bool)
+    comps = []
+    for j0 in range(ny):
+        for i0 in range(nx):
+            if fl[j0, i0] or seen[j0, i0]:
+                continue
+            stack, cells = [(j0, i0)], []
+            seen[j0, i0] = True
+            while stack:
+                j, i = stack.pop()
+                cells.append((j, i))
+                for jj, ii in ((j, i - 1), (j, i + 1), (j - 1, i), (j + 1, i)):
+                    if 0 <= jj < ny and 0 <= ii < nx and not fl[jj, ii] and not seen[jj, ii]:
+                        seen[jj, ii] = True
+                        stack.append((jj, ii))
+            comps.append(cells)
+    return comps
+
+
+def test_adjoint_tends_to_the_dense_solve_gradient():
+    # As k grows, u = Z u* - G phi_k tends to the exact projection
+    # (I - D^T (D D^T)^+ D) Z u* (G = -D^T on open faces), so dL/du* tends to
+    # Z (I - D^T (D D^T)^+ D) g (the dense solve below).  Plain Jacobi never damps the checkerboard
+    # mode (eigenvalue -1 on the bipartite grid graph), so g is taken
+    # orthogonal to D^T s of every component's checkerboard s: the adjoint
+    # sweeps then do not excite that mode and converge.
+    n = 8
+    fl = np.zeros((n, n), np.uint8)
+    fl[2:4, 3:5] = 1
+    fl[6, 1] = 1
+    D, open_f = _dense_divergence(fl)
+    g = np.random.default_rng(12).standard_normal(D.shape[1])
+    for cells in _components(fl):
+        s = np.zeros(n * n)
+        for j, i in cells:
+            s[j * n + i] = (-1.0) ** (i + j)
+        a = D.T @ s
+        if a @ a > 0:
+            g -= (g @ a) / (a @ a) * a
+    # minimum-norm least-squares solve of the singular Poisson system
+    phi = np.linalg.lstsq(D @ D.T, D @ g, rcond=None)[0]
+    assert np.abs(D @ D.T @ phi - D @ g).max() < 1e-12
+    exact = open_f * (g - D.T @ phi)
+    nu = n * (n + 1)
+    gu = g[:nu].reshape(1, n, n + 1)
+    gv = g[nu:].reshape(1, n + 1, n)
+    err = []
+    for k in (50, 400, 3000):
+        gus, gvs, _ = AD.project_fixed_adjoint(gu, gv, None, fl, k)
+        got = np.concatenate([gus.ravel(), gvs.ravel()])
+        err.append(np.abs(got - exact).max())
+    assert err[0] > err[1] > err[2]          # converging with k
+    assert err[2] < 1e-10 * np.abs(exact).max()

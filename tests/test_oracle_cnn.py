@@ -346,3 +346,27 @@ def test_maxpool_backward_routes_to_the_first_maximum():
     gx = C.maxpool2_backward(x, g)
     # ties go to the first maximum in the order (0, 0), (0, 1), (1, 0), (1, 1)
     assert np.array_equal(gx, [[[0.0, 5.0, 7.0, 0.0], [0.0, 0.0, 0.0, 0.0]]])
+
+
+def test_round_bf16_matches_an_independent_conversion():
+    # torch's CPU float32 -> bfloat16 conversion (round to nearest even) on
+    # random values across the exponent range, exact ties, subnormals and
+    # values at the top of the range (which round to infinity)
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    rand = (rng.standard_normal(20000) * np.exp2(rng.integers(-130, 127, 20000))).astype(np.float32)
+    base = rng.integers(0, 1 << 15, 4000).astype(np.uint32) << 16
+    ties = (base | 0x8000).view(np.float32)            # exactly half way
+    above = (base | 0x8001).view(np.float32)
+    below = (base | 0x7FFF).view(np.float32)
+    sub = (rng.integers(1, 1 << 23, 2000).astype(np.uint32)).view(np.float32)
+    top = np.array([3.3895314e38, 3.3961776e38, 3.4028235e38, -3.4028235e38, 0.0, -0.0,
+                    np.float32(1.0) + np.float32(2 ** -8)], np.float32)
+    x = np.concatenate([rand, ties, -ties, above, below, sub, -sub, top]).astype(np.float32)
+    x = x[np.isfinite(x)]
+    exp = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    got = C.round_bf16(x)
+    assert np.array_equal(np.isinf(got), np.isinf(exp))
+    fin = np.isfinite(exp)
+    assert np.array_equal(got[fin], exp[fin])
+    assert np.array_equal(np.signbit(got), np.signbit(exp))

@@ -51,9 +51,49 @@ def test_noalloc_norms_match_context_norms_on_consecutive_calls(dev):
             assert np.allclose(einf_out.cpu().numpy(), einf_ref.cpu().numpy(), rtol=RTOL, atol=0)
 
 
-@pytest.mark.parametrize("B,ny,nx", [(16385, 1, 1), (1, 262145, 1)])
+def test_noalloc_allocates_no_device_memory(dev):
+    # after a first call (which sets up the scratch address of this context),
+    # two calls with preallocated outputs leave the device's free memory as
+    # it was: neither the library nor torch allocates
+    B, ny, nx = 4, 130, 300
+    u, v, fl = (t.to(dev) for t in fields(B, ny, nx, 5))
+    e1_out = torch.empty(B, dtype=torch.float64, device=dev)
+    einf_out = torch.empty(B, dtype=torch.float64, device=dev)
+    hp.hp_div_norms_noalloc(u, v, fl, e1_out, einf_out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(2):
+        hp.hp_div_norms_noalloc(u, v, fl, e1_out, einf_out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert free1 == free0
+    assert stats1 == stats0
+
+
+def test_noalloc_at_its_largest_shape(dev):
+    # 16 x 2048 x 2048 uses every partial-sum slot of the scratch array
+    B, ny, nx = 16, 2048, 2048
+    assert B * ny * ((nx + 255) // 256) == 262144
+    g = torch.Generator(device=dev).manual_seed(11)
+    u = torch.randn((B, ny, nx + 1), generator=g, device=dev)
+    v = torch.randn((B, ny + 1, nx), generator=g, device=dev)
+    fl = (torch.rand((B, ny, nx), generator=g, device=dev) < 0.15).to(torch.uint8)
+    ctx = hp.Context(B, ny, nx)
+    e1_ref, einf_ref = hp.hp_div_norms(ctx, u, v, fl)
+    for _ in range(2):
+        e1, einf = hp.hp_div_norms_noalloc(u, v, fl)
+        torch.cuda.synchronize()
+        assert np.allclose(e1.cpu().numpy(), e1_ref.cpu().numpy(), rtol=RTOL, atol=0)
+        assert np.allclose(einf.cpu().numpy(), einf_ref.cpu().numpy(), rtol=RTOL, atol=0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("B,ny,nx", [(16385, 1, 1), (1, 262145, 1), (1, 70000, 1)])
 def test_noalloc_rejects_shapes_beyond_its_scratch(dev, B, ny, nx):
-    # more grids than max words, or more 256-cell blocks than partial sums
+    # more grids than max words, more 256-cell blocks than partial sums, or
+    # more rows than one CUDA grid dimension covers
     u = torch.zeros((B, ny, nx + 1), dtype=torch.float32, device=dev)
     v = torch.zeros((B, ny + 1, nx), dtype=torch.float32, device=dev)
     fl = torch.zeros((B, ny, nx), dtype=torch.uint8, device=dev)
