@@ -45,8 +45,8 @@ TRAIN_SWEEPS = 40000
 # levels n .. n/16 weighted by 1, 1/4, .., 1/256
 CNN_MACS_PER_PIXEL = {"multiscale": 190422, "smallscale": 60822, "monoscale": 222048,
                       "unet": 68000}
-NETWORKS = ("multiscale", "smallscale", "monoscale")  # trained in the hybrid arm
-FORWARD_NETWORKS = NETWORKS + ("unet",)  # forward only (no trainer for the Unet)
+NETWORKS = ("multiscale", "smallscale", "monoscale", "unet")  # trained in the hybrid arm
+FORWARD_NETWORKS = NETWORKS
 # held-out grids of the training distribution for the in-distribution comparison
 IN_DIST_GRIDS, IN_DIST_SEED = 256, 100000
 T_BLOCK = 8

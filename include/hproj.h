@@ -280,8 +280,8 @@ typedef struct hp_cnn hp_cnn;
  * n/16 32 -> 64 -> 64 -> 32, decoder levels on [bilinear x 2 of the coarser
  * features, skip features] 64 -> 64 -> 32, the last 64 -> 32 -> 32 and a
  * 1 x 1 32 -> 1 (its weights [1][32][1][1] in params); ReLU after all but
- * the last two; 388,545 parameters; grid sizes multiples of 16.  Forward and
- * hybrid projection only: hp_trainer_create returns HP_ERR_UNSUPPORTED. */
+ * the last two; 388,545 parameters; grid sizes multiples of 16 (also for its
+ * trainer). */
 typedef enum {
     HP_CNN_MULTISCALE = 0,
     HP_CNN_SMALLSCALE = 1,
@@ -344,7 +344,7 @@ hp_status hp_project_hybrid(hp_ctx *ctx, hp_cnn *cnn, float *u, float *v, const 
                             uint8_t *converged_out, double *e_hist, int32_t hist_len,
                             void *stream);
 
-/* Training of the MultiScale CNN (Sec. 3.2 trains the networks with a
+/* Training of the CNNs (Sec. 3.2 trains the networks with a
  * gradient-descent algorithm): FP32 master weights on the device, Adam,
  * BF16 weights of the hp_cnn refreshed after every step.  Loss per grid,
  * averaged over the batch, with t = target / s (target = the scaled pressure
@@ -358,8 +358,11 @@ typedef struct {
     float lr, beta1, beta2, eps;
     float lambda_div;
 } hp_train_params;
-/* max_shape may not exceed the network's own (HP_ERR_INVALID_ARG); a Unet has
- * no trainer (HP_ERR_UNSUPPORTED).  *trainer is NULL on every error. */
+/* Every architecture trains (the Unet's backward routes each pooled gradient
+ * to the first maximum of its 2 x 2 window, in the order (0, 0), (0, 1),
+ * (1, 0), (1, 1)).  max_shape may not exceed the network's own, and its sides
+ * are multiples of 4 (16 for the Unet) (HP_ERR_INVALID_ARG).  *trainer is
+ * NULL on every error. */
 hp_status hp_trainer_create(hp_trainer **trainer, hp_cnn *cnn, hp_shape max_shape);
 void hp_trainer_destroy(hp_trainer *trainer);
 /* Loss (double [1], device, may be NULL) and its gradient w.r.t. every

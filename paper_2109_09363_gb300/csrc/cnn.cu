@@ -619,12 +619,24 @@ static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const flo
     return check_launch();
 }
 
+// What a trainer keeps of a Unet forward: every layer's output, the inputs
+// that are not a layer output (the max-pooled skip features of levels 1-4,
+// the concatenated decoder inputs of levels 0-3) and the FP32 first-layer
+// input.
+struct UnetKeep {
+    void* act[kLayersUnet];
+    __nv_bfloat16* pooled[5];  // [lev], lev = 1..4: input of layer 2 lev
+    __nv_bfloat16* cat[4];     // [lev]: input of the first decoder layer of level lev
+    float* xin0;
+};
+
 // The Unet's forward: its 20 layers in order on the stream (tensor-core
 // convolutions from a width of 32 pixels, the gather kernel or CUDA cores
 // below), skip features kept per level, decoder inputs built by
-// up_concat_kernel.  Activations ping-pong between act[0] and act[1].
+// up_concat_kernel.  Activations ping-pong between act[0] and act[1], or with
+// `keep` go to the trainer's buffers.
 static hp_status unet_forward(hp_cnn* c, const float* div, const uint8_t* flags, float* phi_hat,
-                              hp_shape s, cudaStream_t st)
+                              hp_shape s, cudaStream_t st, const UnetKeep* keep = nullptr)
 {
     const LayerSpec* sp = c->spec;
     const int B = s.batch;
@@ -653,42 +665,59 @@ static hp_status unet_forward(hp_cnn* c, const float* div, const uint8_t* flags,
     };
     __nv_bfloat16* a = c->act[0];
     __nv_bfloat16* b = c->act[1];
+    // the output buffer of layer `layer`: the trainer's, else the given one
+    auto out = [&](int layer, __nv_bfloat16* pp) {
+        return keep ? (__nv_bfloat16*)keep->act[layer] : pp;
+    };
+    __nv_bfloat16* skip[4];
     // encoder level 0: [div/s, flags] -> 32 -> 32
     BranchIn in = {div, flags, c->s, nullptr, s.ny, s.nx, 1};
-    rc = launch_first(c, 0, in, sp[0].cin, nullptr, (const float*)c->w[0], c->bias[0], a, B, s.ny,
-                      s.nx, st);
+    __nv_bfloat16* x = out(0, a);
+    rc = launch_first(c, 0, in, sp[0].cin, keep ? keep->xin0 : nullptr, (const float*)c->w[0],
+                      c->bias[0], x, B, s.ny, s.nx, st);
     l = 1;
-    conv(a, c->skip[0], s.ny, s.nx);
+    skip[0] = out(1, c->skip[0]);
+    conv(x, skip[0], s.ny, s.nx);
     // levels 1-3: max pooling, 32 -> 64 -> 32
     for (int lev = 1; lev < 4; ++lev) {
         const int H = s.ny >> lev, W = s.nx >> lev;
-        pool(c->skip[lev - 1], a, 2 * H, 2 * W);
-        conv(a, b, H, W);
-        conv(b, c->skip[lev], H, W);
+        __nv_bfloat16* pin = keep ? keep->pooled[lev] : a;
+        pool(skip[lev - 1], pin, 2 * H, 2 * W);
+        __nv_bfloat16* y = out(l, b);
+        conv(pin, y, H, W);
+        skip[lev] = out(l, c->skip[lev]);
+        conv(y, skip[lev], H, W);
     }
-    // bottom: 32 -> 64 -> 64 -> 32, the result in b
+    // bottom: 32 -> 64 -> 64 -> 32
+    __nv_bfloat16* cur;
     {
         const int H = s.ny >> 4, W = s.nx >> 4;
-        pool(c->skip[3], a, 2 * H, 2 * W);
-        conv(a, b, H, W);
-        conv(b, a, H, W);
-        conv(a, b, H, W);
+        __nv_bfloat16* pin = keep ? keep->pooled[4] : a;
+        pool(skip[3], pin, 2 * H, 2 * W);
+        __nv_bfloat16* y1 = out(l, b);
+        conv(pin, y1, H, W);
+        __nv_bfloat16* y2 = out(l, a);
+        conv(y1, y2, H, W);
+        cur = out(l, b);
+        conv(y2, cur, H, W);
     }
-    // decoder: [up(coarser), skip] -> two convolutions; the result ends in cur
-    __nv_bfloat16* cur = b;
+    // decoder: [up(coarser), skip] -> two convolutions
     __nv_bfloat16* other = a;
     for (int lev = 3; lev >= 0; --lev) {
         const int H = s.ny >> lev, W = s.nx >> lev;
-        up_concat(cur, c->skip[lev], other, H, W);
-        conv(other, cur, H, W);
-        conv(cur, other, H, W);
-        __nv_bfloat16* t = cur;
-        cur = other;
-        other = t;
+        __nv_bfloat16* catb = keep ? keep->cat[lev] : other;
+        up_concat(cur, skip[lev], catb, H, W);
+        __nv_bfloat16* y1 = out(l, cur);
+        conv(catb, y1, H, W);
+        __nv_bfloat16* y2 = out(l, other);
+        conv(y1, y2, H, W);
+        other = y1;
+        cur = y2;
     }
     if (rc != HP_OK) return rc;
     // the 1 x 1 output convolution 32 -> 1 (FP32)
-    return launch_last(c, 0, cur, (const float*)c->w[l], c->bias[l], phi_hat, B, s.ny, s.nx, st);
+    float* o = keep ? (float*)keep->act[l] : phi_hat;
+    return launch_last(c, 0, cur, (const float*)c->w[l], c->bias[l], o, B, s.ny, s.nx, st);
 }
 
 // tensor-core copies of the first and last layer of every branch
@@ -1712,15 +1741,18 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
 // the forward kernels (BF16-rounded) and the FP32 [9][co][ci] copy for dgrad
 // and, for the tensor-core layers, the BF16 weights of the input-gradient
 // convolution: flipped taps, input and output swapped, wdg[8 - t][ci][co]
+// A 1 x 1 layer (ks = 1, masters [co][ci] + bias) is packed as a 3 x 3 whose
+// outer taps are zero.
 __global__ void pack_layer_kernel(const float* __restrict__ master, int ci, int co, int kind,
-                                  void* __restrict__ wfwd, float* __restrict__ bias,
+                                  int ks, void* __restrict__ wfwd, float* __restrict__ bias,
                                   float* __restrict__ wt, __nv_bfloat16* __restrict__ wdg)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int nw = 9 * ci * co;
     if (q < nw) {
         const int t = q % 9, i = (q / 9) % ci, o = q / (9 * ci);
-        const __nv_bfloat16 h = __float2bfloat16_rn(master[q]);
+        const float mv = ks == 3 ? master[q] : (t == 4 ? master[o * ci + i] : 0.0f);
+        const __nv_bfloat16 h = __float2bfloat16_rn(mv);
         const float f = __bfloat162float(h);
         if (kind == 0) reinterpret_cast<__nv_bfloat16*>(wfwd)[((size_t)t * co + o) * ci + i] = h;
         else if (kind == 1) reinterpret_cast<float*>(wfwd)[((size_t)t * ci + i) * co + o] = f;
@@ -1728,8 +1760,97 @@ __global__ void pack_layer_kernel(const float* __restrict__ master, int ci, int 
         wt[((size_t)t * co + o) * ci + i] = f;
         if (wdg) wdg[((size_t)(8 - t) * ci + i) * co + o] = h;
     } else if (q < nw + co) {
-        bias[q - nw] = master[q];
+        bias[q - nw] = master[(ks == 3 ? nw : ci * co) + (q - nw)];
     }
+}
+
+// ------------------------------------------------------ Unet backward
+
+// Transpose of up_concat_kernel at decoder level L (H x W): channels 32-63 of
+// gcat ([P][64]) are the gradient of the skip features (copied to FP32
+// gskip [P][32]); channels 0-31 go back through the bilinear x 2 up-sampling
+// (each coarse pixel gathers its fine pixels with the up-sampling's weights,
+// in a fixed order) to the coarse features gcoarse [Pc][32], times the ReLU
+// derivative of the coarse activation act (BF16 [Pc][32]).  One warp per
+// coarse pixel and one per fine pixel (the copy); lane = channel.
+template <typename GT, typename OT>
+__global__ void cat_backward_kernel(const GT* __restrict__ gcat, float* __restrict__ gskip,
+                                    OT* __restrict__ gcoarse, const __nv_bfloat16* __restrict__ act,
+                                    int B, int H, int W)
+{
+    const int Hc = H / 2, Wc = W / 2;
+    const long Pc = (long)B * Hc * Wc, Pf = (long)B * H * W;
+    const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid < Pc) {
+        const int b = (int)(wid / ((long)Hc * Wc));
+        const int r = (int)(wid - (long)b * Hc * Wc);
+        const int J = r / Wc, I = r - J * Wc;
+        float sum = 0.0f;
+        for (int fy = 2 * J - 1; fy <= 2 * J + 2; ++fy) {
+            if (fy < 0 || fy >= H) continue;
+            const float wy = up_w(fy, J, Hc);
+            if (wy == 0.0f) continue;
+            for (int fx = 2 * I - 1; fx <= 2 * I + 2; ++fx) {
+                if (fx < 0 || fx >= W) continue;
+                const float wx = up_w(fx, I, Wc);
+                if (wx == 0.0f) continue;
+                sum += wy * wx * ld_act(gcat, (((size_t)b * H + fy) * W + fx) * 64 + lane);
+            }
+        }
+        const size_t q = (size_t)wid * 32 + lane;
+        st_val(gcoarse, q, __bfloat162float(act[q]) > 0.0f ? sum : 0.0f);
+    } else if (wid < Pc + Pf) {
+        const size_t p = (size_t)(wid - Pc);
+        gskip[p * 32 + lane] = ld_act(gcat, p * 64 + 32 + lane);
+    }
+}
+
+// Gradient of the skip features x (BF16 [P][32], encoder level L, H x W) into
+// the pre-activation gradient of the layer that produced them: the decoder's
+// share gskip (FP32 [P][32]) plus the max-pooling transpose of gpool
+// ([P/4][32]: each pooled gradient goes to the first maximum of its 2 x 2
+// window in the order (0, 0), (0, 1), (1, 0), (1, 1)), times the ReLU
+// derivative of x.  One thread per (pixel, channel).
+template <typename GT, typename OT>
+__global__ void pool_backward_kernel(const GT* __restrict__ gpool,
+                                     const __nv_bfloat16* __restrict__ x,
+                                     const float* __restrict__ gskip, OT* __restrict__ gout,
+                                     int B, int H, int W)
+{
+    const size_t n = (size_t)B * H * W * 32;
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int c = (int)(q & 31);
+    const size_t p = q >> 5;
+    const int b = (int)(p / ((size_t)H * W));
+    const int r = (int)(p - (size_t)b * H * W);
+    const int j = r / W, i = r - j * W;
+    const int j0 = j & ~1, i0 = i & ~1;
+    const size_t base = (size_t)b * H * W;
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        v[k] = __bfloat162float(x[((base + (size_t)(j0 + (k >> 1)) * W + i0 + (k & 1)) << 5) + c]);
+    const float m = fmaxf(fmaxf(v[0], v[1]), fmaxf(v[2], v[3]));
+    const int first = v[0] == m ? 0 : v[1] == m ? 1 : v[2] == m ? 2 : 3;
+    const int mine = ((j & 1) << 1) | (i & 1);
+    float g = gskip[q];
+    if (mine == first) {
+        const size_t pc = ((size_t)b * (H / 2) + (j >> 1)) * (W / 2) + (i >> 1);
+        g += ld_act(gpool, pc * 32 + c);
+    }
+    st_val(gout, q, v[mine] > 0.0f ? g : 0.0f);
+}
+
+// weight and bias gradient of a 1 x 1 layer from the 3 x 3 gradient of the
+// same layer (g9 [co = 1][ci][9] + bias): its centre tap
+__global__ void center_tap_kernel(const float* __restrict__ g9, int ci, float* __restrict__ gw,
+                                  float* __restrict__ gb)
+{
+    const int i = threadIdx.x;
+    if (i < ci) gw[i] = g9[i * 9 + 4];
+    if (i == 0) gb[0] = g9[9 * ci];
 }
 
 }  // namespace
@@ -1755,6 +1876,12 @@ struct hp_trainer {
     double* loss;
     uint8_t* mask;
     int step;
+    // Unet: the max-pooled and concatenated layer inputs, the skip features'
+    // gradients from the decoder, the 3 x 3 gradient of the 1 x 1 layer
+    __nv_bfloat16* upool[5];
+    __nv_bfloat16* ucat[4];
+    float* gskip[4];
+    float* g9;
 };
 
 static long layer_offset(const LayerSpec* sp, int l)
@@ -1784,6 +1911,9 @@ void hp_trainer_destroy(hp_trainer* t)
     cudaFree(t->g[0]); cudaFree(t->g[1]); cudaFree(t->gsmall);
     cudaFree(t->part); cudaFree(t->partb); cudaFree(t->rbuf); cudaFree(t->stats);
     cudaFree(t->loss); cudaFree(t->mask);
+    for (int k = 0; k < 5; ++k) cudaFree(t->upool[k]);
+    for (int k = 0; k < 4; ++k) { cudaFree(t->ucat[k]); cudaFree(t->gskip[k]); }
+    cudaFree(t->g9);
     delete t;
 }
 
@@ -1792,9 +1922,9 @@ static constexpr int kWgradChunk = 2048;
 hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
 {
     if (out) *out = nullptr;
-    if (!out || !cnn || !shape_ok(mx) || mx.ny % 4 || mx.nx % 4) return HP_ERR_INVALID_ARG;
-    // the Unet's backward (max pooling, concatenated skips) is not built
-    if (cnn->arch == HP_CNN_UNET) return HP_ERR_UNSUPPORTED;
+    if (!out || !cnn || !shape_ok(mx) || mx.ny % size_multiple(cnn->arch) ||
+        mx.nx % size_multiple(cnn->arch))
+        return HP_ERR_INVALID_ARG;
     // the forward pass of training runs in the network's own input workspace
     // (scale, BF16 branch input), sized for its max_shape
     if (mx.batch > cnn->max_shape.batch || mx.ny > cnn->max_shape.ny ||
@@ -1821,7 +1951,7 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
         const int sc = sp[l].scale;
         const size_t Pl = P / (sc * sc);
         al(&t->act[l], sp[l].cout == 1 ? Pl * 4 : Pl * sp[l].cout * 2);
-        al((void**)&t->wt[l], layer_wcount(sp, l) * 4);
+        al((void**)&t->wt[l], dev_wcount(sp, l) * 4);
         if (tc_layer(sp, l)) al((void**)&t->wdg[l], layer_wcount(sp, l) * 2);
     }
     al((void**)&t->zero_bias, 64 * 4);
@@ -1845,6 +1975,17 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     al((void**)&t->stats, (size_t)mx.batch * kStats * 8);
     al((void**)&t->loss, 8);
     al((void**)&t->mask, P);
+    if (cnn->arch == HP_CNN_UNET) {
+        for (int lev = 0; lev < 5; ++lev) {
+            const size_t Pl = P >> (2 * lev);
+            if (lev >= 1) al((void**)&t->upool[lev], Pl * 32 * 2);
+            if (lev <= 3) {
+                al((void**)&t->ucat[lev], Pl * 64 * 2);
+                al((void**)&t->gskip[lev], Pl * 32 * 4);
+            }
+        }
+        al((void**)&t->g9, (9 * 32 + 1) * 4);
+    }
     if (!ok) { set_cuda_error(cudaGetLastError()); hp_trainer_destroy(t); return HP_ERR_OOM; }
     // masters from the network's current parameters
     cudaError_t e = cudaMemcpy(t->master, cnn->master.data(), t->param_count * 4,
@@ -1866,8 +2007,8 @@ static hp_status trainer_pack(hp_trainer* t, cudaStream_t st)
         const int kind = (ci >= 32 && co >= 32) ? 0 : (co == 1 ? 2 : 1);
         const int n = 9 * ci * co + co;
         pack_layer_kernel<<<(n + 255) / 256, 256, 0, st>>>(t->master + layer_offset(sp, l), ci, co,
-                                                          kind, t->cnn->w[l], t->cnn->bias[l],
-                                                          t->wt[l], t->wdg[l]);
+                                                          kind, sp[l].ks, t->cnn->w[l],
+                                                          t->cnn->bias[l], t->wt[l], t->wdg[l]);
     }
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
@@ -1883,6 +2024,14 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
     const size_t cells = (size_t)s.ny * s.nx;
     hp_status rc = launch_scale(c, div, flags, s.batch, cells, st);
     if (rc != HP_OK) return rc;
+    if (c->arch == HP_CNN_UNET) {
+        UnetKeep keep;
+        for (int l = 0; l < kLayersUnet; ++l) keep.act[l] = t->act[l];
+        for (int k = 0; k < 5; ++k) keep.pooled[k] = t->upool[k];
+        for (int k = 0; k < 4; ++k) keep.cat[k] = t->ucat[k];
+        keep.xin0 = t->xin[0];
+        return unet_forward(c, div, flags, nullptr, s, st, &keep);
+    }
     const float* prev = nullptr;
     for (int k = 0, l = 0; k < c->br.n; ++k) {
         const int scale = c->br.scale[k];
@@ -2105,6 +2254,174 @@ static hp_status branch_backward_tc(hp_trainer* t, int k, int lfirst, int llast,
     return first_layer_bf16(t, k, lfirst, gbuf[cur], B, H, W, st);
 }
 
+// Backward of one 3 x 3 layer l (32/64 channels) of an image H x W from the
+// gradient gy of its pre-activation: weight and bias gradients into t->grad;
+// with gx, the gradient of its input x with the ReLU derivative of mask_act
+// (the activation x, when the layer that made it has a ReLU; may be null)
+// applied.  From the width the tensor-core kernels serve, gy and gx are BF16
+// and the contractions run on the tensor cores; below it they are FP32 on
+// CUDA cores.
+static hp_status layer_backward(hp_trainer* t, int l, const __nv_bfloat16* x, const void* gy,
+                                void* gx, const __nv_bfloat16* mask_act, int B, int H, int W,
+                                cudaStream_t st)
+{
+    const LayerSpec* sp = t->cnn->spec;
+    hp_cnn* c = t->cnn;
+    const int ci = sp[l].cin, co = sp[l].cout;
+    float* gw = t->grad + layer_offset(sp, l);
+    float* gb = gw + layer_wcount(sp, l);
+    hp_status rc;
+    if (W >= conv_tc_min_width()) {
+        int grid = 0;
+        rc = launch_conv3x3_tc_wgrad(x, gy, t->part, t->part_len, t->partb, t->partb_len, B, H, W,
+                                     ci, co, c->err, c->num_sms, &grid, st, c->wait_limit);
+        if (rc != HP_OK) return rc;
+        wgrad_reduce_kernel<<<reduce_blocks(ci, co), 256, 0, st>>>(t->part, t->partb, grid, ci, co,
+                                                                   gw, gb);
+        if ((rc = check_launch()) != HP_OK || !gx) return rc;
+        const __nv_bfloat16* g16 = (const __nv_bfloat16*)gy;
+        __nv_bfloat16* gx16 = (__nv_bfloat16*)gx;
+        rc = launch_conv3x3_tc_dgrad(g16, t->wdg[l], t->zero_bias, mask_act, gx16, B, H, W, ci, co,
+                                     c->err, c->num_sms, st, c->wait_limit);
+        if (rc != HP_OK) return rc;
+        if (ci == 64 && co == 64) return border_terms<64, 64>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
+        if (ci == 32 && co == 64) return border_terms<32, 64>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
+        if (ci == 64 && co == 32) return border_terms<64, 32>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
+        return border_terms<32, 32>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
+    }
+    const float* g32 = (const float*)gy;
+    rc = wgrad_dispatch(t, 0, l, g32, x, gw, gb, B, H, W, st);
+    if (rc != HP_OK || !gx) return rc;
+    float* gx32 = (float*)gx;
+    const int nsm = c->num_sms;
+    if (ci == 64 && co == 64) return dgrad<64, 64>(g32, t->wt[l], gx32, B, H, W, nsm, st, mask_act);
+    if (ci == 32 && co == 64) return dgrad<32, 64>(g32, t->wt[l], gx32, B, H, W, nsm, st, mask_act);
+    if (ci == 64 && co == 32) return dgrad<64, 32>(g32, t->wt[l], gx32, B, H, W, nsm, st, mask_act);
+    return dgrad<32, 32>(g32, t->wt[l], gx32, B, H, W, nsm, st, mask_act);
+}
+
+template <typename GT, typename OT>
+static hp_status cat_backward(const void* gcat, float* gskip, void* gcoarse,
+                              const __nv_bfloat16* act, int B, int H, int W, cudaStream_t st)
+{
+    const long warps = (long)B * H * W + (long)B * (H / 2) * (W / 2);
+    cat_backward_kernel<GT, OT><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+        (const GT*)gcat, gskip, (OT*)gcoarse, act, B, H, W);
+    return check_launch();
+}
+
+template <typename GT, typename OT>
+static hp_status pool_backward(const void* gpool, const __nv_bfloat16* x, const float* gskip,
+                               void* gout, int B, int H, int W, cudaStream_t st)
+{
+    const size_t n = (size_t)B * H * W * 32;
+    pool_backward_kernel<GT, OT><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        (const GT*)gpool, x, gskip, (OT*)gout, B, H, W);
+    return check_launch();
+}
+
+// The Unet's backward (the reading of the network is in the forward above):
+// from dL/dphi_hat in t->g[0] down the decoder, through the bottom and back
+// up the encoder, where each level's skip features collect the decoder's
+// share and the max-pooling transpose.  Gradients ping-pong between g[0] and
+// g[1] (BF16 at levels the tensor-core kernels serve, FP32 below).
+static hp_status unet_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
+{
+    hp_cnn* c = t->cnn;
+    const LayerSpec* sp = c->spec;
+    const int B = s.batch;
+    auto Hl = [&](int lev) { return s.ny >> lev; };
+    auto Wl = [&](int lev) { return s.nx >> lev; };
+    auto bf = [&](int lev) { return Wl(lev) >= conv_tc_min_width(); };
+    auto act = [&](int l) { return (const __nv_bfloat16*)t->act[l]; };
+    // the activation of layer l when that layer has a ReLU (its derivative
+    // is then applied), else null
+    auto relu_of = [&](int l) { return sp[l].relu ? act(l) : nullptr; };
+    void* g[2] = {t->g[0], t->g[1]};
+    hp_status rc;
+    // layer 19, the 1 x 1 output convolution 32 -> 1 (run as a 3 x 3 with
+    // zero outer taps): its weight gradient is the centre tap
+    const int L1 = kLayersUnet - 1;
+    const float* gout = t->g[0];
+    rc = wgrad_last(t, L1, gout, t->g9, t->g9 + 9 * 32, B, Hl(0), Wl(0), st);
+    if (rc != HP_OK) return rc;
+    {
+        float* gw = t->grad + layer_offset(sp, L1);
+        center_tap_kernel<<<1, 32, 0, st>>>(t->g9, 32, gw, gw + 32);
+        if ((rc = check_launch()) != HP_OK) return rc;
+    }
+    if (bf(0))
+        rc = dgrad_last(t, L1, gout, (__nv_bfloat16*)g[1], B, Hl(0), Wl(0), relu_of(L1 - 1), st);
+    else
+        rc = dgrad_last(t, L1, gout, (float*)g[1], B, Hl(0), Wl(0), relu_of(L1 - 1), st);
+    if (rc != HP_OK) return rc;
+    int cur = 1;  // g[cur] holds the pre-activation gradient of the next layer
+    int l = L1 - 1;
+    // decoder, level 0 up to 3: two convolutions, then the concatenation's
+    // transpose into the skip gradient and the coarser level
+    for (int lev = 0; lev < 4; ++lev) {
+        const int H = Hl(lev), W = Wl(lev);
+        // second convolution: input = output of the first (ReLU)
+        rc = layer_backward(t, l, act(l - 1), g[cur], g[cur ^ 1], relu_of(l - 1), B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1;
+        --l;
+        // first convolution: input = [up(coarser), skip], no ReLU of its own
+        rc = layer_backward(t, l, t->ucat[lev], g[cur], g[cur ^ 1], nullptr, B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1;
+        --l;
+        // l is now the layer whose output was up-sampled (the coarser level)
+        const bool a = bf(lev), b2 = bf(lev + 1);
+        if (a && b2) rc = cat_backward<__nv_bfloat16, __nv_bfloat16>(g[cur], t->gskip[lev], g[cur ^ 1], act(l), B, H, W, st);
+        else if (a) rc = cat_backward<__nv_bfloat16, float>(g[cur], t->gskip[lev], g[cur ^ 1], act(l), B, H, W, st);
+        else rc = cat_backward<float, float>(g[cur], t->gskip[lev], g[cur ^ 1], act(l), B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1;
+    }
+    // bottom (level 4): 64 -> 32, 64 -> 64, 32 -> 64 on the pooled skip 3
+    {
+        const int H = Hl(4), W = Wl(4);
+        rc = layer_backward(t, l, act(l - 1), g[cur], g[cur ^ 1], relu_of(l - 1), B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1; --l;
+        rc = layer_backward(t, l, act(l - 1), g[cur], g[cur ^ 1], relu_of(l - 1), B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1; --l;
+        rc = layer_backward(t, l, t->upool[4], g[cur], g[cur ^ 1], nullptr, B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1; --l;
+    }
+    // encoder, level 3 down to 0: the skip features' gradient (decoder share
+    // plus the pooling transpose), then the level's two convolutions
+    for (int lev = 3; lev >= 0; --lev) {
+        const int H = Hl(lev), W = Wl(lev);
+        // l is the layer that produced the skip features of this level
+        const bool a = bf(lev + 1), b2 = bf(lev);
+        if (a && b2) rc = pool_backward<__nv_bfloat16, __nv_bfloat16>(g[cur], act(l), t->gskip[lev], g[cur ^ 1], B, H, W, st);
+        else if (b2) rc = pool_backward<float, __nv_bfloat16>(g[cur], act(l), t->gskip[lev], g[cur ^ 1], B, H, W, st);
+        else rc = pool_backward<float, float>(g[cur], act(l), t->gskip[lev], g[cur ^ 1], B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1;
+        rc = layer_backward(t, l, act(l - 1), g[cur], g[cur ^ 1], relu_of(l - 1), B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1; --l;
+        if (lev == 0) break;  // l = 0: the first layer, below
+        // the level's first convolution reads the pooled skip features of
+        // the level above; its input gradient feeds that level's pooling
+        rc = layer_backward(t, l, t->upool[lev], g[cur], g[cur ^ 1], nullptr, B, H, W, st);
+        if (rc != HP_OK) return rc;
+        cur ^= 1; --l;
+    }
+    // layer 0, [div/s, flags] -> 32: weight gradient only
+    float* gw = t->grad + layer_offset(sp, 0);
+    if (bf(0))
+        return wgrad_first(t, 0, 0, (const __nv_bfloat16*)g[cur], gw, gw + layer_wcount(sp, 0), B,
+                           Hl(0), Wl(0), st);
+    return wgrad_first(t, 0, 0, (const float*)g[cur], gw, gw + layer_wcount(sp, 0), B, Hl(0),
+                       Wl(0), st);
+}
+
 // dL/dparams into t->grad from dL/dphi_hat in t->g[0] (the activations of
 // the last trainer_forward)
 static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
@@ -2112,6 +2429,7 @@ static hp_status trainer_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
     const LayerSpec* sp = t->cnn->spec;
     hp_cnn* c = t->cnn;
     hp_status rc = HP_OK;
+    if (c->arch == HP_CNN_UNET) return unet_backward(t, s, st);
     // backward, branch by branch from full resolution
     int cur = 0;
     for (int k = c->br.n - 1, l = c->nlayers - 1; k >= 0; --k) {
@@ -2237,8 +2555,9 @@ static hp_status trainer_adam(hp_trainer* t, const hp_train_params* p, cudaStrea
 
 static bool trainer_shape_ok(const hp_trainer* t, hp_shape s)
 {
+    const int m = size_multiple(t->cnn->arch);
     return shape_ok(s) && s.batch <= t->max.batch && s.ny <= t->max.ny && s.nx <= t->max.nx &&
-           s.ny % 4 == 0 && s.nx % 4 == 0;
+           s.ny % m == 0 && s.nx % m == 0;
 }
 
 extern "C" {

@@ -18,7 +18,7 @@ SMALL_LAYERS = ([(2, 32), (32, 32), (32, 32), (32, 32), (32, 1)] +
                 2 * [(3, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1)])
 # the MonoScale: one full-resolution branch of nine convolutions
 MONO_LAYERS = [(2, 32), (32, 64)] + 5 * [(64, 64)] + [(64, 32), (32, 1)]
-# the Unet (forward only): (cin, cout, kernel size), the last layer 1 x 1
+# the Unet: (cin, cout, kernel size), the last layer 1 x 1
 UNET_LAYERS = ([(2, 32), (32, 32)] + 3 * [(32, 64), (64, 32)] + [(32, 64), (64, 64), (64, 32)]
                + 3 * [(64, 64), (64, 32)] + [(64, 32), (32, 32), (32, 1, 1)])
 ARCH_LAYERS = {"multiscale": LAYERS, "smallscale": SMALL_LAYERS, "monoscale": MONO_LAYERS,

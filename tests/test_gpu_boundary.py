@@ -186,9 +186,12 @@ def test_trainer_checkpoint_resumes_bit_exactly(dev, tmp_path):
 def test_adam_matches_the_oracle_update(dev, arch):
     # three steps; the oracle takes the GPU's own gradient of each step (the
     # gradient itself is checked against the oracle backward elsewhere) and
-    # applies Adam in FP64 to FP64 copies of the state
+    # applies Adam in FP64 to FP64 copies of the state, with the
+    # hyper-parameters the library receives (FP32 values: 1 - beta2 alone
+    # differs by 1.3e-5 relative between 0.999 and its FP32 value)
     B, n = 2, 64
     lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    f32 = [float(np.float32(x)) for x in (lr, b1, b2, eps)]
     data = T.generate_pairs(6, n, seed0=330, sweeps=300, chunk=6, device=dev)
     cnn = hp.CNN(B, n, n, params=T.init_params(seed=6, arch=arch), arch=arch)
     tr = hp.Trainer(cnn, B, n, n)
@@ -201,8 +204,7 @@ def test_adam_matches_the_oracle_update(dev, arch):
         d, f, t = (x[2 * k:2 * k + 2].contiguous() for x in data)
         g, _ = tr.gradient(d, f, t, lambda_div=1.0)
         tr.step(d, f, t, lr=lr, beta1=b1, beta2=b2, eps=eps, lambda_div=1.0)
-        th, m, v = TR.adam_step(th, m, v, g.cpu().numpy().astype(np.float64), k + 1, lr, b1,
-                                b2, eps)
+        th, m, v = TR.adam_step(th, m, v, g.cpu().numpy().astype(np.float64), k + 1, *f32)
     w, mg, vg, st = tr.state()
     assert st == 3
     assert np.abs(mg - m).max() <= 1e-5 * np.abs(m).max()

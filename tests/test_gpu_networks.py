@@ -1,7 +1,7 @@
 """The SmallScale network (Sec. 3.1: the MultiScale with fewer filters, every
 64-channel layer at 32 channels), the MonoScale (one feed-forward branch of
 nine convolutions at full resolution) and the Unet (five scales, max pooling,
-concatenated skip features; forward only) on the GPU against the FP64 oracle:
+concatenated skip features) on the GPU against the FP64 oracle:
 1. the forward (hp_cnn_forward), under the bar of the MultiScale forward test;
 2. the hybrid projection from the same guess;
 3. the training gradient (hand-written backward: on the tensor cores from a
@@ -22,8 +22,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 hp = pytest.importorskip("paper_2109_09363_gb300")
 
-ARCHS = ["smallscale", "monoscale"]   # forward and training
-FORWARD_ARCHS = ARCHS + ["unet"]     # forward and hybrid projection
+ARCHS = ["smallscale", "monoscale", "unet"]   # forward, hybrid projection and training
+FORWARD_ARCHS = ARCHS
 
 
 @pytest.fixture(scope="module")
@@ -136,13 +136,18 @@ def oracle_gradient(params, phi_gpu, div, fl, tgt, s, lam, act_round):
     return L, total
 
 
-@pytest.mark.parametrize("arch", ARCHS)
-@pytest.mark.parametrize("B,ny,nx", [(2, 16, 16), (2, 32, 32), (2, 128, 128), (1, 64, 160)])
+@pytest.mark.parametrize("arch,B,ny,nx", [
+    (a, *shape) for a in ARCHS
+    for shape in [(2, 16, 16), (2, 32, 32), (2, 128, 128), (1, 64, 160)]] + [
+    ("unet", 1, 256, 512)])
 def test_network_gradient_matches_oracle_backward(dev, arch, B, ny, nx):
     """16 x 16: every branch on CUDA cores; 32 x 32: the SmallScale's coarse
     branches (8 and 16 pixels wide) on CUDA cores, full resolution on the
     tensor cores; the larger sizes on the tensor cores throughout (160 = a
-    full and a partial 128-pixel segment)."""
+    full and a partial 128-pixel segment).  The Unet's levels narrower than
+    32 pixels (down to 1 x 1 at 16 x 16) run on CUDA cores, with the
+    concatenation and pooling transposes between BF16 and FP32 levels;
+    256 x 512 puts levels 0-3 on the tensor cores."""
     rng = np.random.default_rng(B + nx + 1)
     params = random_params(13, arch)
     u, v, fl = W.training_case(1, max(ny, nx), 710)
@@ -216,8 +221,8 @@ def test_parameter_counts_are_checked(dev, arch):
 
 def test_unet_at_the_tensor_core_widths_and_argument_checks(dev):
     """512 x 256: every level from 32 pixels wide up on the tensor cores, the
-    n/16 bottom (32 x 16) on the gather kernel; the Unet has no trainer and
-    wants sizes that are multiples of 16."""
+    n/16 bottom (32 x 16) on the gather kernel; the Unet and its trainer want
+    sizes that are multiples of 16."""
     B, ny, nx = 1, 256, 512
     params = random_params(9, "unet")
     u, v = W.vortex_velocity(ny, nx, 61, n_vortices=12, width=(4, 24))
@@ -235,6 +240,6 @@ def test_unet_at_the_tensor_core_widths_and_argument_checks(dev):
     got = phi_hat[0].cpu().numpy()
     assert np.abs(got - ref).max() <= 2e-2 * np.abs(ref).max(), np.abs(got - ref).max()
     with pytest.raises(hp.HprojError):
-        hp.Trainer(cnn, B, ny, nx)
-    with pytest.raises(hp.HprojError):
         hp.CNN(1, 40, 48, arch="unet")
+    with pytest.raises(hp.HprojError):
+        hp.Trainer(cnn, B, 40, 48)
