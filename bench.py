@@ -566,6 +566,141 @@ def compare_plume_min_threshold(hp, nets, dev, n=128, steps=300, cap=20000, refe
     return res
 
 
+def plume_eval(hp, nets, dev, n, steps, flags_np, inlet, literal_thr=1e-3, literal_cap=2000,
+               rule_cap=5000, scheme=0, dt=0.1, gravity=-0.002, seed=3):
+    """One plume of BASELINE's configs 3 / 5 (first-order semi-Lagrangian by
+    default, g = -0.002, dt = 0.1, inlet rho = 1.1, rho = 1 + N(0, 1e-4^2)),
+    run `steps` steps per arm; each arm's projections are timed alone (CUDA
+    events around the projection of every step).  Arms:
+    - literal: plain Jacobi and the MultiScale hybrid at E_t = literal_thr;
+    - the paper's rule (Sec. 4.2): every network first runs the plume alone
+      (its guess is the projection, no sweep) and E_t of step k is the
+      smallest E_1 any of them reaches; then plain Jacobi and the hybrid with
+      each network at that per-step E_t (cap rule_cap).
+    Per arm: projections/s over the projection time, sweeps (mean, max),
+    converged steps, and the largest plume-head distance to plain Jacobi's
+    trajectory (cells)."""
+    import torch
+    from paper_2109_09363_gb300 import workloads as W
+    from paper_2109_09363_gb300.plume import Plume, PlumeConfig
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    fl = t(flags_np[None])
+    u0, v0, rho0 = W.plume_initial_state(n, seed=seed)
+    stream = torch.cuda.current_stream()
+
+    def run(arch, thresholds, cap):
+        cfg = PlumeConfig(ny=n, nx=n, dt=dt, gravity=gravity, inlet=tuple(inlet),
+                          threshold=float(thresholds[0]), max_iters=cap, scheme=scheme)
+        cnn = hp.CNN(1, n, n, params=nets[arch], arch=arch) if arch else None
+        sim = Plume(cfg, t(u0[None].astype(np.float32)), t(v0[None].astype(np.float32)),
+                    t(rho0[None].astype(np.float32)), fl, cnn=cnn)
+        it = torch.zeros(steps, dtype=torch.int32, device=dev)
+        cv = torch.zeros(steps, dtype=torch.uint8, device=dev)
+        e1 = torch.zeros(steps, dtype=torch.float64, device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        hd = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            sim.prm.threshold = float(thresholds[k])
+            sim.advect()
+            ev[k][0].record(stream)
+            out = sim.project()
+            ev[k][1].record(stream)
+            it[k:k + 1].copy_(out["iters"])
+            cv[k:k + 1].copy_(out["converged"])
+            e1[k:k + 1].copy_(out["e1"])
+            hd.append(torch.stack(sim.head()).view(-1))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        proj_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if cnn is not None:
+            cnn.check()
+            cnn.close()
+        sim.ctx.close()
+        its = it.cpu().numpy()
+        return {"projections_per_s": steps / (proj_ms * 1e-3), "projection_ms_total": proj_ms,
+                "solver_seconds": wall, "sweeps_mean": float(its.mean()),
+                "sweeps_max": int(its.max()), "converged_steps": int(cv.sum().item()),
+                "e1": e1.cpu().numpy(), "heads": torch.stack(hd).cpu().numpy() * n}
+
+    def summary(runs):
+        ref = runs["plain"]["heads"]
+        out = {}
+        for mode, r in runs.items():
+            o = {k: v for k, v in r.items() if k not in ("e1", "heads")}
+            if mode != "plain":
+                d = np.abs(r["heads"] - ref).max(axis=0)
+                o["max_head_difference_cells"] = {"h_y": float(d[0]), "left": float(d[1]),
+                                                  "right": float(d[2])}
+                if mode.startswith("hybrid"):
+                    o["speedup_vs_plain"] = (runs["plain"]["projection_ms_total"] /
+                                             r["projection_ms_total"])
+            out[mode] = o
+        return out
+
+    lit = np.full(steps, literal_thr)
+    res = {"literal": summary({"plain": run(None, lit, literal_cap),
+                               "hybrid_multiscale": run("multiscale", lit, literal_cap)})}
+    res["literal"]["threshold"] = literal_thr
+    res["literal"]["cap"] = literal_cap
+    alone = {a: run(a, np.zeros(steps), 0) for a in nets}
+    e_t = np.min(np.stack([r["e1"] for r in alone.values()]), axis=0)
+    runs = {"plain": run(None, e_t, rule_cap)}
+    runs.update({"hybrid_" + a: run(a, e_t, rule_cap) for a in nets})
+    runs.update({"alone_" + a: r for a, r in alone.items()})
+    res["paper_rule"] = summary(runs)
+    res["paper_rule"]["threshold"] = {
+        "min": float(e_t.min()), "median": float(np.median(e_t)), "max": float(e_t.max()),
+        "set_by": {a: int(np.sum(r["e1"] == e_t)) for a, r in alone.items()}, "cap": rule_cap}
+    return res
+
+
+def run_baseline_plumes(hp, dev, pairs=10000, epochs=20, batch=64):
+    """BASELINE's configs 3 and 5 at their sizes, with the networks trained
+    by config 5's recipe: `pairs` 128^2 pairs from the plain solver (the
+    training distribution of the hybrid arm), Adam lr 1e-3, batch 64, 20
+    epochs, every network.  Config 3: the 1024^2 plume (inlet 128 cells) with
+    a solid disc of radius 64 centred 256 cells above the inlet, 200 steps;
+    config 5's evaluation: the 2048^2 plume (inlet 256 cells) with 8
+    non-overlapping discs of radius U(32, 128), 500 steps (plume_eval)."""
+    import torch
+    from paper_2109_09363_gb300 import training as T
+    from paper_2109_09363_gb300 import workloads as W
+    t0 = time.perf_counter()
+    data = T.generate_pairs(pairs, 128, seed0=0, sweeps=TRAIN_SWEEPS, device=dev)
+    torch.cuda.synchronize()
+    res = {"training": {"pairs": pairs, "grid": [128, 128], "target_sweeps": TRAIN_SWEEPS,
+                        "batch": batch, "epochs": epochs,
+                        "pair_generation_seconds": time.perf_counter() - t0}}
+    nets = {}
+    for arch in NETWORKS:
+        t1 = time.perf_counter()
+        cnn = hp.CNN(batch, 128, 128, params=T.init_params(seed=1, arch=arch), arch=arch)
+        losses = T.train(cnn, data, epochs=epochs, batch=batch, lr=1e-3, lambda_div=1.0)
+        nets[arch] = cnn.get_params()
+        cnn.close()
+        res["training"][arch] = {"steps": len(losses), "seconds": time.perf_counter() - t1,
+                                 "final_loss": float(np.mean(losses[-20:]))}
+    del data
+    torch.cuda.empty_cache()
+    n3 = 1024
+    fl3 = W.plume_flags(n3, cylinder_radius=64, cylinder_height=256)
+    res["config3"] = plume_eval(hp, nets, dev, n3, 200, fl3, W.inlet_columns(n3))
+    res["config3"]["workload"] = ("1024^2 plume, inlet cols [448, 576) of the bottom row, solid "
+                                  "disc r = 64 centred 256 cells above it, first-order "
+                                  "semi-Lagrangian, g = -0.002, dt = 0.1, 200 steps")
+    n5 = 2048
+    fl5 = W.random_cylinders(n5, 8, 5, radius=(32, 128), inlet=W.inlet_columns(n5))
+    res["config5"] = plume_eval(hp, nets, dev, n5, 500, fl5, W.inlet_columns(n5))
+    res["config5"]["workload"] = ("2048^2 plume, inlet cols [896, 1152) of the bottom row, 8 "
+                                  "non-overlapping solid discs r ~ U(32, 128) (seed 5), "
+                                  "first-order semi-Lagrangian, g = -0.002, dt = 0.1, "
+                                  "500 steps")
+    return res
+
+
 def compare_in_distribution(hp, nets, flush, stream, dev, ws):
     """Plain vs hybrid with each trained network (nets: architecture ->
     parameters; the MultiScale's run keeps the key "hybrid") on held-out grids
@@ -870,6 +1005,10 @@ def main():
                     help="skip the timing of physics-driven training steps")
     ap.add_argument("--train-steps", type=int, default=1200,
                     help="Adam steps of the network trained for the hybrid arm")
+    ap.add_argument("--baseline-plumes", action="store_true",
+                    help="only run BASELINE's configs 3 and 5 at their sizes (1024^2 and "
+                         "2048^2 plumes, networks trained by config 5's recipe) and print "
+                         "their JSON")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the sweep blocks from a host-polled loop instead of the "
                          "CUDA-graph conditional loop (same kernels; ncu cannot profile kernel "
@@ -889,6 +1028,16 @@ def main():
         return profile_cnn_scaling()
     if args.profile_train:
         return profile_train(*args.profile_train)
+    if args.baseline_plumes:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2109_09363_gb300 as hp
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"mode": "baseline_plumes",
+                          **run_baseline_plumes(hp, dev)}), flush=True)
+        return 0
 
     import torch
     import torch.distributed as dist
@@ -1129,7 +1278,12 @@ def main():
             # the cap lifted so that every grid of both arms converges (the
             # paper's comparison at equal mean|div|)
             unc = hybrid["equal_threshold_uncapped"]
+            eq = {"multiscale": unc["speedup"]}
+            eq.update({a: hybrid[a]["equal_threshold_uncapped"]["speedup"]
+                       for a in NETWORKS[1:] if a in hybrid})
+            best = max(eq, key=eq.get)
             line["hybrid_vs_plain"] = {
+                "best_network_equal_threshold": {"network": best, "speedup": eq[best]},
                 "network": "multiscale",
                 "equal_threshold": {
                     "speedup": unc["speedup"], "threshold": THR, "cap": unc["cap"],

@@ -145,3 +145,31 @@ def training_case(batch: int, n: int, seed0: int = 0):
                               disc_radius=(n / 32, n / 8))
         us.append(u1 + u2); vs.append(v1 + v2); fs.append(fl)
     return np.stack(us), np.stack(vs), np.stack(fs)
+
+
+def random_cylinders(n: int, count: int, seed: int, radius=(32.0, 128.0), inlet=None,
+                     clearance: float = 8.0, tries: int = 10000):
+    """uint8 flags with `count` solid discs of radius U(radius), centres drawn
+    until the discs overlap neither each other nor the walls nor the inlet
+    (a band of the inlet's columns, `clearance` cells beyond each side, over
+    the bottom rows up to the disc), all with `clearance` cells to spare."""
+    g = _rng(seed)
+    x, y = np.meshgrid(np.arange(n) + 0.5, np.arange(n) + 0.5)
+    fl = np.zeros((n, n), np.uint8)
+    discs = []
+    for _ in range(tries):
+        if len(discs) == count:
+            break
+        r = g.uniform(radius[0], radius[1])
+        cx, cy = g.uniform(r + clearance, n - r - clearance, 2)
+        if any((cx - a) ** 2 + (cy - b) ** 2 < (r + c + clearance) ** 2 for a, b, c in discs):
+            continue
+        if inlet is not None and inlet[0] - clearance - r < cx < inlet[1] + clearance + r and \
+                cy + r + clearance > n - 4 * clearance:
+            continue
+        discs.append((cx, cy, r))
+    if len(discs) < count:
+        raise ValueError(f"only {len(discs)} of {count} discs fit")
+    for cx, cy, r in discs:
+        fl[(x - cx) ** 2 + (y - cy) ** 2 <= r * r] = 1
+    return fl
