@@ -88,7 +88,19 @@ typedef struct {
  *                  grid is larger than 512 x 512 cells or the cluster does
  *                  not fit on the device.  All give the same iterates bit for
  *                  bit; the FP64 E_k may differ in the last bits between
- *                  kernels (their partial sums are grouped differently). */
+ *                  kernels (their partial sums are grouped differently).
+ *   open_top       1 = the top boundary (the v faces of row 0) is open to an
+ *                  exterior at p = 0: the faces of fluid cells of row 0 are
+ *                  open (counted in n, in the divergence and corrected from
+ *                  the exterior value 0); 0 = a closed wall (the default).
+ *   inflow_x0, inflow_x1  bottom-boundary v faces (row ny) of the columns
+ *                  [x0, x1) under fluid cells keep the velocity the caller
+ *                  gives (a prescribed inflow, e.g. -U_in): they enter the
+ *                  divergence of the cells above them, are never corrected
+ *                  and stay closed for the pressure; x1 <= x0 = none.
+ *   A closed box (both 0, the default) leaves the pressure defined up to a
+ *   constant; with an open top it is unique.  Prescribed inflow without an
+ *   open top has no solution unless the inflow sums to zero. */
 typedef struct {
     double threshold;
     int32_t max_iters;
@@ -98,6 +110,9 @@ typedef struct {
     int32_t temporal_block;
     int32_t use_graph;
     int32_t sweep_kernel;
+    int32_t open_top;
+    int32_t inflow_x0;
+    int32_t inflow_x1;
 } hp_project_params;
 
 typedef struct hp_ctx hp_ctx;
@@ -194,7 +209,15 @@ int32_t hp_resident_clusters(hp_ctx *ctx, hp_shape shape);
  *             value q_f, the forward field sampled backwards at x + dt vel(x)
  *             (q_b), and q_f + (q - q_b) / 2 clamped to the range of the four
  *             samples the forward step interpolated; for rho, u and v alike.
- *             Other values return HP_ERR_INVALID_ARG. */
+ *             Other values return HP_ERR_INVALID_ARG.
+ *   u_in      speed of the injected fluid (Sec. 4.1): the bottom-boundary v
+ *             faces of the inlet columns under fluid cells are set to -u_in
+ *             (upwards) after the step; 0 = no velocity injection
+ *   open_top  1: the top boundary is open (the outflow of the injected
+ *             fluid); its v faces keep their advected velocity instead of
+ *             being closed; 0 = a closed wall.
+ *   Project such a step with open_top and inflow_x0, inflow_x1 of
+ *   hp_project_params set to the same values. */
 typedef struct {
     float dt;
     float gravity;
@@ -203,6 +226,8 @@ typedef struct {
     int32_t inlet_x0;
     int32_t inlet_x1;
     int32_t scheme;
+    float u_in;
+    int32_t open_top;
 } hp_plume_params;
 
 /* One driver step on B grids, out of place (outputs must not alias inputs):
@@ -212,7 +237,9 @@ typedef struct {
  *      component; positions clamped to each quantity's sample span;
  *   3. v += dt * g * (mean of the two advected densities next to the face
  *      - rho_amb) on interior v faces;
- *   4. every closed face set to zero.
+ *   4. every closed face set to zero, except the top faces of fluid cells
+ *      when open_top (advected like interior faces); the inlet faces of the
+ *      bottom boundary set to -u_in (when u_in != 0).
  * u, u_out float [B][ny][nx+1]; v, v_out [B][ny+1][nx]; rho, rho_out, flags
  * [B][ny][nx]; device memory. */
 hp_status hp_advect_step(const float *u, const float *v, const float *rho, const uint8_t *flags,
@@ -251,7 +278,8 @@ hp_status hp_conv3x3_bf16(const uint16_t *x, const uint16_t *w, const float *bia
  * Sec. 3.2).  Forward map (hp_project with fixed_iters = k and a guess phi0):
  * (u*, v*, phi_0) -> (u, v, p).  Given gu = dL/du, gv = dL/dv and gp = dL/dp
  * (may be NULL), returns dL/du*, dL/dv* (0 on closed faces) and dL/dphi_0,
- * using k transposed sweeps (no stored iterates: the map is affine).
+ * using k transposed sweeps (no stored iterates: the map is affine).  The
+ * closed box only (open_top = 0, no inflow faces).
  * gu, gu_star float [B][ny][nx+1]; gv, gv_star [B][ny+1][nx]; gp, g_phi0
  * [B][ny][nx]; device memory; outputs must not alias inputs.  Uses the
  * context's workspaces. */

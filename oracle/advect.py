@@ -86,12 +86,16 @@ def velocity_at(u, v, x, y):
 
 
 def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, inlet=None,
-                scheme="sl"):
+                scheme="sl", u_in=0.0, open_top=False):
     """One driver step on one grid; returns (u*, v*, rho) in FP64.
 
     u [ny][nx+1], v [ny+1][nx], rho, flags [ny][nx]; inlet = (x0, x1) columns
     of the bottom-row density source or None; scheme "sl" (first-order
-    semi-Lagrangian) or "maccormack".
+    semi-Lagrangian) or "maccormack".  Velocity injection (the plume's inlet
+    speed U_in of Sec. 4.1): the bottom-boundary v faces of the inlet columns
+    under fluid cells get v = -u_in (upwards) after the step; with open_top
+    the top-boundary v faces of fluid cells keep their advected velocity (the
+    outflow) instead of being closed.
     """
     u = np.asarray(u, np.float64)
     v = np.asarray(v, np.float64)
@@ -117,7 +121,15 @@ def advect_step(u, v, rho, flags, dt, gravity=-0.002, rho_amb=1.0, rho_in=1.1, i
     rho_face = 0.5 * (rho_new[:-1, :] + rho_new[1:, :])
     v_new[1:ny, :] += dt * gravity * (rho_face - rho_amb)
     uz, vz = oracle.zero_closed_faces(u_new, v_new, flags)
-    return uz[0], vz[0], rho_new
+    uz, vz = uz[0], vz[0]
+    fluid = np.asarray(flags).reshape(ny, nx) == 0
+    if open_top:
+        vz[0, fluid[0]] = v_new[0, fluid[0]]
+    if inlet is not None and u_in != 0.0:
+        cols = np.zeros(nx, bool)
+        cols[max(inlet[0], 0):max(min(inlet[1], nx), 0)] = True
+        vz[ny, cols & fluid[ny - 1]] = -u_in
+    return uz, vz, rho_new
 
 
 def plume_head(rho, rho_amb=1.0, contrast=0.01):

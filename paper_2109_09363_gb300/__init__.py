@@ -36,13 +36,15 @@ class hp_project_params(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("fixed_iters", ctypes.c_int32), ("dt", ctypes.c_float), ("rho0", ctypes.c_float),
                 ("temporal_block", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("sweep_kernel", ctypes.c_int32)]
+                ("sweep_kernel", ctypes.c_int32), ("open_top", ctypes.c_int32),
+                ("inflow_x0", ctypes.c_int32), ("inflow_x1", ctypes.c_int32)]
 
 
 class hp_plume_params(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_float), ("gravity", ctypes.c_float), ("rho_amb", ctypes.c_float),
                 ("rho_in", ctypes.c_float), ("inlet_x0", ctypes.c_int32),
-                ("inlet_x1", ctypes.c_int32), ("scheme", ctypes.c_int32)]
+                ("inlet_x1", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("u_in", ctypes.c_float), ("open_top", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -197,11 +199,14 @@ class ProjectParams:
     temporal_block: int = 0
     use_graph: int = 1
     sweep_kernel: int = 0
+    open_top: int = 0      # 1: the top boundary is open to p = 0 (outflow)
+    inflow: tuple = (0, 0)  # bottom-boundary v faces of these columns keep their velocity
 
     def c(self):
         return hp_project_params(self.threshold, self.max_iters, self.fixed_iters, self.dt,
                                  self.rho0, self.temporal_block, self.use_graph,
-                                 self.sweep_kernel)
+                                 self.sweep_kernel, self.open_top, self.inflow[0],
+                                 self.inflow[1])
 
 
 def hp_face_mask(flags, mask_out=None, stream=None):
@@ -338,10 +343,12 @@ class PlumeParams:
     inlet_x0: int = 0
     inlet_x1: int = 0
     scheme: int = 0  # 0 first-order semi-Lagrangian, 1 MacCormack
+    u_in: float = 0.0  # injection speed on the inlet faces (upwards)
+    open_top: int = 0  # 1: the top boundary is open (outflow)
 
     def c(self):
         return hp_plume_params(self.dt, self.gravity, self.rho_amb, self.rho_in, self.inlet_x0,
-                               self.inlet_x1, self.scheme)
+                               self.inlet_x1, self.scheme, self.u_in, self.open_top)
 
 
 def hp_advect_step(u, v, rho, flags, params: PlumeParams, u_out=None, v_out=None, rho_out=None,

@@ -189,14 +189,19 @@ __global__ void advect_kernel(const float* __restrict__ u, const float* __restri
         u_out[(size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1) + i] = val;
     }
     if (i < nx) {
-        const bool open = j > 0 && j < ny && fluid(fl, nx, i, j - 1) && fluid(fl, nx, i, j);
+        const bool interior = j > 0 && j < ny && fluid(fl, nx, i, j - 1) && fluid(fl, nx, i, j);
+        // an open top keeps (advects) its faces; buoyancy acts on interior faces
+        const bool top = j == 0 && p.open_top && fluid(fl, nx, i, 0);
         float val = 0.0f;
-        if (open) {
-            val = advected<MC>(fv, nx, ny + 1, 0.5f, 0.0f, fu, fv, dt, i, j);
+        if (interior || top) val = advected<MC>(fv, nx, ny + 1, 0.5f, 0.0f, fu, fv, dt, i, j);
+        if (interior) {
             const float rf = 0.5f * (rho_new_at<MC>(r, fu, fv, dt, i, j - 1) +
                                      rho_new_at<MC>(r, fu, fv, dt, i, j));
             val += dt * p.gravity * (rf - p.rho_amb);
         }
+        // injection through the inlet faces of the bottom boundary (upwards)
+        if (j == ny && i >= p.inlet_x0 && i < p.inlet_x1 && fluid(fl, nx, i, ny - 1))
+            val = -p.u_in;
         v_out[(size_t)b * (ny + 1) * nx + (size_t)j * nx + i] = val;
     }
 }
@@ -284,6 +289,7 @@ extern "C" hp_status hp_advect_step(const float* u, const float* v, const float*
         return HP_ERR_INVALID_ARG;
     if (u_out == u || v_out == v || rho_out == rho || !(p->dt >= 0.0f)) return HP_ERR_INVALID_ARG;
     if (p->scheme != 0 && p->scheme != 1) return HP_ERR_INVALID_ARG;
+    if ((p->open_top != 0 && p->open_top != 1) || !isfinite(p->u_in)) return HP_ERR_INVALID_ARG;
     return hp::launch_advect(u, v, rho, flags, u_out, v_out, rho_out, s, *p, (cudaStream_t)stream);
 }
 

@@ -48,6 +48,9 @@ bool project_args_ok(const hp_ctx* c, const float* u, const float* v, const uint
         prm->temporal_block > kMaxBlock || !(prm->threshold >= 0.0) || !(prm->dt > 0.0f) ||
         !(prm->rho0 > 0.0f) || prm->sweep_kernel < 0 || prm->sweep_kernel > 4)
         return false;
+    if (prm->open_top != 0 && prm->open_top != 1) return false;
+    if (prm->inflow_x1 > prm->inflow_x0 && (prm->inflow_x0 < 0 || prm->inflow_x1 > s.nx))
+        return false;
     return (e_hist == nullptr) == (hist_len <= 0);
 }
 

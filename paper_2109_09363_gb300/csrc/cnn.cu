@@ -976,7 +976,7 @@ hp_status hp_project_hybrid(hp_ctx* ctx, hp_cnn* cnn, float* u, float* v, const 
         return HP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     // divergence into the context, CNN guess into the second phi buffer
-    hp_status rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st);
+    hp_status rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st, boundary_of(*prm));
     if (rc != HP_OK) return rc;
     float* phi_hat = cnn->out[cnn->br.n - 1];
     rc = hp_cnn_forward(cnn, ctx->div, flags, phi_hat, nullptr, s, stream);

@@ -21,6 +21,19 @@ constexpr int kTileWarps = 16;
 constexpr int kTileRows = 4 * kTileWarps;  // 64
 constexpr int kTileCols = 128;
 
+// Boundary of the box beyond the closed walls: an open top (exterior at
+// phi = 0) and the bottom-boundary v faces of columns [x0, x1) under fluid
+// cells with a prescribed (inflow) velocity.  All zero: a closed box.
+struct Boundary {
+    int32_t open_top;
+    int32_t x0, x1;
+};
+
+__host__ __device__ inline Boundary boundary_of(const hp_project_params& p)
+{
+    return Boundary{p.open_top, p.inflow_x0, p.inflow_x1};
+}
+
 // Per-grid state of one projection, device resident.
 struct GridState {
     int32_t active;      // 1 while the grid still sweeps
@@ -195,7 +208,7 @@ bool shape_ok(hp_shape s);
 
 // kernels launched from the API layer
 hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
-                          float* div, hp_shape s, cudaStream_t st);
+                          float* div, hp_shape s, cudaStream_t st, Boundary bc = Boundary{});
 hp_status launch_mask(const uint8_t* flags, uint8_t* mask, hp_shape s, cudaStream_t st);
 // out = (phi + J(phi)) / 2, J one masked Jacobi sweep on the right-hand side div
 hp_status launch_mean_sweep(const float* phi, const float* div, const uint8_t* mask, float* out,

@@ -27,10 +27,12 @@ namespace hp {
 // --------------------------------------------------------- mask + divergence
 
 // One thread per cell.  mask (optional) receives the open-face bits, div
-// (optional) the forward-difference divergence over open faces (Eq. 3).
+// (optional) the forward-difference divergence over open faces (Eq. 3); with
+// an open top the top faces of fluid cells of row 0 are open, and the
+// prescribed inflow faces of the bottom boundary enter the divergence.
 __global__ void mask_div_kernel(const float* __restrict__ u, const float* __restrict__ v,
                                 const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask,
-                                float* __restrict__ div, int ny, int nx)
+                                float* __restrict__ div, int ny, int nx, Boundary bc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
@@ -42,7 +44,7 @@ __global__ void mask_div_kernel(const float* __restrict__ u, const float* __rest
     if (fl[c] == 0) {
         if (i > 0 && fl[c - 1] == 0) m |= 1u;
         if (i < nx - 1 && fl[c + 1] == 0) m |= 2u;
-        if (j > 0 && fl[c - nx] == 0) m |= 4u;
+        if (j > 0 ? fl[c - nx] == 0 : bc.open_top != 0) m |= 4u;
         if (j < ny - 1 && fl[c + nx] == 0) m |= 8u;
     }
     if (mask) mask[(size_t)b * ny * nx + c] = (uint8_t)m;
@@ -51,17 +53,18 @@ __global__ void mask_div_kernel(const float* __restrict__ u, const float* __rest
         const float* vb = v + (size_t)b * (ny + 1) * nx;
         const float ue = (m & 2u) ? ub[i + 1] : 0.0f;
         const float uw = (m & 1u) ? ub[i] : 0.0f;
-        const float vs = (m & 8u) ? vb[(size_t)(j + 1) * nx + i] : 0.0f;
+        const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && fl[c] == 0;
+        const float vs = ((m & 8u) || inflow) ? vb[(size_t)(j + 1) * nx + i] : 0.0f;
         const float vn = (m & 4u) ? vb[(size_t)j * nx + i] : 0.0f;
         div[(size_t)b * ny * nx + c] = __fadd_rn(__fsub_rn(ue, uw), __fsub_rn(vs, vn));
     }
 }
 
 hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
-                          float* div, hp_shape s, cudaStream_t st)
+                          float* div, hp_shape s, cudaStream_t st, Boundary bc)
 {
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
-    mask_div_kernel<<<grd, blk, 0, st>>>(u, v, flags, mask, div, s.ny, s.nx);
+    mask_div_kernel<<<grd, blk, 0, st>>>(u, v, flags, mask, div, s.ny, s.nx, bc);
     return check_launch();
 }
 
@@ -544,11 +547,15 @@ __global__ void __launch_bounds__(kS1Rows * 32) sweep1_kernel(SweepArgs a)
 
 // One thread per cell: corrects its west (u[j][i]) and north (v[j][i]) faces,
 // zeroes the closed domain faces u[j][nx] and v[ny][i], writes p = phi*scale.
+// u = u* - grad phi on open faces, 0 on closed faces (Eq. 2); with an open
+// top its faces take the exterior value phi = 0, and prescribed inflow faces
+// keep their velocity.
 __global__ void correct_kernel(float* __restrict__ u, float* __restrict__ v,
-                               const uint8_t* __restrict__ mask, const float* __restrict__ phi0,
+                               const uint8_t* __restrict__ mask,
+                               const uint8_t* __restrict__ flags, const float* __restrict__ phi0,
                                const float* __restrict__ phi1, const GridState* __restrict__ gs,
                                float* __restrict__ p_out, float* __restrict__ phi_out,
-                               float scale, int ny, int nx)
+                               float scale, int ny, int nx, Boundary bc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
@@ -564,11 +571,14 @@ __global__ void correct_kernel(float* __restrict__ u, float* __restrict__ v,
         float* vb = v + (size_t)b * (ny + 1) * nx;
         float uw = 0.0f, vn = 0.0f;
         if (m & 1u) uw = __fsub_rn(ub[i], __fsub_rn(pc, ph[c - 1]));
-        if (m & 4u) vn = __fsub_rn(vb[(size_t)j * nx + i], __fsub_rn(pc, ph[c - nx]));
+        if (m & 4u)
+            vn = __fsub_rn(vb[(size_t)j * nx + i], __fsub_rn(pc, j > 0 ? ph[c - nx] : 0.0f));
         ub[i] = uw;
         vb[(size_t)j * nx + i] = vn;
         if (i == nx - 1) ub[nx] = 0.0f;
-        if (j == ny - 1) vb[(size_t)ny * nx + i] = 0.0f;
+        if (j == ny - 1 &&
+            !(i >= bc.x0 && i < bc.x1 && flags[(size_t)b * ny * nx + c] == 0))
+            vb[(size_t)ny * nx + i] = 0.0f;
     }
     if (p_out) p_out[gb + c] = __fmul_rn(pc, scale);
     if (phi_out) phi_out[gb + c] = pc;
@@ -578,11 +588,13 @@ __global__ void correct_kernel(float* __restrict__ u, float* __restrict__ v,
 
 // One thread per cell: |div u| over open faces, FP32 per thread and warp, FP64
 // per block into partial[b][block]; max via an atomic on the float bits.
+// (flags is always given; mask may be null, the closed box's open faces are
+// then taken from the flags)
 __global__ void div_norms_kernel(const float* __restrict__ u, const float* __restrict__ v,
                                  const uint8_t* __restrict__ flags,
                                  const uint8_t* __restrict__ mask, double* __restrict__ partial,
                                  uint32_t* __restrict__ einf_bits, size_t einf_stride, int ny,
-                                 int nx)
+                                 int nx, Boundary bc)
 {
     __shared__ float s_w[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -608,7 +620,9 @@ __global__ void div_norms_kernel(const float* __restrict__ u, const float* __res
         const float* vb = v + (size_t)b * (ny + 1) * nx;
         const float ue = (m & 2u) ? ub[i + 1] : 0.0f;
         const float uw = (m & 1u) ? ub[i] : 0.0f;
-        const float vs = (m & 8u) ? vb[(size_t)(j + 1) * nx + i] : 0.0f;
+        const bool inflow =
+            j == ny - 1 && i >= bc.x0 && i < bc.x1 && flags[(size_t)b * ny * nx + c] == 0;
+        const float vs = ((m & 8u) || inflow) ? vb[(size_t)(j + 1) * nx + i] : 0.0f;
         const float vn = (m & 4u) ? vb[(size_t)j * nx + i] : 0.0f;
         a = fabsf(__fadd_rn(__fsub_rn(ue, uw), __fsub_rn(vs, vn)));
     }
@@ -674,7 +688,7 @@ hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, nullptr, partial, einf_bits, stride, s.ny,
-                                          s.nx);
+                                          s.nx, Boundary{});
     if ((rc = check_launch()) != HP_OK) return rc;
     norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
         partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
@@ -694,7 +708,7 @@ hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, nullptr, partial, einf_bits, stride, s.ny,
-                                          s.nx);
+                                          s.nx, Boundary{});
     if ((rc = check_launch()) != HP_OK) return rc;
     norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
         partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
@@ -907,7 +921,7 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     hp_status rc = HP_OK;
     if (u && !have_div) {
         // without a velocity the caller has prepared ctx->mask and ctx->div
-        rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st);
+        rc = launch_mask_div(u, v, flags, ctx->mask, ctx->div, s, st, boundary_of(*prm));
         if (rc != HP_OK) return rc;
     }
     init_phi_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(phi0, ctx->mask, ctx->phi[0],
@@ -939,8 +953,9 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
 
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
     const float scale = prm->rho0 / prm->dt;
-    correct_kernel<<<grd, blk, 0, st>>>(u, v, ctx->mask, ctx->phi[0], ctx->phi[1], ctx->gs, p_out,
-                                        phi_copy_out, scale, s.ny, s.nx);
+    const Boundary bc = boundary_of(*prm);
+    correct_kernel<<<grd, blk, 0, st>>>(u, v, ctx->mask, flags, ctx->phi[0], ctx->phi[1], ctx->gs,
+                                        p_out, phi_copy_out, scale, s.ny, s.nx, bc);
     if ((rc = check_launch()) != HP_OK) return rc;
 
     // norms of the corrected velocity; the einf word lives in GridState
@@ -949,8 +964,8 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     uint32_t* einf_bits = &ctx->gs[0].einf_bits;
     const size_t stride = sizeof(GridState) / sizeof(uint32_t);
     if (u) {
-        div_norms_kernel<<<grd, blk, 0, st>>>(u, v, nullptr, ctx->mask, ctx->partial2, einf_bits,
-                                              stride, s.ny, s.nx);
+        div_norms_kernel<<<grd, blk, 0, st>>>(u, v, flags, ctx->mask, ctx->partial2, einf_bits,
+                                              stride, s.ny, s.nx, bc);
         if ((rc = check_launch()) != HP_OK) return rc;
     }
     norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(

@@ -38,7 +38,7 @@ def test_status_strings(lib):
 def test_argument_errors_are_returned_before_any_launch(lib):
     # null context / pointers are rejected on the host
     s = hp.hp_shape(1, 4, 4)
-    prm = hp.hp_project_params(1e-3, 10, 0, 1.0, 1.0, 0, 1, 0)
+    prm = hp.hp_project_params(1e-3, 10, 0, 1.0, 1.0, 0, 1, 0, 0, 0, 0)
     rc = lib.hp_project(None, None, None, None, s, ctypes.byref(prm), None, None, None, None,
                         None, None, None, 0, None)
     assert rc == 1
@@ -90,8 +90,9 @@ def test_ctypes_structures_match_the_header(tmp_path):
         "int main(void) {\n"
         '  printf("%zu %zu %zu %zu\\n", sizeof(hp_shape), sizeof(hp_project_params),\n'
         "         sizeof(hp_plume_params), sizeof(hp_train_params));\n"
-        '  printf("%zu %zu %zu\\n", offsetof(hp_plume_params, scheme),\n'
-        "         offsetof(hp_project_params, fixed_iters), offsetof(hp_train_params, lambda_div));\n"
+        '  printf("%zu %zu %zu %zu %zu\\n", offsetof(hp_plume_params, scheme),\n'
+        "         offsetof(hp_project_params, fixed_iters), offsetof(hp_train_params, lambda_div),\n"
+        "         offsetof(hp_project_params, inflow_x1), offsetof(hp_plume_params, open_top));\n"
         "  return 0; }\n")
     exe = tmp_path / "layout"
     r = subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], capture_output=True,
@@ -103,7 +104,8 @@ def test_ctypes_structures_match_the_header(tmp_path):
     assert sizes == [ctypes.sizeof(hp.hp_shape), ctypes.sizeof(hp.hp_project_params),
                      ctypes.sizeof(hp.hp_plume_params), ctypes.sizeof(hp.hp_train_params)]
     assert offs == [hp.hp_plume_params.scheme.offset, hp.hp_project_params.fixed_iters.offset,
-                    hp.hp_train_params.lambda_div.offset]
+                    hp.hp_train_params.lambda_div.offset, hp.hp_project_params.inflow_x1.offset,
+                    hp.hp_plume_params.open_top.offset]
 
 
 def test_architecture_numbers_match_the_header(tmp_path):
