@@ -281,19 +281,23 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     """CNN-hybrid projection of the same grids to the same threshold, with the
     MultiScale, the SmallScale and the MonoScale network (Sec. 3.1).
 
-    Untimed set-up: training pairs from the plain solver (128^2, vortex field +
-    divergence sources + 0-4 obstacles), Adam training of each network on the
-    GPU with the same pairs and schedule.  Timed: the same per-step protocol
-    as the plain arm (device restore of u*, L2 flush between steps, CUDA
-    events)."""
+    Untimed set-up (config 5's recipe): training pairs from the plain solver
+    (128^2, vortex field + divergence sources + 0-4 obstacles), Adam training
+    of each network on the GPU with the same pairs and schedule (batch 64,
+    lr 1e-3).  Timed: the same per-step protocol as the plain arm (device
+    restore of u*, L2 flush between steps, CUDA events).  Then, with the same
+    networks, BASELINE's configs 3 and 5 at their sizes (plume_eval)."""
     import torch
     from paper_2109_09363_gb300 import training as T
+    from paper_2109_09363_gb300 import workloads as W
     t0 = time.perf_counter()
     n_tr = 128
-    data = T.generate_pairs(2048, n_tr, seed0=0, sweeps=TRAIN_SWEEPS, device=u0.device)
+    data = T.generate_pairs(args.train_pairs, n_tr, seed0=0, sweeps=TRAIN_SWEEPS,
+                            device=u0.device)
+    torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
-    batch = 32
-    epochs = max(1, (args.train_steps * batch + 2047) // 2048)
+    batch = 64
+    epochs = args.train_epochs
     trained, train_info = {}, {}
     for arch in NETWORKS:
         t1 = time.perf_counter()
@@ -402,8 +406,8 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
                                          "cap": CAP_UNCAPPED, "steps": UNCAPPED_STEPS,
                                          "speedup": uncapped_plain["ms_per_step"] /
                                          unc["ms_per_step"]},
-            "training": dict(train_info[arch], pairs=2048, grid=[n_tr, n_tr],
-                             target_sweeps=TRAIN_SWEEPS, batch=batch,
+            "training": dict(train_info[arch], pairs=args.train_pairs, grid=[n_tr, n_tr],
+                             target_sweeps=TRAIN_SWEEPS, batch=batch, epochs=epochs,
                              pair_generation_seconds=t_pairs)}
         net.close()
     ms_arm = arms.pop("multiscale")
@@ -422,6 +426,9 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
         ms_arm[arch] = arms[arch]
         ms_arm[arch]["t_inf_over_multiscale"] = (arms[arch]["t_inf_ms_16_grids"] /
                                                  ms_arm["t_inf_ms_16_grids"])
+    if not args.no_baseline_configs:
+        torch.cuda.empty_cache()
+        ms_arm["baseline_configs"] = baseline_configs(hp, trained, u0.device)
     return ms_arm
 
 
@@ -657,34 +664,15 @@ def plume_eval(hp, nets, dev, n, steps, flags_np, inlet, literal_thr=1e-3, liter
     return res
 
 
-def run_baseline_plumes(hp, dev, pairs=10000, epochs=20, batch=64):
-    """BASELINE's configs 3 and 5 at their sizes, with the networks trained
-    by config 5's recipe: `pairs` 128^2 pairs from the plain solver (the
-    training distribution of the hybrid arm), Adam lr 1e-3, batch 64, 20
-    epochs, every network.  Config 3: the 1024^2 plume (inlet 128 cells) with
-    a solid disc of radius 64 centred 256 cells above the inlet, 200 steps;
-    config 5's evaluation: the 2048^2 plume (inlet 256 cells) with 8
-    non-overlapping discs of radius U(32, 128), 500 steps (plume_eval)."""
-    import torch
-    from paper_2109_09363_gb300 import training as T
+def baseline_configs(hp, nets, dev):
+    """BASELINE's configs 3 and 5 at their sizes with the trained networks
+    (nets: architecture -> parameters).  Config 3: the 1024^2 plume (inlet
+    128 cells) with a solid disc of radius 64 centred 256 cells above the
+    inlet, 200 steps; config 5's evaluation: the 2048^2 plume (inlet 256
+    cells) with 8 non-overlapping discs of radius U(32, 128), 500 steps
+    (plume_eval: the literal E_t = 1e-3 and the paper's per-step rule)."""
     from paper_2109_09363_gb300 import workloads as W
-    t0 = time.perf_counter()
-    data = T.generate_pairs(pairs, 128, seed0=0, sweeps=TRAIN_SWEEPS, device=dev)
-    torch.cuda.synchronize()
-    res = {"training": {"pairs": pairs, "grid": [128, 128], "target_sweeps": TRAIN_SWEEPS,
-                        "batch": batch, "epochs": epochs,
-                        "pair_generation_seconds": time.perf_counter() - t0}}
-    nets = {}
-    for arch in NETWORKS:
-        t1 = time.perf_counter()
-        cnn = hp.CNN(batch, 128, 128, params=T.init_params(seed=1, arch=arch), arch=arch)
-        losses = T.train(cnn, data, epochs=epochs, batch=batch, lr=1e-3, lambda_div=1.0)
-        nets[arch] = cnn.get_params()
-        cnn.close()
-        res["training"][arch] = {"steps": len(losses), "seconds": time.perf_counter() - t1,
-                                 "final_loss": float(np.mean(losses[-20:]))}
-    del data
-    torch.cuda.empty_cache()
+    res = {}
     n3 = 1024
     fl3 = W.plume_flags(n3, cylinder_radius=64, cylinder_height=256)
     res["config3"] = plume_eval(hp, nets, dev, n3, 200, fl3, W.inlet_columns(n3))
@@ -1003,12 +991,13 @@ def main():
                     help="skip the CNN-hybrid arm (training + timing)")
     ap.add_argument("--no-pdnn", action="store_true",
                     help="skip the timing of physics-driven training steps")
-    ap.add_argument("--train-steps", type=int, default=1200,
-                    help="Adam steps of the network trained for the hybrid arm")
-    ap.add_argument("--baseline-plumes", action="store_true",
-                    help="only run BASELINE's configs 3 and 5 at their sizes (1024^2 and "
-                         "2048^2 plumes, networks trained by config 5's recipe) and print "
-                         "their JSON")
+    ap.add_argument("--train-pairs", type=int, default=10000,
+                    help="training pairs (128^2) of the networks of the hybrid arm")
+    ap.add_argument("--train-epochs", type=int, default=20,
+                    help="epochs (batch 64) of the networks of the hybrid arm")
+    ap.add_argument("--no-baseline-configs", action="store_true",
+                    help="skip BASELINE's configs 3 and 5 (1024^2 and 2048^2 plumes) in the "
+                         "hybrid arm")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the sweep blocks from a host-polled loop instead of the "
                          "CUDA-graph conditional loop (same kernels; ncu cannot profile kernel "
@@ -1028,16 +1017,6 @@ def main():
         return profile_cnn_scaling()
     if args.profile_train:
         return profile_train(*args.profile_train)
-    if args.baseline_plumes:
-        import torch
-        import __graft_entry__
-        __graft_entry__.build()
-        import paper_2109_09363_gb300 as hp
-        dev = torch.device("cuda", 0)
-        torch.cuda.set_device(dev)
-        print(json.dumps({"mode": "baseline_plumes",
-                          **run_baseline_plumes(hp, dev)}), flush=True)
-        return 0
 
     import torch
     import torch.distributed as dist
@@ -1297,6 +1276,18 @@ def main():
                 "others": {a: {"equal_threshold": hybrid[a]["equal_threshold_uncapped"]["speedup"],
                                "capped": hybrid[a]["speedup_vs_plain"]}
                            for a in NETWORKS[1:] if a in hybrid}}
+            bc = hybrid.get("baseline_configs")
+            if bc:
+                # projection time of the hybrid against plain Jacobi on the
+                # plumes of configs 3 and 5 (literal E_t, and the paper's rule)
+                line["hybrid_vs_plain"]["plumes"] = {
+                    c: {"literal_multiscale": bc[c]["literal"]["hybrid_multiscale"][
+                            "speedup_vs_plain"],
+                        "paper_rule": {a: bc[c]["paper_rule"]["hybrid_" + a]["speedup_vs_plain"]
+                                       for a in NETWORKS},
+                        "plain_sweeps_mean_paper_rule": bc[c]["paper_rule"]["plain"][
+                            "sweeps_mean"]}
+                    for c in ("config3", "config5")}
         if pdnn is not None:
             line["pdnn_training"] = pdnn
         line["driver_step"] = driver
