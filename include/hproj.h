@@ -50,6 +50,8 @@ typedef enum {
     HP_ERR_TIMEOUT = 7,     /* a tensor-core completion wait gave up (hp_cnn_check) */
     HP_ERR_IO = 8,          /* a checkpoint file could not be written, or is missing,
                                truncated, corrupted or of another format version */
+    HP_ERR_GUARD = 9,       /* a workspace's guard zone was overwritten (hp_ctx_check,
+                               hp_cnn_check, hp_trainer_check) */
     /* not an error: the network's guess of some grid was not finite, and the
      * hybrid projection started that grid's sweeps from zero (hp_cnn_check) */
     HP_WARN_CNN_NONFINITE = 100
@@ -123,6 +125,13 @@ typedef struct hp_ctx hp_ctx;
  * sm_103. */
 hp_status hp_ctx_create(hp_ctx **ctx, hp_shape max_shape, int device);
 void hp_ctx_destroy(hp_ctx *ctx);
+/* Memory check of a context (a substitute for a memory checker): every
+ * device workspace of a context, a network and a trainer is allocated 256
+ * bytes longer and those guard bytes hold a fixed pattern; this call
+ * synchronises the device and returns HP_ERR_GUARD if a kernel wrote into a
+ * guard zone (past the end of a workspace), HP_ERR_CUDA on a pending CUDA
+ * error, else HP_OK. */
+hp_status hp_ctx_check(hp_ctx *ctx);
 
 const char *hp_status_string(hp_status s);
 const char *hp_last_cuda_error(void);
@@ -339,8 +348,9 @@ hp_status hp_cnn_set_params(hp_cnn *cnn, const float *params, int64_t n);
  * that it replaced a non-finite guess.  This call synchronises the device,
  * reads and clears that word: HP_ERR_TIMEOUT if a wait gave up since the last
  * check (in hp_cnn_forward, hp_project_hybrid or a trainer built on the
- * network), else HP_WARN_CNN_NONFINITE if a hybrid projection fell back to a
- * zero guess, else HP_OK. */
+ * network), else HP_ERR_GUARD if a guard zone of the network's workspaces was
+ * overwritten (as hp_ctx_check), else HP_WARN_CNN_NONFINITE if a hybrid
+ * projection fell back to a zero guess, else HP_OK. */
 hp_status hp_cnn_check(hp_cnn *cnn);
 /* Polls of each bounded pipeline wait (copies and MMAs of the warp-
  * specialised convolution and weight-gradient kernels, images from 32 pixels
@@ -427,6 +437,9 @@ hp_status hp_trainer_pdnn_step(hp_trainer *trainer, const float *div, const uint
  * returns them); synchronises the device and then reports the network's
  * device status as hp_cnn_check does (the masters are copied either way). */
 hp_status hp_trainer_sync_params(hp_trainer *trainer);
+/* The guard zones of a trainer's workspaces (as hp_ctx_check), then
+ * hp_cnn_check of its network. */
+hp_status hp_trainer_check(hp_trainer *trainer);
 
 /* Optimiser state of a trainer, copied to HOST memory (synchronous): the FP32
  * masters, the first and second Adam moments (float [the network's parameter

@@ -51,6 +51,8 @@ _P = ctypes.c_void_p
 _SIGS = {
     "hp_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), hp_shape, ctypes.c_int]),
     "hp_ctx_destroy": (None, [_P]),
+    "hp_ctx_check": (ctypes.c_int, [_P]),
+    "hp_trainer_check": (ctypes.c_int, [_P]),
     "hp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hp_last_cuda_error": (ctypes.c_char_p, []),
     "hp_face_mask": (ctypes.c_int, [_P, _P, hp_shape, _P]),
@@ -176,6 +178,11 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+    def check(self):
+        """Raise if a kernel wrote into a guard zone past one of this
+        context's workspaces (synchronises the device)."""
+        _check(load_library().hp_ctx_check(self._h))
 
     def close(self):
         if self._h:
@@ -571,6 +578,13 @@ class Trainer:
 
     def sync_params(self):
         _check(load_library().hp_trainer_sync_params(self._h))
+
+    def check(self):
+        """Raise on overwritten guard zones of the trainer's or its network's
+        workspaces or a timed-out wait (synchronises the device)."""
+        rc = load_library().hp_trainer_check(self._h)
+        if rc != HP_WARN_CNN_NONFINITE:
+            _check(rc)
 
     def state(self):
         """(masters, m, v, step): the FP32 masters, the Adam moments (numpy,

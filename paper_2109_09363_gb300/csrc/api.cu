@@ -54,13 +54,44 @@ bool project_args_ok(const hp_ctx* c, const float* u, const float* v, const uint
     return (e_hist == nullptr) == (hist_len <= 0);
 }
 
-template <typename T>
-static hp_status dalloc(T** p, size_t n)
+cudaError_t guarded_malloc(void** p, size_t bytes, Guards* g)
 {
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes + kGuardBytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    unsigned char* b = (unsigned char*)*p;
+    e = cudaMemset(b, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(b + bytes, kGuardByte, kGuardBytes);
+    if (e == cudaSuccess && g) g->zones.push_back(b + bytes);
+    return e;
+}
+
+hp_status check_guards(const Guards& g)
+{
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned char buf[kGuardBytes];
+    for (size_t k = 0; e == cudaSuccess && k < g.zones.size(); ++k) {
+        e = cudaMemcpy(buf, g.zones[k], kGuardBytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) break;
+        for (size_t i = 0; i < kGuardBytes; ++i)
+            if (buf[i] != (unsigned char)kGuardByte) return HP_ERR_GUARD;
+    }
     if (e != cudaSuccess) {
         set_cuda_error(e);
-        *p = nullptr;
+        return HP_ERR_CUDA;
+    }
+    return HP_OK;
+}
+
+template <typename T>
+static hp_status dalloc(T** p, size_t n, Guards* g)
+{
+    cudaError_t e = guarded_malloc((void**)p, n * sizeof(T), g);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
         return e == cudaErrorMemoryAllocation ? HP_ERR_OOM : HP_ERR_CUDA;
     }
     return HP_OK;
@@ -83,6 +114,7 @@ const char* hp_status_string(hp_status s)
     case HP_ERR_UNSUPPORTED: return "unsupported";
     case HP_ERR_TIMEOUT: return "a tensor-core wait timed out";
     case HP_ERR_IO: return "checkpoint file error";
+    case HP_ERR_GUARD: return "a workspace guard zone was overwritten";
     case HP_WARN_CNN_NONFINITE:
         return "warning: a network guess was not finite; its grids started from zero";
     }
@@ -109,7 +141,7 @@ void hp_ctx_destroy(hp_ctx* c)
     cudaFree(c->ls);
     if (c->host_flag) cudaFreeHost(c->host_flag);
     if (prev >= 0) cudaSetDevice(prev);
-    free(c);
+    delete c;
 }
 
 hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
@@ -127,8 +159,7 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
     }
     e = cudaSetDevice(device);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
-    hp_ctx* c = (hp_ctx*)calloc(1, sizeof(hp_ctx));
-    if (!c) return HP_ERR_OOM;
+    hp_ctx* c = new hp_ctx();
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
     c->max_shape = mx;
@@ -144,14 +175,14 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
     }
     c->partial2_len = (size_t)mx.batch * ((mx.nx + 255) / 256) * mx.ny;
     hp_status rc;
-    if ((rc = dalloc(&c->mask, c->max_cells)) != HP_OK ||
-        (rc = dalloc(&c->div, c->max_cells)) != HP_OK ||
-        (rc = dalloc(&c->phi[0], c->max_cells)) != HP_OK ||
-        (rc = dalloc(&c->phi[1], c->max_cells)) != HP_OK ||
-        (rc = dalloc(&c->ckpt, c->max_cells)) != HP_OK ||
-        (rc = dalloc(&c->partial, c->partial_len)) != HP_OK ||
-        (rc = dalloc(&c->partial2, c->partial2_len)) != HP_OK ||
-        (rc = dalloc(&c->gs, (size_t)mx.batch)) != HP_OK || (rc = dalloc(&c->ls, 1)) != HP_OK) {
+    if ((rc = dalloc(&c->mask, c->max_cells, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->div, c->max_cells, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->phi[0], c->max_cells, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->phi[1], c->max_cells, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->ckpt, c->max_cells, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->partial, c->partial_len, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->partial2, c->partial2_len, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->gs, (size_t)mx.batch, &c->guards)) != HP_OK || (rc = dalloc(&c->ls, 1, &c->guards)) != HP_OK) {
         hp_ctx_destroy(c);
         return rc;
     }
@@ -175,6 +206,12 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
     }
     *out = c;
     return HP_OK;
+}
+
+hp_status hp_ctx_check(hp_ctx* c)
+{
+    if (!c) return HP_ERR_INVALID_ARG;
+    return check_guards(c->guards);
 }
 
 hp_status hp_face_mask(const uint8_t* flags, uint8_t* mask_out, hp_shape s, void* stream)

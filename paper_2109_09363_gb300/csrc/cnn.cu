@@ -522,6 +522,7 @@ __global__ void phi0_kernel(const float* __restrict__ out, const float* __restri
 using namespace hp;
 
 struct hp_cnn {
+    Guards guards;          // guard zones of the workspaces
     int arch;               // hp_cnn_arch
     const LayerSpec* spec;  // its layer table
     int nlayers;
@@ -808,38 +809,40 @@ hp_status hp_cnn_create_arch(hp_cnn** out, int32_t arch, hp_shape mx, int device
     c->master.assign((size_t)hp_cnn_arch_param_count(arch), 0.0f);
     const size_t px = (size_t)mx.batch * mx.ny * mx.nx;
     bool okm = true;
+    // every buffer with a guard zone (checked by hp_cnn_check)
+    auto ga = [&](auto pp, size_t bytes) {
+        return guarded_malloc((void**)pp, bytes, &c->guards);
+    };
     for (int l = 0; l < c->nlayers && okm; ++l) {
         const LayerSpec& ls = c->spec[l];
         const size_t wb = dev_wcount(c->spec, l) * (ls.cin >= 32 && ls.cout >= 32 ? 2 : 4);
-        okm = cudaMalloc(&c->w[l], wb) == cudaSuccess &&
-              cudaMalloc((void**)&c->bias[l], c->spec[l].cout * sizeof(float)) == cudaSuccess;
+        okm = ga(&c->w[l], wb) == cudaSuccess &&
+              ga((void**)&c->bias[l], c->spec[l].cout * sizeof(float)) == cudaSuccess;
         if (okm) {
             cudaMemset(c->w[l], 0, wb);
             cudaMemset(c->bias[l], 0, c->spec[l].cout * sizeof(float));
         }
     }
-    okm = okm && cudaMalloc((void**)&c->act[0], px * 64 * 2) == cudaSuccess &&
-          cudaMalloc((void**)&c->act[1], px * 64 * 2) == cudaSuccess &&
-
-          cudaMalloc((void**)&c->xin, px * 3 * sizeof(float)) == cudaSuccess &&
-          cudaMalloc((void**)&c->x16, px * 16 * 2) == cudaSuccess &&
-          cudaMalloc((void**)&c->s_part, (size_t)mx.batch * kScaleCtas * sizeof(double)) ==
+    okm = okm && ga((void**)&c->act[0], px * 64 * 2) == cudaSuccess &&
+          ga((void**)&c->act[1], px * 64 * 2) == cudaSuccess &&
+          ga((void**)&c->xin, px * 3 * sizeof(float)) == cudaSuccess &&
+          ga((void**)&c->x16, px * 16 * 2) == cudaSuccess &&
+          ga((void**)&c->s_part, (size_t)mx.batch * kScaleCtas * sizeof(double)) ==
               cudaSuccess &&
-          cudaMalloc((void**)&c->s_cnt,
-                     (size_t)mx.batch * kScaleCtas * sizeof(unsigned long long)) == cudaSuccess &&
-          cudaMalloc((void**)&c->s, mx.batch * sizeof(float)) == cudaSuccess &&
-          cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess &&
-          cudaMalloc((void**)&c->guess_bad, mx.batch * sizeof(int32_t)) == cudaSuccess;
+          ga((void**)&c->s_cnt, (size_t)mx.batch * kScaleCtas * sizeof(unsigned long long)) ==
+              cudaSuccess &&
+          ga((void**)&c->s, mx.batch * sizeof(float)) == cudaSuccess &&
+          ga((void**)&c->err, sizeof(int)) == cudaSuccess &&
+          ga((void**)&c->guess_bad, mx.batch * sizeof(int32_t)) == cudaSuccess;
     for (int k = 0; k < c->br.n && okm; ++k)
-        okm = cudaMalloc((void**)&c->out[k],
-                         px / ((size_t)c->br.scale[k] * c->br.scale[k]) * 4 + 16) ==
+        okm = ga((void**)&c->out[k], px / ((size_t)c->br.scale[k] * c->br.scale[k]) * 4) ==
                   cudaSuccess &&
-              cudaMalloc((void**)&c->wtc_first[k], 9 * 32 * 16 * 2) == cudaSuccess &&
-              cudaMalloc((void**)&c->wtc_last[k], 9 * 16 * 32 * 2) == cudaSuccess &&
-              cudaMalloc((void**)&c->btc_last[k], 16 * sizeof(float)) == cudaSuccess;
+              ga((void**)&c->wtc_first[k], 9 * 32 * 16 * 2) == cudaSuccess &&
+              ga((void**)&c->wtc_last[k], 9 * 16 * 32 * 2) == cudaSuccess &&
+              ga((void**)&c->btc_last[k], 16 * sizeof(float)) == cudaSuccess;
     if (arch == HP_CNN_UNET)
         for (int k = 0; k < 4 && okm; ++k)
-            okm = cudaMalloc((void**)&c->skip[k], (px >> (2 * k)) * 32 * 2) == cudaSuccess;
+            okm = ga((void**)&c->skip[k], (px >> (2 * k)) * 32 * 2) == cudaSuccess;
     if (!okm) {
         set_cuda_error(cudaGetLastError());
         hp_cnn_destroy(c);
@@ -1876,6 +1879,7 @@ struct hp_trainer {
     double* loss;
     uint8_t* mask;
     int step;
+    Guards guards;  // guard zones of the workspaces
     // Unet: the max-pooled and concatenated layer inputs, the skip features'
     // gradients from the decoder, the 3 x 3 gradient of the 1 x 1 layer
     __nv_bfloat16* upool[5];
@@ -1932,7 +1936,6 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
         return HP_ERR_INVALID_ARG;
     *out = nullptr;
     hp_trainer* t = new hp_trainer();
-    memset(t, 0, sizeof(*t));
     t->cnn = cnn;
     t->max = mx;
     t->param_count = hp_cnn_arch_param_count(cnn->arch);
@@ -1940,8 +1943,7 @@ hp_status hp_trainer_create(hp_trainer** out, hp_cnn* cnn, hp_shape mx)
     const size_t P = (size_t)mx.batch * mx.ny * mx.nx;
     bool ok = true;
     auto al = [&](void** p, size_t bytes) {
-        if (ok && cudaMalloc(p, bytes + 16) != cudaSuccess) ok = false;
-        if (ok) cudaMemset(*p, 0, bytes + 16);
+        if (ok && guarded_malloc(p, bytes, &t->guards) != cudaSuccess) ok = false;
     };
     al((void**)&t->master, t->param_count * 4);
     al((void**)&t->grad, t->param_count * 4);
@@ -2712,7 +2714,18 @@ hp_status hp_cnn_check(hp_cnn* c)
     if (e == cudaSuccess) e = cudaMemcpy(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && flag) e = cudaMemset(c->err, 0, sizeof(int));
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
-    return (flag & 1) ? HP_ERR_TIMEOUT : (flag & 2) ? HP_WARN_CNN_NONFINITE : HP_OK;
+    if (flag & 1) return HP_ERR_TIMEOUT;
+    const hp_status g = check_guards(c->guards);
+    if (g != HP_OK) return g;
+    return (flag & 2) ? HP_WARN_CNN_NONFINITE : HP_OK;
+}
+
+hp_status hp_trainer_check(hp_trainer* t)
+{
+    if (!t) return HP_ERR_INVALID_ARG;
+    const hp_status g = check_guards(t->guards);
+    if (g != HP_OK) return g;
+    return hp_cnn_check(t->cnn);
 }
 
 }  // extern "C"

@@ -77,6 +77,20 @@ struct SweepArgs {
     unsigned long long cond;     // CUDA-graph conditional handle (0 = none)
 };
 
+// Guard zones (a substitute for a memory checker): every device workspace
+// of a context, a network and a trainer is allocated kGuardBytes longer and
+// the extra bytes are filled with kGuardByte; the check calls compare them,
+// so a kernel that writes past the end of a workspace is reported.
+constexpr size_t kGuardBytes = 256;
+constexpr int kGuardByte = 0xA5;
+struct Guards {
+    std::vector<unsigned char*> zones;  // device address of each guard zone
+};
+// cudaMalloc(bytes + kGuardBytes), zero the buffer, fill its guard zone
+cudaError_t guarded_malloc(void** p, size_t bytes, Guards* g);
+// synchronous: HP_ERR_GUARD if a guard byte changed, HP_ERR_CUDA on a CUDA error
+hp_status check_guards(const Guards& g);
+
 // Contents of a network checkpoint file (checkpoint.cu).
 struct CkptData {
     int32_t arch = -1;
@@ -91,6 +105,7 @@ hp_status ckpt_read(const char* path, CkptData* d);
 }  // namespace hp
 
 struct hp_ctx {
+    hp::Guards guards;
     int device;
     int num_sms;
     hp_shape max_shape;
