@@ -925,9 +925,10 @@ def profile_cnn_scaling(sizes=(32, 64, 128, 256, 512, 1024, 2048)) -> int:
     return 0
 
 
-def profile_train(batch, n, norm=1) -> int:
+def profile_train(batch, n, norm=1, arch="multiscale") -> int:
     """Time the physics-driven loss gradient (network forward, loss, backward)
-    on BATCH training-distribution grids of N x N, after 3 untimed calls."""
+    of the network `arch` on BATCH training-distribution grids of N x N,
+    after 3 untimed calls."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -939,7 +940,7 @@ def profile_train(batch, n, norm=1) -> int:
     ud = torch.from_numpy(u.astype(np.float32)).to(dev)
     vd = torch.from_numpy(v.astype(np.float32)).to(dev)
     fd = torch.from_numpy(fl).to(dev)
-    cnn = hp.CNN(batch, n, n, params=T.init_params(seed=1))
+    cnn = hp.CNN(batch, n, n, params=T.init_params(seed=1, arch=arch), arch=arch)
     tr = hp.Trainer(cnn, batch, n, n)
     div = hp.hp_divergence(ud, vd, fd)
     w = torch.full((batch,), 1.0 / batch, dtype=torch.float32, device=dev)
@@ -952,9 +953,11 @@ def profile_train(batch, n, norm=1) -> int:
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 5
+    tr.check()
     # forward + two backward contractions (data and weight gradients)
-    flop = 3 * 2.0 * 190422 * batch * n * n
-    print(json.dumps({"profile_train": [batch, n], "ms": ms, "tflops": flop / ms / 1e9}))
+    flop = 3 * 2.0 * CNN_MACS_PER_PIXEL[arch] * batch * n * n
+    print(json.dumps({"profile_train": [batch, n], "arch": arch, "ms": ms,
+                      "tflops": flop / ms / 1e9}))
     return 0
 
 
@@ -983,7 +986,7 @@ def main():
     ap.add_argument("--profile-cnn-scaling", action="store_true",
                     help="only time one forward of every network on one grid of 32^2 .. 2048^2")
     ap.add_argument("--arch", default="multiscale", choices=list(FORWARD_NETWORKS),
-                    help="network of --profile-cnn")
+                    help="network of --profile-cnn and --profile-train")
     ap.add_argument("--profile-train", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the physics-driven loss gradient on BATCH grids of N x N, "
                          "8 times (a small case for ncu)")
@@ -1016,7 +1019,7 @@ def main():
     if args.profile_cnn_scaling:
         return profile_cnn_scaling()
     if args.profile_train:
-        return profile_train(*args.profile_train)
+        return profile_train(*args.profile_train, arch=args.arch)
 
     import torch
     import torch.distributed as dist
