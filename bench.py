@@ -390,6 +390,7 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
         # scale-1/2 branch and a sixteenth of the scale-1/4 branch
         flop = 2.0 * CNN_MACS_PER_PIXEL[arch] * B * N * N
         tf = flop / (t_inf * 1e-3) / 1e12
+        t_roof = cnn_layer_roofline(arch, B * N * N, float(peaks.get("hbm_gbs", 6800.0)), tpk)
         arms[arch] = {
             "params": net.n_params, "value": ws * B / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms, "speedup_vs_plain": ms_plain / ms,
@@ -401,7 +402,11 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
                              "peak_kind": "measured" if peaks else "fallback",
                              "note": "whole network forward (BF16, FP32 accumulate), "
                                      f"{2 * CNN_MACS_PER_PIXEL[arch] / 1e3:.1f} kFLOP per "
-                                     "full-resolution pixel"},
+                                     "full-resolution pixel",
+                             "layer_roofline_ms": t_roof, "frac_of_layer_roofline": t_roof / t_inf,
+                             "layer_roofline_note": "every kernel at its own bound (HBM bytes "
+                                                    "or tensor FLOPs, measured peaks), summed: "
+                                                    "most layers sit at or below the ridge"},
             "equal_threshold_uncapped": {"hybrid": unc, "plain": uncapped_plain,
                                          "cap": CAP_UNCAPPED, "steps": UNCAPPED_STEPS,
                                          "speedup": uncapped_plain["ms_per_step"] /
@@ -571,6 +576,51 @@ def compare_plume_min_threshold(hp, nets, dev, n=128, steps=300, cap=20000, refe
     if reference is not None:
         res["reference"] = "plain Jacobi with every projection stopped at E_t = 1e-5 (cap 20,000)"
     return res
+
+
+# scales (down-sampling factors) of the layers of each network, in order
+LAYER_SCALES = {"multiscale": [4] * 5 + [2] * 7 + [1] * 7, "smallscale": [4] * 5 + [2] * 7 + [1] * 7,
+                "monoscale": [1] * 9,
+                "unet": [1, 1, 2, 2, 4, 4, 8, 8, 16, 16, 16, 8, 8, 4, 4, 2, 2, 1, 1, 1]}
+
+
+def cnn_layer_roofline(arch, pixels, hbm_gbs, tflops):
+    """Roofline time of one network forward on `pixels` full-resolution
+    pixels: every kernel at its own bound, max(algorithmic bytes / HBM
+    bandwidth, FLOPs / tensor rate), summed over the kernels (no overlap
+    between kernels).  Bytes per pixel at a kernel's resolution: a 32/64-
+    channel convolution reads and writes its BF16 activations (2 B per
+    channel); a branch's first layer reads the 16-channel BF16 input (32 B),
+    its last writes FP32 (4 B); a branch input reads div and flags (5 B) of
+    the pixels it pools and writes 32 B; the scale s reads 5 B per pixel; the
+    Unet's pooling reads four 64 B pixels and writes one, its up-sampling
+    concatenation writes 128 B and reads the 64 B skip and a quarter of a
+    coarse pixel.  FLOPs: 2 x 9 x cin x cout per output pixel (1 x 1: 2 x cin)."""
+    from paper_2109_09363_gb300 import training as T
+    layers, scales = T.ARCH_LAYERS[arch], LAYER_SCALES[arch]
+    hbm, tc = hbm_gbs * 1e9, tflops * 1e12
+    t = 5.0 * pixels / hbm                          # the scale s
+    prev_cout = None
+    for (lay, sc) in zip(layers, scales):
+        cin, cout = lay[0], lay[1]
+        ks = lay[2] if len(lay) > 2 else 3
+        px = pixels / (sc * sc)
+        flops = 2.0 * ks * ks * cin * cout * px
+        if cin <= 3:                                 # branch input + first layer
+            t += (5.0 * sc * sc + 32.0) * px / hbm
+            rd = 32.0
+        elif arch == "unet" and prev_cout is not None and (sc != prev_sc):
+            if sc > prev_sc:                         # max pooling before the layer
+                t += (4 * 64.0 + 64.0) * px / hbm
+            else:                                    # up-sampling concatenation
+                t += (128.0 + 64.0 + 16.0) * px / hbm
+            rd = 2.0 * cin
+        else:
+            rd = 2.0 * cin
+        wr = 4.0 if cout == 1 else 2.0 * cout
+        t += max((rd + wr) * px / hbm, flops / tc)
+        prev_cout, prev_sc = cout, sc
+    return t * 1e3
 
 
 def plume_eval(hp, nets, dev, n, steps, flags_np, inlet, literal_thr=1e-3, literal_cap=2000,

@@ -1061,15 +1061,20 @@ __global__ void conv_dgrad_kernel(const GT* __restrict__ gy, const float* __rest
     extern __shared__ float sw[];
     for (int q = threadIdx.x; q < 9 * CO * CI; q += blockDim.x) sw[q] = w[q];
     __syncthreads();
+    // a thread computes 16 input channels of one pixel (more threads than
+    // one per pixel: the narrow images this kernel serves have few pixels)
+    constexpr int CG = 16, NG = CI / CG;
     const long P = (long)B * H * W;
-    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-         p += (long)gridDim.x * blockDim.x) {
+    for (long item = (long)blockIdx.x * blockDim.x + threadIdx.x; item < P * NG;
+         item += (long)gridDim.x * blockDim.x) {
+        const long p = item / NG;
+        const int c0 = (int)(item - p * NG) * CG;
         const int b = (int)(p / ((long)H * W));
         const int r = (int)(p - (long)b * H * W);
         const int i = r / W, j = r - i * W;
-        float acc[CI];
+        float acc[CG];
 #pragma unroll
-        for (int c = 0; c < CI; ++c) acc[c] = 0.0f;
+        for (int c = 0; c < CG; ++c) acc[c] = 0.0f;
         for (int t = 0; t < 9; ++t) {
             const int oy = t / 3 - 1, ox = t % 3 - 1;
             for (int yy = i - oy - 1; yy <= i - oy + 1; ++yy) {
@@ -1077,19 +1082,20 @@ __global__ void conv_dgrad_kernel(const GT* __restrict__ gy, const float* __rest
                 for (int xx = j - ox - 1; xx <= j - ox + 1; ++xx) {
                     if (!reads(xx, ox, j, W)) continue;
                     const size_t g = (((size_t)b * H + yy) * W + xx) * CO;
-                    const float* wt = sw + t * CO * CI;
+                    const float* wt = sw + t * CO * CI + c0;
                     for (int co = 0; co < CO; ++co) {
                         const float gv = ld_act(gy, g + co);
 #pragma unroll
-                        for (int c = 0; c < CI; ++c) acc[c] = fmaf(wt[co * CI + c], gv, acc[c]);
+                        for (int c = 0; c < CG; ++c) acc[c] = fmaf(wt[co * CI + c], gv, acc[c]);
                     }
                 }
             }
         }
 #pragma unroll
-        for (int c = 0; c < CI; ++c) {
-            const bool keep = !act || __bfloat162float(act[(size_t)p * CI + c]) > 0.0f;
-            st_val(gx, (size_t)p * CI + c, keep ? acc[c] : 0.0f);
+        for (int c = 0; c < CG; ++c) {
+            const size_t q = (size_t)p * CI + c0 + c;
+            const bool keep = !act || __bfloat162float(act[q]) > 0.0f;
+            st_val(gx, q, keep ? acc[c] : 0.0f);
         }
     }
 }
@@ -2070,8 +2076,8 @@ static hp_status dgrad(const GT* gy, const float* w, OT* gx, int B, int H, int W
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    const long P = (long)B * H * W;
-    const int blocks = (int)((P + 127) / 128 < 4L * nsm ? (P + 127) / 128 : 4L * nsm);
+    const long items = (long)B * H * W * (CI / 16);
+    const int blocks = (int)((items + 127) / 128 < 4L * nsm ? (items + 127) / 128 : 4L * nsm);
     conv_dgrad_kernel<CI, CO, GT, OT><<<blocks, 128, smem, st>>>(gy, w, gx, B, H, W, act);
     return check_launch();
 }
@@ -2091,11 +2097,21 @@ static hp_status wgrad_t(hp_trainer* t, const GT* gy, const XT* x, float* gw, fl
                          int H, int W, cudaStream_t st)
 {
     const long P = (long)B * H * W;
-    const int nchunks = (int)((P + kWgradChunk - 1) / kWgradChunk);
-    if ((size_t)nchunks * 9 * CO * CI > t->part_len) return HP_ERR_INVALID_ARG;
+    // pixels per chunk: enough CTAs (9 taps x chunks) to fill the GPU about
+    // four times over, whole 32-pixel tiles, at most kWgradChunk, and no more
+    // chunks than the partial-sum buffer holds
+    const long cap = (long)(t->part_len / ((size_t)9 * CO * CI));
+    const long target = (4L * t->cnn->num_sms + 8) / 9;
+    long chunk = (P + target - 1) / target;
+    chunk = (chunk + 31) / 32 * 32;
+    if (chunk > kWgradChunk) chunk = kWgradChunk;
+    if ((P + chunk - 1) / chunk > cap) chunk = ((P + cap - 1) / cap + 31) / 32 * 32;
+    const int nchunks = (int)((P + chunk - 1) / chunk);
+    if ((size_t)nchunks * 9 * CO * CI > t->part_len || (size_t)nchunks * CO > t->partb_len)
+        return HP_ERR_INVALID_ARG;
     const int threads = ((CO / BCO) * (CI / BCI) + 31) / 32 * 32;
     conv_wgrad_kernel<CI, CO, BCI, BCO, XT, GT><<<dim3(nchunks, 9), threads, 0, st>>>(
-        gy, x, t->part, t->partb, B, H, W, kWgradChunk);
+        gy, x, t->part, t->partb, B, H, W, (int)chunk);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     wgrad_reduce_kernel<<<reduce_blocks(CI, CO), 256, 0, st>>>(t->part, t->partb, nchunks, CI, CO,
