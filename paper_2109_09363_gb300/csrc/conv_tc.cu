@@ -313,6 +313,16 @@ constexpr int kAccSlots = 8;
 constexpr int kWsThreads = 192;
 constexpr uint32_t kWsSpinLimit = 1u << 22;
 
+// CTAs per SM: the edge layers of a branch (16 -> 32 and the 32 -> 1 layer
+// as 32 -> 16) and 32 -> 32 leave room in shared memory, registers and tensor
+// memory for two or three CTAs, whose pipelines then hide each other's
+// latency; the 64-channel layers take one.
+template <int CIN, int COUT, bool OUT1>
+constexpr int ws_ctas_per_sm()
+{
+    return OUT1 ? 3 : (CIN == 16 || (CIN == 32 && COUT == 32)) ? 2 : 1;
+}
+
 // OUT1: the layer has one output channel (the last convolution of a
 // branch), computed as channel 0 of COUT = 16 (the other weights are zero)
 // and stored as FP32 [P] without rounding.
@@ -326,9 +336,17 @@ struct WsSmem {
     static constexpr int kStageBytes = OUT1 ? 0 : 4 * 32 * COUT * 2;
     static constexpr int kBytes = kRingBytes + kBBytes + kStageBytes;
     static constexpr int kTmemCols = kAccSlots * COUT;  // 128, 256 or 512
+    static constexpr int kCtas = ws_ctas_per_sm<CIN, COUT, OUT1>();
+    // shared memory requested per CTA: enough that no more than kCtas CTAs
+    // share an SM (228 KB, 1 KB reserved per CTA), so their tensor memory
+    // (kCtas x kTmemCols <= 512 columns) always fits
+    static constexpr int kSmemRequest =
+        kCtas == 1 || kBytes > 228 * 1024 / (kCtas + 1) ? kBytes : 228 * 1024 / (kCtas + 1) + 1;
     static_assert(COUT == 32 || COUT == 64 || (COUT == 16 && OUT1),
                   "accumulator ring sized for 32 or 64 channels (16 for one output)");
     static_assert(CIN % 16 == 0, "K steps of 16 channels");
+    static_assert(kCtas * kTmemCols <= 512, "tensor memory of the CTAs that share an SM");
+    static_assert(kCtas * (kSmemRequest + 1024) <= 228 * 1024, "shared memory per SM");
 };
 
 // A bounded wait on an mbarrier phase: gives up after `limit` polls, or
@@ -479,7 +497,7 @@ __device__ __forceinline__ uint32_t idesc_for_rows(int n_out, int cout)
 // act (same layout as the output) is not positive is zeroed (the ReLU
 // derivative of the layer that produced act; act may be null).
 template <int CIN, int COUT, bool OUT1, bool DGRAD = false>
-__global__ void __launch_bounds__(kWsThreads, 1)
+__global__ void __launch_bounds__(kWsThreads, (ws_ctas_per_sm<CIN, COUT, OUT1>()))
     conv3x3_tc_ws_kernel(const uint4* __restrict__ x, const uint4* __restrict__ w,
                          const float* __restrict__ bias, void* __restrict__ yout, int H, int W,
                          int segs, int nbands, int band, int items, int relu, int* err,
@@ -832,19 +850,20 @@ hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, in
     if (!rattr) {
         cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             R::kBytes);
+                                             R::kSmemRequest);
         if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
         rattr = true;
     }
     const int segs = (W + kTileM - 1) / kTileM;
     const long rows = (long)B * H * segs;
-    int band = (int)((rows + 8L * nsm - 1) / (8L * nsm));
+    const long ctas = (long)R::kCtas * nsm;
+    int band = (int)((rows + 8L * ctas - 1) / (8L * ctas));
     band = band < 4 ? 4 : band > H ? H : band;
     const int nbands = (H + band - 1) / band;
     const long items = (long)B * segs * nbands;
     if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
-    const int grid = items < nsm ? (int)items : nsm;
-    conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD><<<grid, kWsThreads, R::kBytes, st>>>(
+    const int grid = items < ctas ? (int)items : (int)ctas;
+    conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD><<<grid, kWsThreads, R::kSmemRequest, st>>>(
         (const uint4*)x, (const uint4*)w, bias, y, H, W, segs, nbands, band, (int)items, relu,
         err, wait_limit, (const uint4*)act);
     return check_launch();
