@@ -1170,9 +1170,10 @@ __global__ void conv_wgrad_kernel(const GT* __restrict__ gy, const XT* __restric
     }
 }
 
-// grad[co][ci][t] (oracle order) = sum over chunks; bias likewise.  A block
-// of 256 threads serves 32 outputs; thread group j (of 8) sums the chunks
-// k = j (mod 8) in FP64, and the 8 group sums are added in a fixed order.
+// grad[co][ci][t] (oracle order) = sum over chunks of part[k][t][co][ci];
+// bias likewise.  A block of 256 threads serves 32 outputs; thread group j
+// (of 8) sums the chunks k = j (mod 8) in FP64, and the 8 group sums are
+// added in a fixed order.
 // Launch with ceil((9 CO CI + CO) / 32) blocks of 256 threads.
 __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ part,
                                                            const float* __restrict__ partb,
@@ -1182,13 +1183,15 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restri
 {
     __shared__ double sh[8][32];
     const int o = threadIdx.x & 31, j = threadIdx.x >> 5;
+    // q walks the partials' own layout [t][co][ci], so that the 32 lanes of a
+    // group read 32 consecutive floats of every partial; the result goes to
+    // the oracle order [co][ci][t]
     const int q = blockIdx.x * 32 + o;
     const int nw = 9 * CO * CI;
     double s = 0.0;
     if (q < nw) {
-        const int t = q % 9, ci = (q / 9) % CI, co = q / (9 * CI);
-        const size_t off = (size_t)t * CO * CI + co * CI + ci, step = (size_t)9 * CO * CI;
-        for (int k = j; k < nchunks; k += 8) s += part[(size_t)k * step + off];
+        const size_t step = (size_t)9 * CO * CI;
+        for (int k = j; k < nchunks; k += 8) s += part[(size_t)k * step + q];
     } else if (q < nw + CO) {
         const int co = q - nw;
         for (int k = j; k < nchunks; k += 8) s += partb[(size_t)k * CO + co];
@@ -1198,8 +1201,12 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restri
     if (j == 0) {
         double t = 0.0;
         for (int g = 0; g < 8; ++g) t += sh[g][o];
-        if (q < nw) gw[q] = (float)t;
-        else if (q < nw + CO) gb[q - nw] = (float)t;
+        if (q < nw) {
+            const int tap = q / (CO * CI), co = (q / CI) % CO, ci = q % CI;
+            gw[((size_t)co * CI + ci) * 9 + tap] = (float)t;
+        } else if (q < nw + CO) {
+            gb[q - nw] = (float)t;
+        }
     }
 }
 
