@@ -182,7 +182,8 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
         (rc = dalloc(&c->ckpt, c->max_cells, &c->guards)) != HP_OK ||
         (rc = dalloc(&c->partial, c->partial_len, &c->guards)) != HP_OK ||
         (rc = dalloc(&c->partial2, c->partial2_len, &c->guards)) != HP_OK ||
-        (rc = dalloc(&c->gs, (size_t)mx.batch, &c->guards)) != HP_OK || (rc = dalloc(&c->ls, 1, &c->guards)) != HP_OK) {
+        (rc = dalloc(&c->gs, (size_t)mx.batch, &c->guards)) != HP_OK ||
+        (rc = dalloc(&c->ls, 1, &c->guards)) != HP_OK) {
         hp_ctx_destroy(c);
         return rc;
     }
@@ -211,6 +212,8 @@ hp_status hp_ctx_create(hp_ctx** out, hp_shape mx, int device)
 hp_status hp_ctx_check(hp_ctx* c)
 {
     if (!c) return HP_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return check_guards(c->guards);
 }
 
@@ -276,7 +279,8 @@ hp_status hp_jacobi_target(hp_ctx* c, const float* div, const uint8_t* flags, in
     const size_t cells = (size_t)s.batch * s.ny * s.nx;
     hp_status rc = launch_mask(flags, c->mask, s, st);
     if (rc != HP_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(c->div, div, cells * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e =
+        cudaMemcpyAsync(c->div, div, cells * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     // phi_n into the checkpoint workspace (free once the sweeps are done)
     if (n > 0) {

@@ -2309,10 +2309,11 @@ static hp_status layer_backward(hp_trainer* t, int l, const __nv_bfloat16* x, co
         rc = launch_conv3x3_tc_dgrad(g16, t->wdg[l], t->zero_bias, mask_act, gx16, B, H, W, ci, co,
                                      c->err, c->num_sms, st, c->wait_limit);
         if (rc != HP_OK) return rc;
-        if (ci == 64 && co == 64) return border_terms<64, 64>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
-        if (ci == 32 && co == 64) return border_terms<32, 64>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
-        if (ci == 64 && co == 32) return border_terms<64, 32>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
-        return border_terms<32, 32>(g16, t->wt[l], mask_act, gx16, B, H, W, st);
+        const float* wl = t->wt[l];
+        if (ci == 64 && co == 64) return border_terms<64, 64>(g16, wl, mask_act, gx16, B, H, W, st);
+        if (ci == 32 && co == 64) return border_terms<32, 64>(g16, wl, mask_act, gx16, B, H, W, st);
+        if (ci == 64 && co == 32) return border_terms<64, 32>(g16, wl, mask_act, gx16, B, H, W, st);
+        return border_terms<32, 32>(g16, wl, mask_act, gx16, B, H, W, st);
     }
     const float* g32 = (const float*)gy;
     rc = wgrad_dispatch(t, 0, l, g32, x, gw, gb, B, H, W, st);
@@ -2397,10 +2398,15 @@ static hp_status unet_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
         cur ^= 1;
         --l;
         // l is now the layer whose output was up-sampled (the coarser level)
-        const bool a = bf(lev), b2 = bf(lev + 1);
-        if (a && b2) rc = cat_backward<__nv_bfloat16, __nv_bfloat16>(g[cur], t->gskip[lev], g[cur ^ 1], act(l), B, H, W, st);
-        else if (a) rc = cat_backward<__nv_bfloat16, float>(g[cur], t->gskip[lev], g[cur ^ 1], act(l), B, H, W, st);
-        else rc = cat_backward<float, float>(g[cur], t->gskip[lev], g[cur ^ 1], act(l), B, H, W, st);
+        const void* gc = g[cur];
+        void* gn = g[cur ^ 1];
+        float* gs = t->gskip[lev];
+        if (bf(lev) && bf(lev + 1))
+            rc = cat_backward<__nv_bfloat16, __nv_bfloat16>(gc, gs, gn, act(l), B, H, W, st);
+        else if (bf(lev))
+            rc = cat_backward<__nv_bfloat16, float>(gc, gs, gn, act(l), B, H, W, st);
+        else
+            rc = cat_backward<float, float>(gc, gs, gn, act(l), B, H, W, st);
         if (rc != HP_OK) return rc;
         cur ^= 1;
     }
@@ -2422,10 +2428,15 @@ static hp_status unet_backward(hp_trainer* t, hp_shape s, cudaStream_t st)
     for (int lev = 3; lev >= 0; --lev) {
         const int H = Hl(lev), W = Wl(lev);
         // l is the layer that produced the skip features of this level
-        const bool a = bf(lev + 1), b2 = bf(lev);
-        if (a && b2) rc = pool_backward<__nv_bfloat16, __nv_bfloat16>(g[cur], act(l), t->gskip[lev], g[cur ^ 1], B, H, W, st);
-        else if (b2) rc = pool_backward<float, __nv_bfloat16>(g[cur], act(l), t->gskip[lev], g[cur ^ 1], B, H, W, st);
-        else rc = pool_backward<float, float>(g[cur], act(l), t->gskip[lev], g[cur ^ 1], B, H, W, st);
+        const void* gc = g[cur];
+        void* gn = g[cur ^ 1];
+        const float* gs = t->gskip[lev];
+        if (bf(lev + 1) && bf(lev))
+            rc = pool_backward<__nv_bfloat16, __nv_bfloat16>(gc, act(l), gs, gn, B, H, W, st);
+        else if (bf(lev))
+            rc = pool_backward<float, __nv_bfloat16>(gc, act(l), gs, gn, B, H, W, st);
+        else
+            rc = pool_backward<float, float>(gc, act(l), gs, gn, B, H, W, st);
         if (rc != HP_OK) return rc;
         cur ^= 1;
         rc = layer_backward(t, l, act(l - 1), g[cur], g[cur ^ 1], relu_of(l - 1), B, H, W, st);
@@ -2648,7 +2659,8 @@ hp_status hp_trainer_get_state(hp_trainer* t, float* master, float* m, float* v,
     if (!t) return HP_ERR_INVALID_ARG;
     cudaError_t e = cudaDeviceSynchronize();
     const size_t bytes = (size_t)t->param_count * 4;
-    if (e == cudaSuccess && master) e = cudaMemcpy(master, t->master, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && master)
+        e = cudaMemcpy(master, t->master, bytes, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && m) e = cudaMemcpy(m, t->m, bytes, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && v) e = cudaMemcpy(v, t->v, bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
@@ -2738,6 +2750,8 @@ hp_status hp_cnn_check(hp_cnn* c)
     if (e == cudaSuccess && flag) e = cudaMemset(c->err, 0, sizeof(int));
     if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     if (flag & 1) return HP_ERR_TIMEOUT;
+    e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     const hp_status g = check_guards(c->guards);
     if (g != HP_OK) return g;
     return (flag & 2) ? HP_WARN_CNN_NONFINITE : HP_OK;

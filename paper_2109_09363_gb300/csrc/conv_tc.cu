@@ -1234,10 +1234,14 @@ hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, voi
                             int H, int W, int cin, int cout, int relu, int* err, int nsm,
                             cudaStream_t st, uint32_t wait_limit)
 {
-    if (cin == 32 && cout == 32) return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
-    if (cin == 32 && cout == 64) return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
-    if (cin == 64 && cout == 32) return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
-    if (cin == 64 && cout == 64) return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 32 && cout == 32)
+        return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 32 && cout == 64)
+        return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 64 && cout == 32)
+        return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+    if (cin == 64 && cout == 64)
+        return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
     // first layer of a branch, input padded to 16 channels (warp-specialised
     // kernel only; narrower images take the CUDA-core layer)
     if (cin == 16 && cout == 32 && W >= kWsMinWidth)
