@@ -13,7 +13,9 @@
    128-cell inlet: three driver steps teacher-forced against the oracle
    (advection and projection at E_t = 1e-8; at the raw E_t = 1e-3 this plume
    needs no sweeps), then one hybrid projection from a randomly initialised
-   network's guess against the oracle projection from the same guess."""
+   network's guess against the oracle projection from the same guess.
+3. Config 5's evaluation geometry at 2048^2 (8 random discs): two driver steps
+   teacher-forced, then a hybrid projection with the Unet from its guess."""
 import numpy as np
 import pytest
 
@@ -196,3 +198,68 @@ def test_plume_1024_cylinder_and_hybrid_step(dev):
         umax = max(np.abs(ref["u"]).max(), np.abs(ref["v"]).max(), 1e-30)
         assert np.abs(uh.cpu().numpy()[0] - ref["u"][0]).max() <= tol * umax
         assert np.abs(vh.cpu().numpy()[0] - ref["v"][0]).max() <= tol * umax
+
+
+def test_plume_2048_eight_cylinders_and_unet_hybrid(dev):
+    """Config 5's evaluation geometry at its size: the 2048^2 plume (inlet
+    256 cells) with 8 non-overlapping discs of radius U(32, 128), two driver
+    steps teacher-forced against the oracle (the temporally blocked sweeps
+    serve grids of this size), then one hybrid projection with the Unet from
+    its own guess against the oracle projection from the same guess."""
+    from paper_2109_09363_gb300.plume import Plume, PlumeConfig
+    n, thr, cap, tol = 2048, 1e-10, 800, 1e-5
+    u0, v0, rho0 = W.plume_initial_state(n, seed=5)
+    x0, x1 = W.inlet_columns(n)
+    fl = W.random_cylinders(n, 8, 5, radius=(32, 128), inlet=(x0, x1))[None]
+    cfg = PlumeConfig(ny=n, nx=n, dt=0.1, inlet=(x0, x1), threshold=thr, max_iters=cap)
+    t32 = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sim = Plume(cfg, t32(u0[None].astype(np.float32)), t32(v0[None].astype(np.float32)),
+                t32(rho0[None].astype(np.float32)), t32(fl))
+    oracle.set_threads(0)
+
+    def check(ustar, kg, pu, pv, phi0=None):
+        ref = oracle.project(ustar[0][None], ustar[1][None], fl, thr, cap, dt=cfg.dt,
+                             phi0=phi0, hist_len=cap + 2)
+        ko = int(ref["iters"][0])
+        if kg != ko:
+            eh = ref["e_hist"][0]
+            lo, hi = sorted((kg, ko))
+            assert np.all(np.abs(eh[lo:hi + 1] - thr) / thr <= 5e-5), (kg, ko)
+            ref = oracle.project(ustar[0][None], ustar[1][None], fl, thr, cap, dt=cfg.dt,
+                                 phi0=phi0, fixed_iters=kg)
+        umax = max(np.abs(ref["u"]).max(), np.abs(ref["v"]).max(), 1e-30)
+        assert np.abs(pu - ref["u"][0]).max() <= tol * umax
+        assert np.abs(pv - ref["v"][0]).max() <= tol * umax
+
+    for step in range(2):
+        su, sv, sr = (x.cpu().numpy()[0].astype(np.float64) for x in (sim.u, sim.v, sim.rho))
+        sim.advect()
+        eu, ev, er = A.advect_step(su, sv, sr, fl[0], cfg.dt, inlet=(x0, x1))
+        gu, gv, gr = (x.cpu().numpy()[0] for x in (sim.u, sim.v, sim.rho))
+        umax = max(np.abs(eu).max(), np.abs(ev).max(), 1e-30)
+        assert np.abs(gu - eu).max() <= tol * umax, step
+        assert np.abs(gv - ev).max() <= tol * umax, step
+        assert np.abs(gr - er).max() <= tol * np.abs(er).max(), step
+        ustar = (gu.astype(np.float64), gv.astype(np.float64))
+        out = sim.project()
+        torch.cuda.synchronize()
+        check(ustar, int(out["iters"].cpu()[0]), sim.u.cpu().numpy()[0], sim.v.cpu().numpy()[0])
+        assert hp.hp_resident_clusters(sim.ctx, 1, n, n) == 0   # the blocked kernel ran
+
+    sim.advect()
+    us, vs = sim.u.clone(), sim.v.clone()
+    ctx = hp.Context(1, n, n)
+    cnn = hp.CNN(1, n, n, params=C.flatten(C.init_params(seed=8, arch="unet")), arch="unet")
+    fd = t32(fl)
+    div = hp.hp_divergence(us, vs, fd)
+    phi_hat, s = hp.hp_cnn_forward(cnn, div, fd)
+    phi0 = (phi_hat.cpu().numpy() * s.cpu().numpy()[:, None, None]).astype(np.float64)
+    assert np.all(np.isfinite(phi0))
+    uh, vh = us.clone(), vs.clone()
+    out = hp.hp_project_hybrid(ctx, cnn, uh, vh, fd, hp.ProjectParams(
+        threshold=thr, max_iters=cap, dt=cfg.dt))
+    torch.cuda.synchronize()
+    assert cnn.check() == 0
+    check((us.cpu().numpy()[0].astype(np.float64), vs.cpu().numpy()[0].astype(np.float64)),
+          int(out["iters"].cpu()[0]), uh.cpu().numpy()[0], vh.cpu().numpy()[0], phi0=phi0)
+    ctx.check()
