@@ -284,19 +284,22 @@ __global__ void maxpool2_kernel(const uint4* __restrict__ x, uint4* __restrict__
 // x 2 up-sampling (half-pixel centres, edge sample repeated, FP32 then
 // rounded to BF16) of coarse [B][H/2][W/2][32], channels 32-63 the skip
 // features [B][H][W][32].  Block x = one output row (b, j); its threads cover
-// the row's (pixel, 8-channel chunk) items.
+// first the row's interpolated (pixel, 8-channel chunk) items, then its copied
+// ones, so that a warp takes one kind only.
 __global__ void up_concat_kernel(const uint4* __restrict__ coarse, const uint4* __restrict__ skip,
                                  uint4* __restrict__ y, int H, int W)
 {
     const int Hc = H / 2, Wc = W / 2;
     const int xi = blockIdx.y * blockDim.x + threadIdx.x;
     if (xi >= W * 8) return;
-    const int c = xi & 7;
-    const int i = xi >> 3;  // column
     const int row = blockIdx.x;
+    const bool copy = xi >= W * 4;
+    const int k = copy ? xi - W * 4 : xi;
+    const int c = (k & 3) + (copy ? 4 : 0);  // chunk of the 64-channel output pixel
+    const int i = k >> 2;                      // column
     const size_t p = (size_t)row * W + i;
     const size_t q = p * 8 + c;
-    if (c >= 4) {
+    if (copy) {
         y[q] = skip[p * 4 + (c - 4)];
         return;
     }
@@ -314,10 +317,10 @@ __global__ void up_concat_kernel(const uint4* __restrict__ coarse, const uint4* 
     const __nv_bfloat16* a11 = reinterpret_cast<const __nv_bfloat16*>(&q11);
     __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const float rx0 = 0.75f * __bfloat162float(a00[k]) + 0.25f * __bfloat162float(a01[k]);
-        const float rx1 = 0.75f * __bfloat162float(a10[k]) + 0.25f * __bfloat162float(a11[k]);
-        o[k] = __float2bfloat16_rn(0.75f * rx0 + 0.25f * rx1);
+    for (int e = 0; e < 8; ++e) {
+        const float rx0 = 0.75f * __bfloat162float(a00[e]) + 0.25f * __bfloat162float(a01[e]);
+        const float rx1 = 0.75f * __bfloat162float(a10[e]) + 0.25f * __bfloat162float(a11[e]);
+        o[e] = __float2bfloat16_rn(0.75f * rx0 + 0.25f * rx1);
     }
     y[q] = *reinterpret_cast<const uint4*>(o);
 }
