@@ -193,16 +193,25 @@ struct BranchIn {
     __device__ void at(int b, int i, int j, float out[3]) const
     {
         const int hs = H / scale, ws = W / scale;
-        double sd = 0.0, sf = 0.0;
-        for (int dy = 0; dy < scale; ++dy)
-            for (int dx = 0; dx < scale; ++dx) {
-                const size_t q = ((size_t)b * H + (size_t)j * scale + dy) * W + (size_t)i * scale + dx;
-                sd += div[q];
-                sf += flags[q] != 0 ? 1.0 : 0.0;
-            }
-        const double inv = 1.0 / (scale * scale);
-        out[0] = bf16r((float)(sd * inv) / s[b]);
-        out[1] = bf16r((float)(sf * inv));
+        if (scale == 1) {
+            // one pixel: the FP64 mean of one FP32 value is that value, so
+            // this is the pooled form below without the FP64 arithmetic
+            const size_t q = ((size_t)b * H + j) * W + i;
+            out[0] = bf16r(div[q] / s[b]);
+            out[1] = flags[q] != 0 ? 1.0f : 0.0f;
+        } else {
+            double sd = 0.0, sf = 0.0;
+            for (int dy = 0; dy < scale; ++dy)
+                for (int dx = 0; dx < scale; ++dx) {
+                    const size_t q = ((size_t)b * H + (size_t)j * scale + dy) * W +
+                                     (size_t)i * scale + dx;
+                    sd += div[q];
+                    sf += flags[q] != 0 ? 1.0 : 0.0;
+                }
+            const double inv = 1.0 / (scale * scale);
+            out[0] = bf16r((float)(sd * inv) / s[b]);
+            out[1] = bf16r((float)(sf * inv));
+        }
         out[2] = 0.0f;
         if (prev) {
             // bilinear x 2 from the coarser (hs/2 x ws/2) output
@@ -220,27 +229,28 @@ struct BranchIn {
 
 // Branch input, once per pixel of the branch: xin [P][cin] FP32 holding the
 // BF16-rounded values [pool(div)/s, pool(flags)(, up(coarser output))].
+// Block (x, y) covers blockDim.x pixels of the rows y, y + gridDim.y, ... of
+// the B x hs rows of the branch.
 __global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xin,
                                     __nv_bfloat16* __restrict__ x16, int B)
 {
     const int hs = in.H / in.scale, ws = in.W / in.scale;
-    const long P = (long)B * hs * ws;
-    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-         p += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(p / ((long)hs * ws));
-        const int r = (int)(p - (long)b * hs * ws);
-        const int j = r / ws, i = r - j * ws;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ws) return;
+    for (int row = blockIdx.y; row < B * hs; row += gridDim.y) {
+        const int b = row / hs, j = row - b * hs;
+        const size_t p = (size_t)row * ws + i;
         float xc[3];
         in.at(b, i, j, xc);
         if (xin)
-            for (int c = 0; c < cin; ++c) xin[(size_t)p * cin + c] = xc[c];
+            for (int c = 0; c < cin; ++c) xin[p * cin + c] = xc[c];
         if (x16) {
             // the tensor-core first layer: 16 channels, the inputs then zeros
             // (the values are BF16-rounded already, so this is exact)
             __align__(16) __nv_bfloat16 v[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < cin ? xc[c] : 0.0f);
-            uint4* dst = reinterpret_cast<uint4*>(x16 + (size_t)p * 16);
+            uint4* dst = reinterpret_cast<uint4*>(x16 + p * 16);
             dst[0] = reinterpret_cast<const uint4*>(v)[0];
             dst[1] = reinterpret_cast<const uint4*>(v)[1];
         }
@@ -588,10 +598,10 @@ static hp_status launch_first(hp_cnn* c, int k, const BranchIn& in, int cin, flo
 {
     const bool tc = W >= conv_tc_min_width();
     float* xin = xin_keep ? xin_keep : (tc ? nullptr : c->xin);
-    const long P = (long)B * H * W;
     const long cap = 16L * c->num_sms;
-    const int blocks = (int)((P + 255) / 256 < cap ? (P + 255) / 256 : cap);
-    branch_input_kernel<<<blocks, 256, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
+    const int rows = B * H;
+    const dim3 grid((W + 127) / 128, rows < 65535 ? rows : 65535);
+    branch_input_kernel<<<grid, 128, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     if (tc)
