@@ -257,6 +257,150 @@ __global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xi
     }
 }
 
+// The same inputs for four consecutive pixels i0..i0+3 of a row of the branch
+// (i0 a multiple of 4, W a multiple of 4 * scale): vector loads of the rows
+// the four pixels pool, issued before any arithmetic.  The pooled mean is
+// taken in FP32 as the mean of 2 x 2 means (for scale 4, of the four 2 x 2
+// means), the flag count as an exact integer.
+__device__ __forceinline__ void branch_at4(const BranchIn& in, int b, int i0, int j,
+                                           float out[4][3])
+{
+    const float sb = in.s[b];
+    const int W = in.W;
+    if (in.scale == 1) {
+        const size_t q = ((size_t)b * in.H + j) * W + i0;
+        const float4 d = *reinterpret_cast<const float4*>(in.div + q);
+        const uint32_t f = *reinterpret_cast<const uint32_t*>(in.flags + q);
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            out[k][0] = bf16r(dv[k] / sb);
+            out[k][1] = ((f >> (8 * k)) & 0xffu) != 0u ? 1.0f : 0.0f;
+        }
+    } else if (in.scale == 2) {
+        const size_t q = ((size_t)b * in.H + 2 * j) * W + 2 * i0;
+        float v[2][8];
+        uint2 f[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float4 a = *reinterpret_cast<const float4*>(in.div + q + (size_t)r * W);
+            const float4 c = *reinterpret_cast<const float4*>(in.div + q + (size_t)r * W + 4);
+            v[r][0] = a.x; v[r][1] = a.y; v[r][2] = a.z; v[r][3] = a.w;
+            v[r][4] = c.x; v[r][5] = c.y; v[r][6] = c.z; v[r][7] = c.w;
+            f[r] = *reinterpret_cast<const uint2*>(in.flags + q + (size_t)r * W);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float m = ((v[0][2 * k] + v[0][2 * k + 1]) + (v[1][2 * k] + v[1][2 * k + 1])) * 0.25f;
+            int cnt = 0;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const uint32_t w2 = ((k < 2 ? f[r].x : f[r].y) >> (16 * (k & 1))) & 0xffffu;
+                cnt += ((w2 & 0xffu) != 0u) + ((w2 >> 8) != 0u);
+            }
+            out[k][0] = bf16r(m / sb);
+            out[k][1] = (float)cnt * 0.25f;
+        }
+    } else {
+        const size_t q = ((size_t)b * in.H + 4 * j) * W + 4 * i0;
+        float m2[2][8];  // 2 x 2 means of the two row pairs, 8 per pair
+        int cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int rp = 0; rp < 2; ++rp) {
+            float v[2][16];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const float* src = in.div + q + (size_t)(2 * rp + r) * W;
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const float4 a = *reinterpret_cast<const float4*>(src + 4 * c4);
+                    v[r][4 * c4] = a.x; v[r][4 * c4 + 1] = a.y;
+                    v[r][4 * c4 + 2] = a.z; v[r][4 * c4 + 3] = a.w;
+                }
+                const uint4 f = *reinterpret_cast<const uint4*>(in.flags + q + (size_t)(2 * rp + r) * W);
+                const uint32_t fw[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cnt[k] += __popc(__vcmpne4(fw[k], 0u)) >> 3;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                m2[rp][c] = ((v[0][2 * c] + v[0][2 * c + 1]) + (v[1][2 * c] + v[1][2 * c + 1])) * 0.25f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float m = ((m2[0][2 * k] + m2[0][2 * k + 1]) + (m2[1][2 * k] + m2[1][2 * k + 1])) * 0.25f;
+            out[k][0] = bf16r(m / sb);
+            out[k][1] = (float)cnt[k] * 0.0625f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k][2] = 0.0f;
+    if (in.prev) {
+        // bilinear x 2 from the coarser output: coarse columns i0/2 - 1 ..
+        // i0/2 + 2 (clamped) of coarse rows cj and nj
+        const int hs = in.H / in.scale, ws = W / in.scale;
+        const int hc = hs / 2, wc = ws / 2;
+        const float* pc = in.prev + (size_t)b * hc * wc;
+        const int cj = j >> 1;
+        const int nj = (j & 1) ? min(cj + 1, hc - 1) : max(cj - 1, 0);
+        const int c0 = i0 >> 1;
+        float r0[4], r1[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int cc = min(max(c0 - 1 + t, 0), wc - 1);
+            r0[t] = pc[(size_t)cj * wc + cc];
+            r1[t] = pc[(size_t)nj * wc + cc];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            // pixel i0 + k: coarse column c0 + k / 2 (index 1 + k / 2), its
+            // neighbour one to the left (even k) or right (odd k)
+            const int ci = 1 + (k >> 1), ni = (k & 1) ? ci + 1 : ci - 1;
+            const float rx0 = 0.75f * r0[ci] + 0.25f * r0[ni];
+            const float rx1 = 0.75f * r1[ci] + 0.25f * r1[ni];
+            out[k][2] = bf16r(0.75f * rx0 + 0.25f * rx1);
+        }
+    }
+}
+
+// Branch input, four pixels per thread (rows of the branch a multiple of 4
+// wide); the same outputs as branch_input_kernel.
+__global__ void branch_input4_kernel(BranchIn in, int cin, float* __restrict__ xin,
+                                     __nv_bfloat16* __restrict__ x16, int B)
+{
+    const int hs = in.H / in.scale, ws = in.W / in.scale;
+    const size_t quads = (size_t)B * hs * ws / 4;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < quads;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = 4 * t;
+        const size_t row = p / (size_t)ws;
+        const int i0 = (int)(p - row * ws);
+        const int b = (int)(row / (size_t)hs), j = (int)(row - (size_t)b * hs);
+        float xc[4][3];
+        branch_at4(in, b, i0, j, xc);
+        if (xin) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (c < cin) xin[(p + k) * cin + c] = xc[k][c];
+            }
+        }
+        if (x16) {
+            uint4* dst = reinterpret_cast<uint4*>(x16 + p * 16);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                // 16 channels: the inputs, then zeros (exact: already BF16)
+                const uint32_t w0 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(xc[k][0])) |
+                                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(xc[k][1])) << 16);
+                const uint32_t w1 = cin > 2 ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(xc[k][2])) : 0u;
+                dst[2 * k] = make_uint4(w0, w1, 0u, 0u);
+                dst[2 * k + 1] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+}
+
 // 2 x 2 max pooling of BF16 [B][H][W][C] (H, W even) into [B][H/2][W/2][C].
 // Block x = one output row (b, i); its threads cover the row's (pixel,
 // 8-channel chunk) items, c8 chunks per pixel.  The maximum of BF16 values is
@@ -599,9 +743,17 @@ static hp_status launch_first(hp_cnn* c, int k, const BranchIn& in, int cin, flo
     const bool tc = W >= conv_tc_min_width();
     float* xin = xin_keep ? xin_keep : (tc ? nullptr : c->xin);
     const long cap = 16L * c->num_sms;
-    const int rows = B * H;
-    const dim3 grid((W + 127) / 128, rows < 65535 ? rows : 65535);
-    branch_input_kernel<<<grid, 128, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
+    // the four-pixel kernel's vector loads need 16-byte aligned rows
+    if (W % 4 == 0 && in.W % (4 * in.scale) == 0 && (reinterpret_cast<uintptr_t>(in.div) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(in.flags) & 15) == 0) {
+        const long quads = (long)B * H * W / 4;
+        const int blocks = (int)((quads + 255) / 256 < cap ? (quads + 255) / 256 : cap);
+        branch_input4_kernel<<<blocks, 256, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
+    } else {
+        const int rows = B * H;
+        const dim3 grid((W + 127) / 128, rows < 65535 ? rows : 65535);
+        branch_input_kernel<<<grid, 128, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
+    }
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     if (tc)
