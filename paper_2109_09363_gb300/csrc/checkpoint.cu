@@ -14,8 +14,10 @@
 //   float32  w[n]       parameters in network order (as hp_cnn_set_params)
 //   float32  m[n], v[n] first and second Adam moments (moments == 1)
 //   uint64   checksum   FNV-1a (64 bit) of every byte before it
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
+#include <sys/types.h>
 
 #include <string>
 #include <vector>
@@ -103,11 +105,20 @@ hp_status ckpt_read(const char* path, CkptData* d)
     if (!path || !d) return HP_ERR_INVALID_ARG;
     FILE* f = fopen(path, "rb");
     if (!f) return HP_ERR_IO;
+    // the file's size first: a header is only trusted (and its arrays
+    // allocated) when the file holds exactly what it announces
+    int64_t size = -1;
+    if (fseeko(f, 0, SEEK_END) == 0) size = (int64_t)ftello(f);
+    if (size < 0 || fseeko(f, 0, SEEK_SET) != 0) {
+        fclose(f);
+        return HP_ERR_IO;
+    }
     Header h;
     Fnv fnv;
     bool ok = get(f, fnv, &h, sizeof(h)) && memcmp(h.magic, kMagic, 8) == 0 &&
               h.version == kVersion && h.n > 0 && h.n < (int64_t)1 << 32 && h.moments <= 1 &&
-              h.step >= 0;
+              h.step >= 0 && h.step <= INT32_MAX &&
+              size == (int64_t)sizeof(Header) + h.n * 4 * (h.moments ? 3 : 1) + 8;
     if (ok) {
         d->arch = h.arch;
         d->step = h.step;

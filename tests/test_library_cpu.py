@@ -192,6 +192,7 @@ def _checkpoint_bytes(arch, n, step=0, moments=False, seed=0):
 
 
 def test_checkpoint_reader_errors_need_no_gpu(lib, tmp_path):
+    import struct
     out = ctypes.c_void_p()
     s = hp.hp_shape(1, 64, 64)
     assert lib.hp_cnn_load(ctypes.byref(out), str(tmp_path / "missing").encode(), s, 0) == 8
@@ -204,7 +205,10 @@ def test_checkpoint_reader_errors_need_no_gpu(lib, tmp_path):
     for bad in (good[:-1], good[:50], good + b"\0",
                 good[:60] + bytes([good[60] ^ 4]) + good[61:],      # a parameter bit
                 _checkpoint_bytes(1, n - 1),                        # wrong count
-                _checkpoint_bytes(7, n)):                           # unknown arch
+                _checkpoint_bytes(7, n),                            # unknown arch
+                # a header announcing 2^31 parameters in a file of a few
+                # bytes: rejected on the file size, before any allocation
+                struct.pack("<8sIiqqII", b"HPCNNCK1", 1, 1, 2 ** 31, 0, 0, 0) + bytes(64)):
         p = tmp_path / "bad.hpcnn"
         p.write_bytes(bad)
         assert lib.hp_cnn_load(ctypes.byref(out), str(p).encode(), s, 0) == 8
