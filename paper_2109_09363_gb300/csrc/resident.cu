@@ -296,7 +296,7 @@ __device__ __forceinline__ float res_update(const ResGeom& g, float (&phi)[kResR
 __device__ __forceinline__ float* ckpt_buf(const ResArgs& a, int m)
 {
     // checkpoint m holds phi_{m * kCkptEvery}; m = 0 is the input phi_0
-    return m == 0 ? a.phi : a.ck[m & 1];
+    return m == 0 ? a.phi : (m & 1) ? a.ck[1] : a.ck[0];
 }
 
 template <bool CLUSTER>
@@ -453,6 +453,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             for (int q = 0; q < kBatch; ++q) ev[q] = __shfl_sync(0xffffffffu, t1, 8 * q);
             if (g.lane == 0) {
                 // the round's decisions in sweep order; the first stop counts
+#pragma unroll
                 for (int q = 0; q < kBatch; ++q) {
                     const int j = k - 2 * kBatch - 1 + q;
                     if (j < 0) continue;
