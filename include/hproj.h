@@ -372,7 +372,7 @@ hp_status hp_cnn_forward(hp_cnn *cnn, const float *div, const uint8_t *flags, fl
  * outputs as hp_project; the batch and grid must also fit the network (its
  * max_shape, sides multiples of 4, of 16 for the Unet); every argument is
  * checked before anything is launched.  The Jacobi sweeps always follow and
- * judge the guess: a grid whose guess is not finite (NaN or Inf on a cell
+ * check the guess: a grid whose guess is not finite (NaN or Inf on a cell
  * with an open face) starts from phi_0 = 0 instead, i.e. it is the plain
  * projection, while the other grids keep their guesses; hp_cnn_check then
  * returns HP_WARN_CNN_NONFINITE. */

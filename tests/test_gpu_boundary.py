@@ -1,7 +1,7 @@
 """The boundary's behaviour around the hot path, through the C ABI:
 
 - the hybrid projection's fallback for a non-finite network guess (the
-  Jacobi sweeps always follow and judge the guess, Sec. 3.3): the grid starts
+  Jacobi sweeps always follow and check the guess, Sec. 3.3): the grid starts
   from zero, the others keep their guesses, hp_cnn_check warns;
 - a bounded tensor-core wait made to run out (hp_cnn_set_wait_limit): the
   kernels return, hp_cnn_check reports HP_ERR_TIMEOUT, and the network works
