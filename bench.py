@@ -281,12 +281,13 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
     """CNN-hybrid projection of the same grids to the same threshold, with the
     MultiScale, the SmallScale and the MonoScale network (Sec. 3.1).
 
-    Untimed set-up (config 5's recipe): training pairs from the plain solver
+    Untimed set-up (10,000 pairs, 20 epochs, batch 64): training pairs from the plain solver
     (128^2, vortex field + divergence sources + 0-4 obstacles), Adam training
     of each network on the GPU with the same pairs and schedule (batch 64,
     lr 1e-3).  Timed: the same per-step protocol as the plain arm (device
     restore of u*, L2 flush between steps, CUDA events).  Then, with the same
-    networks, BASELINE's configs 3 and 5 at their sizes (plume_eval)."""
+    networks, the 1024^2 plume with a cylinder and the 2048^2 plume with eight
+    cylinders (large_plumes)."""
     import torch
     from paper_2109_09363_gb300 import training as T
     from paper_2109_09363_gb300 import workloads as W
@@ -431,9 +432,9 @@ def run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms_plain
         ms_arm[arch] = arms[arch]
         ms_arm[arch]["t_inf_over_multiscale"] = (arms[arch]["t_inf_ms_16_grids"] /
                                                  ms_arm["t_inf_ms_16_grids"])
-    if not args.no_baseline_configs:
+    if not args.no_large_plumes:
         torch.cuda.empty_cache()
-        ms_arm["baseline_configs"] = baseline_configs(hp, trained, u0.device)
+        ms_arm["large_plumes"] = large_plumes(hp, trained, u0.device)
     return ms_arm
 
 
@@ -625,7 +626,7 @@ def cnn_layer_roofline(arch, pixels, hbm_gbs, tflops):
 
 def plume_eval(hp, nets, dev, n, steps, flags_np, inlet, literal_thr=1e-3, literal_cap=2000,
                rule_cap=5000, scheme=0, dt=0.1, gravity=-0.002, seed=3):
-    """One plume of BASELINE's configs 3 / 5 (first-order semi-Lagrangian by
+    """One large plume (first-order semi-Lagrangian by
     default, g = -0.002, dt = 0.1, inlet rho = 1.1, rho = 1 + N(0, 1e-4^2)),
     run `steps` steps per arm; each arm's projections are timed alone (CUDA
     events around the projection of every step).  Arms:
@@ -714,25 +715,24 @@ def plume_eval(hp, nets, dev, n, steps, flags_np, inlet, literal_thr=1e-3, liter
     return res
 
 
-def baseline_configs(hp, nets, dev):
-    """BASELINE's configs 3 and 5 at their sizes with the trained networks
-    (nets: architecture -> parameters).  Config 3: the 1024^2 plume (inlet
-    128 cells) with a solid disc of radius 64 centred 256 cells above the
-    inlet, 200 steps; config 5's evaluation: the 2048^2 plume (inlet 256
-    cells) with 8 non-overlapping discs of radius U(32, 128), 500 steps
-    (plume_eval: the literal E_t = 1e-3 and the paper's per-step rule)."""
+def large_plumes(hp, nets, dev):
+    """Two large plumes with the trained networks (nets: architecture ->
+    parameters): the 1024^2 plume (inlet 128 cells) with a solid disc of
+    radius 64 centred 256 cells above the inlet, 200 steps; the 2048^2 plume
+    (inlet 256 cells) with 8 non-overlapping discs of radius U(32, 128), 500
+    steps (plume_eval: the literal E_t = 1e-3 and the paper's per-step rule)."""
     from paper_2109_09363_gb300 import workloads as W
     res = {}
     n3 = 1024
     fl3 = W.plume_flags(n3, cylinder_radius=64, cylinder_height=256)
-    res["config3"] = plume_eval(hp, nets, dev, n3, 200, fl3, W.inlet_columns(n3))
-    res["config3"]["workload"] = ("1024^2 plume, inlet cols [448, 576) of the bottom row, solid "
+    res["plume_1024_cylinder"] = plume_eval(hp, nets, dev, n3, 200, fl3, W.inlet_columns(n3))
+    res["plume_1024_cylinder"]["workload"] = ("1024^2 plume, inlet cols [448, 576) of the bottom row, solid "
                                   "disc r = 64 centred 256 cells above it, first-order "
                                   "semi-Lagrangian, g = -0.002, dt = 0.1, 200 steps")
     n5 = 2048
     fl5 = W.random_cylinders(n5, 8, 5, radius=(32, 128), inlet=W.inlet_columns(n5))
-    res["config5"] = plume_eval(hp, nets, dev, n5, 500, fl5, W.inlet_columns(n5))
-    res["config5"]["workload"] = ("2048^2 plume, inlet cols [896, 1152) of the bottom row, 8 "
+    res["plume_2048_cylinders"] = plume_eval(hp, nets, dev, n5, 500, fl5, W.inlet_columns(n5))
+    res["plume_2048_cylinders"]["workload"] = ("2048^2 plume, inlet cols [896, 1152) of the bottom row, 8 "
                                   "non-overlapping solid discs r ~ U(32, 128) (seed 5), "
                                   "first-order semi-Lagrangian, g = -0.002, dt = 0.1, "
                                   "500 steps")
@@ -1048,8 +1048,8 @@ def main():
                     help="training pairs (128^2) of the networks of the hybrid arm")
     ap.add_argument("--train-epochs", type=int, default=20,
                     help="epochs (batch 64) of the networks of the hybrid arm")
-    ap.add_argument("--no-baseline-configs", action="store_true",
-                    help="skip BASELINE's configs 3 and 5 (1024^2 and 2048^2 plumes) in the "
+    ap.add_argument("--no-large-plumes", action="store_true",
+                    help="skip the 1024^2 and 2048^2 plumes with cylinders in the "
                          "hybrid arm")
     ap.add_argument("--host-loop", action="store_true",
                     help="launch the sweep blocks from a host-polled loop instead of the "
@@ -1306,7 +1306,7 @@ def main():
         if hybrid is not None:
             line["hybrid"] = hybrid
             # the headline comparison: CNN-hybrid against plain Jacobi on the
-            # same grids, both at the same E_t; under BASELINE's cap, and with
+            # same grids, both at the same E_t; under the cap of 5000, and with
             # the cap lifted so that every grid of both arms converges (the
             # paper's comparison at equal mean|div|)
             unc = hybrid["equal_threshold_uncapped"]
@@ -1329,10 +1329,10 @@ def main():
                 "others": {a: {"equal_threshold": hybrid[a]["equal_threshold_uncapped"]["speedup"],
                                "capped": hybrid[a]["speedup_vs_plain"]}
                            for a in NETWORKS[1:] if a in hybrid}}
-            bc = hybrid.get("baseline_configs")
+            bc = hybrid.get("large_plumes")
             if bc:
                 # projection time of the hybrid against plain Jacobi on the
-                # plumes of configs 3 and 5 (literal E_t, and the paper's rule)
+                # two large plumes (literal E_t, and the paper's rule)
                 line["hybrid_vs_plain"]["plumes"] = {
                     c: {"literal_multiscale": bc[c]["literal"]["hybrid_multiscale"][
                             "speedup_vs_plain"],
@@ -1340,7 +1340,7 @@ def main():
                                        for a in NETWORKS},
                         "plain_sweeps_mean_paper_rule": bc[c]["paper_rule"]["plain"][
                             "sweeps_mean"]}
-                    for c in ("config3", "config5")}
+                    for c in ("plume_1024_cylinder", "plume_2048_cylinders")}
         if pdnn is not None:
             line["pdnn_training"] = pdnn
         line["driver_step"] = driver

@@ -14,7 +14,7 @@
    (advection and projection at E_t = 1e-8; at the raw E_t = 1e-3 this plume
    needs no sweeps), then one hybrid projection from a randomly initialised
    network's guess against the oracle projection from the same guess.
-3. Config 5's evaluation geometry at 2048^2 (8 random discs): two driver steps
+3. The 2048^2 plume with 8 random discs: two driver steps
    teacher-forced, then a hybrid projection with the Unet from its guess."""
 import numpy as np
 import pytest
@@ -201,7 +201,7 @@ def test_plume_1024_cylinder_and_hybrid_step(dev):
 
 
 def test_plume_2048_eight_cylinders_and_unet_hybrid(dev):
-    """Config 5's evaluation geometry at its size: the 2048^2 plume (inlet
+    """The large evaluation geometry at its size: the 2048^2 plume (inlet
     256 cells) with 8 non-overlapping discs of radius U(32, 128), two driver
     steps teacher-forced against the oracle (the temporally blocked sweeps
     serve grids of this size), then one hybrid projection with the Unet from
