@@ -909,6 +909,55 @@ def profile_conv(batch, h, w, cin, cout) -> int:
     return 0
 
 
+def profile_stencil(batch, n) -> int:
+    """Time the HBM-streaming stencil calls on batch grids of n x n with
+    obstacles (CUDA events around 20 back-to-back calls after 3, so that the
+    host's launch overhead stays hidden behind the device's work): the
+    divergence, the face mask, the divergence norms, and a projection with no
+    sweep (mask and divergence, correction, norms); GB/s from each call's
+    algorithmic bytes per cell (divergence: u 4 + v 4 + flags 1 read, div 4
+    written; mask: 1 + 1; norms: 9; correction: u 4 + v 4 + phi 4 + mask 1
+    read, u 4 + v 4 + p 4 written = 25)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    from paper_2109_09363_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    u0 = torch.randn((batch, n, n + 1), generator=g, device=dev)
+    v0 = torch.randn((batch, n + 1, n), generator=g, device=dev)
+    fl = torch.from_numpy(np.stack([W.random_obstacles(n, n, 100 + b) for b in range(batch)])).to(dev)
+    ctx = hp.Context(batch, n, n)
+    div = torch.empty((batch, n, n), dtype=torch.float32, device=dev)
+    mask = torch.empty_like(fl)
+    u, v = u0.clone(), v0.clone()
+    prm = hp.ProjectParams(threshold=1e30, max_iters=0, sweep_kernel=2)
+    calls = {
+        "divergence": (lambda: hp.hp_divergence(u0, v0, fl, div_out=div), 13),
+        "face_mask": (lambda: hp.hp_face_mask(fl, mask_out=mask), 2),
+        "div_norms": (lambda: hp.hp_div_norms(ctx, u0, v0, fl), 9),
+        "projection_no_sweep": (lambda: hp.hp_project(ctx, u, v, fl, prm), 13 + 25 + 9),
+    }
+    cells = batch * n * n
+    out = {"profile_stencil": [batch, n]}
+    for name, (fn, bpc) in calls.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 20
+        out[name] = {"ms": ms, "bytes_per_cell": bpc, "gbs": bpc * cells / (ms * 1e-3) / 1e9}
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
 def profile_cnn(batch, n, arch="multiscale") -> int:
     """Time the CNN forward (t_inf) on BATCH vortex grids of N x N."""
     import torch
@@ -1031,6 +1080,9 @@ def main():
     ap.add_argument("--profile-conv", nargs=5, type=int,
                     metavar=("BATCH", "H", "W", "CIN", "COUT"),
                     help="only run the tensor-core 3x3 convolution, 3 times (a small case for ncu)")
+    ap.add_argument("--profile-stencil", nargs=2, type=int, metavar=("BATCH", "N"),
+                    help="only time the divergence, mask, norms and a projection without "
+                         "sweeps on BATCH grids of N x N")
     ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
     ap.add_argument("--profile-cnn-scaling", action="store_true",
@@ -1064,6 +1116,8 @@ def main():
                              kernel=args.sweep_kernel)
     if args.profile_conv:
         return profile_conv(*args.profile_conv)
+    if args.profile_stencil:
+        return profile_stencil(*args.profile_stencil)
     if args.profile_cnn:
         return profile_cnn(*args.profile_cnn, arch=args.arch)
     if args.profile_cnn_scaling:
