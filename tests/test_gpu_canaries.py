@@ -69,7 +69,7 @@ def out_dict(B, ny, nx, dev, hist=0):
     return o
 
 
-@pytest.mark.parametrize("B,ny,nx", [(3, 67, 130), (1, 129, 257), (2, 5, 3)])
+@pytest.mark.parametrize("B,ny,nx", [(3, 67, 130), (1, 129, 257), (2, 5, 3), (2, 37, 264)])
 def test_projection_path_writes_only_its_outputs(dev, B, ny, nx):
     u0, v0, f0 = fields(B, ny, nx, ny + nx)
     ctx = hp.Context(B, ny, nx)

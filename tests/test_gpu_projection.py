@@ -121,7 +121,7 @@ def check_projection(g, u, v, fl, thr, cap, phi0=None, hist_len=0):
 # ------------------------------------------------------------------ tests
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 5, 7), (1, 64, 128), (3, 67, 130),
-                                   (2, 129, 257)])
+                                   (2, 129, 257), (1, 3, 4), (2, 37, 264), (1, 5, 1028)])
 def test_face_mask_bit_exact(dev, shape):
     rng = np.random.default_rng(sum(shape))
     fl = (rng.random(shape) < 0.3).astype(np.uint8)
@@ -129,7 +129,8 @@ def test_face_mask_bit_exact(dev, shape):
     assert np.array_equal(got, oracle.face_mask(fl))
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 33, 47), (4, 128, 128), (1, 300, 260)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 33, 47), (4, 128, 128), (1, 300, 260),
+                                   (2, 37, 1028), (3, 2, 4)])
 def test_divergence(dev, shape):
     B, ny, nx = shape
     rng = np.random.default_rng(ny)
@@ -167,7 +168,7 @@ def test_jacobi_sweeps_and_residual_history(dev, shape, n):
 
 
 @pytest.mark.parametrize("shape,thr,cap", [((4, 64, 64), 2e-3, 3000), ((2, 67, 130), 1e-3, 3000),
-                                           ((3, 128, 128), 5e-4, 2500)])
+                                           ((3, 128, 128), 5e-4, 2500), ((2, 37, 264), 1e-3, 3000)])
 def test_project_matches_oracle(dev, shape, thr, cap):
     B, ny, nx = shape
     u, v, fl = vortex(B, ny, nx, seed=ny)
@@ -264,9 +265,12 @@ def test_context_reuse_and_shape_checks(dev):
         run_gpu(dev, *vortex(1, 80, 64), hp.ProjectParams(1e-3, 10), ctx=ctx)
 
 
-def test_div_norms(dev):
-    u, v, fl = vortex(3, 70, 90, seed=3)
-    ctx = hp.Context(3, 70, 90)
+@pytest.mark.parametrize("shape", [(3, 70, 90), (2, 37, 264), (1, 9, 1032), (2, 3, 8)])
+def test_div_norms(dev, shape):
+    """Rows of any length (one cell per thread), and rows a multiple of 8
+    cells (one warp per 256-cell segment, the last one ragged)."""
+    u, v, fl = vortex(*shape, seed=3)
+    ctx = hp.Context(*shape)
     e1, einf = hp.hp_div_norms(ctx, to_dev(u, dev), to_dev(v, dev), to_dev(fl, dev))
     r1, rinf = oracle.div_norms(u.astype(np.float64), v.astype(np.float64), fl)
     assert np.allclose(e1.cpu().numpy(), r1, rtol=1e-5)
