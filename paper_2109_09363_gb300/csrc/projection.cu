@@ -194,16 +194,14 @@ __global__ void __launch_bounds__(kQuadThreads)
 
 static bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// Blocks of a streaming kernel: a few per SM, no more than the work needs.
+// Blocks of a streaming kernel: a few per SM of the current device, no more
+// than the work needs.
 static int stream_blocks(uint64_t items, int per_block)
 {
-    static int nsm = 0;
-    if (nsm == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            nsm = 148;
-    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        nsm = 148;
     const uint64_t need = (items + per_block - 1) / per_block;
     const uint64_t cap = (uint64_t)kStreamBlocksPerSm * nsm;
     return (int)(need < cap ? (need > 0 ? need : 1) : cap);
