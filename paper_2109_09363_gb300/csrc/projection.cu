@@ -105,18 +105,19 @@ __device__ __forceinline__ void open_bits(const uint8_t* __restrict__ fl, int j,
     uint32_t right = byte_of(__shfl_down_sync(0xffffffffu, fc[0], 1), 0);
     if (!from_left) left = (act && i0 > 0) ? fl[row + i0 - 1] : 1u;
     if (!from_right) right = (act && i0 + 4 * N4 < nx) ? fl[row + i0 + 4 * N4] : 1u;
+    // four cells at a time, one byte each: the flags of the west and east
+    // neighbours as words shifted by one byte, each compared with zero
 #pragma unroll
-    for (int q = 0; q < 4 * N4; ++q) {
-        const uint32_t w = q == 0 ? left : byte_of(fc[(q - 1) / 4], (q - 1) % 4);
-        const uint32_t e = q == 4 * N4 - 1 ? right : byte_of(fc[(q + 1) / 4], (q + 1) % 4);
-        uint32_t bits = 0;
-        if (byte_of(fc[q / 4], q % 4) == 0) {
-            if (w == 0) bits |= 1u;
-            if (e == 0) bits |= 2u;
-            if (byte_of(fu[q / 4], q % 4) == 0) bits |= 4u;
-            if (byte_of(fd[q / 4], q % 4) == 0) bits |= 8u;
-        }
-        m[q] = bits;
+    for (int h = 0; h < N4; ++h) {
+        const uint32_t west = (fc[h] << 8) | (h == 0 ? left : fc[h - 1] >> 24);
+        const uint32_t east = (fc[h] >> 8) | ((h == N4 - 1 ? right : fc[h + 1] & 0xffu) << 24);
+        const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
+                              (__vcmpeq4(east, 0u) & 0x02020202u) |
+                              (__vcmpeq4(fu[h], 0u) & 0x04040404u) |
+                              (__vcmpeq4(fd[h], 0u) & 0x08080808u);
+        const uint32_t mw = __vcmpeq4(fc[h], 0u) & open;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m[4 * h + q] = byte_of(mw, q);
     }
 }
 
@@ -872,7 +873,8 @@ __global__ void div_norms_kernel(const float* __restrict__ u, const float* __res
 // row, segment) order), eight consecutive cells per lane with vector loads
 // (measured faster than a lane-strided layout whose every load is one
 // contiguous run: 177 against 303 us at 16 x 2048^2); each warp strides over
-// the segments and raises the grid's max once per grid it visits.
+// the segments, keeps its lanes' maxima and raises the grid's max once per
+// grid it visits.
 constexpr int kSegCells = 256;
 
 __global__ void __launch_bounds__(kStreamThreads)
@@ -892,8 +894,13 @@ __global__ void __launch_bounds__(kStreamThreads)
         const int sx = (int)(sg - row * nseg);
         const int b = (int)(row / (uint32_t)ny), j = (int)row - b * ny;
         if (b != cur) {
-            if (cur >= 0 && lane == 0)
-                atomicMax(einf_bits + (size_t)cur * einf_stride, __float_as_uint(run_max));
+            // the lanes' maxima of the previous grid, reduced once
+            if (cur >= 0) {
+                for (int off = 16; off > 0; off >>= 1)
+                    run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, off));
+                if (lane == 0)
+                    atomicMax(einf_bits + (size_t)cur * einf_stride, __float_as_uint(run_max));
+            }
             run_max = 0.0f;
             cur = b;
         }
@@ -932,14 +939,15 @@ __global__ void __launch_bounds__(kStreamThreads)
                           __fadd_rn(__fadd_rn(d[4], d[5]), __fadd_rn(d[6], d[7])));
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, off));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        }
+        for (int off = 16; off > 0; off >>= 1) a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, off));
         run_max = fmaxf(run_max, mx);
         if (lane == 0) partial[sg] = (double)a;
     }
-    if (cur >= 0 && lane == 0) atomicMax(einf_bits + (size_t)cur * einf_stride, __float_as_uint(run_max));
+    if (cur >= 0) {
+        for (int off = 16; off > 0; off >>= 1)
+            run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, off));
+        if (lane == 0) atomicMax(einf_bits + (size_t)cur * einf_stride, __float_as_uint(run_max));
+    }
 }
 
 // The norms kernel for one shape: the warp-per-segment kernel where rows allow
