@@ -909,21 +909,18 @@ def profile_conv(batch, h, w, cin, cout) -> int:
     return 0
 
 
-def profile_stencil(batch, n) -> int:
-    """Time the HBM-streaming stencil calls on batch grids of n x n with
-    obstacles (CUDA events around 20 back-to-back calls after 3, so that the
-    host's launch overhead stays hidden behind the device's work): the
-    divergence, the face mask, the divergence norms, and a projection with no
-    sweep (mask and divergence, correction, norms); GB/s from each call's
+def stencil_timing(hp, dev, batch, n):
+    """The HBM-streaming stencil calls on batch grids of n x n with obstacles
+    and random velocities (CUDA events around 20 back-to-back calls after 3,
+    so that the host's launch overhead stays behind the device's work): the
+    divergence, the face mask and the divergence norms; GB/s from each call's
     algorithmic bytes per cell (divergence: u 4 + v 4 + flags 1 read, div 4
-    written; mask: 1 + 1; norms: 9; correction: u 4 + v 4 + phi 4 + mask 1
-    read, u 4 + v 4 + p 4 written = 25)."""
+    written; mask: 1 + 1; norms: 9) and the fraction of the measured HBM
+    bandwidth.  (The correction runs only inside a projection; its kernel is
+    measured with ncu.)"""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2109_09363_gb300 as hp
     from paper_2109_09363_gb300 import workloads as W
-    dev = torch.device("cuda", 0)
+    hbm, kind = load_peaks()
     g = torch.Generator(device=dev).manual_seed(0)
     u0 = torch.randn((batch, n, n + 1), generator=g, device=dev)
     v0 = torch.randn((batch, n + 1, n), generator=g, device=dev)
@@ -931,16 +928,14 @@ def profile_stencil(batch, n) -> int:
     ctx = hp.Context(batch, n, n)
     div = torch.empty((batch, n, n), dtype=torch.float32, device=dev)
     mask = torch.empty_like(fl)
-    u, v = u0.clone(), v0.clone()
-    prm = hp.ProjectParams(threshold=1e30, max_iters=0, sweep_kernel=2)
     calls = {
         "divergence": (lambda: hp.hp_divergence(u0, v0, fl, div_out=div), 13),
         "face_mask": (lambda: hp.hp_face_mask(fl, mask_out=mask), 2),
         "div_norms": (lambda: hp.hp_div_norms(ctx, u0, v0, fl), 9),
-        "projection_no_sweep": (lambda: hp.hp_project(ctx, u, v, fl, prm), 13 + 25 + 9),
     }
     cells = batch * n * n
-    out = {"profile_stencil": [batch, n]}
+    out = {"workload": f"{batch} x {n}^2, random obstacles and velocities",
+           "peak_gbs": hbm, "peak_kind": kind}
     for name, (fn, bpc) in calls.items():
         for _ in range(3):
             fn()
@@ -952,9 +947,24 @@ def profile_stencil(batch, n) -> int:
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / 20
-        out[name] = {"ms": ms, "bytes_per_cell": bpc, "gbs": bpc * cells / (ms * 1e-3) / 1e9}
-    print(json.dumps(out))
+        gbs = bpc * cells / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes_per_cell": bpc, "gbs": gbs, "frac": gbs / hbm}
+    out["note"] = "whole calls (the norms with their clearing and FP64 finishing kernels)"
     ctx.close()
+    del u0, v0, div, mask, fl
+    torch.cuda.empty_cache()
+    return out
+
+
+def profile_stencil(batch, n) -> int:
+    """Print stencil_timing for batch grids of n x n."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    out = {"profile_stencil": [batch, n]}
+    out.update(stencil_timing(hp, torch.device("cuda", 0), batch, n))
+    print(json.dumps(out))
     return 0
 
 
@@ -1329,6 +1339,8 @@ def main():
         hybrid = run_hybrid_arm(args, hp, u0, v0, fl, u, v, ctx, prm, flush, stream, ms, ws)
     pdnn = None if args.no_pdnn else run_pdnn_arm(hp, dev)
     driver = run_driver_timing(hp, u0, v0, fl)
+    # the streaming stencil calls on a DRAM-sized batch (16 x 2048^2)
+    stencil = stencil_timing(hp, dev, 16, 2048) if rank == 0 else None
 
     if rank == 0:
         line = {
@@ -1398,6 +1410,7 @@ def main():
         if pdnn is not None:
             line["pdnn_training"] = pdnn
         line["driver_step"] = driver
+        line["stencil_roofline"] = stencil
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(u_np, v_np, fl_np, gpu=gpu_result)
         print(json.dumps(line), flush=True)
