@@ -309,6 +309,24 @@ int ctas_per_grid(int ny, int nx, int T)
     return ctas_x(nx, H) * ctas_y(ny, H);
 }
 
+// Lane-ordered FP64 sum of n partials p[lane], p[lane + 32], ... (the same
+// order as one add per iteration), eight loads in flight at a time; L2 reads
+// (the partials were just written by other CTAs).
+__device__ __forceinline__ double lane_sum(const double* p, int n, int lane)
+{
+    double s = 0.0;
+    int i = lane;
+    for (; i + 7 * 32 < n; i += 8 * 32) {
+        double t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[k] = __ldcg(p + i + 32 * k);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += t[k];
+    }
+    for (; i < n; i += 32) s += __ldcg(p + i);
+    return s;
+}
+
 // Called by the last CTA of grid b after all its CTAs wrote their per-sweep
 // partial sums: E_k for the sweeps of this launch, stop decision.
 __device__ void grid_decide(const SweepArgs& a, int b, int T, int k0, int src, int nct)
@@ -318,8 +336,7 @@ __device__ void grid_decide(const SweepArgs& a, int b, int T, int k0, int src, i
     const double inv_cells = 1.0 / ((double)a.nx * (double)a.ny);
     if (wid < T) {
         const double* p = a.partial + ((size_t)b * kMaxBlock + wid) * nct;
-        double s = 0.0;
-        for (int i = lane; i < nct; i += 32) s += __ldcg(p + i);
+        double s = lane_sum(p, nct, lane);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if (lane == 0) s_e[wid] = s * inv_cells;
@@ -568,8 +585,7 @@ __device__ __forceinline__ double s1_grid_e(const SweepArgs& a, int b, int kprev
 {
     const int lane = threadIdx.x & 31;
     const double* p = a.partial + ((size_t)b * 2 + (kprev & 1)) * nct;
-    double sum = 0.0;
-    for (int i = lane; i < nct; i += 32) sum += p[i];
+    double sum = lane_sum(p, nct, lane);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
     return __shfl_sync(0xffffffffu, sum, 0) / ((double)a.nx * (double)a.ny);
@@ -977,8 +993,7 @@ __global__ void norms_finish_kernel(const double* __restrict__ partial, int nblk
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= B) return;
-    double s = 0.0;
-    for (int q = lane; q < nblk; q += 32) s += partial[(size_t)b * nblk + q];
+    double s = lane_sum(partial + (size_t)b * nblk, nblk, lane);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) {
