@@ -165,6 +165,14 @@ def cpu_oracle_sample(u, v, fl, budget_s=20.0, gpu=None):
     res = {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{done} of the {B} grids (512^2, full projection each), FP64 C oracle, "
                      f"{el:.1f} s"}
+    # the same oracle on one host core: the first grid's full projection
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    oracle.project(u[0].astype(np.float64), v[0].astype(np.float64), fl[0], THR, CAP)
+    e1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    res["single_thread"] = {"value": 1.0 / e1, "unit": UNIT, "cores": 1,
+                            "sample": f"grid 0 (512^2, full projection), {e1:.1f} s"}
     if gpu is not None:
         it_g, u_g, v_g = gpu
         equal, near_tie, err = 0, 0, 0.0
