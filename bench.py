@@ -173,6 +173,14 @@ def cpu_oracle_sample(u, v, fl, budget_s=20.0, gpu=None):
     oracle.set_threads(cores)
     res["single_thread"] = {"value": 1.0 / e1, "unit": UNIT, "cores": 1,
                             "sample": f"grid 0 (512^2, full projection), {e1:.1f} s"}
+    # the oracle network (FP64 numpy): one MultiScale forward of one 128^2 grid
+    from oracle import cnn as OC
+    g = np.random.default_rng(0)
+    params = OC.init_params(seed=0)
+    t2 = time.perf_counter()
+    OC.forward(params, g.standard_normal((128, 128)), (g.random((128, 128)) < 0.1).astype(np.uint8))
+    res["cnn_forward_128"] = {"ms": (time.perf_counter() - t2) * 1e3,
+                              "sample": "one MultiScale forward of one 128^2 grid, FP64 numpy oracle"}
     if gpu is not None:
         it_g, u_g, v_g = gpu
         equal, near_tie, err = 0, 0, 0.0
