@@ -168,6 +168,9 @@ __global__ void cnn_scale_finish_kernel(const double* __restrict__ part_sum,
                                         const unsigned long long* __restrict__ part_cnt,
                                         float* __restrict__ s)
 {
+    // a programmatic dependent of the partial sums
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int b = blockIdx.x, lane = threadIdx.x;
     double t = lane < kScaleCtas ? part_sum[(size_t)b * kScaleCtas + lane] : 0.0;
     unsigned long long c = lane < kScaleCtas ? part_cnt[(size_t)b * kScaleCtas + lane] : 0ull;
@@ -234,6 +237,9 @@ struct BranchIn {
 __global__ void branch_input_kernel(BranchIn in, int cin, float* __restrict__ xin,
                                     __nv_bfloat16* __restrict__ x16, int B)
 {
+    // a programmatic dependent of the kernel before it (s, the coarser output)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int hs = in.H / in.scale, ws = in.W / in.scale;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ws) return;
@@ -368,6 +374,9 @@ __device__ __forceinline__ void branch_at4(const BranchIn& in, int b, int i0, in
 __global__ void branch_input4_kernel(BranchIn in, int cin, float* __restrict__ xin,
                                      __nv_bfloat16* __restrict__ x16, int B)
 {
+    // a programmatic dependent of the kernel before it (s, the coarser output)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int hs = in.H / in.scale, ws = in.W / in.scale;
     const size_t quads = (size_t)B * hs * ws / 4;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < quads;
@@ -408,6 +417,10 @@ __global__ void branch_input4_kernel(BranchIn in, int cin, float* __restrict__ x
 __global__ void maxpool2_kernel(const uint4* __restrict__ x, uint4* __restrict__ y, int H, int W,
                                 int c8)
 {
+    // a programmatic dependent of the layer before it
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     const int Ho = H / 2, Wo = W / 2;
     const int xi = blockIdx.y * blockDim.x + threadIdx.x;
     if (xi >= Wo * c8) return;
@@ -443,6 +456,10 @@ __global__ void maxpool2_kernel(const uint4* __restrict__ x, uint4* __restrict__
 __global__ void up_concat_kernel(const uint4* __restrict__ coarse, const uint4* __restrict__ skip,
                                  uint4* __restrict__ y, int H, int W)
 {
+    // a programmatic dependent of the layer before it
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     const int Hc = H / 2, Wc = W / 2;
     const int xi = blockIdx.y * blockDim.x + threadIdx.x;
     if (xi >= W * 8) return;
@@ -514,6 +531,10 @@ __global__ void __launch_bounds__(128)
     for (int q = threadIdx.x; q < 9 * CIN * 32; q += blockDim.x) sw[q] = w[q];
     if (threadIdx.x < 32) sb[threadIdx.x] = bias[threadIdx.x];
     __syncthreads();
+    // weights staged; the input is the branch input kernel's output
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
     const int W2 = (W + 1) / 2;
     const long P2 = (long)B * H * W2;
     for (long p2 = (long)blockIdx.x * blockDim.x + threadIdx.x; p2 < P2;
@@ -586,6 +607,9 @@ __global__ void __launch_bounds__(128)
     __shared__ __align__(16) float sw[9 * 32];
     for (int q = threadIdx.x; q < 9 * 32; q += blockDim.x) sw[q] = w[q];
     __syncthreads();
+    // weights staged; the input is the layer before's output
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const float b0 = bias[0];
     const int strips = (H + kLastRows - 1) / kLastRows;
     const long T = (long)B * strips * W;
@@ -720,6 +744,25 @@ static bool cnn_shape_ok(const hp_cnn* c, hp_shape s)
                (size_t)c->max_shape.batch * c->max_shape.ny * c->max_shape.nx;
 }
 
+// A launch as a programmatic dependent of the kernel before it in the stream:
+// the kernel waits (griddepcontrol.wait) before it reads what that kernel
+// wrote, and may start while that kernel ends.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                    cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 static hp_status launch_scale(hp_cnn* c, const float* div, const uint8_t* flags, int B,
                               size_t cells, cudaStream_t st)
 {
@@ -727,7 +770,10 @@ static hp_status launch_scale(hp_cnn* c, const float* div, const uint8_t* flags,
                                                                           c->s_cnt, cells);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
-    cnn_scale_finish_kernel<<<B, 32, 0, st>>>(c->s_part, c->s_cnt, c->s);
+    cudaError_t e = launch_dependent(cnn_scale_finish_kernel, dim3(B), dim3(32), st,
+                                     (const double*)c->s_part,
+                                     (const unsigned long long*)c->s_cnt, c->s);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return check_launch();
 }
 
@@ -748,25 +794,33 @@ static hp_status launch_first(hp_cnn* c, int k, const BranchIn& in, int cin, flo
         (reinterpret_cast<uintptr_t>(in.flags) & 15) == 0) {
         const long quads = (long)B * H * W / 4;
         const int blocks = (int)((quads + 255) / 256 < cap ? (quads + 255) / 256 : cap);
-        branch_input4_kernel<<<blocks, 256, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
+        cudaError_t e = launch_dependent(branch_input4_kernel, dim3(blocks), dim3(256), st, in, cin,
+                                         xin, tc ? c->x16 : nullptr, B);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     } else {
         const int rows = B * H;
         const dim3 grid((W + 127) / 128, rows < 65535 ? rows : 65535);
-        branch_input_kernel<<<grid, 128, 0, st>>>(in, cin, xin, tc ? c->x16 : nullptr, B);
+        cudaError_t e = launch_dependent(branch_input_kernel, grid, dim3(128), st, in, cin, xin,
+                                         tc ? c->x16 : nullptr, B);
+        if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     }
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     if (tc)
         return launch_conv3x3_tc(c->x16, c->wtc_first[k], bias, y, B, H, W, 16, 32, 1, c->err,
-                                 c->num_sms, st, c->wait_limit);
+                                 c->num_sms, st, c->wait_limit, true);
     const long P2 = (long)B * H * ((W + 1) / 2);
     const int blocks2 = (int)((P2 + 127) / 128 < cap ? (P2 + 127) / 128 : cap);
+    cudaError_t e;
     if (cin == 2)
-        conv_first_kernel<2><<<blocks2, 128, 0, st>>>(xin, w, bias, y, B, H, W);
+        e = launch_dependent(conv_first_kernel<2>, dim3(blocks2), dim3(128), st,
+                             (const float*)xin, w, bias, y, B, H, W);
     else if (cin == 3)
-        conv_first_kernel<3><<<blocks2, 128, 0, st>>>(xin, w, bias, y, B, H, W);
+        e = launch_dependent(conv_first_kernel<3>, dim3(blocks2), dim3(128), st,
+                             (const float*)xin, w, bias, y, B, H, W);
     else
         return HP_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return check_launch();
 }
 
@@ -777,11 +831,13 @@ static hp_status launch_last(hp_cnn* c, int k, const __nv_bfloat16* x, const flo
 {
     if (W >= conv_tc_min_width())
         return launch_conv3x3_tc_out1(x, c->wtc_last[k], c->btc_last[k], y, B, H, W, c->err,
-                                      c->num_sms, st, c->wait_limit);
+                                      c->num_sms, st, c->wait_limit, true);
     const long T = (long)B * ((H + kLastRows - 1) / kLastRows) * W;
     const long cap = 16L * c->num_sms;
     const int blocks = (int)((T + 127) / 128 < cap ? (T + 127) / 128 : cap);
-    conv_last_kernel<<<blocks, 128, 0, st>>>(x, w, bias, y, B, H, W);
+    cudaError_t e = launch_dependent(conv_last_kernel, dim3(blocks), dim3(128), st, x, w, bias, y,
+                                     B, H, W);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return check_launch();
 }
 
@@ -811,22 +867,25 @@ static hp_status unet_forward(hp_cnn* c, const float* div, const uint8_t* flags,
     auto conv = [&](const void* x, void* y, int H, int W) {
         if (rc == HP_OK)
             rc = launch_conv3x3_tc(x, c->w[l], c->bias[l], y, B, H, W, sp[l].cin, sp[l].cout,
-                                   sp[l].relu, c->err, c->num_sms, st, c->wait_limit);
+                                   sp[l].relu, c->err, c->num_sms, st, c->wait_limit, true);
         ++l;
     };
     // one block row per output row, the row's items across blockIdx.y
     auto pool = [&](const __nv_bfloat16* x, __nv_bfloat16* y, int H, int W) {
         if (rc != HP_OK) return;
         const dim3 grid((unsigned)(B * (H / 2)), (unsigned)((W / 2 * 4 + 255) / 256));
-        maxpool2_kernel<<<grid, 256, 0, st>>>((const uint4*)x, (uint4*)y, H, W, 4);
+        cudaError_t e = launch_dependent(maxpool2_kernel, grid, dim3(256), st, (const uint4*)x,
+                                         (uint4*)y, H, W, 4);
+        if (e != cudaSuccess) { set_cuda_error(e); rc = HP_ERR_CUDA; return; }
         rc = check_launch();
     };
     auto up_concat = [&](const __nv_bfloat16* coarse, const __nv_bfloat16* sk, __nv_bfloat16* y,
                          int H, int W) {
         if (rc != HP_OK) return;
         const dim3 grid((unsigned)(B * H), (unsigned)((W * 8 + 255) / 256));
-        up_concat_kernel<<<grid, 256, 0, st>>>((const uint4*)coarse, (const uint4*)sk, (uint4*)y,
-                                               H, W);
+        cudaError_t e = launch_dependent(up_concat_kernel, grid, dim3(256), st,
+                                         (const uint4*)coarse, (const uint4*)sk, (uint4*)y, H, W);
+        if (e != cudaSuccess) { set_cuda_error(e); rc = HP_ERR_CUDA; return; }
         rc = check_launch();
     };
     __nv_bfloat16* a = c->act[0];
@@ -1113,7 +1172,7 @@ hp_status hp_cnn_forward(hp_cnn* c, const float* div, const uint8_t* flags, floa
         while (c->spec[l].cout != 1) {
             rc = launch_conv3x3_tc(c->act[cur], c->w[l], c->bias[l], c->act[cur ^ 1], s.batch, H,
                                    W, c->spec[l].cin, c->spec[l].cout, c->spec[l].relu, c->err,
-                                   c->num_sms, st, c->wait_limit);
+                                   c->num_sms, st, c->wait_limit, true);
             if (rc != HP_OK) return rc;
             cur ^= 1;
             ++l;
@@ -2224,7 +2283,7 @@ static hp_status trainer_forward(hp_trainer* t, const float* div, const uint8_t*
         while (sp[l].cout != 1) {
             rc = launch_conv3x3_tc(t->act[l - 1], c->w[l], c->bias[l], t->act[l], s.batch, H, W,
                                    sp[l].cin, sp[l].cout, sp[l].relu, c->err, c->num_sms,
-                                   st, c->wait_limit);
+                                   st, c->wait_limit, true);
             if (rc != HP_OK) return rc;
             ++l;
         }

@@ -152,6 +152,10 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
+    // a programmatic dependent of the layer before it: inputs read and outputs
+    // written once that layer has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     const long P = (long)B * H * W;
     const uint32_t idesc = mma_idesc(kTileM, COUT);
@@ -575,6 +579,12 @@ __global__ void __launch_bounds__(kWsThreads, (ws_ctas_per_sm<CIN, COUT, OUT1>()
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // Launched as a programmatic dependent of the layer before it, the
+    // prologue above (tensor memory, barriers, weights, bias) overlaps that
+    // layer's end; the inputs are read, and the outputs written, only once it
+    // has completed.  The next layer may then start its own prologue.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     bool ok = true;
 
     if (warp == 5) {
@@ -843,7 +853,7 @@ __global__ void __launch_bounds__(kWsThreads, (ws_ctas_per_sm<CIN, COUT, OUT1>()
 template <int CIN, int COUT, bool OUT1, bool DGRAD = false>
 hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, int B, int H,
                     int W, int relu, int* err, int nsm, cudaStream_t st,
-                    const void* act = nullptr, uint32_t wait_limit = 0)
+                    const void* act = nullptr, uint32_t wait_limit = 0, bool pdl = false)
 {
     using R = WsSmem<CIN, COUT, OUT1>;
     static bool rattr = false;
@@ -863,9 +873,22 @@ hp_status launch_ws(const void* x, const void* w, const float* bias, void* y, in
     const long items = (long)B * segs * nbands;
     if (items > 0x7fffffffL) return HP_ERR_INVALID_ARG;
     const int grid = items < ctas ? (int)items : (int)ctas;
-    conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD><<<grid, kWsThreads, R::kSmemRequest, st>>>(
-        (const uint4*)x, (const uint4*)w, bias, y, H, W, segs, nbands, band, (int)items, relu,
-        err, wait_limit, (const uint4*)act);
+    // pdl: a programmatic dependent of the kernel before it in the stream
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kWsThreads);
+    cfg.dynamicSmemBytes = R::kSmemRequest;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, conv3x3_tc_ws_kernel<CIN, COUT, OUT1, DGRAD>,
+                                       (const uint4*)x, (const uint4*)w, bias, y, H, W, segs,
+                                       nbands, band, (int)items, relu, err, wait_limit,
+                                       (const uint4*)act);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return check_launch();
 }
 
@@ -1208,10 +1231,11 @@ hp_status launch_wgrad_t(const void* x, const void* gy, float* part, size_t part
 
 template <int CIN, int COUT>
 hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y, int B, int H,
-                        int W, int relu, int* err, int nsm, cudaStream_t st, uint32_t wait_limit)
+                        int W, int relu, int* err, int nsm, cudaStream_t st, uint32_t wait_limit,
+                        bool pdl)
 {
     if (W >= kWsMinWidth) return launch_ws<CIN, COUT, false>(x, w, bias, y, B, H, W, relu, err,
-                                                            nsm, st, nullptr, wait_limit);
+                                                            nsm, st, nullptr, wait_limit, pdl);
     using S = ConvSmem<CIN, COUT>;
     static bool attr = false;
     if (!attr) {
@@ -1223,8 +1247,20 @@ hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y
     const long P = (long)B * H * W;
     const int ntiles = (int)((P + kTileM - 1) / kTileM);
     const int grid = ntiles < nsm ? ntiles : nsm;
-    conv3x3_tc_kernel<CIN, COUT><<<grid, kConvThreads, S::kBytes, st>>>(
-        (const uint4*)x, (const uint4*)w, bias, (__nv_bfloat16*)y, B, H, W, relu, ntiles, err);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kConvThreads);
+    cfg.dynamicSmemBytes = S::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, conv3x3_tc_kernel<CIN, COUT>, (const uint4*)x,
+                                       (const uint4*)w, bias, (__nv_bfloat16*)y, B, H, W, relu,
+                                       ntiles, err);
+    if (e != cudaSuccess) { set_cuda_error(e); return HP_ERR_CUDA; }
     return check_launch();
 }
 
@@ -1232,21 +1268,21 @@ hp_status launch_conv_t(const void* x, const void* w, const float* bias, void* y
 
 hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
                             int H, int W, int cin, int cout, int relu, int* err, int nsm,
-                            cudaStream_t st, uint32_t wait_limit)
+                            cudaStream_t st, uint32_t wait_limit, bool pdl)
 {
     if (cin == 32 && cout == 32)
-        return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+        return launch_conv_t<32, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit, pdl);
     if (cin == 32 && cout == 64)
-        return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+        return launch_conv_t<32, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit, pdl);
     if (cin == 64 && cout == 32)
-        return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+        return launch_conv_t<64, 32>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit, pdl);
     if (cin == 64 && cout == 64)
-        return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit);
+        return launch_conv_t<64, 64>(x, w, bias, y, B, H, W, relu, err, nsm, st, wait_limit, pdl);
     // first layer of a branch, input padded to 16 channels (warp-specialised
     // kernel only; narrower images take the CUDA-core layer)
     if (cin == 16 && cout == 32 && W >= kWsMinWidth)
         return launch_ws<16, 32, false>(x, w, bias, y, B, H, W, relu, err, nsm, st, nullptr,
-                                        wait_limit);
+                                        wait_limit, pdl);
     return HP_ERR_UNSUPPORTED;
 }
 
@@ -1308,10 +1344,11 @@ hp_status launch_conv3x3_tc_wgrad(const void* x, const void* gy, float* part, si
 // warp-specialised kernel serves.
 hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias, float* y,
                                  int B, int H, int W, int* err, int nsm, cudaStream_t st,
-                                 uint32_t wait_limit)
+                                 uint32_t wait_limit, bool pdl)
 {
     if (W < kWsMinWidth) return HP_ERR_UNSUPPORTED;
-    return launch_ws<32, 16, true>(x, w, bias, y, B, H, W, 0, err, nsm, st, nullptr, wait_limit);
+    return launch_ws<32, 16, true>(x, w, bias, y, B, H, W, 0, err, nsm, st, nullptr, wait_limit,
+                                   pdl);
 }
 
 }  // namespace hp

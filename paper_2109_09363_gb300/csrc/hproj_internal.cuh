@@ -248,16 +248,19 @@ bool project_args_ok(const hp_ctx* c, const float* u, const float* v, const uint
 
 int ctas_per_grid(int ny, int nx, int T);
 // wait_limit: polls of each bounded pipeline wait of the tensor-core kernels
-// before it gives up and raises bit 0 of *err (0 = the compiled limit)
+// before it gives up and raises bit 0 of *err (0 = the compiled limit); pdl:
+// launched as a programmatic dependent of the kernel before it in the stream
+// (its prologue overlaps that kernel's end; it reads and writes activations
+// only after that kernel has completed)
 hp_status launch_conv3x3_tc(const void* x, const void* w, const float* bias, void* y, int B,
                             int H, int W, int cin, int cout, int relu, int* err, int nsm,
-                            cudaStream_t st, uint32_t wait_limit = 0);
+                            cudaStream_t st, uint32_t wait_limit = 0, bool pdl = false);
 // narrowest image the warp-specialised convolution (and the tensor-core first
 // and last layers of a branch) serves
 int conv_tc_min_width();
 hp_status launch_conv3x3_tc_out1(const void* x, const void* w, const float* bias, float* y,
                                  int B, int H, int W, int* err, int nsm, cudaStream_t st,
-                                 uint32_t wait_limit = 0);
+                                 uint32_t wait_limit = 0, bool pdl = false);
 // backward of a tensor-core layer cin -> cout (32 or 64 channels each):
 // input gradient (BF16, zero-padded transposed convolution with the flipped
 // weights wdg BF16 [9][cin][cout], ReLU derivative of act applied; the
