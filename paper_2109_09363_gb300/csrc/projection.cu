@@ -985,18 +985,29 @@ static void norms_kernel(const float* u, const float* v, const uint8_t* flags,
 }
 
 // One warp per grid: E_1 = sum of block partials (fixed order) / cells.
+// One block of kFinishWarps warps per grid: warp w adds its contiguous share
+// of the grid's partials (lane order), then thread 0 the warps' sums in
+// order; a fixed order, so E_1 is the same on every call.
+constexpr int kFinishWarps = 8;
+
 __global__ void norms_finish_kernel(const double* __restrict__ partial, int nblk,
                                     const uint32_t* __restrict__ einf_bits, size_t einf_stride,
                                     double* e1, double* einf, const GridState* gs, int32_t* iters,
                                     uint8_t* conv, int B, double inv_cells)
 {
-    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (b >= B) return;
-    double s = lane_sum(partial + (size_t)b * nblk, nblk, lane);
+    __shared__ double s_w[kFinishWarps];
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int share = (nblk + kFinishWarps - 1) / kFinishWarps;
+    const int q0 = wid * share, q1 = min(nblk, q0 + share);
+    double s = q1 > q0 ? lane_sum(partial + (size_t)b * nblk + q0, q1 - q0, lane) : 0.0;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) {
+    if (lane == 0) s_w[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s = 0.0;
+        for (int w = 0; w < kFinishWarps; ++w) s += s_w[w];
         if (e1) e1[b] = s * inv_cells;
         if (einf) einf[b] = (double)__uint_as_float(einf_bits[(size_t)b * einf_stride]);
         if (gs) {
@@ -1027,7 +1038,7 @@ hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
     if (rc != HP_OK) return rc;
     norms_kernel(u, v, flags, nullptr, partial, einf_bits, stride, s, Boundary{}, st);
     if ((rc = check_launch()) != HP_OK) return rc;
-    norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
+    norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
         partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
         1.0 / ((double)s.nx * (double)s.ny));
     return check_launch();
@@ -1046,7 +1057,7 @@ hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t
     if (rc != HP_OK) return rc;
     norms_kernel(u, v, flags, nullptr, partial, einf_bits, stride, s, Boundary{}, st);
     if ((rc = check_launch()) != HP_OK) return rc;
-    norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
+    norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
         partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
         1.0 / ((double)s.nx * (double)s.ny));
     return check_launch();
@@ -1311,7 +1322,7 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
         norms_kernel(u, v, flags, ctx->mask, ctx->partial2, einf_bits, stride, s, bc, st);
         if ((rc = check_launch()) != HP_OK) return rc;
     }
-    norms_finish_kernel<<<(s.batch + 7) / 8, 256, 0, st>>>(
+    norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
         ctx->partial2, nblk, einf_bits, stride, u ? e1_out : nullptr, u ? einf_out : nullptr,
         ctx->gs, iters_out, fixed ? nullptr : conv_out, s.batch,
         1.0 / ((double)s.nx * (double)s.ny));
