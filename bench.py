@@ -194,7 +194,8 @@ def cpu_oracle_sample(u, v, fl, budget_s=20.0, gpu=None):
             else:
                 lo, hi = sorted((ko, kg))
                 eh = ref["e_hist"][0, lo:hi + 1]
-                near_tie += int(np.all(np.abs(eh - THR) / THR <= 5e-5))
+                eh = eh[np.isfinite(eh)]  # the oracle's history ends at its own stop
+                near_tie += int(eh.size > 0 and np.all(np.abs(eh - THR) / THR <= 5e-5))
         res["parity"] = {"grids": min(done, B), "iters_equal": equal,
                          "iters_differ_at_a_near_tie": near_tie,
                          "max_velocity_error_rel": err,

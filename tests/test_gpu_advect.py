@@ -86,7 +86,9 @@ def test_plume_128_teacher_forced(dev, threshold):
         if kg != ko:
             eh = ref["e_hist"][0]
             lo, hi = min(kg, ko), max(kg, ko)
-            assert np.all(np.abs(eh[lo:hi + 1] - threshold) / threshold <= 5e-5), (step, kg, ko)
+            seg = eh[lo:hi + 1]
+            seg = seg[np.isfinite(seg)]  # the oracle's history ends at its own stop
+            assert seg.size and np.all(np.abs(seg - threshold) / threshold <= 5e-5), (step, kg, ko)
             ref = oracle.project(ustar[0], ustar[1], fl, threshold, 2000, dt=cfg.dt,
                                  fixed_iters=kg)
         pu, pv = sim.u.cpu().numpy()[0], sim.v.cpu().numpy()[0]

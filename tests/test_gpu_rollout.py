@@ -164,7 +164,9 @@ def test_plume_1024_cylinder_and_hybrid_step(dev):
         if kg != ko:
             eh = ref["e_hist"][0]
             lo, hi = sorted((kg, ko))
-            assert np.all(np.abs(eh[lo:hi + 1] - thr) / thr <= 5e-5), (step, kg, ko)
+            seg = eh[lo:hi + 1]
+            seg = seg[np.isfinite(seg)]  # the oracle's history ends at its own stop
+            assert seg.size and np.all(np.abs(seg - thr) / thr <= 5e-5), (step, kg, ko)
             ref = oracle.project(ustar[0][None], ustar[1][None], fl, thr, cap, dt=cfg.dt,
                                  fixed_iters=kg)
         pu, pv = sim.u.cpu().numpy()[0], sim.v.cpu().numpy()[0]
@@ -193,7 +195,9 @@ def test_plume_1024_cylinder_and_hybrid_step(dev):
     if kg != ko:
         eh = ref["e_hist"][0]
         lo, hi = sorted((kg, ko))
-        assert np.all(np.abs(eh[lo:hi + 1] - thr) / thr <= 5e-5), (kg, ko)
+        seg = eh[lo:hi + 1]
+        seg = seg[np.isfinite(seg)]  # the oracle's history ends at its own stop
+        assert seg.size and np.all(np.abs(seg - thr) / thr <= 5e-5), (kg, ko)
     else:
         umax = max(np.abs(ref["u"]).max(), np.abs(ref["v"]).max(), 1e-30)
         assert np.abs(uh.cpu().numpy()[0] - ref["u"][0]).max() <= tol * umax
@@ -224,7 +228,9 @@ def test_plume_2048_eight_cylinders_and_unet_hybrid(dev):
         if kg != ko:
             eh = ref["e_hist"][0]
             lo, hi = sorted((kg, ko))
-            assert np.all(np.abs(eh[lo:hi + 1] - thr) / thr <= 5e-5), (kg, ko)
+            seg = eh[lo:hi + 1]
+            seg = seg[np.isfinite(seg)]  # the oracle's history ends at its own stop
+            assert seg.size and np.all(np.abs(seg - thr) / thr <= 5e-5), (kg, ko)
             ref = oracle.project(ustar[0][None], ustar[1][None], fl, thr, cap, dt=cfg.dt,
                                  phi0=phi0, fixed_iters=kg)
         umax = max(np.abs(ref["u"]).max(), np.abs(ref["v"]).max(), 1e-30)
