@@ -886,6 +886,15 @@ def run_driver_timing(hp, u0, v0, fl, reps: int = 10):
         b.record()
         torch.cuda.synchronize()
         res[f"{name}_ms"] = a.elapsed_time(b) / reps
+    # algorithmic bytes of one step: u, v, rho and the flags read once, u*,
+    # v* and the new rho written once
+    floats = ny * (nx + 1) + (ny + 1) * nx + ny * nx
+    step_bytes = B_ * (2 * 4 * floats + ny * nx)
+    peak, kind = load_peaks()
+    for name in ("sl", "maccormack"):
+        gbs = step_bytes / res[f"{name}_ms"] / 1e6
+        res[f"{name}_hbm"] = {"gbs": gbs, "frac": gbs / peak, "peak_kind": kind,
+                              "bytes_per_step": step_bytes}
     head = torch.empty((B_, 3), dtype=torch.int32, device=u0.device)
     for _ in range(3):
         hp.hp_plume_head(outs[2], 1.0, 0.01, out=head)
@@ -981,6 +990,24 @@ def profile_stencil(batch, n) -> int:
     import paper_2109_09363_gb300 as hp
     out = {"profile_stencil": [batch, n]}
     out.update(stencil_timing(hp, torch.device("cuda", 0), batch, n))
+    print(json.dumps(out))
+    return 0
+
+
+def profile_advect(batch, n) -> int:
+    """Print run_driver_timing for batch vortex grids of n x n."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_09363_gb300 as hp
+    from paper_2109_09363_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    u, v, fl = W.batched_vortex_case(batch, n)
+    ud = torch.from_numpy(u.astype(np.float32)).to(dev)
+    vd = torch.from_numpy(v.astype(np.float32)).to(dev)
+    fd = torch.from_numpy(fl).to(dev)
+    out = {"profile_advect": [batch, n]}
+    out.update(run_driver_timing(hp, ud, vd, fd))
     print(json.dumps(out))
     return 0
 
@@ -1110,6 +1137,9 @@ def main():
     ap.add_argument("--profile-stencil", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only time the divergence, mask, norms and a projection without "
                          "sweeps on BATCH grids of N x N")
+    ap.add_argument("--profile-advect", nargs=2, type=int, metavar=("BATCH", "N"),
+                    help="time the driver step (first-order and MacCormack advection) on "
+                         "BATCH vortex grids of N x N and exit")
     ap.add_argument("--profile-cnn", nargs=2, type=int, metavar=("BATCH", "N"),
                     help="only run the CNN forward on BATCH grids of N x N, 3 times")
     ap.add_argument("--profile-cnn-scaling", action="store_true",
@@ -1145,6 +1175,8 @@ def main():
         return profile_conv(*args.profile_conv)
     if args.profile_stencil:
         return profile_stencil(*args.profile_stencil)
+    if args.profile_advect:
+        return profile_advect(*args.profile_advect)
     if args.profile_cnn:
         return profile_cnn(*args.profile_cnn, arch=args.arch)
     if args.profile_cnn_scaling:

@@ -26,7 +26,7 @@ struct Field {
     const float* q;  // [My][Mx]
     int Mx, My;
     float ox, oy;    // position of sample (0, 0)
-    __device__ float at(int i, int j) const { return q[(size_t)j * Mx + i]; }
+    __device__ float at(int i, int j) const { return __ldg(q + (size_t)j * Mx + i); }
 };
 
 // Bilinear sample at (x, y); the position is clamped to the sample span.
@@ -39,8 +39,11 @@ __device__ __forceinline__ float sample(const Field& f, float x, float y)
     j0 = min(j0, max(f.My - 2, 0));
     const float fx = tx - (float)i0, fy = ty - (float)j0;
     const int i1 = min(i0 + 1, f.Mx - 1), j1 = min(j0 + 1, f.My - 1);
-    const float q00 = f.q[(size_t)j0 * f.Mx + i0], q01 = f.q[(size_t)j0 * f.Mx + i1];
-    const float q10 = f.q[(size_t)j1 * f.Mx + i0], q11 = f.q[(size_t)j1 * f.Mx + i1];
+    // read-only for the whole step (the outputs do not alias the inputs)
+    const float* r0 = f.q + (size_t)j0 * f.Mx;
+    const float* r1 = f.q + (size_t)j1 * f.Mx;
+    const float q00 = __ldg(r0 + i0), q01 = __ldg(r0 + i1);
+    const float q10 = __ldg(r1 + i0), q11 = __ldg(r1 + i1);
     const float top = q00 * (1.0f - fx) + q01 * fx;
     const float bot = q10 * (1.0f - fx) + q11 * fx;
     return top * (1.0f - fy) + bot * fy;
@@ -53,7 +56,7 @@ struct Rho {
     float rho_in;
     __device__ float at(int i, int j) const
     {
-        return (j == ny - 1 && i >= x0 && i < x1) ? rho_in : q[(size_t)j * nx + i];
+        return (j == ny - 1 && i >= x0 && i < x1) ? rho_in : __ldg(q + (size_t)j * nx + i);
     }
 };
 
@@ -97,12 +100,19 @@ struct Forward {
     const Field& fv;
     int Mx, My;
     float ox, oy, dt;
-    __device__ float at(int i, int j) const
+    // the forward value at sample (i, j), with the velocity (vx, vy) there
+    __device__ float at_vel(int i, int j, float& vx, float& vy) const
     {
         const float x = (float)i + ox, y = (float)j + oy;
-        const float vx = sample(fu, x, y), vy = sample(fv, x, y);
+        vx = sample(fu, x, y);
+        vy = sample(fv, x, y);
         const View<Q> w = {q, Mx, My, ox, oy};
         return sample_range(w, x - dt * vx, y - dt * vy, nullptr, nullptr);
+    }
+    __device__ float at(int i, int j) const
+    {
+        float vx, vy;
+        return at_vel(i, j, vx, vy);
     }
 };
 
@@ -160,49 +170,159 @@ __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const
     }
 }
 
-// One thread per (i, j) in [0, nx] x [0, ny]: cell (i, j) density, u face
-// (j, i), v face (j, i) with buoyancy.
-template <bool MC>
-__global__ void advect_kernel(const float* __restrict__ u, const float* __restrict__ v,
-                              const float* __restrict__ rho, const uint8_t* __restrict__ flags,
-                              float* __restrict__ u_out, float* __restrict__ v_out,
-                              float* __restrict__ rho_out, int ny, int nx, hp_plume_params p)
+// Tiles of the fused step: a CTA produces the outputs of kAdvTX x kAdvTY
+// indices (i, j) of [0, nx] x [0, ny] (cell (i, j) density, u face (j, i),
+// v face (j, i)).  MacCormack's backward sample reads the forward field at
+// four corners within kAdvH samples of its own index whenever the
+// displacement dt |vel| is below kAdvH cells; the CTA evaluates the forward
+// field of each quantity once on its tile widened by kAdvH (and one row more
+// above, for the density of the row above the tile that the buoyancy of the
+// tile's top v faces reads) and keeps it in shared memory.  A corner outside
+// that window (a faster flow) is evaluated where it is needed, with the same
+// arithmetic, so the result does not depend on the window.
+constexpr int kAdvTX = 32, kAdvTY = 16, kAdvH = 2, kAdvThreads = 256;
+constexpr int kFW = kAdvTX + 2 * kAdvH;      // columns of a forward-field window
+constexpr int kFH = kAdvTY + 2 * kAdvH + 1;  // rows: tile rows - 1 - kAdvH .. + kAdvH
+
+// Forward field of quantity Q on its window (sample (ci, cj) at entry 0),
+// evaluated where it is not in the window.
+template <class Q>
+struct WindowedForward {
+    Forward<Q> f;
+    const float* s;
+    int ci, cj;
+    __device__ float at(int i, int j) const
+    {
+        const int a = i - ci, b = j - cj;
+        if (a >= 0 && a < kFW && b >= 0 && b < kFH) return s[b * kFW + a];
+        return f.at(i, j);
+    }
+};
+
+// Fills the window of quantity q (Mx x My samples at (ox, oy)) with the
+// forward values and the velocities at the samples: the samples of the field
+// only (entries outside it are never read: every corner of a bilinear sample
+// lies in the field, and so does every output sample).
+template <class Q>
+__device__ __forceinline__ void fill_window(float* s, float* svx, float* svy, const Forward<Q>& f,
+                                            int ci, int cj)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const int b = blockIdx.z;
-    if (i > nx) return;
+    for (int t = threadIdx.x; t < kFH * kFW; t += kAdvThreads) {
+        const int b = t / kFW, a = t - b * kFW;
+        const int i = ci + a, j = cj + b;
+        if (i >= 0 && i < f.Mx && j >= 0 && j < f.My) {
+            float vx, vy;
+            s[t] = f.at_vel(i, j, vx, vy);
+            svx[t] = vx;
+            svy[t] = vy;
+        }
+    }
+}
+
+// New value of sample (i, j) of quantity q: as advected<MC>, MacCormack's
+// backward sample and the velocity at (i, j) taken from the window.
+template <bool MC, class Q>
+__device__ __forceinline__ float advected_w(const Q& q, int Mx, int My, float ox, float oy,
+                                            const Field& fu, const Field& fv, float dt,
+                                            const float* win, const float* wvx,
+                                            const float* wvy, int ci, int cj, int i, int j)
+{
+    if constexpr (!MC) {
+        return advected<false>(q, Mx, My, ox, oy, fu, fv, dt, i, j);
+    } else {
+        const float x = (float)i + ox, y = (float)j + oy;
+        const int t = (j - cj) * kFW + (i - ci);
+        const float vx = wvx[t], vy = wvy[t];
+        const View<Q> w = {q, Mx, My, ox, oy};
+        float lo, hi;
+        const float qf = sample_range(w, x - dt * vx, y - dt * vy, &lo, &hi);
+        const WindowedForward<Q> fwd = {{q, fu, fv, Mx, My, ox, oy, dt}, win, ci, cj};
+        const View<WindowedForward<Q>> wf = {fwd, Mx, My, ox, oy};
+        const float qb = sample_range(wf, x + dt * vx, y + dt * vy, nullptr, nullptr);
+        return fminf(fmaxf(qf + 0.5f * (q.at(i, j) - qb), lo), hi);
+    }
+}
+
+// One CTA per tile: (MacCormack) the three forward-field windows; the new
+// density of the tile's rows and the row above, kept in shared memory for
+// the buoyancy; then the u and v faces.
+template <bool MC>
+__global__ void __launch_bounds__(kAdvThreads) advect_kernel(
+    const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ rho,
+    const uint8_t* __restrict__ flags, float* __restrict__ u_out, float* __restrict__ v_out,
+    float* __restrict__ rho_out, int ny, int nx, hp_plume_params p)
+{
+    // forward rho, u, v and the velocity at their samples
+    __shared__ float s_win[MC ? 3 : 1][MC ? kFH * kFW : 1];
+    __shared__ float s_vx[MC ? 3 : 1][MC ? kFH * kFW : 1];
+    __shared__ float s_vy[MC ? 3 : 1][MC ? kFH * kFW : 1];
+    __shared__ float s_rho[(kAdvTY + 1) * kAdvTX];           // new rho, rows j0 - 1 ..
+    const int i0 = blockIdx.x * kAdvTX, j0 = blockIdx.y * kAdvTY, b = blockIdx.z;
     const size_t cells = (size_t)ny * nx;
     const Field fu = {u + (size_t)b * ny * (nx + 1), nx + 1, ny, 0.0f, 0.5f};
     const Field fv = {v + (size_t)b * (ny + 1) * nx, nx, ny + 1, 0.5f, 0.0f};
     const Rho r = {rho + b * cells, nx, ny, p.inlet_x0, p.inlet_x1, p.rho_in};
     const uint8_t* fl = flags + b * cells;
     const float dt = p.dt;
+    const int ci = i0 - kAdvH, cj = j0 - 1 - kAdvH;  // sample at entry 0 of a window
 
-    if (i < nx && j < ny)
-        rho_out[b * cells + (size_t)j * nx + i] = rho_new_at<MC>(r, fu, fv, dt, i, j);
-
-    if (j < ny) {
-        const bool open = i > 0 && i < nx && fluid(fl, nx, i - 1, j) && fluid(fl, nx, i, j);
-        float val = 0.0f;
-        if (open) val = advected<MC>(fu, nx + 1, ny, 0.0f, 0.5f, fu, fv, dt, i, j);
-        u_out[(size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1) + i] = val;
+    if constexpr (MC) {
+        fill_window(s_win[0], s_vx[0], s_vy[0], Forward<Rho>{r, fu, fv, nx, ny, 0.5f, 0.5f, dt},
+                    ci, cj);
+        fill_window(s_win[1], s_vx[1], s_vy[1],
+                    Forward<Field>{fu, fu, fv, nx + 1, ny, 0.0f, 0.5f, dt}, ci, cj);
+        fill_window(s_win[2], s_vx[2], s_vy[2],
+                    Forward<Field>{fv, fu, fv, nx, ny + 1, 0.5f, 0.0f, dt}, ci, cj);
+        __syncthreads();
     }
-    if (i < nx) {
-        const bool interior = j > 0 && j < ny && fluid(fl, nx, i, j - 1) && fluid(fl, nx, i, j);
-        // an open top keeps (advects) its faces; buoyancy acts on interior faces
-        const bool top = j == 0 && p.open_top && fluid(fl, nx, i, 0);
-        float val = 0.0f;
-        if (interior || top) val = advected<MC>(fv, nx, ny + 1, 0.5f, 0.0f, fu, fv, dt, i, j);
-        if (interior) {
-            const float rf = 0.5f * (rho_new_at<MC>(r, fu, fv, dt, i, j - 1) +
-                                     rho_new_at<MC>(r, fu, fv, dt, i, j));
-            val += dt * p.gravity * (rf - p.rho_amb);
+    constexpr int kU = MC ? 1 : 0, kV = MC ? 2 : 0;
+
+    for (int t = threadIdx.x; t < (kAdvTY + 1) * kAdvTX; t += kAdvThreads) {
+        const int rr = t / kAdvTX, c = t - rr * kAdvTX;
+        const int i = i0 + c, j = j0 - 1 + rr;
+        if (i < nx && j >= 0 && j < ny) {
+            float val;
+            if constexpr (MC)
+                val = advected_w<true>(r, nx, ny, 0.5f, 0.5f, fu, fv, dt, s_win[0], s_vx[0],
+                                       s_vy[0], ci, cj, i, j);
+            else
+                val = rho_new_at<false>(r, fu, fv, dt, i, j);
+            s_rho[t] = val;
+            if (rr > 0) rho_out[b * cells + (size_t)j * nx + i] = val;
         }
-        // injection through the inlet faces of the bottom boundary (upwards)
-        if (j == ny && i >= p.inlet_x0 && i < p.inlet_x1 && fluid(fl, nx, i, ny - 1))
-            val = -p.u_in;
-        v_out[(size_t)b * (ny + 1) * nx + (size_t)j * nx + i] = val;
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < kAdvTY * kAdvTX; t += kAdvThreads) {
+        const int rr = t / kAdvTX, c = t - rr * kAdvTX;
+        const int i = i0 + c, j = j0 + rr;
+        if (i > nx || j > ny) continue;
+        if (j < ny) {
+            const bool open = i > 0 && i < nx && fluid(fl, nx, i - 1, j) && fluid(fl, nx, i, j);
+            float val = 0.0f;
+            if (open)
+                val = advected_w<MC>(fu, nx + 1, ny, 0.0f, 0.5f, fu, fv, dt, s_win[kU], s_vx[kU],
+                                     s_vy[kU], ci, cj, i, j);
+            u_out[(size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1) + i] = val;
+        }
+        if (i < nx) {
+            const bool interior = j > 0 && j < ny && fluid(fl, nx, i, j - 1) && fluid(fl, nx, i, j);
+            // an open top keeps (advects) its faces; buoyancy acts on interior faces
+            const bool top = j == 0 && p.open_top && fluid(fl, nx, i, 0);
+            float val = 0.0f;
+            if (interior || top)
+                val = advected_w<MC>(fv, nx, ny + 1, 0.5f, 0.0f, fu, fv, dt, s_win[kV], s_vx[kV],
+                                     s_vy[kV], ci, cj, i, j);
+            if (interior) {
+                // new density of cells (i, j - 1) and (i, j): rows rr and rr + 1
+                const float rf = 0.5f * (s_rho[rr * kAdvTX + c] + s_rho[(rr + 1) * kAdvTX + c]);
+                val += dt * p.gravity * (rf - p.rho_amb);
+            }
+            // injection through the inlet faces of the bottom boundary (upwards)
+            if (j == ny && i >= p.inlet_x0 && i < p.inlet_x1 && fluid(fl, nx, i, ny - 1))
+                val = -p.u_in;
+            v_out[(size_t)b * (ny + 1) * nx + (size_t)j * nx + i] = val;
+        }
     }
 }
 
@@ -268,7 +388,8 @@ hp_status launch_advect(const float* u, const float* v, const float* rho, const 
                         float* u_out, float* v_out, float* rho_out, hp_shape s,
                         const hp_plume_params& p, cudaStream_t st)
 {
-    dim3 blk(128), grd((s.nx + 1 + 127) / 128, s.ny + 1, s.batch);
+    dim3 blk(kAdvThreads),
+        grd((s.nx + 1 + kAdvTX - 1) / kAdvTX, (s.ny + 1 + kAdvTY - 1) / kAdvTY, s.batch);
     if (p.scheme == 1)
         advect_kernel<true><<<grd, blk, 0, st>>>(u, v, rho, flags, u_out, v_out, rho_out, s.ny,
                                                  s.nx, p);

@@ -133,6 +133,37 @@ def test_maccormack_step_matches_oracle(dev, shape, dt):
                           hp.PlumeParams(dt=dt, scheme=2))
 
 
+def test_maccormack_fast_flow_matches_oracle(dev):
+    """A displacement dt |vel| of up to 4.4 cells: the backward sample's
+    corners fall inside the forward field's shared-memory window (up to two
+    samples away) for most samples and outside it for the rest, where the
+    kernel evaluates the forward field where it needs it."""
+    B, ny, nx, dt = 2, 70, 100, 8.0
+    rng = np.random.default_rng(5)
+    us, vs, rs, fs = [], [], [], []
+    for b in range(B):
+        u, v = W.vortex_velocity(ny, nx, 3 + b, n_vortices=6, width=(3, 12))
+        us.append(u); vs.append(v)
+        rs.append(1.0 + 0.05 * rng.standard_normal((ny, nx)))
+        fs.append(W.random_obstacles(ny, nx, 29 + b, rect_side=(3, 12), disc_radius=(2, 6)))
+    u = np.stack(us).astype(np.float32); v = np.stack(vs).astype(np.float32)
+    far = dt * np.abs(u) >= 2.0
+    assert 0.02 < far.mean() < 0.5
+    rho = np.stack(rs).astype(np.float32); fl = np.stack(fs)
+    inlet = (nx // 2 - 4, nx // 2 + 4)
+    pp = hp.PlumeParams(dt=dt, inlet_x0=inlet[0], inlet_x1=inlet[1], scheme=1)
+    uo, vo, ro = hp.hp_advect_step(t(u, dev), t(v, dev), t(rho, dev), t(fl, dev), pp)
+    torch.cuda.synchronize()
+    uo, vo, ro = uo.cpu().numpy(), vo.cpu().numpy(), ro.cpu().numpy()
+    for b in range(B):
+        eu, ev, er = A.advect_step(u[b], v[b], rho[b], fl[b], dt, inlet=inlet,
+                                   scheme="maccormack")
+        umax = max(np.abs(eu).max(), np.abs(ev).max())
+        assert np.abs(uo[b] - eu).max() <= TOL * umax
+        assert np.abs(vo[b] - ev).max() <= TOL * umax
+        assert np.abs(ro[b] - er).max() <= TOL * np.abs(er).max()
+
+
 def test_plume_head_matches_oracle(dev):
     n = 96
     rng = np.random.default_rng(4)
