@@ -7,9 +7,10 @@
 // MacCormack (the scheme Sec. 2.2 names, after Selle et al. 2008): q_f, the
 // forward semi-Lagrangian value, q_b, the forward field sampled backwards at
 // x + dt vel(x), and q_f + (q - q_b) / 2 clamped to the range of the four
-// samples the forward step interpolated.  The forward field is not stored:
-// the backward sample recomputes it at its four corners, so the step needs
-// no workspace.
+// samples the forward step interpolated.  The forward field is not stored
+// in global memory: each CTA evaluates it on a window around its tile in
+// shared memory (and evaluates a corner outside the window where it needs
+// it), so the step needs no workspace.
 //
 // Positions: cell (i, j) centred at (i + 1/2, j + 1/2); u face (j, i) at
 // (i, j + 1/2); v face (j, i) at (i + 1/2, j); row 0 is the top of the image.
@@ -29,24 +30,39 @@ struct Field {
     __device__ float at(int i, int j) const { return __ldg(q + (size_t)j * Mx + i); }
 };
 
-// Bilinear sample at (x, y); the position is clamped to the sample span.
-__device__ __forceinline__ float sample(const Field& f, float x, float y)
+// Velocity at sample (i, j) of a quantity whose samples sit at (i + ox,
+// j + oy): cell centres (1/2, 1/2), u faces (0, 1/2) or v faces (1/2, 0).
+// There the bilinear sample of each component has weights 0, 1 or 1/2 on a
+// row or column pair (pairs clamped to the field at its borders), so it is a
+// copy or the mean of two or four values; for finite inputs the result is
+// the same FP32 value as the general bilinear sample of sample_range()
+// (products by 1/2 are exact, and the one rounding of each weighted sum is
+// the rounding of the plain sum, halved).
+__device__ __forceinline__ void vel_at_sample(const Field& fu, const Field& fv, float ox,
+                                              float oy, int i, int j, float& vx, float& vy)
 {
-    const float tx = fminf(fmaxf(x - f.ox, 0.0f), (float)(f.Mx - 1));
-    const float ty = fminf(fmaxf(y - f.oy, 0.0f), (float)(f.My - 1));
-    int i0 = (int)floorf(tx), j0 = (int)floorf(ty);
-    i0 = min(i0, max(f.Mx - 2, 0));
-    j0 = min(j0, max(f.My - 2, 0));
-    const float fx = tx - (float)i0, fy = ty - (float)j0;
-    const int i1 = min(i0 + 1, f.Mx - 1), j1 = min(j0 + 1, f.My - 1);
-    // read-only for the whole step (the outputs do not alias the inputs)
-    const float* r0 = f.q + (size_t)j0 * f.Mx;
-    const float* r1 = f.q + (size_t)j1 * f.Mx;
-    const float q00 = __ldg(r0 + i0), q01 = __ldg(r0 + i1);
-    const float q10 = __ldg(r1 + i0), q11 = __ldg(r1 + i1);
-    const float top = q00 * (1.0f - fx) + q01 * fx;
-    const float bot = q10 * (1.0f - fx) + q11 * fx;
-    return top * (1.0f - fy) + bot * fy;
+    const int su = fu.Mx, nx = fv.Mx, ny = fu.My;  // u rows hold nx + 1 faces
+    const float* u = fu.q;
+    const float* v = fv.q;
+    if (ox != 0.0f && oy != 0.0f) {  // cell (i, j)
+        const float* ur = u + (size_t)j * su;
+        vx = 0.5f * (__ldg(ur + i) + __ldg(ur + i + 1));
+        vy = 0.5f * (__ldg(v + (size_t)j * nx + i) + __ldg(v + (size_t)(j + 1) * nx + i));
+    } else if (ox == 0.0f) {  // u face (j, i), i in [0, nx]
+        vx = __ldg(u + (size_t)j * su + i);
+        const int c0 = max(i - 1, 0), c1 = min(i, nx - 1);
+        const float* v0 = v + (size_t)j * nx;
+        const float* v1 = v0 + nx;
+        vy = 0.5f * (0.5f * (__ldg(v0 + c0) + __ldg(v0 + c1)) +
+                     0.5f * (__ldg(v1 + c0) + __ldg(v1 + c1)));
+    } else {  // v face (j, i), j in [0, ny]
+        vy = __ldg(v + (size_t)j * nx + i);
+        const int r0 = max(j - 1, 0), r1 = min(j, ny - 1);
+        const float* u0 = u + (size_t)r0 * su;
+        const float* u1 = u + (size_t)r1 * su;
+        vx = 0.5f * (0.5f * (__ldg(u0 + i) + __ldg(u0 + i + 1)) +
+                     0.5f * (__ldg(u1 + i) + __ldg(u1 + i + 1)));
+    }
 }
 
 // Density field with the inlet applied: rho_in on the inlet cells.
@@ -104,8 +120,7 @@ struct Forward {
     __device__ float at_vel(int i, int j, float& vx, float& vy) const
     {
         const float x = (float)i + ox, y = (float)j + oy;
-        vx = sample(fu, x, y);
-        vy = sample(fv, x, y);
+        vel_at_sample(fu, fv, ox, oy, i, j, vx, vy);
         const View<Q> w = {q, Mx, My, ox, oy};
         return sample_range(w, x - dt * vx, y - dt * vy, nullptr, nullptr);
     }
@@ -123,7 +138,8 @@ __device__ __forceinline__ float advected(const Q& q, int Mx, int My, float ox, 
                                           int j)
 {
     const float x = (float)i + ox, y = (float)j + oy;
-    const float vx = sample(fu, x, y), vy = sample(fv, x, y);
+    float vx, vy;
+    vel_at_sample(fu, fv, ox, oy, i, j, vx, vy);
     const View<Q> w = {q, Mx, My, ox, oy};
     if constexpr (!MC) {
         return sample_range(w, x - dt * vx, y - dt * vy, nullptr, nullptr);
@@ -163,7 +179,8 @@ __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const
 {
     if constexpr (!MC) {
         const float x = i + 0.5f, y = j + 0.5f;
-        const float vx = sample(fu, x, y), vy = sample(fv, x, y);
+        float vx, vy;
+        vel_at_sample(fu, fv, 0.5f, 0.5f, i, j, vx, vy);
         return sample_rho(r, x - dt * vx, y - dt * vy);
     } else {
         return advected<true>(r, r.nx, r.ny, 0.5f, 0.5f, fu, fv, dt, i, j);
