@@ -187,7 +187,7 @@ __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const
     }
 }
 
-// Tiles of the fused step: a CTA produces the outputs of kAdvTX x kAdvTY
+// Tiles of the fused step: a CTA produces the outputs of kAdvTX x adv_ty(MC)
 // indices (i, j) of [0, nx] x [0, ny] (cell (i, j) density, u face (j, i),
 // v face (j, i)).  MacCormack's backward sample reads the forward field at
 // four corners within kAdvH samples of its own index whenever the
@@ -197,9 +197,12 @@ __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const
 // tile's top v faces reads) and keeps it in shared memory.  A corner outside
 // that window (a faster flow) is evaluated where it is needed, with the same
 // arithmetic, so the result does not depend on the window.
-constexpr int kAdvTX = 32, kAdvTY = 16, kAdvH = 2, kAdvThreads = 256;
-constexpr int kFW = kAdvTX + 2 * kAdvH;      // columns of a forward-field window
-constexpr int kFH = kAdvTY + 2 * kAdvH + 1;  // rows: tile rows - 1 - kAdvH .. + kAdvH
+// (16 rows for MacCormack, whose windows then cost 1.48 forward values per
+// output; 32 rows for the first-order scheme, which has no windows).
+constexpr int kAdvTX = 32, kAdvH = 2, kAdvThreads = 256;
+__host__ __device__ constexpr int adv_ty(bool mc) { return mc ? 16 : 32; }
+constexpr int kFW = kAdvTX + 2 * kAdvH;          // columns of a forward-field window
+constexpr int kFH = adv_ty(true) + 2 * kAdvH + 1;  // rows: tile rows - 1 - kAdvH .. + kAdvH
 
 // Forward field of quantity Q on its window (sample (ci, cj) at entry 0),
 // evaluated where it is not in the window.
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(kAdvThreads) advect_kernel(
     __shared__ float s_win[MC ? 3 : 1][MC ? kFH * kFW : 1];
     __shared__ float s_vx[MC ? 3 : 1][MC ? kFH * kFW : 1];
     __shared__ float s_vy[MC ? 3 : 1][MC ? kFH * kFW : 1];
-    __shared__ float s_rho[(kAdvTY + 1) * kAdvTX];           // new rho, rows j0 - 1 ..
+    constexpr int kAdvTY = adv_ty(MC);
+    __shared__ float s_rho[(kAdvTY + 1) * kAdvTX];  // new rho, rows j0 - 1 ..
     const int i0 = blockIdx.x * kAdvTX, j0 = blockIdx.y * kAdvTY, b = blockIdx.z;
     const size_t cells = (size_t)ny * nx;
     const Field fu = {u + (size_t)b * ny * (nx + 1), nx + 1, ny, 0.0f, 0.5f};
@@ -405,8 +409,8 @@ hp_status launch_advect(const float* u, const float* v, const float* rho, const 
                         float* u_out, float* v_out, float* rho_out, hp_shape s,
                         const hp_plume_params& p, cudaStream_t st)
 {
-    dim3 blk(kAdvThreads),
-        grd((s.nx + 1 + kAdvTX - 1) / kAdvTX, (s.ny + 1 + kAdvTY - 1) / kAdvTY, s.batch);
+    const int ty = adv_ty(p.scheme == 1);
+    dim3 blk(kAdvThreads), grd((s.nx + 1 + kAdvTX - 1) / kAdvTX, (s.ny + ty) / ty, s.batch);
     if (p.scheme == 1)
         advect_kernel<true><<<grd, blk, 0, st>>>(u, v, rho, flags, u_out, v_out, rho_out, s.ny,
                                                  s.nx, p);
