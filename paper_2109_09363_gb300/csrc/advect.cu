@@ -189,7 +189,9 @@ __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const
 
 // Tiles of the fused step: a CTA produces the outputs of kAdvTX x adv_ty(MC)
 // indices (i, j) of [0, nx] x [0, ny] (cell (i, j) density, u face (j, i),
-// v face (j, i)).  MacCormack's backward sample reads the forward field at
+// v face (j, i)): 16 rows for MacCormack, whose windows (below) then cost
+// 1.48 forward values per output, 32 for the first-order scheme, which has
+// none.  MacCormack's backward sample reads the forward field at
 // four corners within kAdvH samples of its own index whenever the
 // displacement dt |vel| is below kAdvH cells; the CTA evaluates the forward
 // field of each quantity once on its tile widened by kAdvH (and one row more
@@ -197,8 +199,6 @@ __device__ __forceinline__ float rho_new_at(const Rho& r, const Field& fu, const
 // tile's top v faces reads) and keeps it in shared memory.  A corner outside
 // that window (a faster flow) is evaluated where it is needed, with the same
 // arithmetic, so the result does not depend on the window.
-// (16 rows for MacCormack, whose windows then cost 1.48 forward values per
-// output; 32 rows for the first-order scheme, which has no windows).
 constexpr int kAdvTX = 32, kAdvH = 2, kAdvThreads = 256;
 __host__ __device__ constexpr int adv_ty(bool mc) { return mc ? 16 : 32; }
 constexpr int kFW = kAdvTX + 2 * kAdvH;          // columns of a forward-field window
