@@ -12,11 +12,11 @@
 //      neighbouring CTAs' halo buffers (distributed shared memory); sweep k-1
 //      stored each of them as soon as it had computed it;
 //   2. one cluster barrier (release / acquire), split in arrive and wait;
-//   3. every kBatch-th sweep, between arrive and wait and on data visible
-//      since the previous barrier, warp 0 runs one round of the E
+//   3. every kBatch-th sweep, between arrive and wait and on data that a
+//      barrier already made visible, warp 0 runs one round of the E
 //      book-keeping for kBatch sweeps at once (8 lanes per sweep): the CTA
-//      partials (sums of the 16 warp sums of |r|) of sweeps k-5..k-2, stored
-//      into every CTA of the cluster, and E of sweeps k-9..k-6 from the
+//      partials (sums of the 16 warp sums of |r|) of sweeps k-6..k-3, stored
+//      into every CTA of the cluster, and E of sweeps k-10..k-7 from the
 //      cluster's partials (FP64, fixed shuffle trees, identical in every
 //      CTA), with the stop decisions in sweep order (E <= E_t, cap, or
 //      non-finite E); a round costs about one sweep's FP64 latency, paid
@@ -50,9 +50,12 @@ constexpr int kResThreads = kResWarps * 32;
 constexpr int kResTile = 128;  // tile side per CTA
 constexpr int kCkptEvery = 32;  // > kResLag: the two latest checkpoints cover k*
 // E book-keeping in rounds of kBatch sweeps (every kBatch-th sweep, 8 lanes
-// of warp 0 per sweep); the stop decision of sweep j is read at sweep j + kResLag
+// of warp 0 per sweep); the stop decision of sweep j is read at sweep j + kResLag.
+// The warp sums of sweep j are stored during sweep j + 1, after its arrive,
+// so a barrier orders them before a read only from sweep j + 3 on: a round
+// at sweep k takes the warp sums of sweeps k - kBatch - 2 .. k - 3.
 constexpr int kBatch = 4;
-constexpr int kResLag = 2 * kBatch + 2;
+constexpr int kResLag = 2 * kBatch + 3;
 constexpr int kWsumRing = 8;   // warp sums, by sweep
 constexpr int kEpartRing = 8;  // CTA partials, by sweep
 constexpr int kDecRing = 16;   // decisions, by sweep
@@ -415,13 +418,16 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
             if (g.lane == 0) s_wsum[((k - 1) % kWsumRing) * kResWarps + g.wid] = t;
         }
         if (P == 0 && g.wid == 0 && k % kBatch == 0) {
-            // one round, between arrive and wait, on data visible since the
-            // previous barrier; lane group gi (8 lanes) takes sweep
-            // jc = k - kBatch - 1 + gi for the CTA partial (its 16 warp sums)
+            // one round, between arrive and wait, on data that an earlier
+            // barrier made visible (the warp sums of sweep jc were stored in
+            // sweep jc + 1 and passed the barrier of sweep jc + 2 <= k - 1,
+            // the CTA partials of je in the round before and the barrier of
+            // sweep k - 3); lane group gi (8 lanes) takes sweep
+            // jc = k - kBatch - 2 + gi for the CTA partial (its 16 warp sums)
             // and sweep je = jc - kBatch for E (the cluster's CTA partials);
             // fixed FP64 trees, the same in every CTA
             const int gi = g.lane >> 3, li = g.lane & 7;
-            const int jc = k - kBatch - 1 + gi, je = jc - kBatch;
+            const int jc = k - kBatch - 2 + gi, je = jc - kBatch;
             double t0 = 0.0, t1 = 0.0;
             if (jc >= 0) {
                 const float* ws = s_wsum + (jc % kWsumRing) * kResWarps;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(kResThreads, 1) sweep_resident_kernel(ResArgs 
                 // the round's decisions in sweep order; the first stop counts
 #pragma unroll
                 for (int q = 0; q < kBatch; ++q) {
-                    const int j = k - 2 * kBatch - 1 + q;
+                    const int j = k - 2 * kBatch - 2 + q;
                     if (j < 0) continue;
                     const double e = ev[q] * inv_cells;
                     int dj = 0;
