@@ -975,7 +975,7 @@ def stencil_timing(hp, dev, batch, n):
         ms = a.elapsed_time(b) / 20
         gbs = bpc * cells / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "bytes_per_cell": bpc, "gbs": gbs, "frac": gbs / hbm}
-    out["note"] = "whole calls (the norms with their clearing and FP64 finishing kernels)"
+    out["note"] = "whole calls (the norms with their FP64 finishing kernel)"
     ctx.close()
     del u0, v0, div, mask, fl
     torch.cuda.empty_cache()

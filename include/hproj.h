@@ -483,9 +483,9 @@ hp_status hp_trainer_load(hp_trainer *trainer, const char *path);
  * context; it computes the same E_1 and E_inf as hp_div_norms, with the same
  * kernel.
  *
- * Its scratch (one FP64 partial sum per 256-cell block and one max word per
- * grid) is a fixed array inside libhproj.so: every GPU that loads the library
- * holds it (about 2.1 MB) until the process exits.  Limits: batch <=
+ * Its scratch (one 8-byte partial, the FP32 sum and max of |div|, per
+ * 256-cell block) is a fixed array inside libhproj.so: every GPU that loads
+ * the library holds it (2 MB) until the process exits.  Limits: batch <=
  * HP_NOALLOC_MAX_BATCH and batch * ny * ceil(nx / 256) <= HP_NOALLOC_MAX_BLOCKS
  * (16 grids of 2048 x 2048 fit), and batch, ny within HP_MAX_BATCH,
  * HP_MAX_NY like every call; larger shapes return HP_ERR_INVALID_ARG and
@@ -498,9 +498,8 @@ hp_status hp_trainer_load(hp_trainer *trainer, const char *path);
  * before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other host threads) race and give wrong
  * results.  Each call
- * clears the max words it uses before the reduction and overwrites the
- * partial sums it reads; no cudaMalloc, cudaFree or allocating library
- * routine is called.  u, v, flags, e1_out, einf_out as in hp_div_norms. */
+ * overwrites every partial it reads before reading it; no cudaMalloc,
+ * cudaFree or allocating library routine is called.  u, v, flags, e1_out, einf_out as in hp_div_norms. */
 #define HP_NOALLOC_MAX_BATCH 16384
 #define HP_NOALLOC_MAX_BLOCKS 262144
 hp_status hp_div_norms_noalloc(const float *u, const float *v, const uint8_t *flags,

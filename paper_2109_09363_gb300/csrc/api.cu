@@ -234,8 +234,8 @@ hp_status hp_div_norms(hp_ctx* c, const float* u, const float* v, const uint8_t*
                        double* e1_out, double* einf_out, hp_shape s, void* stream)
 {
     if (!c || !u || !v || !flags || !fits(c, s)) return HP_ERR_INVALID_ARG;
-    return launch_div_norms(u, v, flags, c->partial2, (int)(c->partial2_len / s.batch),
-                            c->gs, e1_out, einf_out, s, (cudaStream_t)stream);
+    return launch_div_norms(u, v, flags, c->partial2, (int)(c->partial2_len / s.batch), e1_out,
+                            einf_out, s, (cudaStream_t)stream);
 }
 
 hp_status hp_project(hp_ctx* c, float* u, float* v, const uint8_t* flags, hp_shape s,

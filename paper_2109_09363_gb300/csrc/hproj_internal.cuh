@@ -46,7 +46,7 @@ struct GridState {
     int32_t pad_;
     double e_stop;       // E(phi_{k*})
     uint32_t arrivals;   // CTA arrival counter of the current launch
-    uint32_t einf_bits;  // max |div| of the corrected velocity (float bits)
+    uint32_t pad2_;
 };
 
 // Loop state shared by all grids.
@@ -228,12 +228,14 @@ hp_status launch_mask(const uint8_t* flags, uint8_t* mask, hp_shape s, cudaStrea
 // out = (phi + J(phi)) / 2, J one masked Jacobi sweep on the right-hand side div
 hp_status launch_mean_sweep(const float* phi, const float* div, const uint8_t* mask, float* out,
                             hp_shape s, cudaStream_t st);
+// E_1, E_inf of a velocity (closed box); partial: >= nblk_cap 8-byte slots
+// per grid, one per 256-cell segment of a row
 hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags,
-                           double* partial, int nblk_cap, GridState* gs, double* e1,
-                           double* einf, hp_shape s, cudaStream_t st);
+                           double* partial, int nblk_cap, double* e1, double* einf, hp_shape s,
+                           cudaStream_t st);
 hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t* flags,
-                                   double* partial, uint32_t* einf_bits, size_t stride,
-                                   double* e1, double* einf, hp_shape s, cudaStream_t st);
+                                   double* partial, double* e1, double* einf, hp_shape s,
+                                   cudaStream_t st);
 // have_div: ctx->mask and ctx->div already hold this velocity's open faces
 // and divergence (no second pass over u, v)
 hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp_shape s,

@@ -10,21 +10,20 @@
 
 namespace {
 
-// Scratch of hp_div_norms_noalloc.  Every device that loads the library holds
-// these arrays until the process exits.
+// Scratch of hp_div_norms_noalloc: one 8-byte partial (the FP32 sum and max
+// of |div|) per 256-cell segment.  Every device that loads the library holds
+// this array until the process exits.
 static __device__ __align__(256) double g_noalloc_partial[HP_NOALLOC_MAX_BLOCKS];
-static __device__ __align__(256) uint32_t g_noalloc_einf[HP_NOALLOC_MAX_BATCH];
 
 // The device address of a __device__ array belongs to the CUDA context that
 // loaded this library's module, not to the device: after cudaDeviceReset, or
 // with another (non-primary) context current, the array sits elsewhere.  The
-// addresses are therefore cached per context, keyed by the driver's context
-// id (unique for the life of the process, never reused).  In host code the
-// array names are host-side stand-ins, never device addresses.
+// address is therefore cached per context, keyed by the driver's context id
+// (unique for the life of the process, never reused).  In host code the array
+// name is a host-side stand-in, never a device address.
 struct ScratchAddr {
     unsigned long long ctx_id;
     double* partial;
-    uint32_t* einf;
 };
 constexpr int kCacheSlots = 16;
 std::mutex g_setup_mu;
@@ -68,7 +67,7 @@ hp_status current_ctx_id(unsigned long long* id)
     return HP_OK;
 }
 
-hp_status scratch_for_current_context(double** partial, uint32_t** einf)
+hp_status scratch_for_current_context(double** partial)
 {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     hp_status rc = resolve_driver_calls();
@@ -78,24 +77,19 @@ hp_status scratch_for_current_context(double** partial, uint32_t** einf)
     for (int k = 0; id && k < kCacheSlots; ++k) {
         if (g_cache[k].ctx_id == id) {
             *partial = g_cache[k].partial;
-            *einf = g_cache[k].einf;
             return HP_OK;
         }
     }
-    // Set-up for this context: look the arrays up with it current (the
+    // Set-up for this context: look the array up with it current (the
     // runtime makes the device's primary context current first if no context
     // is; the id is then read again).
     void* p = nullptr;
-    void* q = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
     if (e != cudaSuccess) { hp::set_cuda_error(e); return HP_ERR_CUDA; }
-    e = cudaGetSymbolAddress(&q, g_noalloc_einf);
-    if (e != cudaSuccess) { hp::set_cuda_error(e); return HP_ERR_CUDA; }
     if (!id && ((rc = current_ctx_id(&id)) != HP_OK || !id)) return HP_ERR_CUDA;
-    g_cache[g_cache_next] = {id, (double*)p, (uint32_t*)q};
+    g_cache[g_cache_next] = {id, (double*)p};
     g_cache_next = (g_cache_next + 1) % kCacheSlots;
     *partial = (double*)p;
-    *einf = (uint32_t*)q;
     return HP_OK;
 }
 
@@ -111,9 +105,8 @@ extern "C" hp_status hp_div_norms_noalloc(const float* u, const float* v, const 
         return HP_ERR_INVALID_ARG;
     }
     double* partial = nullptr;
-    uint32_t* einf = nullptr;
-    hp_status rc = scratch_for_current_context(&partial, &einf);
+    hp_status rc = scratch_for_current_context(&partial);
     if (rc != HP_OK) return rc;
-    return hp::launch_div_norms_scratch(u, v, flags, partial, einf, 1, e1_out, einf_out, s,
+    return hp::launch_div_norms_scratch(u, v, flags, partial, e1_out, einf_out, s,
                                         (cudaStream_t)stream);
 }

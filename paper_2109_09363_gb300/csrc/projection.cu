@@ -193,6 +193,56 @@ __global__ void __launch_bounds__(kQuadThreads)
     }
 }
 
+// The face mask alone, sixteen cells per thread (rows a multiple of 16
+// cells, 16-byte aligned flags and mask): each of the three flag rows as one
+// 16-byte load, the mask as one 16-byte store, the bytes left and right of
+// the sixteen from the neighbouring lanes; the same bits as mask_div4_kernel
+// (four cells per word, byte-wise comparisons).
+constexpr int kMask16Threads = 128;
+
+__global__ void __launch_bounds__(kMask16Threads)
+    mask16_kernel(const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask, int ny, int nx,
+                  int open_top)
+{
+    constexpr uint32_t kSolid = 0x01010101u;
+    const int i0 = 16 * (blockIdx.x * kMask16Threads + threadIdx.x);
+    const int j = blockIdx.y, b = blockIdx.z, lane = threadIdx.x & 31;
+    const bool act = i0 < nx;
+    const bool from_left = lane > 0 && i0 > 0;
+    const bool from_right = lane < 31 && i0 + 16 < nx;
+    const uint8_t* fl = flags + (size_t)b * ny * nx;
+    const size_t row = (size_t)j * nx;
+    const uint4 solid = make_uint4(kSolid, kSolid, kSolid, kSolid);
+    const uint4 open4 = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 c4 = act ? *reinterpret_cast<const uint4*>(fl + row + i0) : solid;
+    const uint4 u4 = !act ? solid
+                     : j > 0 ? *reinterpret_cast<const uint4*>(fl + row - nx + i0)
+                     : open_top ? open4 : solid;
+    const uint4 d4 = (act && j < ny - 1) ? *reinterpret_cast<const uint4*>(fl + row + nx + i0)
+                                         : solid;
+    const uint32_t fc[4] = {c4.x, c4.y, c4.z, c4.w};
+    const uint32_t fu[4] = {u4.x, u4.y, u4.z, u4.w};
+    const uint32_t fd[4] = {d4.x, d4.y, d4.z, d4.w};
+    uint32_t left = byte_of(__shfl_up_sync(0xffffffffu, fc[3], 1), 3);
+    uint32_t right = byte_of(__shfl_down_sync(0xffffffffu, fc[0], 1), 0);
+    if (!from_left) left = (act && i0 > 0) ? fl[row + i0 - 1] : 1u;
+    if (!from_right) right = (act && i0 + 16 < nx) ? fl[row + i0 + 16] : 1u;
+    if (!act) return;
+    uint32_t mw[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const uint32_t west = (fc[h] << 8) | (h == 0 ? left : fc[h - 1] >> 24);
+        const uint32_t east = (fc[h] >> 8) | ((h == 3 ? right : fc[h + 1] & 0xffu) << 24);
+        const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
+                              (__vcmpeq4(east, 0u) & 0x02020202u) |
+                              (__vcmpeq4(fu[h], 0u) & 0x04040404u) |
+                              (__vcmpeq4(fd[h], 0u) & 0x08080808u);
+        mw[h] = __vcmpeq4(fc[h], 0u) & open;
+    }
+    *reinterpret_cast<uint4*>(mask + (size_t)b * ny * nx + row + i0) =
+        make_uint4(mw[0], mw[1], mw[2], mw[3]);
+}
+
 static bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // Blocks of a streaming kernel: a few per SM of the current device, no more
@@ -217,6 +267,11 @@ static bool vec_shape(hp_shape s, int multiple)
 hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
                           float* div, hp_shape s, cudaStream_t st, Boundary bc)
 {
+    if (!div && mask && s.nx % 16 == 0 && aligned16(flags) && aligned16(mask)) {
+        dim3 grd((s.nx / 16 + kMask16Threads - 1) / kMask16Threads, s.ny, s.batch);
+        mask16_kernel<<<grd, kMask16Threads, 0, st>>>(flags, mask, s.ny, s.nx, bc.open_top);
+        return check_launch();
+    }
     if (s.nx % 4 == 0 && aligned16(flags) && aligned16(mask) && aligned16(div) &&
         (!div || aligned16(v))) {
         dim3 grd((s.nx / 4 + kQuadThreads - 1) / kQuadThreads, s.ny, s.batch);
@@ -824,18 +879,22 @@ __global__ void __launch_bounds__(kStreamThreads)
 }
 
 // --------------------------------------------------------- divergence norms
+//
+// E_1 = mean |div u| and E_inf = max |div u| (Sec. 4.1) of a velocity: one
+// 8-byte partial per 256-cell segment of a row, in (grid, row, segment)
+// order, holding the segment's FP32 sum and max of |div| (float2), then per
+// grid the FP64 sum of the sums in a fixed order and the max of the maxima.
+// No atomics: every partial has one writer, and E_1 is the same on every call.
 
-// One thread per cell: |div u| over open faces, FP32 per thread and warp, FP64
-// per block into partial[b][block]; max via an atomic on the float bits.
-// (flags is always given; mask may be null, the closed box's open faces are
-// then taken from the flags)
+// One thread per cell, a block per segment: |div u| over open faces, FP32
+// sums per warp and of the warps in order.  (flags is always given; mask may
+// be null, the closed box's open faces are then taken from the flags)
 __global__ void div_norms_kernel(const float* __restrict__ u, const float* __restrict__ v,
                                  const uint8_t* __restrict__ flags,
-                                 const uint8_t* __restrict__ mask, double* __restrict__ partial,
-                                 uint32_t* __restrict__ einf_bits, size_t einf_stride, int ny,
-                                 int nx, Boundary bc)
+                                 const uint8_t* __restrict__ mask, float2* __restrict__ partial,
+                                 int ny, int nx, Boundary bc)
 {
-    __shared__ float s_w[8];
+    __shared__ float s_w[8], s_m[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const int b = blockIdx.z;
@@ -874,142 +933,158 @@ __global__ void div_norms_kernel(const float* __restrict__ u, const float* __res
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         s_w[wid] = a;
-        atomicMax(einf_bits + (size_t)b * einf_stride, __float_as_uint(mx));
+        s_m[wid] = mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)s_w[w];
-        partial[(size_t)b * gridDim.x * gridDim.y + (size_t)j * gridDim.x + blockIdx.x] = s;
+        float sum = 0.0f, m = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sum = __fadd_rn(sum, s_w[w]);
+            m = fmaxf(m, s_m[w]);
+        }
+        partial[(size_t)b * gridDim.x * gridDim.y + (size_t)j * gridDim.x + blockIdx.x] =
+            make_float2(sum, m);
     }
 }
 
-// div_norms_kernel with one warp per 256-cell segment of a row (the blocks
-// of div_norms_kernel: the same partial layout, partial[segment] in (grid,
-// row, segment) order), eight consecutive cells per lane with vector loads
-// (measured faster than a lane-strided layout whose every load is one
-// contiguous run: 177 against 303 us at 16 x 2048^2); each warp strides over
-// the segments, keeps its lanes' maxima and raises the grid's max once per
-// grid it visits.
+// The same partials over quads (rows a multiple of 4 cells, 16-byte aligned
+// v, flags and mask), laid out like mask_div4_kernel: grid (segment pairs,
+// ny, B), a block of 4 warps takes two consecutive segments of a row, warp
+// 2 s + h the quads at 128 h + 4 lane of its segment s, one quad per thread;
+// a segment's partial is the FP32 sum of its two warps' sums.
 constexpr int kSegCells = 256;
+constexpr int kNormThreads = 128;
 
-__global__ void __launch_bounds__(kStreamThreads)
-    div_norms8_kernel(const float* __restrict__ u, const float* __restrict__ v,
+__global__ void __launch_bounds__(kNormThreads)
+    div_norms4_kernel(const float* __restrict__ u, const float* __restrict__ v,
                       const uint8_t* __restrict__ flags, const uint8_t* __restrict__ mask,
-                      double* __restrict__ partial, uint32_t* __restrict__ einf_bits,
-                      size_t einf_stride, int ny, int nx, uint32_t segs, Boundary bc)
+                      float2* __restrict__ partial, int ny, int nx, int nseg, Boundary bc)
 {
-    const uint32_t nseg = ((uint32_t)nx + kSegCells - 1) / kSegCells;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (kStreamThreads / 32);
-    float run_max = 0.0f;
-    int cur = -1;
-    for (uint32_t sg = blockIdx.x * (kStreamThreads / 32) + (threadIdx.x >> 5); sg < segs;
-         sg += warps) {
-        const uint32_t row = sg / nseg;
-        const int sx = (int)(sg - row * nseg);
-        const int b = (int)(row / (uint32_t)ny), j = (int)row - b * ny;
-        if (b != cur) {
-            // the lanes' maxima of the previous grid, reduced once
-            if (cur >= 0) {
-                for (int off = 16; off > 0; off >>= 1)
-                    run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, off));
-                if (lane == 0)
-                    atomicMax(einf_bits + (size_t)cur * einf_stride, __float_as_uint(run_max));
-            }
-            run_max = 0.0f;
-            cur = b;
-        }
-        const int i0 = sx * kSegCells + 8 * lane;
-        const bool act = i0 < nx;
-        const bool from_left = lane > 0;
-        const bool from_right = lane < 31 && i0 + 8 < nx;
-        const size_t gb = (size_t)b * ny * nx;
-        uint32_t m[8], fc[2] = {0x01010101u, 0x01010101u};
-        if (mask) {
+    __shared__ float s_w[4], s_m[4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int j = blockIdx.y, b = blockIdx.z;
+    const int sx = 2 * blockIdx.x + (wid >> 1);
+    const int i0 = sx * kSegCells + 128 * (wid & 1) + 4 * lane;
+    const bool act = i0 < nx;
+    // the neighbouring quads of the half segment sit in the neighbouring lanes
+    const bool from_left = lane > 0;
+    const bool from_right = lane < 31 && i0 + 4 < nx;
+    const size_t gb = (size_t)b * ny * nx;
+    uint32_t m[4], fc[1] = {0x01010101u};
+    if (mask) {
+        const uint32_t m4 = act ? ld_u32(mask + gb + (size_t)j * nx + i0) : 0u;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint32_t m4 = act ? ld_u32(mask + gb + (size_t)j * nx + i0 + 4 * h) : 0u;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) m[4 * h + q] = byte_of(m4, q);
-                if (act && j == ny - 1) fc[h] = ld_u32(flags + gb + (size_t)j * nx + i0 + 4 * h);
-            }
-        } else {
-            // the closed box's open faces from the flags
-            open_bits<2>(flags + gb, j, i0, act, ny, nx, 0, from_left, from_right, m, fc);
-        }
-        float uf[9], vn[8], vs[8];
-        faces<2>(u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1), v + (size_t)b * (ny + 1) * nx,
-                 j, i0, act, nx, from_right, uf, vn, vs);
-        float a = 0.0f, mx = 0.0f;
-        if (act) {
-            float d[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int i = i0 + q;
-                const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && byte_of(fc[q / 4], q % 4) == 0;
-                d[q] = fabsf(face_div(m[q], inflow, uf[q], uf[q + 1], vn[q], vs[q]));
-                mx = fmaxf(mx, d[q]);
-            }
-            a = __fadd_rn(__fadd_rn(__fadd_rn(d[0], d[1]), __fadd_rn(d[2], d[3])),
-                          __fadd_rn(__fadd_rn(d[4], d[5]), __fadd_rn(d[6], d[7])));
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, off));
-        run_max = fmaxf(run_max, mx);
-        if (lane == 0) partial[sg] = (double)a;
-    }
-    if (cur >= 0) {
-        for (int off = 16; off > 0; off >>= 1)
-            run_max = fmaxf(run_max, __shfl_xor_sync(0xffffffffu, run_max, off));
-        if (lane == 0) atomicMax(einf_bits + (size_t)cur * einf_stride, __float_as_uint(run_max));
-    }
-}
-
-// The norms kernel for one shape: the warp-per-segment kernel where rows allow
-// vector access, else one cell per thread; the same partials either way.
-static void norms_kernel(const float* u, const float* v, const uint8_t* flags,
-                         const uint8_t* mask, double* partial, uint32_t* einf_bits, size_t stride,
-                         hp_shape s, Boundary bc, cudaStream_t st)
-{
-    if (vec_shape(s, 8) && aligned16(v) && aligned16(flags) && aligned16(mask)) {
-        const uint32_t segs =
-            (uint32_t)((uint64_t)s.batch * s.ny * ((s.nx + kSegCells - 1) / kSegCells));
-        div_norms8_kernel<<<stream_blocks(segs, kStreamThreads / 32), kStreamThreads, 0, st>>>(
-            u, v, flags, mask, partial, einf_bits, stride, s.ny, s.nx, segs, bc);
+        for (int q = 0; q < 4; ++q) m[q] = byte_of(m4, q);
+        if (act && j == ny - 1) fc[0] = ld_u32(flags + gb + (size_t)j * nx + i0);
     } else {
-        dim3 grd((s.nx + 255) / 256, s.ny, s.batch);
-        div_norms_kernel<<<grd, 256, 0, st>>>(u, v, flags, mask, partial, einf_bits, stride, s.ny,
-                                              s.nx, bc);
+        // the closed box's open faces from the flags
+        open_bits<1>(flags + gb, j, i0, act, ny, nx, 0, from_left, from_right, m, fc);
+    }
+    float uf[5], vn[4], vs[4];
+    faces<1>(u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1), v + (size_t)b * (ny + 1) * nx, j,
+             i0, act, nx, from_right, uf, vn, vs);
+    float a = 0.0f, mx = 0.0f;
+    if (act) {
+        float d[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q;
+            const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && byte_of(fc[0], q) == 0;
+            d[q] = fabsf(face_div(m[q], inflow, uf[q], uf[q + 1], vn[q], vs[q]));
+            mx = fmaxf(mx, d[q]);
+        }
+        a = __fadd_rn(__fadd_rn(d[0], d[1]), __fadd_rn(d[2], d[3]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, off));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) {
+        s_w[wid] = a;
+        s_m[wid] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int sq = 2 * blockIdx.x + threadIdx.x;
+        if (sq < nseg)
+            partial[((size_t)b * ny + j) * nseg + sq] =
+                make_float2(__fadd_rn(s_w[2 * threadIdx.x], s_w[2 * threadIdx.x + 1]),
+                            fmaxf(s_m[2 * threadIdx.x], s_m[2 * threadIdx.x + 1]));
     }
 }
 
-// One warp per grid: E_1 = sum of block partials (fixed order) / cells.
+// The norms kernel for one shape: the quad kernel where rows allow vector
+// access, else one cell per thread; the same partial layout either way.
+static void norms_kernel(const float* u, const float* v, const uint8_t* flags,
+                         const uint8_t* mask, float2* partial, hp_shape s, Boundary bc,
+                         cudaStream_t st)
+{
+    const int nseg = (s.nx + kSegCells - 1) / kSegCells;
+    if (s.nx % 4 == 0 && aligned16(v) && aligned16(flags) && aligned16(mask)) {
+        dim3 grd((nseg + 1) / 2, s.ny, s.batch);
+        div_norms4_kernel<<<grd, kNormThreads, 0, st>>>(u, v, flags, mask, partial, s.ny, s.nx,
+                                                        nseg, bc);
+    } else {
+        dim3 grd(nseg, s.ny, s.batch);
+        div_norms_kernel<<<grd, kSegCells, 0, st>>>(u, v, flags, mask, partial, s.ny, s.nx, bc);
+    }
+}
+
 // One block of kFinishWarps warps per grid: warp w adds its contiguous share
-// of the grid's partials (lane order), then thread 0 the warps' sums in
-// order; a fixed order, so E_1 is the same on every call.
+// of the grid's partial sums (lane order, FP64) and takes their max, then
+// thread 0 the warps' results in order; a fixed order, so E_1 is the same on
+// every call.
 constexpr int kFinishWarps = 8;
 
-__global__ void norms_finish_kernel(const double* __restrict__ partial, int nblk,
-                                    const uint32_t* __restrict__ einf_bits, size_t einf_stride,
-                                    double* e1, double* einf, const GridState* gs, int32_t* iters,
+__global__ void norms_finish_kernel(const float2* __restrict__ partial, int nblk, double* e1,
+                                    double* einf, const GridState* gs, int32_t* iters,
                                     uint8_t* conv, int B, double inv_cells)
 {
     __shared__ double s_w[kFinishWarps];
+    __shared__ float s_m[kFinishWarps];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int share = (nblk + kFinishWarps - 1) / kFinishWarps;
     const int q0 = wid * share, q1 = min(nblk, q0 + share);
-    double s = q1 > q0 ? lane_sum(partial + (size_t)b * nblk + q0, q1 - q0, lane) : 0.0;
+    const float2* p = partial + (size_t)b * nblk;
+    double s = 0.0;
+    float m = 0.0f;
+    int i = q0 + lane;
+    for (; i + 7 * 32 < q1; i += 8 * 32) {
+        float2 t[8];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) s_w[wid] = s;
+        for (int k = 0; k < 8; ++k) t[k] = __ldcg(p + i + 32 * k);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            s += (double)t[k].x;
+            m = fmaxf(m, t[k].y);
+        }
+    }
+    for (; i < q1; i += 32) {
+        const float2 t = __ldcg(p + i);
+        s += (double)t.x;
+        m = fmaxf(m, t.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, off);
+        m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, off));
+    }
+    if (lane == 0) {
+        s_w[wid] = s;
+        s_m[wid] = m;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         s = 0.0;
-        for (int w = 0; w < kFinishWarps; ++w) s += s_w[w];
+        m = 0.0f;
+        for (int w = 0; w < kFinishWarps; ++w) {
+            s += s_w[w];
+            m = fmaxf(m, s_m[w]);
+        }
         if (e1) e1[b] = s * inv_cells;
-        if (einf) einf[b] = (double)__uint_as_float(einf_bits[(size_t)b * einf_stride]);
+        if (einf) einf[b] = (double)m;
         if (gs) {
             if (iters) iters[b] = gs[b].kstar;
             if (conv) conv[b] = (uint8_t)gs[b].converged;
@@ -1017,49 +1092,27 @@ __global__ void norms_finish_kernel(const double* __restrict__ partial, int nblk
     }
 }
 
-__global__ void clear_einf_kernel(uint32_t* bits, size_t stride, int B)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < B) bits[(size_t)b * stride] = 0u;
-}
-
 hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags, double* partial,
-                           int nblk_cap, GridState* gs, double* e1, double* einf, hp_shape s,
-                           cudaStream_t st)
+                           int nblk_cap, double* e1, double* einf, hp_shape s, cudaStream_t st)
 {
-    const dim3 grd((s.nx + 255) / 256, s.ny, s.batch);
-    const int nblk = grd.x * grd.y;
+    const int nblk = ((s.nx + kSegCells - 1) / kSegCells) * s.ny;
     if (nblk > nblk_cap) return HP_ERR_INVALID_ARG;
-    // the per-grid max word lives in the grid state array of the context
-    uint32_t* einf_bits = &gs[0].einf_bits;
-    const size_t stride = sizeof(GridState) / sizeof(uint32_t);
-    clear_einf_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(einf_bits, stride, s.batch);
-    hp_status rc = check_launch();
-    if (rc != HP_OK) return rc;
-    norms_kernel(u, v, flags, nullptr, partial, einf_bits, stride, s, Boundary{}, st);
-    if ((rc = check_launch()) != HP_OK) return rc;
-    norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
-        partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
-        1.0 / ((double)s.nx * (double)s.ny));
-    return check_launch();
+    return launch_div_norms_scratch(u, v, flags, partial, e1, einf, s, st);
 }
 
 // Same reduction as launch_div_norms with caller-given scratch: partial
-// (>= batch * blocks doubles) and one max word per grid at einf_bits[b * stride].
+// holds >= batch * ny * ceil(nx / 256) slots of 8 bytes.
 hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t* flags,
-                                   double* partial, uint32_t* einf_bits, size_t stride,
-                                   double* e1, double* einf, hp_shape s, cudaStream_t st)
+                                   double* partial, double* e1, double* einf, hp_shape s,
+                                   cudaStream_t st)
 {
-    const dim3 grd((s.nx + 255) / 256, s.ny, s.batch);
-    const int nblk = grd.x * grd.y;
-    clear_einf_kernel<<<(s.batch + 255) / 256, 256, 0, st>>>(einf_bits, stride, s.batch);
+    const int nblk = ((s.nx + kSegCells - 1) / kSegCells) * s.ny;
+    float2* p2 = reinterpret_cast<float2*>(partial);
+    norms_kernel(u, v, flags, nullptr, p2, s, Boundary{}, st);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
-    norms_kernel(u, v, flags, nullptr, partial, einf_bits, stride, s, Boundary{}, st);
-    if ((rc = check_launch()) != HP_OK) return rc;
     norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
-        partial, nblk, einf_bits, stride, e1, einf, nullptr, nullptr, nullptr, s.batch,
-        1.0 / ((double)s.nx * (double)s.ny));
+        p2, nblk, e1, einf, nullptr, nullptr, nullptr, s.batch, 1.0 / ((double)s.nx * (double)s.ny));
     return check_launch();
 }
 
@@ -1313,19 +1366,17 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     }
     if ((rc = check_launch()) != HP_OK) return rc;
 
-    // norms of the corrected velocity; the einf word lives in GridState
-    const int nblk = grd.x * grd.y;
+    // norms of the corrected velocity
+    const int nblk = ((s.nx + kSegCells - 1) / kSegCells) * s.ny;
     if ((size_t)s.batch * nblk > ctx->partial2_len) return HP_ERR_INVALID_ARG;
-    uint32_t* einf_bits = &ctx->gs[0].einf_bits;
-    const size_t stride = sizeof(GridState) / sizeof(uint32_t);
+    float2* p2 = reinterpret_cast<float2*>(ctx->partial2);
     if (u) {
-        norms_kernel(u, v, flags, ctx->mask, ctx->partial2, einf_bits, stride, s, bc, st);
+        norms_kernel(u, v, flags, ctx->mask, p2, s, bc, st);
         if ((rc = check_launch()) != HP_OK) return rc;
     }
     norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
-        ctx->partial2, nblk, einf_bits, stride, u ? e1_out : nullptr, u ? einf_out : nullptr,
-        ctx->gs, iters_out, fixed ? nullptr : conv_out, s.batch,
-        1.0 / ((double)s.nx * (double)s.ny));
+        p2, nblk, u ? e1_out : nullptr, u ? einf_out : nullptr, ctx->gs, iters_out,
+        fixed ? nullptr : conv_out, s.batch, 1.0 / ((double)s.nx * (double)s.ny));
     if ((rc = check_launch()) != HP_OK) return rc;
     if (fixed && conv_out) {
         cudaError_t e = cudaMemsetAsync(conv_out, 1, (size_t)s.batch, st);

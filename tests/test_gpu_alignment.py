@@ -73,6 +73,31 @@ def test_stencil_calls_match_their_scalar_fallbacks(dev, B, ny, nx):
     ctx.check()
 
 
+@pytest.mark.parametrize("off", [1, 2, 3])
+@pytest.mark.parametrize("B,ny,nx", [(2, 37, 264), (3, 5, 516)])
+def test_misaligned_u_alone_stays_on_the_vector_path(dev, B, ny, nx, off):
+    # u may start at any float (its rows of nx + 1 values start at every
+    # offset anyway): with v and the flags aligned the vector kernels run and
+    # give the results of aligned u bit for bit
+    u, v, fl = (t.to(dev) for t in case(B, ny, nx, 17))
+    us = shifted(u, off)
+    assert torch.equal(hp.hp_divergence(u, v, fl), hp.hp_divergence(us, v, fl))
+    ctx = hp.Context(B, ny, nx)
+    e1a, eia = hp.hp_div_norms(ctx, u, v, fl)
+    e1b, eib = hp.hp_div_norms(ctx, us, v, fl)
+    assert torch.equal(e1a, e1b) and torch.equal(eia, eib)
+    prm = hp.ProjectParams(threshold=1e-3, max_iters=300)
+    ua, va = u.clone(), v.clone()
+    vb = v.clone()
+    oa = hp.hp_project(ctx, ua, va, fl, prm)
+    ob = hp.hp_project(ctx, us, vb, fl, prm)
+    torch.cuda.synchronize()
+    assert torch.equal(oa["iters"], ob["iters"])
+    assert torch.equal(ua, us) and torch.equal(va, vb)
+    assert torch.equal(oa["e1"], ob["e1"])
+    ctx.check()
+
+
 def test_network_input_matches_its_scalar_fallback(dev):
     from paper_2109_09363_gb300 import training as T
     B, n = 2, 64

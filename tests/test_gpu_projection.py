@@ -124,8 +124,12 @@ def check_projection(g, u, v, fl, thr, cap, phi0=None, hist_len=0):
 # ------------------------------------------------------------------ tests
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (2, 5, 7), (1, 64, 128), (3, 67, 130),
-                                   (2, 129, 257), (1, 3, 4), (2, 37, 264), (1, 5, 1028)])
+                                   (2, 129, 257), (1, 3, 4), (2, 37, 264), (1, 5, 1028),
+                                   (1, 3, 16), (2, 37, 272), (3, 9, 2064)])
 def test_face_mask_bit_exact(dev, shape):
+    """Rows of any length (one cell per thread), a multiple of 4 cells (one
+    quad per thread) and of 16 cells (the mask-only kernel, sixteen per
+    thread; 2064 = 129 x 16 spans two blocks per row)."""
     rng = np.random.default_rng(sum(shape))
     fl = (rng.random(shape) < 0.3).astype(np.uint8)
     got = hp.hp_face_mask(to_dev(fl, dev)).cpu().numpy()
@@ -268,10 +272,12 @@ def test_context_reuse_and_shape_checks(dev):
         run_gpu(dev, *vortex(1, 80, 64), hp.ProjectParams(1e-3, 10), ctx=ctx)
 
 
-@pytest.mark.parametrize("shape", [(3, 70, 90), (2, 37, 264), (1, 9, 1032), (2, 3, 8)])
+@pytest.mark.parametrize("shape", [(3, 70, 90), (2, 37, 264), (1, 9, 1032), (2, 3, 8),
+                                   (2, 5, 516), (6, 2, 12), (5, 3, 4)])
 def test_div_norms(dev, shape):
-    """Rows of any length (one cell per thread), and rows a multiple of 8
-    cells (one warp per 256-cell segment, the last one ragged)."""
+    """Rows of any length (one cell per thread), and rows a multiple of 4
+    cells (two warps per 256-cell segment, the last one ragged or empty;
+    an odd number of segments per row; tiny grids)."""
     u, v, fl = vortex(*shape, seed=3)
     ctx = hp.Context(*shape)
     e1, einf = hp.hp_div_norms(ctx, to_dev(u, dev), to_dev(v, dev), to_dev(fl, dev))

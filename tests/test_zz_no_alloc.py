@@ -92,7 +92,7 @@ def test_noalloc_at_its_largest_shape(dev):
 
 @pytest.mark.parametrize("B,ny,nx", [(16385, 1, 1), (1, 262145, 1), (1, 70000, 1)])
 def test_noalloc_rejects_shapes_beyond_its_scratch(dev, B, ny, nx):
-    # more grids than max words, more 256-cell blocks than partial sums, or
+    # more grids than its batch limit, more 256-cell blocks than partials, or
     # more rows than one CUDA grid dimension covers
     u = torch.zeros((B, ny, nx + 1), dtype=torch.float32, device=dev)
     v = torch.zeros((B, ny + 1, nx), dtype=torch.float32, device=dev)
