@@ -67,9 +67,10 @@ __global__ void mask_div_kernel(const float* __restrict__ u, const float* __rest
 // of the cells left and right of the four come from the adjacent lanes when
 // they hold them), v and div, p, phi as float4 (16-byte aligned rows), u
 // (rows of nx + 1) as scalars with the fifth face from the next lane.  The
-// kernels stride over the cells with a grid of a few blocks per SM, so that
-// each thread streams many cells; every lane of a warp takes part in the
-// shuffles, lanes past the end do no memory access.
+// mask/divergence and norm kernels walk column strips (a quad column of a
+// few rows per thread), the correction strides over the quads with a grid of
+// a few blocks per SM; every lane of a warp takes part in the shuffles, lanes
+// past the end do no memory access.
 
 constexpr int kStreamThreads = 256;
 constexpr int kStreamBlocksPerSm = 8;
@@ -81,69 +82,6 @@ __device__ __forceinline__ uint32_t ld_u32(const uint8_t* p)
 
 __device__ __forceinline__ uint32_t byte_of(uint32_t w, int q) { return (w >> (8 * q)) & 0xffu; }
 
-// Open-face bits (as mask_div_kernel) of the n4 x 4 cells i0.. of row j of one
-// grid's flags fl; fc receives their flag words.  Lane l - 1 holds the cells
-// left of i0 when from_left, lane l + 1 those right of the last when
-// from_right (then they are in the same row).
-template <int N4>
-__device__ __forceinline__ void open_bits(const uint8_t* __restrict__ fl, int j, int i0, bool act,
-                                          int ny, int nx, int open_top, bool from_left,
-                                          bool from_right, uint32_t (&m)[4 * N4],
-                                          uint32_t (&fc)[N4])
-{
-    constexpr uint32_t kSolid = 0x01010101u;
-    const size_t row = (size_t)j * nx;
-    uint32_t fu[N4], fd[N4];
-#pragma unroll
-    for (int h = 0; h < N4; ++h) {
-        const int x = i0 + 4 * h;
-        fc[h] = act ? ld_u32(fl + row + x) : kSolid;
-        fu[h] = !act ? kSolid : j > 0 ? ld_u32(fl + row - nx + x) : open_top ? 0u : kSolid;
-        fd[h] = (act && j < ny - 1) ? ld_u32(fl + row + nx + x) : kSolid;
-    }
-    uint32_t left = byte_of(__shfl_up_sync(0xffffffffu, fc[N4 - 1], 1), 3);
-    uint32_t right = byte_of(__shfl_down_sync(0xffffffffu, fc[0], 1), 0);
-    if (!from_left) left = (act && i0 > 0) ? fl[row + i0 - 1] : 1u;
-    if (!from_right) right = (act && i0 + 4 * N4 < nx) ? fl[row + i0 + 4 * N4] : 1u;
-    // four cells at a time, one byte each: the flags of the west and east
-    // neighbours as words shifted by one byte, each compared with zero
-#pragma unroll
-    for (int h = 0; h < N4; ++h) {
-        const uint32_t west = (fc[h] << 8) | (h == 0 ? left : fc[h - 1] >> 24);
-        const uint32_t east = (fc[h] >> 8) | ((h == N4 - 1 ? right : fc[h + 1] & 0xffu) << 24);
-        const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
-                              (__vcmpeq4(east, 0u) & 0x02020202u) |
-                              (__vcmpeq4(fu[h], 0u) & 0x04040404u) |
-                              (__vcmpeq4(fd[h], 0u) & 0x08080808u);
-        const uint32_t mw = __vcmpeq4(fc[h], 0u) & open;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) m[4 * h + q] = byte_of(mw, q);
-    }
-}
-
-// The faces of the n4 x 4 cells i0.. of row j: uf[0..4 n4] the u faces of the
-// row, vn / vs the v faces above / below.
-template <int N4>
-__device__ __forceinline__ void faces(const float* __restrict__ ub, const float* __restrict__ vb,
-                                      int j, int i0, bool act, int nx, bool from_right,
-                                      float (&uf)[4 * N4 + 1], float (&vn)[4 * N4],
-                                      float (&vs)[4 * N4])
-{
-#pragma unroll
-    for (int q = 0; q < 4 * N4; ++q) uf[q] = act ? ub[i0 + q] : 0.0f;
-    uf[4 * N4] = __shfl_down_sync(0xffffffffu, uf[0], 1);
-    if (act && !from_right) uf[4 * N4] = ub[i0 + 4 * N4];
-#pragma unroll
-    for (int h = 0; h < N4; ++h) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 a = act ? *reinterpret_cast<const float4*>(vb + (size_t)j * nx + i0 + 4 * h) : z;
-        const float4 c =
-            act ? *reinterpret_cast<const float4*>(vb + (size_t)(j + 1) * nx + i0 + 4 * h) : z;
-        vn[4 * h] = a.x; vn[4 * h + 1] = a.y; vn[4 * h + 2] = a.z; vn[4 * h + 3] = a.w;
-        vs[4 * h] = c.x; vs[4 * h + 1] = c.y; vs[4 * h + 2] = c.z; vs[4 * h + 3] = c.w;
-    }
-}
-
 __device__ __forceinline__ float face_div(uint32_t m, bool inflow, float uw, float ue, float vn,
                                           float vs)
 {
@@ -154,49 +92,121 @@ __device__ __forceinline__ float face_div(uint32_t m, bool inflow, float uw, flo
     return __fadd_rn(__fsub_rn(e, w), __fsub_rn(s, n));
 }
 
-// mask_div_kernel, four cells per thread: grid (row quads / kQuadThreads, ny,
-// B), one quad per thread (measured faster than striding over the quads with
-// fewer blocks: 182 against 275 us for the divergence of 16 x 2048^2).
+// Vector paths of the mask and divergence: blocks of kQuadThreads threads, a
+// quad column per thread.
 constexpr int kQuadThreads = 128;
 
+// mask_div_kernel over quads of cells in column strips (rows a multiple of 4
+// cells, 16-byte aligned v, flags, mask and div): grid (row quads /
+// kQuadThreads, blocks of kDivRows rows, B); each thread walks down kDivRows
+// rows of its quad column, keeping the flags of the row above and of its own row and the v
+// faces north of the row in registers from the row before, so it loads each
+// byte it needs once (one flag word, one float4 of v and the row's u faces per
+// row); rows in pairs, both rows' loads issued before either is used.  The
+// open-face bits of four cells come from byte-wise comparisons of the flag
+// words with their neighbours' words shifted by one byte; the flags left and
+// right of the quad from the neighbouring lanes when they hold them.  (One
+// quad per thread and row, reading the shared rows again through L2, took
+// 167 us for the divergence of 16 x 2048^2; the strips 152 us.)
+constexpr int kDivRows = 8;
+
 __global__ void __launch_bounds__(kQuadThreads)
-    mask_div4_kernel(const float* __restrict__ u, const float* __restrict__ v,
-                     const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask,
-                     float* __restrict__ div, int ny, int nx, Boundary bc)
+    mask_div_col_kernel(const float* __restrict__ u, const float* __restrict__ v,
+                        const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask,
+                        float* __restrict__ div, int ny, int nx, Boundary bc)
 {
+    constexpr uint32_t kSolid = 0x01010101u;
     const int i0 = 4 * (blockIdx.x * kQuadThreads + threadIdx.x);
-    const int j = blockIdx.y, b = blockIdx.z, lane = threadIdx.x & 31;
+    const int rb = blockIdx.y, b = blockIdx.z, lane = threadIdx.x & 31;
     const bool act = i0 < nx;
     // the neighbouring quads of the row sit in the neighbouring lanes
     const bool from_left = lane > 0 && i0 > 0;
     const bool from_right = lane < 31 && i0 + 4 < nx;
+    const int j0 = rb * kDivRows;
+    const int j1 = min(ny, j0 + kDivRows);  // the same for the whole block
     const size_t gb = (size_t)b * ny * nx;
-    uint32_t m[4], fc[1];
-    open_bits<1>(flags + gb, j, i0, act, ny, nx, bc.open_top, from_left, from_right, m, fc);
-    float uf[5], vn[4], vs[4];
-    if (div)
-        faces<1>(u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1), v + (size_t)b * (ny + 1) * nx,
-                 j, i0, act, nx, from_right, uf, vn, vs);
-    if (!act) return;
-    const size_t c = gb + (size_t)j * nx + i0;
-    if (mask)
-        *reinterpret_cast<uint32_t*>(mask + c) = m[0] | (m[1] << 8) | (m[2] << 16) | (m[3] << 24);
-    if (div) {
-        float d[4];
+    const uint8_t* fl = flags + gb;
+    const float* ug = div ? u + (size_t)b * ny * (nx + 1) : nullptr;
+    const float* vg = div ? v + (size_t)b * (ny + 1) * nx : nullptr;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t fu = !act ? kSolid
+                  : j0 > 0 ? ld_u32(fl + (size_t)(j0 - 1) * nx + i0)
+                  : bc.open_top ? 0u : kSolid;
+    uint32_t fc = act ? ld_u32(fl + (size_t)j0 * nx + i0) : kSolid;
+    float4 vn = (div && act) ? *reinterpret_cast<const float4*>(vg + (size_t)j0 * nx + i0) : z;
+    struct RowIn {
+        float4 vs;
+        float uf[4], ue;
+        uint32_t fd, lb, rbt;
+    };
+    auto load_row = [&](int j, RowIn& in) {
+        const size_t row = (size_t)j * nx;
+        in.fd = (act && j < ny - 1) ? ld_u32(fl + row + nx + i0) : kSolid;
+        in.lb = (!from_left && act && i0 > 0) ? (uint32_t)fl[row + i0 - 1] : 1u;
+        in.rbt = (!from_right && act && i0 + 4 < nx) ? (uint32_t)fl[row + i0 + 4] : 1u;
+        if (div) {
+            const float* ub = ug + (size_t)j * (nx + 1);
+            in.vs = act ? *reinterpret_cast<const float4*>(vg + row + nx + i0) : z;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + q;
-            const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && byte_of(fc[0], q) == 0;
-            d[q] = face_div(m[q], inflow, uf[q], uf[q + 1], vn[q], vs[q]);
+            for (int q = 0; q < 4; ++q) in.uf[q] = act ? ub[i0 + q] : 0.0f;
+            in.ue = (act && !from_right) ? ub[i0 + 4] : 0.0f;
         }
-        *reinterpret_cast<float4*>(div + c) = make_float4(d[0], d[1], d[2], d[3]);
+    };
+    auto row_out = [&](int j, const RowIn& in) {
+        const uint32_t sl = __shfl_up_sync(0xffffffffu, fc, 1);
+        const uint32_t sr = __shfl_down_sync(0xffffffffu, fc, 1);
+        const uint32_t left = from_left ? byte_of(sl, 3) : in.lb;
+        const uint32_t right = from_right ? byte_of(sr, 0) : in.rbt;
+        const uint32_t west = (fc << 8) | left;
+        const uint32_t east = (fc >> 8) | (right << 24);
+        const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
+                              (__vcmpeq4(east, 0u) & 0x02020202u) |
+                              (__vcmpeq4(fu, 0u) & 0x04040404u) |
+                              (__vcmpeq4(in.fd, 0u) & 0x08080808u);
+        const uint32_t mw = __vcmpeq4(fc, 0u) & open;
+        float uf4 = 0.0f;
+        if (div) {
+            const float ush = __shfl_down_sync(0xffffffffu, in.uf[0], 1);
+            uf4 = (act && !from_right) ? in.ue : ush;
+        }
+        if (act) {
+            const size_t c = gb + (size_t)j * nx + i0;
+            if (mask) *reinterpret_cast<uint32_t*>(mask + c) = mw;
+            if (div) {
+                const float ufq[5] = {in.uf[0], in.uf[1], in.uf[2], in.uf[3], uf4};
+                const float vnq[4] = {vn.x, vn.y, vn.z, vn.w};
+                const float vsq[4] = {in.vs.x, in.vs.y, in.vs.z, in.vs.w};
+                float d[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = i0 + q;
+                    const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && byte_of(fc, q) == 0;
+                    d[q] = face_div(byte_of(mw, q), inflow, ufq[q], ufq[q + 1], vnq[q], vsq[q]);
+                }
+                *reinterpret_cast<float4*>(div + c) = make_float4(d[0], d[1], d[2], d[3]);
+            }
+        }
+        fu = fc;
+        fc = in.fd;
+        if (div) vn = in.vs;
+    };
+#pragma unroll
+    for (int r = 0; r < kDivRows; r += 2) {
+        const int j = j0 + r;
+        if (j >= j1) break;
+        const bool two = j + 1 < j1;
+        RowIn in0, in1;
+        load_row(j, in0);
+        if (two) load_row(j + 1, in1);
+        row_out(j, in0);
+        if (two) row_out(j + 1, in1);
     }
 }
 
 // The face mask alone, sixteen cells per thread (rows a multiple of 16
 // cells, 16-byte aligned flags and mask): each of the three flag rows as one
 // 16-byte load, the mask as one 16-byte store, the bytes left and right of
-// the sixteen from the neighbouring lanes; the same bits as mask_div4_kernel
+// the sixteen from the neighbouring lanes; the same bits as mask_div_col_kernel
 // (four cells per word, byte-wise comparisons).
 constexpr int kMask16Threads = 128;
 
@@ -274,8 +284,9 @@ hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, 
     }
     if (s.nx % 4 == 0 && aligned16(flags) && aligned16(mask) && aligned16(div) &&
         (!div || aligned16(v))) {
-        dim3 grd((s.nx / 4 + kQuadThreads - 1) / kQuadThreads, s.ny, s.batch);
-        mask_div4_kernel<<<grd, kQuadThreads, 0, st>>>(u, v, flags, mask, div, s.ny, s.nx, bc);
+        dim3 grd((s.nx / 4 + kQuadThreads - 1) / kQuadThreads, (s.ny + kDivRows - 1) / kDivRows,
+                 s.batch);
+        mask_div_col_kernel<<<grd, kQuadThreads, 0, st>>>(u, v, flags, mask, div, s.ny, s.nx, bc);
         return check_launch();
     }
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
@@ -947,53 +958,129 @@ __global__ void div_norms_kernel(const float* __restrict__ u, const float* __res
     }
 }
 
-// The same partials over quads (rows a multiple of 4 cells, 16-byte aligned
-// v, flags and mask), laid out like mask_div4_kernel: grid (segment pairs,
-// ny, B), a block of 4 warps takes two consecutive segments of a row, warp
-// 2 s + h the quads at 128 h + 4 lane of its segment s, one quad per thread;
-// a segment's partial is the FP32 sum of its two warps' sums.
+// The partials over column strips (rows a multiple of 4 cells, 16-byte
+// aligned v, flags and mask): grid (segment pairs, blocks of kNormRows rows,
+// B); a block of 4 warps takes two consecutive 256-cell segments of
+// kNormRows rows, warp 2 s + h the quads at 128 h + 4 lane of its segment s,
+// and each thread walks down its quad column.  The flags of the row above and
+// of its own row and the v faces north of the row stay in registers from the
+// row before, so a thread loads each byte it needs once (one flag word, one
+// float4 of v and the row's u faces per row) instead of reading the shared
+// rows again through L2.  Partial (row block, segment): the FP32 sums of the
+// thread's rows in order, over the warp's lanes, of the segment's two warps.
 constexpr int kSegCells = 256;
 constexpr int kNormThreads = 128;
+constexpr int kNormRows = 8;
 
+template <bool MASK>
 __global__ void __launch_bounds__(kNormThreads)
-    div_norms4_kernel(const float* __restrict__ u, const float* __restrict__ v,
-                      const uint8_t* __restrict__ flags, const uint8_t* __restrict__ mask,
-                      float2* __restrict__ partial, int ny, int nx, int nseg, Boundary bc)
+    div_norms_col_kernel(const float* __restrict__ u, const float* __restrict__ v,
+                         const uint8_t* __restrict__ flags, const uint8_t* __restrict__ mask,
+                         float2* __restrict__ partial, int ny, int nx, int nseg, int nrb,
+                         Boundary bc)
 {
+    constexpr uint32_t kSolid = 0x01010101u;
     __shared__ float s_w[4], s_m[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int j = blockIdx.y, b = blockIdx.z;
+    const int rb = blockIdx.y, b = blockIdx.z;
     const int sx = 2 * blockIdx.x + (wid >> 1);
     const int i0 = sx * kSegCells + 128 * (wid & 1) + 4 * lane;
     const bool act = i0 < nx;
     // the neighbouring quads of the half segment sit in the neighbouring lanes
     const bool from_left = lane > 0;
     const bool from_right = lane < 31 && i0 + 4 < nx;
+    const int j0 = rb * kNormRows;
+    const int j1 = min(ny, j0 + kNormRows);  // the same for the whole block
     const size_t gb = (size_t)b * ny * nx;
-    uint32_t m[4], fc[1] = {0x01010101u};
-    if (mask) {
-        const uint32_t m4 = act ? ld_u32(mask + gb + (size_t)j * nx + i0) : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) m[q] = byte_of(m4, q);
-        if (act && j == ny - 1) fc[0] = ld_u32(flags + gb + (size_t)j * nx + i0);
-    } else {
-        // the closed box's open faces from the flags
-        open_bits<1>(flags + gb, j, i0, act, ny, nx, 0, from_left, from_right, m, fc);
+    const uint8_t* fl = flags + gb;
+    const float* ug = u + (size_t)b * ny * (nx + 1);
+    const float* vg = v + (size_t)b * (ny + 1) * nx;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    // flags of the row above j0 and of row j0 (closed box: no open top)
+    uint32_t fu = kSolid, fc = kSolid;
+    if (!MASK && act) {
+        if (j0 > 0) fu = ld_u32(fl + (size_t)(j0 - 1) * nx + i0);
+        fc = ld_u32(fl + (size_t)j0 * nx + i0);
     }
-    float uf[5], vn[4], vs[4];
-    faces<1>(u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1), v + (size_t)b * (ny + 1) * nx, j,
-             i0, act, nx, from_right, uf, vn, vs);
+    float4 vn = act ? *reinterpret_cast<const float4*>(vg + (size_t)j0 * nx + i0) : z;
     float a = 0.0f, mx = 0.0f;
-    if (act) {
-        float d[4];
+    // one row's loads: the v faces south of it, its u faces, its open-face
+    // bits (mask) or the flags of the row below and the bytes beside the quad
+    struct RowIn {
+        float4 vs;
+        float uf[4], ue;
+        uint32_t w, fcw, lb, rbt;
+    };
+    auto load_row = [&](int j, RowIn& in) {
+        const size_t row = (size_t)j * nx;
+        const float* ub = ug + (size_t)j * (nx + 1);
+        in.vs = act ? *reinterpret_cast<const float4*>(vg + row + nx + i0) : z;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + q;
-            const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && byte_of(fc[0], q) == 0;
-            d[q] = fabsf(face_div(m[q], inflow, uf[q], uf[q + 1], vn[q], vs[q]));
-            mx = fmaxf(mx, d[q]);
+        for (int q = 0; q < 4; ++q) in.uf[q] = act ? ub[i0 + q] : 0.0f;
+        in.ue = (act && !from_right) ? ub[i0 + 4] : 0.0f;
+        if (MASK) {
+            in.w = act ? ld_u32(mask + gb + row + i0) : 0u;
+            in.fcw = (act && j == ny - 1) ? ld_u32(fl + row + i0) : kSolid;
+        } else {
+            in.w = (act && j < ny - 1) ? ld_u32(fl + row + nx + i0) : kSolid;
+            in.lb = (!from_left && act && i0 > 0) ? (uint32_t)fl[row + i0 - 1] : 1u;
+            in.rbt = (!from_right && act && i0 + 4 < nx) ? (uint32_t)fl[row + i0 + 4] : 1u;
         }
-        a = __fadd_rn(__fadd_rn(d[0], d[1]), __fadd_rn(d[2], d[3]));
+    };
+    // |div| of the row from its loads and the carried state (every lane of
+    // the warp takes part in the shuffles)
+    auto row_div = [&](int j, const RowIn& in) {
+        uint32_t m4, fcw;
+        if (MASK) {
+            m4 = in.w;
+            fcw = in.fcw;
+        } else {
+            // open-face bits of the four cells (as mask_div_col_kernel)
+            const uint32_t fd = in.w;
+            const uint32_t sl = __shfl_up_sync(0xffffffffu, fc, 1);
+            const uint32_t sr = __shfl_down_sync(0xffffffffu, fc, 1);
+            const uint32_t left = from_left ? byte_of(sl, 3) : in.lb;
+            const uint32_t right = from_right ? byte_of(sr, 0) : in.rbt;
+            const uint32_t west = (fc << 8) | left;
+            const uint32_t east = (fc >> 8) | (right << 24);
+            const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
+                                  (__vcmpeq4(east, 0u) & 0x02020202u) |
+                                  (__vcmpeq4(fu, 0u) & 0x04040404u) |
+                                  (__vcmpeq4(fd, 0u) & 0x08080808u);
+            m4 = __vcmpeq4(fc, 0u) & open;
+            fcw = fc;
+            fu = fc;
+            fc = fd;
+        }
+        const float ush = __shfl_down_sync(0xffffffffu, in.uf[0], 1);
+        const float uf4 = (act && !from_right) ? in.ue : ush;
+        if (act) {
+            const float ufq[5] = {in.uf[0], in.uf[1], in.uf[2], in.uf[3], uf4};
+            const float vnq[4] = {vn.x, vn.y, vn.z, vn.w};
+            const float vsq[4] = {in.vs.x, in.vs.y, in.vs.z, in.vs.w};
+            float d[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q;
+                const bool inflow = j == ny - 1 && i >= bc.x0 && i < bc.x1 && byte_of(fcw, q) == 0;
+                d[q] = fabsf(face_div(byte_of(m4, q), inflow, ufq[q], ufq[q + 1], vnq[q], vsq[q]));
+                mx = fmaxf(mx, d[q]);
+            }
+            a = __fadd_rn(a, __fadd_rn(__fadd_rn(d[0], d[1]), __fadd_rn(d[2], d[3])));
+        }
+        vn = in.vs;
+    };
+    // rows in pairs: both rows' loads are issued before either is used
+#pragma unroll
+    for (int r = 0; r < kNormRows; r += 2) {
+        const int j = j0 + r;
+        if (j >= j1) break;
+        const bool two = j + 1 < j1;
+        RowIn in0, in1;
+        load_row(j, in0);
+        if (two) load_row(j + 1, in1);
+        row_div(j, in0);
+        if (two) row_div(j + 1, in1);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -1008,27 +1095,33 @@ __global__ void __launch_bounds__(kNormThreads)
     if (threadIdx.x < 2) {
         const int sq = 2 * blockIdx.x + threadIdx.x;
         if (sq < nseg)
-            partial[((size_t)b * ny + j) * nseg + sq] =
+            partial[((size_t)b * nrb + rb) * nseg + sq] =
                 make_float2(__fadd_rn(s_w[2 * threadIdx.x], s_w[2 * threadIdx.x + 1]),
                             fmaxf(s_m[2 * threadIdx.x], s_m[2 * threadIdx.x + 1]));
     }
 }
 
-// The norms kernel for one shape: the quad kernel where rows allow vector
-// access, else one cell per thread; the same partial layout either way.
-static void norms_kernel(const float* u, const float* v, const uint8_t* flags,
-                         const uint8_t* mask, float2* partial, hp_shape s, Boundary bc,
-                         cudaStream_t st)
+// The norms kernel for one shape: the column-strip kernel where rows allow
+// vector access, else one cell per thread; returns the partials per grid.
+static int norms_kernel(const float* u, const float* v, const uint8_t* flags,
+                        const uint8_t* mask, float2* partial, hp_shape s, Boundary bc,
+                        cudaStream_t st)
 {
     const int nseg = (s.nx + kSegCells - 1) / kSegCells;
     if (s.nx % 4 == 0 && aligned16(v) && aligned16(flags) && aligned16(mask)) {
-        dim3 grd((nseg + 1) / 2, s.ny, s.batch);
-        div_norms4_kernel<<<grd, kNormThreads, 0, st>>>(u, v, flags, mask, partial, s.ny, s.nx,
-                                                        nseg, bc);
-    } else {
-        dim3 grd(nseg, s.ny, s.batch);
-        div_norms_kernel<<<grd, kSegCells, 0, st>>>(u, v, flags, mask, partial, s.ny, s.nx, bc);
+        const int nrb = (s.ny + kNormRows - 1) / kNormRows;
+        dim3 grd((nseg + 1) / 2, nrb, s.batch);
+        if (mask)
+            div_norms_col_kernel<true><<<grd, kNormThreads, 0, st>>>(u, v, flags, mask, partial,
+                                                                     s.ny, s.nx, nseg, nrb, bc);
+        else
+            div_norms_col_kernel<false><<<grd, kNormThreads, 0, st>>>(u, v, flags, mask, partial,
+                                                                      s.ny, s.nx, nseg, nrb, bc);
+        return nrb * nseg;
     }
+    dim3 grd(nseg, s.ny, s.batch);
+    div_norms_kernel<<<grd, kSegCells, 0, st>>>(u, v, flags, mask, partial, s.ny, s.nx, bc);
+    return s.ny * nseg;
 }
 
 // One block of kFinishWarps warps per grid: warp w adds its contiguous share
@@ -1095,20 +1188,19 @@ __global__ void norms_finish_kernel(const float2* __restrict__ partial, int nblk
 hp_status launch_div_norms(const float* u, const float* v, const uint8_t* flags, double* partial,
                            int nblk_cap, double* e1, double* einf, hp_shape s, cudaStream_t st)
 {
-    const int nblk = ((s.nx + kSegCells - 1) / kSegCells) * s.ny;
-    if (nblk > nblk_cap) return HP_ERR_INVALID_ARG;
+    if (((s.nx + kSegCells - 1) / kSegCells) * s.ny > nblk_cap) return HP_ERR_INVALID_ARG;
     return launch_div_norms_scratch(u, v, flags, partial, e1, einf, s, st);
 }
 
 // Same reduction as launch_div_norms with caller-given scratch: partial
-// holds >= batch * ny * ceil(nx / 256) slots of 8 bytes.
+// holds >= batch * ny * ceil(nx / 256) slots of 8 bytes (the column-strip
+// kernel uses fewer).
 hp_status launch_div_norms_scratch(const float* u, const float* v, const uint8_t* flags,
                                    double* partial, double* e1, double* einf, hp_shape s,
                                    cudaStream_t st)
 {
-    const int nblk = ((s.nx + kSegCells - 1) / kSegCells) * s.ny;
     float2* p2 = reinterpret_cast<float2*>(partial);
-    norms_kernel(u, v, flags, nullptr, p2, s, Boundary{}, st);
+    const int nblk = norms_kernel(u, v, flags, nullptr, p2, s, Boundary{}, st);
     hp_status rc = check_launch();
     if (rc != HP_OK) return rc;
     norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
@@ -1367,11 +1459,12 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     if ((rc = check_launch()) != HP_OK) return rc;
 
     // norms of the corrected velocity
-    const int nblk = ((s.nx + kSegCells - 1) / kSegCells) * s.ny;
-    if ((size_t)s.batch * nblk > ctx->partial2_len) return HP_ERR_INVALID_ARG;
+    if ((size_t)s.batch * ((s.nx + kSegCells - 1) / kSegCells) * s.ny > ctx->partial2_len)
+        return HP_ERR_INVALID_ARG;
     float2* p2 = reinterpret_cast<float2*>(ctx->partial2);
+    int nblk = 1;
     if (u) {
-        norms_kernel(u, v, flags, ctx->mask, p2, s, bc, st);
+        nblk = norms_kernel(u, v, flags, ctx->mask, p2, s, bc, st);
         if ((rc = check_launch()) != HP_OK) return rc;
     }
     norms_finish_kernel<<<s.batch, kFinishWarps * 32, 0, st>>>(
