@@ -108,7 +108,8 @@ constexpr int kQuadThreads = 128;
 // right of the quad from the neighbouring lanes when they hold them.  (One
 // quad per thread and row, reading the shared rows again through L2, took
 // 167 us for the divergence of 16 x 2048^2; the strips 152 us.)
-constexpr int kDivRows = 8;  // (four rows' loads in flight at a time measured no faster: 80 registers)
+// (four rows' loads in flight at a time measured no faster: 80 registers)
+constexpr int kDivRows = 8;
 
 __global__ void __launch_bounds__(kQuadThreads)
     mask_div_col_kernel(const float* __restrict__ u, const float* __restrict__ v,
