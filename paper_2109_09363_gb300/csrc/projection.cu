@@ -67,13 +67,10 @@ __global__ void mask_div_kernel(const float* __restrict__ u, const float* __rest
 // of the cells left and right of the four come from the adjacent lanes when
 // they hold them), v and div, p, phi as float4 (16-byte aligned rows), u
 // (rows of nx + 1) as scalars with the fifth face from the next lane.  The
-// mask/divergence and norm kernels walk column strips (a quad column of a
-// few rows per thread), the correction strides over the quads with a grid of
-// a few blocks per SM; every lane of a warp takes part in the shuffles, lanes
-// past the end do no memory access.
-
-constexpr int kStreamThreads = 256;
-constexpr int kStreamBlocksPerSm = 8;
+// mask/divergence, correction and norm kernels walk column strips (a quad
+// column of a few rows per thread), so each thread loads every byte it needs
+// once; every lane of a warp takes part in the shuffles, lanes past the end do
+// no memory access.
 
 __device__ __forceinline__ uint32_t ld_u32(const uint8_t* p)
 {
@@ -204,83 +201,93 @@ __global__ void __launch_bounds__(kQuadThreads)
     }
 }
 
-// The face mask alone, sixteen cells per thread (rows a multiple of 16
-// cells, 16-byte aligned flags and mask): each of the three flag rows as one
-// 16-byte load, the mask as one 16-byte store, the bytes left and right of
-// the sixteen from the neighbouring lanes; the same bits as mask_div_col_kernel
-// (four cells per word, byte-wise comparisons).
+// The face mask alone over column strips of sixteen cells (rows a multiple
+// of 16 cells, 16-byte aligned flags and mask): grid (row sixteens /
+// kMask16Threads, blocks of kDivRows rows, B); each thread walks down its
+// column keeping the flag words of the row above and of its own row from the
+// row before, one 16-byte load (the row below) and one 16-byte store per row,
+// rows in pairs; the bytes left and right of the sixteen from the
+// neighbouring lanes.  The same bits as mask_div_col_kernel.  (A sixteen per
+// thread and row, the three flag rows loaded each time: 0.0395 ms for
+// 16 x 2048^2; a quad per thread: 0.078 ms.)
 constexpr int kMask16Threads = 128;
 
 __global__ void __launch_bounds__(kMask16Threads)
-    mask16_kernel(const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask, int ny, int nx,
-                  int open_top)
+    mask16_col_kernel(const uint8_t* __restrict__ flags, uint8_t* __restrict__ mask, int ny,
+                      int nx, int open_top)
 {
     constexpr uint32_t kSolid = 0x01010101u;
     const int i0 = 16 * (blockIdx.x * kMask16Threads + threadIdx.x);
-    const int j = blockIdx.y, b = blockIdx.z, lane = threadIdx.x & 31;
+    const int rb = blockIdx.y, b = blockIdx.z, lane = threadIdx.x & 31;
     const bool act = i0 < nx;
     const bool from_left = lane > 0 && i0 > 0;
     const bool from_right = lane < 31 && i0 + 16 < nx;
+    const int j0 = rb * kDivRows;
+    const int j1 = min(ny, j0 + kDivRows);  // the same for the whole block
     const uint8_t* fl = flags + (size_t)b * ny * nx;
-    const size_t row = (size_t)j * nx;
+    uint8_t* mk = mask + (size_t)b * ny * nx;
     const uint4 solid = make_uint4(kSolid, kSolid, kSolid, kSolid);
-    const uint4 open4 = make_uint4(0u, 0u, 0u, 0u);
-    const uint4 c4 = act ? *reinterpret_cast<const uint4*>(fl + row + i0) : solid;
-    const uint4 u4 = !act ? solid
-                     : j > 0 ? *reinterpret_cast<const uint4*>(fl + row - nx + i0)
-                     : open_top ? open4 : solid;
-    const uint4 d4 = (act && j < ny - 1) ? *reinterpret_cast<const uint4*>(fl + row + nx + i0)
-                                         : solid;
-    const uint32_t fc[4] = {c4.x, c4.y, c4.z, c4.w};
-    const uint32_t fu[4] = {u4.x, u4.y, u4.z, u4.w};
-    const uint32_t fd[4] = {d4.x, d4.y, d4.z, d4.w};
-    uint32_t left = byte_of(__shfl_up_sync(0xffffffffu, fc[3], 1), 3);
-    uint32_t right = byte_of(__shfl_down_sync(0xffffffffu, fc[0], 1), 0);
-    if (!from_left) left = (act && i0 > 0) ? fl[row + i0 - 1] : 1u;
-    if (!from_right) right = (act && i0 + 16 < nx) ? fl[row + i0 + 16] : 1u;
-    if (!act) return;
-    uint32_t mw[4];
+    uint4 fu = !act ? solid
+               : j0 > 0 ? *reinterpret_cast<const uint4*>(fl + (size_t)(j0 - 1) * nx + i0)
+               : open_top ? make_uint4(0u, 0u, 0u, 0u) : solid;
+    uint4 fc = act ? *reinterpret_cast<const uint4*>(fl + (size_t)j0 * nx + i0) : solid;
+    struct RowIn {
+        uint4 fd;
+        uint32_t lb, rbt;
+    };
+    auto load_row = [&](int j, RowIn& in) {
+        const size_t row = (size_t)j * nx;
+        in.fd = (act && j < ny - 1) ? *reinterpret_cast<const uint4*>(fl + row + nx + i0) : solid;
+        in.lb = (!from_left && act && i0 > 0) ? (uint32_t)fl[row + i0 - 1] : 1u;
+        in.rbt = (!from_right && act && i0 + 16 < nx) ? (uint32_t)fl[row + i0 + 16] : 1u;
+    };
+    auto row_out = [&](int j, const RowIn& in) {
+        const uint32_t c[4] = {fc.x, fc.y, fc.z, fc.w};
+        const uint32_t up[4] = {fu.x, fu.y, fu.z, fu.w};
+        const uint32_t dn[4] = {in.fd.x, in.fd.y, in.fd.z, in.fd.w};
+        const uint32_t sl = __shfl_up_sync(0xffffffffu, c[3], 1);
+        const uint32_t sr = __shfl_down_sync(0xffffffffu, c[0], 1);
+        const uint32_t left = from_left ? byte_of(sl, 3) : in.lb;
+        const uint32_t right = from_right ? byte_of(sr, 0) : in.rbt;
+        uint32_t mw[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const uint32_t west = (fc[h] << 8) | (h == 0 ? left : fc[h - 1] >> 24);
-        const uint32_t east = (fc[h] >> 8) | ((h == 3 ? right : fc[h + 1] & 0xffu) << 24);
-        const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
-                              (__vcmpeq4(east, 0u) & 0x02020202u) |
-                              (__vcmpeq4(fu[h], 0u) & 0x04040404u) |
-                              (__vcmpeq4(fd[h], 0u) & 0x08080808u);
-        mw[h] = __vcmpeq4(fc[h], 0u) & open;
+        for (int h = 0; h < 4; ++h) {
+            const uint32_t west = (c[h] << 8) | (h == 0 ? left : c[h - 1] >> 24);
+            const uint32_t east = (c[h] >> 8) | ((h == 3 ? right : c[h + 1] & 0xffu) << 24);
+            const uint32_t open = (__vcmpeq4(west, 0u) & 0x01010101u) |
+                                  (__vcmpeq4(east, 0u) & 0x02020202u) |
+                                  (__vcmpeq4(up[h], 0u) & 0x04040404u) |
+                                  (__vcmpeq4(dn[h], 0u) & 0x08080808u);
+            mw[h] = __vcmpeq4(c[h], 0u) & open;
+        }
+        if (act)
+            *reinterpret_cast<uint4*>(mk + (size_t)j * nx + i0) =
+                make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        fu = fc;
+        fc = in.fd;
+    };
+#pragma unroll
+    for (int r = 0; r < kDivRows; r += 2) {
+        const int j = j0 + r;
+        if (j >= j1) break;
+        const bool two = j + 1 < j1;
+        RowIn in0, in1;
+        load_row(j, in0);
+        if (two) load_row(j + 1, in1);
+        row_out(j, in0);
+        if (two) row_out(j + 1, in1);
     }
-    *reinterpret_cast<uint4*>(mask + (size_t)b * ny * nx + row + i0) =
-        make_uint4(mw[0], mw[1], mw[2], mw[3]);
 }
 
 static bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-
-// Blocks of a streaming kernel: a few per SM of the current device, no more
-// than the work needs.
-static int stream_blocks(uint64_t items, int per_block)
-{
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-        nsm = 148;
-    const uint64_t need = (items + per_block - 1) / per_block;
-    const uint64_t cap = (uint64_t)kStreamBlocksPerSm * nsm;
-    return (int)(need < cap ? (need > 0 ? need : 1) : cap);
-}
-
-// the vector paths index quads and segments with 32-bit integers
-static bool vec_shape(hp_shape s, int multiple)
-{
-    return s.nx % multiple == 0 && (uint64_t)s.batch * s.ny * s.nx < (1ull << 32);
-}
 
 hp_status launch_mask_div(const float* u, const float* v, const uint8_t* flags, uint8_t* mask,
                           float* div, hp_shape s, cudaStream_t st, Boundary bc)
 {
     if (!div && mask && s.nx % 16 == 0 && aligned16(flags) && aligned16(mask)) {
-        dim3 grd((s.nx / 16 + kMask16Threads - 1) / kMask16Threads, s.ny, s.batch);
-        mask16_kernel<<<grd, kMask16Threads, 0, st>>>(flags, mask, s.ny, s.nx, bc.open_top);
+        dim3 grd((s.nx / 16 + kMask16Threads - 1) / kMask16Threads, (s.ny + kDivRows - 1) / kDivRows,
+                 s.batch);
+        mask16_col_kernel<<<grd, kMask16Threads, 0, st>>>(flags, mask, s.ny, s.nx, bc.open_top);
         return check_launch();
     }
     if (s.nx % 4 == 0 && aligned16(flags) && aligned16(mask) && aligned16(div) &&
@@ -827,66 +834,102 @@ __global__ void correct_kernel(float* __restrict__ u, float* __restrict__ v,
     if (phi_out) phi_out[gb + c] = pc;
 }
 
-// correct_kernel over quads (four cells) of all rows, quads = B ny nx / 4.
-__global__ void __launch_bounds__(kStreamThreads)
-    correct4_kernel(float* __restrict__ u, float* __restrict__ v, const uint8_t* __restrict__ mask,
-                    const uint8_t* __restrict__ flags, const float* __restrict__ phi0,
-                    const float* __restrict__ phi1, const GridState* __restrict__ gs,
-                    float* __restrict__ p_out, float* __restrict__ phi_out, float scale, int ny,
-                    int nx, uint32_t quads, Boundary bc)
+// correct_kernel over quads of cells in column strips (rows a multiple of 4
+// cells, 16-byte aligned v, flags, p and phi copy): grid (row quads /
+// kQuadThreads, blocks of kDivRows rows, B); each thread walks down kDivRows
+// rows of its quad column and keeps phi of the row above (its cells' north
+// neighbours) in registers from the row before instead of reading it again
+// through L2; phi west of the quad from the previous lane; rows in pairs,
+// both rows' loads issued before either is used.  (A grid-stride kernel over
+// single quads took 335 us for 16 x 2048^2.)
+__global__ void __launch_bounds__(kQuadThreads)
+    correct_col_kernel(float* __restrict__ u, float* __restrict__ v,
+                       const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+                       const float* __restrict__ phi0, const float* __restrict__ phi1,
+                       const GridState* __restrict__ gs, float* __restrict__ p_out,
+                       float* __restrict__ phi_out, float scale, int ny, int nx, Boundary bc)
 {
-    const uint32_t nxq = (uint32_t)nx / 4;
-    const int lane = threadIdx.x & 31;
+    const int i0 = 4 * (blockIdx.x * kQuadThreads + threadIdx.x);
+    const int rb = blockIdx.y, b = blockIdx.z, lane = threadIdx.x & 31;
+    const bool act = i0 < nx;
+    // phi west of cell i0: the previous lane's last cell in the same row
+    const bool from_left = lane > 0 && i0 > 0;
+    const int j0 = rb * kDivRows;
+    const int j1 = min(ny, j0 + kDivRows);  // the same for the whole block
+    const size_t gb = (size_t)b * ny * nx;
+    const float* ph = (gs[b].final_buf ? phi1 : phi0) + gb;
+    float* ug = u ? u + (size_t)b * ny * (nx + 1) : nullptr;
+    float* vg = u ? v + (size_t)b * (ny + 1) * nx : nullptr;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t base = blockIdx.x * kStreamThreads; base < quads; base += gridDim.x * kStreamThreads) {
-        const uint32_t item = base + threadIdx.x;
-        const bool act = item < quads;
-        const uint32_t row = act ? item / nxq : 0u;
-        const int i0 = act ? 4 * (int)(item - row * nxq) : 0;
-        const int b = (int)(row / (uint32_t)ny), j = (int)row - b * ny;
-        const size_t gb = (size_t)b * ny * nx;
-        const float* ph = (gs[b].final_buf ? phi1 : phi0) + gb;
+    // phi north of row j0 (the exterior above row 0 reads as 0)
+    float4 pn = (act && j0 > 0) ? *reinterpret_cast<const float4*>(ph + (size_t)(j0 - 1) * nx + i0) : z;
+    struct RowIn {
+        float4 p4, vn4;
+        float pwm, uw[4];
+        uint32_t m4;
+    };
+    auto load_row = [&](int j, RowIn& in) {
         const size_t c = (size_t)j * nx + i0;
-        const float4 p4 = act ? *reinterpret_cast<const float4*>(ph + c) : z;
-        // phi west of cell i0: the previous lane's last cell in the same row
-        float pw = __shfl_up_sync(0xffffffffu, p4.w, 1);
-        if (!(lane > 0 && i0 > 0)) pw = (act && i0 > 0) ? ph[c - 1] : 0.0f;
-        if (!act) continue;
-        const float pc[4] = {p4.x, p4.y, p4.z, p4.w};
+        in.p4 = act ? *reinterpret_cast<const float4*>(ph + c) : z;
+        in.pwm = (!from_left && act && i0 > 0) ? ph[c - 1] : 0.0f;
         if (u) {
-            const uint32_t m4 = ld_u32(mask + gb + c);
-            const float4 pu4 = j > 0 ? *reinterpret_cast<const float4*>(ph + c - nx) : z;
-            const float pu[4] = {pu4.x, pu4.y, pu4.z, pu4.w};
-            float* ub = u + (size_t)b * ny * (nx + 1) + (size_t)j * (nx + 1);
-            float* vb = v + (size_t)b * (ny + 1) * nx;
-            const float4 vn4 = *reinterpret_cast<const float4*>(vb + (size_t)j * nx + i0);
-            const float vn[4] = {vn4.x, vn4.y, vn4.z, vn4.w};
-            float uo[4], vo[4];
+            in.m4 = act ? ld_u32(mask + gb + c) : 0u;
+            in.vn4 = act ? *reinterpret_cast<const float4*>(vg + c) : z;
+            const float* ub = ug + (size_t)j * (nx + 1);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t m = byte_of(m4, q);
-                const float west = q == 0 ? pw : pc[q - 1];
-                uo[q] = (m & 1u) ? __fsub_rn(ub[i0 + q], __fsub_rn(pc[q], west)) : 0.0f;
-                vo[q] = (m & 4u) ? __fsub_rn(vn[q], __fsub_rn(pc[q], pu[q])) : 0.0f;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) ub[i0 + q] = uo[q];
-            *reinterpret_cast<float4*>(vb + (size_t)j * nx + i0) = make_float4(vo[0], vo[1], vo[2], vo[3]);
-            if (i0 + 4 == nx) ub[nx] = 0.0f;
-            if (j == ny - 1) {
-                const uint32_t f4 = ld_u32(flags + gb + c);
+            for (int q = 0; q < 4; ++q) in.uw[q] = act ? ub[i0 + q] : 0.0f;
+        }
+    };
+    auto row_out = [&](int j, const RowIn& in) {
+        const float sh = __shfl_up_sync(0xffffffffu, in.p4.w, 1);
+        const float pw = from_left ? sh : in.pwm;
+        if (act) {
+            const size_t c = (size_t)j * nx + i0;
+            const float pc[4] = {in.p4.x, in.p4.y, in.p4.z, in.p4.w};
+            if (u) {
+                const float pu[4] = {pn.x, pn.y, pn.z, pn.w};
+                const float vn[4] = {in.vn4.x, in.vn4.y, in.vn4.z, in.vn4.w};
+                float* ub = ug + (size_t)j * (nx + 1);
+                float uo[4], vo[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int i = i0 + q;
-                    if (!(i >= bc.x0 && i < bc.x1 && byte_of(f4, q) == 0)) vb[(size_t)ny * nx + i] = 0.0f;
+                    const uint32_t m = byte_of(in.m4, q);
+                    const float west = q == 0 ? pw : pc[q - 1];
+                    uo[q] = (m & 1u) ? __fsub_rn(in.uw[q], __fsub_rn(pc[q], west)) : 0.0f;
+                    vo[q] = (m & 4u) ? __fsub_rn(vn[q], __fsub_rn(pc[q], pu[q])) : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ub[i0 + q] = uo[q];
+                *reinterpret_cast<float4*>(vg + c) = make_float4(vo[0], vo[1], vo[2], vo[3]);
+                if (i0 + 4 == nx) ub[nx] = 0.0f;
+                if (j == ny - 1) {
+                    const uint32_t f4 = ld_u32(flags + gb + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int i = i0 + q;
+                        if (!(i >= bc.x0 && i < bc.x1 && byte_of(f4, q) == 0))
+                            vg[(size_t)ny * nx + i] = 0.0f;
+                    }
                 }
             }
+            if (p_out)
+                *reinterpret_cast<float4*>(p_out + gb + c) =
+                    make_float4(__fmul_rn(pc[0], scale), __fmul_rn(pc[1], scale),
+                                __fmul_rn(pc[2], scale), __fmul_rn(pc[3], scale));
+            if (phi_out) *reinterpret_cast<float4*>(phi_out + gb + c) = in.p4;
         }
-        if (p_out)
-            *reinterpret_cast<float4*>(p_out + gb + c) =
-                make_float4(__fmul_rn(pc[0], scale), __fmul_rn(pc[1], scale), __fmul_rn(pc[2], scale),
-                            __fmul_rn(pc[3], scale));
-        if (phi_out) *reinterpret_cast<float4*>(phi_out + gb + c) = p4;
+        pn = in.p4;
+    };
+#pragma unroll
+    for (int r = 0; r < kDivRows; r += 2) {
+        const int j = j0 + r;
+        if (j >= j1) break;
+        const bool two = j + 1 < j1;
+        RowIn in0, in1;
+        load_row(j, in0);
+        if (two) load_row(j + 1, in1);
+        row_out(j, in0);
+        if (two) row_out(j + 1, in1);
     }
 }
 
@@ -1449,12 +1492,13 @@ hp_status project_impl(hp_ctx* ctx, float* u, float* v, const uint8_t* flags, hp
     dim3 blk(256), grd((s.nx + 255) / 256, s.ny, s.batch);
     const float scale = prm->rho0 / prm->dt;
     const Boundary bc = boundary_of(*prm);
-    if (vec_shape(s, 4) && (!u || aligned16(v)) && aligned16(flags) && aligned16(p_out) &&
+    if (s.nx % 4 == 0 && (!u || aligned16(v)) && aligned16(flags) && aligned16(p_out) &&
         aligned16(phi_copy_out)) {
-        const uint32_t quads = (uint32_t)((uint64_t)s.batch * s.ny * s.nx / 4);
-        correct4_kernel<<<stream_blocks(quads, kStreamThreads), kStreamThreads, 0, st>>>(
-            u, v, ctx->mask, flags, ctx->phi[0], ctx->phi[1], ctx->gs, p_out, phi_copy_out, scale,
-            s.ny, s.nx, quads, bc);
+        dim3 g4((s.nx / 4 + kQuadThreads - 1) / kQuadThreads, (s.ny + kDivRows - 1) / kDivRows,
+                s.batch);
+        correct_col_kernel<<<g4, kQuadThreads, 0, st>>>(u, v, ctx->mask, flags, ctx->phi[0],
+                                                        ctx->phi[1], ctx->gs, p_out, phi_copy_out,
+                                                        scale, s.ny, s.nx, bc);
     } else {
         correct_kernel<<<grd, blk, 0, st>>>(u, v, ctx->mask, flags, ctx->phi[0], ctx->phi[1],
                                             ctx->gs, p_out, phi_copy_out, scale, s.ny, s.nx, bc);
