@@ -96,16 +96,16 @@ constexpr int kQuadThreads = 128;
 // mask_div_kernel over quads of cells in column strips (rows a multiple of 4
 // cells, 16-byte aligned v, flags, mask and div): grid (row quads /
 // kQuadThreads, blocks of kDivRows rows, B); each thread walks down kDivRows
-// rows of its quad column, keeping the flags of the row above and of its own row and the v
-// faces north of the row in registers from the row before, so it loads each
-// byte it needs once (one flag word, one float4 of v and the row's u faces per
-// row); rows in pairs, both rows' loads issued before either is used.  The
+// rows of its quad column, keeping the flags of the row above and of its own
+// row and the v faces north of the row in registers from the row before, so
+// it loads each byte it needs once (one flag word, one float4 of v and the
+// row's u faces per row); rows in pairs, both rows' loads issued before either
+// is used (four rows at a time measured no faster, with 80 registers).  The
 // open-face bits of four cells come from byte-wise comparisons of the flag
 // words with their neighbours' words shifted by one byte; the flags left and
 // right of the quad from the neighbouring lanes when they hold them.  (One
 // quad per thread and row, reading the shared rows again through L2, took
 // 167 us for the divergence of 16 x 2048^2; the strips 152 us.)
-// (four rows' loads in flight at a time measured no faster: 80 registers)
 constexpr int kDivRows = 8;
 
 __global__ void __launch_bounds__(kQuadThreads)
@@ -936,8 +936,9 @@ __global__ void __launch_bounds__(kQuadThreads)
 // --------------------------------------------------------- divergence norms
 //
 // E_1 = mean |div u| and E_inf = max |div u| (Sec. 4.1) of a velocity: one
-// 8-byte partial per 256-cell segment of a row, in (grid, row, segment)
-// order, holding the segment's FP32 sum and max of |div| (float2), then per
+// 8-byte partial per 256-cell segment of a row (one cell per thread) or of a
+// block of kNormRows rows (column strips), in (grid, row or row block,
+// segment) order, holding the FP32 sum and max of |div| (float2), then per
 // grid the FP64 sum of the sums in a fixed order and the max of the maxima.
 // No atomics: every partial has one writer, and E_1 is the same on every call.
 
